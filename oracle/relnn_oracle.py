@@ -1,0 +1,280 @@
+"""FP64 CPU oracle for RelaNN rule evaluation -- TEST INFRASTRUCTURE ONLY.
+
+This module is the plain, slow, obviously-correct definition of what the GPU path computes. Only the
+test suite, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of ``bench.py`` may
+import it; the library never does. It shares no code with the CUDA path.
+
+Every floating-point step runs in float64. Inputs that the device holds in bf16 are passed in after
+rounding to bf16 (an exact upcast), so both sides see the same values.
+
+Definitions followed (paper sections):
+  * embedded relation (r, eta): content tuples plus one embedding per tuple          -- Sec. 2.1
+  * join: natural join on shared attributes; embedding = concatenation eta1 (+) eta2   -- Sec. 2.2
+  * projected union with aggregator alpha: group by the projected key, alpha over the
+    multiset B_t of contributing tuples (alpha = SUM here)                            -- Sec. 2.2
+  * transformation T_tau: tau applied to each tuple embedding independently            -- Sec. 2.2
+  * join rule R(x; alpha(tau)) :- R1,...,Rk  ==  U_{alpha,x}(T_tau(R1 |><| ... |><| Rk)) -- Sec. 3.1
+  * union rule / "|..." replicator: branch results added by the head's sum             -- Sec. 3.1, 3.7
+  * fit: parameters (weights and per-tuple embeddings) minimise a loss relation        -- Sec. 2.3, 3.2, 3.6
+
+Readings where the paper is silent (each is listed with its reason in the design notes):
+  * bag semantics: every E row is a distinct tuple, duplicate H keys each match;
+  * a tuple whose key is absent from H is dropped by the join;
+  * output keys are exactly the keys with >= 1 contributing tuple, sorted ascending;
+  * Concat order is (z_src, z_dst[, r_edge]); Linear is y = x W^T + b with W [d_out, d_in];
+  * ReLU (when present) is applied per tuple, inside the SUM.
+
+Parity status: every function here is pinned by ``tests/test_oracle.py`` (nested-loop brute force,
+closed forms, invariants, finite differences, a hand-derived golden fixture).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "key_index", "join", "join_pairs", "join_cardinality", "concat_rows", "group_sum",
+    "rule_forward", "rule_backward", "mse", "mse_grad", "stacked_forward", "stacked_backward",
+]
+
+CHUNK = 1 << 20  # join triples processed per NumPy block in the Linear/SUM steps
+
+
+def key_index(h_ids) -> dict:
+    """Key -> list of H row numbers, in row order (a bag: every duplicate row is kept). Sec. 2.2."""
+    idx: dict = {}
+    for row, k in enumerate(np.asarray(h_ids).tolist()):
+        idx.setdefault(k, []).append(row)
+    return idx
+
+
+def join_pairs(probe_keys, build_keys):
+    """One-sided equi-join P(k) |><| B(k) under bag semantics (Sec. 2.2 Join).
+
+    Returns int64 arrays (probe_row, build_row), ordered by probe row then build row."""
+    idx = key_index(build_keys)
+    pr, br = [], []
+    for i, k in enumerate(np.asarray(probe_keys).tolist()):
+        rows = idx.get(k)
+        if rows:
+            for b in rows:
+                pr.append(i)
+                br.append(b)
+    return np.asarray(pr, np.int64), np.asarray(br, np.int64)
+
+
+def join(src, dst, h_ids, join_dst: bool = True):
+    """E(src, dst) |><| H(src) [|><| H(dst)] under bag semantics (Sec. 2.2 Join, Sec. 3.1 rule body).
+
+    Returns int64 arrays (e, hs, hd): one entry per join output tuple, ordered by E row, then the
+    src-side H row, then the dst-side H row. With ``join_dst`` false the dst key is carried as
+    content only and hd is -1."""
+    idx = key_index(h_ids)
+    e_l, hs_l, hd_l = [], [], []
+    none = [-1]
+    for e, (s, d) in enumerate(zip(np.asarray(src).tolist(), np.asarray(dst).tolist())):
+        rs = idx.get(s)
+        if not rs:
+            continue
+        rd = idx.get(d) if join_dst else none
+        if not rd:
+            continue
+        for a in rs:
+            for b in rd:
+                e_l.append(e)
+                hs_l.append(a)
+                hd_l.append(b)
+    return (np.asarray(e_l, np.int64), np.asarray(hs_l, np.int64), np.asarray(hd_l, np.int64))
+
+
+def join_cardinality(src, dst, h_ids, join_dst: bool = True) -> int:
+    """|E |><| H |><| H| = sum over E rows of cnt_H(src) * cnt_H(dst) (bag semantics)."""
+    cnt: dict = {}
+    for k in np.asarray(h_ids).tolist():
+        cnt[k] = cnt.get(k, 0) + 1
+    total = 0
+    for s, d in zip(np.asarray(src).tolist(), np.asarray(dst).tolist()):
+        total += cnt.get(s, 0) * (cnt.get(d, 0) if join_dst else 1)
+    return total
+
+
+def concat_rows(z, r, e, hs, hd, concat_dst: bool = True):
+    """X_t = z[hs_t] (+) z[hd_t] (+) r[e_t] in float64 (Sec. 2.2 Join embedding semantics)."""
+    z = np.asarray(z, np.float64)
+    parts = [z[hs]]
+    if concat_dst:
+        parts.append(z[hd])
+    if r is not None:
+        parts.append(np.asarray(r, np.float64)[e])
+    return np.concatenate(parts, axis=1)
+
+
+def group_sum(keys, values):
+    """Projected union with alpha = SUM (Sec. 2.2): sorted distinct keys and per-key sums."""
+    uk, inv = np.unique(np.asarray(keys), return_inverse=True)
+    out = np.zeros((uk.size, values.shape[1]), np.float64)
+    np.add.at(out, inv.reshape(-1), values)
+    return uk, out
+
+
+def _tau(X, W, b, act):
+    """T_tau with tau = [ReLU o] Linear (Sec. 2.2 Transformation): y = x W^T + b per tuple."""
+    if W is None:
+        Y = X.copy()
+    else:
+        Y = X @ np.asarray(W, np.float64).T
+        if b is not None:
+            Y = Y + np.asarray(b, np.float64)
+    if act == "relu":
+        Y = np.maximum(Y, 0.0)
+    return Y
+
+
+def rule_forward(h_ids, z, branches, act: str = "none", join_dst: bool = True,
+                 concat_dst: bool = True):
+    """Evaluate H'(dst; SUM(tau(Concat(...)))) :- E_i(src, dst[; r]), H(src; z_src), H(dst; z_dst)
+    for every branch i and add the branch results (Sec. 3.1 join rule; union rule and the "|..."
+    replicator of Sec. 3.7 for several branches).
+
+    ``branches``: sequence of objects with fields src, dst, r (or None), W (or None = identity), b.
+    Returns (out_keys sorted ascending, out_z float64 [n_out, d_out], join sizes per branch)."""
+    acc: dict = {}
+    sizes = []
+    for br in branches:
+        e, hs, hd = join(br.src, br.dst, h_ids, join_dst)
+        sizes.append(int(e.size))
+        dst = np.asarray(br.dst)
+        for lo in range(0, e.size, CHUNK):
+            sl = slice(lo, lo + CHUNK)
+            X = concat_rows(z, br.r, e[sl], hs[sl], hd[sl], concat_dst)
+            Y = _tau(X, br.W, br.b, act)
+            uk, part = group_sum(dst[e[sl]], Y)
+            for k, row in zip(uk.tolist(), part):
+                if k in acc:
+                    acc[k] = acc[k] + row
+                else:
+                    acc[k] = row
+    keys = sorted(acc)
+    d_out = _out_dim(z, branches, concat_dst)
+    out = np.stack([acc[k] for k in keys]) if keys else np.zeros((0, d_out))
+    key_dtype = np.asarray(h_ids).dtype if join_dst else np.asarray(branches[0].dst).dtype
+    return np.asarray(keys, key_dtype), out, sizes
+
+
+def _out_dim(z, branches, concat_dst):
+    br = branches[0]
+    if br.W is not None:
+        return int(np.asarray(br.W).shape[0])
+    d = np.asarray(z).shape[1] * (2 if concat_dst else 1)
+    return d + (0 if br.r is None else np.asarray(br.r).shape[1])
+
+
+def rule_backward(h_ids, z, branches, dout_keys, dout, act: str = "none", join_dst: bool = True,
+                  concat_dst: bool = True):
+    """Chain rule through the rule of ``rule_forward`` in float64 (the fit of Sec. 2.3 optimises the
+    weights and the per-tuple embeddings, Sec. 3.6).
+
+    SUM backward broadcasts dOut[dst] to every contributing tuple; ReLU masks by the recomputed
+    pre-activation; Linear gives dW = dY^T X, db = sum dY, dX = dY W; Concat backward splits dX and
+    adds each slice to the embedding row it was gathered from.
+
+    Returns (dW list, db list, dz [n_h, d], dr list (None where a branch has no r))."""
+    z64 = np.asarray(z, np.float64)
+    d = z64.shape[1]
+    dz = np.zeros_like(z64)
+    pos = {k: i for i, k in enumerate(np.asarray(dout_keys).tolist())}
+    dout = np.asarray(dout, np.float64)
+    dWs, dbs, drs = [], [], []
+    for br in branches:
+        e, hs, hd = join(br.src, br.dst, h_ids, join_dst)
+        dst = np.asarray(br.dst)
+        W = None if br.W is None else np.asarray(br.W, np.float64)
+        dW = None if W is None else np.zeros_like(W)
+        db = None if W is None else np.zeros(W.shape[0])
+        dr = None if br.r is None else np.zeros(np.asarray(br.r).shape, np.float64)
+        for lo in range(0, e.size, CHUNK):
+            sl = slice(lo, lo + CHUNK)
+            X = concat_rows(z, br.r, e[sl], hs[sl], hd[sl], concat_dst)
+            rows = np.asarray([pos[k] for k in dst[e[sl]].tolist()], np.int64)
+            G = dout[rows]
+            if act == "relu":
+                pre = _tau(X, W, br.b, "none")
+                G = G * (pre > 0.0)
+            if W is not None:
+                dW += G.T @ X
+                db += G.sum(axis=0)
+                dX = G @ W
+            else:
+                dX = G
+            np.add.at(dz, hs[sl], dX[:, :d])
+            off = d
+            if concat_dst:
+                np.add.at(dz, hd[sl], dX[:, d:2 * d])
+                off = 2 * d
+            if dr is not None:
+                np.add.at(dr, e[sl], dX[:, off:])
+        dWs.append(dW)
+        dbs.append(db)
+        drs.append(dr)
+    return dWs, dbs, dz, drs
+
+
+def mse(pred_keys, pred, target_keys, target):
+    """Loss relation L(; mean((zp - zt)^2)) :- Pred(g; zp), Target(g; zt): a join on g, then the
+    mean over every embedding cell of the joined pairs (Sec. 3.2 loss relation of arity 0)."""
+    pos = {k: i for i, k in enumerate(np.asarray(target_keys).tolist())}
+    pairs = [(i, pos[k]) for i, k in enumerate(np.asarray(pred_keys).tolist()) if k in pos]
+    if not pairs:
+        return 0.0
+    p = np.asarray(pred, np.float64)[[a for a, _ in pairs]]
+    t = np.asarray(target, np.float64)[[b for _, b in pairs]]
+    return float(np.mean((p - t) ** 2))
+
+
+def mse_grad(pred_keys, pred, target_keys, target):
+    """d mse / d pred (rows of pred that join no target get zero gradient)."""
+    pos = {k: i for i, k in enumerate(np.asarray(target_keys).tolist())}
+    pred = np.asarray(pred, np.float64)
+    g = np.zeros_like(pred)
+    rows = [(i, pos[k]) for i, k in enumerate(np.asarray(pred_keys).tolist()) if k in pos]
+    n = len(rows) * pred.shape[1]
+    for i, j in rows:
+        g[i] = 2.0 * (pred[i] - np.asarray(target[j], np.float64)) / n
+    return g
+
+
+class _Br:
+    """Plain branch record (src, dst, r, W, b) for the stacked program."""
+
+    def __init__(self, src, dst, W, b, r=None):
+        self.src, self.dst, self.W, self.b, self.r = src, dst, W, b, r
+
+
+def stacked_forward(h_ids, z, src, dst, W1, b1, W2, b2, g_keys, g_groups, t_groups, targets):
+    """Two stacked rules and a SUM readout with an MSE loss:
+
+        H1(d; SUM ReLU(Linear1(Concat(z_s, z_d)))) :- E(s, d), H(s; z_s), H(d; z_d)
+        H2(d; SUM Linear2(Concat(z_s, z_d)))       :- E(s, d), H1(s; z_s), H1(d; z_d)
+        Out(g; SUM z)                              :- H2(k; z), G(k, g)
+        L(; mean((z_o - z_t)^2))                   :- Out(g; z_o), T(g; z_t)
+
+    Returns a dict with every intermediate relation and the loss."""
+    k1, h1, _ = rule_forward(h_ids, z, [_Br(src, dst, W1, b1)], act="relu")
+    k2, h2, _ = rule_forward(k1, h1, [_Br(src, dst, W2, b2)], act="none")
+    ko, ho, _ = rule_forward(k2, h2, [_Br(g_keys, g_groups, None, None)], join_dst=False,
+                             concat_dst=False)
+    loss = mse(ko, ho, t_groups, targets)
+    return dict(k1=k1, h1=h1, k2=k2, h2=h2, ko=ko, ho=ho, loss=loss)
+
+
+def stacked_backward(h_ids, z, src, dst, W1, b1, W2, b2, g_keys, g_groups, t_groups, targets,
+                     fwd=None):
+    """Analytic float64 gradient of ``stacked_forward``'s loss w.r.t. W1, b1, W2, b2 and z."""
+    f = fwd if fwd is not None else stacked_forward(h_ids, z, src, dst, W1, b1, W2, b2, g_keys,
+                                                    g_groups, t_groups, targets)
+    d_ho = mse_grad(f["ko"], f["ho"], t_groups, targets)
+    _, _, d_h2, _ = rule_backward(f["k2"], f["h2"], [_Br(g_keys, g_groups, None, None)], f["ko"],
+                                  d_ho, join_dst=False, concat_dst=False)
+    (dW2,), (db2,), d_h1, _ = rule_backward(f["k1"], f["h1"], [_Br(src, dst, W2, b2)], f["k2"], d_h2)
+    (dW1,), (db1,), dz, _ = rule_backward(h_ids, z, [_Br(src, dst, W1, b1)], f["k1"], d_h1,
+                                          act="relu")
+    return dict(dW1=dW1, db1=db1, dW2=dW2, db2=db2, dz=dz, d_h1=d_h1, d_h2=d_h2, d_ho=d_ho)

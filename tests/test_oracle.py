@@ -1,0 +1,390 @@
+"""Pins for the FP64 oracle against things other than itself (CPU only).
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term, a swapped operand, a
+wrong index, set instead of bag semantics) fails at least one of them:
+  * nested-loop brute force over E x H x H (join, Linear, SUM written as explicit loops);
+  * the join cardinality identity |E |><| H |><| H| = sum_e cnt_H(src_e) * cnt_H(dst_e);
+  * closed forms: W = [I;0], b = 0 equals a sparse incidence product (scipy); W = [0;I] gives
+    deg(k) z_k; W = 0 gives deg(k) b;
+  * union = sum of branches; invariance under row permutations of E and H; linearity in (W, b);
+  * a hand-derived golden example (tests/golden/hand_rule.json);
+  * central finite differences (h = 1e-3) and the adjoint identity for the backward.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import relnn_oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "hand_rule.json")
+
+
+class Br:
+    def __init__(self, src, dst, W, b, r=None):
+        self.src, self.dst, self.W, self.b, self.r = src, dst, W, b, r
+
+
+def tiny(seed, n_e=40, n_h=12, d=3, d_out=4, d_r=0, key_range=10, key_dtype=np.int64, neg=False):
+    """Tiny relations with duplicate H keys, keys missing from H and (optionally) negative keys."""
+    rng = np.random.default_rng(seed)
+    lo = -key_range if neg else 0
+    h_ids = rng.integers(lo, key_range, size=n_h).astype(key_dtype)
+    z = rng.standard_normal((n_h, d))
+    src = rng.integers(lo, key_range + 3, size=n_e).astype(key_dtype)
+    dst = rng.integers(lo, key_range + 3, size=n_e).astype(key_dtype)
+    d_in = 2 * d + d_r
+    W = rng.standard_normal((d_out, d_in))
+    b = rng.standard_normal(d_out)
+    r = rng.standard_normal((n_e, d_r)) if d_r else None
+    return h_ids, z, Br(src, dst, W, b, r)
+
+
+# ----------------------------------------------------------------------------- brute force
+def brute_join(src, dst, h_ids, join_dst=True):
+    out = []
+    for e in range(len(src)):
+        for a in range(len(h_ids)):
+            if h_ids[a] != src[e]:
+                continue
+            if not join_dst:
+                out.append((e, a, -1))
+                continue
+            for c in range(len(h_ids)):
+                if h_ids[c] == dst[e]:
+                    out.append((e, a, c))
+    return sorted(out)
+
+
+def brute_rule(h_ids, z, branches, act="none", join_dst=True, concat_dst=True):
+    acc = {}
+    for br in branches:
+        for (e, a, c) in brute_join(br.src, br.dst, h_ids, join_dst):
+            x = list(z[a])
+            if concat_dst:
+                x += list(z[c])
+            if br.r is not None:
+                x += list(br.r[e])
+            if br.W is None:
+                y = x
+            else:
+                y = []
+                for o in range(len(br.W)):
+                    s = br.b[o]
+                    for k in range(len(x)):
+                        s += br.W[o][k] * x[k]
+                    y.append(s)
+            if act == "relu":
+                y = [v if v > 0 else 0.0 for v in y]
+            key = br.dst[e]
+            if key not in acc:
+                acc[key] = [0.0] * len(y)
+            acc[key] = [p + q for p, q in zip(acc[key], y)]
+    keys = sorted(acc)
+    return keys, np.array([acc[k] for k in keys])
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("join_dst", [True, False])
+def test_join_matches_nested_loops(seed, join_dst):
+    h_ids, z, br = tiny(seed, neg=(seed % 2 == 1), key_dtype=np.int32 if seed % 3 == 0 else np.int64)
+    e, hs, hd = O.join(br.src, br.dst, h_ids, join_dst)
+    got = sorted(zip(e.tolist(), hs.tolist(), hd.tolist()))
+    assert got == brute_join(br.src.tolist(), br.dst.tolist(), h_ids.tolist(), join_dst)
+    # the oracle's own order is already (e, hs, hd) ascending
+    assert list(zip(e.tolist(), hs.tolist(), hd.tolist())) == got
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_join_cardinality_identity(seed):
+    h_ids, z, br = tiny(seed, n_e=64, n_h=20, key_range=6)
+    e, _, _ = O.join(br.src, br.dst, h_ids)
+    cnt = {}
+    for k in h_ids.tolist():
+        cnt[k] = cnt.get(k, 0) + 1
+    expect = sum(cnt.get(s, 0) * cnt.get(d, 0) for s, d in zip(br.src.tolist(), br.dst.tolist()))
+    assert e.size == expect == O.join_cardinality(br.src, br.dst, h_ids)
+    # one-sided form: sum over keys of c_probe(k) * c_build(k)
+    pr, bu = O.join_pairs(br.src, h_ids)
+    cp = {}
+    for k in br.src.tolist():
+        cp[k] = cp.get(k, 0) + 1
+    assert pr.size == sum(c * cnt.get(k, 0) for k, c in cp.items())
+    assert sorted(zip(pr.tolist(), bu.tolist())) == sorted(
+        (i, j) for i in range(br.src.size) for j in range(h_ids.size) if br.src[i] == h_ids[j])
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("act", ["none", "relu"])
+def test_forward_matches_brute_force(seed, act):
+    h_ids, z, br = tiny(seed, d_r=2 if seed % 2 else 0)
+    keys, out, sizes = O.rule_forward(h_ids, z, [br], act=act)
+    bk, bo = brute_rule(h_ids, z, [br], act=act)
+    assert keys.tolist() == bk
+    np.testing.assert_allclose(out, bo, rtol=1e-12, atol=1e-12)
+    assert sizes[0] == len(brute_join(br.src, br.dst, h_ids))
+
+
+def test_forward_readout_form_matches_brute_force():
+    h_ids, z, br = tiny(7)
+    br.W, br.b = None, None
+    keys, out, _ = O.rule_forward(h_ids, z, [br], join_dst=False, concat_dst=False)
+    bk, bo = brute_rule(h_ids, z, [br], join_dst=False, concat_dst=False)
+    assert keys.tolist() == bk
+    np.testing.assert_allclose(out, bo, rtol=1e-12, atol=1e-12)
+
+
+def test_union_matches_brute_force_and_is_sum_of_branches():
+    h_ids, z, b1 = tiny(11, d_r=2)
+    _, _, b2 = tiny(12, d_r=2)
+    _, _, b3 = tiny(13, d_r=2)
+    b2.W = np.random.default_rng(5).standard_normal(b1.W.shape)
+    keys, out, _ = O.rule_forward(h_ids, z, [b1, b2, b3])
+    bk, bo = brute_rule(h_ids, z, [b1, b2, b3])
+    assert keys.tolist() == bk
+    np.testing.assert_allclose(out, bo, rtol=1e-12, atol=1e-12)
+    acc = {}
+    for br in (b1, b2, b3):
+        k, o, _ = O.rule_forward(h_ids, z, [br])
+        for kk, row in zip(k.tolist(), o):
+            acc[kk] = acc.get(kk, 0) + row
+    np.testing.assert_allclose(out, np.array([acc[k] for k in keys.tolist()]), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_identity_linear_is_sparse_incidence_product(seed):
+    """W = [I; 0], b = 0: H'[k] = sum over matched tuples with dst = k of z[hs] = A^T Z, where A is
+    the (tuple x H-row) incidence of the src side restricted to tuples whose dst matches."""
+    h_ids, z, br = tiny(seed, n_e=80, n_h=15, d=3, d_out=3, key_range=8)
+    d = z.shape[1]
+    br.W = np.concatenate([np.eye(d), np.zeros((d, d))], axis=1)
+    br.b = np.zeros(d)
+    keys, out, _ = O.rule_forward(h_ids, z, [br])
+    # independent construction with scipy.sparse: rows = distinct output keys, cols = H rows
+    cnt = {}
+    for k in h_ids.tolist():
+        cnt[k] = cnt.get(k, 0) + 1
+    uk = sorted({dd for s, dd in zip(br.src.tolist(), br.dst.tolist()) if s in cnt and dd in cnt})
+    rowpos = {k: i for i, k in enumerate(uk)}
+    rr, cc = [], []
+    for s, dd in zip(br.src.tolist(), br.dst.tolist()):
+        if s in cnt and dd in cnt:
+            for j in range(h_ids.size):
+                if h_ids[j] == s:
+                    for _ in range(cnt[dd]):
+                        rr.append(rowpos[dd])
+                        cc.append(j)
+    A = sp.coo_matrix((np.ones(len(rr)), (rr, cc)), shape=(len(uk), h_ids.size)).tocsr()
+    assert keys.tolist() == uk
+    np.testing.assert_allclose(out, A @ z, rtol=1e-12, atol=1e-12)
+
+
+def _deg(br, h_ids, keys):
+    cnt = {}
+    for k in h_ids.tolist():
+        cnt[k] = cnt.get(k, 0) + 1
+    deg = {}
+    for s, d in zip(br.src.tolist(), br.dst.tolist()):
+        m = cnt.get(s, 0) * cnt.get(d, 0)
+        if m:
+            deg[d] = deg.get(d, 0) + m
+    return np.array([deg[k] for k in keys.tolist()], np.float64)
+
+
+def test_closed_forms_dst_identity_and_zero_weight():
+    h_ids, z, br = tiny(3, n_e=60, n_h=10, key_range=12)
+    # unique H keys so that z_dst is the embedding of the key itself
+    h_ids = np.arange(10, dtype=np.int64) * 3 - 7
+    br.src = h_ids[np.random.default_rng(1).integers(0, 10, 60)]
+    br.dst = h_ids[np.random.default_rng(2).integers(0, 10, 60)]
+    d = z.shape[1]
+    br.W = np.concatenate([np.zeros((d, d)), np.eye(d)], axis=1)
+    br.b = np.zeros(d)
+    keys, out, _ = O.rule_forward(h_ids, z, [br])
+    deg = _deg(br, h_ids, keys)
+    zk = np.array([z[h_ids.tolist().index(k)] for k in keys.tolist()])
+    np.testing.assert_allclose(out, deg[:, None] * zk, rtol=1e-12, atol=1e-12)
+    br.W = np.zeros((4, 2 * d))
+    br.b = np.array([1.0, -2.0, 0.5, 3.0])
+    keys, out, _ = O.rule_forward(h_ids, z, [br])
+    np.testing.assert_allclose(out, _deg(br, h_ids, keys)[:, None] * br.b[None, :], rtol=1e-12)
+
+
+def test_permutation_invariance():
+    h_ids, z, br = tiny(21, n_e=70, d_r=2)
+    keys, out, _ = O.rule_forward(h_ids, z, [br])
+    rng = np.random.default_rng(0)
+    pe = rng.permutation(br.src.size)
+    ph = rng.permutation(h_ids.size)
+    br2 = Br(br.src[pe], br.dst[pe], br.W, br.b, br.r[pe])
+    k2, o2, _ = O.rule_forward(h_ids[ph], z[ph], [br2])
+    assert k2.tolist() == keys.tolist()
+    np.testing.assert_allclose(o2, out, rtol=1e-11, atol=1e-11)
+
+
+def test_linearity_in_weights():
+    h_ids, z, br = tiny(22, n_e=50)
+    rng = np.random.default_rng(3)
+    W2, b2 = rng.standard_normal(br.W.shape), rng.standard_normal(br.b.shape)
+    a, c = 0.7, -1.3
+    k1, o1, _ = O.rule_forward(h_ids, z, [br])
+    _, o2, _ = O.rule_forward(h_ids, z, [Br(br.src, br.dst, W2, b2)])
+    _, o3, _ = O.rule_forward(h_ids, z, [Br(br.src, br.dst, a * br.W + c * W2, a * br.b + c * b2)])
+    np.testing.assert_allclose(o3, a * o1 + c * o2, rtol=1e-11, atol=1e-11)
+
+
+# ----------------------------------------------------------------------------- golden
+def test_golden_hand_example():
+    g = json.load(open(GOLD))
+    h = np.array(g["h_ids"], np.int64)
+    z = np.array(g["z"], np.float64)
+    br = Br(np.array(g["src"]), np.array(g["dst"]), np.array(g["W"], float), np.array(g["b"], float))
+    e, hs, hd = O.join(br.src, br.dst, h)
+    assert [list(t) for t in zip(e.tolist(), hs.tolist(), hd.tolist())] == g["triples"]
+    keys, out, _ = O.rule_forward(h, z, [br])
+    assert keys.tolist() == g["out_keys"]
+    assert out.tolist() == g["out"]
+    _, out_r, _ = O.rule_forward(h, z, [br], act="relu")
+    assert out_r.tolist() == g["out_relu"]
+    br2 = Br(np.array(g["src2"]), np.array(g["dst2"]), np.array(g["W2"], float), np.array(g["b2"], float))
+    _, out_u, _ = O.rule_forward(h, z, [br, br2])
+    assert out_u.tolist() == g["out_union"]
+    dW, db, dz, _ = O.rule_backward(h, z, [br], keys, np.ones_like(out))
+    assert dW[0].tolist() == g["dW_ones"]
+    assert db[0].tolist() == g["db_ones"]
+    assert dz.tolist() == g["dz_ones"]
+
+
+# ----------------------------------------------------------------------------- backward
+def _loss(h_ids, z, brs, act, C):
+    keys, out, _ = O.rule_forward(h_ids, z, brs, act=act)
+    return float(np.sum(C[: out.shape[0]] * out)), keys, out
+
+
+@pytest.mark.parametrize("act", ["none", "relu"])
+def test_backward_finite_differences(act):
+    h_ids, z, br = tiny(31, n_e=30, n_h=10, d=3, d_out=4, d_r=2)
+    keys, out, _ = O.rule_forward(h_ids, z, [br], act=act)
+    C = np.random.default_rng(4).standard_normal(out.shape)
+    if act == "relu":
+        # keep every pre-activation away from the kink so that h = 1e-3 stays on one side
+        e, hs, hd = O.join(br.src, br.dst, h_ids)
+        pre = O.concat_rows(z, br.r, e, hs, hd) @ br.W.T + br.b
+        assert np.min(np.abs(pre)) > 1e-2
+    dW, db, dz, dr = O.rule_backward(h_ids, z, [br], keys, C, act=act)
+    h = 1e-3
+    rng = np.random.default_rng(9)
+
+    def fd(arr, idx, setter):
+        old = arr[idx]
+        arr[idx] = old + h
+        lp = _loss(h_ids, z, [br], act, C)[0]
+        arr[idx] = old - h
+        lm = _loss(h_ids, z, [br], act, C)[0]
+        arr[idx] = old
+        return (lp - lm) / (2 * h)
+
+    for _ in range(6):
+        i = tuple(rng.integers(0, s) for s in br.W.shape)
+        assert fd(br.W, i, None) == pytest.approx(dW[0][i], rel=1e-6, abs=1e-8)
+        j = int(rng.integers(0, br.b.size))
+        assert fd(br.b, j, None) == pytest.approx(db[0][j], rel=1e-6, abs=1e-8)
+        k = tuple(rng.integers(0, s) for s in z.shape)
+        assert fd(z, k, None) == pytest.approx(dz[k], rel=1e-6, abs=1e-8)
+        m = tuple(rng.integers(0, s) for s in br.r.shape)
+        assert fd(br.r, m, None) == pytest.approx(dr[0][m], rel=1e-6, abs=1e-8)
+
+
+def test_backward_adjoint_identity():
+    """<dOut, J v> = <J^T dOut, v> for the map (z, r) -> H' at fixed weights (linear when act=none)."""
+    h_ids, z, br = tiny(41, n_e=40, n_h=12, d=3, d_out=5, d_r=2)
+    rng = np.random.default_rng(2)
+    br.b = np.zeros_like(br.b)  # pure linear map in (z, r)
+    keys, out, _ = O.rule_forward(h_ids, z, [br])
+    dout = rng.standard_normal(out.shape)
+    vz, vr = rng.standard_normal(z.shape), rng.standard_normal(br.r.shape)
+    _, Jv, _ = O.rule_forward(h_ids, vz, [Br(br.src, br.dst, br.W, br.b, vr)])
+    _, _, dz, dr = O.rule_backward(h_ids, z, [br], keys, dout)
+    lhs = float(np.sum(dout * Jv))
+    rhs = float(np.sum(dz * vz) + np.sum(dr[0] * vr))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def _stacked_case(seed=0):
+    rng = np.random.default_rng(seed)
+    K, T, d = 14, 60, 4
+    h_ids = rng.permutation(K).astype(np.int64) * 5
+    z = rng.standard_normal((K, d))
+    src = h_ids[rng.integers(0, K, T)]
+    dst = h_ids[rng.integers(0, K, T)]
+    W1, b1 = rng.standard_normal((d, 2 * d)) * 0.5, rng.standard_normal(d) * 0.5
+    W2, b2 = rng.standard_normal((d, 2 * d)) * 0.5, rng.standard_normal(d) * 0.5
+    g_groups = rng.integers(0, 3, K).astype(np.int64)
+    t_groups = np.arange(3, dtype=np.int64)
+    targets = rng.standard_normal((3, d))
+    return h_ids, z, src, dst, W1, b1, W2, b2, h_ids.copy(), g_groups, t_groups, targets
+
+
+def test_stacked_gradient_finite_differences():
+    args = list(_stacked_case())
+    f = O.stacked_forward(*args)
+    g = O.stacked_backward(*args, fwd=f)
+    h = 1e-3
+    rng = np.random.default_rng(1)
+    names = {1: "dz", 4: "dW1", 5: "db1", 6: "dW2", 7: "db2"}
+    checked = 0
+    for pos, gname in names.items():
+        arr = args[pos]
+        for _ in range(5):
+            i = tuple(int(rng.integers(0, s)) for s in arr.shape)
+            old = arr[i]
+            arr[i] = old + h
+            lp = O.stacked_forward(*args)["loss"]
+            arr[i] = old - h
+            lm = O.stacked_forward(*args)["loss"]
+            arr[i] = old
+            fd = (lp - lm) / (2 * h)
+            assert fd == pytest.approx(g[gname][i], rel=1e-4, abs=1e-6)
+            checked += 1
+    assert checked == 25
+
+
+def test_mse_matches_definition_and_gradient():
+    pk = np.array([0, 1, 2, 5])
+    p = np.arange(8.0).reshape(4, 2)
+    tk = np.array([2, 0, 1])
+    t = np.array([[1.0, 1.0], [0.0, 0.0], [2.0, 2.0]])
+    # joined pairs: 0<->t[1], 1<->t[2], 2<->t[0]; key 5 joins nothing
+    want = np.mean(np.array([[0, 1], [0, 1], [3, 4]], float) ** 2)
+    assert O.mse(pk, p, tk, t) == pytest.approx(want)
+    g = O.mse_grad(pk, p, tk, t)
+    assert g[3].tolist() == [0.0, 0.0]
+    assert g[2].tolist() == [2 * 3 / 6, 2 * 4 / 6]
+
+
+# ----------------------------------------------------------------------------- planted mistakes
+def test_pins_detect_planted_mistakes(monkeypatch):
+    """Plant typical slips in the oracle (on the CPU) and check that a pin above catches each."""
+    g = json.load(open(GOLD))
+    h = np.array(g["h_ids"], np.int64)
+    z = np.array(g["z"], np.float64)
+    br = Br(np.array(g["src"]), np.array(g["dst"]), np.array(g["W"], float), np.array(g["b"], float))
+    good = O.rule_forward(h, z, [br])[1].tolist()
+    assert good == g["out"]
+    orig_tau, orig_concat, orig_index = O._tau, O.concat_rows, O.key_index
+
+    # dropped bias term
+    monkeypatch.setattr(O, "_tau", lambda X, W, b, act: orig_tau(X, W, None, act))
+    assert O.rule_forward(h, z, [br])[1].tolist() != g["out"]
+    monkeypatch.setattr(O, "_tau", orig_tau)
+    # swapped Concat order
+    monkeypatch.setattr(O, "concat_rows", lambda z_, r, e, hs, hd, c=True: orig_concat(z_, r, e, hd, hs, c))
+    assert O.rule_forward(h, z, [br])[1].tolist() != g["out"]
+    monkeypatch.setattr(O, "concat_rows", orig_concat)
+    # set semantics on H (first duplicate only)
+    monkeypatch.setattr(O, "key_index", lambda ids: {k: v[:1] for k, v in orig_index(ids).items()})
+    e, _, _ = O.join(br.src, br.dst, h)
+    assert e.size != len(g["triples"])
+    monkeypatch.setattr(O, "key_index", orig_index)
