@@ -1,0 +1,178 @@
+/*
+ * relnn.h -- C ABI of librelnn.so: evaluation of RelaNN rules over embedded relations on one
+ * NVIDIA B300 (sm_103a).
+ *
+ * The operation (paper Sec. 2.2 and Sec. 3.1): a join rule
+ *
+ *     H'(dst; SUM(tau(Concat(z_src, z_dst [, r])))) :- E(src, dst [; r]), H(src; z_src), H(dst; z_dst)
+ *
+ * compiles to U_{SUM,dst}(T_tau(E |><| H |><| H)): an integer-key equi-join of the tuple relation E
+ * with the embedded relation H on both src and dst (bag semantics: duplicate keys all match, a key
+ * absent from H drops the tuple), the concatenation of the matched embeddings (Sec. 2.2, Join), a
+ * per-tuple Linear tau(x) = x W^T + b with optional ReLU (Sec. 2.2, Transformation), and a SUM
+ * group-by on the dst key (Sec. 2.2, Projected union). Several tuple relations E_1..E_n with their
+ * own Linear each ("union rule" / "|..." replicator, Sec. 3.1 and Sec. 3.7) add into one output.
+ *
+ * Conventions for every entry point:
+ *   - Returns relnn_status; no C++ exception crosses the ABI. relnn_last_error() gives a message.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller (the library never frees them);
+ *     h_* pointers are host memory. Handles (join, plan, server) are owned by the library and are
+ *     released only by the matching *_destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls marked
+ *     "async" only enqueue work on it; calls marked "sync" return after the stream has drained.
+ *   - Keys are int32 (RELNN_I32) or int64 (RELNN_I64). INT64_MAX is reserved and rejected as an H
+ *     key. Embeddings are row-major [rows, width] with contiguous rows, f32 or bf16.
+ *   - W uses the torch nn.Linear layout [d_out, d_in] row-major; b is f32 [d_out].
+ *   - Device-side checks never trap: a failed check writes a code to the plan's status word and the
+ *     kernel returns; relnn_plan_check() reports it as RELNN_EDEVICE with relnn_last_device_error().
+ */
+#ifndef RELNN_H
+#define RELNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum relnn_status {
+    RELNN_OK = 0,
+    RELNN_EINVAL = 1,     /* invalid argument (null pointer, bad size, unsupported shape)        */
+    RELNN_ENOMEM = 2,     /* device allocation failed, or a query can never fit the memory budget */
+    RELNN_ENOSPC = 3,     /* caller-provided output capacity too small (required size reported)   */
+    RELNN_EAGAIN = 4,     /* try again: serving queue full, or a ticket not finished yet           */
+    RELNN_ETIMEDOUT = 5,  /* a bounded wait ran out                                                */
+    RELNN_ECUDA = 6,      /* a CUDA runtime/driver call failed                                     */
+    RELNN_EDEVICE = 7,    /* a device-side check failed; code in relnn_last_device_error()         */
+    RELNN_ENOTSUP = 8     /* feature/shape combination not supported by this build                 */
+} relnn_status;
+
+typedef enum relnn_key_t { RELNN_I32 = 0, RELNN_I64 = 1 } relnn_key_t;
+typedef enum relnn_float_t { RELNN_F32 = 0, RELNN_BF16 = 1 } relnn_float_t;
+typedef enum relnn_act_t { RELNN_ACT_NONE = 0, RELNN_ACT_RELU = 1 } relnn_act_t;
+
+/* relnn_rule_desc.flags */
+#define RELNN_FLAG_BF16 0x1u          /* Linear on tcgen05 tensor cores: bf16 operands, f32 accumulate.
+                                         Without it: the FP32 form (f32 FMA on CUDA cores, no TF32). */
+#define RELNN_FLAG_KAHAN 0x2u         /* compensated (Kahan) f32 summation in the SUM group-by        */
+#define RELNN_FLAG_IDENTITY 0x4u      /* tau = identity: no Linear, d_out = width of the Concat        */
+#define RELNN_FLAG_NO_JOIN_DST 0x8u   /* dst is content only: not joined with H, no z_dst; the output
+                                         is keyed by the raw dst value (e.g. a readout into groups)    */
+#define RELNN_FLAG_NO_CONCAT_DST 0x10u /* join H(dst) (it filters tuples) but leave z_dst out of Concat */
+#define RELNN_FLAG_RELU_MASK 0x20u    /* forward stores the per-tuple ReLU mask for a later backward   */
+
+/* Device status codes (relnn_last_device_error) */
+#define RELNN_DEV_OK 0
+#define RELNN_DEV_TIMEOUT 1           /* a bounded spin/mbarrier wait gave up                         */
+#define RELNN_DEV_BOUNDS 2            /* an index failed its bounds check                             */
+#define RELNN_DEV_HASH_FULL 3         /* hash insert found no free slot                               */
+
+typedef struct relnn_join_s* relnn_join_t;
+typedef struct relnn_plan_s* relnn_plan_t;
+typedef struct relnn_server_s* relnn_server_t;
+
+/* ---------------------------------------------------------------------------------------------
+ * Library
+ * ------------------------------------------------------------------------------------------- */
+int32_t relnn_version(void);                      /* 100 * major + minor                          */
+const char* relnn_status_string(relnn_status s);  /* static string                                */
+const char* relnn_last_error(void);               /* calling thread's last error message          */
+int32_t relnn_last_device_error(void);            /* RELNN_DEV_* of the last RELNN_EDEVICE        */
+
+/* ---------------------------------------------------------------------------------------------
+ * Join (paper Sec. 2.2 "Join": natural join on shared attributes; Sec. 4.2: the join emits row-index
+ * tensors). Build side: a key column. Probe side: another key column. Bag semantics.
+ * ------------------------------------------------------------------------------------------- */
+
+/* sync. Builds a lookup structure over d_keys[0..n) (radix-sorted (key,row) pairs plus a hash
+ * table, or a direct-address table when the key range is small). d_keys may be freed after return.
+ * Errors: EINVAL (null/negative n, INT64_MAX key), ENOMEM, ECUDA. */
+relnn_status relnn_join_build(const void* d_keys, int64_t n, relnn_key_t kt, void* stream,
+                              relnn_join_t* out);
+
+/* sync. Emits every matching (probe row, build row) pair of d_probe_keys[0..m) against the build
+ * side into d_probe_idx / d_build_idx (int32, capacity entries each), ordered by probe row and then
+ * by build row. *d_count (device int64) receives the number of pairs. If it exceeds `capacity`,
+ * nothing is written to the index arrays, *d_count holds the required size and RELNN_ENOSPC is
+ * returned. Probe keys must have the build's key type. */
+relnn_status relnn_join_probe(relnn_join_t j, const void* d_probe_keys, int64_t m,
+                              int32_t* d_probe_idx, int32_t* d_build_idx, int64_t capacity,
+                              int64_t* d_count, void* stream);
+
+/* Releases the join's device memory (waits for the device first). */
+relnn_status relnn_join_destroy(relnn_join_t j);
+
+/* ---------------------------------------------------------------------------------------------
+ * Rules (paper Sec. 3.1 join rule, union rule; Sec. 3.7 "|..." replicator).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct relnn_branch_desc {
+    const void* d_src;     /* [n_tuples] keys of E.src (device)                                   */
+    const void* d_dst;     /* [n_tuples] keys of E.dst (device)                                   */
+    int64_t n_tuples;      /* rows of this E relation (< 2^31)                                     */
+    int32_t d_r;           /* width of the per-tuple embedding r (0 = none)                        */
+} relnn_branch_desc;
+
+typedef struct relnn_rule_desc {
+    relnn_key_t key_type;  /* type of H.id, E.src, E.dst                                          */
+    const void* d_h_ids;   /* [n_h] keys of H (device)                                            */
+    int64_t n_h;
+    int32_t d;             /* width of H.z                                                        */
+    int32_t d_out;         /* width of the output embedding (ignored with RELNN_FLAG_IDENTITY)     */
+    int32_t n_branches;    /* >= 1; branches share H and the output key space                     */
+    const relnn_branch_desc* branches;  /* host array [n_branches]                                */
+    relnn_act_t act;
+    uint32_t flags;        /* RELNN_FLAG_*                                                        */
+} relnn_rule_desc;
+
+/* sync. The content track of the rule (join build on H.id, probe of every branch's src and dst,
+ * grouping of the matched tuples by output key), cached in the plan and reused by every forward and
+ * backward (the paper's content caching across training iterations). Key columns may be freed
+ * after return. Errors: EINVAL, ENOTSUP (shape the kernels do not cover), ENOMEM, ECUDA, EDEVICE. */
+relnn_status relnn_rule_plan(const relnn_rule_desc* desc, void* stream, relnn_plan_t* out);
+
+/* Host-side sizes of a plan: number of output rows, total matched (join-output) tuples over all
+ * branches, and the matched tuples of branch i in h_matched[i] (may be NULL). */
+relnn_status relnn_plan_info(relnn_plan_t p, int64_t* n_out, int64_t* n_matched_total,
+                             int64_t* h_matched);
+
+/* async. Writes the sorted output keys ([n_out], plan key type) to d_out_keys. */
+relnn_status relnn_plan_out_keys(relnn_plan_t p, void* d_out_keys, void* stream);
+
+/* sync. Drains `stream` and reports a device-side failure of any earlier call on this plan as
+ * RELNN_EDEVICE (and clears it). */
+relnn_status relnn_plan_check(relnn_plan_t p, void* stream);
+
+typedef struct relnn_rule_params {
+    const void* d_z;               /* H.z [n_h, d]                                                 */
+    relnn_float_t z_dtype;
+    const void* const* d_r;        /* host array [n_branches] of device [n_tuples_i, d_r] or NULL   */
+    relnn_float_t r_dtype;
+    const void* const* d_W;        /* host array [n_branches] of device W_i [d_out, d_in]           */
+    relnn_float_t w_dtype;
+    const float* const* d_b;       /* host array [n_branches] of device b_i [d_out] (or NULL = 0)   */
+} relnn_rule_params;
+
+/* async. Forward of the rule: d_out_z [n_out, d_out] f32 receives, for each output key (sorted as
+ * relnn_plan_out_keys), the SUM over every branch's matched tuples with that dst key of
+ * tau(Concat(...)). d_out_keys (may be NULL) receives the keys; d_out_count (device int64, may be
+ * NULL) receives n_out. d_out_z is fully overwritten. Concat widths: the BF16 form needs d and d_r
+ * to be multiples of 8 and d_in, d_out <= 256; the FP32 form needs d_in, d_out <= 256. */
+relnn_status relnn_rule_forward(relnn_plan_t p, const relnn_rule_params* prm, void* d_out_keys,
+                                float* d_out_z, int64_t* d_out_count, void* stream);
+
+/* async. Backward of relnn_rule_forward for the output gradient d_dout [n_out, d_out] f32:
+ * d_dW[i] [d_out, d_in] f32, d_db[i] [d_out] f32, d_dz [n_h, d] f32 and d_dr[i] [n_tuples_i, d_r]
+ * f32 are OVERWRITTEN with the gradients (any of the host arrays or entries may be NULL to skip).
+ * The gathered Concat rows are recomputed, not stored. With act = RELU the plan's forward must have
+ * run with RELNN_FLAG_RELU_MASK (the mask is kept in the plan). */
+relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, const float* d_dout,
+                                 float* const* d_dW, float* const* d_db, float* d_dz,
+                                 float* const* d_dr, void* stream);
+
+/* Releases the plan's device memory (waits for the device first). */
+relnn_status relnn_plan_destroy(relnn_plan_t p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RELNN_H */

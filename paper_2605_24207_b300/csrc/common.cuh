@@ -1,0 +1,154 @@
+// Internal helpers shared by the librelnn translation units: status plumbing, device status word,
+// bounded waits, key encodings and small device utilities.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/relnn.h"
+
+namespace relnn {
+
+// ----------------------------------------------------------------------------------- host errors
+void set_error(const std::string& msg);
+void set_device_error(int32_t code);
+
+#define RELNN_CHECK_ARG(cond, msg)                  \
+    do {                                           \
+        if (!(cond)) {                             \
+            ::relnn::set_error(msg);               \
+            return RELNN_EINVAL;                   \
+        }                                          \
+    } while (0)
+
+#define RELNN_CUDA(call)                                                                      \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            ::relnn::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));           \
+            return e_ == cudaErrorMemoryAllocation ? RELNN_ENOMEM : RELNN_ECUDA;              \
+        }                                                                                     \
+    } while (0)
+
+#define RELNN_TRY(expr)                     \
+    do {                                    \
+        relnn_status s_ = (expr);           \
+        if (s_ != RELNN_OK) return s_;      \
+    } while (0)
+
+// Stream-ordered device buffer owned by a handle (freed by the handle's destructor).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    relnn_status alloc(size_t n) {
+        if (n <= bytes && p) return RELNN_OK;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error(std::string("cudaMalloc(") + std::to_string(n) + "): " + cudaGetErrorString(e));
+            return RELNN_ENOMEM;
+        }
+        bytes = n;
+        return RELNN_OK;
+    }
+    template <class T>
+    T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+inline int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// ----------------------------------------------------------------------------------- device side
+// Wall-clock budget for any spin or mbarrier wait inside a kernel (nanoseconds).
+constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void raise_status(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// Order-preserving maps from signed keys to unsigned integers (for radix sorting).
+__device__ __forceinline__ uint64_t ordered64(int64_t k) { return (uint64_t)k ^ 0x8000000000000000ull; }
+__device__ __forceinline__ uint32_t ordered32(int32_t k) { return (uint32_t)k ^ 0x80000000u; }
+
+// Load key i of a column as int64 (RELNN_I32 columns are sign-extended).
+__device__ __forceinline__ int64_t load_key(const void* keys, int kt, int64_t i) {
+    return kt == RELNN_I64 ? reinterpret_cast<const int64_t*>(keys)[i]
+                           : (int64_t) reinterpret_cast<const int32_t*>(keys)[i];
+}
+
+// splitmix64 finalizer (Steele, Lea, Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014) used as the hash of a 64-bit key.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return x;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t h) {
+    return __uint_as_float(((uint32_t)h) << 16);
+}
+
+// Kahan step: sum += v with compensation c (never contracted into FMA).
+__device__ __forceinline__ void kahan_add(float& sum, float& c, float v) {
+    float y = __fsub_rn(v, c);
+    float t = __fadd_rn(sum, y);
+    c = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
+}  // namespace relnn

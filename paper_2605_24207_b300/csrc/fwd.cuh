@@ -1,0 +1,34 @@
+// Forward of a planned rule: gather -> Concat -> Linear (+ReLU) -> segmented SUM by output key.
+//
+// Both forms cut the dst-sorted matched tuples into fixed tiles. Inside a tile every output row
+// whose tuples all lie in the tile is written once with a plain store; a segment cut by a tile
+// boundary leaves one partial per tile in `carry` (slot 0: the piece holding the tile's first row,
+// slot 1: the piece holding its last row) and fixup_kernel adds the pieces in tile order
+// (compensated with RELNN_FLAG_KAHAN) and writes the row. Results are deterministic.
+#pragma once
+
+#include "plan.cuh"
+
+namespace relnn {
+
+// Per-branch inputs of a forward/backward call, resolved from relnn_rule_params.
+struct BranchIO {
+    const void* r = nullptr;   // [n_tuples, d_r]
+    const void* W = nullptr;   // [d_out, d_in]
+    const float* b = nullptr;  // [d_out]
+};
+
+struct CallIO {
+    const void* z = nullptr;
+    int z_bf16 = 0, r_bf16 = 0, w_bf16 = 0;
+    std::vector<BranchIO> br;
+};
+
+relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st);
+relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st);
+
+// Adds the carried partials of tile-split segments into `out` (see file comment).
+void launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,
+                  float* out, int d_out, bool accumulate, bool kahan, cudaStream_t st);
+
+}  // namespace relnn

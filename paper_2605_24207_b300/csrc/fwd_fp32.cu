@@ -1,0 +1,216 @@
+// FP32 form of the rule forward: f32 FMA on CUDA cores (no TF32), used where the output must match
+// the FP64 definition to ~1e-5 relative. One block owns 32-tuple tiles in turn; one thread owns one
+// output feature o and keeps y[t][o] for the tile's 32 tuples in registers, so the SUM over a run of
+// equal output rows is a sequential walk in registers (Sec. 2.2 projected union with SUM).
+#include "fwd.cuh"
+
+#include <algorithm>
+
+namespace relnn {
+
+namespace {
+
+constexpr int kTT = 32;  // tuples per tile
+
+struct Fp32Args {
+    const void* z;
+    int z_bf16, d;
+    const void* r;
+    int r_bf16, d_r;
+    const float* Wt;     // [d_in][d_out] (transposed Linear weight), nullptr = identity
+    const float* bias;   // [d_out] or nullptr
+    const int32_t *hs, *hd, *er, *seg;
+    int64_t m, n_tiles;
+    int concat_dst, d_in, d_out, act, kahan, accumulate, w_in_smem;
+    float* out;
+    float* carry;
+};
+
+__device__ __forceinline__ float load_elem(const void* base, int bf16, int64_t idx) {
+    return bf16 ? bf16_to_f32(reinterpret_cast<const uint16_t*>(base)[idx])
+                : reinterpret_cast<const float*>(base)[idx];
+}
+
+__global__ void __launch_bounds__(256) fwd_fp32_kernel(Fp32Args a) {
+    extern __shared__ float sm[];
+    float* Ws = sm;                                            // [d_in][d_out] if w_in_smem
+    float* X = sm + (a.w_in_smem ? (size_t)a.d_in * a.d_out : 0);  // [kTT][d_in]
+    __shared__ int seg_s[kTT];
+    const int tid = threadIdx.x;
+    if (a.w_in_smem && a.Wt) {
+        for (int i = tid; i < a.d_in * a.d_out; i += blockDim.x) Ws[i] = a.Wt[i];
+    }
+    const float* W = a.w_in_smem ? Ws : a.Wt;
+    const int o = tid;
+    const float bo = (a.bias && o < a.d_out) ? a.bias[o] : 0.f;
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        const int64_t t0 = tile * kTT;
+        const int nt = (int)imin64(kTT, a.m - t0);
+        __syncthreads();  // previous tile's X fully consumed
+        if (tid < kTT) seg_s[tid] = tid < nt ? a.seg[t0 + tid] : -1;
+        for (int idx = tid; idx < nt * a.d_in; idx += blockDim.x) {
+            const int t = idx / a.d_in, k = idx - t * a.d_in;
+            float v;
+            if (k < a.d) {
+                v = load_elem(a.z, a.z_bf16, (int64_t)a.hs[t0 + t] * a.d + k);
+            } else if (a.concat_dst && k < 2 * a.d) {
+                v = load_elem(a.z, a.z_bf16, (int64_t)a.hd[t0 + t] * a.d + (k - a.d));
+            } else {
+                const int kr = k - (a.concat_dst ? 2 : 1) * a.d;
+                v = load_elem(a.r, a.r_bf16, (int64_t)a.er[t0 + t] * a.d_r + kr);
+            }
+            X[t * a.d_in + k] = v;
+        }
+        __syncthreads();
+        if (o >= a.d_out) continue;
+        float y[kTT];
+#pragma unroll
+        for (int t = 0; t < kTT; ++t) y[t] = bo;
+        if (W) {
+            for (int k = 0; k < a.d_in; ++k) {
+                const float w = W[k * a.d_out + o];
+#pragma unroll
+                for (int t = 0; t < kTT; ++t) y[t] = fmaf(X[t * a.d_in + k], w, y[t]);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < kTT; ++t) y[t] = t < nt ? X[t * a.d_in + o] : 0.f;
+        }
+        if (a.act == RELNN_ACT_RELU) {
+#pragma unroll
+            for (int t = 0; t < kTT; ++t) y[t] = fmaxf(y[t], 0.f);
+        }
+        const int prev_seg = t0 > 0 ? a.seg[t0 - 1] : -1;
+        const int next_seg = t0 + nt < a.m ? a.seg[t0 + nt] : -1;
+        float acc = 0.f, comp = 0.f;
+        bool first = true;
+#pragma unroll
+        for (int t = 0; t < kTT; ++t) {
+            if (t < nt) {
+                if (a.kahan) kahan_add(acc, comp, y[t]);
+                else acc += y[t];
+                const int s = seg_s[t];
+                const bool last = (t == nt - 1);
+                const int sn = last ? next_seg : seg_s[t + 1 < kTT ? t + 1 : t];
+                if (sn != s || last) {
+                    const bool split = (first && prev_seg == s) || (last && sn == s);
+                    if (split) {
+                        a.carry[(tile * 2 + (first ? 0 : 1)) * a.d_out + o] = acc;
+                    } else {
+                        float* dst = a.out + (int64_t)s * a.d_out + o;
+                        *dst = a.accumulate ? *dst + acc : acc;
+                    }
+                    acc = 0.f;
+                    comp = 0.f;
+                    first = false;
+                }
+            }
+        }
+    }
+}
+
+// One block per tile boundary b (1..n_tiles-1). The block that sees the FIRST boundary crossed by
+// a segment adds that segment's pieces in tile order and writes the output row.
+__global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int tile, int64_t n_tiles,
+                             const float* __restrict__ carry, float* __restrict__ out, int d_out,
+                             int accumulate, int kahan) {
+    for (int64_t b = blockIdx.x + 1; b < n_tiles; b += gridDim.x) {
+        const int64_t row = b * tile;
+        if (row >= m) continue;
+        const int s = seg[row];
+        if (seg[row - 1] != s) continue;                         // boundary b cuts no segment
+        if (b >= 2 && seg[(b - 1) * tile - 1] == s) continue;    // not the first boundary of s
+        const int first_slot = (seg[(b - 1) * tile] == s) ? 0 : 1;
+        for (int o = threadIdx.x; o < d_out; o += blockDim.x) {
+            float acc = carry[((b - 1) * 2 + first_slot) * d_out + o];
+            float comp = 0.f;
+            int64_t j = b;
+            while (true) {
+                const float v = carry[(j * 2) * d_out + o];
+                if (kahan) kahan_add(acc, comp, v);
+                else acc += v;
+                const int64_t nb = (j + 1) * tile;
+                if (j + 1 < n_tiles && nb < m && seg[nb - 1] == s && seg[nb] == s) ++j;
+                else break;
+            }
+            float* dst = out + (int64_t)s * d_out + o;
+            *dst = accumulate ? *dst + acc : acc;
+        }
+    }
+}
+
+// Wt[k][o] = W[o][k] in f32.
+__global__ void transpose_w_kernel(const void* W, int w_bf16, int d_out, int d_in, float* Wt) {
+    const int n = d_out * d_in;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int o = i / d_in, k = i - o * d_in;
+        Wt[k * d_out + o] = w_bf16 ? bf16_to_f32(reinterpret_cast<const uint16_t*>(W)[i])
+                                   : reinterpret_cast<const float*>(W)[i];
+    }
+}
+
+}  // namespace
+
+void launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,
+                  float* out, int d_out, bool accumulate, bool kahan, cudaStream_t st) {
+    if (n_tiles <= 1) return;
+    const int blocks = (int)std::min<int64_t>(n_tiles - 1, (int64_t)num_sms() * 8);
+    const int threads = d_out >= 128 ? 128 : (d_out > 32 ? ((d_out + 31) / 32) * 32 : 32);
+    fixup_kernel<<<blocks, threads, 0, st>>>(seg, m, tile, n_tiles, carry, out, d_out, accumulate ? 1 : 0,
+                                             kahan ? 1 : 0);
+}
+
+relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
+    RELNN_CHECK_ARG(p.d_in <= 1024 && p.d_out <= 256, "FP32 form: d_in <= 1024 and d_out <= 256 required");
+    const bool multi = p.br.size() > 1;
+    if (multi) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));
+    const int threads = std::max(32, ((p.d_out + 31) / 32) * 32);
+    int64_t max_tiles = 1;
+    for (auto& b : p.br) max_tiles = std::max<int64_t>(max_tiles, ceil_div(b.m, kTT));
+    RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * max_tiles));
+    const size_t wt_bytes = sizeof(float) * p.d_in * p.d_out;
+    RELNN_TRY(p.scratch.alloc(wt_bytes));
+    const bool w_in_smem = !p.identity && wt_bytes <= 160 * 1024;
+    const size_t smem = (w_in_smem ? wt_bytes : 0) + sizeof(float) * kTT * p.d_in;
+    RELNN_CHECK_ARG(smem <= 220 * 1024, "FP32 form: tile does not fit in shared memory");
+    RELNN_CUDA(cudaFuncSetAttribute(fwd_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (size_t i = 0; i < p.br.size(); ++i) {
+        BranchPlan& b = p.br[i];
+        if (b.m == 0) continue;
+        Fp32Args a{};
+        a.z = io.z;
+        a.z_bf16 = io.z_bf16;
+        a.d = p.d;
+        a.r = io.br[i].r;
+        a.r_bf16 = io.r_bf16;
+        a.d_r = b.d_r;
+        if (!p.identity) {
+            transpose_w_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, p.scratch.as<float>());
+            a.Wt = p.scratch.as<float>();
+            a.bias = io.br[i].b;
+        }
+        a.hs = b.hs.as<int32_t>();
+        a.hd = b.hd.as<int32_t>();
+        a.er = b.er.as<int32_t>();
+        a.seg = b.seg.as<int32_t>();
+        a.m = b.m;
+        a.n_tiles = ceil_div(b.m, kTT);
+        a.concat_dst = p.concat_dst;
+        a.d_in = p.d_in;
+        a.d_out = p.d_out;
+        a.act = p.act;
+        a.kahan = p.kahan;
+        a.accumulate = multi;
+        a.w_in_smem = w_in_smem;
+        a.out = out;
+        a.carry = p.carry.as<float>();
+        const int grid = (int)std::min<int64_t>(a.n_tiles, (int64_t)num_sms() * (smem > 100 * 1024 ? 1 : 4));
+        fwd_fp32_kernel<<<grid, threads, smem, st>>>(a);
+        RELNN_CUDA(cudaGetLastError());
+        launch_fixup(a.seg, a.m, kTT, a.n_tiles, a.carry, out, p.d_out, multi, p.kahan, st);
+        RELNN_CUDA(cudaGetLastError());
+    }
+    return RELNN_OK;
+}
+
+}  // namespace relnn

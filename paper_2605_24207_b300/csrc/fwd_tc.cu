@@ -1,0 +1,484 @@
+// BF16 form of the rule forward on tcgen05 tensor cores (sm_103a): gather -> Concat -> Linear
+// (+ReLU) -> segmented SUM, fused in one persistent kernel.
+//
+// The Linear is computed transposed: D[o][t] = sum_k W[o][k] X[t][k], M = output features (a
+// 128-row block of W), N = a tile of tile_n matched tuples, K = the Concat width in 64-element
+// blocks. TMEM lane o then holds feature o of every tuple of the tile in consecutive columns, so the
+// epilogue thread that owns feature o reads its tuples in output-key order and the SUM over a run of
+// equal output rows is a walk in registers; each emitted row is a 128-byte coalesced store per warp.
+//
+// Roles (288 threads, one CTA per SM):
+//   warps 0-3  producers: gather rows z[hs], z[hd], r[er] for one 64-column K block of a tile into
+//              a 128B-swizzled stage (cp.async for bf16 sources, convert-and-store for f32 sources)
+//   warp 4     TMEM allocation; lane 0 issues tcgen05.mma (A = W block staged once by TMA,
+//              B = the gathered stage) and tcgen05.commit
+//   warps 5-8  epilogue: tcgen05.ld of the accumulator (double-buffered in TMEM so the next tile's
+//              MMAs overlap), bias, ReLU, SUM walk, stores / tile-boundary partials.
+#include "fwd.cuh"
+#include "tc.cuh"
+
+#include <algorithm>
+#include <mutex>
+
+namespace relnn {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 288;
+constexpr int kProducerThreads = 128;
+constexpr int kMmaWarp = 4;  // warps 5..8 are the epilogue
+constexpr int kMaxKb = 12;
+constexpr int kLag = 2;  // cp.async groups kept in flight per producer thread before arriving
+constexpr int kSmemLimit = 227 * 1024;
+
+struct TcArgs {
+    const void* z;
+    const void* r;
+    const int32_t* hs;
+    const int32_t* hd;
+    const int32_t* er;
+    const int32_t* seg;
+    const float* bias;
+    float* out;
+    float* carry;
+    int* status;
+    uint32_t* relu_mask;
+    int64_t m;
+    int64_t n_tiles;
+    int z_bf16, r_bf16, d, d_r;
+    int d_out, act, kahan, accumulate;
+    int n_kb, tile_n, m_blocks, stages, mask_words;
+    uint32_t idesc, tmem_cols;
+    int kb_src[kMaxKb];   // 0: z[hs], 1: z[hd], 2: r[er]
+    int kb_col[kMaxKb];   // first element of the block within its part
+    int kb_width[kMaxKb]; // width of that part
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ TcArgs a) {
+    extern __shared__ uint8_t dyn_smem[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~(uintptr_t)1023);
+    const uint32_t w_bytes = (uint32_t)a.n_kb * a.m_blocks * 16384u;
+    const uint32_t stage_bytes = (uint32_t)a.tile_n * 128u;
+    uint8_t* w_smem = base;
+    uint8_t* st_smem = base + w_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(st_smem + (size_t)a.stages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + a.stages;
+    uint64_t* tfull = bars + 2 * a.stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wbar = tempty + 2;
+    uint64_t* drain = wbar + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(smem_u32(&full[s]), kProducerThreads);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&tfull[i]), 1);
+            mbar_init(smem_u32(&tempty[i]), 128);
+        }
+        mbar_init(smem_u32(wbar), 1);
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t acc_stride = (uint32_t)a.m_blocks * a.tile_n;
+
+    if (warp < 4) {
+        // ------------------------------------------------------------------ producers
+        const int chunk = tid & 7;
+        const int row0 = tid >> 3;  // 0..15
+        const int rows_per_thread = a.tile_n / 16;
+        int it = 0;
+        int pending = 0;  // stages issued but not yet arrived
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+            const int64_t t0 = tile * a.tile_n;
+            for (int kb = 0; kb < a.n_kb && ok; ++kb, ++it) {
+                const int s = it % a.stages;
+                const uint32_t ph = (uint32_t)((it / a.stages) & 1);
+                if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.status, abort_flag)) { ok = false; break; }
+                const int src = a.kb_src[kb];
+                const int col = a.kb_col[kb] + chunk * 8;
+                const int width = a.kb_width[kb];
+                const bool in_part = col < width;
+                const int32_t* idx_arr = src == 0 ? a.hs : (src == 1 ? a.hd : a.er);
+                const void* tbl = src == 2 ? a.r : a.z;
+                const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
+                const int row_elems = src == 2 ? a.d_r : a.d;
+                const uint32_t sbase = smem_u32(st_smem + (size_t)s * stage_bytes);
+                for (int j = 0; j < rows_per_thread; ++j) {
+                    const int row = row0 + 16 * j;
+                    const int64_t t = t0 + row;
+                    const uint32_t dst = sbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
+                    const bool valid = (t < a.m) && in_part;
+                    if (tbl_bf16) {
+                        const uint16_t* p = reinterpret_cast<const uint16_t*>(tbl);
+                        const uint16_t* srcp = p;
+                        if (valid) srcp = p + (int64_t)idx_arr[t] * row_elems + col;
+                        if (src == 2) cp_async_16_stream(dst, srcp, valid ? 16u : 0u);
+                        else cp_async_16(dst, srcp, valid ? 16u : 0u);
+                    } else {
+                        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+                        if (valid) {
+                            const float4* q = reinterpret_cast<const float4*>(
+                                reinterpret_cast<const float*>(tbl) + (int64_t)idx_arr[t] * row_elems + col);
+                            const float4 u = __ldg(q);
+                            const float4 v = __ldg(q + 1);
+                            w0 = pack_bf16x2(u.x, u.y);
+                            w1 = pack_bf16x2(u.z, u.w);
+                            w2 = pack_bf16x2(v.x, v.y);
+                            w3 = pack_bf16x2(v.z, v.w);
+                        }
+                        st_shared_v4(dst, w0, w1, w2, w3);
+                    }
+                }
+                cp_async_commit();
+                ++pending;
+                if (pending > kLag) {
+                    cp_async_wait<kLag>();
+                    fence_proxy_async();
+                    mbar_arrive(smem_u32(&full[(it - kLag) % a.stages]));
+                    --pending;
+                }
+            }
+        }
+        cp_async_wait<0>();
+        fence_proxy_async();
+        for (int k = pending; k > 0; --k) mbar_arrive(smem_u32(&full[(it - k) % a.stages]));
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            bool ok = true;
+            const uint32_t wb = smem_u32(wbar);
+            mbar_arrive_expect_tx(wb, w_bytes);
+            for (int kb = 0; kb < a.n_kb; ++kb)
+                for (int mb = 0; mb < a.m_blocks; ++mb)
+                    tma_load_2d(smem_u32(w_smem + (size_t)(kb * a.m_blocks + mb) * 16384u), &wmap, kb * 64,
+                                mb * 128, wb);
+            ok = mbar_wait(wb, 0, a.status, abort_flag);
+            tc_fence_after();
+            int it = 0;
+            int lt = 0;
+            for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++lt) {
+                const int acc = lt & 1;
+                const uint32_t use = (uint32_t)(lt >> 1);
+                if (!mbar_wait(smem_u32(&tempty[acc]), (use & 1u) ^ 1u, a.status, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_acc = tmem_base + (uint32_t)acc * acc_stride;
+                for (int kb = 0; kb < a.n_kb; ++kb, ++it) {
+                    const int s = it % a.stages;
+                    const uint32_t ph = (uint32_t)((it / a.stages) & 1);
+                    if (!mbar_wait(smem_u32(&full[s]), ph, a.status, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t b_base = smem_u32(st_smem + (size_t)s * stage_bytes);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t bdesc = sw128_kmajor_desc(b_base + k * 32);
+                        for (int mb = 0; mb < a.m_blocks; ++mb) {
+                            const uint64_t adesc = sw128_kmajor_desc(
+                                smem_u32(w_smem + (size_t)(kb * a.m_blocks + mb) * 16384u) + k * 32);
+                            mma_bf16(d_acc + (uint32_t)mb * a.tile_n, adesc, bdesc, a.idesc, (kb | k) != 0);
+                        }
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&tfull[acc]));
+            }
+            // make sure every issued MMA has finished before TMEM is released
+            mma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0, a.status, abort_flag);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------ epilogue
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            const uint32_t use = (uint32_t)(lt >> 1);
+            if (!mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag)) break;
+            tc_fence_after();
+            const int64_t t0 = tile * a.tile_n;
+            const int nt = (int)imin64(a.tile_n, a.m - t0);
+            const int prev_seg = t0 > 0 ? a.seg[t0 - 1] : -1;
+            for (int mb = 0; mb < a.m_blocks; ++mb) {
+                const int obase = mb * 128 + 32 * q;
+                if (obase >= a.d_out) continue;
+                const int o = obase + lane;
+                const bool o_ok = o < a.d_out;
+                const float bo = (a.bias && o_ok) ? a.bias[o] : 0.f;
+                float sum = 0.f, comp = 0.f;
+                bool first = true;
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_stride +
+                                       (uint32_t)mb * a.tile_n;
+                for (int c = 0; c * 32 < nt; ++c) {
+                    uint32_t v[32];
+                    tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
+                    tmem_ld_wait();
+                    const int64_t tr = t0 + c * 32 + lane;   // this lane's tuple for the seg load
+                    const bool tvalid = (c * 32 + lane) < nt;
+                    const int sg = tvalid ? a.seg[tr] : -1;
+                    int nx = __shfl_down_sync(0xffffffffu, sg, 1);
+                    if (lane == 31) nx = (tr + 1 < a.m) ? a.seg[tr + 1] : -1;
+                    // the last valid row's successor may lie past the tile (or past m)
+                    const int last_row = nt - 1 - c * 32;  // index in this chunk of the tile's last row
+                    if (lane == last_row && lane < 31) nx = (tr + 1 < a.m) ? a.seg[tr + 1] : -1;
+                    const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && sg != nx);
+                    uint32_t mword = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        if (c * 32 + j >= nt) break;
+                        float y = __uint_as_float(v[j]) + bo;
+                        if (a.act == RELNN_ACT_RELU) {
+                            if (a.relu_mask) {
+                                const unsigned w = __ballot_sync(0xffffffffu, y > 0.f);
+                                if (lane == j) mword = w;
+                            }
+                            y = fmaxf(y, 0.f);
+                        }
+                        if (a.kahan) kahan_add(sum, comp, y);
+                        else sum += y;
+                        const bool last = (c * 32 + j == nt - 1);
+                        if (((endmask >> j) & 1u) || last) {
+                            const int s = __shfl_sync(0xffffffffu, sg, j);
+                            const int sn = __shfl_sync(0xffffffffu, nx, j);
+                            const bool split = (first && prev_seg == s) || (last && sn == s);
+                            if (o_ok) {
+                                if (split) {
+                                    a.carry[(tile * 2 + (first ? 0 : 1)) * a.d_out + o] = sum;
+                                } else {
+                                    float* dst = a.out + (int64_t)s * a.d_out + o;
+                                    *dst = a.accumulate ? *dst + sum : sum;
+                                }
+                            }
+                            sum = 0.f;
+                            comp = 0.f;
+                            first = false;
+                        }
+                    }
+                    if (a.relu_mask && a.act == RELNN_ACT_RELU && tvalid)
+                        a.relu_mask[tr * a.mask_words + mb * 4 + q] = mword;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&tempty[acc]));
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, a.tmem_cols);
+    }
+}
+
+// W_pad[mb*128 + o][kb*64 + kk] (bf16) = W[o][k(kb, kk)] with zero padding.
+__global__ void pack_w_kernel(const void* W, int w_bf16, int d_out, int d_in, int rows_pad, int n_kb,
+                              const int* kb_kofs, const int* kb_width_left, uint16_t* wp) {
+    const int cols = n_kb * 64;
+    const int n = rows_pad * cols;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int row = i / cols, cc = i - row * cols;
+        const int kb = cc >> 6, kk = cc & 63;
+        uint16_t v = 0;
+        if (row < d_out && kk < kb_width_left[kb]) {
+            const int k = kb_kofs[kb] + kk;
+            if (w_bf16) {
+                v = reinterpret_cast<const uint16_t*>(W)[row * d_in + k];
+            } else {
+                const float f = reinterpret_cast<const float*>(W)[row * d_in + k];
+                v = __bfloat16_as_ushort(__float2bfloat16_rn(f));
+            }
+        }
+        wp[i] = v;
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+// Concat layout for the tensor-core path: every part (z_src, z_dst, r) starts on a 64-column
+// K block; K blocks never straddle parts.
+struct KbLayout {
+    int n_kb = 0;
+    int src[kMaxKb], col[kMaxKb], width[kMaxKb], kofs[kMaxKb], left[kMaxKb];
+};
+
+static bool make_layout(const Plan& p, KbLayout& L) {
+    int kofs = 0;
+    auto add_part = [&](int src, int width) {
+        for (int c = 0; c < width; c += 64) {
+            if (L.n_kb >= kMaxKb) return false;
+            L.src[L.n_kb] = src;
+            L.col[L.n_kb] = c;
+            L.width[L.n_kb] = width;
+            L.kofs[L.n_kb] = kofs + c;
+            L.left[L.n_kb] = std::min(64, width - c);
+            ++L.n_kb;
+        }
+        kofs += width;
+        return true;
+    };
+    if (!add_part(0, p.d)) return false;
+    if (p.concat_dst && !add_part(1, p.d)) return false;
+    if (p.br[0].d_r > 0 && !add_part(2, p.br[0].d_r)) return false;
+    return true;
+}
+
+relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
+    if (p.identity) {
+        set_error("BF16 form needs a Linear (identity rules run in the FP32 form)");
+        return RELNN_ENOTSUP;
+    }
+    if (p.d % 8 != 0 || p.br[0].d_r % 8 != 0) {
+        set_error("BF16 form: d and d_r must be multiples of 8");
+        return RELNN_ENOTSUP;
+    }
+    if (p.d_out > 256) {
+        set_error("BF16 form: d_out must be <= 256");
+        return RELNN_ENOTSUP;
+    }
+    KbLayout L;
+    if (!make_layout(p, L)) {
+        set_error("BF16 form: Concat too wide");
+        return RELNN_ENOTSUP;
+    }
+    const int m_blocks = (p.d_out + 127) / 128;
+    const int tile_n = m_blocks == 1 ? 256 : 128;
+    const uint32_t w_bytes = (uint32_t)L.n_kb * m_blocks * 16384u;
+    const uint32_t stage_bytes = (uint32_t)tile_n * 128u;
+    const int bar_bytes = 256;
+    int stages = (int)((kSmemLimit - 1024 - bar_bytes - (int)w_bytes) / (int)stage_bytes);
+    stages = std::min(stages, 8);
+    if (stages < 3) {
+        set_error("BF16 form: weights too large for shared memory");
+        return RELNN_ENOTSUP;
+    }
+    const size_t smem = 1024 + w_bytes + (size_t)stages * stage_bytes + bar_bytes;
+    EncodeTiledFn enc = get_encode_fn();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return RELNN_ECUDA;
+    }
+    const bool multi = p.br.size() > 1;
+    if (multi) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));
+    int64_t max_tiles = 1;
+    for (auto& b : p.br) max_tiles = std::max<int64_t>(max_tiles, ceil_div(b.m, tile_n));
+    RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * max_tiles));
+    const int rows_pad = m_blocks * 128;
+    const size_t wp_elems = (size_t)rows_pad * L.n_kb * 64;
+    RELNN_TRY(p.wpack.alloc(wp_elems * 2 + 256));
+    int* d_meta = reinterpret_cast<int*>(p.wpack.as<uint8_t>() + wp_elems * 2);
+    int meta[2 * kMaxKb];
+    for (int i = 0; i < L.n_kb; ++i) {
+        meta[i] = L.kofs[i];
+        meta[kMaxKb + i] = L.left[i];
+    }
+    RELNN_CUDA(cudaMemcpyAsync(d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice, st));
+    CUtensorMap wmap;
+    {
+        cuuint64_t gdim[2] = {(cuuint64_t)L.n_kb * 64, (cuuint64_t)rows_pad};
+        cuuint64_t gstride[1] = {(cuuint64_t)L.n_kb * 64 * 2};
+        cuuint32_t box[2] = {64, 128};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p.wpack.p, gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+            return RELNN_ECUDA;
+        }
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        attr_set = true;
+    }
+    const bool want_mask = p.act == RELNN_ACT_RELU && (p.flags & RELNN_FLAG_RELU_MASK);
+    const int mask_words = m_blocks * 4;
+    for (size_t i = 0; i < p.br.size(); ++i) {
+        BranchPlan& b = p.br[i];
+        if (b.m == 0) continue;
+        pack_w_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, rows_pad, L.n_kb, d_meta,
+                                          d_meta + kMaxKb, p.wpack.as<uint16_t>());
+        RELNN_CUDA(cudaGetLastError());
+        TcArgs a{};
+        a.z = io.z;
+        a.r = io.br[i].r;
+        a.hs = b.hs.as<int32_t>();
+        a.hd = b.hd.as<int32_t>();
+        a.er = b.er.as<int32_t>();
+        a.seg = b.seg.as<int32_t>();
+        a.bias = io.br[i].b;
+        a.out = out;
+        a.carry = p.carry.as<float>();
+        a.status = p.status.as<int>();
+        if (want_mask) {
+            RELNN_TRY(b.relu_mask.alloc(sizeof(uint32_t) * (size_t)b.m * mask_words));
+            a.relu_mask = b.relu_mask.as<uint32_t>();
+        }
+        a.mask_words = mask_words;
+        a.m = b.m;
+        a.n_tiles = ceil_div(b.m, tile_n);
+        a.z_bf16 = io.z_bf16;
+        a.r_bf16 = io.r_bf16;
+        a.d = p.d;
+        a.d_r = b.d_r;
+        a.d_out = p.d_out;
+        a.act = p.act;
+        a.kahan = p.kahan;
+        a.accumulate = multi;
+        a.n_kb = L.n_kb;
+        a.tile_n = tile_n;
+        a.m_blocks = m_blocks;
+        a.stages = stages;
+        a.idesc = tc::idesc_bf16_f32(128, tile_n);
+        a.tmem_cols = (uint32_t)(2 * m_blocks * tile_n) <= 256 ? 256u : 512u;
+        for (int k = 0; k < L.n_kb; ++k) {
+            a.kb_src[k] = L.src[k];
+            a.kb_col[k] = L.col[k];
+            a.kb_width[k] = L.width[k];
+        }
+        const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
+        fwd_tc_kernel<<<grid, kThreads, smem, st>>>(wmap, a);
+        RELNN_CUDA(cudaGetLastError());
+        launch_fixup(a.seg, a.m, tile_n, a.n_tiles, a.carry, out, p.d_out, multi, p.kahan, st);
+        RELNN_CUDA(cudaGetLastError());
+    }
+    return RELNN_OK;
+}
+
+}  // namespace relnn

@@ -1,0 +1,307 @@
+// Join build (sort + distinct runs + lookup table) and the standalone probe entry point.
+#include "join.cuh"
+#include "primitives.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace relnn {
+
+namespace {
+
+__global__ void key_minmax_kernel(const void* keys, int64_t n, int kt, unsigned long long* mm) {
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long o = ordered64(load_key(keys, kt, i));
+        lo = o < lo ? o : lo;
+        hi = o > hi ? o : hi;
+    }
+#pragma unroll
+    for (int s = 16; s; s >>= 1) {
+        unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, s);
+        unsigned long long b = __shfl_xor_sync(0xffffffffu, hi, s);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+    }
+}
+
+// Sort keys: ordered(key) - ordered(min), as 32- or 64-bit unsigned; values = row numbers.
+template <class K>
+__global__ void make_sort_keys_kernel(const void* keys, int64_t n, int kt, uint64_t omin, K* sk,
+                                      int32_t* rows) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        sk[i] = (K)(ordered64(load_key(keys, kt, i)) - omin);
+        rows[i] = (int32_t)i;
+    }
+}
+
+template <class K>
+__global__ void run_flags_kernel(const K* sk, int64_t n, int32_t* flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i == 0 || sk[i] != sk[i - 1]) ? 1 : 0;
+}
+
+// flags_excl = exclusive scan of run flags. Writes run_start, uid_of_pos and the distinct keys.
+template <class K>
+__global__ void runs_kernel(const K* sk, const int32_t* flags_excl, int64_t n, uint64_t omin,
+                            int32_t* run_start, int32_t* uid_of_pos, int64_t* ukeys, int64_t U) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool head = (i == 0 || sk[i] != sk[i - 1]);
+        int32_t u = flags_excl[i] + (head ? 0 : -1);
+        uid_of_pos[i] = u;
+        if (head) {
+            run_start[u] = (int32_t)i;
+            ukeys[u] = (int64_t)(((uint64_t)sk[i] + omin) ^ 0x8000000000000000ull);
+        }
+        if (i == 0) run_start[U] = (int32_t)n;
+    }
+}
+
+__global__ void fill_i32_kernel(int32_t* p, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void fill_i64_kernel(int64_t* p, int64_t n, int64_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void direct_insert_kernel(const int64_t* ukeys, int64_t U, int64_t kmin, int32_t* table) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
+         u += (int64_t)gridDim.x * blockDim.x)
+        table[(uint64_t)ukeys[u] - (uint64_t)kmin] = (int32_t)u;
+}
+
+__global__ void hash_insert_kernel(const int64_t* ukeys, int64_t U, uint64_t mask,
+                                   unsigned long long* slot_keys, int32_t* slot_vals, int* status) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long key = (unsigned long long)ukeys[u];
+        uint64_t h = mix64(key) & mask;
+        bool done = false;
+        for (uint64_t it = 0; it <= mask; ++it) {
+            unsigned long long prev = atomicCAS(&slot_keys[h], (unsigned long long)kEmptyKey, key);
+            if (prev == (unsigned long long)kEmptyKey) {
+                slot_vals[h] = (int32_t)u;
+                done = true;
+                break;
+            }
+            h = (h + 1) & mask;
+        }
+        if (!done) raise_status(status, RELNN_DEV_HASH_FULL);
+    }
+}
+
+// Standalone probe, pass 1: distinct-key index and match count per probe row; per-warp totals.
+__global__ void probe_count_kernel(JoinView j, const void* keys, int64_t m, int kt, int32_t* uarr,
+                                   int64_t* warp_tot) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t cnt = 0;
+    if (i < m) {
+        int32_t u = j.lookup(load_key(keys, kt, i));
+        uarr[i] = u;
+        if (u >= 0) cnt = j.run_start[u + 1] - j.run_start[u];
+    }
+#pragma unroll
+    for (int s = 16; s; s >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, s);
+    if ((threadIdx.x & 31) == 0 && (i >> 5) * 32 < m) warp_tot[i >> 5] = cnt;
+}
+
+// Pass 2: each warp writes its pairs at its scanned offset; lanes find their slot with a ballot
+// (all counts <= 1, the unique-key case) or a shuffle scan (multi-match).
+__global__ void probe_emit_kernel(JoinView j, const int32_t* uarr, int64_t m, const int64_t* warp_off,
+                                  int32_t* probe_idx, int32_t* build_idx) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int32_t u = -1;
+    int64_t cnt = 0;
+    if (i < m) {
+        u = uarr[i];
+        if (u >= 0) cnt = j.run_start[u + 1] - j.run_start[u];
+    }
+    int64_t pre;
+    if (__all_sync(0xffffffffu, cnt <= 1)) {
+        pre = __popc(__ballot_sync(0xffffffffu, cnt != 0) & lanemask_lt());
+    } else {
+        int64_t v = cnt;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, v, s);
+            if (lane >= s) v += t;
+        }
+        pre = v - cnt;
+    }
+    if (cnt == 0) return;
+    const int64_t base = warp_off[i >> 5] + pre;
+    const int32_t rs = j.run_start[u];
+    for (int64_t k = 0; k < cnt; ++k) {
+        probe_idx[base + k] = (int32_t)i;
+        build_idx[base + k] = j.rows_sorted[rs + k];
+    }
+}
+
+inline int grid_for(int64_t n, int threads = 256) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 16));
+}
+
+}  // namespace
+
+relnn_status key_range(const void* keys, int64_t n, int kt, int64_t* kmin, int64_t* kmax,
+                       cudaStream_t st) {
+    *kmin = *kmax = 0;
+    if (n <= 0) return RELNN_OK;
+    unsigned long long* mm = nullptr;
+    RELNN_CUDA(cudaMallocAsync(&mm, 16, st));
+    unsigned long long init[2] = {~0ull, 0ull};
+    cudaMemcpyAsync(mm, init, 16, cudaMemcpyHostToDevice, st);
+    key_minmax_kernel<<<grid_for(n), 256, 0, st>>>(keys, n, kt, mm);
+    unsigned long long h[2];
+    cudaMemcpyAsync(h, mm, 16, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(mm, st);
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    *kmin = (int64_t)(h[0] ^ 0x8000000000000000ull);
+    *kmax = (int64_t)(h[1] ^ 0x8000000000000000ull);
+    return RELNN_OK;
+}
+
+relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt, cudaStream_t st) {
+    RELNN_CHECK_ARG(n >= 0 && n < (1ll << 31) - 1, "join build: n out of range");
+    RELNN_CHECK_ARG(n == 0 || keys, "join build: null keys");
+    jt.kt = kt;
+    jt.n = n;
+    RELNN_TRY(jt.status.alloc(sizeof(int)));
+    RELNN_CUDA(cudaMemsetAsync(jt.status.p, 0, sizeof(int), st));
+    RELNN_TRY(jt.rows_sorted.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1)));
+    RELNN_TRY(jt.uid_of_pos.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1)));
+    if (n == 0) {
+        jt.n_unique = 0;
+        RELNN_TRY(jt.run_start.alloc(sizeof(int32_t)));
+        RELNN_CUDA(cudaMemsetAsync(jt.run_start.p, 0, sizeof(int32_t), st));
+        RELNN_TRY(jt.ukeys.alloc(sizeof(int64_t)));
+        jt.mode = 1;
+        jt.direct_size = 0;
+        RELNN_TRY(jt.slot_vals.alloc(sizeof(int32_t)));
+        return RELNN_OK;
+    }
+    int64_t kmin, kmax;
+    RELNN_TRY(key_range(keys, n, kt, &kmin, &kmax, st));
+    RELNN_CHECK_ARG(kmax != kEmptyKey, "join build: key INT64_MAX is reserved");
+    jt.key_min = kmin;
+    jt.key_max = kmax;
+    const uint64_t omin = (uint64_t)kmin ^ 0x8000000000000000ull;
+    const uint64_t span = ((uint64_t)kmax ^ 0x8000000000000000ull) - omin;
+    const int nbits = bit_length(span);
+    const bool narrow = nbits <= 32;
+    const size_t kb = narrow ? 4 : 8;
+    DevBuf sk, sk_tmp, rows_tmp, flags;
+    RELNN_TRY(sk.alloc(kb * n));
+    RELNN_TRY(sk_tmp.alloc(kb * n));
+    RELNN_TRY(rows_tmp.alloc(sizeof(int32_t) * n));
+    RELNN_TRY(flags.alloc(sizeof(int32_t) * (n + 1)));
+    int32_t* rows = jt.rows_sorted.as<int32_t>();
+    const int g = grid_for(n);
+    if (narrow) {
+        make_sort_keys_kernel<uint32_t><<<g, 256, 0, st>>>(keys, n, kt, omin, sk.as<uint32_t>(), rows);
+        RELNN_TRY(radix_sort_pairs<uint32_t>(sk.as<uint32_t>(), rows, sk_tmp.as<uint32_t>(),
+                                             rows_tmp.as<int32_t>(), n, nbits, st));
+        run_flags_kernel<uint32_t><<<g, 256, 0, st>>>(sk.as<uint32_t>(), n, flags.as<int32_t>());
+    } else {
+        make_sort_keys_kernel<uint64_t><<<g, 256, 0, st>>>(keys, n, kt, omin, sk.as<uint64_t>(), rows);
+        RELNN_TRY(radix_sort_pairs<uint64_t>(sk.as<uint64_t>(), rows, sk_tmp.as<uint64_t>(),
+                                             rows_tmp.as<int32_t>(), n, nbits, st));
+        run_flags_kernel<uint64_t><<<g, 256, 0, st>>>(sk.as<uint64_t>(), n, flags.as<int32_t>());
+    }
+    RELNN_TRY(exclusive_scan<int32_t>(flags.as<int32_t>(), flags.as<int32_t>(), n,
+                                      flags.as<int32_t>() + n, st));
+    int32_t U32 = 0;
+    RELNN_CUDA(cudaMemcpyAsync(&U32, flags.as<int32_t>() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    const int64_t U = U32;
+    jt.n_unique = U;
+    RELNN_TRY(jt.run_start.alloc(sizeof(int32_t) * (U + 1)));
+    RELNN_TRY(jt.ukeys.alloc(sizeof(int64_t) * std::max<int64_t>(U, 1)));
+    if (narrow)
+        runs_kernel<uint32_t><<<g, 256, 0, st>>>(sk.as<uint32_t>(), flags.as<int32_t>(), n, omin,
+                                                 jt.run_start.as<int32_t>(), jt.uid_of_pos.as<int32_t>(),
+                                                 jt.ukeys.as<int64_t>(), U);
+    else
+        runs_kernel<uint64_t><<<g, 256, 0, st>>>(sk.as<uint64_t>(), flags.as<int32_t>(), n, omin,
+                                                 jt.run_start.as<int32_t>(), jt.uid_of_pos.as<int32_t>(),
+                                                 jt.ukeys.as<int64_t>(), U);
+    // Lookup: direct addressing when the key span is at most 4x the distinct keys (+1M slack).
+    const uint64_t direct_limit = (uint64_t)std::max<int64_t>(4 * U, 1 << 20);
+    if (span < direct_limit) {
+        jt.mode = 1;
+        jt.direct_size = (int64_t)span + 1;
+        jt.cap = 0;
+        RELNN_TRY(jt.slot_vals.alloc(sizeof(int32_t) * jt.direct_size));
+        fill_i32_kernel<<<grid_for(jt.direct_size), 256, 0, st>>>(jt.slot_vals.as<int32_t>(), jt.direct_size, -1);
+        direct_insert_kernel<<<grid_for(U), 256, 0, st>>>(jt.ukeys.as<int64_t>(), U, kmin,
+                                                          jt.slot_vals.as<int32_t>());
+    } else {
+        jt.mode = 0;
+        uint64_t cap = 1024;
+        while (cap < (uint64_t)(2 * U)) cap <<= 1;
+        jt.cap = cap;
+        RELNN_TRY(jt.slot_keys.alloc(sizeof(int64_t) * cap));
+        RELNN_TRY(jt.slot_vals.alloc(sizeof(int32_t) * cap));
+        fill_i64_kernel<<<grid_for(cap), 256, 0, st>>>(jt.slot_keys.as<int64_t>(), cap, kEmptyKey);
+        fill_i32_kernel<<<grid_for(cap), 256, 0, st>>>(jt.slot_vals.as<int32_t>(), cap, -1);
+        hash_insert_kernel<<<grid_for(U), 256, 0, st>>>(jt.ukeys.as<int64_t>(), U, cap - 1,
+                                                        jt.slot_keys.as<unsigned long long>(),
+                                                        jt.slot_vals.as<int32_t>(), jt.status.as<int>());
+    }
+    RELNN_CUDA(cudaGetLastError());
+    int dev_status = 0;
+    RELNN_CUDA(cudaMemcpyAsync(&dev_status, jt.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    if (dev_status) {
+        set_device_error(dev_status);
+        set_error("join build: device check failed");
+        return RELNN_EDEVICE;
+    }
+    return RELNN_OK;
+}
+
+relnn_status join_probe_pairs(const JoinTable& jt, const void* probe, int64_t m, int32_t* probe_idx,
+                              int32_t* build_idx, int64_t capacity, int64_t* d_count, cudaStream_t st) {
+    if (m == 0) {
+        if (d_count) RELNN_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int64_t), st));
+        RELNN_CUDA(cudaStreamSynchronize(st));
+        return RELNN_OK;
+    }
+    const int64_t nwarps = ceil_div(m, 32);
+    DevBuf uarr, wt;
+    RELNN_TRY(uarr.alloc(sizeof(int32_t) * m));
+    RELNN_TRY(wt.alloc(sizeof(int64_t) * (nwarps + 1)));
+    const JoinView v = jt.view();
+    const int blocks = (int)ceil_div(m, 256);
+    probe_count_kernel<<<blocks, 256, 0, st>>>(v, probe, m, jt.kt, uarr.as<int32_t>(), wt.as<int64_t>());
+    RELNN_TRY(exclusive_scan<int64_t>(wt.as<int64_t>(), wt.as<int64_t>(), nwarps, wt.as<int64_t>() + nwarps, st));
+    int64_t total = 0;
+    RELNN_CUDA(cudaMemcpyAsync(&total, wt.as<int64_t>() + nwarps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    if (d_count) RELNN_CUDA(cudaMemcpyAsync(d_count, &total, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (total > capacity) {
+        RELNN_CUDA(cudaStreamSynchronize(st));
+        set_error("join probe: " + std::to_string(total) + " pairs exceed capacity " + std::to_string(capacity));
+        return RELNN_ENOSPC;
+    }
+    probe_emit_kernel<<<blocks, 256, 0, st>>>(v, uarr.as<int32_t>(), m, wt.as<int64_t>(), probe_idx, build_idx);
+    RELNN_CUDA(cudaGetLastError());
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    return RELNN_OK;
+}
+
+}  // namespace relnn

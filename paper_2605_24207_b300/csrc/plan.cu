@@ -1,0 +1,330 @@
+// Content track of a rule (join build, probe of src and dst, grouping by output key).
+// Follows the join rule of Sec. 3.1: E |><| H(src) |><| H(dst) under bag semantics, then the
+// projected union over dst (Sec. 2.2) whose group index is built here once and cached.
+#include "plan.cuh"
+#include "primitives.cuh"
+
+#include <algorithm>
+
+namespace relnn {
+
+namespace {
+
+inline int grid_for(int64_t n, int threads = 256) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 16));
+}
+
+// Pass 1 over E: distinct-key indices of src and dst, matches per tuple, per-warp totals.
+__global__ void tri_count_kernel(JoinView j, const void* src, const void* dst, int64_t T, int kt,
+                                 bool join_dst, int32_t* us, int32_t* ud, int64_t* warp_tot) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t m = 0;
+    if (e < T) {
+        int32_t a = j.lookup(load_key(src, kt, e));
+        int32_t b = join_dst ? j.lookup(load_key(dst, kt, e)) : 0;
+        us[e] = a;
+        ud[e] = b;
+        if (a >= 0 && b >= 0) {
+            int64_t cs = j.run_start[a + 1] - j.run_start[a];
+            int64_t cd = join_dst ? (int64_t)(j.run_start[b + 1] - j.run_start[b]) : 1;
+            m = cs * cd;
+        }
+    }
+#pragma unroll
+    for (int s = 16; s; s >>= 1) m += __shfl_xor_sync(0xffffffffu, m, s);
+    if ((threadIdx.x & 31) == 0 && e < T) warp_tot[e >> 5] = m;
+}
+
+// Pass 2 over E: emit the join-output tuples (e, hs, hd) in (e, hs, hd) order with their group
+// sort key. Lane offsets inside a warp come from a ballot when every tuple matches at most once
+// (unique keys) and from a shuffle scan otherwise.
+template <class K>
+__global__ void tri_emit_kernel(JoinView j, const void* dst, int64_t T, int kt, bool join_dst,
+                                uint64_t omin, const int32_t* us, const int32_t* ud,
+                                const int64_t* warp_off, int32_t* t_hs, int32_t* t_hd, int32_t* t_e,
+                                K* t_key) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int32_t a = -1, b = -1;
+    int64_t cs = 0, cd = 0;
+    if (e < T) {
+        a = us[e];
+        b = ud[e];
+        if (a >= 0 && b >= 0) {
+            cs = j.run_start[a + 1] - j.run_start[a];
+            cd = join_dst ? (int64_t)(j.run_start[b + 1] - j.run_start[b]) : 1;
+        }
+    }
+    const int64_t cnt = cs * cd;
+    int64_t pre;
+    if (__all_sync(0xffffffffu, cnt <= 1)) {
+        pre = __popc(__ballot_sync(0xffffffffu, cnt != 0) & lanemask_lt());
+    } else {
+        int64_t v = cnt;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, v, s);
+            if (lane >= s) v += t;
+        }
+        pre = v - cnt;
+    }
+    if (cnt == 0) return;
+    int64_t pos = warp_off[e >> 5] + pre;
+    const int32_t rs = j.run_start[a];
+    const int32_t rd = join_dst ? j.run_start[b] : 0;
+    K rawkey = 0;
+    if (!join_dst) rawkey = (K)(ordered64(load_key(dst, kt, e)) - omin);
+    for (int64_t x = 0; x < cs; ++x) {
+        for (int64_t y = 0; y < cd; ++y, ++pos) {
+            t_hs[pos] = j.rows_sorted[rs + x];
+            t_e[pos] = (int32_t)e;
+            if (join_dst) {
+                t_hd[pos] = j.rows_sorted[rd + y];
+                t_key[pos] = (K)(rd + y);  // sorted position of the dst H row: groups by key, then row
+            } else {
+                t_hd[pos] = -1;
+                t_key[pos] = rawkey;
+            }
+        }
+    }
+}
+
+__global__ void gather3_kernel(const int32_t* perm, int64_t m, const int32_t* a, const int32_t* b,
+                               const int32_t* c, int32_t* oa, int32_t* ob, int32_t* oc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t p = perm[i];
+        oa[i] = a[p];
+        ob[i] = b[p];
+        oc[i] = c[p];
+    }
+}
+
+__global__ void mark_present_kernel(const uint32_t* pos_d, int64_t m, const int32_t* uid_of_pos,
+                                    int32_t* present) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        present[uid_of_pos[pos_d[i]]] = 1;
+}
+
+__global__ void seg_from_pos_kernel(const uint32_t* pos_d, int64_t m, const int32_t* uid_of_pos,
+                                    const int32_t* out_row, int32_t* seg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        seg[i] = out_row[uid_of_pos[pos_d[i]]];
+}
+
+// present / out_row: exclusive scan of the presence flags; writes the output keys.
+__global__ void out_keys_kernel(const int32_t* present, const int32_t* out_row, const int64_t* ukeys,
+                                int64_t U, int64_t* out_keys) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U;
+         u += (int64_t)gridDim.x * blockDim.x)
+        if (present[u]) out_keys[out_row[u]] = ukeys[u];
+}
+
+template <class K>
+__global__ void key_flags_kernel(const K* key, int64_t m, int32_t* flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+template <class K>
+__global__ void raw_seg_kernel(const K* key, const int32_t* flags_excl, int64_t m, uint64_t omin,
+                               int32_t* seg, int64_t* out_keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool head = (i == 0 || key[i] != key[i - 1]);
+        int32_t s = flags_excl[i] - (head ? 0 : 1);
+        seg[i] = s;
+        if (head) out_keys[s] = (int64_t)(((uint64_t)key[i] + omin) ^ 0x8000000000000000ull);
+    }
+}
+
+// Branch-local matched tuples before grouping.
+struct Tmp {
+    DevBuf t_hs, t_hd, t_e, key, key_tmp, perm, perm_tmp;
+    bool wide = false;
+    uint64_t omin = 0;
+};
+
+relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tmp& t, cudaStream_t st) {
+    const int64_t T = bd.n_tuples;
+    const JoinView v = p.H.view();
+    const int64_t nwarps = ceil_div(std::max<int64_t>(T, 1), 32);
+    DevBuf us, ud, wt;
+    RELNN_TRY(us.alloc(sizeof(int32_t) * std::max<int64_t>(T, 1)));
+    RELNN_TRY(ud.alloc(sizeof(int32_t) * std::max<int64_t>(T, 1)));
+    RELNN_TRY(wt.alloc(sizeof(int64_t) * (nwarps + 1)));
+    RELNN_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(int64_t) * (nwarps + 1), st));
+    const int blocks = (int)ceil_div(std::max<int64_t>(T, 1), 256);
+    if (T > 0)
+        tri_count_kernel<<<blocks, 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst,
+                                                 us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>());
+    RELNN_TRY(exclusive_scan<int64_t>(wt.as<int64_t>(), wt.as<int64_t>(), nwarps, wt.as<int64_t>() + nwarps, st));
+    int64_t M = 0;
+    RELNN_CUDA(cudaMemcpyAsync(&M, wt.as<int64_t>() + nwarps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    if (M >= (1ll << 31) - 1) {
+        set_error("rule plan: join output of " + std::to_string(M) + " tuples exceeds 2^31-1");
+        return RELNN_ENOTSUP;
+    }
+    b.m = M;
+    const int64_t m1 = std::max<int64_t>(M, 1);
+    // group key width: dst sorted position (n_h < 2^31) or the raw dst key span
+    int nbits = 0;
+    if (p.join_dst) {
+        nbits = bit_length((uint64_t)std::max<int64_t>(p.n_h - 1, 0));
+        t.wide = false;
+    } else {
+        int64_t kmin = 0, kmax = 0;
+        RELNN_TRY(key_range(bd.d_dst, T, p.kt, &kmin, &kmax, st));
+        t.omin = (uint64_t)kmin ^ 0x8000000000000000ull;
+        uint64_t span = ((uint64_t)kmax ^ 0x8000000000000000ull) - t.omin;
+        nbits = bit_length(span);
+        t.wide = nbits > 32;
+    }
+    const size_t kb = t.wide ? 8 : 4;
+    RELNN_TRY(t.t_hs.alloc(4 * m1));
+    RELNN_TRY(t.t_hd.alloc(4 * m1));
+    RELNN_TRY(t.t_e.alloc(4 * m1));
+    RELNN_TRY(t.key.alloc(kb * m1));
+    RELNN_TRY(t.key_tmp.alloc(kb * m1));
+    RELNN_TRY(t.perm.alloc(4 * m1));
+    RELNN_TRY(t.perm_tmp.alloc(4 * m1));
+    if (T > 0) {
+        if (t.wide)
+            tri_emit_kernel<uint64_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
+                us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>(), t.t_hs.as<int32_t>(),
+                t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(), t.key.as<uint64_t>());
+        else
+            tri_emit_kernel<uint32_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
+                us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>(), t.t_hs.as<int32_t>(),
+                t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(), t.key.as<uint32_t>());
+        RELNN_CUDA(cudaGetLastError());
+    }
+    RELNN_TRY(iota_i32(t.perm.as<int32_t>(), M, st));
+    if (t.wide)
+        RELNN_TRY(radix_sort_pairs<uint64_t>(t.key.as<uint64_t>(), t.perm.as<int32_t>(), t.key_tmp.as<uint64_t>(),
+                                             t.perm_tmp.as<int32_t>(), M, nbits, st));
+    else
+        RELNN_TRY(radix_sort_pairs<uint32_t>(t.key.as<uint32_t>(), t.perm.as<int32_t>(), t.key_tmp.as<uint32_t>(),
+                                             t.perm_tmp.as<int32_t>(), M, nbits, st));
+    RELNN_TRY(b.hs.alloc(4 * m1));
+    RELNN_TRY(b.hd.alloc(4 * m1));
+    RELNN_TRY(b.er.alloc(4 * m1));
+    RELNN_TRY(b.seg.alloc(4 * (m1 + 1)));
+    if (M > 0)
+        gather3_kernel<<<grid_for(M), 256, 0, st>>>(t.perm.as<int32_t>(), M, t.t_hs.as<int32_t>(),
+                                                    t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(),
+                                                    b.hs.as<int32_t>(), b.hd.as<int32_t>(), b.er.as<int32_t>());
+    RELNN_CUDA(cudaGetLastError());
+    return RELNN_OK;
+}
+
+}  // namespace
+
+relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
+    RELNN_CHECK_ARG(desc, "rule plan: null descriptor");
+    RELNN_CHECK_ARG(desc->key_type == RELNN_I32 || desc->key_type == RELNN_I64, "rule plan: bad key type");
+    RELNN_CHECK_ARG(desc->n_branches >= 1 && desc->branches, "rule plan: need >= 1 branch");
+    RELNN_CHECK_ARG(desc->d > 0 && desc->d <= 4096, "rule plan: bad embedding width d");
+    RELNN_CHECK_ARG(desc->n_h >= 0 && (desc->n_h == 0 || desc->d_h_ids), "rule plan: bad H");
+    RELNN_CHECK_ARG(desc->act == RELNN_ACT_NONE || desc->act == RELNN_ACT_RELU, "rule plan: bad act");
+    p.kt = desc->key_type;
+    p.flags = desc->flags;
+    p.act = desc->act;
+    p.d = desc->d;
+    p.n_h = desc->n_h;
+    p.join_dst = !(desc->flags & RELNN_FLAG_NO_JOIN_DST);
+    p.concat_dst = p.join_dst && !(desc->flags & RELNN_FLAG_NO_CONCAT_DST);
+    p.identity = (desc->flags & RELNN_FLAG_IDENTITY) != 0;
+    p.bf16 = (desc->flags & RELNN_FLAG_BF16) != 0;
+    p.kahan = (desc->flags & RELNN_FLAG_KAHAN) != 0;
+    RELNN_CHECK_ARG(p.join_dst || desc->n_branches == 1, "rule plan: a union needs the dst join (shared key space)");
+    const int d_r0 = desc->branches[0].d_r;
+    for (int i = 0; i < desc->n_branches; ++i) {
+        const relnn_branch_desc& b = desc->branches[i];
+        RELNN_CHECK_ARG(b.n_tuples >= 0 && b.n_tuples < (1ll << 31) - 1, "rule plan: n_tuples out of range");
+        RELNN_CHECK_ARG(b.n_tuples == 0 || (b.d_src && b.d_dst), "rule plan: null E column");
+        RELNN_CHECK_ARG(b.d_r >= 0 && b.d_r <= 4096, "rule plan: bad d_r");
+        RELNN_CHECK_ARG(b.d_r == d_r0, "rule plan: branches must share the Concat width");
+    }
+    p.d_in = p.d * (p.concat_dst ? 2 : 1) + d_r0;
+    p.d_out = p.identity ? p.d_in : desc->d_out;
+    RELNN_CHECK_ARG(p.d_out > 0 && p.d_out <= 4096, "rule plan: bad d_out");
+    RELNN_TRY(p.status.alloc(sizeof(int)));
+    RELNN_CUDA(cudaMemsetAsync(p.status.p, 0, sizeof(int), st));
+
+    // a1: build side over H.id
+    RELNN_TRY(join_table_build(p.H, desc->d_h_ids, desc->n_h, p.kt, st));
+    const int64_t U = p.H.n_unique;
+
+    // a2: probe and emit per branch; a3: sort by group key
+    p.br.clear();
+    p.br.resize(desc->n_branches);
+    std::vector<Tmp> tmp(desc->n_branches);
+    for (int i = 0; i < desc->n_branches; ++i) {
+        p.br[i].n_tuples = desc->branches[i].n_tuples;
+        p.br[i].d_r = desc->branches[i].d_r;
+        RELNN_TRY(emit_branch(p, p.br[i], desc->branches[i], tmp[i], st));
+    }
+
+    // output key set and output row of every matched tuple
+    if (p.join_dst) {
+        DevBuf present;
+        RELNN_TRY(present.alloc(sizeof(int32_t) * (U + 1)));
+        RELNN_CUDA(cudaMemsetAsync(present.p, 0, sizeof(int32_t) * (U + 1), st));
+        DevBuf out_row;
+        RELNN_TRY(out_row.alloc(sizeof(int32_t) * (U + 1)));
+        for (auto i = 0u; i < p.br.size(); ++i)
+            if (p.br[i].m > 0)
+                mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                    tmp[i].key.as<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), present.as<int32_t>());
+        RELNN_TRY(exclusive_scan<int32_t>(present.as<int32_t>(), out_row.as<int32_t>(), U, out_row.as<int32_t>() + U, st));
+        int32_t nout = 0;
+        RELNN_CUDA(cudaMemcpyAsync(&nout, out_row.as<int32_t>() + U, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RELNN_CUDA(cudaStreamSynchronize(st));
+        p.n_out = nout;
+        RELNN_TRY(p.out_keys.alloc(sizeof(int64_t) * std::max<int64_t>(nout, 1)));
+        if (U > 0)
+            out_keys_kernel<<<grid_for(U), 256, 0, st>>>(present.as<int32_t>(), out_row.as<int32_t>(),
+                                                         p.H.ukeys.as<int64_t>(), U, p.out_keys.as<int64_t>());
+        for (auto i = 0u; i < p.br.size(); ++i)
+            if (p.br[i].m > 0)
+                seg_from_pos_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                    tmp[i].key.as<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), out_row.as<int32_t>(),
+                    p.br[i].seg.as<int32_t>());
+        RELNN_CUDA(cudaGetLastError());
+        RELNN_CUDA(cudaStreamSynchronize(st));
+    } else {
+        BranchPlan& b = p.br[0];
+        Tmp& t = tmp[0];
+        const int64_t M = b.m;
+        DevBuf flags;
+        RELNN_TRY(flags.alloc(sizeof(int32_t) * (M + 1)));
+        if (M > 0) {
+            if (t.wide) key_flags_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), M, flags.as<int32_t>());
+            else key_flags_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), M, flags.as<int32_t>());
+        }
+        RELNN_TRY(exclusive_scan<int32_t>(flags.as<int32_t>(), flags.as<int32_t>(), M, flags.as<int32_t>() + M, st));
+        int32_t nout = 0;
+        RELNN_CUDA(cudaMemcpyAsync(&nout, flags.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RELNN_CUDA(cudaStreamSynchronize(st));
+        p.n_out = nout;
+        RELNN_TRY(p.out_keys.alloc(sizeof(int64_t) * std::max<int64_t>(nout, 1)));
+        if (M > 0) {
+            if (t.wide)
+                raw_seg_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), flags.as<int32_t>(), M,
+                                                                      t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>());
+            else
+                raw_seg_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), flags.as<int32_t>(), M,
+                                                                      t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>());
+        }
+        RELNN_CUDA(cudaGetLastError());
+        RELNN_CUDA(cudaStreamSynchronize(st));
+    }
+    return RELNN_OK;
+}
+
+}  // namespace relnn

@@ -1,0 +1,60 @@
+// Rule plan: the cached content track of a join rule (paper Sec. 3.1 compiled as
+// U_{SUM,dst}(T_tau(E |><| H |><| H)); Sec. 4.2 join row indices and group indices).
+//
+// Per branch, the matched (join-output) tuples are stored once, sorted by output key, as
+//   hs[m]   int32  H row of the src side
+//   hd[m]   int32  H row of the dst side (-1 without a dst join)
+//   er[m]   int32  E row (index into the per-tuple embedding r)
+//   seg[m]  int32  output row of the tuple (position of its dst key among the output keys)
+// Within one output key the tuples are ordered by dst H row, then E row, then src H row, so runs of
+// equal hd are contiguous (used by the backward's scatter to z_dst).
+// For the backward's scatter to z_src a second order sorted by src H row is kept:
+//   src_perm[m] int32  position (in the order above) of the k-th tuple in src order
+//   src_hs[m]   int32  its src H row (non-decreasing)
+#pragma once
+
+#include <vector>
+
+#include "join.cuh"
+
+namespace relnn {
+
+struct BranchPlan {
+    int64_t n_tuples = 0;
+    int64_t m = 0;  // matched tuples
+    int32_t d_r = 0;
+    DevBuf hs, hd, er, seg;
+    DevBuf src_perm, src_hs;
+    DevBuf relu_mask;  // uint32 [m][ceil(d_out/32)] when RELNN_FLAG_RELU_MASK
+};
+
+struct Plan {
+    int kt = RELNN_I32;
+    uint32_t flags = 0;
+    int act = RELNN_ACT_NONE;
+    int d = 0, d_out = 0, d_in = 0;
+    bool join_dst = true, concat_dst = true, identity = false, bf16 = false, kahan = false;
+    int64_t n_h = 0;
+    JoinTable H;
+    int64_t n_out = 0;
+    DevBuf out_keys;  // int64 [n_out] (converted to the key type on copy-out)
+    std::vector<BranchPlan> br;
+    DevBuf status;    // device status word
+    // forward/backward workspace (grown on demand, reused across calls)
+    DevBuf carry;     // f32 [tiles][2][d_out] partial sums of segments cut by tile boundaries
+    DevBuf wpack;     // bf16 packed/padded weights for the tensor-core kernels
+    DevBuf scratch;   // misc per-call scratch
+    int64_t total_matched() const {
+        int64_t s = 0;
+        for (auto& b : br) s += b.m;
+        return s;
+    }
+};
+
+relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st);
+
+}  // namespace relnn
+
+struct relnn_plan_s {
+    relnn::Plan p;
+};

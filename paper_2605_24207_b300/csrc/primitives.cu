@@ -1,0 +1,255 @@
+// Exclusive scan and stable LSD radix sort (hand-written; no CUB).
+//
+// Scan: reduce-then-scan. A block owns 4096 consecutive items (512 threads x 8 items in blocked
+// order); the block sums are scanned recursively and added back.
+//
+// Radix sort: 8 bits per pass. Each block owns a tile of 4096 keys split into 8 warp sub-tiles of
+// 512 keys that a warp visits in 16 steps of 32. Pass = (1) per-block digit histogram with
+// warp-aggregated shared-memory counts, (2) exclusive scan of the digit-major histogram, (3) stable
+// scatter: a key's destination is digit base + (keys of its digit in earlier blocks) + (in earlier
+// warps of its block) + (in earlier steps of its warp) + (in lower lanes of its step), the last two
+// found with __match_any_sync / popc.
+#include "primitives.cuh"
+
+#include <algorithm>
+
+namespace relnn {
+
+namespace {
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+template <class T>
+__global__ void scan_reduce_kernel(const T* __restrict__ in, int64_t n, T* __restrict__ sums) {
+    __shared__ T ws[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    T s = 0;
+    for (int j = threadIdx.x; j < kScanTile; j += kScanThreads) {
+        int64_t i = base + j;
+        if (i < n) s += in[i];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        T v = threadIdx.x < kScanThreads / 32 ? ws[threadIdx.x] : T(0);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = v;
+    }
+}
+
+// Block-local exclusive scan of a 4096-item tile plus an optional per-block offset.
+template <class T>
+__global__ void scan_apply_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t n,
+                                  const T* __restrict__ block_off, T* __restrict__ total) {
+    __shared__ T ws[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        v[k] = i < n ? in[i] : T(0);
+        T t = v[k];
+        v[k] = run;
+        run += t;
+    }
+    T incl = warp_incl_scan(run);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < kScanThreads / 32 ? ws[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < kScanThreads / 32) ws[lane] = wi - w;
+    }
+    __syncthreads();
+    T off = ws[warp] + incl - run + (block_off ? block_off[blockIdx.x] : T(0));
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        if (i < n) out[i] = v[k] + off;
+    }
+    if (total && threadIdx.x == kScanThreads - 1 && blockIdx.x == gridDim.x - 1) {
+        *total = off + run;  // the last thread's exclusive offset plus its own items
+    }
+}
+
+__global__ void iota_kernel(int32_t* out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)i;
+}
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortSteps = 16;
+constexpr int kSortTile = kSortThreads * kSortSteps;  // 4096
+
+template <class K>
+__global__ void rs_hist_kernel(const K* __restrict__ keys, int64_t n, int shift,
+                               int32_t* __restrict__ hist, int nblocks) {
+    __shared__ int32_t h[256];
+    for (int i = threadIdx.x; i < 256; i += kSortThreads) h[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortSteps);
+    for (int s = 0; s < kSortSteps; ++s) {
+        int64_t i = base + s * 32 + lane;
+        bool valid = i < n;
+        unsigned d = valid ? (unsigned)((keys[i] >> shift) & 255u) : 256u + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += kSortThreads) hist[(int64_t)i * nblocks + blockIdx.x] = h[i];
+}
+
+template <class K>
+__global__ void rs_scatter_kernel(const K* __restrict__ keys, const int32_t* __restrict__ vals,
+                                  K* __restrict__ okeys, int32_t* __restrict__ ovals, int64_t n,
+                                  int shift, const int32_t* __restrict__ offs, int nblocks) {
+    __shared__ int32_t wcnt[kSortWarps][256];
+    __shared__ int32_t gbase[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 256; i += kSortThreads) {
+        gbase[i] = offs[(int64_t)i * nblocks + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) wcnt[w][i] = 0;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortSteps);
+    K k[kSortSteps];
+    int32_t v[kSortSteps];
+    int32_t rank[kSortSteps];
+#pragma unroll
+    for (int s = 0; s < kSortSteps; ++s) {
+        int64_t i = base + s * 32 + lane;
+        bool valid = i < n;
+        k[s] = valid ? keys[i] : K(0);
+        v[s] = valid ? vals[i] : 0;
+        unsigned d = valid ? (unsigned)((k[s] >> shift) & 255u) : 256u + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        int old = 0;
+        if (valid && lane == leader) {
+            old = wcnt[warp][d];
+            wcnt[warp][d] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[s] = old + __popc(peers & lanemask_lt());
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += kSortThreads) {
+        int32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            int32_t t = wcnt[w][i];
+            wcnt[w][i] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < kSortSteps; ++s) {
+        int64_t i = base + s * 32 + lane;
+        if (i < n) {
+            unsigned d = (unsigned)((k[s] >> shift) & 255u);
+            int64_t pos = (int64_t)gbase[d] + wcnt[warp][d] + rank[s];
+            okeys[pos] = k[s];
+            ovals[pos] = v[s];
+        }
+    }
+}
+
+}  // namespace
+
+template <class T>
+relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream_t st) {
+    if (n <= 0) {
+        if (total) RELNN_CUDA(cudaMemsetAsync(total, 0, sizeof(T), st));
+        return RELNN_OK;
+    }
+    const int64_t nb = ceil_div(n, kScanTile);
+    if (nb == 1) {
+        scan_apply_kernel<T><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
+        RELNN_CUDA(cudaGetLastError());
+        return RELNN_OK;
+    }
+    T* sums = nullptr;
+    RELNN_CUDA(cudaMallocAsync(&sums, sizeof(T) * nb, st));
+    scan_reduce_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
+    relnn_status s = exclusive_scan<T>(sums, sums, nb, nullptr, st);
+    if (s == RELNN_OK) {
+        scan_apply_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums, total);
+        if (cudaGetLastError() != cudaSuccess) s = RELNN_ECUDA;
+    }
+    cudaFreeAsync(sums, st);
+    return s;
+}
+
+template relnn_status exclusive_scan<int32_t>(const int32_t*, int32_t*, int64_t, int32_t*, cudaStream_t);
+template relnn_status exclusive_scan<int64_t>(const int64_t*, int64_t*, int64_t, int64_t*, cudaStream_t);
+
+template <class K>
+relnn_status radix_sort_pairs(K* keys, int32_t* vals, K* keys_tmp, int32_t* vals_tmp, int64_t n,
+                              int nbits, cudaStream_t st) {
+    if (n <= 1 || nbits <= 0) return RELNN_OK;
+    const int64_t nb64 = ceil_div(n, kSortTile);
+    RELNN_CHECK_ARG(nb64 * 256 < (1ll << 31), "radix sort: too many keys");
+    const int nb = (int)nb64;
+    int32_t* hist = nullptr;
+    RELNN_CUDA(cudaMallocAsync(&hist, sizeof(int32_t) * 256 * (size_t)nb, st));
+    K *src_k = keys, *dst_k = keys_tmp;
+    int32_t *src_v = vals, *dst_v = vals_tmp;
+    relnn_status s = RELNN_OK;
+    int passes = 0;
+    for (int shift = 0; shift < nbits; shift += 8, ++passes) {
+        rs_hist_kernel<K><<<nb, kSortThreads, 0, st>>>(src_k, n, shift, hist, nb);
+        s = exclusive_scan<int32_t>(hist, hist, (int64_t)256 * nb, nullptr, st);
+        if (s != RELNN_OK) break;
+        rs_scatter_kernel<K><<<nb, kSortThreads, 0, st>>>(src_k, src_v, dst_k, dst_v, n, shift, hist, nb);
+        if (cudaGetLastError() != cudaSuccess) {
+            s = RELNN_ECUDA;
+            break;
+        }
+        K* tk = src_k; src_k = dst_k; dst_k = tk;
+        int32_t* tv = src_v; src_v = dst_v; dst_v = tv;
+    }
+    if (s == RELNN_OK && (passes & 1)) {
+        cudaMemcpyAsync(keys, keys_tmp, sizeof(K) * n, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(vals, vals_tmp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
+    }
+    cudaFreeAsync(hist, st);
+    if (s != RELNN_OK) set_error("radix sort failed");
+    return s;
+}
+
+template relnn_status radix_sort_pairs<uint32_t>(uint32_t*, int32_t*, uint32_t*, int32_t*, int64_t, int, cudaStream_t);
+template relnn_status radix_sort_pairs<uint64_t>(uint64_t*, int32_t*, uint64_t*, int32_t*, int64_t, int, cudaStream_t);
+
+relnn_status iota_i32(int32_t* out, int64_t n, cudaStream_t st) {
+    if (n <= 0) return RELNN_OK;
+    int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 148 * 16);
+    iota_kernel<<<blocks, 256, 0, st>>>(out, n);
+    RELNN_CUDA(cudaGetLastError());
+    return RELNN_OK;
+}
+
+}  // namespace relnn

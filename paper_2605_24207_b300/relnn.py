@@ -1,0 +1,261 @@
+"""Thin Python binding of librelnn.so (argument marshalling only; every step runs in the library's
+CUDA kernels). PyTorch supplies device memory and the current stream.
+
+The library is built in-tree by ``build_lib.build()``; importing this module never compiles and
+never falls back to another implementation: if the shared library is missing the import of
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Sequence
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librelnn.so")
+
+I32, I64 = 0, 1
+F32, BF16 = 0, 1
+ACT_NONE, ACT_RELU = 0, 1
+FLAG_BF16 = 0x1
+FLAG_KAHAN = 0x2
+FLAG_IDENTITY = 0x4
+FLAG_NO_JOIN_DST = 0x8
+FLAG_NO_CONCAT_DST = 0x10
+FLAG_RELU_MASK = 0x20
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOSPC", 4: "EAGAIN", 5: "ETIMEDOUT", 6: "ECUDA",
+          7: "EDEVICE", 8: "ENOTSUP"}
+
+
+class RelnnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BranchDesc(C.Structure):
+    _fields_ = [("d_src", C.c_void_p), ("d_dst", C.c_void_p), ("n_tuples", C.c_int64), ("d_r", C.c_int32)]
+
+
+class RuleDesc(C.Structure):
+    _fields_ = [("key_type", C.c_int), ("d_h_ids", C.c_void_p), ("n_h", C.c_int64), ("d", C.c_int32),
+                ("d_out", C.c_int32), ("n_branches", C.c_int32), ("branches", C.POINTER(BranchDesc)),
+                ("act", C.c_int), ("flags", C.c_uint32)]
+
+
+class RuleParams(C.Structure):
+    _fields_ = [("d_z", C.c_void_p), ("z_dtype", C.c_int), ("d_r", C.POINTER(C.c_void_p)), ("r_dtype", C.c_int),
+                ("d_W", C.POINTER(C.c_void_p)), ("w_dtype", C.c_int), ("d_b", C.POINTER(C.c_void_p))]
+
+
+_LIB = None
+
+EXPORTS = [
+    "relnn_version", "relnn_status_string", "relnn_last_error", "relnn_last_device_error",
+    "relnn_join_build", "relnn_join_probe", "relnn_join_destroy",
+    "relnn_rule_plan", "relnn_plan_info", "relnn_plan_out_keys", "relnn_plan_check",
+    "relnn_rule_forward", "relnn_rule_backward", "relnn_plan_destroy",
+]
+
+
+def lib():
+    """Load librelnn.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"librelnn.so not built at {LIB_PATH}; run paper_2605_24207_b300/build_lib.py")
+    L = C.CDLL(LIB_PATH)
+    L.relnn_version.restype = C.c_int32
+    L.relnn_status_string.restype = C.c_char_p
+    L.relnn_last_error.restype = C.c_char_p
+    L.relnn_last_device_error.restype = C.c_int32
+    vp, i64 = C.c_void_p, C.c_int64
+    L.relnn_join_build.argtypes = [vp, i64, C.c_int, vp, C.POINTER(vp)]
+    L.relnn_join_probe.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
+    L.relnn_join_destroy.argtypes = [vp]
+    L.relnn_rule_plan.argtypes = [C.POINTER(RuleDesc), vp, C.POINTER(vp)]
+    L.relnn_plan_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    L.relnn_plan_out_keys.argtypes = [vp, vp, vp]
+    L.relnn_plan_check.argtypes = [vp, vp]
+    L.relnn_rule_forward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp]
+    L.relnn_rule_backward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp, vp, vp]
+    L.relnn_plan_destroy.argtypes = [vp]
+    for name in EXPORTS[4:]:
+        getattr(L, name).restype = C.c_int
+    _LIB = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().relnn_last_error().decode(errors="replace")
+        raise RelnnError(status, msg)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return t.data_ptr()
+
+
+def _key_type(t: torch.Tensor) -> int:
+    if t.dtype == torch.int32:
+        return I32
+    if t.dtype == torch.int64:
+        return I64
+    raise TypeError(f"keys must be int32 or int64, got {t.dtype}")
+
+
+def _float_type(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"embeddings must be float32 or bfloat16, got {t.dtype}")
+
+
+# ------------------------------------------------------------------------------------------ join
+class Join:
+    """relnn_join_build / relnn_join_probe (bag-semantics equi-join of two key columns)."""
+
+    def __init__(self, keys: torch.Tensor, stream=None):
+        self._h = C.c_void_p()
+        self.kt = _key_type(keys)
+        self.dtype = keys.dtype
+        _check(lib().relnn_join_build(_ptr(keys), keys.numel(), self.kt, _stream(stream), C.byref(self._h)))
+
+    def probe(self, keys: torch.Tensor, capacity: int | None = None, stream=None):
+        """All (probe row, build row) pairs, ordered by probe row then build row."""
+        assert keys.dtype == self.dtype, "probe keys must have the build key type"
+        dev = keys.device
+        cap = keys.numel() if capacity is None else int(capacity)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        while True:
+            pi = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            bi = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            st = lib().relnn_join_probe(self._h, _ptr(keys), keys.numel(), _ptr(pi), _ptr(bi), cap, _ptr(cnt),
+                                        _stream(stream))
+            if st == 3 and capacity is None:  # ENOSPC: grow to the reported size
+                cap = int(cnt.item())
+                continue
+            _check(st)
+            n = int(cnt.item())
+            return pi[:n], bi[:n]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value and _LIB is not None:
+            _LIB.relnn_join_destroy(self._h)
+            self._h = C.c_void_p()
+
+
+# ------------------------------------------------------------------------------------------ rules
+class RulePlan:
+    """relnn_rule_plan: the cached content track of
+    H'(dst; SUM tau(Concat(z_src, z_dst[, r]))) :- E_i(src, dst[; r]), H(src; z_src), H(dst; z_dst)."""
+
+    def __init__(self, h_ids: torch.Tensor, branches: Sequence, d: int, d_out: int, act: int = ACT_NONE,
+                 flags: int = 0, d_r: int = 0, stream=None):
+        """``branches``: sequence of (src, dst) device key tensors."""
+        self.kt = _key_type(h_ids)
+        self.key_dtype = h_ids.dtype
+        self.device = h_ids.device
+        self.n_branches = len(branches)
+        self.flags, self.act, self.d, self.d_r = flags, act, d, d_r
+        self.n_tuples = [int(s.numel()) for s, _ in branches]
+        arr = (BranchDesc * len(branches))()
+        for i, (s, t) in enumerate(branches):
+            assert s.dtype == self.key_dtype and t.dtype == self.key_dtype
+            arr[i] = BranchDesc(_ptr(s), _ptr(t), s.numel(), d_r)
+        desc = RuleDesc(self.kt, _ptr(h_ids), h_ids.numel(), d, d_out, len(branches), arr, act, flags)
+        self._h = C.c_void_p()
+        _check(lib().relnn_rule_plan(C.byref(desc), _stream(stream), C.byref(self._h)))
+        n_out, n_tot = C.c_int64(), C.c_int64()
+        per = (C.c_int64 * len(branches))()
+        _check(lib().relnn_plan_info(self._h, C.byref(n_out), C.byref(n_tot), per))
+        self.n_out = n_out.value
+        self.n_matched = n_tot.value
+        self.matched = list(per)
+        concat = d * (1 if (flags & (FLAG_NO_JOIN_DST | FLAG_NO_CONCAT_DST)) else 2) + d_r
+        self.d_in = concat
+        self.d_out = concat if flags & FLAG_IDENTITY else d_out
+
+    def out_keys(self, stream=None) -> torch.Tensor:
+        k = torch.empty(max(self.n_out, 1), dtype=self.key_dtype, device=self.device)
+        _check(lib().relnn_plan_out_keys(self._h, _ptr(k), _stream(stream)))
+        return k[: self.n_out]
+
+    def check(self, stream=None):
+        _check(lib().relnn_plan_check(self._h, _stream(stream)))
+
+    def _params(self, z, W, b, r):
+        n = self.n_branches
+        Ws = (C.c_void_p * n)(*[_ptr(w) for w in W]) if W is not None else None
+        bs = (C.c_void_p * n)(*[_ptr(x) for x in b]) if b is not None else None
+        rs = (C.c_void_p * n)(*[_ptr(x) for x in r]) if r is not None else None
+        w_dt = _float_type(W[0]) if W is not None else F32
+        r_dt = _float_type(r[0]) if r is not None else F32
+        keep = (Ws, bs, rs)
+        prm = RuleParams(_ptr(z), _float_type(z), rs, r_dt, Ws, w_dt, bs)
+        return prm, keep
+
+    def forward(self, z, W=None, b=None, r=None, out=None, stream=None) -> torch.Tensor:
+        """Output embeddings [n_out, d_out] f32 (rows in out_keys() order)."""
+        if out is None:
+            out = torch.empty((max(self.n_out, 1), self.d_out), dtype=torch.float32, device=self.device)
+        prm, keep = self._params(z, W, b, r)
+        _check(lib().relnn_rule_forward(self._h, C.byref(prm), None, _ptr(out), None, _stream(stream)))
+        return out[: self.n_out]
+
+    def backward(self, dout, z, W=None, b=None, r=None, need_dz=True, stream=None):
+        """Gradients (dW list, db list, dz, dr list) of the forward for output gradient ``dout``."""
+        dev, n = self.device, self.n_branches
+        dW = [torch.empty((self.d_out, self.d_in), dtype=torch.float32, device=dev) for _ in range(n)] \
+            if W is not None else None
+        db = [torch.empty(self.d_out, dtype=torch.float32, device=dev) for _ in range(n)] if W is not None else None
+        dz = torch.empty(z.shape, dtype=torch.float32, device=dev) if need_dz else None
+        dr = [torch.empty((self.n_tuples[i], self.d_r), dtype=torch.float32, device=dev) for i in range(n)] \
+            if (r is not None and self.d_r > 0) else None
+        prm, keep = self._params(z, W, b, r)
+        dWp = (C.c_void_p * n)(*[_ptr(x) for x in dW]) if dW else None
+        dbp = (C.c_void_p * n)(*[_ptr(x) for x in db]) if db else None
+        drp = (C.c_void_p * n)(*[_ptr(x) for x in dr]) if dr else None
+        dout = dout.contiguous()
+        _check(lib().relnn_rule_backward(self._h, C.byref(prm), _ptr(dout), dWp, dbp, _ptr(dz), drp,
+                                         _stream(stream)))
+        return dW, db, dz, dr
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value and _LIB is not None:
+            _LIB.relnn_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+
+class RelnnRule(torch.autograd.Function):
+    """Autograd wrapper: forward = relnn_rule_forward, backward = relnn_rule_backward (the gathered
+    Concat is recomputed in the backward, not stored). Single-branch rules; for a union use the
+    plan's forward/backward directly."""
+
+    @staticmethod
+    def forward(ctx, plan: RulePlan, z, W, b, r=None):
+        ctx.plan = plan
+        ctx.save_for_backward(z, W, b, r)
+        return plan.forward(z, [W] if W is not None else None, [b] if b is not None else None,
+                            [r] if r is not None else None)
+
+    @staticmethod
+    def backward(ctx, dout):
+        z, W, b, r = ctx.saved_tensors
+        dW, db, dz, dr = ctx.plan.backward(dout, z, [W] if W is not None else None,
+                                           [b] if b is not None else None, [r] if r is not None else None,
+                                           need_dz=ctx.needs_input_grad[1])
+        return (None, dz, dW[0] if dW else None, db[0] if db else None, dr[0] if dr else None)
