@@ -14,8 +14,9 @@ def _case(seed, n_build, n_probe, key_dtype, span, dup=True, neg=False):
     rng = np.random.default_rng(seed)
     lo = -span if neg else 0
     build = rng.integers(lo, span, size=n_build).astype(key_dtype)
-    if not dup:
-        build = rng.permutation(np.arange(lo, span))[:n_build].astype(key_dtype)
+    if not dup:  # distinct keys drawn from a possibly huge range
+        u = np.unique(rng.integers(lo, span, size=2 * n_build))
+        build = rng.permutation(u)[:n_build].astype(key_dtype)
     probe = rng.integers(lo - 5, span + 5, size=n_probe).astype(key_dtype)
     return build, probe
 
