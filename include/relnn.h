@@ -172,6 +172,26 @@ relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, c
 /* Releases the plan's device memory (waits for the device first). */
 relnn_status relnn_plan_destroy(relnn_plan_t p);
 
+/* ---------------------------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper; used to report roofline fractions).
+ * ------------------------------------------------------------------------------------------- */
+#define RELNN_PROF_FWD_TC 0      /* fused tcgen05 forward kernel                                   */
+#define RELNN_PROF_FWD_FP32 1    /* FP32-form forward kernel                                       */
+#define RELNN_PROF_FIXUP 2       /* tile-boundary fix-up of split segments                         */
+#define RELNN_PROF_BWD_TC 3      /* tensor-core backward kernels                                   */
+#define RELNN_PROF_BWD_FP32 4    /* FP32-form backward kernels                                     */
+#define RELNN_PROF_PLAN 5        /* content track (whole relnn_rule_plan)                          */
+
+/* Number of kernels this library has launched since it was loaded (host counter). */
+uint64_t relnn_launch_count(void);
+/* Turns CUDA-event timing of the kernels above on (1) or off (0). Events are recorded on the stream
+ * each kernel is launched on; timing adds two event records per launch. */
+relnn_status relnn_profile_enable(int32_t on);
+/* sync (waits for the recorded events). Total device milliseconds and launch count of kernel `id`
+ * accumulated since the last reset. */
+relnn_status relnn_profile_read(int32_t id, double* total_ms, int64_t* launches);
+relnn_status relnn_profile_reset(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ relnn_status copy_out_keys(const Plan& p, void* d_out_keys, cudaStream_t st) {
         RELNN_CUDA(cudaMemcpyAsync(d_out_keys, p.out_keys.p, sizeof(int64_t) * p.n_out, cudaMemcpyDeviceToDevice, st));
     } else {
         const int blocks = (int)std::min<int64_t>(ceil_div(p.n_out, 256), 4096);
-        keys_to_i32_kernel<<<blocks, 256, 0, st>>>(p.out_keys.as<int64_t>(), p.n_out, reinterpret_cast<int32_t*>(d_out_keys));
+        { keys_to_i32_kernel<<<blocks, 256, 0, st>>>(p.out_keys.as<int64_t>(), p.n_out, reinterpret_cast<int32_t*>(d_out_keys)); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
     }
     return RELNN_OK;
@@ -121,7 +121,9 @@ relnn_status relnn_rule_plan(const relnn_rule_desc* desc, void* stream, relnn_pl
     *out = nullptr;
     relnn_plan_s* p = new (std::nothrow) relnn_plan_s();
     if (!p) return RELNN_ENOMEM;
+    ProfToken pt = prof_begin(RELNN_PROF_PLAN, (cudaStream_t)stream);
     relnn_status s = build_plan(p->p, desc, (cudaStream_t)stream);
+    prof_end(pt, (cudaStream_t)stream);
     if (s != RELNN_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
         delete p;

@@ -201,17 +201,17 @@ relnn_status backward_fp32(Plan& p, const CallIO& io, const GradIO& g, cudaStrea
         RELNN_CHECK_ARG(smem <= 200 * 1024, "backward: tile too large");
         RELNN_CUDA(cudaFuncSetAttribute(bw_dy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int grid = (int)std::min<int64_t>(a.n_tiles, (int64_t)num_sms() * 4);
-        bw_dy_kernel<<<grid, threads, smem, st>>>(a);
+        { ProfToken pt = prof_begin(RELNN_PROF_BWD_FP32, st); bw_dy_kernel<<<grid, threads, smem, st>>>(a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
         if (need_w) {
             float* part = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + dy_bytes);
             float* dbpart = part + (size_t)nchunks * p.d_out * p.d_in;
             dim3 grid3((unsigned)ceil_div(p.d_out, kDwTile), (unsigned)ceil_div(p.d_in, kDwTile), (unsigned)nchunks);
-            bw_dw_kernel<<<grid3, 256, 0, st>>>(a, part, dbpart);
+            { ProfToken pt = prof_begin(RELNN_PROF_BWD_FP32, st); bw_dw_kernel<<<grid3, 256, 0, st>>>(a, part, dbpart); note_launch(); prof_end(pt, st); }
             RELNN_CUDA(cudaGetLastError());
             const int64_t nw = (int64_t)p.d_out * p.d_in;
-            if (g.dW[i]) bw_reduce_kernel<<<(int)std::min<int64_t>(ceil_div(nw, 256), 1024), 256, 0, st>>>(part, (int)nchunks, nw, g.dW[i]);
-            if (g.db[i]) bw_reduce_kernel<<<1, 256, 0, st>>>(dbpart, (int)nchunks, p.d_out, g.db[i]);
+            if (g.dW[i]) { bw_reduce_kernel<<<(int)std::min<int64_t>(ceil_div(nw, 256), 1024), 256, 0, st>>>(part, (int)nchunks, nw, g.dW[i]); note_launch(); }
+            if (g.db[i]) { bw_reduce_kernel<<<1, 256, 0, st>>>(dbpart, (int)nchunks, p.d_out, g.db[i]); note_launch(); }
             RELNN_CUDA(cudaGetLastError());
         }
     }

@@ -16,6 +16,17 @@ namespace relnn {
 void set_error(const std::string& msg);
 void set_device_error(int32_t code);
 
+// Counts every kernel launch made by the library (relnn_launch_count).
+void note_launch();
+
+// Optional CUDA-event timing of the main kernels (relnn_profile_*): a token brackets one launch.
+struct ProfToken {
+    int id = -1;
+    void* ev = nullptr;
+};
+ProfToken prof_begin(int id, cudaStream_t st);
+void prof_end(ProfToken& tok, cudaStream_t st);
+
 #define RELNN_CHECK_ARG(cond, msg)                  \
     do {                                           \
         if (!(cond)) {                             \

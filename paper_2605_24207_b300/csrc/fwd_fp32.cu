@@ -156,8 +156,10 @@ void launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, cons
     if (n_tiles <= 1) return;
     const int blocks = (int)std::min<int64_t>(n_tiles - 1, (int64_t)num_sms() * 8);
     const int threads = d_out >= 128 ? 128 : (d_out > 32 ? ((d_out + 31) / 32) * 32 : 32);
-    fixup_kernel<<<blocks, threads, 0, st>>>(seg, m, tile, n_tiles, carry, out, d_out, accumulate ? 1 : 0,
-                                             kahan ? 1 : 0);
+    ProfToken pt = prof_begin(RELNN_PROF_FIXUP, st);
+    { fixup_kernel<<<blocks, threads, 0, st>>>(seg, m, tile, n_tiles, carry, out, d_out, accumulate ? 1 : 0,
+                                             kahan ? 1 : 0); note_launch(); }
+    prof_end(pt, st);
 }
 
 relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
@@ -185,7 +187,7 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
         a.r_bf16 = io.r_bf16;
         a.d_r = b.d_r;
         if (!p.identity) {
-            transpose_w_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, p.scratch.as<float>());
+            { transpose_w_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, p.scratch.as<float>()); note_launch(); }
             a.Wt = p.scratch.as<float>();
             a.bias = io.br[i].b;
         }
@@ -205,7 +207,7 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
         a.out = out;
         a.carry = p.carry.as<float>();
         const int grid = (int)std::min<int64_t>(a.n_tiles, (int64_t)num_sms() * (smem > 100 * 1024 ? 1 : 4));
-        fwd_fp32_kernel<<<grid, threads, smem, st>>>(a);
+        { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); fwd_fp32_kernel<<<grid, threads, smem, st>>>(a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
         launch_fixup(a.seg, a.m, kTT, a.n_tiles, a.carry, out, p.d_out, multi, p.kahan, st);
         RELNN_CUDA(cudaGetLastError());

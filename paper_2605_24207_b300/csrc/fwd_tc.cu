@@ -432,8 +432,8 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         if (b.m == 0) continue;
-        pack_w_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, rows_pad, L.n_kb, d_meta,
-                                          d_meta + kMaxKb, p.wpack.as<uint16_t>());
+        { pack_w_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, rows_pad, L.n_kb, d_meta,
+                                          d_meta + kMaxKb, p.wpack.as<uint16_t>()); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
         TcArgs a{};
         a.z = io.z;
@@ -473,7 +473,7 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
             a.kb_width[k] = L.width[k];
         }
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
-        fwd_tc_kernel<<<grid, kThreads, smem, st>>>(wmap, a);
+        { ProfToken pt = prof_begin(RELNN_PROF_FWD_TC, st); fwd_tc_kernel<<<grid, kThreads, smem, st>>>(wmap, a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
         launch_fixup(a.seg, a.m, tile_n, a.n_tiles, a.carry, out, p.d_out, multi, p.kahan, st);
         RELNN_CUDA(cudaGetLastError());

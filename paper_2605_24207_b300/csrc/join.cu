@@ -165,7 +165,7 @@ relnn_status key_range(const void* keys, int64_t n, int kt, int64_t* kmin, int64
     RELNN_CUDA(cudaMallocAsync(&mm, 16, st));
     unsigned long long init[2] = {~0ull, 0ull};
     cudaMemcpyAsync(mm, init, 16, cudaMemcpyHostToDevice, st);
-    key_minmax_kernel<<<grid_for(n), 256, 0, st>>>(keys, n, kt, mm);
+    { key_minmax_kernel<<<grid_for(n), 256, 0, st>>>(keys, n, kt, mm); note_launch(); }
     unsigned long long h[2];
     cudaMemcpyAsync(h, mm, 16, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(mm, st);
@@ -212,15 +212,15 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     int32_t* rows = jt.rows_sorted.as<int32_t>();
     const int g = grid_for(n);
     if (narrow) {
-        make_sort_keys_kernel<uint32_t><<<g, 256, 0, st>>>(keys, n, kt, omin, sk.as<uint32_t>(), rows);
+        { make_sort_keys_kernel<uint32_t><<<g, 256, 0, st>>>(keys, n, kt, omin, sk.as<uint32_t>(), rows); note_launch(); }
         RELNN_TRY(radix_sort_pairs<uint32_t>(sk.as<uint32_t>(), rows, sk_tmp.as<uint32_t>(),
                                              rows_tmp.as<int32_t>(), n, nbits, st));
-        run_flags_kernel<uint32_t><<<g, 256, 0, st>>>(sk.as<uint32_t>(), n, flags.as<int32_t>());
+        { run_flags_kernel<uint32_t><<<g, 256, 0, st>>>(sk.as<uint32_t>(), n, flags.as<int32_t>()); note_launch(); }
     } else {
-        make_sort_keys_kernel<uint64_t><<<g, 256, 0, st>>>(keys, n, kt, omin, sk.as<uint64_t>(), rows);
+        { make_sort_keys_kernel<uint64_t><<<g, 256, 0, st>>>(keys, n, kt, omin, sk.as<uint64_t>(), rows); note_launch(); }
         RELNN_TRY(radix_sort_pairs<uint64_t>(sk.as<uint64_t>(), rows, sk_tmp.as<uint64_t>(),
                                              rows_tmp.as<int32_t>(), n, nbits, st));
-        run_flags_kernel<uint64_t><<<g, 256, 0, st>>>(sk.as<uint64_t>(), n, flags.as<int32_t>());
+        { run_flags_kernel<uint64_t><<<g, 256, 0, st>>>(sk.as<uint64_t>(), n, flags.as<int32_t>()); note_launch(); }
     }
     RELNN_TRY(exclusive_scan<int32_t>(flags.as<int32_t>(), flags.as<int32_t>(), n,
                                       flags.as<int32_t>() + n, st));
@@ -232,13 +232,13 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     RELNN_TRY(jt.run_start.alloc(sizeof(int32_t) * (U + 1)));
     RELNN_TRY(jt.ukeys.alloc(sizeof(int64_t) * std::max<int64_t>(U, 1)));
     if (narrow)
-        runs_kernel<uint32_t><<<g, 256, 0, st>>>(sk.as<uint32_t>(), flags.as<int32_t>(), n, omin,
+        { runs_kernel<uint32_t><<<g, 256, 0, st>>>(sk.as<uint32_t>(), flags.as<int32_t>(), n, omin,
                                                  jt.run_start.as<int32_t>(), jt.uid_of_pos.as<int32_t>(),
-                                                 jt.ukeys.as<int64_t>(), U);
+                                                 jt.ukeys.as<int64_t>(), U); note_launch(); }
     else
-        runs_kernel<uint64_t><<<g, 256, 0, st>>>(sk.as<uint64_t>(), flags.as<int32_t>(), n, omin,
+        { runs_kernel<uint64_t><<<g, 256, 0, st>>>(sk.as<uint64_t>(), flags.as<int32_t>(), n, omin,
                                                  jt.run_start.as<int32_t>(), jt.uid_of_pos.as<int32_t>(),
-                                                 jt.ukeys.as<int64_t>(), U);
+                                                 jt.ukeys.as<int64_t>(), U); note_launch(); }
     // Lookup: direct addressing when the key span is at most 4x the distinct keys (+1M slack).
     const uint64_t direct_limit = (uint64_t)std::max<int64_t>(4 * U, 1 << 20);
     if (span < direct_limit) {
@@ -246,9 +246,9 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
         jt.direct_size = (int64_t)span + 1;
         jt.cap = 0;
         RELNN_TRY(jt.slot_vals.alloc(sizeof(int32_t) * jt.direct_size));
-        fill_i32_kernel<<<grid_for(jt.direct_size), 256, 0, st>>>(jt.slot_vals.as<int32_t>(), jt.direct_size, -1);
-        direct_insert_kernel<<<grid_for(U), 256, 0, st>>>(jt.ukeys.as<int64_t>(), U, kmin,
-                                                          jt.slot_vals.as<int32_t>());
+        { fill_i32_kernel<<<grid_for(jt.direct_size), 256, 0, st>>>(jt.slot_vals.as<int32_t>(), jt.direct_size, -1); note_launch(); }
+        { direct_insert_kernel<<<grid_for(U), 256, 0, st>>>(jt.ukeys.as<int64_t>(), U, kmin,
+                                                          jt.slot_vals.as<int32_t>()); note_launch(); }
     } else {
         jt.mode = 0;
         uint64_t cap = 1024;
@@ -256,11 +256,11 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
         jt.cap = cap;
         RELNN_TRY(jt.slot_keys.alloc(sizeof(int64_t) * cap));
         RELNN_TRY(jt.slot_vals.alloc(sizeof(int32_t) * cap));
-        fill_i64_kernel<<<grid_for(cap), 256, 0, st>>>(jt.slot_keys.as<int64_t>(), cap, kEmptyKey);
-        fill_i32_kernel<<<grid_for(cap), 256, 0, st>>>(jt.slot_vals.as<int32_t>(), cap, -1);
-        hash_insert_kernel<<<grid_for(U), 256, 0, st>>>(jt.ukeys.as<int64_t>(), U, cap - 1,
+        { fill_i64_kernel<<<grid_for(cap), 256, 0, st>>>(jt.slot_keys.as<int64_t>(), cap, kEmptyKey); note_launch(); }
+        { fill_i32_kernel<<<grid_for(cap), 256, 0, st>>>(jt.slot_vals.as<int32_t>(), cap, -1); note_launch(); }
+        { hash_insert_kernel<<<grid_for(U), 256, 0, st>>>(jt.ukeys.as<int64_t>(), U, cap - 1,
                                                         jt.slot_keys.as<unsigned long long>(),
-                                                        jt.slot_vals.as<int32_t>(), jt.status.as<int>());
+                                                        jt.slot_vals.as<int32_t>(), jt.status.as<int>()); note_launch(); }
     }
     RELNN_CUDA(cudaGetLastError());
     int dev_status = 0;
@@ -287,7 +287,7 @@ relnn_status join_probe_pairs(const JoinTable& jt, const void* probe, int64_t m,
     RELNN_TRY(wt.alloc(sizeof(int64_t) * (nwarps + 1)));
     const JoinView v = jt.view();
     const int blocks = (int)ceil_div(m, 256);
-    probe_count_kernel<<<blocks, 256, 0, st>>>(v, probe, m, jt.kt, uarr.as<int32_t>(), wt.as<int64_t>());
+    { probe_count_kernel<<<blocks, 256, 0, st>>>(v, probe, m, jt.kt, uarr.as<int32_t>(), wt.as<int64_t>()); note_launch(); }
     RELNN_TRY(exclusive_scan<int64_t>(wt.as<int64_t>(), wt.as<int64_t>(), nwarps, wt.as<int64_t>() + nwarps, st));
     int64_t total = 0;
     RELNN_CUDA(cudaMemcpyAsync(&total, wt.as<int64_t>() + nwarps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -298,7 +298,7 @@ relnn_status join_probe_pairs(const JoinTable& jt, const void* probe, int64_t m,
         set_error("join probe: " + std::to_string(total) + " pairs exceed capacity " + std::to_string(capacity));
         return RELNN_ENOSPC;
     }
-    probe_emit_kernel<<<blocks, 256, 0, st>>>(v, uarr.as<int32_t>(), m, wt.as<int64_t>(), probe_idx, build_idx);
+    { probe_emit_kernel<<<blocks, 256, 0, st>>>(v, uarr.as<int32_t>(), m, wt.as<int64_t>(), probe_idx, build_idx); note_launch(); }
     RELNN_CUDA(cudaGetLastError());
     RELNN_CUDA(cudaStreamSynchronize(st));
     return RELNN_OK;

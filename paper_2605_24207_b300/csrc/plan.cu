@@ -159,8 +159,8 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
     RELNN_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(int64_t) * (nwarps + 1), st));
     const int blocks = (int)ceil_div(std::max<int64_t>(T, 1), 256);
     if (T > 0)
-        tri_count_kernel<<<blocks, 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst,
-                                                 us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>());
+        { tri_count_kernel<<<blocks, 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst,
+                                                 us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>()); note_launch(); }
     RELNN_TRY(exclusive_scan<int64_t>(wt.as<int64_t>(), wt.as<int64_t>(), nwarps, wt.as<int64_t>() + nwarps, st));
     int64_t M = 0;
     RELNN_CUDA(cudaMemcpyAsync(&M, wt.as<int64_t>() + nwarps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -194,13 +194,13 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
     RELNN_TRY(t.perm_tmp.alloc(4 * m1));
     if (T > 0) {
         if (t.wide)
-            tri_emit_kernel<uint64_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
+            { tri_emit_kernel<uint64_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
                 us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>(), t.t_hs.as<int32_t>(),
-                t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(), t.key.as<uint64_t>());
+                t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(), t.key.as<uint64_t>()); note_launch(); }
         else
-            tri_emit_kernel<uint32_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
+            { tri_emit_kernel<uint32_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
                 us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>(), t.t_hs.as<int32_t>(),
-                t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(), t.key.as<uint32_t>());
+                t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(), t.key.as<uint32_t>()); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
     }
     RELNN_TRY(iota_i32(t.perm.as<int32_t>(), M, st));
@@ -215,9 +215,9 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
     RELNN_TRY(b.er.alloc(4 * m1));
     RELNN_TRY(b.seg.alloc(4 * (m1 + 1)));
     if (M > 0)
-        gather3_kernel<<<grid_for(M), 256, 0, st>>>(t.perm.as<int32_t>(), M, t.t_hs.as<int32_t>(),
+        { gather3_kernel<<<grid_for(M), 256, 0, st>>>(t.perm.as<int32_t>(), M, t.t_hs.as<int32_t>(),
                                                     t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(),
-                                                    b.hs.as<int32_t>(), b.hd.as<int32_t>(), b.er.as<int32_t>());
+                                                    b.hs.as<int32_t>(), b.hd.as<int32_t>(), b.er.as<int32_t>()); note_launch(); }
     RELNN_CUDA(cudaGetLastError());
     return RELNN_OK;
 }
@@ -279,8 +279,8 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         RELNN_TRY(out_row.alloc(sizeof(int32_t) * (U + 1)));
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
-                mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
-                    tmp[i].key.as<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), present.as<int32_t>());
+                { mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                    tmp[i].key.as<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), present.as<int32_t>()); note_launch(); }
         RELNN_TRY(exclusive_scan<int32_t>(present.as<int32_t>(), out_row.as<int32_t>(), U, out_row.as<int32_t>() + U, st));
         int32_t nout = 0;
         RELNN_CUDA(cudaMemcpyAsync(&nout, out_row.as<int32_t>() + U, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -288,13 +288,13 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         p.n_out = nout;
         RELNN_TRY(p.out_keys.alloc(sizeof(int64_t) * std::max<int64_t>(nout, 1)));
         if (U > 0)
-            out_keys_kernel<<<grid_for(U), 256, 0, st>>>(present.as<int32_t>(), out_row.as<int32_t>(),
-                                                         p.H.ukeys.as<int64_t>(), U, p.out_keys.as<int64_t>());
+            { out_keys_kernel<<<grid_for(U), 256, 0, st>>>(present.as<int32_t>(), out_row.as<int32_t>(),
+                                                         p.H.ukeys.as<int64_t>(), U, p.out_keys.as<int64_t>()); note_launch(); }
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
-                seg_from_pos_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                { seg_from_pos_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
                     tmp[i].key.as<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), out_row.as<int32_t>(),
-                    p.br[i].seg.as<int32_t>());
+                    p.br[i].seg.as<int32_t>()); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
         RELNN_CUDA(cudaStreamSynchronize(st));
     } else {
@@ -304,8 +304,8 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         DevBuf flags;
         RELNN_TRY(flags.alloc(sizeof(int32_t) * (M + 1)));
         if (M > 0) {
-            if (t.wide) key_flags_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), M, flags.as<int32_t>());
-            else key_flags_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), M, flags.as<int32_t>());
+            if (t.wide) { key_flags_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), M, flags.as<int32_t>()); note_launch(); }
+            else { key_flags_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), M, flags.as<int32_t>()); note_launch(); }
         }
         RELNN_TRY(exclusive_scan<int32_t>(flags.as<int32_t>(), flags.as<int32_t>(), M, flags.as<int32_t>() + M, st));
         int32_t nout = 0;
@@ -315,11 +315,11 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         RELNN_TRY(p.out_keys.alloc(sizeof(int64_t) * std::max<int64_t>(nout, 1)));
         if (M > 0) {
             if (t.wide)
-                raw_seg_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), flags.as<int32_t>(), M,
-                                                                      t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>());
+                { raw_seg_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), flags.as<int32_t>(), M,
+                                                                      t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>()); note_launch(); }
             else
-                raw_seg_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), flags.as<int32_t>(), M,
-                                                                      t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>());
+                { raw_seg_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), flags.as<int32_t>(), M,
+                                                                      t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>()); note_launch(); }
         }
         RELNN_CUDA(cudaGetLastError());
         RELNN_CUDA(cudaStreamSynchronize(st));

@@ -188,16 +188,16 @@ relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream
     }
     const int64_t nb = ceil_div(n, kScanTile);
     if (nb == 1) {
-        scan_apply_kernel<T><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
+        { scan_apply_kernel<T><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
         return RELNN_OK;
     }
     T* sums = nullptr;
     RELNN_CUDA(cudaMallocAsync(&sums, sizeof(T) * nb, st));
-    scan_reduce_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
+    { scan_reduce_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums); note_launch(); }
     relnn_status s = exclusive_scan<T>(sums, sums, nb, nullptr, st);
     if (s == RELNN_OK) {
-        scan_apply_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums, total);
+        { scan_apply_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums, total); note_launch(); }
         if (cudaGetLastError() != cudaSuccess) s = RELNN_ECUDA;
     }
     cudaFreeAsync(sums, st);
@@ -221,10 +221,10 @@ relnn_status radix_sort_pairs(K* keys, int32_t* vals, K* keys_tmp, int32_t* vals
     relnn_status s = RELNN_OK;
     int passes = 0;
     for (int shift = 0; shift < nbits; shift += 8, ++passes) {
-        rs_hist_kernel<K><<<nb, kSortThreads, 0, st>>>(src_k, n, shift, hist, nb);
+        { rs_hist_kernel<K><<<nb, kSortThreads, 0, st>>>(src_k, n, shift, hist, nb); note_launch(); }
         s = exclusive_scan<int32_t>(hist, hist, (int64_t)256 * nb, nullptr, st);
         if (s != RELNN_OK) break;
-        rs_scatter_kernel<K><<<nb, kSortThreads, 0, st>>>(src_k, src_v, dst_k, dst_v, n, shift, hist, nb);
+        { rs_scatter_kernel<K><<<nb, kSortThreads, 0, st>>>(src_k, src_v, dst_k, dst_v, n, shift, hist, nb); note_launch(); }
         if (cudaGetLastError() != cudaSuccess) {
             s = RELNN_ECUDA;
             break;
@@ -247,7 +247,7 @@ template relnn_status radix_sort_pairs<uint64_t>(uint64_t*, int32_t*, uint64_t*,
 relnn_status iota_i32(int32_t* out, int64_t n, cudaStream_t st) {
     if (n <= 0) return RELNN_OK;
     int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 148 * 16);
-    iota_kernel<<<blocks, 256, 0, st>>>(out, n);
+    { iota_kernel<<<blocks, 256, 0, st>>>(out, n); note_launch(); }
     RELNN_CUDA(cudaGetLastError());
     return RELNN_OK;
 }

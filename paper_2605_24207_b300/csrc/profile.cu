@@ -1,0 +1,111 @@
+// Launch counter and optional per-kernel CUDA-event timing (relnn_launch_count, relnn_profile_*).
+// Events are recorded on the stream the kernel is launched on, so the elapsed time is that of the
+// launch as the device ran it inside the caller's stream order.
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace relnn {
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_prof_on{0};
+std::mutex g_mu;
+
+struct EvPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int id = -1;
+};
+std::vector<EvPair*> g_free, g_pending;
+constexpr int kIds = 16;
+double g_total_ms[kIds];
+int64_t g_count[kIds];
+
+EvPair* take() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_free.empty()) {
+        EvPair* e = g_free.back();
+        g_free.pop_back();
+        return e;
+    }
+    EvPair* e = new EvPair();
+    if (cudaEventCreate(&e->a) != cudaSuccess || cudaEventCreate(&e->b) != cudaSuccess) {
+        delete e;
+        return nullptr;
+    }
+    return e;
+}
+
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfToken prof_begin(int id, cudaStream_t st) {
+    ProfToken t;
+    if (!g_prof_on.load(std::memory_order_relaxed) || id < 0 || id >= kIds) return t;
+    EvPair* e = take();
+    if (!e) return t;
+    e->id = id;
+    cudaEventRecord(e->a, st);
+    t.id = id;
+    t.ev = e;
+    return t;
+}
+
+void prof_end(ProfToken& tok, cudaStream_t st) {
+    if (!tok.ev) return;
+    EvPair* e = reinterpret_cast<EvPair*>(tok.ev);
+    cudaEventRecord(e->b, st);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_pending.push_back(e);
+    tok.ev = nullptr;
+}
+
+}  // namespace relnn
+
+using namespace relnn;
+
+extern "C" {
+
+uint64_t relnn_launch_count(void) { return g_launches.load(); }
+
+relnn_status relnn_profile_enable(int32_t on) {
+    g_prof_on.store(on ? 1 : 0);
+    return RELNN_OK;
+}
+
+relnn_status relnn_profile_read(int32_t id, double* total_ms, int64_t* launches) {
+    RELNN_CHECK_ARG(id >= 0 && id < kIds, "profile: bad id");
+    std::vector<EvPair*> done;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        done.swap(g_pending);
+    }
+    for (EvPair* e : done) {
+        cudaEventSynchronize(e->b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e->a, e->b) == cudaSuccess) {
+            g_total_ms[e->id] += ms;
+            g_count[e->id] += 1;
+        }
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_free.push_back(e);
+    }
+    if (total_ms) *total_ms = g_total_ms[id];
+    if (launches) *launches = g_count[id];
+    return RELNN_OK;
+}
+
+relnn_status relnn_profile_reset(void) {
+    relnn_profile_read(0, nullptr, nullptr);
+    for (int i = 0; i < kIds; ++i) {
+        g_total_ms[i] = 0.0;
+        g_count[i] = 0;
+    }
+    return RELNN_OK;
+}
+
+}  // extern "C"

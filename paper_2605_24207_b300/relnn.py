@@ -58,7 +58,9 @@ EXPORTS = [
     "relnn_join_build", "relnn_join_probe", "relnn_join_destroy",
     "relnn_rule_plan", "relnn_plan_info", "relnn_plan_out_keys", "relnn_plan_check",
     "relnn_rule_forward", "relnn_rule_backward", "relnn_plan_destroy",
+    "relnn_profile_enable", "relnn_profile_read", "relnn_profile_reset", "relnn_launch_count",
 ]
+PROF_FWD_TC, PROF_FWD_FP32, PROF_FIXUP, PROF_BWD_TC, PROF_BWD_FP32, PROF_PLAN = range(6)
 
 
 def lib():
@@ -84,8 +86,11 @@ def lib():
     L.relnn_rule_forward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp]
     L.relnn_rule_backward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp, vp, vp]
     L.relnn_plan_destroy.argtypes = [vp]
-    for name in EXPORTS[4:]:
+    L.relnn_profile_enable.argtypes = [C.c_int32]
+    L.relnn_profile_read.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(i64)]
+    for name in EXPORTS[4:-1]:
         getattr(L, name).restype = C.c_int
+    L.relnn_launch_count.restype = C.c_uint64
     _LIB = L
     return L
 
@@ -122,6 +127,26 @@ def _float_type(t: torch.Tensor) -> int:
     if t.dtype == torch.bfloat16:
         return BF16
     raise TypeError(f"embeddings must be float32 or bfloat16, got {t.dtype}")
+
+
+def launch_count() -> int:
+    """Kernels launched by librelnn since it was loaded."""
+    return int(lib().relnn_launch_count())
+
+
+def profile_enable(on: bool = True):
+    _check(lib().relnn_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(lib().relnn_profile_reset())
+
+
+def profile_read(kernel_id: int):
+    """(total device ms, launches) of a library kernel since the last reset (waits for events)."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().relnn_profile_read(kernel_id, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 # ------------------------------------------------------------------------------------------ join
