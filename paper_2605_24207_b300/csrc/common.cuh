@@ -154,6 +154,19 @@ __device__ __forceinline__ float bf16_to_f32(uint16_t h) {
     return __uint_as_float(((uint32_t)h) << 16);
 }
 
+// Writes one output element. Single-branch rules write every output row exactly once (streaming
+// store); unions add the later branches into rows the earlier ones wrote, so only that path reads
+// the old value (the read is volatile asm so that it is never hoisted onto the store-only path).
+__device__ __forceinline__ void emit_out(float* dst, float v, int accumulate) {
+    if (accumulate) {
+        float old;
+        asm volatile("ld.global.f32 %0, [%1];" : "=f"(old) : "l"(dst) : "memory");
+        __stcg(dst, old + v);
+    } else {
+        __stcs(dst, v);
+    }
+}
+
 // Kahan step: sum += v with compensation c (never contracted into FMA).
 __device__ __forceinline__ void kahan_add(float& sum, float& c, float v) {
     float y = __fsub_rn(v, c);

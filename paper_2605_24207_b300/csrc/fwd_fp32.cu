@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(Fp32Args a) {
                         a.carry[(tile * 2 + (first ? 0 : 1)) * a.d_out + o] = acc;
                     } else {
                         float* dst = a.out + (int64_t)s * a.d_out + o;
-                        *dst = a.accumulate ? *dst + acc : acc;
+                        emit_out(dst, acc, a.accumulate);
                     }
                     acc = 0.f;
                     comp = 0.f;
@@ -134,7 +134,7 @@ __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int til
                 else break;
             }
             float* dst = out + (int64_t)s * d_out + o;
-            *dst = accumulate ? *dst + acc : acc;
+            emit_out(dst, acc, accumulate);
         }
     }
 }

@@ -30,7 +30,7 @@ constexpr int kThreads = 288;
 constexpr int kProducerThreads = 128;
 constexpr int kMmaWarp = 4;  // warps 5..8 are the epilogue
 constexpr int kMaxKb = 12;
-constexpr int kLag = 2;  // cp.async groups kept in flight per producer thread before arriving
+constexpr int kMaxLag = 6;  // cp.async groups a producer thread may keep in flight before arriving
 constexpr int kSmemLimit = 227 * 1024;
 
 struct TcArgs {
@@ -49,12 +49,49 @@ struct TcArgs {
     int64_t n_tiles;
     int z_bf16, r_bf16, d, d_r;
     int d_out, act, kahan, accumulate;
-    int n_kb, tile_n, m_blocks, stages, mask_words;
+    int n_kb, tile_n, m_blocks, stages, lag, mask_words;
     uint32_t idesc, tmem_cols;
     int kb_src[kMaxKb];   // 0: z[hs], 1: z[hd], 2: r[er]
     int kb_col[kMaxKb];   // first element of the block within its part
     int kb_width[kMaxKb]; // width of that part
+    int need_arr[3];      // which of hs, hd, er the K blocks read
 };
+
+// Segmented running sum over the 32 tuples of a chunk held by one epilogue thread (one feature):
+// y = acc + bias (ReLU'd), sum restarts at every row whose bit is set in `startmask`, and v[j] is
+// replaced by the sum of its piece up to row j. Branch-free, so the unrolled body stays small.
+template <bool RELU, bool KAHAN, bool MASK>
+__device__ __forceinline__ void seg_scan(uint32_t (&v)[32], float bo, unsigned startmask, float& sum, float& comp,
+                                         uint32_t& mword, int lane) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        float y = __uint_as_float(v[j]) + bo;
+        if (RELU) {
+            if (MASK) {
+                const unsigned w = __ballot_sync(0xffffffffu, y > 0.f);
+                mword = (lane == j) ? w : mword;
+            }
+            y = fmaxf(y, 0.f);
+        }
+        const bool st = (startmask >> j) & 1u;
+        if (KAHAN) {
+            sum = st ? 0.f : sum;
+            comp = st ? 0.f : comp;
+            kahan_add(sum, comp, y);
+        } else {
+            sum = st ? y : sum + y;
+        }
+        v[j] = __float_as_uint(sum);
+    }
+}
+
+// v[j] for a warp-uniform run-time j without local-memory indexing.
+__device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], int j) {
+    uint32_t r = v[0];
+#pragma unroll
+    for (int i = 1; i < 32; ++i) r = (j == i) ? v[i] : r;
+    return r;
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
 fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ TcArgs a) {
@@ -64,7 +101,11 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
     const uint32_t stage_bytes = (uint32_t)a.tile_n * 128u;
     uint8_t* w_smem = base;
     uint8_t* st_smem = base + w_bytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(st_smem + (size_t)a.stages * stage_bytes);
+    // row indices of the tile being gathered (2 slots x {hs, hd, er} x tile_n), filled one tile ahead
+    int32_t* idx_smem = reinterpret_cast<int32_t*>(st_smem + (size_t)a.stages * stage_bytes);
+    // output rows of the tile being reduced, one copy per epilogue warp
+    int32_t* seg_smem = idx_smem + 6 * a.tile_n;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(seg_smem + 4 * a.tile_n);
     uint64_t* full = bars;
     uint64_t* empty = bars + a.stages;
     uint64_t* tfull = bars + 2 * a.stages;
@@ -100,45 +141,73 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
 
     if (warp < 4) {
         // ------------------------------------------------------------------ producers
+        // Thread (row group rg, 16-byte chunk) copies chunk `chunk` of rows [rg*rpt, rg*rpt + rpt) of
+        // every K block; the 8 threads of a row group read one 128-byte row segment together.
         const int chunk = tid & 7;
-        const int row0 = tid >> 3;  // 0..15
-        const int rows_per_thread = a.tile_n / 16;
+        const int rpt = a.tile_n >> 4;
+        const int row_base = (tid >> 3) * rpt;
+        const int32_t* arrs[3] = {a.hs, a.hd, a.er};
+        const int per_thr = a.tile_n / kProducerThreads;  // index entries each thread stages per array
+        // stage the first tile's row indices
+        {
+            const int64_t t0 = (int64_t)blockIdx.x * a.tile_n;
+            for (int r = 0; r < 3; ++r) {
+                if (!a.need_arr[r]) continue;
+                for (int k = 0; k < per_thr; ++k) {
+                    const int qq = tid + k * kProducerThreads;
+                    idx_smem[r * a.tile_n + qq] = (t0 + qq < a.m) ? __ldg(arrs[r] + t0 + qq) : 0;
+                }
+            }
+        }
+        named_bar_sync(1, kProducerThreads);
         int it = 0;
         int pending = 0;  // stages issued but not yet arrived
         bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int64_t t0 = tile * a.tile_n;
-            for (int kb = 0; kb < a.n_kb && ok; ++kb, ++it) {
+            const int slot = lt & 1;
+            const int32_t* islot = idx_smem + slot * 3 * a.tile_n;
+            // prefetch the next tile's indices into registers (stored after this tile's K blocks)
+            const int64_t tn = (tile + gridDim.x) * a.tile_n;
+            int pre[3][2];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int qq = tid + k * kProducerThreads;
+                    pre[r][k] = (a.need_arr[r] && k < per_thr && tn + qq < a.m) ? __ldg(arrs[r] + tn + qq) : 0;
+                }
+            for (int kb = 0; kb < a.n_kb; ++kb) {
+                if (!ok) break;
                 const int s = it % a.stages;
                 const uint32_t ph = (uint32_t)((it / a.stages) & 1);
                 if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.status, abort_flag)) { ok = false; break; }
                 const int src = a.kb_src[kb];
                 const int col = a.kb_col[kb] + chunk * 8;
-                const int width = a.kb_width[kb];
-                const bool in_part = col < width;
-                const int32_t* idx_arr = src == 0 ? a.hs : (src == 1 ? a.hd : a.er);
+                const bool in_part = col < a.kb_width[kb];
+                const int32_t* rows_idx = islot + src * a.tile_n;
                 const void* tbl = src == 2 ? a.r : a.z;
                 const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
                 const int row_elems = src == 2 ? a.d_r : a.d;
                 const uint32_t sbase = smem_u32(st_smem + (size_t)s * stage_bytes);
-                for (int j = 0; j < rows_per_thread; ++j) {
-                    const int row = row0 + 16 * j;
-                    const int64_t t = t0 + row;
+                for (int j = 0; j < rpt; ++j) {
+                    const int row = row_base + j;
                     const uint32_t dst = sbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
-                    const bool valid = (t < a.m) && in_part;
+                    const bool valid = (t0 + row < a.m) && in_part;
+                    const int64_t ridx = rows_idx[row];
                     if (tbl_bf16) {
                         const uint16_t* p = reinterpret_cast<const uint16_t*>(tbl);
-                        const uint16_t* srcp = p;
-                        if (valid) srcp = p + (int64_t)idx_arr[t] * row_elems + col;
+                        const uint16_t* srcp = valid ? p + ridx * row_elems + col : p;
                         if (src == 2) cp_async_16_stream(dst, srcp, valid ? 16u : 0u);
                         else cp_async_16(dst, srcp, valid ? 16u : 0u);
                     } else {
                         uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
                         if (valid) {
-                            const float4* q = reinterpret_cast<const float4*>(
-                                reinterpret_cast<const float*>(tbl) + (int64_t)idx_arr[t] * row_elems + col);
-                            const float4 u = __ldg(q);
-                            const float4 v = __ldg(q + 1);
+                            const float4* qp = reinterpret_cast<const float4*>(
+                                reinterpret_cast<const float*>(tbl) + ridx * row_elems + col);
+                            const float4 u = __ldg(qp);
+                            const float4 v = __ldg(qp + 1);
                             w0 = pack_bf16x2(u.x, u.y);
                             w1 = pack_bf16x2(u.z, u.w);
                             w2 = pack_bf16x2(v.x, v.y);
@@ -149,13 +218,22 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 }
                 cp_async_commit();
                 ++pending;
-                if (pending > kLag) {
-                    cp_async_wait<kLag>();
+                ++it;
+                if (pending > a.lag) {
+                    cp_async_wait_n(a.lag);
                     fence_proxy_async();
-                    mbar_arrive(smem_u32(&full[(it - kLag) % a.stages]));
+                    mbar_arrive(smem_u32(&full[(it - 1 - a.lag) % a.stages]));
                     --pending;
                 }
             }
+            // publish the next tile's indices in the other slot (read by nobody since the last barrier)
+            int32_t* oslot = idx_smem + (slot ^ 1) * 3 * a.tile_n;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (k < per_thr) oslot[r * a.tile_n + tid + k * kProducerThreads] = pre[r][k];
+            named_bar_sync(1, kProducerThreads);
         }
         cp_async_wait<0>();
         fence_proxy_async();
@@ -208,15 +286,37 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
     } else {
         // ------------------------------------------------------------------ epilogue
         const int q = warp & 3;  // TMEM lane quarter this warp may access
+        int32_t* wseg = seg_smem + (warp - kMmaWarp - 1) * a.tile_n;
+        // output rows of the next tile, loaded one tile ahead (8 x 32 = up to 256 tuples)
+        int pf[8];
+        int pf_prev = -1, pf_after = -1;
+        auto prefetch = [&](int64_t tile) {
+            const int64_t t0 = tile * a.tile_n;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int64_t t = t0 + 32 * c + lane;
+                pf[c] = (tile < a.n_tiles && 32 * c < a.tile_n && t < a.m) ? __ldg(a.seg + t) : -1;
+            }
+            pf_prev = (tile < a.n_tiles && t0 > 0) ? __ldg(a.seg + t0 - 1) : -1;
+            pf_after = (tile < a.n_tiles && t0 + a.tile_n < a.m) ? __ldg(a.seg + t0 + a.tile_n) : -1;
+        };
+        prefetch(blockIdx.x);
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int acc = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (32 * c < a.tile_n) wseg[32 * c + lane] = pf[c];
+            const int prev_seg = pf_prev;
+            const int after_seg = pf_after;
+            __syncwarp();
+            prefetch(tile + gridDim.x);
             if (!mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag)) break;
             tc_fence_after();
             const int64_t t0 = tile * a.tile_n;
             const int nt = (int)imin64(a.tile_n, a.m - t0);
-            const int prev_seg = t0 > 0 ? a.seg[t0 - 1] : -1;
             for (int mb = 0; mb < a.m_blocks; ++mb) {
                 const int obase = mb * 128 + 32 * q;
                 if (obase >= a.d_out) continue;
@@ -225,55 +325,50 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 const float bo = (a.bias && o_ok) ? a.bias[o] : 0.f;
                 float sum = 0.f, comp = 0.f;
                 bool first = true;
+                unsigned prev_end = 1u;  // did the tuple before this chunk end a piece? (tile start: yes)
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_stride +
                                        (uint32_t)mb * a.tile_n;
+                const bool relu = a.act == RELNN_ACT_RELU;
+                const bool mask = relu && a.relu_mask != nullptr;
                 for (int c = 0; c * 32 < nt; ++c) {
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
                     tmem_ld_wait();
-                    const int64_t tr = t0 + c * 32 + lane;   // this lane's tuple for the seg load
-                    const bool tvalid = (c * 32 + lane) < nt;
-                    const int sg = tvalid ? a.seg[tr] : -1;
-                    int nx = __shfl_down_sync(0xffffffffu, sg, 1);
-                    if (lane == 31) nx = (tr + 1 < a.m) ? a.seg[tr + 1] : -1;
-                    // the last valid row's successor may lie past the tile (or past m)
-                    const int last_row = nt - 1 - c * 32;  // index in this chunk of the tile's last row
-                    if (lane == last_row && lane < 31) nx = (tr + 1 < a.m) ? a.seg[tr + 1] : -1;
-                    const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && sg != nx);
+                    const int li = c * 32 + lane;  // this lane's row in the tile
+                    const bool tvalid = li < nt;
+                    // a piece ends at row j if the next row has another output row or j is the tile's
+                    // last row; it starts at j if row j-1 ended one
+                    const int sg = wseg[li];
+                    const int nx = (li + 1 < a.tile_n) ? wseg[li + 1] : after_seg;
+                    const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && (sg != nx || li == nt - 1));
+                    const unsigned startmask = (endmask << 1) | prev_end;
+                    prev_end = endmask >> 31;
                     uint32_t mword = 0;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if (c * 32 + j >= nt) break;
-                        float y = __uint_as_float(v[j]) + bo;
-                        if (a.act == RELNN_ACT_RELU) {
-                            if (a.relu_mask) {
-                                const unsigned w = __ballot_sync(0xffffffffu, y > 0.f);
-                                if (lane == j) mword = w;
-                            }
-                            y = fmaxf(y, 0.f);
-                        }
-                        if (a.kahan) kahan_add(sum, comp, y);
-                        else sum += y;
-                        const bool last = (c * 32 + j == nt - 1);
-                        if (((endmask >> j) & 1u) || last) {
-                            const int s = __shfl_sync(0xffffffffu, sg, j);
-                            const int sn = __shfl_sync(0xffffffffu, nx, j);
-                            const bool split = (first && prev_seg == s) || (last && sn == s);
-                            if (o_ok) {
-                                if (split) {
-                                    a.carry[(tile * 2 + (first ? 0 : 1)) * a.d_out + o] = sum;
-                                } else {
-                                    float* dst = a.out + (int64_t)s * a.d_out + o;
-                                    *dst = a.accumulate ? *dst + sum : sum;
-                                }
-                            }
-                            sum = 0.f;
-                            comp = 0.f;
-                            first = false;
-                        }
+                    // segmented running sum over the chunk: v[j] <- sum of its piece up to row j
+                    if (a.kahan) {
+                        if (mask) seg_scan<true, true, true>(v, bo, startmask, sum, comp, mword, lane);
+                        else if (relu) seg_scan<true, true, false>(v, bo, startmask, sum, comp, mword, lane);
+                        else seg_scan<false, true, false>(v, bo, startmask, sum, comp, mword, lane);
+                    } else {
+                        if (mask) seg_scan<true, false, true>(v, bo, startmask, sum, comp, mword, lane);
+                        else if (relu) seg_scan<true, false, false>(v, bo, startmask, sum, comp, mword, lane);
+                        else seg_scan<false, false, false>(v, bo, startmask, sum, comp, mword, lane);
                     }
-                    if (a.relu_mask && a.act == RELNN_ACT_RELU && tvalid)
-                        a.relu_mask[tr * a.mask_words + mb * 4 + q] = mword;
+                    // one store per piece end (uniform loop over the set bits)
+                    for (unsigned em = endmask; em; em &= em - 1u) {
+                        const int j = __ffs(em) - 1;
+                        const float val = __uint_as_float(select32(v, j));
+                        const int s = wseg[c * 32 + j];
+                        const bool last = (c * 32 + j == nt - 1);
+                        const int sn = last ? ((nt == a.tile_n) ? after_seg : -1) : s + 1;
+                        const bool split = (first && prev_seg == s) || (last && sn == s);
+                        if (o_ok) {
+                            if (split) __stcg(a.carry + (tile * 2 + (first ? 0 : 1)) * a.d_out + o, val);
+                            else emit_out(a.out + (int64_t)s * a.d_out + o, val, a.accumulate);
+                        }
+                        first = false;
+                    }
+                    if (mask && tvalid) a.relu_mask[(t0 + li) * a.mask_words + mb * 4 + q] = mword;
                 }
             }
             tc_fence_before();
@@ -381,13 +476,14 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
     const uint32_t w_bytes = (uint32_t)L.n_kb * m_blocks * 16384u;
     const uint32_t stage_bytes = (uint32_t)tile_n * 128u;
     const int bar_bytes = 256;
-    int stages = (int)((kSmemLimit - 1024 - bar_bytes - (int)w_bytes) / (int)stage_bytes);
+    const int aux_bytes = 40 * tile_n;  // staged row indices (2 x 3 x tile_n) + epilogue rows (4 x tile_n)
+    int stages = (int)((kSmemLimit - 1024 - bar_bytes - aux_bytes - (int)w_bytes) / (int)stage_bytes);
     stages = std::min(stages, 8);
-    if (stages < 3) {
+    if (stages < 2) {
         set_error("BF16 form: weights too large for shared memory");
         return RELNN_ENOTSUP;
     }
-    const size_t smem = 1024 + w_bytes + (size_t)stages * stage_bytes + bar_bytes;
+    const size_t smem = 1024 + w_bytes + (size_t)stages * stage_bytes + aux_bytes + bar_bytes;
     EncodeTiledFn enc = get_encode_fn();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled unavailable");
@@ -465,9 +561,12 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
         a.tile_n = tile_n;
         a.m_blocks = m_blocks;
         a.stages = stages;
+        a.lag = std::min(stages - 1, kMaxLag);
         a.idesc = tc::idesc_bf16_f32(128, tile_n);
         a.tmem_cols = (uint32_t)(2 * m_blocks * tile_n) <= 256 ? 256u : 512u;
+        a.need_arr[0] = a.need_arr[1] = a.need_arr[2] = 0;
         for (int k = 0; k < L.n_kb; ++k) {
+            a.need_arr[L.src[k]] = 1;
             a.kb_src[k] = L.src[k];
             a.kb_col[k] = L.col[k];
             a.kb_width[k] = L.width[k];
