@@ -85,12 +85,18 @@ __device__ __forceinline__ void seg_scan(uint32_t (&v)[32], float bo, unsigned s
     }
 }
 
-// v[j] for a warp-uniform run-time j without local-memory indexing.
+// v[j] for a warp-uniform run-time j without local-memory indexing (a 5-level select tree).
 __device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], int j) {
-    uint32_t r = v[0];
+    uint32_t t16[16], t8[8], t4[4];
 #pragma unroll
-    for (int i = 1; i < 32; ++i) r = (j == i) ? v[i] : r;
-    return r;
+    for (int i = 0; i < 16; ++i) t16[i] = (j & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t8[i] = (j & 2) ? t16[2 * i + 1] : t16[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t4[i] = (j & 4) ? t8[2 * i + 1] : t8[2 * i];
+    const uint32_t a0 = (j & 8) ? t4[1] : t4[0];
+    const uint32_t a1 = (j & 8) ? t4[3] : t4[2];
+    return (j & 16) ? a1 : a0;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
