@@ -172,6 +172,26 @@ relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, c
 /* Releases the plan's device memory (waits for the device first). */
 relnn_status relnn_plan_destroy(relnn_plan_t p);
 
+/* async. Allocation-free FP32-form forward (the paper has no counterpart: this is a deployment aid).
+ * Some callers cannot call cudaMalloc: a host that handed all device memory to another allocator at
+ * start-up and works within that fixed budget, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation a cudaMalloc/cudaFree may cause. This entry point allocates nothing:
+ * its scratch (the transposed W and the tile-boundary partial sums) is one fixed 4 MiB device array
+ * inside the library, which every GPU that loads the library keeps until the process exits.
+ * Inputs are the join output already grouped by output row (e.g. the grouping of relnn_rule_plan, or
+ * the caller's own): for m matched tuples, d_hs / d_hd = src / dst H rows and d_seg = output row, with
+ * d_seg non-decreasing; z f32 [n_h, d]; W f32 [d_out, 2d]; b f32 [d_out] (may be NULL). d_out_z
+ * [n_out, d_out] receives, for every output row present in d_seg, the SUM over its tuples of
+ * act(Concat(z[hs], z[hd]) W^T + b); rows absent from d_seg are not written.
+ * Limits: d_out <= 256, 2d <= 1024, and (2d + 2 ceil(m/32)) * d_out * 4 bytes <= 4 MiB; larger calls
+ * return RELNN_ENOSPC before any device work. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and must come before any stream capture. All calls share the one
+ * array and nothing in it needs to start at zero (each call writes every slot it reads), but calls
+ * that overlap on the device race on it: issue them on one stream or otherwise serialise them. */
+relnn_status relnn_rule_forward_noalloc(const float* d_z, int32_t d, const int32_t* d_hs, const int32_t* d_hd,
+                                        const int32_t* d_seg, int64_t m, const float* d_W, const float* d_b,
+                                        int32_t d_out, relnn_act_t act, float* d_out_z, void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to report roofline fractions).
  * ------------------------------------------------------------------------------------------- */

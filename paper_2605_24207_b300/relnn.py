@@ -86,6 +86,8 @@ def lib():
     L.relnn_rule_forward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp]
     L.relnn_rule_backward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp, vp, vp]
     L.relnn_plan_destroy.argtypes = [vp]
+    L.relnn_rule_forward_noalloc.argtypes = [vp, C.c_int32, vp, vp, vp, i64, vp, vp, C.c_int32, C.c_int, vp, vp]
+    L.relnn_rule_forward_noalloc.restype = C.c_int
     L.relnn_profile_enable.argtypes = [C.c_int32]
     L.relnn_profile_read.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(i64)]
     for name in EXPORTS[4:-1]:
@@ -147,6 +149,15 @@ def profile_read(kernel_id: int):
     ms, n = C.c_double(), C.c_int64()
     _check(lib().relnn_profile_read(kernel_id, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def rule_forward_noalloc(z, hs, hd, seg, W, b, out, act: int = ACT_NONE, stream=None):
+    """relnn_rule_forward_noalloc: FP32-form forward over join output already grouped by output row,
+    with no device allocation (the library's fixed scratch array is used). ``out`` must be a
+    preallocated f32 [n_out, d_out] tensor; returns it."""
+    _check(lib().relnn_rule_forward_noalloc(_ptr(z), z.shape[1], _ptr(hs), _ptr(hd), _ptr(seg), hs.numel(),
+                                            _ptr(W), _ptr(b), W.shape[0], act, _ptr(out), _stream(stream)))
+    return out
 
 
 # ------------------------------------------------------------------------------------------ join
