@@ -29,8 +29,9 @@ struct BwArgs {
     float* dY;          // [m][d_out] scratch
     float* dz;
     float* dr;
+    const uint32_t* mask;  // ReLU mask stored by a BF16-form forward ([m][mask_words]) or nullptr
     int64_t m, n_tiles;
-    int z_bf16, r_bf16, w_bf16, d, d_r, d_in, d_out, concat_dst, act;
+    int z_bf16, r_bf16, w_bf16, d, d_r, d_in, d_out, concat_dst, act, mask_words;
 };
 
 // X value k of matched tuple t.
@@ -61,7 +62,14 @@ __global__ void bw_dy_kernel(BwArgs a) {
             Yg[idx] = a.dout[(int64_t)a.seg[t0 + t] * a.d_out + o];
         }
         __syncthreads();
-        if (a.act == RELNN_ACT_RELU && a.W) {
+        if (a.act == RELNN_ACT_RELU && a.mask) {
+            // the mask the forward used (keeps a BF16-form forward and this backward consistent)
+            for (int idx = tid; idx < nt * a.d_out; idx += blockDim.x) {
+                const int t = idx / a.d_out, o = idx - t * a.d_out;
+                if (!((a.mask[(t0 + t) * a.mask_words + (o >> 5)] >> (o & 31)) & 1u)) Yg[idx] = 0.f;
+            }
+            __syncthreads();
+        } else if (a.act == RELNN_ACT_RELU && a.W) {
             for (int idx = tid; idx < nt * a.d_out; idx += blockDim.x) {
                 const int t = idx / a.d_out, o = idx - t * a.d_out;
                 float pre = a.bias ? a.bias[o] : 0.f;
@@ -196,6 +204,8 @@ relnn_status backward_fp32(Plan& p, const CallIO& io, const GradIO& g, cudaStrea
         a.d_out = p.d_out;
         a.concat_dst = p.concat_dst;
         a.act = p.act;
+        a.mask = b.relu_mask.p ? b.relu_mask.as<uint32_t>() : nullptr;
+        a.mask_words = ((p.d_out + 127) / 128) * 4;
         const int threads = std::min(1024, std::max(32, ((std::max(p.d_in, p.d_out) + 31) / 32) * 32));
         const size_t smem = sizeof(float) * kTT * (p.d_in + p.d_out);
         RELNN_CHECK_ARG(smem <= 200 * 1024, "backward: tile too large");

@@ -1,11 +1,567 @@
-// Backward of the BF16 form (placeholder until the tensor-core backward lands): the FP32 CUDA-core
-// backward on the device.
+// Backward of the BF16 form on tcgen05 tensor cores (sm_103a), one persistent kernel per branch.
+//
+// For the dst-sorted matched tuples of a branch, with dY_t = dOut[seg_t] (masked by the ReLU mask
+// the forward stored), the kernel computes per tile of N tuples
+//   GEMM A (dX):  D2[k][t] = sum_o W^T[k][o] dY[t][o]   M = input feature k (128-row blocks of W^T,
+//                 staged once by TMA), N = tuples, K = output features; both operands K-major.
+//   GEMM B (dW):  D1[o][k] += sum_t dY[t][o] X[t][k]    M = output features, N = input features,
+//                 K = tuples; both operands read MN-major from the same staged dY and X tiles.
+// The gathered Concat X is regathered (not stored by the forward). The epilogue reads D2 (TMEM lane =
+// input feature, columns = tuples) and adds dX into dz / dr: per tuple for the src slice and r,
+// per run of equal dst row (a segmented sum in registers) for the dst slice. D1 accumulates over all
+// tiles of the CTA; each CTA writes its partial dW and a reduction kernel adds them in CTA order.
+//
+// Roles (288 threads, one CTA per SM): warps 0-3 producers (dY: dOut rows -> mask -> bf16; X: rows
+// of z / r as in the forward; db partial sums), warp 4 TMEM allocation + MMA issue, warps 5-8
+// epilogue.
+#include <algorithm>
+#include <mutex>
+
 #include "bwd.cuh"
+#include "tc.cuh"
 
 namespace relnn {
 
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 288;
+constexpr int kProducerThreads = 128;
+constexpr int kMmaWarp = 4;
+constexpr int kMaxKb = 4;  // input-feature K blocks (d_in <= 256)
+constexpr int kSmemLimit = 227 * 1024;
+
+struct BwArgs {
+    const void* z;
+    const void* r;
+    const float* dout;
+    const uint32_t* mask;   // [m][mask_words] or nullptr (no ReLU)
+    const int32_t* hs;
+    const int32_t* hd;
+    const int32_t* er;
+    const int32_t* seg;
+    float* dz;
+    float* dr;
+    float* db;              // [d_out], accumulated with atomics (zeroed by the host)
+    float* dw_part;         // [grid][d_out][d_in]
+    const int* row_src;     // input feature of each padded K row (-1 = padding), [mbk * 128]
+    int* status;
+    int64_t m, n_tiles;
+    int z_bf16, r_bf16, d, d_r, d_in, d_out, concat_dst, mask_words;
+    int n_kb, d_in_pad, mbk, tile_n, stages, lag;
+    uint32_t idesc_dx, idesc_dw, tmem_cols, d2_col;
+    int kb_src[kMaxKb], kb_col[kMaxKb], kb_width[kMaxKb];
+    int need_arr[3];
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__ BwArgs a) {
+    extern __shared__ uint8_t dyn_smem[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~(uintptr_t)1023);
+    const int N = a.tile_n;
+    const uint32_t wt_bytes = (uint32_t)a.mbk * 2u * 16384u;          // W^T: mbk x 2 blocks of 128 x 64
+    const uint32_t dy_bytes = 2u * (uint32_t)N * 128u;                  // dY: 2 blocks of 64 outputs
+    const uint32_t x_bytes = (uint32_t)a.n_kb * (uint32_t)N * 128u;     // X: n_kb blocks of 64 inputs
+    const uint32_t stage_bytes = dy_bytes + x_bytes;
+    uint8_t* wt_smem = base;
+    uint8_t* st_smem = base + wt_bytes;
+    int32_t* idx_smem = reinterpret_cast<int32_t*>(st_smem + (size_t)a.stages * stage_bytes);  // 2 x 4 x N
+    int32_t* epi_smem = idx_smem + 8 * N;                                                      // 4 warps x 3 x N
+    uint64_t* bars = reinterpret_cast<uint64_t*>(epi_smem + 12 * N);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + a.stages;
+    uint64_t* tfull = bars + 2 * a.stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wbar = tempty + 2;
+    uint64_t* dwdone = wbar + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dwdone + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(smem_u32(&full[s]), kProducerThreads);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&tfull[i]), 1);
+            mbar_init(smem_u32(&tempty[i]), 128);
+        }
+        mbar_init(smem_u32(wbar), 1);
+        mbar_init(smem_u32(dwdone), 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t d2_stride = (uint32_t)a.mbk * N;
+
+    if (warp < 4) {
+        // ------------------------------------------------------------------ producers
+        const int chunk = tid & 7;
+        const int rpt = N >> 4;
+        const int row_base = (tid >> 3) * rpt;
+        const int32_t* arrs[4] = {a.hs, a.hd, a.er, a.seg};
+        const int per_thr = N / kProducerThreads;  // 0 when N = 64: threads below N load one entry
+        auto stage_idx = [&](int64_t tile, int32_t* slot) {
+            const int64_t t0 = tile * N;
+            for (int r = 0; r < 4; ++r) {
+                if (r < 3 && !a.need_arr[r]) continue;
+                for (int qq = tid; qq < N; qq += kProducerThreads)
+                    slot[r * N + qq] = (tile < a.n_tiles && t0 + qq < a.m) ? __ldg(arrs[r] + t0 + qq) : 0;
+            }
+        };
+        (void)per_thr;
+        stage_idx(blockIdx.x, idx_smem);
+        named_bar_sync(1, kProducerThreads);
+        float dbacc[2][8];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dbacc[i][k] = 0.f;
+        int it = 0, pending = 0, lt = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
+            const int64_t t0 = tile * N;
+            const int32_t* islot = idx_smem + (lt & 1) * 4 * N;
+            if (ok) {
+                const int s = it % a.stages;
+                const uint32_t ph = (uint32_t)((it / a.stages) & 1);
+                if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.status, abort_flag)) ok = false;
+                if (ok) {
+                    uint8_t* stg = st_smem + (size_t)s * stage_bytes;
+                    const uint32_t dyb = smem_u32(stg);
+                    const uint32_t xb = smem_u32(stg + dy_bytes);
+                    // dY rows: dOut[seg_t] masked by the stored ReLU mask, as bf16; 2 blocks of 64 outputs
+                    for (int j = 0; j < rpt; ++j) {
+                        const int row = row_base + j;
+                        const bool tv = t0 + row < a.m;
+                        const int sg = islot[3 * N + row];
+#pragma unroll
+                        for (int ob = 0; ob < 2; ++ob) {
+                            const int o0 = ob * 64 + chunk * 8;
+                            float v[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) v[k] = 0.f;
+                            if (tv && o0 < a.d_out) {
+                                const float4* q = reinterpret_cast<const float4*>(a.dout + (int64_t)sg * a.d_out + o0);
+                                const float4 u = __ldg(q), w = __ldg(q + 1);
+                                v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+                                v[4] = w.x; v[5] = w.y; v[6] = w.z; v[7] = w.w;
+                                if (a.mask) {
+                                    const uint32_t bits = a.mask[(t0 + row) * a.mask_words + (o0 >> 5)] >> (o0 & 31);
+#pragma unroll
+                                    for (int k = 0; k < 8; ++k) v[k] = ((bits >> k) & 1u) ? v[k] : 0.f;
+                                }
+                            }
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) dbacc[ob][k] += v[k];
+                            const uint32_t dst = dyb + (uint32_t)ob * N * 128u + (uint32_t)row * 128u +
+                                                 ((uint32_t)(chunk ^ (row & 7)) << 4);
+                            st_shared_v4(dst, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                         pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+                        }
+                    }
+                    // X rows, K-block by K-block (as in the forward)
+                    for (int kb = 0; kb < a.n_kb; ++kb) {
+                        const int src = a.kb_src[kb];
+                        const int col = a.kb_col[kb] + chunk * 8;
+                        const bool in_part = col < a.kb_width[kb];
+                        const int32_t* rows_idx = islot + src * N;
+                        const void* tbl = src == 2 ? a.r : a.z;
+                        const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
+                        const int row_elems = src == 2 ? a.d_r : a.d;
+                        const uint32_t kbase = xb + (uint32_t)kb * N * 128u;
+                        for (int j = 0; j < rpt; ++j) {
+                            const int row = row_base + j;
+                            const uint32_t dst = kbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
+                            const bool valid = (t0 + row < a.m) && in_part;
+                            const int64_t ridx = rows_idx[row];
+                            if (tbl_bf16) {
+                                const uint16_t* p = reinterpret_cast<const uint16_t*>(tbl);
+                                cp_async_16(dst, valid ? p + ridx * row_elems + col : p, valid ? 16u : 0u);
+                            } else {
+                                float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
+                                if (valid) {
+                                    const float4* q = reinterpret_cast<const float4*>(
+                                        reinterpret_cast<const float*>(tbl) + ridx * row_elems + col);
+                                    u = __ldg(q);
+                                    w = __ldg(q + 1);
+                                }
+                                st_shared_v4(dst, pack_bf16x2(u.x, u.y), pack_bf16x2(u.z, u.w), pack_bf16x2(w.x, w.y),
+                                             pack_bf16x2(w.z, w.w));
+                            }
+                        }
+                    }
+                    cp_async_commit();
+                    ++pending;
+                    ++it;
+                    if (pending > a.lag) {
+                        cp_async_wait_n(a.lag);
+                        fence_proxy_async();
+                        mbar_arrive(smem_u32(&full[(it - 1 - a.lag) % a.stages]));
+                        --pending;
+                    }
+                }
+            }
+            // indices of this CTA's next tile into the other slot
+            stage_idx(tile + gridDim.x, idx_smem + ((lt + 1) & 1) * 4 * N);
+            named_bar_sync(1, kProducerThreads);
+        }
+        cp_async_wait<0>();
+        fence_proxy_async();
+        for (int k = pending; k > 0; --k) mbar_arrive(smem_u32(&full[(it - k) % a.stages]));
+        // db partial sums of this thread's output chunk
+#pragma unroll
+        for (int ob = 0; ob < 2; ++ob)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int o = ob * 64 + chunk * 8 + k;
+                if (o < a.d_out && a.db) atomicAdd(a.db + o, dbacc[ob][k]);
+            }
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t wb = smem_u32(wbar);
+            mbar_arrive_expect_tx(wb, wt_bytes);
+            for (int mb = 0; mb < a.mbk; ++mb)
+                for (int kk = 0; kk < 2; ++kk)
+                    tma_load_2d(smem_u32(wt_smem + (size_t)(mb * 2 + kk) * 16384u), &wtmap, kk * 64, mb * 128, wb);
+            bool ok = mbar_wait(wb, 0, a.status, abort_flag);
+            tc_fence_after();
+            int lt = 0;
+            for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++lt) {
+                const int s = lt % a.stages;
+                const uint32_t ph = (uint32_t)((lt / a.stages) & 1);
+                const int acc = lt & 1;
+                const uint32_t use = (uint32_t)(lt >> 1);
+                if (!mbar_wait(smem_u32(&full[s]), ph, a.status, abort_flag)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&tempty[acc]), (use & 1u) ^ 1u, a.status, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t dyb = smem_u32(st_smem + (size_t)s * stage_bytes);
+                const uint32_t xb = dyb + dy_bytes;
+                // GEMM A: dX^T for this tile
+                const uint32_t d2 = tmem_base + a.d2_col + (uint32_t)acc * d2_stride;
+                for (int mb = 0; mb < a.mbk; ++mb)
+                    for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint64_t ad = sw128_kmajor_desc(smem_u32(wt_smem + (size_t)(mb * 2 + kk) * 16384u) + k * 32);
+                            const uint64_t bd = sw128_kmajor_desc(dyb + (uint32_t)kk * N * 128u + k * 32);
+                            mma_bf16(d2 + (uint32_t)mb * N, ad, bd, a.idesc_dx, (kk | k) != 0);
+                        }
+                mma_commit(smem_u32(&tfull[acc]));
+                // GEMM B: dW += dY^T X, 16 tuples per instruction
+                for (int step = 0; step < N / 16; ++step) {
+                    const uint64_t ad = sw128_mnmajor_desc(dyb + (uint32_t)step * 2048u, (uint32_t)N * 128u);
+                    const uint64_t bd = sw128_mnmajor_desc(xb + (uint32_t)step * 2048u, (uint32_t)N * 128u);
+                    mma_bf16(tmem_base, ad, bd, a.idesc_dw, (lt > 0 || step > 0) ? 1u : 0u);
+                }
+                mma_commit(smem_u32(&empty[s]));
+            }
+            mma_commit(smem_u32(dwdone));
+            // every issued MMA must finish before TMEM is released (also when another role aborted)
+            mbar_wait(smem_u32(dwdone), 0, a.status, abort_flag);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------ epilogue
+        const int q = warp & 3;
+        int32_t* wix = epi_smem + (warp - kMmaWarp - 1) * 3 * N;  // hs, hd, er of the tile
+        int lt = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
+            const int64_t t0 = tile * N;
+            const int nt = (int)imin64(N, a.m - t0);
+            __syncwarp();
+            for (int rr = lane; rr < N; rr += 32) {
+                const bool v = rr < nt;
+                wix[rr] = v ? __ldg(a.hs + t0 + rr) : 0;
+                wix[N + rr] = (v && a.concat_dst) ? __ldg(a.hd + t0 + rr) : -1;
+                wix[2 * N + rr] = (v && a.d_r > 0) ? __ldg(a.er + t0 + rr) : 0;
+            }
+            __syncwarp();
+            const int acc = lt & 1;
+            const uint32_t use = (uint32_t)(lt >> 1);
+            if (!mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            for (int mb = 0; mb < a.mbk; ++mb) {
+                const int kbase = mb * 128 + 32 * q;  // padded K row of lane 0
+                if (kbase >= a.d_in_pad) continue;
+                // which Concat slice (and column in it) this lane's padded K row holds
+                const int kr = kbase + lane;
+                const int kblk = kr >> 6;
+                const int part = a.kb_src[kblk < a.n_kb ? kblk : 0];
+                const int kk = a.kb_col[kblk < a.n_kb ? kblk : 0] + (kr & 63);
+                const bool k_ok = kblk < a.n_kb && kk < a.kb_width[kblk];
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + a.d2_col + (uint32_t)acc * d2_stride +
+                                       (uint32_t)mb * N;
+                for (int c = 0; c * 32 < nt; ++c) {
+                    uint32_t v[32];
+                    tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
+                    tmem_ld_wait();
+                    const int cnt = min(32, nt - c * 32);
+                    if (part == 1) {
+                        // runs of equal dst row inside the chunk: one add per run
+                        float run = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (j < cnt) {
+                                const int h = wix[N + c * 32 + j];
+                                run += __uint_as_float(v[j]);
+                                const bool end = (j == cnt - 1) || (wix[N + c * 32 + j + 1] != h);
+                                if (end) {
+                                    if (k_ok && a.dz) atomicAdd(a.dz + (int64_t)h * a.d + kk, run);
+                                    run = 0.f;
+                                }
+                            }
+                        }
+                    } else if (part == 0) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < cnt && k_ok && a.dz)
+                                atomicAdd(a.dz + (int64_t)wix[c * 32 + j] * a.d + kk, __uint_as_float(v[j]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < cnt && k_ok && a.dr)
+                                atomicAdd(a.dr + (int64_t)wix[2 * N + c * 32 + j] * a.d_r + kk, __uint_as_float(v[j]));
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&tempty[acc]));
+        }
+        // this CTA's dW partial: TMEM lane o (output feature), columns k (input features)
+        if (ok && mbar_wait(smem_u32(dwdone), 0, a.status, abort_flag)) {
+            tc_fence_after();
+            const int o = 32 * q + lane;
+            float* dst = a.dw_part + ((int64_t)blockIdx.x * a.d_out + o) * a.d_in;
+            for (int c = 0; c * 32 < a.d_in_pad; ++c) {
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)c * 32, v);
+                tmem_ld_wait();
+                if (o < a.d_out) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int k = a.row_src[c * 32 + j];  // padded column -> input feature
+                        if (k >= 0) dst[k] = __uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, a.tmem_cols);
+    }
+}
+
+// W^T padded to [mbk*128 rows (input features)][128 cols (output features)] in bf16.
+__global__ void pack_wt_kernel(const void* W, int w_bf16, int d_out, int d_in, int rows_pad, const int* row_src,
+                               uint16_t* wt) {
+    const int n = rows_pad * 128;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int kr = i >> 7, o = i & 127;
+        const int k = row_src[kr];  // input feature of padded row kr, or -1
+        uint16_t v = 0;
+        if (k >= 0 && o < d_out) {
+            if (w_bf16) v = reinterpret_cast<const uint16_t*>(W)[o * d_in + k];
+            else v = __bfloat16_as_ushort(__float2bfloat16_rn(reinterpret_cast<const float*>(W)[o * d_in + k]));
+        }
+        wt[i] = v;
+    }
+}
+
+__global__ void reduce_parts_kernel(const float* part, int nparts, int64_t n, float* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * n + i];
+        out[i] = s;
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+// Whether the tensor-core backward covers this plan (else the FP32-form backward runs).
+static bool tc_backward_supported(const Plan& p) {
+    if (p.identity || p.d_out > 128 || p.d_out % 8 || p.d % 8 || p.br[0].d_r % 8) return false;
+    int kb = 0;
+    kb += (p.d + 63) / 64;
+    if (p.concat_dst) kb += (p.d + 63) / 64;
+    if (p.br[0].d_r) kb += (p.br[0].d_r + 63) / 64;
+    return kb <= kMaxKb;
+}
+
 relnn_status backward_tc(Plan& p, const CallIO& io, const GradIO& g, cudaStream_t st) {
-    return backward_fp32(p, io, g, st);
+    if (!tc_backward_supported(p)) return backward_fp32(p, io, g, st);
+    RELNN_CHECK_ARG(g.dout, "backward: null output gradient");
+    const bool relu = p.act == RELNN_ACT_RELU;
+    // K-block layout of the Concat (each part starts on a 64-column block)
+    int n_kb = 0, kb_src[kMaxKb], kb_col[kMaxKb], kb_width[kMaxKb];
+    std::vector<int> row_src;  // input feature of each padded K row (-1 = padding)
+    auto add_part = [&](int src, int width, int kofs) {
+        for (int c = 0; c < width; c += 64) {
+            kb_src[n_kb] = src;
+            kb_col[n_kb] = c;
+            kb_width[n_kb] = width;
+            for (int i = 0; i < 64; ++i) row_src.push_back(c + i < width ? kofs + c + i : -1);
+            ++n_kb;
+        }
+    };
+    add_part(0, p.d, 0);
+    if (p.concat_dst) add_part(1, p.d, p.d);
+    if (p.br[0].d_r) add_part(2, p.br[0].d_r, p.d * (p.concat_dst ? 2 : 1));
+    const int d_in_pad = n_kb * 64;
+    const int mbk = (d_in_pad + 127) / 128;
+    while ((int)row_src.size() < mbk * 128) row_src.push_back(-1);
+    // tile size: 128 tuples when three stages fit, else 64
+    const uint32_t wt_bytes = (uint32_t)mbk * 2u * 16384u;
+    auto stage_of = [&](int N) { return 2u * N * 128u + (uint32_t)n_kb * N * 128u; };
+    auto aux_of = [&](int N) { return (uint32_t)(20 * N * 4); };
+    int N = 128;
+    int stages = (int)((kSmemLimit - 1024 - 256 - (int)wt_bytes - (int)aux_of(128)) / (int)stage_of(128));
+    if (stages < 3) {
+        N = 64;
+        stages = (int)((kSmemLimit - 1024 - 256 - (int)wt_bytes - (int)aux_of(64)) / (int)stage_of(64));
+    }
+    stages = std::min(stages, 6);
+    if (stages < 2) return backward_fp32(p, io, g, st);
+    const uint32_t d2_col = (uint32_t)((d_in_pad + 31) / 32 * 32);
+    const uint32_t cols_needed = d2_col + 2u * mbk * N;
+    if (cols_needed > 512) return backward_fp32(p, io, g, st);
+    const uint32_t tmem_cols = cols_needed <= 256 ? 256u : 512u;
+    const size_t smem = 1024 + wt_bytes + (size_t)stages * stage_of(N) + aux_of(N) + 256;
+
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return RELNN_ECUDA;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        RELNN_CUDA(cudaFuncSetAttribute(bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        attr_set = true;
+    }
+    if (g.dz) RELNN_CUDA(cudaMemsetAsync(g.dz, 0, sizeof(float) * p.n_h * p.d, st));
+    const int grid_max = num_sms();
+    const size_t wt_elems = (size_t)mbk * 128 * 128;
+    for (size_t i = 0; i < p.br.size(); ++i) {
+        BranchPlan& b = p.br[i];
+        float* dW = g.dW.size() > i ? g.dW[i] : nullptr;
+        float* db = g.db.size() > i ? g.db[i] : nullptr;
+        float* dr = (g.dr.size() > i && b.d_r > 0) ? g.dr[i] : nullptr;
+        if (dr) RELNN_CUDA(cudaMemsetAsync(dr, 0, sizeof(float) * b.n_tuples * b.d_r, st));
+        if (db) RELNN_CUDA(cudaMemsetAsync(db, 0, sizeof(float) * p.d_out, st));
+        if (b.m == 0) {
+            if (dW) RELNN_CUDA(cudaMemsetAsync(dW, 0, sizeof(float) * p.d_out * p.d_in, st));
+            continue;
+        }
+        if (relu && !b.relu_mask.p) {
+            set_error("BF16 backward with ReLU needs the forward's mask (plan flag RELNN_FLAG_RELU_MASK)");
+            return RELNN_EINVAL;
+        }
+        const int64_t n_tiles = ceil_div(b.m, N);
+        const int grid = (int)std::min<int64_t>(n_tiles, grid_max);
+        // scratch: W^T (bf16), row map, dW partials
+        const size_t part_elems = (size_t)grid * p.d_out * p.d_in;
+        const size_t bytes = wt_elems * 2 + sizeof(int) * row_src.size() + 256 + sizeof(float) * part_elems;
+        RELNN_TRY(p.scratch.alloc(bytes));
+        uint16_t* wt = p.scratch.as<uint16_t>();
+        int* d_rows = reinterpret_cast<int*>(p.scratch.as<uint8_t>() + wt_elems * 2);
+        float* part = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + ((wt_elems * 2 + sizeof(int) * row_src.size() + 255) & ~(size_t)255));
+        RELNN_CUDA(cudaMemcpyAsync(d_rows, row_src.data(), sizeof(int) * row_src.size(), cudaMemcpyHostToDevice, st));
+        { pack_wt_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, mbk * 128, d_rows, wt); note_launch(); }
+        CUtensorMap wtmap;
+        {
+            cuuint64_t gdim[2] = {128, (cuuint64_t)mbk * 128};
+            cuuint64_t gstride[1] = {128 * 2};
+            cuuint32_t box[2] = {64, 128};
+            cuuint32_t estr[2] = {1, 1};
+            CUresult r = enc(&wtmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, wt, gdim, gstride, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+                return RELNN_ECUDA;
+            }
+        }
+        BwArgs a{};
+        a.z = io.z;
+        a.r = io.br[i].r;
+        a.dout = g.dout;
+        a.mask = relu ? b.relu_mask.as<uint32_t>() : nullptr;
+        a.hs = b.hs.as<int32_t>();
+        a.hd = b.hd.as<int32_t>();
+        a.er = b.er.as<int32_t>();
+        a.seg = b.seg.as<int32_t>();
+        a.dz = g.dz;
+        a.dr = dr;
+        a.db = db;
+        a.dw_part = part;
+        a.row_src = d_rows;
+        a.status = p.status.as<int>();
+        a.m = b.m;
+        a.n_tiles = n_tiles;
+        a.z_bf16 = io.z_bf16;
+        a.r_bf16 = io.r_bf16;
+        a.d = p.d;
+        a.d_r = b.d_r;
+        a.d_in = p.d_in;
+        a.d_out = p.d_out;
+        a.concat_dst = p.concat_dst;
+        a.mask_words = ((p.d_out + 127) / 128) * 4;
+        a.n_kb = n_kb;
+        a.d_in_pad = d_in_pad;
+        a.mbk = mbk;
+        a.tile_n = N;
+        a.stages = stages;
+        a.lag = stages - 1;
+        a.idesc_dx = tc::idesc_bf16_f32(128, N);
+        a.idesc_dw = tc::idesc_bf16_f32(128, d_in_pad, true, true);
+        a.tmem_cols = tmem_cols;
+        a.d2_col = d2_col;
+        a.need_arr[0] = a.need_arr[1] = a.need_arr[2] = 0;
+        for (int k = 0; k < n_kb; ++k) {
+            a.kb_src[k] = kb_src[k];
+            a.kb_col[k] = kb_col[k];
+            a.kb_width[k] = kb_width[k];
+            a.need_arr[kb_src[k]] = 1;
+        }
+        { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<grid, kThreads, smem, st>>>(wtmap, a); note_launch(); prof_end(pt, st); }
+        RELNN_CUDA(cudaGetLastError());
+        if (dW) {
+            const int64_t nw = (int64_t)p.d_out * p.d_in;
+            { reduce_parts_kernel<<<(int)std::min<int64_t>(ceil_div(nw, 256), 1024), 256, 0, st>>>(part, grid, nw, dW); note_launch(); }
+            RELNN_CUDA(cudaGetLastError());
+        }
+    }
+    return RELNN_OK;
 }
 
 }  // namespace relnn

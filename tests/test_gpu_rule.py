@@ -153,3 +153,38 @@ def test_autograd_function_fp32(gpu):
     assert rel_frob(Wt.grad.cpu().numpy(), oW[0]) <= FP32_TOL
     assert rel_frob(bt.grad.cpu().numpy(), ob[0]) <= FP32_TOL
     assert rel_frob(z.grad.cpu().numpy(), oz) <= FP32_TOL
+
+
+# ------------------------------------------------------------------------------ BF16 backward
+def _bf16_grads(rel, flags=0):
+    keys, out, plan, t = run_rule(rel, flags=flags | R.FLAG_BF16 | R.FLAG_RELU_MASK, z_dtype=torch.bfloat16,
+                                  r_dtype=torch.float32, w_dtype=torch.float32)
+    dout = np.random.default_rng(2).standard_normal(out.shape).astype(np.float32)
+    dW, db, dz, dr = plan.backward(to_dev(dout), t["z"], t["W"], t["b"], t["r"])
+    torch.cuda.synchronize()
+    plan.check()
+    # oracle on the bf16-rounded operands the device used
+    brs = [OBr(b.src, b.dst, bf16_round(b.W), b.b, None if b.r is None else bf16_round(b.r)) for b in rel.branches]
+    oW, ob, oz, orr = O.rule_backward(rel.h_ids, bf16_round(rel.z), brs, keys, dout, act=rel.act)
+    return (dW, db, dz, dr), (oW, ob, oz, orr)
+
+
+@pytest.mark.parametrize("shape", ["c2", "c3", "c4", "odd"])
+def test_bf16_backward_matches_oracle(gpu, shape):
+    if shape == "c2":
+        rel = W.make_rule(41, 30_011, 3000, 128, 128, np.int64, src_dist="zipf", src_s=1.1)
+    elif shape == "c3":
+        rel = W.make_rule(42, 20_000, 2500, 64, 64, np.int32, src_dist="zipf", src_s=1.2, act="relu")
+    elif shape == "c4":
+        rel = W.make_rule(43, 0, 2000, 64, 96, np.int32, dst_dist="zipf", dst_s=1.0, d_r=64,
+                          branch_tuples=[9000, 5000, 2500])
+    else:
+        rel = W.make_rule(44, 7000, 600, 72, 40, np.int32, d_r=8, act="relu", dup_frac=0.05)
+    (dW, db, dz, dr), (oW, ob, oz, orr) = _bf16_grads(rel)
+    for i in range(len(rel.branches)):
+        # dY is rounded to bf16 before the tensor-core GEMMs: 2e-2 is the BF16-form bar
+        assert rel_frob(dW[i].cpu().numpy(), oW[i]) <= BF16_TOL
+        assert rel_frob(db[i].cpu().numpy(), ob[i]) <= 1e-5  # db is summed in f32 from unrounded dY
+        if dr is not None:
+            assert rel_frob(dr[i].cpu().numpy(), orr[i]) <= BF16_TOL
+    assert rel_frob(dz.cpu().numpy(), oz) <= BF16_TOL
