@@ -50,14 +50,23 @@ void prof_end(ProfToken& tok, cudaStream_t st);
         if (s_ != RELNN_OK) return s_;      \
     } while (0)
 
-// Stream-ordered device buffer owned by a handle (freed by the handle's destructor).
+// Keeps freed blocks of the device's default memory pool cached (no return to the OS at syncs), so
+// repeated plan builds reuse memory instead of mapping it again.
+void ensure_pool_cached();
+
+// Device buffer drawn from the device's default memory pool.
+//   alloc(n, s):     persistent (owned by a handle, usable on any stream once alloc returns; freed
+//                    with cudaFree, which synchronises, so only from destroy paths or on growth)
+//   alloc_tmp(n, s): temporary, allocated and freed in the order of stream s only
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    bool ordered = false;
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) {
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), st(o.st), ordered(o.ordered) {
         o.p = nullptr;
         o.bytes = 0;
     }
@@ -66,6 +75,8 @@ struct DevBuf {
             release();
             p = o.p;
             bytes = o.bytes;
+            st = o.st;
+            ordered = o.ordered;
             o.p = nullptr;
             o.bytes = 0;
         }
@@ -73,21 +84,43 @@ struct DevBuf {
     }
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (ordered) cudaFreeAsync(p, st);
+            else cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
     }
-    relnn_status alloc(size_t n) {
+    relnn_status alloc(size_t n, cudaStream_t s = nullptr) {
         if (n <= bytes && p) return RELNN_OK;
         release();
         if (n == 0) n = 16;
-        cudaError_t e = cudaMalloc(&p, n);
+        ensure_pool_cached();
+        cudaError_t e = cudaMallocAsync(&p, n, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
+            if (p) cudaFree(p);
             p = nullptr;
-            set_error(std::string("cudaMalloc(") + std::to_string(n) + "): " + cudaGetErrorString(e));
+            set_error(std::string("device allocation of ") + std::to_string(n) + " bytes: " + cudaGetErrorString(e));
             return RELNN_ENOMEM;
         }
         bytes = n;
+        ordered = false;
+        return RELNN_OK;
+    }
+    relnn_status alloc_tmp(size_t n, cudaStream_t s) {
+        release();
+        if (n == 0) n = 16;
+        ensure_pool_cached();
+        cudaError_t e = cudaMallocAsync(&p, n, s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error(std::string("device allocation of ") + std::to_string(n) + " bytes: " + cudaGetErrorString(e));
+            return RELNN_ENOMEM;
+        }
+        bytes = n;
+        st = s;
+        ordered = true;
         return RELNN_OK;
     }
     template <class T>

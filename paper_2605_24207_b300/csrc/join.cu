@@ -205,10 +205,10 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     const bool narrow = nbits <= 32;
     const size_t kb = narrow ? 4 : 8;
     DevBuf sk, sk_tmp, rows_tmp, flags;
-    RELNN_TRY(sk.alloc(kb * n));
-    RELNN_TRY(sk_tmp.alloc(kb * n));
-    RELNN_TRY(rows_tmp.alloc(sizeof(int32_t) * n));
-    RELNN_TRY(flags.alloc(sizeof(int32_t) * (n + 1)));
+    RELNN_TRY(sk.alloc_tmp(kb * n, st));
+    RELNN_TRY(sk_tmp.alloc_tmp(kb * n, st));
+    RELNN_TRY(rows_tmp.alloc_tmp(sizeof(int32_t) * n, st));
+    RELNN_TRY(flags.alloc_tmp(sizeof(int32_t) * (n + 1), st));
     int32_t* rows = jt.rows_sorted.as<int32_t>();
     const int g = grid_for(n);
     if (narrow) {
@@ -283,8 +283,8 @@ relnn_status join_probe_pairs(const JoinTable& jt, const void* probe, int64_t m,
     }
     const int64_t nwarps = ceil_div(m, 32);
     DevBuf uarr, wt;
-    RELNN_TRY(uarr.alloc(sizeof(int32_t) * m));
-    RELNN_TRY(wt.alloc(sizeof(int64_t) * (nwarps + 1)));
+    RELNN_TRY(uarr.alloc_tmp(sizeof(int32_t) * m, st));
+    RELNN_TRY(wt.alloc_tmp(sizeof(int64_t) * (nwarps + 1), st));
     const JoinView v = jt.view();
     const int blocks = (int)ceil_div(m, 256);
     { probe_count_kernel<<<blocks, 256, 0, st>>>(v, probe, m, jt.kt, uarr.as<int32_t>(), wt.as<int64_t>()); note_launch(); }

@@ -153,9 +153,9 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
     const JoinView v = p.H.view();
     const int64_t nwarps = ceil_div(std::max<int64_t>(T, 1), 32);
     DevBuf us, ud, wt;
-    RELNN_TRY(us.alloc(sizeof(int32_t) * std::max<int64_t>(T, 1)));
-    RELNN_TRY(ud.alloc(sizeof(int32_t) * std::max<int64_t>(T, 1)));
-    RELNN_TRY(wt.alloc(sizeof(int64_t) * (nwarps + 1)));
+    RELNN_TRY(us.alloc_tmp(sizeof(int32_t) * std::max<int64_t>(T, 1), st));
+    RELNN_TRY(ud.alloc_tmp(sizeof(int32_t) * std::max<int64_t>(T, 1), st));
+    RELNN_TRY(wt.alloc_tmp(sizeof(int64_t) * (nwarps + 1), st));
     RELNN_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(int64_t) * (nwarps + 1), st));
     const int blocks = (int)ceil_div(std::max<int64_t>(T, 1), 256);
     if (T > 0)
@@ -185,13 +185,13 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
         t.wide = nbits > 32;
     }
     const size_t kb = t.wide ? 8 : 4;
-    RELNN_TRY(t.t_hs.alloc(4 * m1));
-    RELNN_TRY(t.t_hd.alloc(4 * m1));
-    RELNN_TRY(t.t_e.alloc(4 * m1));
-    RELNN_TRY(t.key.alloc(kb * m1));
-    RELNN_TRY(t.key_tmp.alloc(kb * m1));
-    RELNN_TRY(t.perm.alloc(4 * m1));
-    RELNN_TRY(t.perm_tmp.alloc(4 * m1));
+    RELNN_TRY(t.t_hs.alloc_tmp(4 * m1, st));
+    RELNN_TRY(t.t_hd.alloc_tmp(4 * m1, st));
+    RELNN_TRY(t.t_e.alloc_tmp(4 * m1, st));
+    RELNN_TRY(t.key.alloc_tmp(kb * m1, st));
+    RELNN_TRY(t.key_tmp.alloc_tmp(kb * m1, st));
+    RELNN_TRY(t.perm.alloc_tmp(4 * m1, st));
+    RELNN_TRY(t.perm_tmp.alloc_tmp(4 * m1, st));
     if (T > 0) {
         if (t.wide)
             { tri_emit_kernel<uint64_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
@@ -210,10 +210,10 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
     else
         RELNN_TRY(radix_sort_pairs<uint32_t>(t.key.as<uint32_t>(), t.perm.as<int32_t>(), t.key_tmp.as<uint32_t>(),
                                              t.perm_tmp.as<int32_t>(), M, nbits, st));
-    RELNN_TRY(b.hs.alloc(4 * m1));
-    RELNN_TRY(b.hd.alloc(4 * m1));
-    RELNN_TRY(b.er.alloc(4 * m1));
-    RELNN_TRY(b.seg.alloc(4 * (m1 + 1)));
+    RELNN_TRY(b.hs.alloc(4 * m1, st));
+    RELNN_TRY(b.hd.alloc(4 * m1, st));
+    RELNN_TRY(b.er.alloc(4 * m1, st));
+    RELNN_TRY(b.seg.alloc(4 * (m1 + 1), st));
     if (M > 0)
         { gather3_kernel<<<grid_for(M), 256, 0, st>>>(t.perm.as<int32_t>(), M, t.t_hs.as<int32_t>(),
                                                     t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(),
@@ -273,10 +273,10 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     // output key set and output row of every matched tuple
     if (p.join_dst) {
         DevBuf present;
-        RELNN_TRY(present.alloc(sizeof(int32_t) * (U + 1)));
+        RELNN_TRY(present.alloc_tmp(sizeof(int32_t) * (U + 1), st));
         RELNN_CUDA(cudaMemsetAsync(present.p, 0, sizeof(int32_t) * (U + 1), st));
         DevBuf out_row;
-        RELNN_TRY(out_row.alloc(sizeof(int32_t) * (U + 1)));
+        RELNN_TRY(out_row.alloc_tmp(sizeof(int32_t) * (U + 1), st));
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
                 { mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
@@ -302,7 +302,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         Tmp& t = tmp[0];
         const int64_t M = b.m;
         DevBuf flags;
-        RELNN_TRY(flags.alloc(sizeof(int32_t) * (M + 1)));
+        RELNN_TRY(flags.alloc_tmp(sizeof(int32_t) * (M + 1), st));
         if (M > 0) {
             if (t.wide) { key_flags_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), M, flags.as<int32_t>()); note_launch(); }
             else { key_flags_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), M, flags.as<int32_t>()); note_launch(); }

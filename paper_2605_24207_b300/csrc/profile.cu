@@ -43,6 +43,20 @@ EvPair* take() {
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+void ensure_pool_cached() {
+    static std::atomic<uint64_t> done_mask{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    const uint64_t bit = 1ull << dev;
+    if (done_mask.load() & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done_mask.fetch_or(bit);
+}
+
 ProfToken prof_begin(int id, cudaStream_t st) {
     ProfToken t;
     if (!g_prof_on.load(std::memory_order_relaxed) || id < 0 || id >= kIds) return t;
