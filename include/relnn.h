@@ -172,6 +172,17 @@ relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, c
 /* Releases the plan's device memory (waits for the device first). */
 relnn_status relnn_plan_destroy(relnn_plan_t p);
 
+/* async. Loss relation of content arity 0 (paper Sec. 3.2 fit statement; Sec. 3.6 loss rule):
+ *     L(; mean((z_p - z_t)^2)) :- Pred(g; z_p), Target(g; z_t)
+ * Pred and Target are embedded relations with unique keys sorted ascending (d_pred_keys [n_pred],
+ * d_target_keys [n_target], type kt) and f32 rows of `width`. The join pairs rows with equal keys;
+ * *d_loss (device f32) receives the mean of the squared differences over every cell of the joined
+ * pairs (0 if none join), and d_grad (may be NULL) [n_pred, width] the gradient with respect to
+ * d_pred (zero rows for predictions that join no target). Intended for small readout relations. */
+relnn_status relnn_mse_loss(const float* d_pred, const void* d_pred_keys, int64_t n_pred, const float* d_target,
+                            const void* d_target_keys, int64_t n_target, int32_t width, relnn_key_t kt,
+                            float* d_loss, float* d_grad, void* stream);
+
 /* async. Allocation-free FP32-form forward (the paper has no counterpart: this is a deployment aid).
  * Some callers cannot call cudaMalloc: a host that handed all device memory to another allocator at
  * start-up and works within that fixed budget, or a latency-critical loop that cannot afford the

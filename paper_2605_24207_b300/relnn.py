@@ -88,6 +88,8 @@ def lib():
     L.relnn_plan_destroy.argtypes = [vp]
     L.relnn_rule_forward_noalloc.argtypes = [vp, C.c_int32, vp, vp, vp, i64, vp, vp, C.c_int32, C.c_int, vp, vp]
     L.relnn_rule_forward_noalloc.restype = C.c_int
+    L.relnn_mse_loss.argtypes = [vp, vp, i64, vp, vp, i64, C.c_int32, C.c_int, vp, vp, vp]
+    L.relnn_mse_loss.restype = C.c_int
     L.relnn_profile_enable.argtypes = [C.c_int32]
     L.relnn_profile_read.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(i64)]
     for name in EXPORTS[4:-1]:
@@ -149,6 +151,16 @@ def profile_read(kernel_id: int):
     ms, n = C.c_double(), C.c_int64()
     _check(lib().relnn_profile_read(kernel_id, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def mse_loss(pred, pred_keys, target, target_keys, need_grad: bool = True, stream=None):
+    """relnn_mse_loss: (loss [1] f32 device tensor, d loss / d pred or None)."""
+    loss = torch.empty(1, dtype=torch.float32, device=pred.device)
+    grad = torch.empty_like(pred) if need_grad else None
+    _check(lib().relnn_mse_loss(_ptr(pred), _ptr(pred_keys), pred.shape[0], _ptr(target), _ptr(target_keys),
+                                target.shape[0], pred.shape[1], _key_type(pred_keys), _ptr(loss), _ptr(grad),
+                                _stream(stream)))
+    return loss, grad
 
 
 def rule_forward_noalloc(z, hs, hd, seg, W, b, out, act: int = ACT_NONE, stream=None):
