@@ -1,24 +1,27 @@
 #!/usr/bin/env python
-"""Benchmark of one RelaNN rule evaluation on B300 (prints ONE JSON line on rank 0).
+"""Benchmark of RelaNN rule evaluation on B300; prints ONE JSON line on rank 0.
 
-Workload (default): the single rule at scale -- E has 16M tuples over 1M int64 keys, src ~ Zipf(1.1),
-dst uniform; H(id; z) with z bf16[128]; Linear 256 -> 128 on tcgen05 (bf16 in, f32 accumulate);
-SUM group-by dst. Inputs are seeded synthetic relations (no dataset).
+Default workload (--config c2): the single rule at scale -- E has 16M tuples over 1M int64 keys,
+src ~ Zipf(1.1), dst uniform; H(id; z) with z bf16[128]; Linear 256 -> 128 on tcgen05 (bf16 in, f32
+accumulate); SUM group-by dst. A step is one pass of the whole hot path over the batch: the content
+track (join build on H.id, probe of src and dst, grouping by dst: relnn_rule_plan) and the fused
+gather -> Concat -> Linear -> SUM forward (relnn_rule_forward). `value` = matched (join-output)
+tuples per second, summed over ranks.
 
-A step is one pass of the whole hot path over the batch: the content track (join build on H.id,
-probe of src and dst, grouping by dst: relnn_rule_plan) followed by the fused gather -> Concat ->
-Linear -> SUM forward (relnn_rule_forward). `value` = matched (join-output) tuples per second,
-summed over ranks. Extra keys report the warm forward (content cached, as the paper caches it
-across iterations) and the warm forward+backward.
+Other workloads (reported in the design notes, not the headline):
+  --config c3   two stacked rules + SUM readout + MSE, one training step (forward + backward) with
+                the content track cached across steps as the paper does; 4M tuples, 500k keys, d 64
+  --config c4   union of 3 branches (2M / 1M / 0.5M tuples, 300k keys, z and r f32[64],
+                Linear 192 -> 96 per branch), plan + forward, with and without Kahan summation
 
---impl reference times the FP64 CPU oracle on the host cores instead (bounded sample per step).
+--impl reference times the FP64 CPU oracle on the host cores instead (a bounded sample per step).
 Multi-GPU: the rule does not shard here; N ranks run N independent replicas (weak scaling).
+All inputs are seeded synthetic relations (no dataset).
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -33,8 +36,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rule tuples/s"
 UNIT = "tuples/s"
-# DRAM bytes per launch of fwd_tc_kernel from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# scaled to the 16M-tuple launch; None until a capture of the current kernel exists.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fwd_tc_kernel launch on the
+# default 16M-tuple workload, from the ncu capture summarised in profiles/; None until captured.
 NCU_TRAFFIC_PER_LAUNCH = None
 
 
@@ -44,19 +47,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="relnn", choices=["relnn", "reference"])
-    ap.add_argument("--n-tuples", type=int, default=16_000_000)
-    ap.add_argument("--n-keys", type=int, default=1_000_000)
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4"])
+    ap.add_argument("--n-tuples", type=int, default=None, help="override the tuple count (c2, c3)")
+    ap.add_argument("--n-keys", type=int, default=None, help="override the key count (c2, c3)")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="tuples in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the warm forward/backward extras")
+    ap.add_argument("--no-extras", action="store_true", help="skip warm / comparator extras")
     return ap.parse_args()
 
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
-        d = json.load(open(p))
-        return d, "measured"
+        return json.load(open(p)), "measured"
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
@@ -100,74 +103,389 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(args, seed):
-    from paper_2605_24207_b300 import workloads as W
-    return W.config2(seed=seed, n_tuples=args.n_tuples, n_keys=args.n_keys)
+def cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
-def cpu_oracle_rate(rel, n_sample: int, seed: int = 1):
-    """FP64 oracle (as it stands) on the first n_sample E rows with the full H; tuples/s and info."""
+class _Br:
+    def __init__(self, src, dst, W, b, r=None):
+        self.src, self.dst, self.W, self.b, self.r = src, dst, W, b, r
+
+
+def _bf16(a):
     import torch
-    from oracle import relnn_oracle as O
-    br = rel.branches[0]
-    n = min(n_sample, br.src.size)
-
-    class B:
-        pass
-    ob = B()
-    ob.src, ob.dst, ob.r = br.src[:n], br.dst[:n], None
-    ob.W = torch.from_numpy(br.W).to(torch.bfloat16).float().numpy()
-    ob.b = br.b
-    z = torch.from_numpy(rel.z).to(torch.bfloat16).float().numpy()
-    t0 = time.perf_counter()
-    _, _, sizes = O.rule_forward(rel.h_ids, z, [ob])
-    dt = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return sizes[0] / dt, sizes[0], dt, cores
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).float().numpy()
 
 
-def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle, rank 0 only, bounded sample per step."""
-    if rank != 0:
+# ===================================================================================== workloads
+class C2:
+    """Single rule at scale (the headline)."""
+    name = "c2"
+
+    def __init__(self, args):
+        from paper_2605_24207_b300 import workloads as W
+        self.n_tuples = args.n_tuples or 16_000_000
+        self.n_keys = args.n_keys or 1_000_000
+        self.rel = W.config2(seed=0, n_tuples=self.n_tuples, n_keys=self.n_keys)
+
+    def describe(self):
+        return (f"single rule H'(dst; SUM Linear(Concat(z_src, z_dst))), E {self.n_tuples} tuples over "
+                f"{self.n_keys} int64 keys (src Zipf 1.1, dst uniform), z bf16[128], Linear 256->128 "
+                f"bf16/f32-acc, SUM by dst; step = plan (join build+probe+group) + fused forward")
+
+    def to_device(self, dev):
+        import torch
+        from paper_2605_24207_b300 import relnn as R
+        rel, br = self.rel, self.rel.branches[0]
+        self.t = dict(h=torch.from_numpy(rel.h_ids).to(dev), src=torch.from_numpy(br.src).to(dev),
+                      dst=torch.from_numpy(br.dst).to(dev), z=torch.from_numpy(rel.z).to(dev).to(torch.bfloat16),
+                      W=torch.from_numpy(br.W).to(dev), b=torch.from_numpy(br.b).to(dev))
+        self.d, self.d_out = rel.z.shape[1], br.W.shape[0]
+        self.flags = R.FLAG_BF16
+        p = R.RulePlan(self.t["h"], [(self.t["src"], self.t["dst"])], self.d, self.d_out, flags=self.flags)
+        self.matched, self.n_out = p.n_matched, p.n_out
+        self.plan0 = p
+        self.out = torch.empty((max(self.n_out, 1), self.d_out), dtype=torch.float32, device=dev)
+
+    def step(self):
+        from paper_2605_24207_b300 import relnn as R
+        t = self.t
+        p = R.RulePlan(t["h"], [(t["src"], t["dst"])], self.d, self.d_out, flags=self.flags)
+        p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
+        return p
+
+    def roofline_kernel(self):
+        from paper_2605_24207_b300 import relnn as R
+        return R.PROF_FWD_TC, "fwd_tc_kernel", 2.0 * (2 * self.d) * self.d_out * self.matched
+
+    def e2e_setup(self):
+        import torch
+        self.hp = {k: v.cpu().pin_memory() for k, v in self.t.items()}
+        self.dv = {k: torch.empty_like(v) for k, v in self.t.items()}
+        self.out_host = torch.empty((self.n_out, self.d_out), dtype=torch.float32).pin_memory()
+        self.keys_host = torch.empty(self.n_out, dtype=self.t["h"].dtype).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in self.hp.values())
+        d2h = self.out_host.numel() * 4 + self.keys_host.numel() * self.keys_host.element_size()
+        return h2d, d2h
+
+    def e2e_step(self):
+        from paper_2605_24207_b300 import relnn as R
+        for k in self.hp:
+            self.dv[k].copy_(self.hp[k], non_blocking=True)
+        dv = self.dv
+        p = R.RulePlan(dv["h"], [(dv["src"], dv["dst"])], self.d, self.d_out, flags=self.flags)
+        o = p.forward(dv["z"], [dv["W"]], [dv["b"]], out=self.out)
+        self.out_host.copy_(o, non_blocking=True)
+        self.keys_host.copy_(p.out_keys(), non_blocking=True)
+        return p
+
+    def extras(self, timer, steps):
+        """Warm forward (content cached), warm forward + backward, and the unfused FP32 torch form."""
+        import torch
+        t, p = self.t, self.plan0
+        fwd = lambda: p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
+        ms_f = timer(fwd, max(3, steps))
+        dout = torch.ones_like(self.out[: self.n_out])
+
+        def fb():
+            fwd()
+            p.backward(dout, t["z"], [t["W"]], [t["b"]])
+        ms_fb = timer(fb, 3)
+        ms_torch = timer(self.torch_step, 3)
+        return {"warm_forward_tuples_per_s": self.matched / (ms_f * 1e-3), "warm_forward_ms": ms_f,
+                "warm_fwd_bwd_tuples_per_s": self.matched / (ms_fb * 1e-3), "warm_fwd_bwd_ms": ms_fb,
+                "torch_fp32_unfused": {"tuples_per_s": self.matched / (ms_torch * 1e-3), "ms_per_step": ms_torch,
+                                       "what": "sort+searchsorted join, index_select, cat, F.linear f32 (TF32 off), "
+                                               "unique + index_add_; same step (join + forward)"}}
+
+    def torch_step(self):
+        """The plain unfused FP32 form of the same step in torch ops (the comparator)."""
+        import torch
+        import torch.nn.functional as F
+        t = self.t
+        torch.backends.cuda.matmul.allow_tf32 = False
+        h = t["h"]
+        order = torch.argsort(h)
+        sk = h[order]
+        ps = torch.searchsorted(sk, t["src"]).clamp_(max=sk.numel() - 1)
+        pd = torch.searchsorted(sk, t["dst"]).clamp_(max=sk.numel() - 1)
+        keep = (sk[ps] == t["src"]) & (sk[pd] == t["dst"])
+        hs, hd = order[ps[keep]], order[pd[keep]]
+        z = t["z"].float()
+        X = torch.cat([z.index_select(0, hs), z.index_select(0, hd)], dim=1)
+        Y = F.linear(X, t["W"], t["b"])
+        uk, inv = torch.unique(t["dst"][keep], return_inverse=True)
+        out = torch.zeros((uk.numel(), Y.shape[1]), dtype=torch.float32, device=Y.device)
+        out.index_add_(0, inv, Y)
+        return out
+
+    def cpu_rate(self, n_sample):
+        from oracle import relnn_oracle as O
+        br = self.rel.branches[0]
+        n = min(n_sample, br.src.size)
+        ob = _Br(br.src[:n], br.dst[:n], _bf16(br.W), br.b)
+        z = _bf16(self.rel.z)
+        t0 = time.perf_counter()
+        _, _, sizes = O.rule_forward(self.rel.h_ids, z, [ob])
+        dt = time.perf_counter() - t0
+        return sizes[0] / dt, f"first {n} of {self.n_tuples} E rows with the full H ({sizes[0]} matched tuples, {dt:.1f} s)"
+
+
+class C3:
+    """Two stacked rules + SUM readout + MSE: one training step (content cached)."""
+    name = "c3"
+
+    def __init__(self, args):
+        from paper_2605_24207_b300 import workloads as W
+        self.n_tuples = args.n_tuples or 4_000_000
+        self.n_keys = args.n_keys or 500_000
+        self.args = args
+        r1, W2, b2, groups, targets = W.config3(seed=0, n_tuples=self.n_tuples, n_keys=self.n_keys)
+        br = r1.branches[0]
+        self.host = dict(h=r1.h_ids, z=r1.z, src=br.src, dst=br.dst, W1=br.W, b1=br.b, W2=W2, b2=b2,
+                         g_keys=r1.h_ids.copy(), g_groups=groups, t_keys=np.arange(8, dtype=np.int32),
+                         targets=targets)
+
+    def describe(self):
+        return (f"two stacked rules (Linear 128->64 + ReLU, Linear 128->64) + SUM readout into 8 groups + "
+                f"MSE; E {self.n_tuples} tuples over {self.n_keys} int32 keys (src Zipf 1.2), z f32[64]; "
+                f"step = forward + backward (BF16 form, content cached across steps)")
+
+    def to_device(self, dev):
+        import torch
+        from paper_2605_24207_b300 import programs
+        self.t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in self.host.items()}
+        t = self.t
+        self.prog = programs.StackedReadout(t["h"], t["src"], t["dst"], t["g_keys"], t["g_groups"], t["t_keys"],
+                                            t["targets"], 64, bf16=True)
+        self.matched = self.prog.tuples
+
+    def step(self):
+        t = self.t
+        return self.prog.step(t["z"], t["W1"], t["b1"], t["W2"], t["b2"])
+
+    def roofline_kernel(self):
+        from paper_2605_24207_b300 import relnn as R
+        # the backward's two GEMMs (dX, dW): 2 x 2 x 128 x 64 FLOP per rule tuple; one launch per rule
+        return R.PROF_BWD_TC, "bwd_tc_kernel", 2.0 * 2.0 * 128 * 64 * self.matched / 2.0
+
+    def e2e_setup(self):
+        import torch
+        keys = ("z", "W1", "b1", "W2", "b2")
+        self.hp = {k: self.t[k].cpu().pin_memory() for k in keys}
+        self.dv = {k: torch.empty_like(self.t[k]) for k in keys}
+        self.loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+        return sum(v.numel() * v.element_size() for v in self.hp.values()), 4
+
+    def e2e_step(self):
+        for k in self.hp:
+            self.dv[k].copy_(self.hp[k], non_blocking=True)
+        d = self.dv
+        loss, g = self.prog.step(d["z"], d["W1"], d["b1"], d["W2"], d["b2"])
+        self.loss_host.copy_(loss, non_blocking=True)
+        return loss
+
+    def extras(self, timer, steps):
+        ms_t = timer(self.torch_step, 3)
+        return {"torch_fp32_unfused": {"tuples_per_s": self.matched / (ms_t * 1e-3), "ms_per_step": ms_t,
+                                       "what": "index_select + cat + F.linear f32 (TF32 off) + ReLU + index_add_ "
+                                               "per rule, index_add_ readout, MSE, torch.autograd backward; join "
+                                               "indices cached like the library's plans"}}
+
+    def torch_step(self):
+        import torch
+        import torch.nn.functional as F
+        torch.backends.cuda.matmul.allow_tf32 = False
+        t = self.t
+        if not hasattr(self, "_idx"):
+            def join(keys, src, dst):
+                order = torch.argsort(keys)
+                sk = keys[order]
+                ps = torch.searchsorted(sk, src).clamp_(max=sk.numel() - 1)
+                pd = torch.searchsorted(sk, dst).clamp_(max=sk.numel() - 1)
+                keep = (sk[ps] == src) & (sk[pd] == dst)
+                uk, inv = torch.unique(dst[keep], return_inverse=True)
+                return order[ps[keep]], order[pd[keep]], uk, inv
+            hs1, hd1, k1, inv1 = join(t["h"], t["src"], t["dst"])
+            hs2, hd2, k2, inv2 = join(k1, t["src"], t["dst"])
+            sk = k2
+            pg = torch.searchsorted(sk, t["g_keys"]).clamp_(max=sk.numel() - 1)
+            keep = sk[pg] == t["g_keys"]
+            go, ginv = torch.unique(t["g_groups"][keep], return_inverse=True)
+            self._idx = (hs1, hd1, k1, inv1, hs2, hd2, k2, inv2, pg[keep], ginv, go)
+        hs1, hd1, k1, inv1, hs2, hd2, k2, inv2, gsrc, ginv, go = self._idx
+        z = t["z"].clone().requires_grad_(True)
+        W1 = t["W1"].clone().requires_grad_(True)
+        b1 = t["b1"].clone().requires_grad_(True)
+        W2 = t["W2"].clone().requires_grad_(True)
+        b2 = t["b2"].clone().requires_grad_(True)
+        Y1 = F.relu(F.linear(torch.cat([z.index_select(0, hs1), z.index_select(0, hd1)], 1), W1, b1))
+        h1 = torch.zeros((k1.numel(), 64), device=z.device).index_add(0, inv1, Y1)
+        Y2 = F.linear(torch.cat([h1.index_select(0, hs2), h1.index_select(0, hd2)], 1), W2, b2)
+        h2 = torch.zeros((k2.numel(), 64), device=z.device).index_add(0, inv2, Y2)
+        ho = torch.zeros((go.numel(), 64), device=z.device).index_add(0, ginv, h2.index_select(0, gsrc))
+        loss = ((ho - t["targets"][go.long()]) ** 2).mean()
+        loss.backward()
+        return loss
+
+    def cpu_rate(self, n_sample):
+        from oracle import relnn_oracle as O
+        from paper_2605_24207_b300 import workloads as W
+        # a bounded sample of the same workload: the same recipe at 1/40 of the tuples and keys
+        nt, nk = max(1000, self.n_tuples // 40), max(100, self.n_keys // 40)
+        r1, W2, b2, groups, targets = W.config3(seed=0, n_tuples=nt, n_keys=nk)
+        br = r1.branches[0]
+        a = (r1.h_ids, r1.z, br.src, br.dst, br.W, br.b, W2, b2, r1.h_ids.copy(), groups,
+             np.arange(8, dtype=np.int32), targets)
+        t0 = time.perf_counter()
+        f = O.stacked_forward(*a)
+        O.stacked_backward(*a, fwd=f)
+        dt = time.perf_counter() - t0
+        e1 = O.join(br.src, br.dst, r1.h_ids)[0].size
+        e2 = O.join(br.src, br.dst, f["k1"])[0].size
+        return (e1 + e2) / dt, f"same recipe at {nt} tuples / {nk} keys ({e1 + e2} rule tuples, {dt:.1f} s)"
+
+
+class C4:
+    """Union of three branches into one output (plan + forward)."""
+    name = "c4"
+
+    def __init__(self, args):
+        from paper_2605_24207_b300 import workloads as W
+        self.rel = W.config4(seed=0)
+        self.sizes = [b.src.size for b in self.rel.branches]
+
+    def describe(self):
+        return ("union replicator over 3 relations (2M/1M/0.5M tuples, shared 300k int32 keys, src uniform, "
+                "dst Zipf 1.0), z f32[64], r f32[64] per tuple, BF16 Linear 192->96 per branch, SUM by dst; "
+                "step = plan + forward, Kahan summation")
+
+    def to_device(self, dev):
+        import torch
+        from paper_2605_24207_b300 import relnn as R
+        rel = self.rel
+        self.t = dict(h=torch.from_numpy(rel.h_ids).to(dev), z=torch.from_numpy(rel.z).to(dev))
+        self.brs = [(torch.from_numpy(b.src).to(dev), torch.from_numpy(b.dst).to(dev)) for b in rel.branches]
+        self.W = [torch.from_numpy(b.W).to(dev) for b in rel.branches]
+        self.b = [torch.from_numpy(b.b).to(dev) for b in rel.branches]
+        self.r = [torch.from_numpy(b.r).to(dev) for b in rel.branches]
+        self.flags = R.FLAG_BF16 | R.FLAG_KAHAN
+        p = R.RulePlan(self.t["h"], self.brs, 64, 96, flags=self.flags, d_r=64)
+        self.matched, self.n_out = p.n_matched, p.n_out
+        self.plan0 = p
+        self.out = torch.empty((self.n_out, 96), dtype=torch.float32, device=dev)
+
+    def step(self):
+        from paper_2605_24207_b300 import relnn as R
+        p = R.RulePlan(self.t["h"], self.brs, 64, 96, flags=self.flags, d_r=64)
+        p.forward(self.t["z"], self.W, self.b, self.r, out=self.out)
+        return p
+
+    def roofline_kernel(self):
+        from paper_2605_24207_b300 import relnn as R
+        return R.PROF_FWD_TC, "fwd_tc_kernel", 2.0 * 192 * 96 * self.matched / 3.0
+
+    def e2e_setup(self):
+        import torch
+        self.hp = [v.cpu().pin_memory() for v in [self.t["h"], self.t["z"]] + [x for s, d in self.brs for x in (s, d)] + self.r]
+        self.dv = [torch.empty_like(v, device="cuda") for v in self.hp]
+        self.out_host = torch.empty((self.n_out, 96), dtype=torch.float32).pin_memory()
+        return sum(v.numel() * v.element_size() for v in self.hp), self.out_host.numel() * 4
+
+    def e2e_step(self):
+        from paper_2605_24207_b300 import relnn as R
+        for a, b in zip(self.dv, self.hp):
+            a.copy_(b, non_blocking=True)
+        h, z = self.dv[0], self.dv[1]
+        brs = [(self.dv[2 + 2 * i], self.dv[3 + 2 * i]) for i in range(3)]
+        r = self.dv[8:11]
+        p = R.RulePlan(h, brs, 64, 96, flags=self.flags, d_r=64)
+        o = p.forward(z, self.W, self.b, r, out=self.out)
+        self.out_host.copy_(o, non_blocking=True)
+        return p
+
+    def extras(self, timer, steps):
+        """Error per output relation against the FP64 oracle on sampled keys, Kahan on and off."""
+        from oracle import relnn_oracle as O
+        from paper_2605_24207_b300 import relnn as R
+        res = {}
+        keys = self.plan0.out_keys().cpu().numpy()
+        rng = np.random.default_rng(0)
+        # the hubs (largest segments) plus a uniform sample of the other keys
+        deg = np.zeros(keys.size, np.int64)
+        pos = {k: i for i, k in enumerate(keys.tolist())}
+        for b in self.rel.branches:
+            idx = np.searchsorted(keys, b.dst)
+            ok = (idx < keys.size) & (keys[np.minimum(idx, keys.size - 1)] == b.dst)
+            np.add.at(deg, idx[ok], 1)
+        pick = np.unique(np.concatenate([np.argsort(-deg)[:20], rng.choice(keys.size, 200, replace=False)]))
+        sel = set(keys[pick].tolist())
+        brs = []
+        for b in self.rel.branches:
+            m = np.isin(b.dst, keys[pick])
+            brs.append(_Br(b.src[m], b.dst[m], _bf16(b.W), b.b, _bf16(b.r[m])))
+        ok, oo, _ = O.rule_forward(self.rel.h_ids, _bf16(self.rel.z), brs)
+        for kahan in (False, True):
+            fl = R.FLAG_BF16 | (R.FLAG_KAHAN if kahan else 0)
+            p = R.RulePlan(self.t["h"], self.brs, 64, 96, flags=fl, d_r=64)
+            out = p.forward(self.t["z"], self.W, self.b, self.r).cpu().numpy()[pick]
+            err = float(np.linalg.norm(out - oo) / np.linalg.norm(oo))
+            ms = timer(lambda: p.forward(self.t["z"], self.W, self.b, self.r, out=self.out), max(3, steps))
+            res["kahan" if kahan else "plain"] = {"rel_frob_err_vs_fp64": err, "warm_forward_ms": ms,
+                                                  "warm_forward_tuples_per_s": self.matched / (ms * 1e-3)}
+        res["sampled_keys"] = int(pick.size)
+        return {"union_error_and_kahan": res}
+
+    def cpu_rate(self, n_sample):
+        from oracle import relnn_oracle as O
+        brs, n = [], 0
+        for b in self.rel.branches:
+            k = min(b.src.size, max(1, n_sample // 6))
+            brs.append(_Br(b.src[:k], b.dst[:k], _bf16(b.W), b.b, _bf16(b.r[:k])))
+        t0 = time.perf_counter()
+        _, _, sizes = O.rule_forward(self.rel.h_ids, _bf16(self.rel.z), brs)
+        dt = time.perf_counter() - t0
+        return sum(sizes) / dt, f"first {n_sample // 6} E rows of each branch with the full H ({sum(sizes)} tuples, {dt:.1f} s)"
+
+
+WORKLOADS = {"c2": C2, "c3": C3, "c4": C4}
+
+
+# ===================================================================================== arms
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands on the host cores (rank 0 only)."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
-    rel = make_workload(args, 0)
-    sample = min(args.cpu_sample // 4, rel.branches[0].src.size)
+    wl = WORKLOADS[args.config](args)
+    sample = max(1000, args.cpu_sample // 4)
     for _ in range(args.warmup):
-        cpu_oracle_rate(rel, sample)
-    tot_t, tot_n = 0.0, 0
+        wl.cpu_rate(sample)
+    rates, desc = [], ""
+    t_tot = 0.0
     for _ in range(args.steps):
-        rate, n, dt, cores = cpu_oracle_rate(rel, sample)
-        tot_t += dt
-        tot_n += n
-    value = tot_n / tot_t
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"single rule, E {args.n_tuples} tuples over {args.n_keys} int64 keys, "
-                               f"z bf16[128], Linear 256->128, SUM by dst (oracle on {sample}-tuple samples)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"first {sample} E rows with the full H per step"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
+        t0 = time.perf_counter()
+        rate, desc = wl.cpu_rate(sample)
+        t_tot += time.perf_counter() - t0
+        rates.append(rate)
+    value = float(statistics.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded relations; no dataset)",
+            "config": {"workload": wl.describe() + " -- FP64 CPU oracle on a bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores(), "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-
+def run_relnn(args):
     import torch
     import torch.distributed as dist
     from paper_2605_24207_b300 import relnn as R
 
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -177,30 +495,32 @@ def main():
         if world > 1:
             dist.barrier()
 
-    rel = make_workload(args, 0)
-    br = rel.branches[0]
-    # device-resident inputs
-    h = torch.from_numpy(rel.h_ids).to(dev)
-    src = torch.from_numpy(br.src).to(dev)
-    dst = torch.from_numpy(br.dst).to(dev)
-    z = torch.from_numpy(rel.z).to(dev).to(torch.bfloat16)
-    Wt = torch.from_numpy(br.W).to(dev)
-    bt = torch.from_numpy(br.b).to(dev)
-    d, d_out = rel.z.shape[1], br.W.shape[0]
-    flags = R.FLAG_BF16
-    plan0 = R.RulePlan(h, [(src, dst)], d, d_out, flags=flags)
-    matched, n_out = plan0.n_matched, plan0.n_out
-    out = torch.empty((max(n_out, 1), d_out), dtype=torch.float32, device=dev)
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        tt = torch.tensor([x], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
     stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def step():
-        p = R.RulePlan(h, [(src, dst)], d, d_out, flags=flags)
-        p.forward(z, [Wt], [bt], out=out)
-        return p
+    def timer(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
 
-    # ---------------------------------------------------------------- timed region (device inputs)
+    wl = WORKLOADS[args.config](args)
+    wl.to_device(dev)
+
+    # ------------------------------------------------------------ timed region (device inputs)
     for _ in range(args.warmup):
-        step()
+        wl.step()
     torch.cuda.synchronize()
     barrier()
     clk = Clocks(local)
@@ -209,12 +529,11 @@ def main():
     n_launch0 = R.launch_count()
     torch.cuda.synchronize()
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
     t_wall0 = time.perf_counter()
+    e0.record(stream)
     keep = None
     for _ in range(args.steps):
-        keep = step()
+        keep = wl.step()
     e1.record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
@@ -222,123 +541,69 @@ def main():
     gpu_launches = R.launch_count() - n_launch0
     R.profile_enable(False)
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    fwd_ms, fwd_n = R.profile_read(R.PROF_FWD_TC)
+    t_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    value = world * wl.matched / (t_step * 1e-3)
+    kid, kname, flops = wl.roofline_kernel()
+    k_ms, k_n = R.profile_read(kid)
     plan_ms, plan_n = R.profile_read(R.PROF_PLAN)
-    fix_ms, fix_n = R.profile_read(R.PROF_FIXUP)
-    keep.check()
-    t_step = ms / args.steps
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = world * matched / (t_step * 1e-3)
+    del keep
 
-    # ---------------------------------------------------------------- roofline of the fused kernel
     pk, pk_src = peaks()
-    flops_per_launch = 2.0 * (2 * d) * d_out * matched
-    fwd_avg_ms = fwd_ms / max(fwd_n, 1)
-    achieved = flops_per_launch / (fwd_avg_ms * 1e-3) / 1e12
+    k_avg = k_ms / max(k_n, 1)
+    achieved = flops / (k_avg * 1e-3) / 1e12
     peak = pk["bf16_tflops_sustained"]
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC_PER_LAUNCH,
-                "kernel": "fwd_tc_kernel", "peak_source": f"{pk_src} bf16 sustained",
-                "kernel_ms": fwd_avg_ms}
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC_PER_LAUNCH if wl.name == "c2" else None, "kernel": kname,
+                "kernel_ms": k_avg, "kernel_launches_per_step": k_n / args.steps,
+                "peak_source": f"{pk_src} bf16 sustained"}
 
-    extras = {}
-    if not args.no_extras:
-        # warm forward (content cached) and warm forward + backward
-        keep_plan = plan0
-        for _ in range(3):
-            keep_plan.forward(z, [Wt], [bt], out=out)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        reps = max(3, args.steps)
-        for _ in range(reps):
-            keep_plan.forward(z, [Wt], [bt], out=out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        warm_fwd_ms = e0.elapsed_time(e1) / reps
-        dout = torch.ones_like(out[:n_out])
-        keep_plan.backward(dout, z, [Wt], [bt])
-        torch.cuda.synchronize()
-        e0.record(stream)
-        reps_b = 3
-        for _ in range(reps_b):
-            keep_plan.forward(z, [Wt], [bt], out=out)
-            keep_plan.backward(dout, z, [Wt], [bt])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        warm_fb_ms = e0.elapsed_time(e1) / reps_b
-        extras = {"warm_forward_tuples_per_s": matched / (warm_fwd_ms * 1e-3), "warm_forward_ms": warm_fwd_ms,
-                  "warm_fwd_bwd_tuples_per_s": matched / (warm_fb_ms * 1e-3), "warm_fwd_bwd_ms": warm_fb_ms,
-                  "plan_ms": plan_ms / max(plan_n, 1), "fixup_ms": fix_ms / max(fix_n, 1)}
+    extras = {} if args.no_extras else wl.extras(timer, args.steps)
+    extras["plan_ms"] = plan_ms / plan_n if plan_n else None
 
-    # ---------------------------------------------------------------- end to end (host buffers)
-    hp = {k: v.cpu().pin_memory() for k, v in dict(h=h, src=src, dst=dst, z=z, W=Wt, b=bt).items()}
-    dv = {k: torch.empty_like(v) for k, v in dict(h=h, src=src, dst=dst, z=z, W=Wt, b=bt).items()}
-    out_host = torch.empty((n_out, d_out), dtype=torch.float32).pin_memory()
-    keys_host = torch.empty(n_out, dtype=h.dtype).pin_memory()
-    h2d = sum(v.numel() * v.element_size() for v in hp.values())
-    d2h = out_host.numel() * 4 + keys_host.numel() * keys_host.element_size()
-
-    def e2e_step():
-        for k in hp:
-            dv[k].copy_(hp[k], non_blocking=True)
-        p = R.RulePlan(dv["h"], [(dv["src"], dv["dst"])], d, d_out, flags=flags)
-        o = p.forward(dv["z"], [dv["W"]], [dv["b"]], out=out)
-        out_host.copy_(o, non_blocking=True)
-        keys_host.copy_(p.out_keys(), non_blocking=True)
-        return p
-
+    # ------------------------------------------------------------ end to end (host buffers)
+    h2d, d2h = wl.e2e_setup()
     e2e_steps = max(3, args.steps // 2)
     for _ in range(2):
-        e2e_step()
+        wl.e2e_step()
     torch.cuda.synchronize()
     barrier()
     e0.record(stream)
     for _ in range(e2e_steps):
-        e2e_step()
+        wl.e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, n, dt, cores = cpu_oracle_rate(rel, args.cpu_sample)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {args.cpu_sample} of {args.n_tuples} E rows with the full H "
-                         f"({n} matched tuples, {dt:.1f} s)"}
+        rate, desc = wl.cpu_rate(args.cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores(), "kind": "oracle", "sample": desc}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16",
-            "data": "synthetic (seeded Zipf/uniform relations; no dataset)",
-            "config": {"workload": f"single rule H'(dst; SUM Linear(Concat(z_src, z_dst))), E {args.n_tuples} "
-                                   f"tuples over {args.n_keys} int64 keys (src Zipf 1.1, dst uniform), "
-                                   f"z bf16[{d}], Linear {2 * d}->{d_out} bf16/f32-acc, SUM by dst; step = "
-                                   f"plan (join build+probe+group) + fused forward",
-                       "matched_tuples": matched, "out_keys": n_out,
-                       "l2": "inputs larger than L2 (E 256 MB, H.z 256 MB, output 512 MB)",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded Zipf/uniform relations; no dataset)",
+            "config": {"workload": wl.describe(), "matched_tuples_per_step": wl.matched,
+                       "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": {"value": world * matched / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": world * wl.matched / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": gpu_launches,
-            "clocks": clocks,
-            "wall_s_timed": t_wall,
+            "gpu_launches": gpu_launches, "clocks": clocks, "wall_s_timed": t_wall,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_relnn(args)
 
 
 if __name__ == "__main__":
