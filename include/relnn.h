@@ -60,6 +60,7 @@ typedef enum relnn_act_t { RELNN_ACT_NONE = 0, RELNN_ACT_RELU = 1 } relnn_act_t;
                                          is keyed by the raw dst value (e.g. a readout into groups)    */
 #define RELNN_FLAG_NO_CONCAT_DST 0x10u /* join H(dst) (it filters tuples) but leave z_dst out of Concat */
 #define RELNN_FLAG_RELU_MASK 0x20u    /* forward stores the per-tuple ReLU mask for a later backward   */
+#define RELNN_FLAG_TILE128 0x40u      /* BF16 forward: 128 matched tuples per tile instead of 256      */
 
 /* Device status codes (relnn_last_device_error) */
 #define RELNN_DEV_OK 0
@@ -202,6 +203,61 @@ relnn_status relnn_mse_loss(const float* d_pred, const void* d_pred_keys, int64_
 relnn_status relnn_rule_forward_noalloc(const float* d_z, int32_t d, const int32_t* d_hs, const int32_t* d_hd,
                                         const int32_t* d_seg, int64_t m, const float* d_W, const float* d_b,
                                         int32_t d_out, relnn_act_t act, float* d_out_z, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Serving: a stream of independent rule queries evaluated with one shared Linear (the `?pred`
+ * statement of paper Sec. 3.3 issued by many clients against a fitted rule). Queries of uneven
+ * sizes are admitted by device memory and batched: the admitted queries' relations are placed in
+ * disjoint key ranges of one batch, which is planned and evaluated by one fused persistent launch;
+ * several batches run concurrently on separate streams while new queries keep arriving.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct relnn_server_cfg {
+    int32_t d;                  /* width of every query's H.z                                       */
+    int32_t d_out;              /* width of the output embeddings                                   */
+    const void* d_W;            /* shared Linear [d_out, 2d] (device, caller-owned, must outlive the server) */
+    relnn_float_t w_dtype;
+    const float* d_b;           /* shared bias [d_out] or NULL                                      */
+    relnn_act_t act;
+    uint32_t flags;             /* rule flags (RELNN_FLAG_BF16, RELNN_FLAG_KAHAN)                   */
+    relnn_float_t z_dtype;      /* dtype of every query's H.z                                       */
+    int32_t max_queue;          /* queries waiting or running; submit returns EAGAIN beyond it      */
+    int64_t mem_budget_bytes;   /* device bytes batches may hold at once (0: 80% of free memory)    */
+    int64_t max_batch_tuples;   /* E tuples per batch (a larger single query runs alone)            */
+    int32_t max_batch_queries;  /* queries per batch                                                */
+    int64_t tile128_below;      /* batches with fewer E tuples use 128-tuple tiles (autotuned)       */
+    int32_t n_workers;          /* batches in flight at once (one stream and host thread each)       */
+} relnn_server_cfg;
+
+typedef struct relnn_query {
+    const void* d_h_ids;        /* [n_h] int32 keys of H (device; valid until the query completes)  */
+    int64_t n_h;
+    const void* d_z;            /* [n_h, d] embeddings (server z_dtype)                             */
+    const void* d_src;          /* [n_tuples] int32 E.src                                           */
+    const void* d_dst;          /* [n_tuples] int32 E.dst                                           */
+    int64_t n_tuples;
+} relnn_query;
+
+typedef struct relnn_result {
+    int64_t n_out;              /* output rows                                                      */
+    const int32_t* d_out_keys;  /* [n_out] sorted output keys (device, owned by the server)         */
+    const float* d_out_z;       /* [n_out, d_out] f32 (device, owned by the server)                 */
+    double latency_us;          /* submit -> results ready on the device                            */
+    int32_t batch_queries;      /* queries that shared this query's batch                           */
+} relnn_result;
+
+/* Creates a server (starts its worker threads on the current device). Errors: EINVAL, ENOMEM. */
+relnn_status relnn_server_create(const relnn_server_cfg* cfg, relnn_server_t* out);
+/* Queues a query; *ticket identifies it. EAGAIN: queue full (retry later); ENOMEM: the query can
+ * never fit the memory budget; EINVAL: bad query. Never blocks on the device. */
+relnn_status relnn_serve_submit(relnn_server_t s, const relnn_query* q, uint64_t* ticket);
+/* Waits up to timeout_us (0 = just check) for a ticket. OK: *res filled (buffers stay valid until
+ * relnn_serve_release); EAGAIN: still pending (timeout 0); ETIMEDOUT: pending after the wait;
+ * EINVAL: unknown ticket; EDEVICE / ECUDA: the query's batch failed. */
+relnn_status relnn_serve_poll(relnn_server_t s, uint64_t ticket, relnn_result* res, uint32_t timeout_us);
+/* Frees a completed ticket's result buffers. */
+relnn_status relnn_serve_release(relnn_server_t s, uint64_t ticket);
+/* Stops accepting queries, finishes the queued ones, joins the workers and frees everything. */
+relnn_status relnn_server_destroy(relnn_server_t s);
 
 /* ---------------------------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to report roofline fractions).

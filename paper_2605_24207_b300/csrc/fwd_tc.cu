@@ -478,7 +478,9 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
         return RELNN_ENOTSUP;
     }
     const int m_blocks = (p.d_out + 127) / 128;
-    const int tile_n = m_blocks == 1 ? 256 : 128;
+    // 256 matched tuples per tile; 128 when d_out needs two TMEM blocks or the caller asks for
+    // smaller tiles (more tiles per SM on small inputs)
+    const int tile_n = (m_blocks == 1 && !(p.flags & RELNN_FLAG_TILE128)) ? 256 : 128;
     const uint32_t w_bytes = (uint32_t)L.n_kb * m_blocks * 16384u;
     const uint32_t stage_bytes = (uint32_t)tile_n * 128u;
     const int bar_bytes = 256;

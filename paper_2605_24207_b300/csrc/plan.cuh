@@ -49,6 +49,23 @@ struct Plan {
         for (auto& b : br) s += b.m;
         return s;
     }
+    // Frees every buffer of the plan in the order of stream s when the plan is destroyed (instead of
+    // a synchronising cudaFree), for plans whose work all ran on s.
+    void retire_on(cudaStream_t s) {
+        DevBuf* bufs[] = {&H.rows_sorted, &H.run_start, &H.uid_of_pos, &H.ukeys, &H.slot_keys, &H.slot_vals,
+                          &H.status, &out_keys, &status, &carry, &wpack, &scratch};
+        for (DevBuf* b : bufs) {
+            b->ordered = true;
+            b->st = s;
+        }
+        for (auto& b : br) {
+            DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.src_perm, &b.src_hs, &b.relu_mask};
+            for (DevBuf* x : bb) {
+                x->ordered = true;
+                x->st = s;
+            }
+        }
+    }
 };
 
 relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st);

@@ -1,0 +1,355 @@
+// Serving engine (relnn_server_*): memory-admitted continuous batching of independent rule queries
+// that share one Linear.
+//
+// Host side: submit() queues a query after checking that its device-memory estimate can ever fit the
+// budget; n_workers host threads each own a non-blocking CUDA stream and repeatedly take, in arrival
+// order, as many queued queries as fit (E tuples, query count, free budget), evaluate them as ONE
+// batch and publish per-query results. Queries that arrive while batches run are picked up by the
+// next free worker, so batches overlap on the device.
+//
+// A batch is one rule over disjoint key ranges: key k of the i-th query of the batch becomes
+// (i << 32) + (k + 2^31) (int64, order-preserving), the queries' H.z rows are concatenated, and the
+// usual content track (relnn plan) and fused persistent forward run once over all of it. The output
+// keys come out sorted by (query, key); a binary search per query cuts them back into per-query
+// results (keys restored to int32).
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "fwd.cuh"
+
+namespace relnn {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+__global__ void batch_keys_kernel(const int32_t* __restrict__ in, int64_t n, int64_t prefix, int64_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = prefix + ((int64_t)in[i] + 2147483648ll);
+}
+
+__global__ void strip_keys_kernel(const int64_t* __restrict__ in, int64_t n, int32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)((in[i] & 0xffffffffll) - 2147483648ll);
+}
+
+// lo[q] = first output row of query q (keys are sorted by query prefix); lo[nq] = n.
+__global__ void ranges_kernel(const int64_t* __restrict__ keys, int64_t n, int nq, int64_t* __restrict__ lo) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > nq) return;
+    const int64_t target = (int64_t)q << 32;
+    int64_t a = 0, b = n;
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (keys[mid] < target) a = mid + 1;
+        else b = mid;
+    }
+    lo[q] = (q == nq) ? n : a;
+}
+
+inline int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 148 * 8)); }
+
+struct Query {
+    uint64_t ticket = 0;
+    relnn_query q{};
+    int64_t mem = 0;
+    Clock::time_point t_submit;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    relnn_status st = RELNN_OK;
+    DevBuf keys, z;
+    int64_t n_out = 0;
+    double latency_us = 0;
+    int batch_q = 0;
+};
+
+}  // namespace
+}  // namespace relnn
+
+using namespace relnn;
+
+struct relnn_server_s {
+    relnn_server_cfg cfg{};
+    int dev = 0;
+    size_t z_esz = 4;
+    int64_t budget = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Query*> queue;
+    std::unordered_map<uint64_t, Query*> all;
+    uint64_t next_ticket = 1;
+    int64_t mem_in_use = 0;
+    int in_system = 0;
+    bool stopping = false;
+    std::vector<std::thread> workers;
+};
+
+namespace relnn {
+namespace {
+
+// Device bytes a query may need while its batch runs (keys, sort temporaries, plan, outputs).
+int64_t query_mem(const relnn_server_s* S, const relnn_query& q) {
+    const int64_t T = q.n_tuples, K = q.n_h;
+    return T * 112 + K * (96 + (int64_t)S->cfg.d * (int64_t)S->z_esz) + K * (int64_t)S->cfg.d_out * 8 + (1 << 20);
+}
+
+relnn_status run_batch(relnn_server_s* S, std::vector<Query*>& batch, cudaStream_t st) {
+    const int nq = (int)batch.size();
+    const int d = S->cfg.d, d_out = S->cfg.d_out;
+    int64_t K = 0, T = 0;
+    std::vector<int64_t> h_off(nq), t_off(nq);
+    for (int i = 0; i < nq; ++i) {
+        h_off[i] = K;
+        t_off[i] = T;
+        K += batch[i]->q.n_h;
+        T += batch[i]->q.n_tuples;
+    }
+    DevBuf hk, zb, sk, dk, lo;
+    RELNN_TRY(hk.alloc_tmp(sizeof(int64_t) * std::max<int64_t>(K, 1), st));
+    RELNN_TRY(zb.alloc_tmp(S->z_esz * d * std::max<int64_t>(K, 1), st));
+    RELNN_TRY(sk.alloc_tmp(sizeof(int64_t) * std::max<int64_t>(T, 1), st));
+    RELNN_TRY(dk.alloc_tmp(sizeof(int64_t) * std::max<int64_t>(T, 1), st));
+    RELNN_TRY(lo.alloc_tmp(sizeof(int64_t) * (nq + 1), st));
+    for (int i = 0; i < nq; ++i) {
+        const relnn_query& q = batch[i]->q;
+        const int64_t prefix = (int64_t)i << 32;
+        if (q.n_h > 0) {
+            { batch_keys_kernel<<<grid_for(q.n_h), 256, 0, st>>>((const int32_t*)q.d_h_ids, q.n_h, prefix, hk.as<int64_t>() + h_off[i]); note_launch(); }
+            RELNN_CUDA(cudaMemcpyAsync(zb.as<uint8_t>() + h_off[i] * d * S->z_esz, q.d_z, q.n_h * d * S->z_esz,
+                                       cudaMemcpyDeviceToDevice, st));
+        }
+        if (q.n_tuples > 0) {
+            { batch_keys_kernel<<<grid_for(q.n_tuples), 256, 0, st>>>((const int32_t*)q.d_src, q.n_tuples, prefix, sk.as<int64_t>() + t_off[i]); note_launch(); }
+            { batch_keys_kernel<<<grid_for(q.n_tuples), 256, 0, st>>>((const int32_t*)q.d_dst, q.n_tuples, prefix, dk.as<int64_t>() + t_off[i]); note_launch(); }
+        }
+    }
+    RELNN_CUDA(cudaGetLastError());
+    relnn_branch_desc bd{sk.p, dk.p, T, 0};
+    relnn_rule_desc desc{};
+    desc.key_type = RELNN_I64;
+    desc.d_h_ids = hk.p;
+    desc.n_h = K;
+    desc.d = d;
+    desc.d_out = d_out;
+    desc.n_branches = 1;
+    desc.branches = &bd;
+    desc.act = S->cfg.act;
+    desc.flags = S->cfg.flags & (RELNN_FLAG_BF16 | RELNN_FLAG_KAHAN);
+    if (T < S->cfg.tile128_below) desc.flags |= RELNN_FLAG_TILE128;
+    Plan P;
+    // on every exit the plan's buffers go back to the pool in stream order (no device-wide sync)
+    struct Retire {
+        Plan& p;
+        cudaStream_t s;
+        ~Retire() { p.retire_on(s); }
+    } retire{P, st};
+    RELNN_TRY(build_plan(P, &desc, st));
+    DevBuf bo;
+    RELNN_TRY(bo.alloc_tmp(sizeof(float) * std::max<int64_t>(P.n_out, 1) * d_out, st));
+    if (P.n_out > 0) {
+        CallIO io;
+        io.z = zb.p;
+        io.z_bf16 = S->cfg.z_dtype == RELNN_BF16;
+        io.w_bf16 = S->cfg.w_dtype == RELNN_BF16;
+        io.br.resize(1);
+        io.br[0].W = S->cfg.d_W;
+        io.br[0].b = S->cfg.d_b;
+        if (P.bf16) RELNN_TRY(forward_tc(P, io, bo.as<float>(), st));
+        else RELNN_TRY(forward_fp32(P, io, bo.as<float>(), st));
+    }
+    { ranges_kernel<<<(nq + 1 + 127) / 128, 128, 0, st>>>(P.out_keys.as<int64_t>(), P.n_out, nq, lo.as<int64_t>()); note_launch(); }
+    std::vector<int64_t> hlo(nq + 1);
+    RELNN_CUDA(cudaMemcpyAsync(hlo.data(), lo.p, sizeof(int64_t) * (nq + 1), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < nq; ++i) {
+        Query* q = batch[i];
+        q->n_out = hlo[i + 1] - hlo[i];
+        q->batch_q = nq;
+        if (q->n_out > 0) {
+            RELNN_TRY(q->keys.alloc_tmp(sizeof(int32_t) * q->n_out, st));
+            RELNN_TRY(q->z.alloc_tmp(sizeof(float) * q->n_out * d_out, st));
+            { strip_keys_kernel<<<grid_for(q->n_out), 256, 0, st>>>(P.out_keys.as<int64_t>() + hlo[i], q->n_out, q->keys.as<int32_t>()); note_launch(); }
+            RELNN_CUDA(cudaMemcpyAsync(q->z.p, bo.as<float>() + hlo[i] * d_out, sizeof(float) * q->n_out * d_out,
+                                       cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    RELNN_CUDA(cudaGetLastError());
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    int dev_status = 0;
+    RELNN_CUDA(cudaMemcpy(&dev_status, P.status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dev_status) {
+        set_device_error(dev_status);
+        return RELNN_EDEVICE;
+    }
+    return RELNN_OK;
+}
+
+void worker_main(relnn_server_s* S) {
+    cudaSetDevice(S->dev);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    while (true) {
+        std::vector<Query*> batch;
+        int64_t bmem = 0, btup = 0;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] {
+                return (S->stopping && S->queue.empty()) ||
+                       (!S->queue.empty() && S->mem_in_use + S->queue.front()->mem <= S->budget);
+            });
+            if (S->queue.empty()) break;  // stopping and drained
+            while (!S->queue.empty()) {
+                Query* q = S->queue.front();
+                if (!batch.empty() && ((int)batch.size() >= S->cfg.max_batch_queries ||
+                                       btup + q->q.n_tuples > S->cfg.max_batch_tuples))
+                    break;
+                if (S->mem_in_use + bmem + q->mem > S->budget) break;
+                S->queue.pop_front();
+                q->state = 1;
+                batch.push_back(q);
+                bmem += q->mem;
+                btup += q->q.n_tuples;
+            }
+            S->mem_in_use += bmem;
+        }
+        relnn_status s = run_batch(S, batch, st);
+        cudaStreamSynchronize(st);
+        for (Query* q : batch) {
+            // results outlive this batch; their later frees need no ordering against this stream
+            q->keys.st = nullptr;
+            q->z.st = nullptr;
+        }
+        const Clock::time_point now = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->mem_in_use -= bmem;
+            for (Query* q : batch) {
+                q->st = s;
+                q->latency_us = std::chrono::duration<double, std::micro>(now - q->t_submit).count();
+                q->state = 2;
+            }
+            S->in_system -= (int)batch.size();
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+    cudaStreamDestroy(st);
+}
+
+}  // namespace
+}  // namespace relnn
+
+extern "C" {
+
+relnn_status relnn_server_create(const relnn_server_cfg* cfg, relnn_server_t* out) {
+    RELNN_CHECK_ARG(cfg && out, "server: null argument");
+    RELNN_CHECK_ARG(cfg->d > 0 && cfg->d % 8 == 0 && cfg->d_out > 0 && cfg->d_out <= 256, "server: bad widths");
+    RELNN_CHECK_ARG(cfg->d_W, "server: null W");
+    RELNN_CHECK_ARG(cfg->n_workers >= 1 && cfg->n_workers <= 16, "server: 1..16 workers");
+    RELNN_CHECK_ARG(cfg->max_queue >= 1 && cfg->max_batch_queries >= 1 && cfg->max_batch_tuples >= 1,
+                    "server: bad queue / batch limits");
+    *out = nullptr;
+    relnn_server_s* S = new (std::nothrow) relnn_server_s();
+    if (!S) return RELNN_ENOMEM;
+    S->cfg = *cfg;
+    S->z_esz = cfg->z_dtype == RELNN_BF16 ? 2 : 4;
+    cudaGetDevice(&S->dev);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    S->budget = cfg->mem_budget_bytes > 0 ? cfg->mem_budget_bytes : (int64_t)(0.8 * (double)free_b);
+    for (int i = 0; i < cfg->n_workers; ++i) S->workers.emplace_back(worker_main, S);
+    *out = S;
+    return RELNN_OK;
+}
+
+relnn_status relnn_serve_submit(relnn_server_t S, const relnn_query* q, uint64_t* ticket) {
+    RELNN_CHECK_ARG(S && q && ticket, "submit: null argument");
+    RELNN_CHECK_ARG(q->n_h >= 0 && q->n_tuples >= 0 && q->n_h < (1ll << 31) && q->n_tuples < (1ll << 31),
+                    "submit: bad sizes");
+    RELNN_CHECK_ARG((q->n_h == 0 || (q->d_h_ids && q->d_z)) && (q->n_tuples == 0 || (q->d_src && q->d_dst)),
+                    "submit: null relation");
+    const int64_t mem = query_mem(S, *q);
+    if (mem > S->budget) {
+        set_error("submit: query needs ~" + std::to_string(mem) + " device bytes, budget is " + std::to_string(S->budget));
+        return RELNN_ENOMEM;
+    }
+    Query* Q = new (std::nothrow) Query();
+    if (!Q) return RELNN_ENOMEM;
+    Q->q = *q;
+    Q->mem = mem;
+    Q->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stopping) {
+            delete Q;
+            set_error("submit: server is stopping");
+            return RELNN_EINVAL;
+        }
+        if (S->in_system >= S->cfg.max_queue) {
+            delete Q;
+            set_error("submit: queue full");
+            return RELNN_EAGAIN;
+        }
+        Q->ticket = S->next_ticket++;
+        S->all[Q->ticket] = Q;
+        S->queue.push_back(Q);
+        ++S->in_system;
+        *ticket = Q->ticket;
+    }
+    S->cv_work.notify_one();
+    return RELNN_OK;
+}
+
+relnn_status relnn_serve_poll(relnn_server_t S, uint64_t ticket, relnn_result* res, uint32_t timeout_us) {
+    RELNN_CHECK_ARG(S && res, "poll: null argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    RELNN_CHECK_ARG(it != S->all.end(), "poll: unknown ticket");
+    Query* Q = it->second;
+    if (Q->state != 2) {
+        if (timeout_us == 0) return RELNN_EAGAIN;
+        const bool done = S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return Q->state == 2; });
+        if (!done) return RELNN_ETIMEDOUT;
+    }
+    res->n_out = Q->n_out;
+    res->d_out_keys = Q->keys.as<int32_t>();
+    res->d_out_z = Q->z.as<float>();
+    res->latency_us = Q->latency_us;
+    res->batch_queries = Q->batch_q;
+    if (Q->st != RELNN_OK) set_error("poll: the query's batch failed");
+    return Q->st;
+}
+
+relnn_status relnn_serve_release(relnn_server_t S, uint64_t ticket) {
+    RELNN_CHECK_ARG(S, "release: null server");
+    Query* Q = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->all.find(ticket);
+        RELNN_CHECK_ARG(it != S->all.end(), "release: unknown ticket");
+        RELNN_CHECK_ARG(it->second->state == 2, "release: query still running");
+        Q = it->second;
+        S->all.erase(it);
+    }
+    delete Q;
+    return RELNN_OK;
+}
+
+relnn_status relnn_server_destroy(relnn_server_t S) {
+    if (!S) return RELNN_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+    }
+    S->cv_work.notify_all();
+    for (auto& t : S->workers) t.join();
+    cudaDeviceSynchronize();
+    for (auto& kv : S->all) delete kv.second;
+    delete S;
+    return RELNN_OK;
+}
+
+}  // extern "C"

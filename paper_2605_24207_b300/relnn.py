@@ -25,6 +25,7 @@ FLAG_IDENTITY = 0x4
 FLAG_NO_JOIN_DST = 0x8
 FLAG_NO_CONCAT_DST = 0x10
 FLAG_RELU_MASK = 0x20
+FLAG_TILE128 = 0x40
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOSPC", 4: "EAGAIN", 5: "ETIMEDOUT", 6: "ECUDA",
           7: "EDEVICE", 8: "ENOTSUP"}
@@ -307,3 +308,104 @@ class RelnnRule(torch.autograd.Function):
                                            [b] if b is not None else None, [r] if r is not None else None,
                                            need_dz=ctx.needs_input_grad[1])
         return (None, dz, dW[0] if dW else None, db[0] if db else None, dr[0] if dr else None)
+
+
+# ------------------------------------------------------------------------------------------ serving
+class ServerCfg(C.Structure):
+    _fields_ = [("d", C.c_int32), ("d_out", C.c_int32), ("d_W", C.c_void_p), ("w_dtype", C.c_int),
+                ("d_b", C.c_void_p), ("act", C.c_int), ("flags", C.c_uint32), ("z_dtype", C.c_int),
+                ("max_queue", C.c_int32), ("mem_budget_bytes", C.c_int64), ("max_batch_tuples", C.c_int64),
+                ("max_batch_queries", C.c_int32), ("tile128_below", C.c_int64), ("n_workers", C.c_int32)]
+
+
+class Query(C.Structure):
+    _fields_ = [("d_h_ids", C.c_void_p), ("n_h", C.c_int64), ("d_z", C.c_void_p), ("d_src", C.c_void_p),
+                ("d_dst", C.c_void_p), ("n_tuples", C.c_int64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("n_out", C.c_int64), ("d_out_keys", C.c_void_p), ("d_out_z", C.c_void_p),
+                ("latency_us", C.c_double), ("batch_queries", C.c_int32)]
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_types", False):
+        vp = C.c_void_p
+        L.relnn_server_create.argtypes = [C.POINTER(ServerCfg), C.POINTER(vp)]
+        L.relnn_serve_submit.argtypes = [vp, C.POINTER(Query), C.POINTER(C.c_uint64)]
+        L.relnn_serve_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result), C.c_uint32]
+        L.relnn_serve_release.argtypes = [vp, C.c_uint64]
+        L.relnn_server_destroy.argtypes = [vp]
+        for n in ("relnn_server_create", "relnn_serve_submit", "relnn_serve_poll", "relnn_serve_release",
+                  "relnn_server_destroy"):
+            getattr(L, n).restype = C.c_int
+        L._server_types = True
+    return L
+
+
+class Server:
+    """relnn_server_*: memory-admitted continuous batching of rule queries sharing one Linear.
+    Query tensors (int32 keys, z) must stay alive until their ticket completes."""
+
+    def __init__(self, W, b, d: int, act: int = ACT_NONE, flags: int = FLAG_BF16, z_dtype=torch.bfloat16,
+                 max_queue: int = 256, mem_budget_bytes: int = 0, max_batch_tuples: int = 4_000_000,
+                 max_batch_queries: int = 64, tile128_below: int = 0, n_workers: int = 4):
+        self.L = _server_lib()
+        self.W, self.b = W, b  # keep alive
+        self.d_out = W.shape[0]
+        cfg = ServerCfg(d, W.shape[0], _ptr(W), _float_type(W), _ptr(b), act, flags,
+                        BF16 if z_dtype == torch.bfloat16 else F32, max_queue, mem_budget_bytes, max_batch_tuples,
+                        max_batch_queries, tile128_below, n_workers)
+        self._h = C.c_void_p()
+        _check(self.L.relnn_server_create(C.byref(cfg), C.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, h_ids, z, src, dst) -> int:
+        """Ticket, or raises RelnnError (EAGAIN when the queue is full, ENOMEM if it can never fit)."""
+        q = Query(_ptr(h_ids), h_ids.numel(), _ptr(z), _ptr(src), _ptr(dst), src.numel())
+        t = C.c_uint64()
+        _check(self.L.relnn_serve_submit(self._h, C.byref(q), C.byref(t)))
+        self._keep[t.value] = (h_ids, z, src, dst)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """None while pending; else (keys int32 [n], out f32 [n, d_out], latency_us, batch size) as
+        views of the server's buffers (copy them before release)."""
+        r = Result()
+        st = self.L.relnn_serve_poll(self._h, ticket, C.byref(r), timeout_us)
+        if st in (4, 5):  # EAGAIN / ETIMEDOUT
+            return None
+        _check(st)
+        n = r.n_out
+        if n == 0:
+            keys = torch.zeros(0, dtype=torch.int32, device="cuda")
+            out = torch.zeros((0, self.d_out), dtype=torch.float32, device="cuda")
+        else:
+            keys = _wrap_device(r.d_out_keys, (n,), torch.int32)
+            out = _wrap_device(r.d_out_z, (n, self.d_out), torch.float32)
+        return keys, out, r.latency_us, r.batch_queries
+
+    def release(self, ticket: int):
+        _check(self.L.relnn_serve_release(self._h, ticket))
+        self._keep.pop(ticket, None)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.L.relnn_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()
+
+
+def _wrap_device(ptr: int, shape, dtype):
+    """A torch view of library-owned device memory (no copy, no ownership)."""
+    class _Cai:
+        pass
+    o = _Cai()
+    typestr = {torch.int32: "<i4", torch.float32: "<f4"}[dtype]
+    o.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                  "version": 3, "strides": None, "stream": None}
+    return torch.as_tensor(o, device="cuda")
