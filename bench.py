@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="relnn", choices=["relnn", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4"])
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"])
+    ap.add_argument("--n-queries", type=int, default=10_000, help="c5: queries in the serving trace")
+    ap.add_argument("--cmp-queries", type=int, default=2_000, help="c5: queries for the torch comparator")
     ap.add_argument("--n-tuples", type=int, default=None, help="override the tuple count (c2, c3)")
     ap.add_argument("--n-keys", type=int, default=None, help="override the key count (c2, c3)")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="tuples in the CPU-oracle sample")
@@ -451,6 +453,143 @@ class C4:
 WORKLOADS = {"c2": C2, "c3": C3, "c4": C4}
 
 
+# ===================================================================================== serving
+def _torch_query(h, z, src, dst, Wt, bt):
+    """Plain unfused FP32 form of one query (the serving comparator)."""
+    import torch
+    import torch.nn.functional as F
+    order = torch.argsort(h)
+    sk = h[order]
+    ps = torch.searchsorted(sk, src).clamp_(max=sk.numel() - 1)
+    pd = torch.searchsorted(sk, dst).clamp_(max=sk.numel() - 1)
+    keep = (sk[ps] == src) & (sk[pd] == dst)
+    zf = z.float()
+    X = torch.cat([zf.index_select(0, order[ps[keep]]), zf.index_select(0, order[pd[keep]])], dim=1)
+    Y = F.linear(X, Wt, bt)
+    uk, inv = torch.unique(dst[keep], return_inverse=True)
+    return uk, torch.zeros((uk.numel(), Y.shape[1]), device=Y.device).index_add_(0, inv, Y)
+
+
+def run_serving(args):
+    """--config c5: a stream of rule queries (T ~ logU[1k, 1M], K = T/8, z bf16[64], shared Linear
+    128 -> 64) arriving as a Poisson process at 2,000 queries/s, served by relnn_server_* with
+    memory-admitted continuous batching; latency = arrival -> results ready."""
+    import threading
+
+    import torch
+    from paper_2605_24207_b300 import autotune
+    from paper_2605_24207_b300 import relnn as R
+    from paper_2605_24207_b300 import workloads as W
+
+    torch.backends.cuda.matmul.allow_tf32 = False
+    nq = args.n_queries
+    arrivals, sizes = W.serving_trace(0, nq, 2000.0)
+    grid = np.unique(np.round(np.exp(np.linspace(np.log(1000), np.log(1_000_000), 24))).astype(np.int64))
+    qsize = grid[np.argmin(np.abs(np.log(grid)[None, :] - np.log(sizes)[:, None]), axis=1)]
+    pool = {}
+    for g in grid.tolist():
+        keys, src, dst, z = W.serving_query(0, g, g, 64)
+        pool[g] = (torch.from_numpy(keys).cuda(), torch.from_numpy(z).cuda().to(torch.bfloat16),
+                   torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
+    rng = np.random.default_rng(7)
+    Wt = torch.from_numpy((rng.standard_normal((64, 128)) / np.sqrt(128)).astype(np.float32)).cuda()
+    bt = torch.from_numpy((rng.standard_normal(64) / np.sqrt(128)).astype(np.float32)).cuda()
+    thr = autotune.tune_tile128_below(64, 64)
+    tuples = int(qsize.sum())
+
+    def serve(paced: bool, n: int):
+        srv = R.Server(Wt, bt, 64, flags=R.FLAG_BF16, max_queue=4096, max_batch_tuples=2_000_000,
+                       max_batch_queries=64, tile128_below=thr, n_workers=4)
+        for g in grid[:4].tolist():  # warm-up
+            t = srv.submit(*pool[g])
+            while srv.poll(t, 100_000) is None:
+                pass
+            srv.release(t)
+        tickets, t_sub = [None] * n, [0.0] * n
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i in range(n):
+                if paced:
+                    wait = t0 + arrivals[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                while True:
+                    try:
+                        tickets[i] = srv.submit(*pool[int(qsize[i])])
+                        t_sub[i] = time.perf_counter()
+                        break
+                    except R.RelnnError as e:
+                        if e.status != 4:
+                            raise
+                        time.sleep(50e-6)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, batch_q = [], []
+        for i in range(n):
+            while tickets[i] is None:
+                time.sleep(20e-6)
+            r = None
+            while r is None:
+                r = srv.poll(tickets[i], 200_000)
+            arr = (t0 + arrivals[i]) if paced else t0
+            lat.append((t_sub[i] - arr) * 1e3 + r[2] * 1e-3)
+            batch_q.append(r[3])
+            srv.release(tickets[i])
+        th.join()
+        wall = time.perf_counter() - t0
+        srv.close()
+        return np.array(lat), wall, float(np.mean(batch_q))
+
+    lat, wall, mean_batch = serve(True, nq)
+    lat_s, wall_s, _ = serve(False, nq)
+
+    # comparator: the unfused FP32 form, one query at a time in arrival order, same trace prefix
+    n_cmp = min(nq, args.cmp_queries)
+    for g in grid[:3].tolist():
+        _torch_query(*pool[g], Wt, bt)
+    torch.cuda.synchronize()
+    lat_t = []
+    t0 = time.perf_counter()
+    for i in range(n_cmp):
+        wait = t0 + arrivals[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        h, z, s, d = pool[int(qsize[i])]
+        _torch_query(h, z, s, d, Wt, bt)
+        torch.cuda.synchronize()
+        lat_t.append((time.perf_counter() - (t0 + arrivals[i])) * 1e3)
+    lat_t = np.array(lat_t)
+
+    # CPU oracle on one query of median size
+    from oracle import relnn_oracle as O
+    gm = int(np.median(qsize))
+    keys, src, dst, z = W.serving_query(0, gm, gm, 64)
+    t1 = time.perf_counter()
+    _, _, sz = O.rule_forward(keys, _bf16(z), [_Br(src, dst, _bf16(Wt.cpu().numpy()), bt.cpu().numpy())])
+    cpu_rate = sz[0] / (time.perf_counter() - t1)
+
+    pct = lambda a, q: float(np.percentile(a, q))
+    line = {"metric": METRIC, "value": tuples / wall_s, "unit": UNIT, "n_gpus": 1, "steps": nq, "warmup": 4,
+            "ms_per_step": 1e3 * wall_s / nq, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic (seeded serving trace; no dataset)",
+            "config": {"workload": f"serving stream of {nq} rule queries, T ~ logU[1k,1M] (24 size classes), "
+                                   f"K = T/8, int32 keys, z bf16[64], shared Linear 128->64, Poisson arrivals "
+                                   f"2000/s; value = saturation tuples/s", "tile128_below": thr},
+            "serving": {"paced_p50_ms": pct(lat, 50), "paced_p99_ms": pct(lat, 99),
+                        "paced_queries_per_s": nq / wall, "mean_queries_per_batch": mean_batch,
+                        "saturation_queries_per_s": nq / wall_s, "saturation_tuples_per_s": tuples / wall_s,
+                        "saturation_p50_ms": pct(lat_s, 50), "saturation_p99_ms": pct(lat_s, 99),
+                        "first_n_paced_p50_ms": pct(lat[:n_cmp], 50), "first_n_paced_p99_ms": pct(lat[:n_cmp], 99),
+                        "torch_fp32_unfused_first_n_p50_ms": pct(lat_t, 50),
+                        "torch_fp32_unfused_first_n_p99_ms": pct(lat_t, 99), "first_n": n_cmp},
+            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores(), "kind": "oracle",
+                             "sample": f"one query of {gm} tuples"},
+            "roofline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 # ===================================================================================== arms
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands on the host cores (rank 0 only)."""
@@ -602,6 +741,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "c5":
+        run_serving(args)
     else:
         run_relnn(args)
 
