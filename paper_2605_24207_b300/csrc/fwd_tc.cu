@@ -7,12 +7,12 @@
 // epilogue thread that owns feature o reads its tuples in output-key order and the SUM over a run of
 // equal output rows is a walk in registers; each emitted row is a 128-byte coalesced store per warp.
 //
-// Roles (288 threads, one CTA per SM):
-//   warps 0-3  producers: gather rows z[hs], z[hd], r[er] for one 64-column K block of a tile into
+// Roles (416 threads, one CTA per SM):
+//   warps 0-7  producers: gather rows z[hs], z[hd], r[er] for one 64-column K block of a tile into
 //              a 128B-swizzled stage (cp.async for bf16 sources, convert-and-store for f32 sources)
-//   warp 4     TMEM allocation; lane 0 issues tcgen05.mma (A = W block staged once by TMA,
+//   warp 8     TMEM allocation; lane 0 issues tcgen05.mma (A = W block staged once by TMA,
 //              B = the gathered stage) and tcgen05.commit
-//   warps 5-8  epilogue: tcgen05.ld of the accumulator (double-buffered in TMEM so the next tile's
+//   warps 9-12 epilogue: tcgen05.ld of the accumulator (double-buffered in TMEM so the next tile's
 //              MMAs overlap), bias, ReLU, SUM walk, stores / tile-boundary partials.
 #include "fwd.cuh"
 #include "tc.cuh"
@@ -26,9 +26,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 288;
-constexpr int kProducerThreads = 128;
-constexpr int kMmaWarp = 4;  // warps 5..8 are the epilogue
+constexpr int kThreads = 416;
+constexpr int kProducerThreads = 256;
+constexpr int kMmaWarp = 8;  // warps 0-7 produce, 9-12 are the epilogue
 constexpr int kMaxKb = 12;
 constexpr int kMaxLag = 6;  // cp.async groups a producer thread may keep in flight before arriving
 constexpr int kSmemLimit = 227 * 1024;
@@ -145,15 +145,15 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
     const uint32_t tmem_base = *tmem_slot;
     const uint32_t acc_stride = (uint32_t)a.m_blocks * a.tile_n;
 
-    if (warp < 4) {
+    if (warp < kProducerThreads / 32) {
         // ------------------------------------------------------------------ producers
         // Thread (row group rg, 16-byte chunk) copies chunk `chunk` of rows [rg*rpt, rg*rpt + rpt) of
         // every K block; the 8 threads of a row group read one 128-byte row segment together.
         const int chunk = tid & 7;
-        const int rpt = a.tile_n >> 4;
+        const int rpt = a.tile_n / (kProducerThreads / 8);
         const int row_base = (tid >> 3) * rpt;
         const int32_t* arrs[3] = {a.hs, a.hd, a.er};
-        const int per_thr = a.tile_n / kProducerThreads;  // index entries each thread stages per array
+        const int per_thr = (a.tile_n + kProducerThreads - 1) / kProducerThreads;  // index entries per thread per array
         // stage the first tile's row indices
         {
             const int64_t t0 = (int64_t)blockIdx.x * a.tile_n;
@@ -161,7 +161,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 if (!a.need_arr[r]) continue;
                 for (int k = 0; k < per_thr; ++k) {
                     const int qq = tid + k * kProducerThreads;
-                    idx_smem[r * a.tile_n + qq] = (t0 + qq < a.m) ? __ldg(arrs[r] + t0 + qq) : 0;
+                    if (qq < a.tile_n) idx_smem[r * a.tile_n + qq] = (t0 + qq < a.m) ? __ldg(arrs[r] + t0 + qq) : 0;
                 }
             }
         }
@@ -182,7 +182,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const int qq = tid + k * kProducerThreads;
-                    pre[r][k] = (a.need_arr[r] && k < per_thr && tn + qq < a.m) ? __ldg(arrs[r] + tn + qq) : 0;
+                    pre[r][k] = (a.need_arr[r] && k < per_thr && qq < a.tile_n && tn + qq < a.m) ? __ldg(arrs[r] + tn + qq) : 0;
                 }
             for (int kb = 0; kb < a.n_kb; ++kb) {
                 if (!ok) break;
@@ -238,7 +238,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
             for (int r = 0; r < 3; ++r)
 #pragma unroll
                 for (int k = 0; k < 2; ++k)
-                    if (k < per_thr) oslot[r * a.tile_n + tid + k * kProducerThreads] = pre[r][k];
+                    if (k < per_thr && tid + k * kProducerThreads < a.tile_n) oslot[r * a.tile_n + tid + k * kProducerThreads] = pre[r][k];
             named_bar_sync(1, kProducerThreads);
         }
         cp_async_wait<0>();
