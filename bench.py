@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="relnn", choices=["relnn", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"])
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "c1b"])
+    ap.add_argument("--instances", type=int, default=4096, help="c1b: independent small-rule instances")
     ap.add_argument("--n-queries", type=int, default=10_000, help="c5: queries in the serving trace")
     ap.add_argument("--cmp-queries", type=int, default=2_000, help="c5: queries for the torch comparator")
     ap.add_argument("--n-tuples", type=int, default=None, help="override the tuple count (c2, c3)")
@@ -450,7 +451,94 @@ class C4:
         return sum(sizes) / dt, f"first {n_sample // 6} E rows of each branch with the full H ({sum(sizes)} tuples, {dt:.1f} s)"
 
 
-WORKLOADS = {"c2": C2, "c3": C3, "c4": C4}
+class C1B:
+    """4,096 independent instances of the small FP32 rule (E 2,000 tuples over 500 int32 keys, z f32[16],
+    Linear 32 -> 16) evaluated together: instance i's keys are offset by i * 1024 so the key spaces are
+    disjoint, and one plan + one FP32-form fused launch covers all of them (one shared Linear)."""
+    name = "c1b"
+
+    def __init__(self, args):
+        from paper_2605_24207_b300 import workloads as W
+        self.B = args.instances
+        hs, zs, ss, ds = [], [], [], []
+        for i in range(self.B):
+            r = W.config1(seed=i)
+            br = r.branches[0]
+            off = np.int32(i * 1024)
+            hs.append(r.h_ids + off)
+            zs.append(r.z)
+            ss.append(br.src + off)
+            ds.append(br.dst + off)
+            if i == 0:
+                self.Wn, self.bn = br.W, br.b
+        self.h, self.z = np.concatenate(hs), np.concatenate(zs)
+        self.src, self.dst = np.concatenate(ss), np.concatenate(ds)
+
+    def describe(self):
+        return (f"{self.B} independent instances of the FP32 rule (E 2,000 tuples over 500 int32 keys, z f32[16], "
+                f"Linear 32->16 shared) in one plan + one FP32-form launch; step = plan + forward")
+
+    def to_device(self, dev):
+        import torch
+        from paper_2605_24207_b300 import relnn as R
+        self.t = dict(h=torch.from_numpy(self.h).to(dev), z=torch.from_numpy(self.z).to(dev),
+                      src=torch.from_numpy(self.src).to(dev), dst=torch.from_numpy(self.dst).to(dev),
+                      W=torch.from_numpy(self.Wn).to(dev), b=torch.from_numpy(self.bn).to(dev))
+        p = R.RulePlan(self.t["h"], [(self.t["src"], self.t["dst"])], 16, 16)
+        self.matched, self.n_out = p.n_matched, p.n_out
+        self.out = torch.empty((self.n_out, 16), dtype=torch.float32, device=dev)
+
+    def step(self):
+        from paper_2605_24207_b300 import relnn as R
+        t = self.t
+        p = R.RulePlan(t["h"], [(t["src"], t["dst"])], 16, 16)
+        p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
+        return p
+
+    def roofline_kernel(self):
+        from paper_2605_24207_b300 import relnn as R
+        return R.PROF_FWD_FP32, "fwd_fp32_kernel", 2.0 * 32 * 16 * self.matched
+
+    def roofline_peak(self):
+        # f32 FMA on CUDA cores: 148 SMs x 128 lanes x 2 FLOP x 2.032 GHz (no measured figure exists)
+        return "alu", 148 * 128 * 2 * 2.032e9 / 1e12, "derived f32 CUDA-core peak (148 SM x 128 FMA/clk x 2.032 GHz)"
+
+    def e2e_setup(self):
+        import torch
+        self.hp = {k: v.cpu().pin_memory() for k, v in self.t.items()}
+        self.dv = {k: torch.empty_like(v) for k, v in self.t.items()}
+        self.out_host = torch.empty((self.n_out, 16), dtype=torch.float32).pin_memory()
+        return sum(v.numel() * v.element_size() for v in self.hp.values()), self.out_host.numel() * 4
+
+    def e2e_step(self):
+        from paper_2605_24207_b300 import relnn as R
+        for k in self.hp:
+            self.dv[k].copy_(self.hp[k], non_blocking=True)
+        dv = self.dv
+        p = R.RulePlan(dv["h"], [(dv["src"], dv["dst"])], 16, 16)
+        o = p.forward(dv["z"], [dv["W"]], [dv["b"]], out=self.out)
+        self.out_host.copy_(o, non_blocking=True)
+        return p
+
+    def extras(self, timer, steps):
+        return {}
+
+    def cpu_rate(self, n_sample):
+        from oracle import relnn_oracle as O
+        from paper_2605_24207_b300 import workloads as W
+        n_inst = max(1, min(self.B, n_sample // 2000))
+        t0 = time.perf_counter()
+        tot = 0
+        for i in range(n_inst):
+            r = W.config1(seed=i)
+            br = r.branches[0]
+            _, _, sz = O.rule_forward(r.h_ids, r.z, [_Br(br.src, br.dst, self.Wn, self.bn)])
+            tot += sz[0]
+        dt = time.perf_counter() - t0
+        return tot / dt, f"{n_inst} of the {self.B} instances ({tot} tuples, {dt:.1f} s)"
+
+
+WORKLOADS = {"c2": C2, "c3": C3, "c4": C4, "c1b": C1B}
 
 
 # ===================================================================================== serving
@@ -591,6 +679,26 @@ def run_serving(args):
 
 
 # ===================================================================================== arms
+def reduce_max(x: float, device) -> float:
+    """Maximum of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(step_ms_local: float, units_local: int, device):
+    """Whole-job throughput of replicas: every rank processed `units_local` per step; the job's step
+    time is the slowest rank's. Returns (units per second over all ranks, job step ms)."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    t = reduce_max(step_ms_local, device)
+    return world * units_local / (t * 1e-3), t
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands on the host cores (rank 0 only)."""
     if int(os.environ.get("RANK", "0")) != 0:
@@ -635,11 +743,7 @@ def run_relnn(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        tt = torch.tensor([x], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+        return reduce_max(x, dev)
 
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -680,8 +784,7 @@ def run_relnn(args):
     gpu_launches = R.launch_count() - n_launch0
     R.profile_enable(False)
     clocks = clk.stop()
-    t_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-    value = world * wl.matched / (t_step * 1e-3)
+    value, t_step = job_throughput(e0.elapsed_time(e1) / args.steps, wl.matched, dev)
     kid, kname, flops = wl.roofline_kernel()
     k_ms, k_n = R.profile_read(kid)
     plan_ms, plan_n = R.profile_read(R.PROF_PLAN)
@@ -690,11 +793,12 @@ def run_relnn(args):
     pk, pk_src = peaks()
     k_avg = k_ms / max(k_n, 1)
     achieved = flops / (k_avg * 1e-3) / 1e12
-    peak = pk["bf16_tflops_sustained"]
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    bound, peak, peak_src = "tensor", pk["bf16_tflops_sustained"], f"{pk_src} bf16 sustained"
+    if hasattr(wl, "roofline_peak"):
+        bound, peak, peak_src = wl.roofline_peak()
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": NCU_TRAFFIC_PER_LAUNCH if wl.name == "c2" else None, "kernel": kname,
-                "kernel_ms": k_avg, "kernel_launches_per_step": k_n / args.steps,
-                "peak_source": f"{pk_src} bf16 sustained"}
+                "kernel_ms": k_avg, "kernel_launches_per_step": k_n / args.steps, "peak_source": peak_src}
 
     extras = {} if args.no_extras else wl.extras(timer, args.steps)
     extras["plan_ms"] = plan_ms / plan_n if plan_n else None

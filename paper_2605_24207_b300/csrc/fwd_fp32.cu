@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(Fp32Args a) {
 __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int tile, int64_t n_tiles,
                              const float* __restrict__ carry, float* __restrict__ out, int d_out,
                              int accumulate, int kahan) {
+    __shared__ int64_t last_tile;
     for (int64_t b = blockIdx.x + 1; b < n_tiles; b += gridDim.x) {
         const int64_t row = b * tile;
         if (row >= m) continue;
@@ -121,21 +122,30 @@ __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int til
         if (seg[row - 1] != s) continue;                         // boundary b cuts no segment
         if (b >= 2 && seg[(b - 1) * tile - 1] == s) continue;    // not the first boundary of s
         const int first_slot = (seg[(b - 1) * tile] == s) ? 0 : 1;
+        // last row of s (seg is non-decreasing): its tile is the last one whose first row is in s
+        if (threadIdx.x == 0) {
+            int64_t lo = row, hi = m;  // first row with seg > s lies in (row, m]
+            while (lo + 1 < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (seg[mid] == s) lo = mid;
+                else hi = mid;
+            }
+            last_tile = lo / tile;
+        }
+        __syncthreads();
+        const int64_t e = last_tile;
         for (int o = threadIdx.x; o < d_out; o += blockDim.x) {
             float acc = carry[((b - 1) * 2 + first_slot) * d_out + o];
             float comp = 0.f;
-            int64_t j = b;
-            while (true) {
+            for (int64_t j = b; j <= e; ++j) {  // tiles b..e all start inside s: their slot 0 piece
                 const float v = carry[(j * 2) * d_out + o];
                 if (kahan) kahan_add(acc, comp, v);
                 else acc += v;
-                const int64_t nb = (j + 1) * tile;
-                if (j + 1 < n_tiles && nb < m && seg[nb - 1] == s && seg[nb] == s) ++j;
-                else break;
             }
             float* dst = out + (int64_t)s * d_out + o;
             emit_out(dst, acc, accumulate);
         }
+        __syncthreads();
     }
 }
 
