@@ -11,13 +11,14 @@
 // per run of equal dst row (a segmented sum in registers) for the dst slice. D1 accumulates over all
 // tiles of the CTA; each CTA writes its partial dW and a reduction kernel adds them in CTA order.
 //
-// Roles (288 threads, one CTA per SM): warps 0-3 producers (dY: dOut rows -> mask -> bf16; X: rows
-// of z / r as in the forward; db partial sums), warp 4 TMEM allocation + MMA issue, warps 5-8
-// epilogue.
+// Roles (416 threads, one CTA per SM): warps 0-7 producers (dY: dOut rows -> mask -> bf16; X: rows
+// of z / r as in the forward; db partial sums), warp 8 TMEM allocation + MMA issue, warps 9-12
+// epilogue. 13 warps leave at most 128 registers per thread (four warps share one SM sub-partition).
 #include <algorithm>
 #include <mutex>
 
 #include "bwd.cuh"
+#include "segscan.cuh"
 #include "tc.cuh"
 
 namespace relnn {
@@ -26,9 +27,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 288;
-constexpr int kProducerThreads = 128;
-constexpr int kMmaWarp = 4;
+constexpr int kThreads = 416;
+constexpr int kProducerThreads = 256;
+constexpr int kMmaWarp = 8;
 constexpr int kMaxKb = 4;  // input-feature K blocks (d_in <= 256)
 constexpr int kSmemLimit = 227 * 1024;
 
@@ -101,23 +102,27 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
     const uint32_t tmem_base = *tmem_slot;
     const uint32_t d2_stride = (uint32_t)a.mbk * N;
 
-    if (warp < 4) {
+    if (warp < kProducerThreads / 32) {
         // ------------------------------------------------------------------ producers
+        // thread = (row group of rpt consecutive rows, 16-byte chunk); the tile's hs / hd / er / seg
+        // entries (4N) are staged in shared memory one tile ahead, at most 2 per thread
         const int chunk = tid & 7;
-        const int rpt = N >> 4;
+        const int rpt = N / (kProducerThreads / 8);
         const int row_base = (tid >> 3) * rpt;
-        const int32_t* arrs[4] = {a.hs, a.hd, a.er, a.seg};
-        const int per_thr = N / kProducerThreads;  // 0 when N = 64: threads below N load one entry
-        auto stage_idx = [&](int64_t tile, int32_t* slot) {
-            const int64_t t0 = tile * N;
-            for (int r = 0; r < 4; ++r) {
-                if (r < 3 && !a.need_arr[r]) continue;
-                for (int qq = tid; qq < N; qq += kProducerThreads)
-                    slot[r * N + qq] = (tile < a.n_tiles && t0 + qq < a.m) ? __ldg(arrs[r] + t0 + qq) : 0;
-            }
+        auto idx_load = [&](int64_t tile, int k) -> int32_t {
+            const int e = tid + k * kProducerThreads;
+            const int r = e / N, qq = e - r * N;
+            const int64_t t = tile * N + qq;
+            if (e >= 4 * N || (r < 3 && !a.need_arr[r]) || tile >= a.n_tiles || t >= a.m) return 0;
+            const int32_t* arr = r == 0 ? a.hs : (r == 1 ? a.hd : (r == 2 ? a.er : a.seg));
+            return __ldg(arr + t);
         };
-        (void)per_thr;
-        stage_idx(blockIdx.x, idx_smem);
+        auto idx_store = [&](int32_t* slot, int k, int32_t v) {
+            const int e = tid + k * kProducerThreads;
+            if (e < 4 * N) slot[e] = v;
+        };
+        idx_store(idx_smem, 0, idx_load(blockIdx.x, 0));
+        idx_store(idx_smem, 1, idx_load(blockIdx.x, 1));
         named_bar_sync(1, kProducerThreads);
         float dbacc[2][8];
 #pragma unroll
@@ -129,6 +134,8 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int64_t t0 = tile * N;
             const int32_t* islot = idx_smem + (lt & 1) * 4 * N;
+            // the next tile's indices, stored after this tile's copies are issued
+            const int32_t nxt0 = idx_load(tile + gridDim.x, 0), nxt1 = idx_load(tile + gridDim.x, 1);
             if (ok) {
                 const int s = it % a.stages;
                 const uint32_t ph = (uint32_t)((it / a.stages) & 1);
@@ -137,34 +144,47 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                     uint8_t* stg = st_smem + (size_t)s * stage_bytes;
                     const uint32_t dyb = smem_u32(stg);
                     const uint32_t xb = smem_u32(stg + dy_bytes);
-                    // dY rows: dOut[seg_t] masked by the stored ReLU mask, as bf16; 2 blocks of 64 outputs
-                    for (int j = 0; j < rpt; ++j) {
-                        const int row = row_base + j;
-                        const bool tv = t0 + row < a.m;
-                        const int sg = islot[3 * N + row];
+                    // dY rows: dOut[seg_t] masked by the stored ReLU mask, as bf16; 2 blocks of 64 outputs.
+                    // All loads of this thread's rows are issued before any is used.
 #pragma unroll
-                        for (int ob = 0; ob < 2; ++ob) {
-                            const int o0 = ob * 64 + chunk * 8;
-                            float v[8];
+                    for (int j0 = 0; j0 < 4; j0 += 2) {
+                        if (j0 >= rpt) break;
+                        float4 u[2][2][2];
+                        uint32_t bits[2][2];
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) v[k] = 0.f;
-                            if (tv && o0 < a.d_out) {
+                        for (int jj = 0; jj < 2; ++jj) {
+                            const int row = row_base + j0 + jj;
+                            const bool tv = (j0 + jj < rpt) && (t0 + row < a.m);
+                            const int sg = tv ? islot[3 * N + row] : 0;
+#pragma unroll
+                            for (int ob = 0; ob < 2; ++ob) {
+                                const int o0 = ob * 64 + chunk * 8;
+                                const bool ld = tv && o0 < a.d_out;
                                 const float4* q = reinterpret_cast<const float4*>(a.dout + (int64_t)sg * a.d_out + o0);
-                                const float4 u = __ldg(q), w = __ldg(q + 1);
-                                v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
-                                v[4] = w.x; v[5] = w.y; v[6] = w.z; v[7] = w.w;
-                                if (a.mask) {
-                                    const uint32_t bits = a.mask[(t0 + row) * a.mask_words + (o0 >> 5)] >> (o0 & 31);
-#pragma unroll
-                                    for (int k = 0; k < 8; ++k) v[k] = ((bits >> k) & 1u) ? v[k] : 0.f;
-                                }
+                                u[jj][ob][0] = ld ? __ldg(q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                                u[jj][ob][1] = ld ? __ldg(q + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                                bits[jj][ob] = (ld && a.mask) ? __ldg(a.mask + (t0 + row) * a.mask_words + (o0 >> 5)) >> (o0 & 31)
+                                                              : 0xffffffffu;
                             }
+                        }
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) dbacc[ob][k] += v[k];
-                            const uint32_t dst = dyb + (uint32_t)ob * N * 128u + (uint32_t)row * 128u +
-                                                 ((uint32_t)(chunk ^ (row & 7)) << 4);
-                            st_shared_v4(dst, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                                         pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+                        for (int jj = 0; jj < 2; ++jj) {
+                            if (j0 + jj >= rpt) break;
+                            const int row = row_base + j0 + jj;
+#pragma unroll
+                            for (int ob = 0; ob < 2; ++ob) {
+                                float v[8] = {u[jj][ob][0].x, u[jj][ob][0].y, u[jj][ob][0].z, u[jj][ob][0].w,
+                                              u[jj][ob][1].x, u[jj][ob][1].y, u[jj][ob][1].z, u[jj][ob][1].w};
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) {
+                                    v[k] = ((bits[jj][ob] >> k) & 1u) ? v[k] : 0.f;
+                                    dbacc[ob][k] += v[k];
+                                }
+                                const uint32_t dst = dyb + (uint32_t)ob * N * 128u + (uint32_t)row * 128u +
+                                                     ((uint32_t)(chunk ^ (row & 7)) << 4);
+                                st_shared_v4(dst, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                             pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+                            }
                         }
                     }
                     // X rows, K-block by K-block (as in the forward)
@@ -177,24 +197,35 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                         const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
                         const int row_elems = src == 2 ? a.d_r : a.d;
                         const uint32_t kbase = xb + (uint32_t)kb * N * 128u;
-                        for (int j = 0; j < rpt; ++j) {
-                            const int row = row_base + j;
-                            const uint32_t dst = kbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
-                            const bool valid = (t0 + row < a.m) && in_part;
-                            const int64_t ridx = rows_idx[row];
-                            if (tbl_bf16) {
-                                const uint16_t* p = reinterpret_cast<const uint16_t*>(tbl);
+                        if (tbl_bf16) {
+                            const uint16_t* p = reinterpret_cast<const uint16_t*>(tbl);
+                            for (int j = 0; j < rpt; ++j) {
+                                const int row = row_base + j;
+                                const uint32_t dst = kbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
+                                const bool valid = (t0 + row < a.m) && in_part;
+                                const int64_t ridx = rows_idx[row];
                                 cp_async_16(dst, valid ? p + ridx * row_elems + col : p, valid ? 16u : 0u);
-                            } else {
-                                float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
-                                if (valid) {
-                                    const float4* q = reinterpret_cast<const float4*>(
-                                        reinterpret_cast<const float*>(tbl) + ridx * row_elems + col);
-                                    u = __ldg(q);
-                                    w = __ldg(q + 1);
-                                }
-                                st_shared_v4(dst, pack_bf16x2(u.x, u.y), pack_bf16x2(u.z, u.w), pack_bf16x2(w.x, w.y),
-                                             pack_bf16x2(w.z, w.w));
+                            }
+                        } else {
+                            // f32 rows: all (up to 4) rows' loads in flight before the convert-and-store
+                            float4 u[4], w[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int row = row_base + j;
+                                const bool valid = j < rpt && (t0 + row < a.m) && in_part;
+                                const int64_t ridx = valid ? rows_idx[row] : 0;
+                                const float4* q = reinterpret_cast<const float4*>(
+                                    reinterpret_cast<const float*>(tbl) + ridx * row_elems + col);
+                                u[j] = valid ? __ldg(q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                                w[j] = valid ? __ldg(q + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (j >= rpt) break;
+                                const int row = row_base + j;
+                                const uint32_t dst = kbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
+                                st_shared_v4(dst, pack_bf16x2(u[j].x, u[j].y), pack_bf16x2(u[j].z, u[j].w),
+                                             pack_bf16x2(w[j].x, w[j].y), pack_bf16x2(w[j].z, w[j].w));
                             }
                         }
                     }
@@ -210,7 +241,8 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                 }
             }
             // indices of this CTA's next tile into the other slot
-            stage_idx(tile + gridDim.x, idx_smem + ((lt + 1) & 1) * 4 * N);
+            idx_store(idx_smem + ((lt + 1) & 1) * 4 * N, 0, nxt0);
+            idx_store(idx_smem + ((lt + 1) & 1) * 4 * N, 1, nxt1);
             named_bar_sync(1, kProducerThreads);
         }
         cp_async_wait<0>();
@@ -307,19 +339,22 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                     tmem_ld_wait();
                     const int cnt = min(32, nt - c * 32);
                     if (part == 1) {
-                        // runs of equal dst row inside the chunk: one add per run
-                        float run = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            if (j < cnt) {
-                                const int h = wix[N + c * 32 + j];
-                                run += __uint_as_float(v[j]);
-                                const bool end = (j == cnt - 1) || (wix[N + c * 32 + j + 1] != h);
-                                if (end) {
-                                    if (k_ok && a.dz) atomicAdd(a.dz + (int64_t)h * a.d + kk, run);
-                                    run = 0.f;
-                                }
-                            }
+                        // runs of equal dst row inside the chunk (the tuples are dst-sorted): a
+                        // segmented running sum in registers, then one add per run end
+                        const int li = c * 32 + lane;
+                        const int h = wix[N + li];
+                        const bool tvalid = lane < cnt;
+                        const bool nx_diff = (lane == cnt - 1) || (li + 1 < N && wix[N + li + 1] != h);
+                        const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && nx_diff);
+                        const unsigned startmask = (endmask << 1) | 1u;
+                        float sum = 0.f, comp = 0.f;
+                        uint32_t mword = 0;
+                        seg_scan<false, false, false>(v, 0.f, startmask, sum, comp, mword, lane);
+                        for (unsigned em = endmask; em; em &= em - 1u) {
+                            const int j = __ffs(em) - 1;
+                            const float val = __uint_as_float(select32(v, j));
+                            const int hj = wix[N + c * 32 + j];
+                            if (k_ok && a.dz) atomicAdd(a.dz + (int64_t)hj * a.d + kk, val);
                         }
                     } else if (part == 0) {
 #pragma unroll

@@ -15,6 +15,7 @@
 //   warps 9-12 epilogue: tcgen05.ld of the accumulator (double-buffered in TMEM so the next tile's
 //              MMAs overlap), bias, ReLU, SUM walk, stores / tile-boundary partials.
 #include "fwd.cuh"
+#include "segscan.cuh"
 #include "tc.cuh"
 
 #include <algorithm>
@@ -56,48 +57,6 @@ struct TcArgs {
     int kb_width[kMaxKb]; // width of that part
     int need_arr[3];      // which of hs, hd, er the K blocks read
 };
-
-// Segmented running sum over the 32 tuples of a chunk held by one epilogue thread (one feature):
-// y = acc + bias (ReLU'd), sum restarts at every row whose bit is set in `startmask`, and v[j] is
-// replaced by the sum of its piece up to row j. Branch-free, so the unrolled body stays small.
-template <bool RELU, bool KAHAN, bool MASK>
-__device__ __forceinline__ void seg_scan(uint32_t (&v)[32], float bo, unsigned startmask, float& sum, float& comp,
-                                         uint32_t& mword, int lane) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        float y = __uint_as_float(v[j]) + bo;
-        if (RELU) {
-            if (MASK) {
-                const unsigned w = __ballot_sync(0xffffffffu, y > 0.f);
-                mword = (lane == j) ? w : mword;
-            }
-            y = fmaxf(y, 0.f);
-        }
-        const bool st = (startmask >> j) & 1u;
-        if (KAHAN) {
-            sum = st ? 0.f : sum;
-            comp = st ? 0.f : comp;
-            kahan_add(sum, comp, y);
-        } else {
-            sum = st ? y : sum + y;
-        }
-        v[j] = __float_as_uint(sum);
-    }
-}
-
-// v[j] for a warp-uniform run-time j without local-memory indexing (a 5-level select tree).
-__device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], int j) {
-    uint32_t t16[16], t8[8], t4[4];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) t16[i] = (j & 1) ? v[2 * i + 1] : v[2 * i];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) t8[i] = (j & 2) ? t16[2 * i + 1] : t16[2 * i];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) t4[i] = (j & 4) ? t8[2 * i + 1] : t8[2 * i];
-    const uint32_t a0 = (j & 8) ? t4[1] : t4[0];
-    const uint32_t a1 = (j & 8) ? t4[3] : t4[2];
-    return (j & 16) ? a1 : a0;
-}
 
 __global__ void __launch_bounds__(kThreads, 1)
 fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ TcArgs a) {
