@@ -320,7 +320,10 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
             __syncwarp();
             const int acc = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
-            if (!mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag)) { ok = false; break; }
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag))) {
+                ok = false;
+                break;
+            }
             tc_fence_after();
             for (int mb = 0; mb < a.mbk; ++mb) {
                 const int kbase = mb * 128 + 32 * q;  // padded K row of lane 0
@@ -373,7 +376,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
             mbar_arrive(smem_u32(&tempty[acc]));
         }
         // this CTA's dW partial: TMEM lane o (output feature), columns k (input features)
-        if (ok && mbar_wait(smem_u32(dwdone), 0, a.status, abort_flag)) {
+        if (ok && __all_sync(0xffffffffu, mbar_wait(smem_u32(dwdone), 0, a.status, abort_flag))) {
             tc_fence_after();
             const int o = 32 * q + lane;
             float* dst = a.dw_part + ((int64_t)blockIdx.x * a.d_out + o) * a.d_in;

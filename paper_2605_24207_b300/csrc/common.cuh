@@ -123,6 +123,24 @@ struct DevBuf {
         ordered = true;
         return RELNN_OK;
     }
+    // Long-lived buffer allocated in the order of stream s without a synchronisation: usable on s
+    // at once and on other streams only after s has been synchronised (the plan builders end with
+    // one). Freed by cudaFree like alloc().
+    relnn_status alloc_nosync(size_t n, cudaStream_t s) {
+        if (n <= bytes && p) return RELNN_OK;
+        release();
+        if (n == 0) n = 16;
+        ensure_pool_cached();
+        cudaError_t e = cudaMallocAsync(&p, n, s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error(std::string("device allocation of ") + std::to_string(n) + " bytes: " + cudaGetErrorString(e));
+            return RELNN_ENOMEM;
+        }
+        bytes = n;
+        ordered = false;
+        return RELNN_OK;
+    }
     template <class T>
     T* as() const { return reinterpret_cast<T*>(p); }
 };

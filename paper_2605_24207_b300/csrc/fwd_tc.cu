@@ -278,7 +278,8 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
             const int after_seg = pf_after;
             __syncwarp();
             prefetch(tile + gridDim.x);
-            if (!mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag)) break;
+            // warp-uniform outcome of the bounded wait, so no lane runs the .sync.aligned loads alone
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag))) break;
             tc_fence_after();
             const int64_t t0 = tile * a.tile_n;
             const int nt = (int)imin64(a.tile_n, a.m - t0);

@@ -180,18 +180,19 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     RELNN_CHECK_ARG(n == 0 || keys, "join build: null keys");
     jt.kt = kt;
     jt.n = n;
-    RELNN_TRY(jt.status.alloc(sizeof(int)));
+    RELNN_TRY(jt.status.alloc_nosync(sizeof(int), st));
     RELNN_CUDA(cudaMemsetAsync(jt.status.p, 0, sizeof(int), st));
-    RELNN_TRY(jt.rows_sorted.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1)));
-    RELNN_TRY(jt.uid_of_pos.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1)));
+    RELNN_TRY(jt.rows_sorted.alloc_nosync(sizeof(int32_t) * std::max<int64_t>(n, 1), st));
+    RELNN_TRY(jt.uid_of_pos.alloc_nosync(sizeof(int32_t) * std::max<int64_t>(n, 1), st));
     if (n == 0) {
         jt.n_unique = 0;
-        RELNN_TRY(jt.run_start.alloc(sizeof(int32_t)));
+        RELNN_TRY(jt.run_start.alloc_nosync(sizeof(int32_t), st));
         RELNN_CUDA(cudaMemsetAsync(jt.run_start.p, 0, sizeof(int32_t), st));
-        RELNN_TRY(jt.ukeys.alloc(sizeof(int64_t)));
+        RELNN_TRY(jt.ukeys.alloc_nosync(sizeof(int64_t), st));
         jt.mode = 1;
         jt.direct_size = 0;
-        RELNN_TRY(jt.slot_vals.alloc(sizeof(int32_t)));
+        RELNN_TRY(jt.slot_vals.alloc_nosync(sizeof(int32_t), st));
+        RELNN_CUDA(cudaStreamSynchronize(st));
         return RELNN_OK;
     }
     int64_t kmin, kmax;
@@ -213,13 +214,13 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     const int g = grid_for(n);
     if (narrow) {
         { make_sort_keys_kernel<uint32_t><<<g, 256, 0, st>>>(keys, n, kt, omin, sk.as<uint32_t>(), rows); note_launch(); }
-        RELNN_TRY(radix_sort_pairs<uint32_t>(sk.as<uint32_t>(), rows, sk_tmp.as<uint32_t>(),
-                                             rows_tmp.as<int32_t>(), n, nbits, st));
+        RELNN_TRY((radix_sort_pairs<uint32_t, int32_t>(sk.as<uint32_t>(), rows, sk_tmp.as<uint32_t>(),
+                                                       rows_tmp.as<int32_t>(), n, nbits, st)));
         { run_flags_kernel<uint32_t><<<g, 256, 0, st>>>(sk.as<uint32_t>(), n, flags.as<int32_t>()); note_launch(); }
     } else {
         { make_sort_keys_kernel<uint64_t><<<g, 256, 0, st>>>(keys, n, kt, omin, sk.as<uint64_t>(), rows); note_launch(); }
-        RELNN_TRY(radix_sort_pairs<uint64_t>(sk.as<uint64_t>(), rows, sk_tmp.as<uint64_t>(),
-                                             rows_tmp.as<int32_t>(), n, nbits, st));
+        RELNN_TRY((radix_sort_pairs<uint64_t, int32_t>(sk.as<uint64_t>(), rows, sk_tmp.as<uint64_t>(),
+                                                       rows_tmp.as<int32_t>(), n, nbits, st)));
         { run_flags_kernel<uint64_t><<<g, 256, 0, st>>>(sk.as<uint64_t>(), n, flags.as<int32_t>()); note_launch(); }
     }
     RELNN_TRY(exclusive_scan<int32_t>(flags.as<int32_t>(), flags.as<int32_t>(), n,
@@ -229,8 +230,8 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     RELNN_CUDA(cudaStreamSynchronize(st));
     const int64_t U = U32;
     jt.n_unique = U;
-    RELNN_TRY(jt.run_start.alloc(sizeof(int32_t) * (U + 1)));
-    RELNN_TRY(jt.ukeys.alloc(sizeof(int64_t) * std::max<int64_t>(U, 1)));
+    RELNN_TRY(jt.run_start.alloc_nosync(sizeof(int32_t) * (U + 1), st));
+    RELNN_TRY(jt.ukeys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(U, 1), st));
     if (narrow)
         { runs_kernel<uint32_t><<<g, 256, 0, st>>>(sk.as<uint32_t>(), flags.as<int32_t>(), n, omin,
                                                  jt.run_start.as<int32_t>(), jt.uid_of_pos.as<int32_t>(),
@@ -245,7 +246,7 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
         jt.mode = 1;
         jt.direct_size = (int64_t)span + 1;
         jt.cap = 0;
-        RELNN_TRY(jt.slot_vals.alloc(sizeof(int32_t) * jt.direct_size));
+        RELNN_TRY(jt.slot_vals.alloc_nosync(sizeof(int32_t) * jt.direct_size, st));
         { fill_i32_kernel<<<grid_for(jt.direct_size), 256, 0, st>>>(jt.slot_vals.as<int32_t>(), jt.direct_size, -1); note_launch(); }
         { direct_insert_kernel<<<grid_for(U), 256, 0, st>>>(jt.ukeys.as<int64_t>(), U, kmin,
                                                           jt.slot_vals.as<int32_t>()); note_launch(); }
@@ -254,8 +255,8 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
         uint64_t cap = 1024;
         while (cap < (uint64_t)(2 * U)) cap <<= 1;
         jt.cap = cap;
-        RELNN_TRY(jt.slot_keys.alloc(sizeof(int64_t) * cap));
-        RELNN_TRY(jt.slot_vals.alloc(sizeof(int32_t) * cap));
+        RELNN_TRY(jt.slot_keys.alloc_nosync(sizeof(int64_t) * cap, st));
+        RELNN_TRY(jt.slot_vals.alloc_nosync(sizeof(int32_t) * cap, st));
         { fill_i64_kernel<<<grid_for(cap), 256, 0, st>>>(jt.slot_keys.as<int64_t>(), cap, kEmptyKey); note_launch(); }
         { fill_i32_kernel<<<grid_for(cap), 256, 0, st>>>(jt.slot_vals.as<int32_t>(), cap, -1); note_launch(); }
         { hash_insert_kernel<<<grid_for(U), 256, 0, st>>>(jt.ukeys.as<int64_t>(), U, cap - 1,

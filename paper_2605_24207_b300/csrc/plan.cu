@@ -35,14 +35,16 @@ __global__ void tri_count_kernel(JoinView j, const void* src, const void* dst, i
     if ((threadIdx.x & 31) == 0 && e < T) warp_tot[e >> 5] = m;
 }
 
-// Pass 2 over E: emit the join-output tuples (e, hs, hd) in (e, hs, hd) order with their group
-// sort key. Lane offsets inside a warp come from a ballot when every tuple matches at most once
-// (unique keys) and from a shuffle scan otherwise.
-template <class K>
+// Pass 2 over E: emit the join-output tuples in (e, hs, hd) order as (group key, payload) pairs.
+// The group key is the sorted position of the dst H row (rows of one key are contiguous there, so
+// sorting by it groups by key, then by H row) or, without a dst join, the raw dst key. The payload
+// is the src H row, or (src H row << 32 | E row) when the E row is needed later (r attributes).
+// Lane offsets inside a warp come from a ballot when every tuple matches at most once (unique
+// keys) and from a shuffle scan otherwise.
+template <class K, class V>
 __global__ void tri_emit_kernel(JoinView j, const void* dst, int64_t T, int kt, bool join_dst,
                                 uint64_t omin, const int32_t* us, const int32_t* ud,
-                                const int64_t* warp_off, int32_t* t_hs, int32_t* t_hd, int32_t* t_e,
-                                K* t_key) {
+                                const int64_t* warp_off, K* t_key, V* t_val) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int32_t a = -1, b = -1;
@@ -75,28 +77,35 @@ __global__ void tri_emit_kernel(JoinView j, const void* dst, int64_t T, int kt, 
     K rawkey = 0;
     if (!join_dst) rawkey = (K)(ordered64(load_key(dst, kt, e)) - omin);
     for (int64_t x = 0; x < cs; ++x) {
+        const int32_t hs = j.rows_sorted[rs + x];
+        V val;
+        if (sizeof(V) == 8) val = (V)(((uint64_t)(uint32_t)hs << 32) | (uint32_t)e);
+        else val = (V)hs;
         for (int64_t y = 0; y < cd; ++y, ++pos) {
-            t_hs[pos] = j.rows_sorted[rs + x];
-            t_e[pos] = (int32_t)e;
-            if (join_dst) {
-                t_hd[pos] = j.rows_sorted[rd + y];
-                t_key[pos] = (K)(rd + y);  // sorted position of the dst H row: groups by key, then row
-            } else {
-                t_hd[pos] = -1;
-                t_key[pos] = rawkey;
-            }
+            t_key[pos] = join_dst ? (K)(rd + y) : rawkey;
+            t_val[pos] = val;
         }
     }
 }
 
-__global__ void gather3_kernel(const int32_t* perm, int64_t m, const int32_t* a, const int32_t* b,
-                               const int32_t* c, int32_t* oa, int32_t* ob, int32_t* oc) {
+// Splits (src H row << 32 | E row) payloads into hs / er.
+__global__ void split_pair_kernel(const int64_t* val, int64_t m, int32_t* hs, int32_t* er) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t p = perm[i];
-        oa[i] = a[p];
-        ob[i] = b[p];
-        oc[i] = c[p];
+        const uint64_t v = (uint64_t)val[i];
+        hs[i] = (int32_t)(v >> 32);
+        er[i] = (int32_t)(uint32_t)v;
+    }
+}
+
+// After grouping by dst position: the dst H row and the output row of every matched tuple.
+__global__ void finalize_dst_kernel(const uint32_t* pos_d, int64_t m, const int32_t* rows_sorted,
+                                    const int32_t* uid_of_pos, const int32_t* out_row, int32_t* hd, int32_t* seg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = pos_d[i];
+        hd[i] = rows_sorted[p];
+        seg[i] = out_row[uid_of_pos[p]];
     }
 }
 
@@ -105,13 +114,6 @@ __global__ void mark_present_kernel(const uint32_t* pos_d, int64_t m, const int3
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
         present[uid_of_pos[pos_d[i]]] = 1;
-}
-
-__global__ void seg_from_pos_kernel(const uint32_t* pos_d, int64_t m, const int32_t* uid_of_pos,
-                                    const int32_t* out_row, int32_t* seg) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x)
-        seg[i] = out_row[uid_of_pos[pos_d[i]]];
 }
 
 // present / out_row: exclusive scan of the presence flags; writes the output keys.
@@ -141,12 +143,39 @@ __global__ void raw_seg_kernel(const K* key, const int32_t* flags_excl, int64_t 
     }
 }
 
-// Branch-local matched tuples before grouping.
+// Branch-local matched tuples while they are grouped: group keys (u32 dst position or u32/u64 raw
+// key) and payloads (int32 src H row, or int64 src H row << 32 | E row).
 struct Tmp {
-    DevBuf t_hs, t_hd, t_e, key, key_tmp, perm, perm_tmp;
-    bool wide = false;
+    DevBuf key, key_tmp, val, val_tmp;
+    bool wide = false;    // 64-bit raw keys
+    bool pair = false;    // 64-bit payloads (the E row rides along)
+    bool in_tmp = false;  // the sorted pairs are in key_tmp / val_tmp
     uint64_t omin = 0;
+    template <class K>
+    const K* keys() const { return in_tmp ? key_tmp.as<K>() : key.as<K>(); }
+    DevBuf& sorted_val() { return in_tmp ? val_tmp : val; }
 };
+
+template <class K, class V>
+relnn_status emit_and_sort(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t T, int64_t M, int nbits,
+                           const int32_t* us, const int32_t* ud, const int64_t* warp_off, cudaStream_t st) {
+    const JoinView v = p.H.view();
+    const int64_t m1 = std::max<int64_t>(M, 1);
+    RELNN_TRY(t.key.alloc_tmp(sizeof(K) * m1, st));
+    RELNN_TRY(t.key_tmp.alloc_tmp(sizeof(K) * m1, st));
+    // payload buffers outlive the plan build: the sorted one becomes the branch's hs when it holds
+    // the src H row alone
+    RELNN_TRY(t.val.alloc_nosync(sizeof(V) * m1, st));
+    RELNN_TRY(t.val_tmp.alloc_nosync(sizeof(V) * m1, st));
+    if (T > 0) {
+        const int blocks = (int)ceil_div(T, 256);
+        { tri_emit_kernel<K, V><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin, us, ud, warp_off,
+                                                      t.key.as<K>(), t.val.as<V>()); note_launch(); }
+        RELNN_CUDA(cudaGetLastError());
+    }
+    return radix_sort_pairs<K, V>(t.key.as<K>(), t.val.as<V>(), t.key_tmp.as<K>(), t.val_tmp.as<V>(), M, nbits, st,
+                                  &t.in_tmp);
+}
 
 relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tmp& t, cudaStream_t st) {
     const int64_t T = bd.n_tuples;
@@ -170,7 +199,6 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
         return RELNN_ENOTSUP;
     }
     b.m = M;
-    const int64_t m1 = std::max<int64_t>(M, 1);
     // group key width: dst sorted position (n_h < 2^31) or the raw dst key span
     int nbits = 0;
     if (p.join_dst) {
@@ -184,40 +212,34 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
         nbits = bit_length(span);
         t.wide = nbits > 32;
     }
-    const size_t kb = t.wide ? 8 : 4;
-    RELNN_TRY(t.t_hs.alloc_tmp(4 * m1, st));
-    RELNN_TRY(t.t_hd.alloc_tmp(4 * m1, st));
-    RELNN_TRY(t.t_e.alloc_tmp(4 * m1, st));
-    RELNN_TRY(t.key.alloc_tmp(kb * m1, st));
-    RELNN_TRY(t.key_tmp.alloc_tmp(kb * m1, st));
-    RELNN_TRY(t.perm.alloc_tmp(4 * m1, st));
-    RELNN_TRY(t.perm_tmp.alloc_tmp(4 * m1, st));
-    if (T > 0) {
-        if (t.wide)
-            { tri_emit_kernel<uint64_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
-                us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>(), t.t_hs.as<int32_t>(),
-                t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(), t.key.as<uint64_t>()); note_launch(); }
-        else
-            { tri_emit_kernel<uint32_t><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin,
-                us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>(), t.t_hs.as<int32_t>(),
-                t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(), t.key.as<uint32_t>()); note_launch(); }
-        RELNN_CUDA(cudaGetLastError());
+    t.pair = b.d_r > 0;
+    const int32_t* usp = us.as<int32_t>();
+    const int32_t* udp = ud.as<int32_t>();
+    const int64_t* wo = wt.as<int64_t>();
+    if (t.wide) {
+        if (t.pair) RELNN_TRY((emit_and_sort<uint64_t, int64_t>(p, bd, t, T, M, nbits, usp, udp, wo, st)));
+        else RELNN_TRY((emit_and_sort<uint64_t, int32_t>(p, bd, t, T, M, nbits, usp, udp, wo, st)));
+    } else {
+        if (t.pair) RELNN_TRY((emit_and_sort<uint32_t, int64_t>(p, bd, t, T, M, nbits, usp, udp, wo, st)));
+        else RELNN_TRY((emit_and_sort<uint32_t, int32_t>(p, bd, t, T, M, nbits, usp, udp, wo, st)));
     }
-    RELNN_TRY(iota_i32(t.perm.as<int32_t>(), M, st));
-    if (t.wide)
-        RELNN_TRY(radix_sort_pairs<uint64_t>(t.key.as<uint64_t>(), t.perm.as<int32_t>(), t.key_tmp.as<uint64_t>(),
-                                             t.perm_tmp.as<int32_t>(), M, nbits, st));
-    else
-        RELNN_TRY(radix_sort_pairs<uint32_t>(t.key.as<uint32_t>(), t.perm.as<int32_t>(), t.key_tmp.as<uint32_t>(),
-                                             t.perm_tmp.as<int32_t>(), M, nbits, st));
-    RELNN_TRY(b.hs.alloc(4 * m1, st));
-    RELNN_TRY(b.hd.alloc(4 * m1, st));
-    RELNN_TRY(b.er.alloc(4 * m1, st));
-    RELNN_TRY(b.seg.alloc(4 * (m1 + 1), st));
-    if (M > 0)
-        { gather3_kernel<<<grid_for(M), 256, 0, st>>>(t.perm.as<int32_t>(), M, t.t_hs.as<int32_t>(),
-                                                    t.t_hd.as<int32_t>(), t.t_e.as<int32_t>(),
-                                                    b.hs.as<int32_t>(), b.hd.as<int32_t>(), b.er.as<int32_t>()); note_launch(); }
+    // hs / er from the sorted payloads; hd and seg follow once the output rows are known
+    const int64_t m1 = std::max<int64_t>(M, 1);
+    if (t.pair) {
+        RELNN_TRY(b.hs.alloc_nosync(4 * m1, st));
+        RELNN_TRY(b.er.alloc_nosync(4 * m1, st));
+        if (M > 0)
+            { split_pair_kernel<<<grid_for(M), 256, 0, st>>>(t.sorted_val().as<int64_t>(), M, b.hs.as<int32_t>(),
+                                                           b.er.as<int32_t>()); note_launch(); }
+        t.val.release();
+        t.val_tmp.release();
+    } else {
+        b.hs = std::move(t.sorted_val());
+        t.val.release();
+        t.val_tmp.release();
+    }
+    RELNN_TRY(b.hd.alloc_nosync(4 * m1, st));
+    RELNN_TRY(b.seg.alloc_nosync(4 * (m1 + 1), st));
     RELNN_CUDA(cudaGetLastError());
     return RELNN_OK;
 }
@@ -253,7 +275,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     p.d_in = p.d * (p.concat_dst ? 2 : 1) + d_r0;
     p.d_out = p.identity ? p.d_in : desc->d_out;
     RELNN_CHECK_ARG(p.d_out > 0 && p.d_out <= 4096, "rule plan: bad d_out");
-    RELNN_TRY(p.status.alloc(sizeof(int)));
+    RELNN_TRY(p.status.alloc_nosync(sizeof(int), st));
     RELNN_CUDA(cudaMemsetAsync(p.status.p, 0, sizeof(int), st));
 
     // a1: build side over H.id
@@ -280,21 +302,21 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
                 { mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
-                    tmp[i].key.as<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), present.as<int32_t>()); note_launch(); }
+                    tmp[i].keys<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), present.as<int32_t>()); note_launch(); }
         RELNN_TRY(exclusive_scan<int32_t>(present.as<int32_t>(), out_row.as<int32_t>(), U, out_row.as<int32_t>() + U, st));
         int32_t nout = 0;
         RELNN_CUDA(cudaMemcpyAsync(&nout, out_row.as<int32_t>() + U, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         RELNN_CUDA(cudaStreamSynchronize(st));
         p.n_out = nout;
-        RELNN_TRY(p.out_keys.alloc(sizeof(int64_t) * std::max<int64_t>(nout, 1)));
+        RELNN_TRY(p.out_keys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(nout, 1), st));
         if (U > 0)
             { out_keys_kernel<<<grid_for(U), 256, 0, st>>>(present.as<int32_t>(), out_row.as<int32_t>(),
                                                          p.H.ukeys.as<int64_t>(), U, p.out_keys.as<int64_t>()); note_launch(); }
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
-                { seg_from_pos_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
-                    tmp[i].key.as<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), out_row.as<int32_t>(),
-                    p.br[i].seg.as<int32_t>()); note_launch(); }
+                { finalize_dst_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                    tmp[i].keys<uint32_t>(), p.br[i].m, p.H.rows_sorted.as<int32_t>(), p.H.uid_of_pos.as<int32_t>(),
+                    out_row.as<int32_t>(), p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>()); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
         RELNN_CUDA(cudaStreamSynchronize(st));
     } else {
@@ -304,21 +326,23 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         DevBuf flags;
         RELNN_TRY(flags.alloc_tmp(sizeof(int32_t) * (M + 1), st));
         if (M > 0) {
-            if (t.wide) { key_flags_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), M, flags.as<int32_t>()); note_launch(); }
-            else { key_flags_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), M, flags.as<int32_t>()); note_launch(); }
+            if (t.wide) { key_flags_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.keys<uint64_t>(), M, flags.as<int32_t>()); note_launch(); }
+            else { key_flags_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.keys<uint32_t>(), M, flags.as<int32_t>()); note_launch(); }
         }
         RELNN_TRY(exclusive_scan<int32_t>(flags.as<int32_t>(), flags.as<int32_t>(), M, flags.as<int32_t>() + M, st));
         int32_t nout = 0;
         RELNN_CUDA(cudaMemcpyAsync(&nout, flags.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         RELNN_CUDA(cudaStreamSynchronize(st));
         p.n_out = nout;
-        RELNN_TRY(p.out_keys.alloc(sizeof(int64_t) * std::max<int64_t>(nout, 1)));
+        RELNN_TRY(p.out_keys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(nout, 1), st));
+        // without a dst join there is no dst H row
+        RELNN_CUDA(cudaMemsetAsync(b.hd.p, 0xff, b.hd.bytes, st));
         if (M > 0) {
             if (t.wide)
-                { raw_seg_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint64_t>(), flags.as<int32_t>(), M,
+                { raw_seg_kernel<uint64_t><<<grid_for(M), 256, 0, st>>>(t.keys<uint64_t>(), flags.as<int32_t>(), M,
                                                                       t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>()); note_launch(); }
             else
-                { raw_seg_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.key.as<uint32_t>(), flags.as<int32_t>(), M,
+                { raw_seg_kernel<uint32_t><<<grid_for(M), 256, 0, st>>>(t.keys<uint32_t>(), flags.as<int32_t>(), M,
                                                                       t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>()); note_launch(); }
         }
         RELNN_CUDA(cudaGetLastError());

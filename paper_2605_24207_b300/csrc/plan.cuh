@@ -7,10 +7,8 @@
 //   er[m]   int32  E row (index into the per-tuple embedding r)
 //   seg[m]  int32  output row of the tuple (position of its dst key among the output keys)
 // Within one output key the tuples are ordered by dst H row, then E row, then src H row, so runs of
-// equal hd are contiguous (used by the backward's scatter to z_dst).
-// For the backward's scatter to z_src a second order sorted by src H row is kept:
-//   src_perm[m] int32  position (in the order above) of the k-th tuple in src order
-//   src_hs[m]   int32  its src H row (non-decreasing)
+// equal hd are contiguous (used by the backward's scatter to z_dst). er is kept only for branches
+// with a per-tuple embedding r (d_r > 0).
 #pragma once
 
 #include <vector>
@@ -24,7 +22,6 @@ struct BranchPlan {
     int64_t m = 0;  // matched tuples
     int32_t d_r = 0;
     DevBuf hs, hd, er, seg;
-    DevBuf src_perm, src_hs;
     DevBuf relu_mask;  // uint32 [m][ceil(d_out/32)] when RELNN_FLAG_RELU_MASK
 };
 
@@ -59,7 +56,7 @@ struct Plan {
             b->st = s;
         }
         for (auto& b : br) {
-            DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.src_perm, &b.src_hs, &b.relu_mask};
+            DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.relu_mask};
             for (DevBuf* x : bb) {
                 x->ordered = true;
                 x->st = s;

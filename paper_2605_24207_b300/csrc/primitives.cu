@@ -3,8 +3,9 @@
 // Scan: reduce-then-scan. A block owns 4096 consecutive items (512 threads x 8 items in blocked
 // order); the block sums are scanned recursively and added back.
 //
-// Radix sort: 8 bits per pass. Each block owns a tile of 4096 keys split into 8 warp sub-tiles of
-// 512 keys that a warp visits in 16 steps of 32. Pass = (1) per-block digit histogram with
+// Radix sort: the key bits are split into passes of equal width of at most 11 bits (a 20-bit key
+// takes two passes of 10). Each block owns a tile of 4096 keys split into 8 warp sub-tiles of 512
+// keys that a warp visits in 16 steps of 32. Pass = (1) per-block digit histogram with
 // warp-aggregated shared-memory counts, (2) exclusive scan of the digit-major histogram, (3) stable
 // scatter: a key's destination is digit base + (keys of its digit in earlier blocks) + (in earlier
 // warps of its block) + (in earlier steps of its warp) + (in lower lanes of its step), the last two
@@ -90,78 +91,86 @@ __global__ void scan_apply_kernel(const T* __restrict__ in, T* __restrict__ out,
     }
 }
 
-__global__ void iota_kernel(int32_t* out, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (int32_t)i;
-}
-
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortSteps = 16;
 constexpr int kSortTile = kSortThreads * kSortSteps;  // 4096
+constexpr int kMaxDigitBits = 11;
 
+// Per-block digit counts of one pass (digit = (key >> shift) & mask, bins = mask + 1), stored
+// digit-major: hist[d * nblocks + block].
 template <class K>
-__global__ void rs_hist_kernel(const K* __restrict__ keys, int64_t n, int shift,
+__global__ void rs_hist_kernel(const K* __restrict__ keys, int64_t n, int shift, unsigned mask,
                                int32_t* __restrict__ hist, int nblocks) {
-    __shared__ int32_t h[256];
-    for (int i = threadIdx.x; i < 256; i += kSortThreads) h[i] = 0;
+    extern __shared__ int32_t h[];
+    const int bins = (int)mask + 1;
+    for (int i = threadIdx.x; i < bins; i += kSortThreads) h[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortSteps);
     for (int s = 0; s < kSortSteps; ++s) {
         int64_t i = base + s * 32 + lane;
         bool valid = i < n;
-        unsigned d = valid ? (unsigned)((keys[i] >> shift) & 255u) : 256u + lane;
+        unsigned d = valid ? (unsigned)((keys[i] >> shift) & mask) : 0xffffffffu - lane;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += kSortThreads) hist[(int64_t)i * nblocks + blockIdx.x] = h[i];
+    for (int i = threadIdx.x; i < bins; i += kSortThreads) hist[(int64_t)i * nblocks + blockIdx.x] = h[i];
 }
 
-template <class K>
-__global__ void rs_scatter_kernel(const K* __restrict__ keys, const int32_t* __restrict__ vals,
-                                  K* __restrict__ okeys, int32_t* __restrict__ ovals, int64_t n,
-                                  int shift, const int32_t* __restrict__ offs, int nblocks) {
-    __shared__ int32_t wcnt[kSortWarps][256];
-    __shared__ int32_t gbase[256];
+// Stable scatter of one pass: a key's destination is its digit's base for this block (scanned
+// histogram) + the keys of that digit in earlier warps of the block + in earlier steps of its warp
+// + in lower lanes of its step (__match_any_sync / popc).
+template <class K, class V>
+__global__ void rs_scatter_kernel(const K* __restrict__ keys, const V* __restrict__ vals,
+                                  K* __restrict__ okeys, V* __restrict__ ovals, int64_t n,
+                                  int shift, unsigned mask, const int32_t* __restrict__ offs, int nblocks) {
+    extern __shared__ int32_t sm[];
+    const int bins = (int)mask + 1;
+    int32_t* gbase = sm;          // [bins]
+    int32_t* wcnt = sm + bins;    // [kSortWarps][bins]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < 256; i += kSortThreads) {
+    for (int i = threadIdx.x; i < bins; i += kSortThreads) {
         gbase[i] = offs[(int64_t)i * nblocks + blockIdx.x];
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) wcnt[w][i] = 0;
+        for (int w = 0; w < kSortWarps; ++w) wcnt[w * bins + i] = 0;
     }
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortSteps);
     K k[kSortSteps];
-    int32_t v[kSortSteps];
+    V v[kSortSteps];
     int32_t rank[kSortSteps];
 #pragma unroll
     for (int s = 0; s < kSortSteps; ++s) {
         int64_t i = base + s * 32 + lane;
         bool valid = i < n;
         k[s] = valid ? keys[i] : K(0);
-        v[s] = valid ? vals[i] : 0;
-        unsigned d = valid ? (unsigned)((k[s] >> shift) & 255u) : 256u + lane;
+        v[s] = valid ? vals[i] : V(0);
+    }
+#pragma unroll
+    for (int s = 0; s < kSortSteps; ++s) {
+        int64_t i = base + s * 32 + lane;
+        bool valid = i < n;
+        unsigned d = valid ? (unsigned)((k[s] >> shift) & mask) : 0xffffffffu - lane;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int leader = __ffs(peers) - 1;
         int old = 0;
         if (valid && lane == leader) {
-            old = wcnt[warp][d];
-            wcnt[warp][d] = old + __popc(peers);
+            old = wcnt[warp * bins + d];
+            wcnt[warp * bins + d] = old + __popc(peers);
         }
         old = __shfl_sync(0xffffffffu, old, leader);
         rank[s] = old + __popc(peers & lanemask_lt());
         __syncwarp();
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += kSortThreads) {
+    for (int i = threadIdx.x; i < bins; i += kSortThreads) {
         int32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kSortWarps; ++w) {
-            int32_t t = wcnt[w][i];
-            wcnt[w][i] = run;
+            int32_t t = wcnt[w * bins + i];
+            wcnt[w * bins + i] = run;
             run += t;
         }
     }
@@ -170,8 +179,8 @@ __global__ void rs_scatter_kernel(const K* __restrict__ keys, const int32_t* __r
     for (int s = 0; s < kSortSteps; ++s) {
         int64_t i = base + s * 32 + lane;
         if (i < n) {
-            unsigned d = (unsigned)((k[s] >> shift) & 255u);
-            int64_t pos = (int64_t)gbase[d] + wcnt[warp][d] + rank[s];
+            unsigned d = (unsigned)((k[s] >> shift) & mask);
+            int64_t pos = (int64_t)gbase[d] + wcnt[warp * bins + d] + rank[s];
             okeys[pos] = k[s];
             ovals[pos] = v[s];
         }
@@ -207,49 +216,64 @@ relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream
 template relnn_status exclusive_scan<int32_t>(const int32_t*, int32_t*, int64_t, int32_t*, cudaStream_t);
 template relnn_status exclusive_scan<int64_t>(const int64_t*, int64_t*, int64_t, int64_t*, cudaStream_t);
 
-template <class K>
-relnn_status radix_sort_pairs(K* keys, int32_t* vals, K* keys_tmp, int32_t* vals_tmp, int64_t n,
-                              int nbits, cudaStream_t st) {
+template <class K, class V>
+relnn_status radix_sort_pairs(K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n, int nbits, cudaStream_t st,
+                              bool* result_in_tmp) {
+    if (result_in_tmp) *result_in_tmp = false;
     if (n <= 1 || nbits <= 0) return RELNN_OK;
     const int64_t nb64 = ceil_div(n, kSortTile);
-    RELNN_CHECK_ARG(nb64 * 256 < (1ll << 31), "radix sort: too many keys");
+    // passes of equal width, at most kMaxDigitBits bits each
+    const int passes = (nbits + kMaxDigitBits - 1) / kMaxDigitBits;
+    const int bits = (nbits + passes - 1) / passes;
+    const unsigned mask = (1u << bits) - 1u;
+    const int bins = (int)mask + 1;
+    RELNN_CHECK_ARG(nb64 * bins < (1ll << 31), "radix sort: too many keys");
     const int nb = (int)nb64;
+    const size_t scatter_smem = sizeof(int32_t) * (size_t)bins * (kSortWarps + 1);
+    static bool attr_set = false;
+    if (!attr_set) {
+        const int max_smem = (int)(sizeof(int32_t) * (1u << kMaxDigitBits) * (kSortWarps + 1));
+        RELNN_CUDA(cudaFuncSetAttribute(rs_scatter_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        attr_set = true;
+    }
     int32_t* hist = nullptr;
-    RELNN_CUDA(cudaMallocAsync(&hist, sizeof(int32_t) * 256 * (size_t)nb, st));
+    RELNN_CUDA(cudaMallocAsync(&hist, sizeof(int32_t) * (size_t)bins * nb, st));
     K *src_k = keys, *dst_k = keys_tmp;
-    int32_t *src_v = vals, *dst_v = vals_tmp;
+    V *src_v = vals, *dst_v = vals_tmp;
     relnn_status s = RELNN_OK;
-    int passes = 0;
-    for (int shift = 0; shift < nbits; shift += 8, ++passes) {
-        { rs_hist_kernel<K><<<nb, kSortThreads, 0, st>>>(src_k, n, shift, hist, nb); note_launch(); }
-        s = exclusive_scan<int32_t>(hist, hist, (int64_t)256 * nb, nullptr, st);
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * bits;
+        { rs_hist_kernel<K><<<nb, kSortThreads, sizeof(int32_t) * bins, st>>>(src_k, n, shift, mask, hist, nb); note_launch(); }
+        s = exclusive_scan<int32_t>(hist, hist, (int64_t)bins * nb, nullptr, st);
         if (s != RELNN_OK) break;
-        { rs_scatter_kernel<K><<<nb, kSortThreads, 0, st>>>(src_k, src_v, dst_k, dst_v, n, shift, hist, nb); note_launch(); }
+        { rs_scatter_kernel<K, V><<<nb, kSortThreads, scatter_smem, st>>>(src_k, src_v, dst_k, dst_v, n, shift, mask, hist, nb); note_launch(); }
         if (cudaGetLastError() != cudaSuccess) {
             s = RELNN_ECUDA;
             break;
         }
         K* tk = src_k; src_k = dst_k; dst_k = tk;
-        int32_t* tv = src_v; src_v = dst_v; dst_v = tv;
+        V* tv = src_v; src_v = dst_v; dst_v = tv;
     }
     if (s == RELNN_OK && (passes & 1)) {
-        cudaMemcpyAsync(keys, keys_tmp, sizeof(K) * n, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(vals, vals_tmp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
+        if (result_in_tmp) {
+            *result_in_tmp = true;
+        } else {
+            cudaMemcpyAsync(keys, keys_tmp, sizeof(K) * n, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(vals, vals_tmp, sizeof(V) * n, cudaMemcpyDeviceToDevice, st);
+        }
     }
     cudaFreeAsync(hist, st);
     if (s != RELNN_OK) set_error("radix sort failed");
     return s;
 }
 
-template relnn_status radix_sort_pairs<uint32_t>(uint32_t*, int32_t*, uint32_t*, int32_t*, int64_t, int, cudaStream_t);
-template relnn_status radix_sort_pairs<uint64_t>(uint64_t*, int32_t*, uint64_t*, int32_t*, int64_t, int, cudaStream_t);
-
-relnn_status iota_i32(int32_t* out, int64_t n, cudaStream_t st) {
-    if (n <= 0) return RELNN_OK;
-    int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 148 * 16);
-    { iota_kernel<<<blocks, 256, 0, st>>>(out, n); note_launch(); }
-    RELNN_CUDA(cudaGetLastError());
-    return RELNN_OK;
-}
+template relnn_status radix_sort_pairs<uint32_t, int32_t>(uint32_t*, int32_t*, uint32_t*, int32_t*, int64_t, int,
+                                                          cudaStream_t, bool*);
+template relnn_status radix_sort_pairs<uint64_t, int32_t>(uint64_t*, int32_t*, uint64_t*, int32_t*, int64_t, int,
+                                                          cudaStream_t, bool*);
+template relnn_status radix_sort_pairs<uint32_t, int64_t>(uint32_t*, int64_t*, uint32_t*, int64_t*, int64_t, int,
+                                                          cudaStream_t, bool*);
+template relnn_status radix_sort_pairs<uint64_t, int64_t>(uint64_t*, int64_t*, uint64_t*, int64_t*, int64_t, int,
+                                                          cudaStream_t, bool*);
 
 }  // namespace relnn

@@ -1,5 +1,5 @@
 // Device-wide primitives used by the content track (join build/probe and grouping): exclusive
-// scan and a stable LSD radix sort of (key, int32 value) pairs. All are hand-written kernels.
+// scan and a stable LSD radix sort of (key, value) pairs. All are hand-written kernels.
 #pragma once
 
 #include "common.cuh"
@@ -12,14 +12,13 @@ namespace relnn {
 template <class T>
 relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream_t st);
 
-// Stable LSD radix sort of n (key, value) pairs by the low `nbits` bits of the key.
-// keys/vals are sorted in place; keys_tmp/vals_tmp are scratch of n entries each.
-template <class K>
-relnn_status radix_sort_pairs(K* keys, int32_t* vals, K* keys_tmp, int32_t* vals_tmp, int64_t n,
-                              int nbits, cudaStream_t st);
-
-// out[i] = i for i < n.
-relnn_status iota_i32(int32_t* out, int64_t n, cudaStream_t st);
+// Stable LSD radix sort of n (key, value) pairs by the low `nbits` bits of the key (K = uint32_t or
+// uint64_t, V = int32_t or int64_t). keys_tmp/vals_tmp are scratch of n entries each. With
+// result_in_tmp == nullptr the result is left in keys/vals; otherwise *result_in_tmp tells which
+// pair of buffers holds it (an odd number of passes ends in the scratch pair).
+template <class K, class V>
+relnn_status radix_sort_pairs(K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n, int nbits, cudaStream_t st,
+                              bool* result_in_tmp = nullptr);
 
 // Number of significant bits of v (0 for v == 0).
 inline int bit_length(uint64_t v) {
