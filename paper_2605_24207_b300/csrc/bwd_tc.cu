@@ -50,7 +50,7 @@ struct BwArgs {
     int* status;
     int64_t m, n_tiles;
     int z_bf16, r_bf16, d, d_r, d_in, d_out, concat_dst, mask_words;
-    int n_kb, d_in_pad, mbk, tile_n, stages, lag;
+    int n_kb, d_in_pad, mbk, tile_n, stages;
     uint32_t idesc_dx, idesc_dw, tmem_cols, d2_col;
     int kb_src[kMaxKb], kb_col[kMaxKb], kb_width[kMaxKb];
     int need_arr[3];
@@ -83,7 +83,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
     const int warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < a.stages; ++s) {
-            mbar_init(smem_u32(&full[s]), kProducerThreads);
+            mbar_init(smem_u32(&full[s]), 2 * kProducerThreads);  // a plain and a cp.async arrive per thread
             mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -129,7 +129,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int k = 0; k < 8; ++k) dbacc[i][k] = 0.f;
-        int it = 0, pending = 0, lt = 0;
+        int it = 0, lt = 0;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int64_t t0 = tile * N;
@@ -229,15 +229,12 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                             }
                         }
                     }
-                    cp_async_commit();
-                    ++pending;
+                    // dY and converted f32 rows were stored by this thread: publish them now; the
+                    // cp.async rows arrive on their own once they have landed (no waiting here)
+                    fence_proxy_async();
+                    mbar_arrive(smem_u32(&full[s]));
+                    cp_async_mbar_arrive_noinc(smem_u32(&full[s]));
                     ++it;
-                    if (pending > a.lag) {
-                        cp_async_wait_n(a.lag);
-                        fence_proxy_async();
-                        mbar_arrive(smem_u32(&full[(it - 1 - a.lag) % a.stages]));
-                        --pending;
-                    }
                 }
             }
             // indices of this CTA's next tile into the other slot
@@ -245,9 +242,8 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
             idx_store(idx_smem + ((lt + 1) & 1) * 4 * N, 1, nxt1);
             named_bar_sync(1, kProducerThreads);
         }
+        // no copy may still be writing shared memory when the CTA retires
         cp_async_wait<0>();
-        fence_proxy_async();
-        for (int k = pending; k > 0; --k) mbar_arrive(smem_u32(&full[(it - k) % a.stages]));
         // db partial sums of this thread's output chunk
 #pragma unroll
         for (int ob = 0; ob < 2; ++ob)
@@ -274,6 +270,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                 const uint32_t use = (uint32_t)(lt >> 1);
                 if (!mbar_wait(smem_u32(&full[s]), ph, a.status, abort_flag)) { ok = false; break; }
                 if (!mbar_wait(smem_u32(&tempty[acc]), (use & 1u) ^ 1u, a.status, abort_flag)) { ok = false; break; }
+                fence_proxy_async();  // cp.async rows of the stage, before the tensor core reads them
                 tc_fence_after();
                 const uint32_t dyb = smem_u32(st_smem + (size_t)s * stage_bytes);
                 const uint32_t xb = dyb + dy_bytes;
@@ -579,7 +576,6 @@ relnn_status backward_tc(Plan& p, const CallIO& io, const GradIO& g, cudaStream_
         a.mbk = mbk;
         a.tile_n = N;
         a.stages = stages;
-        a.lag = stages - 1;
         a.idesc_dx = tc::idesc_bf16_f32(128, N);
         a.idesc_dw = tc::idesc_bf16_f32(128, d_in_pad, true, true);
         a.tmem_cols = tmem_cols;

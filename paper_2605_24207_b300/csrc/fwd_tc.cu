@@ -7,13 +7,16 @@
 // epilogue thread that owns feature o reads its tuples in output-key order and the SUM over a run of
 // equal output rows is a walk in registers; each emitted row is a 128-byte coalesced store per warp.
 //
-// Roles (416 threads, one CTA per SM):
-//   warps 0-7  producers: gather rows z[hs], z[hd], r[er] for one 64-column K block of a tile into
-//              a 128B-swizzled stage (cp.async for bf16 sources, convert-and-store for f32 sources)
-//   warp 8     TMEM allocation; lane 0 issues tcgen05.mma (A = W block staged once by TMA,
+// Roles (512 threads, one CTA per SM; 16 warps leave 128 registers per thread):
+//   warps 0-6  producers: gather rows z[hs], z[hd], r[er] for one 64-column K block of a tile into
+//              a 128B-swizzled stage (cp.async for bf16 sources, convert-and-store for f32 sources);
+//              the tile's row indices are staged by cp.async two tiles ahead
+//   warp 7     TMEM allocation; lane 0 issues tcgen05.mma (A = W block staged once by TMA,
 //              B = the gathered stage) and tcgen05.commit
-//   warps 9-12 epilogue: tcgen05.ld of the accumulator (double-buffered in TMEM so the next tile's
-//              MMAs overlap), bias, ReLU, SUM walk, stores / tile-boundary partials.
+//   warps 8-15 epilogue, two warps per TMEM lane quarter, each owning one half of the tile's
+//              columns (a half-tile is the unit of the SUM walk and of the boundary partials):
+//              tcgen05.ld of the accumulator (double-buffered in TMEM so the next tile's MMAs
+//              overlap), bias, ReLU, SUM walk, stores / half-tile-boundary partials.
 #include "fwd.cuh"
 #include "segscan.cuh"
 #include "tc.cuh"
@@ -27,11 +30,12 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 416;
-constexpr int kProducerThreads = 256;
-constexpr int kMmaWarp = 8;  // warps 0-7 produce, 9-12 are the epilogue
+constexpr int kThreads = 512;
+constexpr int kProducerThreads = 224;
+constexpr int kMmaWarp = 7;     // warps 0-6 produce, 8-15 are the epilogue
+constexpr int kEpiWarps = 8;
+constexpr int kIdxSlots = 3;    // row-index ring: the tile in production and the next two
 constexpr int kMaxKb = 12;
-constexpr int kMaxLag = 6;  // cp.async groups a producer thread may keep in flight before arriving
 constexpr int kSmemLimit = 227 * 1024;
 
 struct TcArgs {
@@ -50,7 +54,7 @@ struct TcArgs {
     int64_t n_tiles;
     int z_bf16, r_bf16, d, d_r;
     int d_out, act, kahan, accumulate;
-    int n_kb, tile_n, m_blocks, stages, lag, mask_words;
+    int n_kb, tile_n, m_blocks, stages, mask_words;
     uint32_t idesc, tmem_cols;
     int kb_src[kMaxKb];   // 0: z[hs], 1: z[hd], 2: r[er]
     int kb_col[kMaxKb];   // first element of the block within its part
@@ -66,11 +70,12 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
     const uint32_t stage_bytes = (uint32_t)a.tile_n * 128u;
     uint8_t* w_smem = base;
     uint8_t* st_smem = base + w_bytes;
-    // row indices of the tile being gathered (2 slots x {hs, hd, er} x tile_n), filled one tile ahead
+    // row indices of the tiles being gathered (kIdxSlots x {hs, hd, er} x tile_n)
     int32_t* idx_smem = reinterpret_cast<int32_t*>(st_smem + (size_t)a.stages * stage_bytes);
-    // output rows of the tile being reduced, one copy per epilogue warp
-    int32_t* seg_smem = idx_smem + 6 * a.tile_n;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(seg_smem + 4 * a.tile_n);
+    // output rows of the half-tile being reduced, one copy per epilogue warp
+    const int half_n = a.tile_n / 2;
+    int32_t* seg_smem = idx_smem + kIdxSlots * 3 * a.tile_n;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(seg_smem + kEpiWarps * half_n);
     uint64_t* full = bars;
     uint64_t* empty = bars + a.stages;
     uint64_t* tfull = bars + 2 * a.stages;
@@ -90,7 +95,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(&tfull[i]), 1);
-            mbar_init(smem_u32(&tempty[i]), 128);
+            mbar_init(smem_u32(&tempty[i]), 32 * kEpiWarps);
         }
         mbar_init(smem_u32(wbar), 1);
         mbar_init(smem_u32(drain), 1);
@@ -106,58 +111,52 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
 
     if (warp < kProducerThreads / 32) {
         // ------------------------------------------------------------------ producers
-        // Thread (row group rg, 16-byte chunk) copies chunk `chunk` of rows [rg*rpt, rg*rpt + rpt) of
-        // every K block; the 8 threads of a row group read one 128-byte row segment together.
-        const int chunk = tid & 7;
-        const int rpt = a.tile_n / (kProducerThreads / 8);
-        const int row_base = (tid >> 3) * rpt;
-        const int32_t* arrs[3] = {a.hs, a.hd, a.er};
-        const int per_thr = (a.tile_n + kProducerThreads - 1) / kProducerThreads;  // index entries per thread per array
-        // stage the first tile's row indices
-        {
-            const int64_t t0 = (int64_t)blockIdx.x * a.tile_n;
-            for (int r = 0; r < 3; ++r) {
+        // Copy e (row e / 8, 16-byte chunk e % 8) of a stage goes to thread e mod kProducerThreads,
+        // so the 8 lanes of a row read its 128-byte segment together (4 rows per warp instruction).
+        const int n_copies = a.tile_n * 8;
+        // cp.async of one tile's hs / hd / er entries (16 bytes each, zero-filled past m) into a slot;
+        // committed as one group
+        const int q_per_arr = a.tile_n / 4;
+        auto issue_idx = [&](int64_t tile, int slot) {
+            int32_t* dstb = idx_smem + slot * 3 * a.tile_n;
+            for (int e = tid; e < 3 * q_per_arr; e += kProducerThreads) {
+                const int r = e / q_per_arr, qq = e - r * q_per_arr;
                 if (!a.need_arr[r]) continue;
-                for (int k = 0; k < per_thr; ++k) {
-                    const int qq = tid + k * kProducerThreads;
-                    if (qq < a.tile_n) idx_smem[r * a.tile_n + qq] = (t0 + qq < a.m) ? __ldg(arrs[r] + t0 + qq) : 0;
-                }
+                const int32_t* arr = r == 0 ? a.hs : (r == 1 ? a.hd : a.er);
+                const int64_t t = tile * a.tile_n + 4 * qq;
+                const int64_t left = (tile < a.n_tiles) ? a.m - t : 0;
+                const uint32_t bytes = left >= 4 ? 16u : (left > 0 ? (uint32_t)left * 4u : 0u);
+                cp_async_16_stream(smem_u32(dstb + r * a.tile_n + 4 * qq), bytes ? arr + t : arr, bytes);
             }
-        }
+            cp_async_commit();
+        };
+        issue_idx(blockIdx.x, 0);
+        issue_idx((int64_t)blockIdx.x + gridDim.x, 1);
+        cp_async_wait<1>();
         named_bar_sync(1, kProducerThreads);
         int it = 0;
-        int pending = 0;  // stages issued but not yet arrived
         bool ok = true;
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int64_t t0 = tile * a.tile_n;
-            const int slot = lt & 1;
-            const int32_t* islot = idx_smem + slot * 3 * a.tile_n;
-            // prefetch the next tile's indices into registers (stored after this tile's K blocks)
-            const int64_t tn = (tile + gridDim.x) * a.tile_n;
-            int pre[3][2];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int qq = tid + k * kProducerThreads;
-                    pre[r][k] = (a.need_arr[r] && k < per_thr && qq < a.tile_n && tn + qq < a.m) ? __ldg(arrs[r] + tn + qq) : 0;
-                }
+            const int32_t* islot = idx_smem + (lt % kIdxSlots) * 3 * a.tile_n;
+            // indices two tiles ahead (that slot was last read two tiles ago, before a barrier)
+            issue_idx(tile + 2 * (int64_t)gridDim.x, (lt + 2) % kIdxSlots);
             for (int kb = 0; kb < a.n_kb; ++kb) {
                 if (!ok) break;
                 const int s = it % a.stages;
                 const uint32_t ph = (uint32_t)((it / a.stages) & 1);
                 if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.status, abort_flag)) { ok = false; break; }
                 const int src = a.kb_src[kb];
-                const int col = a.kb_col[kb] + chunk * 8;
-                const bool in_part = col < a.kb_width[kb];
                 const int32_t* rows_idx = islot + src * a.tile_n;
                 const void* tbl = src == 2 ? a.r : a.z;
                 const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
                 const int row_elems = src == 2 ? a.d_r : a.d;
                 const uint32_t sbase = smem_u32(st_smem + (size_t)s * stage_bytes);
-                for (int j = 0; j < rpt; ++j) {
-                    const int row = row_base + j;
+                for (int e = tid; e < n_copies; e += kProducerThreads) {
+                    const int row = e >> 3, chunk = e & 7;
+                    const int col = a.kb_col[kb] + chunk * 8;
+                    const bool in_part = col < a.kb_width[kb];
                     const uint32_t dst = sbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
                     const bool valid = (t0 + row < a.m) && in_part;
                     const int64_t ridx = rows_idx[row];
@@ -181,28 +180,23 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         st_shared_v4(dst, w0, w1, w2, w3);
                     }
                 }
-                cp_async_commit();
-                ++pending;
-                ++it;
-                if (pending > a.lag) {
-                    cp_async_wait_n(a.lag);
+                // The stage is complete for this thread when its copies have landed: cp.async sources
+                // arrive asynchronously (the thread moves on to the next stage at once); converted f32
+                // rows were stored by the thread itself and are published with a proxy fence.
+                if (tbl_bf16) {
+                    cp_async_mbar_arrive_noinc(smem_u32(&full[s]));
+                } else {
                     fence_proxy_async();
-                    mbar_arrive(smem_u32(&full[(it - 1 - a.lag) % a.stages]));
-                    --pending;
+                    mbar_arrive(smem_u32(&full[s]));
                 }
+                ++it;
             }
-            // publish the next tile's indices in the other slot (read by nobody since the last barrier)
-            int32_t* oslot = idx_smem + (slot ^ 1) * 3 * a.tile_n;
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    if (k < per_thr && tid + k * kProducerThreads < a.tile_n) oslot[r * a.tile_n + tid + k * kProducerThreads] = pre[r][k];
+            // the next tile's indices (issued two tiles ago) have landed for every producer thread
+            cp_async_wait<1>();
             named_bar_sync(1, kProducerThreads);
         }
+        // no copy may still be writing shared memory when the CTA retires
         cp_async_wait<0>();
-        fence_proxy_async();
-        for (int k = pending; k > 0; --k) mbar_arrive(smem_u32(&full[(it - k) % a.stages]));
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
@@ -227,6 +221,9 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                     const int s = it % a.stages;
                     const uint32_t ph = (uint32_t)((it / a.stages) & 1);
                     if (!mbar_wait(smem_u32(&full[s]), ph, a.status, abort_flag)) { ok = false; break; }
+                    // the stage was written through the generic proxy (cp.async): order it before the
+                    // tensor core's reads
+                    fence_proxy_async();
                     tc_fence_after();
                     const uint32_t b_base = smem_u32(st_smem + (size_t)s * stage_bytes);
 #pragma unroll
@@ -250,20 +247,31 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
         __syncwarp();
     } else {
         // ------------------------------------------------------------------ epilogue
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
-        int32_t* wseg = seg_smem + (warp - kMmaWarp - 1) * a.tile_n;
-        // output rows of the next tile, loaded one tile ahead (8 x 32 = up to 256 tuples)
-        int pf[8];
+        const int q = warp & 3;                      // TMEM lane quarter this warp may access
+        const int ew = warp - kMmaWarp - 1;          // 0..7 (quarters 0-3, then 0-3 again)
+        const int hh = ew >> 2;                      // which half of the tile's columns
+        const int n_half_chunks = half_n / 32;
+        int32_t* wseg = seg_smem + ew * half_n;
+        const bool relu = a.act == RELNN_ACT_RELU;
+        const bool mask = relu && a.relu_mask != nullptr;
+        float bias_r[2];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+            const int o = mb * 128 + 32 * q + lane;
+            bias_r[mb] = (a.bias && mb < a.m_blocks && o < a.d_out) ? a.bias[o] : 0.f;
+        }
+        // output rows of this warp's half of the next tile, loaded one tile ahead (up to 4 x 32)
+        int pf[4];
         int pf_prev = -1, pf_after = -1;
         auto prefetch = [&](int64_t tile) {
-            const int64_t t0 = tile * a.tile_n;
+            const int64_t h0 = tile * a.tile_n + hh * half_n;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int64_t t = t0 + 32 * c + lane;
-                pf[c] = (tile < a.n_tiles && 32 * c < a.tile_n && t < a.m) ? __ldg(a.seg + t) : -1;
+            for (int c = 0; c < 4; ++c) {
+                const int64_t t = h0 + 32 * c + lane;
+                pf[c] = (tile < a.n_tiles && c < n_half_chunks && t < a.m) ? __ldg(a.seg + t) : -1;
             }
-            pf_prev = (tile < a.n_tiles && t0 > 0) ? __ldg(a.seg + t0 - 1) : -1;
-            pf_after = (tile < a.n_tiles && t0 + a.tile_n < a.m) ? __ldg(a.seg + t0 + a.tile_n) : -1;
+            pf_prev = (tile < a.n_tiles && h0 > 0 && h0 - 1 < a.m) ? __ldg(a.seg + h0 - 1) : -1;
+            pf_after = (tile < a.n_tiles && h0 + half_n < a.m) ? __ldg(a.seg + h0 + half_n) : -1;
         };
         prefetch(blockIdx.x);
         int lt = 0;
@@ -272,8 +280,8 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
             const uint32_t use = (uint32_t)(lt >> 1);
             __syncwarp();
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (32 * c < a.tile_n) wseg[32 * c + lane] = pf[c];
+            for (int c = 0; c < 4; ++c)
+                if (c < n_half_chunks) wseg[32 * c + lane] = pf[c];
             const int prev_seg = pf_prev;
             const int after_seg = pf_after;
             __syncwarp();
@@ -281,31 +289,30 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
             // warp-uniform outcome of the bounded wait, so no lane runs the .sync.aligned loads alone
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag))) break;
             tc_fence_after();
-            const int64_t t0 = tile * a.tile_n;
-            const int nt = (int)imin64(a.tile_n, a.m - t0);
+            const int64_t vtile = tile * 2 + hh;     // half-tile index (unit of the boundary partials)
+            const int64_t t0 = tile * a.tile_n + hh * half_n;
+            const int nt = (int)imin64(half_n, a.m - t0);  // <= 0 for an empty second half
             for (int mb = 0; mb < a.m_blocks; ++mb) {
                 const int obase = mb * 128 + 32 * q;
                 if (obase >= a.d_out) continue;
                 const int o = obase + lane;
                 const bool o_ok = o < a.d_out;
-                const float bo = (a.bias && o_ok) ? a.bias[o] : 0.f;
+                const float bo = mb == 0 ? bias_r[0] : bias_r[1];
                 float sum = 0.f, comp = 0.f;
                 bool first = true;
-                unsigned prev_end = 1u;  // did the tuple before this chunk end a piece? (tile start: yes)
+                unsigned prev_end = 1u;  // did the tuple before this chunk end a piece? (half start: yes)
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_stride +
-                                       (uint32_t)mb * a.tile_n;
-                const bool relu = a.act == RELNN_ACT_RELU;
-                const bool mask = relu && a.relu_mask != nullptr;
+                                       (uint32_t)mb * a.tile_n + (uint32_t)(hh * half_n);
                 for (int c = 0; c * 32 < nt; ++c) {
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
                     tmem_ld_wait();
-                    const int li = c * 32 + lane;  // this lane's row in the tile
+                    const int li = c * 32 + lane;  // this lane's row in the half-tile
                     const bool tvalid = li < nt;
-                    // a piece ends at row j if the next row has another output row or j is the tile's
-                    // last row; it starts at j if row j-1 ended one
+                    // a piece ends at row j if the next row has another output row or j is the
+                    // half-tile's last row; it starts at j if row j-1 ended one
                     const int sg = wseg[li];
-                    const int nx = (li + 1 < a.tile_n) ? wseg[li + 1] : after_seg;
+                    const int nx = (li + 1 < half_n) ? wseg[li + 1] : after_seg;
                     const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && (sg != nx || li == nt - 1));
                     const unsigned startmask = (endmask << 1) | prev_end;
                     prev_end = endmask >> 31;
@@ -326,10 +333,10 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         const float val = __uint_as_float(select32(v, j));
                         const int s = wseg[c * 32 + j];
                         const bool last = (c * 32 + j == nt - 1);
-                        const int sn = last ? ((nt == a.tile_n) ? after_seg : -1) : s + 1;
+                        const int sn = last ? ((nt == half_n) ? after_seg : -1) : s + 1;
                         const bool split = (first && prev_seg == s) || (last && sn == s);
                         if (o_ok) {
-                            if (split) __stcg(a.carry + (tile * 2 + (first ? 0 : 1)) * a.d_out + o, val);
+                            if (split) __stcg(a.carry + (vtile * 2 + (first ? 0 : 1)) * a.d_out + o, val);
                             else emit_out(a.out + (int64_t)s * a.d_out + o, val, a.accumulate);
                         }
                         first = false;
@@ -444,7 +451,8 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
     const uint32_t w_bytes = (uint32_t)L.n_kb * m_blocks * 16384u;
     const uint32_t stage_bytes = (uint32_t)tile_n * 128u;
     const int bar_bytes = 256;
-    const int aux_bytes = 40 * tile_n;  // staged row indices (2 x 3 x tile_n) + epilogue rows (4 x tile_n)
+    // staged row indices (kIdxSlots x 3 x tile_n) + epilogue rows (kEpiWarps x tile_n / 2)
+    const int aux_bytes = 4 * (kIdxSlots * 3 * tile_n + kEpiWarps * tile_n / 2);
     int stages = (int)((kSmemLimit - 1024 - bar_bytes - aux_bytes - (int)w_bytes) / (int)stage_bytes);
     stages = std::min(stages, 8);
     if (stages < 2) {
@@ -459,9 +467,11 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
     }
     const bool multi = p.br.size() > 1;
     if (multi) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));
-    int64_t max_tiles = 1;
-    for (auto& b : p.br) max_tiles = std::max<int64_t>(max_tiles, ceil_div(b.m, tile_n));
-    RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * max_tiles));
+    // boundary partials per half-tile
+    const int half_n = tile_n / 2;
+    int64_t max_halves = 1;
+    for (auto& b : p.br) max_halves = std::max<int64_t>(max_halves, ceil_div(b.m, half_n));
+    RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * max_halves));
     const int rows_pad = m_blocks * 128;
     const size_t wp_elems = (size_t)rows_pad * L.n_kb * 64;
     RELNN_TRY(p.wpack.alloc(wp_elems * 2 + 256));
@@ -529,7 +539,6 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
         a.tile_n = tile_n;
         a.m_blocks = m_blocks;
         a.stages = stages;
-        a.lag = std::min(stages - 1, kMaxLag);
         a.idesc = tc::idesc_bf16_f32(128, tile_n);
         a.tmem_cols = (uint32_t)(2 * m_blocks * tile_n) <= 256 ? 256u : 512u;
         a.need_arr[0] = a.need_arr[1] = a.need_arr[2] = 0;
@@ -542,7 +551,7 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
         { ProfToken pt = prof_begin(RELNN_PROF_FWD_TC, st); fwd_tc_kernel<<<grid, kThreads, smem, st>>>(wmap, a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
-        launch_fixup(a.seg, a.m, tile_n, a.n_tiles, a.carry, out, p.d_out, multi, p.kahan, st);
+        launch_fixup(a.seg, a.m, half_n, ceil_div(a.m, half_n), a.carry, out, p.d_out, multi, p.kahan, st);
         RELNN_CUDA(cudaGetLastError());
     }
     return RELNN_OK;

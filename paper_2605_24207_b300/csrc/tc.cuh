@@ -88,6 +88,11 @@ __device__ __forceinline__ void cp_async_wait_n(int n) {
         default: cp_async_wait<7>(); break;
     }
 }
+// Arrive (without a pending-count increment) on `bar` once every cp.async this thread has issued so
+// far has completed; the thread does not wait.
+__device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
