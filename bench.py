@@ -21,6 +21,7 @@ All inputs are seeded synthetic relations (no dataset).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -67,9 +68,10 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """nvidia-smi sampler (every 20 ms, timestamped), started before the warm-up so that it is
+    running when the timed region begins; stop() keeps the samples taken inside [t0, t1]."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -77,14 +79,15 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
-    def stop(self):
+    def stop(self, t0: float, t1: float):
+        """Summary of the samples whose timestamp lies in [t0, t1] (time.time() seconds)."""
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.p.terminate()
         self.p.wait(timeout=10)
         self.f.flush()
@@ -95,11 +98,15 @@ class Clocks:
         for r in rows:
             r = [x.strip() for x in r]
             try:
-                sm.append(float(r[1]))
-                mx.append(float(r[2]))
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                f_sm, f_mx = float(r[2]), float(r[3])
             except (ValueError, IndexError):
                 continue
-            for n, v in zip(names, r[5:9]):
+            if not (t0 <= ts <= t1):
+                continue
+            sm.append(f_sm)
+            mx.append(f_mx)
+            for n, v in zip(names, r[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
@@ -762,17 +769,18 @@ def run_relnn(args):
     wl.to_device(dev)
 
     # ------------------------------------------------------------ timed region (device inputs)
+    clk = Clocks(local)
     for _ in range(args.warmup):
         wl.step()
     torch.cuda.synchronize()
     barrier()
-    clk = Clocks(local)
     R.profile_reset()
     R.profile_enable(True)
     n_launch0 = R.launch_count()
     torch.cuda.synchronize()
     barrier()
     t_wall0 = time.perf_counter()
+    t_epoch0 = time.time()
     e0.record(stream)
     keep = None
     for _ in range(args.steps):
@@ -780,10 +788,11 @@ def run_relnn(args):
     e1.record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
+    t_epoch1 = time.time()
     barrier()
     gpu_launches = R.launch_count() - n_launch0
     R.profile_enable(False)
-    clocks = clk.stop()
+    clocks = clk.stop(t_epoch0, t_epoch1)
     value, t_step = job_throughput(e0.elapsed_time(e1) / args.steps, wl.matched, dev)
     kid, kname, flops = wl.roofline_kernel()
     k_ms, k_n = R.profile_read(kid)

@@ -109,43 +109,77 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(Fp32Args a) {
     }
 }
 
-// One block per tile boundary b (1..n_tiles-1). The block that sees the FIRST boundary crossed by
-// a segment adds that segment's pieces in tile order and writes the output row.
+// One warp per tile boundary b (1..n_tiles-1). The warp that sees the FIRST boundary crossed by a
+// segment adds that segment's pieces in tile order and writes the output row. The five seg values
+// the decision needs are fetched by five lanes at once; the last tile whose first row lies in the
+// segment is the next tile unless the segment reaches past it (then one lane binary-searches).
 __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int tile, int64_t n_tiles,
                              const float* __restrict__ carry, float* __restrict__ out, int d_out,
-                             int accumulate, int kahan) {
-    __shared__ int64_t last_tile;
-    for (int64_t b = blockIdx.x + 1; b < n_tiles; b += gridDim.x) {
-        const int64_t row = b * tile;
-        if (row >= m) continue;
-        const int s = seg[row];
-        if (seg[row - 1] != s) continue;                         // boundary b cuts no segment
-        if (b >= 2 && seg[(b - 1) * tile - 1] == s) continue;    // not the first boundary of s
-        const int first_slot = (seg[(b - 1) * tile] == s) ? 0 : 1;
-        // last row of s (seg is non-decreasing): its tile is the last one whose first row is in s
-        if (threadIdx.x == 0) {
-            int64_t lo = row, hi = m;  // first row with seg > s lies in (row, m]
-            while (lo + 1 < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (seg[mid] == s) lo = mid;
-                else hi = mid;
+                             int accumulate, int kahan, int vec4) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) + 1; b < n_tiles; b += nwarps) {
+        const int64_t row = b * tile;  // < m because b < n_tiles = ceil(m / tile)
+        int v = -1;
+        if (lane == 0) v = seg[row];
+        else if (lane == 1) v = seg[row - 1];
+        else if (lane == 2) v = seg[(b - 1) * tile];
+        else if (lane == 3 && b >= 2) v = seg[(b - 1) * tile - 1];
+        else if (lane == 4 && row + tile < m) v = seg[row + tile];
+        const int s = __shfl_sync(0xffffffffu, v, 0);
+        const int s_before = __shfl_sync(0xffffffffu, v, 1);
+        const int s_prev_first = __shfl_sync(0xffffffffu, v, 2);
+        const int s_prev_before = __shfl_sync(0xffffffffu, v, 3);
+        const int s_next_first = __shfl_sync(0xffffffffu, v, 4);
+        if (s_before != s) continue;              // boundary b cuts no segment
+        if (b >= 2 && s_prev_before == s) continue;  // not the first boundary of s
+        const int first_slot = (s_prev_first == s) ? 0 : 1;
+        int64_t e = b;  // last tile whose first row is in s (seg is non-decreasing)
+        if (s_next_first == s) {
+            int64_t last = 0;
+            if (lane == 0) {
+                int64_t lo = row + tile, hi = m;  // seg[lo] == s; the first row past s lies in (lo, m]
+                while (lo + 1 < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (seg[mid] == s) lo = mid;
+                    else hi = mid;
+                }
+                last = lo;
             }
-            last_tile = lo / tile;
+            e = __shfl_sync(0xffffffffu, last, 0) / tile;
         }
-        __syncthreads();
-        const int64_t e = last_tile;
-        for (int o = threadIdx.x; o < d_out; o += blockDim.x) {
-            float acc = carry[((b - 1) * 2 + first_slot) * d_out + o];
-            float comp = 0.f;
-            for (int64_t j = b; j <= e; ++j) {  // tiles b..e all start inside s: their slot 0 piece
-                const float v = carry[(j * 2) * d_out + o];
-                if (kahan) kahan_add(acc, comp, v);
-                else acc += v;
+        const float* c0 = carry + ((b - 1) * 2 + first_slot) * (int64_t)d_out;
+        float* dst = out + (int64_t)s * d_out;
+        if (vec4) {
+            for (int o = lane * 4; o < d_out; o += 128) {
+                float4 acc = *reinterpret_cast<const float4*>(c0 + o);
+                float4 comp = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int64_t j = b; j <= e; ++j) {  // tiles b..e all start inside s: their slot 0 piece
+                    const float4 x = *reinterpret_cast<const float4*>(carry + (j * 2) * (int64_t)d_out + o);
+                    if (kahan) {
+                        kahan_add(acc.x, comp.x, x.x); kahan_add(acc.y, comp.y, x.y);
+                        kahan_add(acc.z, comp.z, x.z); kahan_add(acc.w, comp.w, x.w);
+                    } else {
+                        acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
+                    }
+                }
+                if (accumulate) {
+                    const float4 old = *reinterpret_cast<const float4*>(dst + o);
+                    acc.x += old.x; acc.y += old.y; acc.z += old.z; acc.w += old.w;
+                }
+                __stcg(reinterpret_cast<float4*>(dst + o), acc);
             }
-            float* dst = out + (int64_t)s * d_out + o;
-            emit_out(dst, acc, accumulate);
+        } else {
+            for (int o = lane; o < d_out; o += 32) {
+                float acc = c0[o], comp = 0.f;
+                for (int64_t j = b; j <= e; ++j) {
+                    const float x = carry[(j * 2) * (int64_t)d_out + o];
+                    if (kahan) kahan_add(acc, comp, x);
+                    else acc += x;
+                }
+                emit_out(dst + o, acc, accumulate);
+            }
         }
-        __syncthreads();
     }
 }
 
@@ -164,11 +198,13 @@ __global__ void transpose_w_kernel(const void* W, int w_bf16, int d_out, int d_i
 void launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,
                   float* out, int d_out, bool accumulate, bool kahan, cudaStream_t st) {
     if (n_tiles <= 1) return;
-    const int blocks = (int)std::min<int64_t>(n_tiles - 1, (int64_t)num_sms() * 8);
-    const int threads = d_out >= 128 ? 128 : (d_out > 32 ? ((d_out + 31) / 32) * 32 : 32);
+    // one warp per boundary, 8 warps per block
+    const int blocks = (int)std::min<int64_t>(ceil_div(n_tiles - 1, 8), (int64_t)num_sms() * 8);
+    const bool vec4 = d_out % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0 &&
+                      (reinterpret_cast<uintptr_t>(carry) & 15u) == 0;
     ProfToken pt = prof_begin(RELNN_PROF_FIXUP, st);
-    { fixup_kernel<<<blocks, threads, 0, st>>>(seg, m, tile, n_tiles, carry, out, d_out, accumulate ? 1 : 0,
-                                             kahan ? 1 : 0); note_launch(); }
+    { fixup_kernel<<<blocks, 256, 0, st>>>(seg, m, tile, n_tiles, carry, out, d_out, accumulate ? 1 : 0,
+                                         kahan ? 1 : 0, vec4 ? 1 : 0); note_launch(); }
     prof_end(pt, st);
 }
 
