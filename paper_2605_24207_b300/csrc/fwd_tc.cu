@@ -35,6 +35,8 @@ constexpr int kProducerThreads = 224;
 constexpr int kMmaWarp = 7;     // warps 0-6 produce, 8-15 are the epilogue
 constexpr int kEpiWarps = 8;
 constexpr int kIdxSlots = 3;    // row-index ring: the tile in production and the next two
+constexpr int kRowGroups = kProducerThreads / 8;                 // 28 rows per pass of the producers
+constexpr int kMaxRows = (256 + kRowGroups - 1) / kRowGroups;    // rows per producer thread per stage
 constexpr int kMaxKb = 12;
 constexpr int kSmemLimit = 227 * 1024;
 
@@ -111,9 +113,11 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
 
     if (warp < kProducerThreads / 32) {
         // ------------------------------------------------------------------ producers
-        // Copy e (row e / 8, 16-byte chunk e % 8) of a stage goes to thread e mod kProducerThreads,
-        // so the 8 lanes of a row read its 128-byte segment together (4 rows per warp instruction).
-        const int n_copies = a.tile_n * 8;
+        // Thread (row group rg, 16-byte chunk) copies chunk `chunk` of rows rg, rg + 28, rg + 56, ...
+        // of every K block, so the 8 lanes of a row read its 128-byte segment together (4 rows per
+        // warp instruction); the row indices of a stage are all loaded before the copies are issued.
+        const int chunk = tid & 7;
+        const int rg = tid >> 3;
         // cp.async of one tile's hs / hd / er entries (16 bytes each, zero-filled past m) into a slot;
         // committed as one group
         const int q_per_arr = a.tile_n / 4;
@@ -153,31 +157,61 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
                 const int row_elems = src == 2 ? a.d_r : a.d;
                 const uint32_t sbase = smem_u32(st_smem + (size_t)s * stage_bytes);
-                for (int e = tid; e < n_copies; e += kProducerThreads) {
-                    const int row = e >> 3, chunk = e & 7;
-                    const int col = a.kb_col[kb] + chunk * 8;
-                    const bool in_part = col < a.kb_width[kb];
-                    const uint32_t dst = sbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
-                    const bool valid = (t0 + row < a.m) && in_part;
-                    const int64_t ridx = rows_idx[row];
-                    if (tbl_bf16) {
-                        const uint16_t* p = reinterpret_cast<const uint16_t*>(tbl);
-                        const uint16_t* srcp = valid ? p + ridx * row_elems + col : p;
-                        if (src == 2) cp_async_16_stream(dst, srcp, valid ? 16u : 0u);
-                        else cp_async_16(dst, srcp, valid ? 16u : 0u);
-                    } else {
-                        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-                        if (valid) {
-                            const float4* qp = reinterpret_cast<const float4*>(
-                                reinterpret_cast<const float*>(tbl) + ridx * row_elems + col);
-                            const float4 u = __ldg(qp);
-                            const float4 v = __ldg(qp + 1);
-                            w0 = pack_bf16x2(u.x, u.y);
-                            w1 = pack_bf16x2(u.z, u.w);
-                            w2 = pack_bf16x2(v.x, v.y);
-                            w3 = pack_bf16x2(v.z, v.w);
+                const int col = a.kb_col[kb] + chunk * 8;
+                const bool in_part = col < a.kb_width[kb];
+                int32_t ridx[kMaxRows];
+#pragma unroll
+                for (int k = 0; k < kMaxRows; ++k) {
+                    const int row = rg + k * kRowGroups;
+                    ridx[k] = row < a.tile_n ? rows_idx[row] : 0;
+                }
+                // destination of row `row`: 128-byte line, 16-byte chunk swizzled by the row (SW128)
+                auto dst_of = [&](int row) {
+                    return sbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
+                };
+                if (tbl_bf16) {
+                    const uint16_t* p = reinterpret_cast<const uint16_t*>(tbl);
+                    if (src == 2) {
+#pragma unroll
+                        for (int k = 0; k < kMaxRows; ++k) {
+                            const int row = rg + k * kRowGroups;
+                            if (row >= a.tile_n) break;
+                            const bool valid = (t0 + row < a.m) && in_part;
+                            cp_async_16_stream(dst_of(row), valid ? p + (int64_t)ridx[k] * row_elems + col : p,
+                                               valid ? 16u : 0u);
                         }
-                        st_shared_v4(dst, w0, w1, w2, w3);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < kMaxRows; ++k) {
+                            const int row = rg + k * kRowGroups;
+                            if (row >= a.tile_n) break;
+                            const bool valid = (t0 + row < a.m) && in_part;
+                            cp_async_16(dst_of(row), valid ? p + (int64_t)ridx[k] * row_elems + col : p,
+                                        valid ? 16u : 0u);
+                        }
+                    }
+                } else {
+                    // f32 rows: five rows' loads in flight before their convert-and-store
+                    const float* pf32 = reinterpret_cast<const float*>(tbl);
+#pragma unroll
+                    for (int k0 = 0; k0 < kMaxRows; k0 += 5) {
+                        float4 u[5], w[5];
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            const int row = rg + (k0 + k) * kRowGroups;
+                            const bool valid = k0 + k < kMaxRows && row < a.tile_n && (t0 + row < a.m) && in_part;
+                            const float4* qp = reinterpret_cast<const float4*>(
+                                pf32 + (valid ? (int64_t)ridx[k0 + k < kMaxRows ? k0 + k : 0] * row_elems + col : 0));
+                            u[k] = valid ? __ldg(qp) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            w[k] = valid ? __ldg(qp + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            const int row = rg + (k0 + k) * kRowGroups;
+                            if (k0 + k >= kMaxRows || row >= a.tile_n) break;
+                            st_shared_v4(dst_of(row), pack_bf16x2(u[k].x, u[k].y), pack_bf16x2(u[k].z, u[k].w),
+                                         pack_bf16x2(w[k].x, w[k].y), pack_bf16x2(w[k].z, w[k].w));
+                        }
                     }
                 }
                 // The stage is complete for this thread when its copies have landed: cp.async sources
