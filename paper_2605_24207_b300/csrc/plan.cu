@@ -163,10 +163,10 @@ relnn_status emit_and_sort(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t
     const int64_t m1 = std::max<int64_t>(M, 1);
     RELNN_TRY(t.key.alloc_tmp(sizeof(K) * m1, st));
     RELNN_TRY(t.key_tmp.alloc_tmp(sizeof(K) * m1, st));
-    // payload buffers outlive the plan build: the sorted one becomes the branch's hs when it holds
-    // the src H row alone
-    RELNN_TRY(t.val.alloc_nosync(sizeof(V) * m1, st));
-    RELNN_TRY(t.val_tmp.alloc_nosync(sizeof(V) * m1, st));
+    // payload buffers are freed in stream order (kernels on st may still read them); the sorted
+    // one becomes the branch's hs when it holds the src H row alone
+    RELNN_TRY(t.val.alloc_tmp(sizeof(V) * m1, st));
+    RELNN_TRY(t.val_tmp.alloc_tmp(sizeof(V) * m1, st));
     if (T > 0) {
         const int blocks = (int)ceil_div(T, 256);
         { tri_emit_kernel<K, V><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin, us, ud, warp_off,
@@ -235,6 +235,8 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
         t.val_tmp.release();
     } else {
         b.hs = std::move(t.sorted_val());
+        b.hs.ordered = false;  // now a plan buffer: freed with the plan (after its work)
+        b.hs.st = nullptr;
         t.val.release();
         t.val_tmp.release();
     }
