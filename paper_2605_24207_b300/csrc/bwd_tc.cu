@@ -453,8 +453,8 @@ static bool tc_backward_supported(const Plan& p) {
     return kb <= kMaxKb;
 }
 
-relnn_status backward_tc(Plan& p, const CallIO& io, const GradIO& g, cudaStream_t st) {
-    if (!tc_backward_supported(p)) return backward_fp32(p, io, g, st);
+relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStream_t st) {
+    if (!tc_backward_supported(p)) return backward_fp32(p, io_in, g, st);
     RELNN_CHECK_ARG(g.dout, "backward: null output gradient");
     const bool relu = p.act == RELNN_ACT_RELU;
     // K-block layout of the Concat (each part starts on a 64-column block)
@@ -486,13 +486,16 @@ relnn_status backward_tc(Plan& p, const CallIO& io, const GradIO& g, cudaStream_
         stages = (int)((kSmemLimit - 1024 - 256 - (int)wt_bytes - (int)aux_of(64)) / (int)stage_of(64));
     }
     stages = std::min(stages, 6);
-    if (stages < 2) return backward_fp32(p, io, g, st);
+    if (stages < 2) return backward_fp32(p, io_in, g, st);
     const uint32_t d2_col = (uint32_t)((d_in_pad + 31) / 32 * 32);
     const uint32_t cols_needed = d2_col + 2u * mbk * N;
-    if (cols_needed > 512) return backward_fp32(p, io, g, st);
+    if (cols_needed > 512) return backward_fp32(p, io_in, g, st);
     const uint32_t tmem_cols = cols_needed <= 256 ? 256u : 512u;
     const size_t smem = 1024 + wt_bytes + (size_t)stages * stage_of(N) + aux_of(N) + 256;
 
+    // f32 z is gathered as a bf16 copy (the rounding the kernel applies anyway), by cp.async
+    CallIO io;
+    RELNN_TRY(with_bf16_z(p, io_in, io, st));
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled unavailable");

@@ -24,6 +24,11 @@ struct CallIO {
     std::vector<BranchIO> br;
 };
 
+// The f32 H embedding rounded to bf16 (nearest even, as the tensor-core kernels round operands)
+// in the plan's workspace, so that the tensor-core kernels gather it with cp.async; io.z unchanged
+// when it is bf16 already. Returns the CallIO to use.
+relnn_status with_bf16_z(Plan& p, const CallIO& io, CallIO& out, cudaStream_t st);
+
 relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 

@@ -391,6 +391,14 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
     }
 }
 
+// out[i] = bf16(z[i]) (round to nearest even), 4 elements per thread and step.
+__global__ void z_to_bf16_kernel(const float4* __restrict__ z, int64_t n4, uint2* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(z + i);
+        out[i] = make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
+    }
+}
+
 // W_pad[mb*128 + o][kb*64 + kk] (bf16) = W[o][k(kb, kk)] with zero padding.
 __global__ void pack_w_kernel(const void* W, int w_bf16, int d_out, int d_in, int rows_pad, int n_kb,
                               const int* kb_kofs, const int* kb_width_left, uint16_t* wp) {
@@ -460,7 +468,22 @@ static bool make_layout(const Plan& p, KbLayout& L) {
     return true;
 }
 
-relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
+relnn_status with_bf16_z(Plan& p, const CallIO& io, CallIO& out, cudaStream_t st) {
+    out = io;
+    // (an f32 table that is not 16-byte aligned keeps the kernels' convert-as-you-gather path)
+    if (io.z_bf16 || p.n_h == 0 || (reinterpret_cast<uintptr_t>(io.z) & 15u)) return RELNN_OK;
+    const int64_t n = p.n_h * (int64_t)p.d;  // d % 8 == 0 on the tensor-core path
+    RELNN_TRY(p.zbf.alloc(sizeof(uint16_t) * n));
+    const int64_t n4 = n / 4;
+    const int blocks = (int)std::min<int64_t>(ceil_div(n4, 256), (int64_t)num_sms() * 16);
+    { z_to_bf16_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(io.z), n4, p.zbf.as<uint2>()); note_launch(); }
+    RELNN_CUDA(cudaGetLastError());
+    out.z = p.zbf.p;
+    out.z_bf16 = 1;
+    return RELNN_OK;
+}
+
+relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t st) {
     if (p.identity) {
         set_error("BF16 form needs a Linear (identity rules run in the FP32 form)");
         return RELNN_ENOTSUP;
@@ -478,6 +501,8 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st) 
         set_error("BF16 form: Concat too wide");
         return RELNN_ENOTSUP;
     }
+    CallIO io;
+    RELNN_TRY(with_bf16_z(p, io_in, io, st));
     const int m_blocks = (p.d_out + 127) / 128;
     // 256 matched tuples per tile; 128 when d_out needs two TMEM blocks or the caller asks for
     // smaller tiles (more tiles per SM on small inputs)
