@@ -7,9 +7,14 @@
 //   GEMM B (dW):  D1[o][k] += sum_t dY[t][o] X[t][k]    M = output features, N = input features,
 //                 K = tuples; both operands read MN-major from the same staged dY and X tiles.
 // The gathered Concat X is regathered (not stored by the forward). The epilogue reads D2 (TMEM lane =
-// input feature, columns = tuples) and adds dX into dz / dr: per tuple for the src slice and r,
-// per run of equal dst row (a segmented sum in registers) for the dst slice. D1 accumulates over all
-// tiles of the CTA; each CTA writes its partial dW and a reduction kernel adds them in CTA order.
+// input feature, columns = tuples) and adds dX into dz / dr. D1 accumulates over all tiles of the
+// CTA; each CTA writes its partial dW and a reduction kernel adds them in CTA order.
+//
+// Two passes, so that dz receives one add per run of equal H rows rather than one per tuple:
+//   dst pass (tuples in output order, as the forward): the dst slice of dX, added once per run of
+//     equal dst rows (a segmented sum in registers), r per tuple, dW and db;
+//   src pass (the same tuples sorted by src H row, an order the plan caches): only GEMM A, and the
+//     src slice of dX added once per run of equal src rows.
 //
 // Roles (416 threads, one CTA per SM): warps 0-7 producers (dY: dOut rows -> mask -> bf16; X: rows
 // of z / r as in the forward; db partial sums), warp 8 TMEM allocation + MMA issue, warps 9-12
@@ -51,6 +56,8 @@ struct BwArgs {
     int64_t m, n_tiles;
     int z_bf16, r_bf16, d, d_r, d_in, d_out, concat_dst, mask_words;
     int n_kb, d_in_pad, mbk, tile_n, stages;
+    int src_pass;           // 1: tuples in src order; hd then holds each tuple's row in output order
+                            // (its ReLU mask row), hs the src H rows (non-decreasing), seg their output rows
     uint32_t idesc_dx, idesc_dw, tmem_cols, d2_col;
     int kb_src[kMaxKb], kb_col[kMaxKb], kb_width[kMaxKb];
     int need_arr[3];
@@ -156,6 +163,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                             const int row = row_base + j0 + jj;
                             const bool tv = (j0 + jj < rpt) && (t0 + row < a.m);
                             const int sg = tv ? islot[3 * N + row] : 0;
+                            const int64_t mrow = a.src_pass ? (int64_t)islot[N + row] : t0 + row;
 #pragma unroll
                             for (int ob = 0; ob < 2; ++ob) {
                                 const int o0 = ob * 64 + chunk * 8;
@@ -163,7 +171,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                                 const float4* q = reinterpret_cast<const float4*>(a.dout + (int64_t)sg * a.d_out + o0);
                                 u[jj][ob][0] = ld ? __ldg(q) : make_float4(0.f, 0.f, 0.f, 0.f);
                                 u[jj][ob][1] = ld ? __ldg(q + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-                                bits[jj][ob] = (ld && a.mask) ? __ldg(a.mask + (t0 + row) * a.mask_words + (o0 >> 5)) >> (o0 & 31)
+                                bits[jj][ob] = (ld && a.mask) ? __ldg(a.mask + mrow * a.mask_words + (o0 >> 5)) >> (o0 & 31)
                                                               : 0xffffffffu;
                             }
                         }
@@ -187,8 +195,8 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                             }
                         }
                     }
-                    // X rows, K-block by K-block (as in the forward)
-                    for (int kb = 0; kb < a.n_kb; ++kb) {
+                    // X rows, K-block by K-block (as in the forward); the src pass needs no dW
+                    for (int kb = 0; kb < (a.src_pass ? 0 : a.n_kb); ++kb) {
                         const int src = a.kb_src[kb];
                         const int col = a.kb_col[kb] + chunk * 8;
                         const bool in_part = col < a.kb_width[kb];
@@ -285,8 +293,8 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                             mma_bf16(d2 + (uint32_t)mb * N, ad, bd, a.idesc_dx, (kk | k) != 0);
                         }
                 mma_commit(smem_u32(&tfull[acc]));
-                // GEMM B: dW += dY^T X, 16 tuples per instruction
-                for (int step = 0; step < N / 16; ++step) {
+                // GEMM B: dW += dY^T X, 16 tuples per instruction (dst pass only)
+                for (int step = 0; step < (a.src_pass ? 0 : N / 16); ++step) {
                     const uint64_t ad = sw128_mnmajor_desc(dyb + (uint32_t)step * 2048u, (uint32_t)N * 128u);
                     const uint64_t bd = sw128_mnmajor_desc(xb + (uint32_t)step * 2048u, (uint32_t)N * 128u);
                     mma_bf16(tmem_base, ad, bd, a.idesc_dw, (lt > 0 || step > 0) ? 1u : 0u);
@@ -338,13 +346,15 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                     tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
                     tmem_ld_wait();
                     const int cnt = min(32, nt - c * 32);
-                    if (part == 1) {
-                        // runs of equal dst row inside the chunk (the tuples are dst-sorted): a
-                        // segmented running sum in registers, then one add per run end
+                    if ((part == 1 && !a.src_pass) || (part == 0 && a.src_pass)) {
+                        // runs of equal dst (dst pass) or src (src pass) H rows inside the chunk (the
+                        // tuples are sorted by it): a segmented running sum in registers, then one
+                        // add per run end
+                        const int32_t* keyv = part == 1 ? wix + N : wix;
                         const int li = c * 32 + lane;
-                        const int h = wix[N + li];
+                        const int h = keyv[li];
                         const bool tvalid = lane < cnt;
-                        const bool nx_diff = (lane == cnt - 1) || (li + 1 < N && wix[N + li + 1] != h);
+                        const bool nx_diff = (lane == cnt - 1) || (li + 1 < N && keyv[li + 1] != h);
                         const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && nx_diff);
                         const unsigned startmask = (endmask << 1) | 1u;
                         float sum = 0.f, comp = 0.f;
@@ -353,14 +363,11 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                         for (unsigned em = endmask; em; em &= em - 1u) {
                             const int j = __ffs(em) - 1;
                             const float val = __uint_as_float(select32(v, j));
-                            const int hj = wix[N + c * 32 + j];
+                            const int hj = keyv[c * 32 + j];
                             if (k_ok && a.dz) atomicAdd(a.dz + (int64_t)hj * a.d + kk, val);
                         }
-                    } else if (part == 0) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j < cnt && k_ok && a.dz)
-                                atomicAdd(a.dz + (int64_t)wix[c * 32 + j] * a.d + kk, __uint_as_float(v[j]));
+                    } else if (a.src_pass || part == 0) {
+                        // the other pass adds this slice
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
@@ -373,7 +380,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
             mbar_arrive(smem_u32(&tempty[acc]));
         }
         // this CTA's dW partial: TMEM lane o (output feature), columns k (input features)
-        if (ok && __all_sync(0xffffffffu, mbar_wait(smem_u32(dwdone), 0, a.status, abort_flag))) {
+        if (ok && a.dw_part && __all_sync(0xffffffffu, mbar_wait(smem_u32(dwdone), 0, a.status, abort_flag))) {
             tc_fence_after();
             const int o = 32 * q + lane;
             float* dst = a.dw_part + ((int64_t)blockIdx.x * a.d_out + o) * a.d_in;
@@ -592,6 +599,23 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         }
         { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<grid, kThreads, smem, st>>>(wtmap, a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
+        if (g.dz) {
+            // src pass: the src slice of dX over the tuples in src order, one add per run
+            RELNN_TRY(ensure_src_order(p, b, st));
+            BwArgs s2 = a;
+            s2.src_pass = 1;
+            s2.hs = b.hs_src.as<int32_t>();
+            s2.hd = b.src_perm.as<int32_t>();
+            s2.seg = b.seg_src.as<int32_t>();
+            s2.dr = nullptr;
+            s2.db = nullptr;
+            s2.dw_part = nullptr;
+            s2.need_arr[0] = 1;
+            s2.need_arr[1] = relu ? 1 : 0;
+            s2.need_arr[2] = 0;
+            { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<grid, kThreads, smem, st>>>(wtmap, s2); note_launch(); prof_end(pt, st); }
+            RELNN_CUDA(cudaGetLastError());
+        }
         if (dW) {
             const int64_t nw = (int64_t)p.d_out * p.d_in;
             { reduce_parts_kernel<<<(int)std::min<int64_t>(ceil_div(nw, 256), 1024), 256, 0, st>>>(part, grid, nw, dW); note_launch(); }

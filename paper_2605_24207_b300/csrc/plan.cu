@@ -143,6 +143,21 @@ __global__ void raw_seg_kernel(const K* key, const int32_t* flags_excl, int64_t 
     }
 }
 
+// (src H row, position) pairs of the grouped tuples, to be sorted into src order.
+__global__ void src_pairs_kernel(const int32_t* hs, int64_t m, uint32_t* key, int32_t* val) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        key[i] = (uint32_t)hs[i];
+        val[i] = (int32_t)i;
+    }
+}
+
+__global__ void gather_i32_kernel(const int32_t* src, const int32_t* idx, int64_t m, int32_t* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = src[idx[i]];
+}
+
 // Branch-local matched tuples while they are grouped: group keys (u32 dst position or u32/u64 raw
 // key) and payloads (int32 src H row, or int64 src H row << 32 | E row).
 struct Tmp {
@@ -247,6 +262,28 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
 }
 
 }  // namespace
+
+relnn_status ensure_src_order(const Plan& p, BranchPlan& b, cudaStream_t st) {
+    if (b.src_perm.p || b.m == 0) return RELNN_OK;
+    const int64_t M = b.m;
+    DevBuf key, key_tmp, val_tmp;
+    RELNN_TRY(key.alloc_tmp(sizeof(uint32_t) * M, st));
+    RELNN_TRY(key_tmp.alloc_tmp(sizeof(uint32_t) * M, st));
+    RELNN_TRY(val_tmp.alloc_tmp(sizeof(int32_t) * M, st));
+    RELNN_TRY(b.src_perm.alloc_nosync(sizeof(int32_t) * M, st));
+    RELNN_TRY(b.hs_src.alloc_nosync(sizeof(int32_t) * M, st));
+    RELNN_TRY(b.seg_src.alloc_nosync(sizeof(int32_t) * M, st));
+    { src_pairs_kernel<<<grid_for(M), 256, 0, st>>>(b.hs.as<int32_t>(), M, key.as<uint32_t>(), b.src_perm.as<int32_t>()); note_launch(); }
+    RELNN_TRY((radix_sort_pairs<uint32_t, int32_t>(key.as<uint32_t>(), b.src_perm.as<int32_t>(), key_tmp.as<uint32_t>(),
+                                                    val_tmp.as<int32_t>(), M,
+                                                    bit_length((uint64_t)std::max<int64_t>(p.n_h - 1, 0)), st)));
+    RELNN_CUDA(cudaMemcpyAsync(b.hs_src.p, key.p, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st));
+    { gather_i32_kernel<<<grid_for(M), 256, 0, st>>>(b.seg.as<int32_t>(), b.src_perm.as<int32_t>(), M, b.seg_src.as<int32_t>()); note_launch(); }
+    RELNN_CUDA(cudaGetLastError());
+    // the plan's buffers are used on other streams later
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    return RELNN_OK;
+}
 
 relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     RELNN_CHECK_ARG(desc, "rule plan: null descriptor");

@@ -8,7 +8,11 @@
 //   seg[m]  int32  output row of the tuple (position of its dst key among the output keys)
 // Within one output key the tuples are ordered by dst H row, then E row, then src H row, so runs of
 // equal hd are contiguous (used by the backward's scatter to z_dst). er is kept only for branches
-// with a per-tuple embedding r (d_r > 0).
+// with a per-tuple embedding r (d_r > 0). For the backward's scatter to z_src the same tuples are
+// also kept in src order (built on the first backward, stable):
+//   src_perm[m] int32  position in the order above of the k-th tuple in src order
+//   hs_src[m]   int32  its src H row (non-decreasing)
+//   seg_src[m]  int32  its output row
 #pragma once
 
 #include <vector>
@@ -22,6 +26,7 @@ struct BranchPlan {
     int64_t m = 0;  // matched tuples
     int32_t d_r = 0;
     DevBuf hs, hd, er, seg;
+    DevBuf src_perm, hs_src, seg_src;
     DevBuf relu_mask;  // uint32 [m][ceil(d_out/32)] when RELNN_FLAG_RELU_MASK
 };
 
@@ -57,7 +62,7 @@ struct Plan {
             b->st = s;
         }
         for (auto& b : br) {
-            DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.relu_mask};
+            DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.src_perm, &b.hs_src, &b.seg_src, &b.relu_mask};
             for (DevBuf* x : bb) {
                 x->ordered = true;
                 x->st = s;
@@ -67,6 +72,9 @@ struct Plan {
 };
 
 relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st);
+
+// Builds b.src_perm / hs_src / seg_src once (no-op afterwards); synchronises st when it builds.
+relnn_status ensure_src_order(const Plan& p, BranchPlan& b, cudaStream_t st);
 
 }  // namespace relnn
 
