@@ -88,6 +88,127 @@ __global__ void tri_emit_kernel(JoinView j, const void* dst, int64_t T, int kt, 
     }
 }
 
+// Unique H keys (every tuple matches at most once): pass 1 and 2 in one. A block takes the next tile
+// of kEmitTile consecutive E rows (tile numbers are handed out in launch order), counts its matches,
+// publishes the count, adds the counts of the tiles before it (a decoupled look-back that waits,
+// bounded, for tiles still counting) and writes its pairs in E order: the same output as the
+// two passes, without storing the per-tuple lookups.
+constexpr int kEmitThreads = 256;
+constexpr int kEmitItems = 8;  // consecutive E rows per thread
+constexpr int kEmitTile = kEmitThreads * kEmitItems;
+constexpr unsigned long long kTileAgg = 1ull << 62, kTileInc = 2ull << 62, kTileVal = (1ull << 62) - 1;
+
+template <class K, class V>
+__global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
+    JoinView j, const void* src, const void* dst, int64_t T, int kt, bool join_dst, uint64_t omin,
+    unsigned* tile_ctr, unsigned long long* tile_state, unsigned long long* total, int* status, K* t_key, V* t_val) {
+    __shared__ int tile_s;
+    __shared__ int warp_tot[kEmitThreads / 32];
+    __shared__ long long base_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) tile_s = (int)atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const int tile = tile_s;
+    const int64_t e0 = (int64_t)tile * kEmitTile + (int64_t)threadIdx.x * kEmitItems;
+    int64_t ks[kEmitItems], kd[kEmitItems];
+#pragma unroll
+    for (int i = 0; i < kEmitItems; ++i) {
+        const int64_t e = e0 + i;
+        ks[i] = e < T ? load_key(src, kt, e) : 0;
+        kd[i] = (e < T && join_dst) ? load_key(dst, kt, e) : 0;
+    }
+    int32_t a[kEmitItems], bb[kEmitItems];
+    int cnt = 0;
+    if (j.mode == 1) {  // direct addressing: independent table reads
+#pragma unroll
+        for (int i = 0; i < kEmitItems; ++i) {
+            const uint64_t os = (uint64_t)ks[i] - (uint64_t)j.key_min, od = (uint64_t)kd[i] - (uint64_t)j.key_min;
+            a[i] = os < (uint64_t)j.direct_size ? __ldg(j.slot_vals + os) : -1;
+            bb[i] = !join_dst ? 0 : (od < (uint64_t)j.direct_size ? __ldg(j.slot_vals + od) : -1);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kEmitItems; ++i) {
+            a[i] = j.lookup(ks[i]);
+            bb[i] = join_dst ? j.lookup(kd[i]) : 0;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kEmitItems; ++i) {
+        if (e0 + i >= T) a[i] = -1;
+        cnt += (a[i] >= 0 && bb[i] >= 0) ? 1 : 0;
+    }
+    // block-wide exclusive scan of the per-thread counts
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int woff = 0, btot = 0;
+#pragma unroll
+    for (int w = 0; w < kEmitThreads / 32; ++w) {
+        woff += w < warp ? warp_tot[w] : 0;
+        btot += warp_tot[w];
+    }
+    if (warp == 0) {
+        // warp-wide look-back: 32 predecessors per step, nearest first (lane 0 = tile - 1)
+        long long excl = 0;
+        if (lane == 0) atomicExch(&tile_state[tile], (tile == 0 ? kTileInc : kTileAgg) | (unsigned long long)btot);
+        int window = tile - 1;
+        const unsigned long long t_start = globaltimer_ns();
+        unsigned spins = 0;
+        while (window >= 0) {
+            const int idx = window - lane;
+            unsigned long long w = kTileInc | 0ull;  // before tile 0: an inclusive zero
+            if (idx >= 0) w = *reinterpret_cast<volatile unsigned long long*>(&tile_state[idx]);
+            const unsigned flag = (unsigned)(w >> 62);
+            if (__any_sync(0xffffffffu, flag == 0)) {  // a predecessor is still counting
+                if ((++spins & 63u) == 0 && globaltimer_ns() - t_start > kWaitBudgetNs) {
+                    if (lane == 0) raise_status(status, RELNN_DEV_TIMEOUT);
+                    break;
+                }
+                continue;
+            }
+            const unsigned inc_mask = __ballot_sync(0xffffffffu, flag == 2);
+            const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;  // lanes 0..stop contribute
+            long long v = lane <= stop ? (long long)(w & kTileVal) : 0;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            excl += v;
+            if (inc_mask) break;
+            window -= 32;
+        }
+        if (lane == 0) {
+            if (tile > 0) atomicExch(&tile_state[tile], kTileInc | (unsigned long long)(excl + btot));
+            atomicAdd(total, (unsigned long long)btot);
+            base_s = excl;
+        }
+    }
+    __syncthreads();
+    int64_t pos = base_s + woff + (incl - cnt);
+    // unique keys: a key's distinct index is its sorted position, so rd = run_start[b] = b and the
+    // src H row is rows_sorted[a]
+    int32_t hsv[kEmitItems];
+#pragma unroll
+    for (int i = 0; i < kEmitItems; ++i) hsv[i] = (a[i] >= 0 && bb[i] >= 0) ? __ldg(j.rows_sorted + a[i]) : 0;
+#pragma unroll
+    for (int i = 0; i < kEmitItems; ++i) {
+        if (a[i] < 0 || bb[i] < 0) continue;
+        const int64_t e = e0 + i;
+        const int32_t hs = hsv[i];
+        V val;
+        if (sizeof(V) == 8) val = (V)(((uint64_t)(uint32_t)hs << 32) | (uint32_t)e);
+        else val = (V)hs;
+        if (join_dst) t_key[pos] = (K)bb[i];
+        else t_key[pos] = (K)(ordered64(load_key(dst, kt, e)) - omin);
+        t_val[pos] = val;
+        ++pos;
+    }
+}
+
 // Splits (src H row << 32 | E row) payloads into hs / er.
 __global__ void split_pair_kernel(const int64_t* val, int64_t m, int32_t* hs, int32_t* er) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
@@ -171,49 +292,79 @@ struct Tmp {
     DevBuf& sorted_val() { return in_tmp ? val_tmp : val; }
 };
 
+// Emits the matched tuples as (group key, payload) pairs into t.key / t.val and returns their count
+// in *M. Unique H keys: one pass (buffers sized for every E row); otherwise a counting pass first.
 template <class K, class V>
-relnn_status emit_and_sort(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t T, int64_t M, int nbits,
-                           const int32_t* us, const int32_t* ud, const int64_t* warp_off, cudaStream_t st) {
+relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M_out, cudaStream_t st) {
+    const int64_t T = bd.n_tuples;
     const JoinView v = p.H.view();
-    const int64_t m1 = std::max<int64_t>(M, 1);
-    RELNN_TRY(t.key.alloc_tmp(sizeof(K) * m1, st));
-    RELNN_TRY(t.key_tmp.alloc_tmp(sizeof(K) * m1, st));
-    // payload buffers are freed in stream order (kernels on st may still read them); the sorted
-    // one becomes the branch's hs when it holds the src H row alone
-    RELNN_TRY(t.val.alloc_tmp(sizeof(V) * m1, st));
-    RELNN_TRY(t.val_tmp.alloc_tmp(sizeof(V) * m1, st));
-    if (T > 0) {
-        const int blocks = (int)ceil_div(T, 256);
-        { tri_emit_kernel<K, V><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin, us, ud, warp_off,
-                                                      t.key.as<K>(), t.val.as<V>()); note_launch(); }
-        RELNN_CUDA(cudaGetLastError());
+    int64_t M = 0;
+    if (p.H.n_unique == p.n_h) {
+        const int64_t cap = std::max<int64_t>(T, 1);
+        RELNN_TRY(t.key.alloc_tmp(sizeof(K) * cap, st));
+        RELNN_TRY(t.key_tmp.alloc_tmp(sizeof(K) * cap, st));
+        RELNN_TRY(t.val.alloc_tmp(sizeof(V) * cap, st));
+        RELNN_TRY(t.val_tmp.alloc_tmp(sizeof(V) * cap, st));
+        if (T > 0) {
+            const int64_t n_tiles = ceil_div(T, kEmitTile);
+            DevBuf ctl;  // tile states, tile counter, total
+            const size_t ctl_bytes = sizeof(unsigned long long) * (n_tiles + 2);
+            RELNN_TRY(ctl.alloc_tmp(ctl_bytes, st));
+            RELNN_CUDA(cudaMemsetAsync(ctl.p, 0, ctl_bytes, st));
+            unsigned long long* st_words = ctl.as<unsigned long long>();
+            { emit_unique_kernel<K, V><<<(unsigned)n_tiles, kEmitThreads, 0, st>>>(
+                v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst, t.omin, reinterpret_cast<unsigned*>(st_words + n_tiles),
+                st_words, st_words + n_tiles + 1, p.status.as<int>(), t.key.as<K>(), t.val.as<V>()); note_launch(); }
+            RELNN_CUDA(cudaGetLastError());
+            unsigned long long Mu = 0;
+            RELNN_CUDA(cudaMemcpyAsync(&Mu, st_words + n_tiles + 1, sizeof(Mu), cudaMemcpyDeviceToHost, st));
+            RELNN_CUDA(cudaStreamSynchronize(st));
+            M = (int64_t)Mu;
+        }
+    } else {
+        const int64_t nwarps = ceil_div(std::max<int64_t>(T, 1), 32);
+        DevBuf us, ud, wt;
+        RELNN_TRY(us.alloc_tmp(sizeof(int32_t) * std::max<int64_t>(T, 1), st));
+        RELNN_TRY(ud.alloc_tmp(sizeof(int32_t) * std::max<int64_t>(T, 1), st));
+        RELNN_TRY(wt.alloc_tmp(sizeof(int64_t) * (nwarps + 1), st));
+        RELNN_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(int64_t) * (nwarps + 1), st));
+        const int blocks = (int)ceil_div(std::max<int64_t>(T, 1), 256);
+        if (T > 0)
+            { tri_count_kernel<<<blocks, 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst,
+                                                     us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>()); note_launch(); }
+        RELNN_TRY(exclusive_scan<int64_t>(wt.as<int64_t>(), wt.as<int64_t>(), nwarps, wt.as<int64_t>() + nwarps, st));
+        RELNN_CUDA(cudaMemcpyAsync(&M, wt.as<int64_t>() + nwarps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        RELNN_CUDA(cudaStreamSynchronize(st));
+        if (M >= (1ll << 31) - 1) {
+            *M_out = M;
+            return RELNN_OK;  // rejected by the caller
+        }
+        const int64_t m1 = std::max<int64_t>(M, 1);
+        RELNN_TRY(t.key.alloc_tmp(sizeof(K) * m1, st));
+        RELNN_TRY(t.key_tmp.alloc_tmp(sizeof(K) * m1, st));
+        RELNN_TRY(t.val.alloc_tmp(sizeof(V) * m1, st));
+        RELNN_TRY(t.val_tmp.alloc_tmp(sizeof(V) * m1, st));
+        if (T > 0) {
+            { tri_emit_kernel<K, V><<<blocks, 256, 0, st>>>(v, bd.d_dst, T, p.kt, p.join_dst, t.omin, us.as<int32_t>(),
+                                                          ud.as<int32_t>(), wt.as<int64_t>(), t.key.as<K>(),
+                                                          t.val.as<V>()); note_launch(); }
+            RELNN_CUDA(cudaGetLastError());
+        }
     }
-    return radix_sort_pairs<K, V>(t.key.as<K>(), t.val.as<V>(), t.key_tmp.as<K>(), t.val_tmp.as<V>(), M, nbits, st,
+    *M_out = M;
+    return RELNN_OK;
+}
+
+template <class K, class V>
+relnn_status emit_and_sort(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M, int nbits, cudaStream_t st) {
+    RELNN_TRY((emit_pairs<K, V>(p, bd, t, M, st)));
+    if (*M >= (1ll << 31) - 1) return RELNN_OK;
+    return radix_sort_pairs<K, V>(t.key.as<K>(), t.val.as<V>(), t.key_tmp.as<K>(), t.val_tmp.as<V>(), *M, nbits, st,
                                   &t.in_tmp);
 }
 
 relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tmp& t, cudaStream_t st) {
     const int64_t T = bd.n_tuples;
-    const JoinView v = p.H.view();
-    const int64_t nwarps = ceil_div(std::max<int64_t>(T, 1), 32);
-    DevBuf us, ud, wt;
-    RELNN_TRY(us.alloc_tmp(sizeof(int32_t) * std::max<int64_t>(T, 1), st));
-    RELNN_TRY(ud.alloc_tmp(sizeof(int32_t) * std::max<int64_t>(T, 1), st));
-    RELNN_TRY(wt.alloc_tmp(sizeof(int64_t) * (nwarps + 1), st));
-    RELNN_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(int64_t) * (nwarps + 1), st));
-    const int blocks = (int)ceil_div(std::max<int64_t>(T, 1), 256);
-    if (T > 0)
-        { tri_count_kernel<<<blocks, 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst,
-                                                 us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>()); note_launch(); }
-    RELNN_TRY(exclusive_scan<int64_t>(wt.as<int64_t>(), wt.as<int64_t>(), nwarps, wt.as<int64_t>() + nwarps, st));
-    int64_t M = 0;
-    RELNN_CUDA(cudaMemcpyAsync(&M, wt.as<int64_t>() + nwarps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    RELNN_CUDA(cudaStreamSynchronize(st));
-    if (M >= (1ll << 31) - 1) {
-        set_error("rule plan: join output of " + std::to_string(M) + " tuples exceeds 2^31-1");
-        return RELNN_ENOTSUP;
-    }
-    b.m = M;
     // group key width: dst sorted position (n_h < 2^31) or the raw dst key span
     int nbits = 0;
     if (p.join_dst) {
@@ -228,16 +379,19 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
         t.wide = nbits > 32;
     }
     t.pair = b.d_r > 0;
-    const int32_t* usp = us.as<int32_t>();
-    const int32_t* udp = ud.as<int32_t>();
-    const int64_t* wo = wt.as<int64_t>();
+    int64_t M = 0;
     if (t.wide) {
-        if (t.pair) RELNN_TRY((emit_and_sort<uint64_t, int64_t>(p, bd, t, T, M, nbits, usp, udp, wo, st)));
-        else RELNN_TRY((emit_and_sort<uint64_t, int32_t>(p, bd, t, T, M, nbits, usp, udp, wo, st)));
+        if (t.pair) RELNN_TRY((emit_and_sort<uint64_t, int64_t>(p, bd, t, &M, nbits, st)));
+        else RELNN_TRY((emit_and_sort<uint64_t, int32_t>(p, bd, t, &M, nbits, st)));
     } else {
-        if (t.pair) RELNN_TRY((emit_and_sort<uint32_t, int64_t>(p, bd, t, T, M, nbits, usp, udp, wo, st)));
-        else RELNN_TRY((emit_and_sort<uint32_t, int32_t>(p, bd, t, T, M, nbits, usp, udp, wo, st)));
+        if (t.pair) RELNN_TRY((emit_and_sort<uint32_t, int64_t>(p, bd, t, &M, nbits, st)));
+        else RELNN_TRY((emit_and_sort<uint32_t, int32_t>(p, bd, t, &M, nbits, st)));
     }
+    if (M >= (1ll << 31) - 1) {
+        set_error("rule plan: join output of " + std::to_string(M) + " tuples exceeds 2^31-1");
+        return RELNN_ENOTSUP;
+    }
+    b.m = M;
     // hs / er from the sorted payloads; hd and seg follow once the output rows are known
     const int64_t m1 = std::max<int64_t>(M, 1);
     if (t.pair) {
@@ -332,6 +486,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     }
 
     // output key set and output row of every matched tuple
+    int32_t nout_join = 0;
     if (p.join_dst) {
         DevBuf present;
         RELNN_TRY(present.alloc_tmp(sizeof(int32_t) * (U + 1), st));
@@ -343,11 +498,9 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
                 { mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
                     tmp[i].keys<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), present.as<int32_t>()); note_launch(); }
         RELNN_TRY(exclusive_scan<int32_t>(present.as<int32_t>(), out_row.as<int32_t>(), U, out_row.as<int32_t>() + U, st));
-        int32_t nout = 0;
-        RELNN_CUDA(cudaMemcpyAsync(&nout, out_row.as<int32_t>() + U, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        RELNN_CUDA(cudaStreamSynchronize(st));
-        p.n_out = nout;
-        RELNN_TRY(p.out_keys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(nout, 1), st));
+        // the output-row count arrives with the final synchronisation; U bounds it
+        RELNN_CUDA(cudaMemcpyAsync(&nout_join, out_row.as<int32_t>() + U, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RELNN_TRY(p.out_keys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(U, 1), st));
         if (U > 0)
             { out_keys_kernel<<<grid_for(U), 256, 0, st>>>(present.as<int32_t>(), out_row.as<int32_t>(),
                                                          p.H.ukeys.as<int64_t>(), U, p.out_keys.as<int64_t>()); note_launch(); }
@@ -357,7 +510,6 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
                     tmp[i].keys<uint32_t>(), p.br[i].m, p.H.rows_sorted.as<int32_t>(), p.H.uid_of_pos.as<int32_t>(),
                     out_row.as<int32_t>(), p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>()); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
-        RELNN_CUDA(cudaStreamSynchronize(st));
     } else {
         BranchPlan& b = p.br[0];
         Tmp& t = tmp[0];
@@ -385,7 +537,16 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
                                                                       t.omin, b.seg.as<int32_t>(), p.out_keys.as<int64_t>()); note_launch(); }
         }
         RELNN_CUDA(cudaGetLastError());
-        RELNN_CUDA(cudaStreamSynchronize(st));
+    }
+    // device-side checks of the plan kernels (a look-back that gave up), with the final sync
+    int dev_status = 0;
+    RELNN_CUDA(cudaMemcpyAsync(&dev_status, p.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    if (p.join_dst) p.n_out = nout_join;
+    if (dev_status) {
+        set_device_error(dev_status);
+        set_error("rule plan: device check failed");
+        return RELNN_EDEVICE;
     }
     return RELNN_OK;
 }
