@@ -109,6 +109,118 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(Fp32Args a) {
     }
 }
 
+// Narrow widths (d_in <= DIN, d_out <= DOUT): lane = tuple. A warp owns a 32-tuple tile; each lane
+// loads its tuple's Concat row into registers, computes its d_out outputs with W^T broadcast from
+// shared memory (4 outputs per shared load), and the SUM over each run of equal output rows is a
+// segmented scan across the lanes (5 shuffle steps, the segment pattern computed once per tile).
+// The lane holding a run's last tuple writes the row (or the tile-boundary partial).
+template <int DIN, int DOUT>
+__global__ void __launch_bounds__(256) fwd_fp32_lane_kernel(Fp32Args a) {
+    extern __shared__ float sm[];
+    float* Ws = sm;                        // [d_in][DOUT] (zero beyond d_out), when there is a W
+    float* bs = sm + DIN * DOUT;           // [DOUT]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (a.Wt) {
+        for (int i = threadIdx.x; i < DIN * DOUT; i += blockDim.x) {
+            const int k = i / DOUT, o = i - k * DOUT;
+            Ws[i] = (k < a.d_in && o < a.d_out) ? a.Wt[k * a.d_out + o] : 0.f;
+        }
+    }
+    for (int o = threadIdx.x; o < DOUT; o += blockDim.x) bs[o] = (a.bias && o < a.d_out) ? a.bias[o] : 0.f;
+    __syncthreads();
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < a.n_tiles; tile += warps_total) {
+        const int64_t t = tile * 32 + lane;
+        const bool tv = t < a.m;
+        const int nt = (int)imin64(32, a.m - tile * 32);
+        // this lane's Concat row (z[hs] | z[hd] | r[er])
+        float x[DIN];
+        const int64_t rs = tv ? (int64_t)a.hs[t] * a.d : 0;
+        const int64_t rd = (tv && a.concat_dst) ? (int64_t)a.hd[t] * a.d : 0;
+        const int64_t rr = (tv && a.d_r > 0) ? (int64_t)a.er[t] * a.d_r : 0;
+        const int kr0 = a.concat_dst ? 2 * a.d : a.d;
+#pragma unroll
+        for (int k = 0; k < DIN; ++k) {
+            float v = 0.f;
+            if (tv && k < a.d_in) {
+                if (k < a.d) v = load_elem(a.z, a.z_bf16, rs + k);
+                else if (k < kr0) v = load_elem(a.z, a.z_bf16, rd + (k - a.d));
+                else v = load_elem(a.r, a.r_bf16, rr + (k - kr0));
+            }
+            x[k] = v;
+        }
+        float y[DOUT];
+        if (a.Wt) {
+#pragma unroll
+            for (int o = 0; o < DOUT; ++o) y[o] = bs[o];
+#pragma unroll
+            for (int k = 0; k < DIN; ++k) {
+                const float4* wr = reinterpret_cast<const float4*>(Ws + k * DOUT);
+#pragma unroll
+                for (int o4 = 0; o4 < DOUT / 4; ++o4) {
+                    const float4 w = wr[o4];
+                    y[4 * o4 + 0] = fmaf(x[k], w.x, y[4 * o4 + 0]);
+                    y[4 * o4 + 1] = fmaf(x[k], w.y, y[4 * o4 + 1]);
+                    y[4 * o4 + 2] = fmaf(x[k], w.z, y[4 * o4 + 2]);
+                    y[4 * o4 + 3] = fmaf(x[k], w.w, y[4 * o4 + 3]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < DOUT; ++o) y[o] = o < DIN ? x[o < DIN ? o : 0] : 0.f;
+        }
+        if (a.act == RELNN_ACT_RELU) {
+#pragma unroll
+            for (int o = 0; o < DOUT; ++o) y[o] = fmaxf(y[o], 0.f);
+        }
+        if (!tv) {
+#pragma unroll
+            for (int o = 0; o < DOUT; ++o) y[o] = 0.f;
+        }
+        // segment pattern of the tile: lane adds the value d lanes up at step d unless a run
+        // start lies in between
+        const int sg = tv ? a.seg[t] : -1;
+        const int sg_prev = __shfl_up_sync(0xffffffffu, sg, 1);
+        bool head = lane == 0 || sg_prev != sg;
+        unsigned add_mask[5];
+#pragma unroll
+        for (int st = 0; st < 5; ++st) {
+            const int dd = 1 << st;
+            const bool up_head = __shfl_up_sync(0xffffffffu, head ? 1 : 0, dd) != 0;
+            const bool add = lane >= dd && !head;
+            add_mask[st] = add ? 1u : 0u;
+            head = head || (add && up_head);
+        }
+#pragma unroll
+        for (int o = 0; o < DOUT; ++o) {
+#pragma unroll
+            for (int st = 0; st < 5; ++st) {
+                const float u = __shfl_up_sync(0xffffffffu, y[o], 1 << st);
+                if (add_mask[st]) y[o] += u;
+            }
+        }
+        // run ends: the next tuple has another output row, or the tile's last tuple
+        const int sg_next = __shfl_down_sync(0xffffffffu, sg, 1);
+        const bool last = lane == nt - 1;
+        const bool end = tv && (last || sg_next != sg);
+        const unsigned endmask = __ballot_sync(0xffffffffu, end);
+        if (end) {
+            const int prev_seg = (tile > 0) ? a.seg[tile * 32 - 1] : -1;
+            const int next_seg = (tile * 32 + nt < a.m) ? a.seg[tile * 32 + nt] : -1;
+            const bool first_piece = (endmask & ((1u << lane) - 1u)) == 0;  // the tile's first run
+            const bool split = (first_piece && prev_seg == sg) || (last && next_seg == sg);
+            float* dst = split ? a.carry + (tile * 2 + (first_piece ? 0 : 1)) * a.d_out
+                               : a.out + (int64_t)sg * a.d_out;
+#pragma unroll
+            for (int o = 0; o < DOUT; ++o)
+                if (o < a.d_out) {
+                    if (split) __stcg(dst + o, y[o]);
+                    else emit_out(dst + o, y[o], a.accumulate);
+                }
+        }
+    }
+}
+
 // One warp per tile boundary b (1..n_tiles-1). The warp that sees the FIRST boundary crossed by a
 // segment adds that segment's pieces in tile order and writes the output row. The five seg values
 // the decision needs are fetched by five lanes at once; the last tile whose first row lies in the
@@ -152,15 +264,50 @@ __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int til
         float* dst = out + (int64_t)s * d_out;
         if (vec4) {
             for (int o = lane * 4; o < d_out; o += 128) {
-                float4 acc = *reinterpret_cast<const float4*>(c0 + o);
-                float4 comp = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int64_t j = b; j <= e; ++j) {  // tiles b..e all start inside s: their slot 0 piece
+                // tiles b..e all start inside s (their slot 0 piece); long segments are summed in 8
+                // interleaved partial sums (independent loads), combined in order at the end
+                constexpr int kP = 8;
+                float4 ps[kP], pc[kP];
+#pragma unroll
+                for (int u = 0; u < kP; ++u) {
+                    ps[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    pc[u] = ps[u];
+                }
+                int64_t j = b;
+                for (; j + kP - 1 <= e; j += kP) {
+                    float4 x[kP];
+#pragma unroll
+                    for (int u = 0; u < kP; ++u) x[u] = *reinterpret_cast<const float4*>(carry + ((j + u) * 2) * (int64_t)d_out + o);
+#pragma unroll
+                    for (int u = 0; u < kP; ++u) {
+                        if (kahan) {
+                            kahan_add(ps[u].x, pc[u].x, x[u].x); kahan_add(ps[u].y, pc[u].y, x[u].y);
+                            kahan_add(ps[u].z, pc[u].z, x[u].z); kahan_add(ps[u].w, pc[u].w, x[u].w);
+                        } else {
+                            ps[u].x += x[u].x; ps[u].y += x[u].y; ps[u].z += x[u].z; ps[u].w += x[u].w;
+                        }
+                    }
+                }
+                for (; j <= e; ++j) {
                     const float4 x = *reinterpret_cast<const float4*>(carry + (j * 2) * (int64_t)d_out + o);
                     if (kahan) {
-                        kahan_add(acc.x, comp.x, x.x); kahan_add(acc.y, comp.y, x.y);
-                        kahan_add(acc.z, comp.z, x.z); kahan_add(acc.w, comp.w, x.w);
+                        kahan_add(ps[0].x, pc[0].x, x.x); kahan_add(ps[0].y, pc[0].y, x.y);
+                        kahan_add(ps[0].z, pc[0].z, x.z); kahan_add(ps[0].w, pc[0].w, x.w);
                     } else {
-                        acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
+                        ps[0].x += x.x; ps[0].y += x.y; ps[0].z += x.z; ps[0].w += x.w;
+                    }
+                }
+                float4 acc = *reinterpret_cast<const float4*>(c0 + o);
+                float4 comp = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < kP; ++u) {
+                    if (kahan) {
+                        kahan_add(acc.x, comp.x, ps[u].x); kahan_add(acc.x, comp.x, -pc[u].x);
+                        kahan_add(acc.y, comp.y, ps[u].y); kahan_add(acc.y, comp.y, -pc[u].y);
+                        kahan_add(acc.z, comp.z, ps[u].z); kahan_add(acc.z, comp.z, -pc[u].z);
+                        kahan_add(acc.w, comp.w, ps[u].w); kahan_add(acc.w, comp.w, -pc[u].w);
+                    } else {
+                        acc.x += ps[u].x; acc.y += ps[u].y; acc.z += ps[u].z; acc.w += ps[u].w;
                     }
                 }
                 if (accumulate) {
@@ -252,8 +399,22 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
         a.w_in_smem = w_in_smem;
         a.out = out;
         a.carry = p.carry.as<float>();
-        const int grid = (int)std::min<int64_t>(a.n_tiles, (int64_t)num_sms() * (smem > 100 * 1024 ? 1 : 4));
-        { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); fwd_fp32_kernel<<<grid, threads, smem, st>>>(a); note_launch(); prof_end(pt, st); }
+        // narrow widths: the lane-per-tuple kernel (its in-tile sums are 5-level trees, whose error
+        // bound is below that of a compensated 32-term walk; the fix-up compensates across tiles)
+        auto lane_launch = [&](auto kern, int din, int dout) -> bool {
+            if (p.d_in > din || p.d_out > dout) return false;
+            const size_t lsmem = sizeof(float) * (din * dout + dout);
+            const int lgrid = (int)std::min<int64_t>(ceil_div(a.n_tiles, 8), (int64_t)num_sms() * 8);
+            { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); kern<<<lgrid, 256, lsmem, st>>>(a); note_launch(); prof_end(pt, st); }
+            return true;
+        };
+        const bool lane_done = p.identity ? lane_launch(fwd_fp32_lane_kernel<64, 64>, 64, 64)
+                                          : (lane_launch(fwd_fp32_lane_kernel<32, 32>, 32, 32) ||
+                                             lane_launch(fwd_fp32_lane_kernel<64, 16>, 64, 16));
+        if (!lane_done) {
+            const int grid = (int)std::min<int64_t>(a.n_tiles, (int64_t)num_sms() * (smem > 100 * 1024 ? 1 : 4));
+            { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); fwd_fp32_kernel<<<grid, threads, smem, st>>>(a); note_launch(); prof_end(pt, st); }
+        }
         RELNN_CUDA(cudaGetLastError());
         launch_fixup(a.seg, a.m, kTT, a.n_tiles, a.carry, out, p.d_out, multi, p.kahan, st);
         RELNN_CUDA(cudaGetLastError());
