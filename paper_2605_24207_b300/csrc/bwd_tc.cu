@@ -49,13 +49,14 @@ struct BwArgs {
     const int32_t* seg;
     float* dz;
     float* dr;
-    float* db;              // [d_out], accumulated with atomics (zeroed by the host)
+    float* db_part;         // [grid][d_out]: this CTA's db partial (summed in a fixed order)
     float* dw_part;         // [grid][d_out][d_in]
     const int* row_src;     // input feature of each padded K row (-1 = padding), [mbk * 128]
     int* status;
     int64_t m, n_tiles;
     int z_bf16, r_bf16, d, d_r, d_in, d_out, concat_dst, mask_words;
     int n_kb, d_in_pad, mbk, tile_n, stages;
+    int x_blocks;           // K blocks of X staged per tile (n_kb in the dst pass, 0 in the src pass)
     int src_pass;           // 1: tuples in src order; hd then holds each tuple's row in output order
                             // (its ReLU mask row), hs the src H rows (non-decreasing), seg their output rows
     uint32_t idesc_dx, idesc_dw, tmem_cols, d2_col;
@@ -70,13 +71,14 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
     const int N = a.tile_n;
     const uint32_t wt_bytes = (uint32_t)a.mbk * 2u * 16384u;          // W^T: mbk x 2 blocks of 128 x 64
     const uint32_t dy_bytes = 2u * (uint32_t)N * 128u;                  // dY: 2 blocks of 64 outputs
-    const uint32_t x_bytes = (uint32_t)a.n_kb * (uint32_t)N * 128u;     // X: n_kb blocks of 64 inputs
+    const uint32_t x_bytes = (uint32_t)a.x_blocks * (uint32_t)N * 128u; // X: x_blocks blocks of 64 inputs
     const uint32_t stage_bytes = dy_bytes + x_bytes;
     uint8_t* wt_smem = base;
     uint8_t* st_smem = base + wt_bytes;
     int32_t* idx_smem = reinterpret_cast<int32_t*>(st_smem + (size_t)a.stages * stage_bytes);  // 2 x 4 x N
     int32_t* epi_smem = idx_smem + 8 * N;                                                      // 4 warps x 3 x N
-    uint64_t* bars = reinterpret_cast<uint64_t*>(epi_smem + 12 * N);
+    float* db_smem = reinterpret_cast<float*>(epi_smem + 12 * N);  // producer warps x 128 outputs
+    uint64_t* bars = reinterpret_cast<uint64_t*>(db_smem + (kProducerThreads / 32) * 128);
     uint64_t* full = bars;
     uint64_t* empty = bars + a.stages;
     uint64_t* tfull = bars + 2 * a.stages;
@@ -196,7 +198,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                         }
                     }
                     // X rows, K-block by K-block (as in the forward); the src pass needs no dW
-                    for (int kb = 0; kb < (a.src_pass ? 0 : a.n_kb); ++kb) {
+                    for (int kb = 0; kb < a.x_blocks; ++kb) {
                         const int src = a.kb_src[kb];
                         const int col = a.kb_col[kb] + chunk * 8;
                         const bool in_part = col < a.kb_width[kb];
@@ -252,14 +254,24 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
         }
         // no copy may still be writing shared memory when the CTA retires
         cp_async_wait<0>();
-        // db partial sums of this thread's output chunk
+        // db: this CTA's partial, summed in a fixed order (lanes of equal chunk, then warps)
+        if (a.db_part) {
 #pragma unroll
-        for (int ob = 0; ob < 2; ++ob)
+            for (int ob = 0; ob < 2; ++ob)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int o = ob * 64 + chunk * 8 + k;
-                if (o < a.d_out && a.db) atomicAdd(a.db + o, dbacc[ob][k]);
+                for (int k = 0; k < 8; ++k) {
+                    float v = dbacc[ob][k];
+                    v += __shfl_xor_sync(0xffffffffu, v, 8);
+                    v += __shfl_xor_sync(0xffffffffu, v, 16);
+                    if (lane < 8) db_smem[warp * 128 + ob * 64 + chunk * 8 + k] = v;
+                }
+            named_bar_sync(1, kProducerThreads);
+            for (int o = tid; o < a.d_out; o += kProducerThreads) {
+                float v = 0.f;
+                for (int w = 0; w < kProducerThreads / 32; ++w) v += db_smem[w * 128 + o];
+                a.db_part[(int64_t)blockIdx.x * a.d_out + o] = v;
             }
+        }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
@@ -423,6 +435,15 @@ __global__ void pack_wt_kernel(const void* W, int w_bf16, int d_out, int d_in, i
     }
 }
 
+// out[i] = sum over parts of part[c][i], compensated, in part order (deterministic).
+__global__ void reduce_parts_kahan_kernel(const float* part, int nparts, int64_t n, float* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float sum = 0.f, c = 0.f;
+        for (int p = 0; p < nparts; ++p) kahan_add(sum, c, part[(int64_t)p * n + i]);
+        out[i] = sum;
+    }
+}
+
 __global__ void reduce_parts_kernel(const float* part, int nparts, int64_t n, float* out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float s = 0.f;
@@ -482,23 +503,39 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
     const int d_in_pad = n_kb * 64;
     const int mbk = (d_in_pad + 127) / 128;
     while ((int)row_src.size() < mbk * 128) row_src.push_back(-1);
-    // tile size: 128 tuples when three stages fit, else 64
+    // Tile size per pass: 128 tuples when three stages fit, else 64. The src pass stages only dY.
     const uint32_t wt_bytes = (uint32_t)mbk * 2u * 16384u;
-    auto stage_of = [&](int N) { return 2u * N * 128u + (uint32_t)n_kb * N * 128u; };
-    auto aux_of = [&](int N) { return (uint32_t)(20 * N * 4); };
-    int N = 128;
-    int stages = (int)((kSmemLimit - 1024 - 256 - (int)wt_bytes - (int)aux_of(128)) / (int)stage_of(128));
-    if (stages < 3) {
-        N = 64;
-        stages = (int)((kSmemLimit - 1024 - 256 - (int)wt_bytes - (int)aux_of(64)) / (int)stage_of(64));
-    }
-    stages = std::min(stages, 6);
-    if (stages < 2) return backward_fp32(p, io_in, g, st);
     const uint32_t d2_col = (uint32_t)((d_in_pad + 31) / 32 * 32);
-    const uint32_t cols_needed = d2_col + 2u * mbk * N;
-    if (cols_needed > 512) return backward_fp32(p, io_in, g, st);
-    const uint32_t tmem_cols = cols_needed <= 256 ? 256u : 512u;
-    const size_t smem = 1024 + wt_bytes + (size_t)stages * stage_of(N) + aux_of(N) + 256;
+    struct PassCfg {
+        int N = 0, stages = 0;
+        uint32_t tmem_cols = 0;
+        size_t smem = 0;
+    };
+    auto pass_cfg = [&](int x_blocks) {
+        PassCfg c;
+        auto stage_of = [&](int N) { return 2u * N * 128u + (uint32_t)x_blocks * N * 128u; };
+        auto aux_of = [&](int N) { return (uint32_t)(20 * N * 4 + (kProducerThreads / 32) * 128 * 4); };
+        auto stages_at = [&](int N) {
+            return (int)((kSmemLimit - 1024 - 256 - (int)wt_bytes - (int)aux_of(N)) / (int)stage_of(N));
+        };
+        c.N = 128;
+        c.stages = stages_at(128);
+        if (c.stages < 3 || d2_col + 2u * mbk * 128u > 512u) {
+            c.N = 64;
+            c.stages = stages_at(64);
+        }
+        c.stages = std::min(c.stages, 6);
+        const uint32_t cols_needed = d2_col + 2u * mbk * c.N;
+        if (c.stages < 2 || cols_needed > 512) c.stages = 0;  // not runnable
+        c.tmem_cols = cols_needed <= 256 ? 256u : 512u;
+        c.smem = 1024 + wt_bytes + (size_t)c.stages * stage_of(c.N) + aux_of(c.N) + 256;
+        return c;
+    };
+    const PassCfg dcfg = pass_cfg(n_kb), scfg = pass_cfg(0);
+    if (dcfg.stages == 0 || scfg.stages == 0) return backward_fp32(p, io_in, g, st);
+    const int N = dcfg.N, stages = dcfg.stages;
+    const uint32_t tmem_cols = dcfg.tmem_cols;
+    const size_t smem = dcfg.smem;
 
     // f32 z is gathered as a bf16 copy (the rounding the kernel applies anyway), by cp.async
     CallIO io;
@@ -535,11 +572,13 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         const int grid = (int)std::min<int64_t>(n_tiles, grid_max);
         // scratch: W^T (bf16), row map, dW partials
         const size_t part_elems = (size_t)grid * p.d_out * p.d_in;
-        const size_t bytes = wt_elems * 2 + sizeof(int) * row_src.size() + 256 + sizeof(float) * part_elems;
+        const size_t dbp_elems = (size_t)grid * p.d_out;
+        const size_t bytes = wt_elems * 2 + sizeof(int) * row_src.size() + 256 + sizeof(float) * (part_elems + dbp_elems);
         RELNN_TRY(p.scratch.alloc(bytes));
         uint16_t* wt = p.scratch.as<uint16_t>();
         int* d_rows = reinterpret_cast<int*>(p.scratch.as<uint8_t>() + wt_elems * 2);
         float* part = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + ((wt_elems * 2 + sizeof(int) * row_src.size() + 255) & ~(size_t)255));
+        float* db_part = part + part_elems;
         RELNN_CUDA(cudaMemcpyAsync(d_rows, row_src.data(), sizeof(int) * row_src.size(), cudaMemcpyHostToDevice, st));
         { pack_wt_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, mbk * 128, d_rows, wt); note_launch(); }
         CUtensorMap wtmap;
@@ -567,7 +606,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         a.seg = b.seg.as<int32_t>();
         a.dz = g.dz;
         a.dr = dr;
-        a.db = db;
+        a.db_part = db ? db_part : nullptr;
         a.dw_part = part;
         a.row_src = d_rows;
         a.status = p.status.as<int>();
@@ -586,6 +625,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         a.mbk = mbk;
         a.tile_n = N;
         a.stages = stages;
+        a.x_blocks = n_kb;
         a.idesc_dx = tc::idesc_bf16_f32(128, N);
         a.idesc_dw = tc::idesc_bf16_f32(128, d_in_pad, true, true);
         a.tmem_cols = tmem_cols;
@@ -604,21 +644,32 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
             RELNN_TRY(ensure_src_order(p, b, st));
             BwArgs s2 = a;
             s2.src_pass = 1;
+            s2.x_blocks = 0;
+            s2.tile_n = scfg.N;
+            s2.stages = scfg.stages;
+            s2.n_tiles = ceil_div(b.m, scfg.N);
+            s2.idesc_dx = tc::idesc_bf16_f32(128, scfg.N);
+            s2.tmem_cols = scfg.tmem_cols;
+            const int sgrid = (int)std::min<int64_t>(s2.n_tiles, grid_max);
             s2.hs = b.hs_src.as<int32_t>();
             s2.hd = b.src_perm.as<int32_t>();
             s2.seg = b.seg_src.as<int32_t>();
             s2.dr = nullptr;
-            s2.db = nullptr;
+            s2.db_part = nullptr;
             s2.dw_part = nullptr;
             s2.need_arr[0] = 1;
             s2.need_arr[1] = relu ? 1 : 0;
             s2.need_arr[2] = 0;
-            { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<grid, kThreads, smem, st>>>(wtmap, s2); note_launch(); prof_end(pt, st); }
+            { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<sgrid, kThreads, scfg.smem, st>>>(wtmap, s2); note_launch(); prof_end(pt, st); }
             RELNN_CUDA(cudaGetLastError());
         }
         if (dW) {
             const int64_t nw = (int64_t)p.d_out * p.d_in;
             { reduce_parts_kernel<<<(int)std::min<int64_t>(ceil_div(nw, 256), 1024), 256, 0, st>>>(part, grid, nw, dW); note_launch(); }
+            RELNN_CUDA(cudaGetLastError());
+        }
+        if (db) {
+            { reduce_parts_kahan_kernel<<<1, 128, 0, st>>>(db_part, grid, p.d_out, db); note_launch(); }
             RELNN_CUDA(cudaGetLastError());
         }
     }
