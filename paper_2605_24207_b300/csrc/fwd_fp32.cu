@@ -264,52 +264,27 @@ __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int til
         float* dst = out + (int64_t)s * d_out;
         if (vec4) {
             for (int o = lane * 4; o < d_out; o += 128) {
-                // tiles b..e all start inside s (their slot 0 piece); long segments are summed in 8
-                // interleaved partial sums (independent loads), combined in order at the end
-                constexpr int kP = 8;
-                float4 ps[kP], pc[kP];
-#pragma unroll
-                for (int u = 0; u < kP; ++u) {
-                    ps[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    pc[u] = ps[u];
-                }
-                int64_t j = b;
-                for (; j + kP - 1 <= e; j += kP) {
-                    float4 x[kP];
-#pragma unroll
-                    for (int u = 0; u < kP; ++u) x[u] = *reinterpret_cast<const float4*>(carry + ((j + u) * 2) * (int64_t)d_out + o);
-#pragma unroll
-                    for (int u = 0; u < kP; ++u) {
-                        if (kahan) {
-                            kahan_add(ps[u].x, pc[u].x, x[u].x); kahan_add(ps[u].y, pc[u].y, x[u].y);
-                            kahan_add(ps[u].z, pc[u].z, x[u].z); kahan_add(ps[u].w, pc[u].w, x[u].w);
-                        } else {
-                            ps[u].x += x[u].x; ps[u].y += x[u].y; ps[u].z += x[u].z; ps[u].w += x[u].w;
-                        }
-                    }
-                }
-                for (; j <= e; ++j) {
-                    const float4 x = *reinterpret_cast<const float4*>(carry + (j * 2) * (int64_t)d_out + o);
-                    if (kahan) {
-                        kahan_add(ps[0].x, pc[0].x, x.x); kahan_add(ps[0].y, pc[0].y, x.y);
-                        kahan_add(ps[0].z, pc[0].z, x.z); kahan_add(ps[0].w, pc[0].w, x.w);
-                    } else {
-                        ps[0].x += x.x; ps[0].y += x.y; ps[0].z += x.z; ps[0].w += x.w;
-                    }
-                }
+                // tiles b..e all start inside s (their slot 0 piece): added in tile order, with the
+                // loads of 8 tiles in flight at a time
                 float4 acc = *reinterpret_cast<const float4*>(c0 + o);
                 float4 comp = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < kP; ++u) {
+                auto add4 = [&](const float4& x) {
                     if (kahan) {
-                        kahan_add(acc.x, comp.x, ps[u].x); kahan_add(acc.x, comp.x, -pc[u].x);
-                        kahan_add(acc.y, comp.y, ps[u].y); kahan_add(acc.y, comp.y, -pc[u].y);
-                        kahan_add(acc.z, comp.z, ps[u].z); kahan_add(acc.z, comp.z, -pc[u].z);
-                        kahan_add(acc.w, comp.w, ps[u].w); kahan_add(acc.w, comp.w, -pc[u].w);
+                        kahan_add(acc.x, comp.x, x.x); kahan_add(acc.y, comp.y, x.y);
+                        kahan_add(acc.z, comp.z, x.z); kahan_add(acc.w, comp.w, x.w);
                     } else {
-                        acc.x += ps[u].x; acc.y += ps[u].y; acc.z += ps[u].z; acc.w += ps[u].w;
+                        acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
                     }
+                };
+                int64_t j = b;
+                for (; j + 7 <= e; j += 8) {
+                    float4 x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) x[u] = *reinterpret_cast<const float4*>(carry + ((j + u) * 2) * (int64_t)d_out + o);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) add4(x[u]);
                 }
+                for (; j <= e; ++j) add4(*reinterpret_cast<const float4*>(carry + (j * 2) * (int64_t)d_out + o));
                 if (accumulate) {
                     const float4 old = *reinterpret_cast<const float4*>(dst + o);
                     acc.x += old.x; acc.y += old.y; acc.z += old.z; acc.w += old.w;
