@@ -110,6 +110,26 @@ __global__ void bw_dy_kernel(BwArgs a) {
     }
 }
 
+// Identity rule without ReLU (e.g. a SUM readout): dX[t] = dOut[seg_t], added straight into the
+// slice's gradient, 4 features per thread (16-byte loads and 16-byte atomic adds).
+__global__ void bw_identity_kernel(BwArgs a) {
+    const int q = a.d_in / 4;
+    const int64_t n = a.m * q;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / q;
+        const int k = (int)(i - t * q) * 4;
+        const float4 v = *reinterpret_cast<const float4*>(a.dout + (int64_t)a.seg[t] * a.d_out + k);
+        if (k < a.d) {
+            if (a.dz) atomicAdd(reinterpret_cast<float4*>(a.dz + (int64_t)a.hs[t] * a.d + k), v);
+        } else if (a.concat_dst && k < 2 * a.d) {
+            if (a.dz) atomicAdd(reinterpret_cast<float4*>(a.dz + (int64_t)a.hd[t] * a.d + (k - a.d)), v);
+        } else if (a.dr) {
+            const int kr = k - (a.concat_dst ? 2 : 1) * a.d;
+            atomicAdd(reinterpret_cast<float4*>(a.dr + (int64_t)a.er[t] * a.d_r + kr), v);
+        }
+    }
+}
+
 // Split-K SIMT GEMM: block (ob, kb, chunk) computes a 32x32 tile of dW over one tuple chunk.
 constexpr int kDwTile = 32;
 constexpr int kDwChunk = 8192;
@@ -179,7 +199,6 @@ relnn_status backward_fp32(Plan& p, const CallIO& io, const GradIO& g, cudaStrea
         const int64_t nchunks = ceil_div(b.m, kDwChunk);
         const size_t dy_bytes = sizeof(float) * (size_t)b.m * p.d_out;
         const size_t part_bytes = need_w ? sizeof(float) * (size_t)nchunks * p.d_out * (p.d_in + 1) : 0;
-        RELNN_TRY(p.scratch.alloc(dy_bytes + part_bytes + 256));
         BwArgs a{};
         a.z = io.z;
         a.r = io.br[i].r;
@@ -190,7 +209,6 @@ relnn_status backward_fp32(Plan& p, const CallIO& io, const GradIO& g, cudaStrea
         a.hd = b.hd.as<int32_t>();
         a.er = b.er.as<int32_t>();
         a.seg = b.seg.as<int32_t>();
-        a.dY = p.scratch.as<float>();
         a.dz = g.dz;
         a.dr = (g.dr.size() > i && b.d_r > 0) ? g.dr[i] : nullptr;
         a.m = b.m;
@@ -206,6 +224,17 @@ relnn_status backward_fp32(Plan& p, const CallIO& io, const GradIO& g, cudaStrea
         a.act = p.act;
         a.mask = b.relu_mask.p ? b.relu_mask.as<uint32_t>() : nullptr;
         a.mask_words = ((p.d_out + 127) / 128) * 4;
+        // identity without ReLU: a straight gather of dOut rows into the gradients
+        const bool aligned16 = ((reinterpret_cast<uintptr_t>(g.dout) | reinterpret_cast<uintptr_t>(g.dz) |
+                                 reinterpret_cast<uintptr_t>(a.dr)) & 15u) == 0;
+        if (p.identity && p.act != RELNN_ACT_RELU && p.d % 4 == 0 && b.d_r % 4 == 0 && aligned16) {
+            const int blocks = (int)std::min<int64_t>(ceil_div(b.m * (p.d_in / 4), 256), (int64_t)num_sms() * 16);
+            { ProfToken pt = prof_begin(RELNN_PROF_BWD_FP32, st); bw_identity_kernel<<<blocks, 256, 0, st>>>(a); note_launch(); prof_end(pt, st); }
+            RELNN_CUDA(cudaGetLastError());
+            continue;
+        }
+        RELNN_TRY(p.scratch.alloc(dy_bytes + part_bytes + 256));
+        a.dY = p.scratch.as<float>();
         const int threads = std::min(1024, std::max(32, ((std::max(p.d_in, p.d_out) + 31) / 32) * 32));
         const size_t smem = sizeof(float) * kTT * (p.d_in + p.d_out);
         RELNN_CHECK_ARG(smem <= 200 * 1024, "backward: tile too large");

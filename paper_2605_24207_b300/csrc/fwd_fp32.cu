@@ -21,6 +21,9 @@ struct Fp32Args {
     const float* bias;   // [d_out] or nullptr
     const int32_t *hs, *hd, *er, *seg;
     int64_t m, n_tiles;
+    int64_t n_ranges;    // lane kernel: ranges of range_tiles 32-tuple tiles, one warp each
+    int range_tiles;
+    int vec_in;          // widths multiples of 4 and rows aligned: 4-element loads
     int concat_dst, d_in, d_out, act, kahan, accumulate, w_in_smem;
     float* out;
     float* carry;
@@ -29,6 +32,16 @@ struct Fp32Args {
 __device__ __forceinline__ float load_elem(const void* base, int bf16, int64_t idx) {
     return bf16 ? bf16_to_f32(reinterpret_cast<const uint16_t*>(base)[idx])
                 : reinterpret_cast<const float*>(base)[idx];
+}
+
+// Elements idx..idx+3 (idx a multiple of 4, the row base aligned to 4 elements).
+__device__ __forceinline__ float4 load_elem4(const void* base, int bf16, int64_t idx) {
+    if (bf16) {
+        const uint2 u = *reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(base) + idx);
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+    }
+    return *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(base) + idx);
 }
 
 __global__ void __launch_bounds__(256) fwd_fp32_kernel(Fp32Args a) {
@@ -109,17 +122,21 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(Fp32Args a) {
     }
 }
 
-// Narrow widths (d_in <= DIN, d_out <= DOUT): lane = tuple. A warp owns a 32-tuple tile; each lane
-// loads its tuple's Concat row into registers, computes its d_out outputs with W^T broadcast from
-// shared memory (4 outputs per shared load), and the SUM over each run of equal output rows is a
-// segmented scan across the lanes (5 shuffle steps, the segment pattern computed once per tile).
-// The lane holding a run's last tuple writes the row (or the tile-boundary partial).
+// Narrow widths (d_in <= DIN, d_out <= DOUT): lane = tuple. A warp owns a range of range_tiles
+// consecutive 32-tuple tiles; each lane loads its tuple's Concat row into registers, computes its
+// d_out outputs with W^T broadcast from shared memory (4 outputs per shared load), and the SUM over
+// each run of equal output rows is a segmented scan across the lanes (5 shuffle steps, the segment
+// pattern computed once per tile). The lane holding a run's last tuple writes the row; a run that
+// goes on into the next tile of the range leaves its partial in the warp's shared slot, where the
+// next tile's first lane picks it up, so only the range's two boundary runs become fix-up partials.
 template <int DIN, int DOUT>
 __global__ void __launch_bounds__(256) fwd_fp32_lane_kernel(Fp32Args a) {
     extern __shared__ float sm[];
-    float* Ws = sm;                        // [d_in][DOUT] (zero beyond d_out), when there is a W
-    float* bs = sm + DIN * DOUT;           // [DOUT]
+    float* Ws = sm;                                 // [d_in][DOUT] (zero beyond d_out), when there is a W
+    float* bs = sm + (a.Wt ? DIN * DOUT : 0);       // [DOUT]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* cb = bs + DOUT + warp * 2 * DOUT;        // [DOUT] this warp's open-run partial
+    float* cc = cb + DOUT;                          // [DOUT] and its compensation
     if (a.Wt) {
         for (int i = threadIdx.x; i < DIN * DOUT; i += blockDim.x) {
             const int k = i / DOUT, o = i - k * DOUT;
@@ -129,94 +146,158 @@ __global__ void __launch_bounds__(256) fwd_fp32_lane_kernel(Fp32Args a) {
     for (int o = threadIdx.x; o < DOUT; o += blockDim.x) bs[o] = (a.bias && o < a.d_out) ? a.bias[o] : 0.f;
     __syncthreads();
     const int warps_total = gridDim.x * (blockDim.x >> 5);
-    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < a.n_tiles; tile += warps_total) {
-        const int64_t t = tile * 32 + lane;
-        const bool tv = t < a.m;
-        const int nt = (int)imin64(32, a.m - tile * 32);
-        // this lane's Concat row (z[hs] | z[hd] | r[er])
-        float x[DIN];
-        const int64_t rs = tv ? (int64_t)a.hs[t] * a.d : 0;
-        const int64_t rd = (tv && a.concat_dst) ? (int64_t)a.hd[t] * a.d : 0;
-        const int64_t rr = (tv && a.d_r > 0) ? (int64_t)a.er[t] * a.d_r : 0;
-        const int kr0 = a.concat_dst ? 2 * a.d : a.d;
+    const int64_t span = (int64_t)a.range_tiles * 32;
+    for (int64_t rg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; rg < a.n_ranges; rg += warps_total) {
+        const int64_t r0 = rg * span, r1 = imin64(a.m, r0 + span);
+        const int prev_seg = r0 > 0 ? a.seg[r0 - 1] : -1;
+        bool first_run = true;  // no run of this range has ended yet
+        bool open = false;      // the previous tile's last run goes on into this tile
+        for (int64_t t0 = r0; t0 < r1; t0 += 32) {
+            const int64_t t = t0 + lane;
+            const bool tv = t < r1;
+            const int nt = (int)imin64(32, r1 - t0);
+            // this lane's Concat row (z[hs] | z[hd] | r[er])
+            float x[DIN];
+            const int64_t rs = tv ? (int64_t)a.hs[t] * a.d : 0;
+            const int64_t rd = (tv && a.concat_dst) ? (int64_t)a.hd[t] * a.d : 0;
+            const int64_t rr = (tv && a.d_r > 0) ? (int64_t)a.er[t] * a.d_r : 0;
+            const int kr0 = a.concat_dst ? 2 * a.d : a.d;
+            if (a.vec_in) {
 #pragma unroll
-        for (int k = 0; k < DIN; ++k) {
-            float v = 0.f;
-            if (tv && k < a.d_in) {
-                if (k < a.d) v = load_elem(a.z, a.z_bf16, rs + k);
-                else if (k < kr0) v = load_elem(a.z, a.z_bf16, rd + (k - a.d));
-                else v = load_elem(a.r, a.r_bf16, rr + (k - kr0));
-            }
-            x[k] = v;
-        }
-        float y[DOUT];
-        if (a.Wt) {
+                for (int k = 0; k < DIN; k += 4) {
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (tv && k < a.d_in) {
+                        if (k < a.d) v = load_elem4(a.z, a.z_bf16, rs + k);
+                        else if (k < kr0) v = load_elem4(a.z, a.z_bf16, rd + (k - a.d));
+                        else v = load_elem4(a.r, a.r_bf16, rr + (k - kr0));
+                    }
+                    x[k] = v.x;
+                    x[k + 1] = v.y;
+                    x[k + 2] = v.z;
+                    x[k + 3] = v.w;
+                }
+            } else {
 #pragma unroll
-            for (int o = 0; o < DOUT; ++o) y[o] = bs[o];
-#pragma unroll
-            for (int k = 0; k < DIN; ++k) {
-                const float4* wr = reinterpret_cast<const float4*>(Ws + k * DOUT);
-#pragma unroll
-                for (int o4 = 0; o4 < DOUT / 4; ++o4) {
-                    const float4 w = wr[o4];
-                    y[4 * o4 + 0] = fmaf(x[k], w.x, y[4 * o4 + 0]);
-                    y[4 * o4 + 1] = fmaf(x[k], w.y, y[4 * o4 + 1]);
-                    y[4 * o4 + 2] = fmaf(x[k], w.z, y[4 * o4 + 2]);
-                    y[4 * o4 + 3] = fmaf(x[k], w.w, y[4 * o4 + 3]);
+                for (int k = 0; k < DIN; ++k) {
+                    float v = 0.f;
+                    if (tv && k < a.d_in) {
+                        if (k < a.d) v = load_elem(a.z, a.z_bf16, rs + k);
+                        else if (k < kr0) v = load_elem(a.z, a.z_bf16, rd + (k - a.d));
+                        else v = load_elem(a.r, a.r_bf16, rr + (k - kr0));
+                    }
+                    x[k] = v;
                 }
             }
-        } else {
+            float y[DOUT];
+            if (a.Wt) {
 #pragma unroll
-            for (int o = 0; o < DOUT; ++o) y[o] = o < DIN ? x[o < DIN ? o : 0] : 0.f;
-        }
-        if (a.act == RELNN_ACT_RELU) {
+                for (int o = 0; o < DOUT; ++o) y[o] = bs[o];
 #pragma unroll
-            for (int o = 0; o < DOUT; ++o) y[o] = fmaxf(y[o], 0.f);
-        }
-        if (!tv) {
+                for (int k = 0; k < DIN; ++k) {
+                    const float4* wr = reinterpret_cast<const float4*>(Ws + k * DOUT);
 #pragma unroll
-            for (int o = 0; o < DOUT; ++o) y[o] = 0.f;
-        }
-        // segment pattern of the tile: lane adds the value d lanes up at step d unless a run
-        // start lies in between
-        const int sg = tv ? a.seg[t] : -1;
-        const int sg_prev = __shfl_up_sync(0xffffffffu, sg, 1);
-        bool head = lane == 0 || sg_prev != sg;
-        unsigned add_mask[5];
+                    for (int o4 = 0; o4 < DOUT / 4; ++o4) {
+                        const float4 w = wr[o4];
+                        y[4 * o4 + 0] = fmaf(x[k], w.x, y[4 * o4 + 0]);
+                        y[4 * o4 + 1] = fmaf(x[k], w.y, y[4 * o4 + 1]);
+                        y[4 * o4 + 2] = fmaf(x[k], w.z, y[4 * o4 + 2]);
+                        y[4 * o4 + 3] = fmaf(x[k], w.w, y[4 * o4 + 3]);
+                    }
+                }
+            } else {
 #pragma unroll
-        for (int st = 0; st < 5; ++st) {
-            const int dd = 1 << st;
-            const bool up_head = __shfl_up_sync(0xffffffffu, head ? 1 : 0, dd) != 0;
-            const bool add = lane >= dd && !head;
-            add_mask[st] = add ? 1u : 0u;
-            head = head || (add && up_head);
-        }
+                for (int o = 0; o < DOUT; ++o) y[o] = o < DIN ? x[o < DIN ? o : 0] : 0.f;
+            }
+            if (a.act == RELNN_ACT_RELU) {
 #pragma unroll
-        for (int o = 0; o < DOUT; ++o) {
+                for (int o = 0; o < DOUT; ++o) y[o] = fmaxf(y[o], 0.f);
+            }
+            if (!tv) {
+#pragma unroll
+                for (int o = 0; o < DOUT; ++o) y[o] = 0.f;
+            }
+            // segment pattern of the tile: lane adds the value d lanes up at step d unless a run
+            // start lies in between
+            const int sg = tv ? a.seg[t] : -1;
+            const int sg_prev = __shfl_up_sync(0xffffffffu, sg, 1);
+            bool head = lane == 0 || sg_prev != sg;
+            unsigned add_mask[5];
 #pragma unroll
             for (int st = 0; st < 5; ++st) {
-                const float u = __shfl_up_sync(0xffffffffu, y[o], 1 << st);
-                if (add_mask[st]) y[o] += u;
+                const int dd = 1 << st;
+                const bool up_head = __shfl_up_sync(0xffffffffu, head ? 1 : 0, dd) != 0;
+                const bool add = lane >= dd && !head;
+                add_mask[st] = add ? 1u : 0u;
+                head = head || (add && up_head);
             }
-        }
-        // run ends: the next tuple has another output row, or the tile's last tuple
-        const int sg_next = __shfl_down_sync(0xffffffffu, sg, 1);
-        const bool last = lane == nt - 1;
-        const bool end = tv && (last || sg_next != sg);
-        const unsigned endmask = __ballot_sync(0xffffffffu, end);
-        if (end) {
-            const int prev_seg = (tile > 0) ? a.seg[tile * 32 - 1] : -1;
-            const int next_seg = (tile * 32 + nt < a.m) ? a.seg[tile * 32 + nt] : -1;
-            const bool first_piece = (endmask & ((1u << lane) - 1u)) == 0;  // the tile's first run
-            const bool split = (first_piece && prev_seg == sg) || (last && next_seg == sg);
-            float* dst = split ? a.carry + (tile * 2 + (first_piece ? 0 : 1)) * a.d_out
-                               : a.out + (int64_t)sg * a.d_out;
 #pragma unroll
-            for (int o = 0; o < DOUT; ++o)
-                if (o < a.d_out) {
-                    if (split) __stcg(dst + o, y[o]);
-                    else emit_out(dst + o, y[o], a.accumulate);
+            for (int o = 0; o < DOUT; ++o) {
+#pragma unroll
+                for (int st = 0; st < 5; ++st) {
+                    const float u = __shfl_up_sync(0xffffffffu, y[o], 1 << st);
+                    if (add_mask[st]) y[o] += u;
                 }
+            }
+            // run ends: the next tuple has another output row, or the tile's last tuple unless its
+            // run goes on into the next tile of the range
+            const int sg_next = __shfl_down_sync(0xffffffffu, sg, 1);
+            const int sg_last = __shfl_sync(0xffffffffu, sg, nt - 1);
+            const int next_seg = (t0 + nt < a.m) ? a.seg[t0 + nt] : -1;
+            const bool cont = next_seg == sg_last;
+            const bool carry_on = cont && t0 + nt < r1;
+            const bool last = lane == nt - 1;
+            // the partial carried from the previous tile joins the tile's first run at that run's
+            // last lane (compensated for compensated plans)
+            const unsigned runends = __ballot_sync(0xffffffffu, tv && (last || sg_next != sg));
+            const bool merge = open && lane == __ffs(runends) - 1;
+            if (merge) {
+#pragma unroll
+                for (int o4 = 0; o4 < DOUT / 4; ++o4) {
+                    float4 sv = reinterpret_cast<const float4*>(cb)[o4];
+                    if (a.kahan) {
+                        float4 cv = reinterpret_cast<const float4*>(cc)[o4];
+                        kahan_add(sv.x, cv.x, y[4 * o4 + 0]);
+                        kahan_add(sv.y, cv.y, y[4 * o4 + 1]);
+                        kahan_add(sv.z, cv.z, y[4 * o4 + 2]);
+                        kahan_add(sv.w, cv.w, y[4 * o4 + 3]);
+                        reinterpret_cast<float4*>(cc)[o4] = cv;
+                        y[4 * o4 + 0] = sv.x;
+                        y[4 * o4 + 1] = sv.y;
+                        y[4 * o4 + 2] = sv.z;
+                        y[4 * o4 + 3] = sv.w;
+                    } else {
+                        y[4 * o4 + 0] += sv.x;
+                        y[4 * o4 + 1] += sv.y;
+                        y[4 * o4 + 2] += sv.z;
+                        y[4 * o4 + 3] += sv.w;
+                    }
+                }
+            }
+            const bool end = tv && (last ? !carry_on : sg_next != sg);
+            const unsigned endmask = __ballot_sync(0xffffffffu, end);
+            if (last && carry_on) {  // a fresh carry starts without compensation
+#pragma unroll
+                for (int o4 = 0; o4 < DOUT / 4; ++o4) {
+                    reinterpret_cast<float4*>(cb)[o4] =
+                        make_float4(y[4 * o4 + 0], y[4 * o4 + 1], y[4 * o4 + 2], y[4 * o4 + 3]);
+                    if (a.kahan && !merge) reinterpret_cast<float4*>(cc)[o4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            if (end) {
+                const bool first_piece = first_run && (endmask & ((1u << lane) - 1u)) == 0;
+                const bool split = (first_piece && prev_seg == sg) || (last && cont);
+                float* dst = split ? a.carry + (rg * 2 + (first_piece ? 0 : 1)) * a.d_out
+                                   : a.out + (int64_t)sg * a.d_out;
+#pragma unroll
+                for (int o = 0; o < DOUT; ++o)
+                    if (o < a.d_out) {
+                        if (split) __stcg(dst + o, y[o]);
+                        else emit_out(dst + o, y[o], a.accumulate);
+                    }
+            }
+            first_run = first_run && endmask == 0;
+            open = carry_on;
+            __syncwarp();
         }
     }
 }
@@ -373,25 +454,46 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
         a.accumulate = multi;
         a.w_in_smem = w_in_smem;
         a.out = out;
+        {
+            const uintptr_t za = reinterpret_cast<uintptr_t>(io.z), ra = reinterpret_cast<uintptr_t>(a.r);
+            const uintptr_t zmask = io.z_bf16 ? 7u : 15u, rmask = io.r_bf16 ? 7u : 15u;
+            a.vec_in = p.d % 4 == 0 && (za & zmask) == 0 &&
+                       (b.d_r == 0 || (b.d_r % 4 == 0 && (ra & rmask) == 0));
+        }
         a.carry = p.carry.as<float>();
         // narrow widths: the lane-per-tuple kernel (its in-tile sums are 5-level trees, whose error
         // bound is below that of a compensated 32-term walk; the fix-up compensates across tiles)
-        auto lane_launch = [&](auto kern, int din, int dout) -> bool {
+        // one wave of warps, each over an equal range of tiles
+        int64_t fix_tile = kTT, fix_n = a.n_tiles;
+        auto lane_launch = [&](auto kern, int din, int dout, int* bps_cache) -> bool {
             if (p.d_in > din || p.d_out > dout) return false;
-            const size_t lsmem = sizeof(float) * (din * dout + dout);
-            const int lgrid = (int)std::min<int64_t>(ceil_div(a.n_tiles, 8), (int64_t)num_sms() * 8);
+            const size_t lsmem = sizeof(float) * ((a.Wt ? din * dout : 0) + dout + 16 * dout);
+            int& bps = bps_cache[a.Wt ? 1 : 0];
+            if (bps <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, lsmem) != cudaSuccess) {
+                (void)cudaGetLastError();  // the query only sizes the ranges: assume one block per SM
+                bps = 1;
+            }
+            bps = std::max(1, bps);
+            const int64_t n32 = ceil_div(b.m, 32);
+            const int64_t resident = (int64_t)bps * num_sms() * 8;
+            a.range_tiles = (int)std::min<int64_t>(ceil_div(n32, resident), 1 << 20);
+            a.n_ranges = ceil_div(n32, a.range_tiles);
+            fix_tile = (int64_t)a.range_tiles * 32;
+            fix_n = a.n_ranges;
+            const int lgrid = (int)std::min<int64_t>(ceil_div(a.n_ranges, 8), (int64_t)bps * num_sms());
             { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); kern<<<lgrid, 256, lsmem, st>>>(a); note_launch(); prof_end(pt, st); }
             return true;
         };
-        const bool lane_done = p.identity ? lane_launch(fwd_fp32_lane_kernel<64, 64>, 64, 64)
-                                          : (lane_launch(fwd_fp32_lane_kernel<32, 32>, 32, 32) ||
-                                             lane_launch(fwd_fp32_lane_kernel<64, 16>, 64, 16));
+        static int bps64x64[2], bps32x32[2], bps64x16[2];
+        const bool lane_done = p.identity ? lane_launch(fwd_fp32_lane_kernel<64, 64>, 64, 64, bps64x64)
+                                          : (lane_launch(fwd_fp32_lane_kernel<32, 32>, 32, 32, bps32x32) ||
+                                             lane_launch(fwd_fp32_lane_kernel<64, 16>, 64, 16, bps64x16));
         if (!lane_done) {
             const int grid = (int)std::min<int64_t>(a.n_tiles, (int64_t)num_sms() * (smem > 100 * 1024 ? 1 : 4));
             { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); fwd_fp32_kernel<<<grid, threads, smem, st>>>(a); note_launch(); prof_end(pt, st); }
         }
         RELNN_CUDA(cudaGetLastError());
-        launch_fixup(a.seg, a.m, kTT, a.n_tiles, a.carry, out, p.d_out, multi, p.kahan, st);
+        launch_fixup(a.seg, a.m, (int)fix_tile, fix_n, a.carry, out, p.d_out, multi, p.kahan, st);
         RELNN_CUDA(cudaGetLastError());
     }
     return RELNN_OK;

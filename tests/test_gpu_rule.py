@@ -70,6 +70,30 @@ def test_fp32_readout_identity_no_dst_join(gpu):
     assert rel_frob(out, oo) <= FP32_TOL
 
 
+@pytest.mark.parametrize("groups,kahan", [(8, False), (8, True), (3000, False), (3000, True)])
+def test_fp32_readout_ranges_of_tiles(gpu, groups, kahan):
+    """500k rows into few or many groups: a warp walks a range of several 32-tuple tiles, so runs
+    are carried from tile to tile inside a range and from range to range by the fix-up."""
+    rng = np.random.default_rng(1)
+    k = 500_000
+    h = rng.permutation(k).astype(np.int32)
+    z = rng.standard_normal((k, 64)).astype(np.float32)
+    g = rng.integers(0, groups, size=k).astype(np.int32)
+    rel = W.Relations(h_ids=h, z=z, branches=[W.Branch(src=h.copy(), dst=g, W=None, b=None)])
+    keys, out, plan, _ = run_rule(rel, flags=R.FLAG_NO_JOIN_DST | (R.FLAG_KAHAN if kahan else 0))
+    ok, oo, _ = oracle_rule(rel, join_dst=False, concat_dst=False)
+    assert np.array_equal(keys, ok)
+    assert rel_frob(out, oo) <= FP32_TOL
+
+
+@pytest.mark.parametrize("d,kahan", [(16, False), (16, True), (6, False)])
+def test_fp32_ranges_with_hubs(gpu, d, kahan):
+    """600k tuples, Zipf(1.3) dst (the largest run is about a quarter of E): ranges of tiles with
+    runs inside, across and over whole ranges; d = 6 takes the scalar-load form."""
+    rel = W.make_rule(16, 600_000, 20_000, d, 2 * d, np.int32, dst_dist="zipf", dst_s=1.3, act="relu")
+    _check_fp32(rel, flags=R.FLAG_KAHAN if kahan else 0)
+
+
 def test_empty_join(gpu):
     rel = W.make_rule(8, 100, 50, 8, 8, np.int32, missing_frac=1.0)
     keys, out, plan, _ = run_rule(rel)
