@@ -16,7 +16,10 @@
 //   warps 8-15 epilogue, two warps per TMEM lane quarter, each owning one half of the tile's
 //              columns (a half-tile is the unit of the SUM walk and of the boundary partials):
 //              tcgen05.ld of the accumulator (double-buffered in TMEM so the next tile's MMAs
-//              overlap), bias, ReLU, SUM walk, stores / half-tile-boundary partials.
+//              overlap), bias, ReLU, SUM walk, stores / unit-boundary partials.
+// Narrow outputs (d_out <= 64) leave lane quarters empty, so W is replicated into them (2 or 4
+// copies): every quarter then holds all features of the tile, and each of the rep warps sharing a
+// feature quarter walks 1/rep of the half-tile's columns (the unit shrinks to half_n / rep).
 #include "fwd.cuh"
 #include "segscan.cuh"
 #include "tc.cuh"
@@ -57,6 +60,7 @@ struct TcArgs {
     int z_bf16, r_bf16, d, d_r;
     int d_out, act, kahan, accumulate;
     int n_kb, tile_n, m_blocks, stages, mask_words;
+    int rep;              // copies of W in the 128 TMEM lanes (d_out <= 64: 2, <= 32: 4)
     uint32_t idesc, tmem_cols;
     int kb_src[kMaxKb];   // 0: z[hs], 1: z[hd], 2: r[er]
     int kb_col[kMaxKb];   // first element of the block within its part
@@ -284,28 +288,32 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
         const int q = warp & 3;                      // TMEM lane quarter this warp may access
         const int ew = warp - kMmaWarp - 1;          // 0..7 (quarters 0-3, then 0-3 again)
         const int hh = ew >> 2;                      // which half of the tile's columns
-        const int n_half_chunks = half_n / 32;
+        const int n_fq = 4 / a.rep;                  // feature quarters (the rest are W replicas)
+        const int fq = q % n_fq;                     // this warp's features: 32 * fq + lane
+        const int unit = half_n / a.rep;             // columns per warp and tile
+        const int ucol = hh * half_n + (q / n_fq) * unit;  // first column of this warp's unit
+        const int n_unit_chunks = unit / 32;
         int32_t* wseg = seg_smem + ew * half_n;
         const bool relu = a.act == RELNN_ACT_RELU;
         const bool mask = relu && a.relu_mask != nullptr;
         float bias_r[2];
 #pragma unroll
         for (int mb = 0; mb < 2; ++mb) {
-            const int o = mb * 128 + 32 * q + lane;
+            const int o = mb * 128 + 32 * fq + lane;
             bias_r[mb] = (a.bias && mb < a.m_blocks && o < a.d_out) ? a.bias[o] : 0.f;
         }
-        // output rows of this warp's half of the next tile, loaded one tile ahead (up to 4 x 32)
+        // output rows of this warp's unit of the next tile, loaded one tile ahead (up to 4 x 32)
         int pf[4];
         int pf_prev = -1, pf_after = -1;
         auto prefetch = [&](int64_t tile) {
-            const int64_t h0 = tile * a.tile_n + hh * half_n;
+            const int64_t h0 = tile * a.tile_n + ucol;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int64_t t = h0 + 32 * c + lane;
-                pf[c] = (tile < a.n_tiles && c < n_half_chunks && t < a.m) ? __ldg(a.seg + t) : -1;
+                pf[c] = (tile < a.n_tiles && c < n_unit_chunks && t < a.m) ? __ldg(a.seg + t) : -1;
             }
             pf_prev = (tile < a.n_tiles && h0 > 0 && h0 - 1 < a.m) ? __ldg(a.seg + h0 - 1) : -1;
-            pf_after = (tile < a.n_tiles && h0 + half_n < a.m) ? __ldg(a.seg + h0 + half_n) : -1;
+            pf_after = (tile < a.n_tiles && h0 + unit < a.m) ? __ldg(a.seg + h0 + unit) : -1;
         };
         prefetch(blockIdx.x);
         int lt = 0;
@@ -315,7 +323,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
             __syncwarp();
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                if (c < n_half_chunks) wseg[32 * c + lane] = pf[c];
+                if (c < n_unit_chunks) wseg[32 * c + lane] = pf[c];
             const int prev_seg = pf_prev;
             const int after_seg = pf_after;
             __syncwarp();
@@ -323,11 +331,11 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
             // warp-uniform outcome of the bounded wait, so no lane runs the .sync.aligned loads alone
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag))) break;
             tc_fence_after();
-            const int64_t vtile = tile * 2 + hh;     // half-tile index (unit of the boundary partials)
-            const int64_t t0 = tile * a.tile_n + hh * half_n;
-            const int nt = (int)imin64(half_n, a.m - t0);  // <= 0 for an empty second half
+            const int64_t t0 = tile * a.tile_n + ucol;
+            const int64_t vtile = t0 / unit;         // unit index (the boundary partials' slot)
+            const int nt = (int)imin64(unit, a.m - t0);  // <= 0 for an empty unit
             for (int mb = 0; mb < a.m_blocks; ++mb) {
-                const int obase = mb * 128 + 32 * q;
+                const int obase = mb * 128 + 32 * fq;
                 if (obase >= a.d_out) continue;
                 const int o = obase + lane;
                 const bool o_ok = o < a.d_out;
@@ -336,7 +344,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 bool first = true;
                 unsigned prev_end = 1u;  // did the tuple before this chunk end a piece? (half start: yes)
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_stride +
-                                       (uint32_t)mb * a.tile_n + (uint32_t)(hh * half_n);
+                                       (uint32_t)mb * a.tile_n + (uint32_t)ucol;
                 for (int c = 0; c * 32 < nt; ++c) {
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
@@ -346,7 +354,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                     // a piece ends at row j if the next row has another output row or j is the
                     // half-tile's last row; it starts at j if row j-1 ended one
                     const int sg = wseg[li];
-                    const int nx = (li + 1 < half_n) ? wseg[li + 1] : after_seg;
+                    const int nx = (li + 1 < unit) ? wseg[li + 1] : after_seg;
                     const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && (sg != nx || li == nt - 1));
                     const unsigned startmask = (endmask << 1) | prev_end;
                     prev_end = endmask >> 31;
@@ -367,7 +375,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         const float val = __uint_as_float(select32(v, j));
                         const int s = wseg[c * 32 + j];
                         const bool last = (c * 32 + j == nt - 1);
-                        const int sn = last ? ((nt == half_n) ? after_seg : -1) : s + 1;
+                        const int sn = last ? ((nt == unit) ? after_seg : -1) : s + 1;
                         const bool split = (first && prev_seg == s) || (last && sn == s);
                         if (o_ok) {
                             if (split) __stcg(a.carry + (vtile * 2 + (first ? 0 : 1)) * a.d_out + o, val);
@@ -375,7 +383,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         }
                         first = false;
                     }
-                    if (mask && tvalid) a.relu_mask[(t0 + li) * a.mask_words + mb * 4 + q] = mword;
+                    if (mask && tvalid) a.relu_mask[(t0 + li) * a.mask_words + mb * 4 + fq] = mword;
                 }
             }
             tc_fence_before();
@@ -399,13 +407,15 @@ __global__ void z_to_bf16_kernel(const float4* __restrict__ z, int64_t n4, uint2
     }
 }
 
-// W_pad[mb*128 + o][kb*64 + kk] (bf16) = W[o][k(kb, kk)] with zero padding.
-__global__ void pack_w_kernel(const void* W, int w_bf16, int d_out, int d_in, int rows_pad, int n_kb,
+// W_pad[mb*128 + o][kb*64 + kk] (bf16) = W[o][k(kb, kk)] with zero padding; with rep_rows < rows_pad
+// the padded rows repeat W every rep_rows rows.
+__global__ void pack_w_kernel(const void* W, int w_bf16, int d_out, int d_in, int rows_pad, int rep_rows, int n_kb,
                               const int* kb_kofs, const int* kb_width_left, uint16_t* wp) {
     const int cols = n_kb * 64;
     const int n = rows_pad * cols;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int row = i / cols, cc = i - row * cols;
+        const int prow = i / cols, cc = i - prow * cols;
+        const int row = prow % rep_rows;  // replicated copies of W
         const int kb = cc >> 6, kk = cc & 63;
         uint16_t v = 0;
         if (row < d_out && kk < kb_width_left[kb]) {
@@ -526,11 +536,14 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     }
     const bool multi = p.br.size() > 1;
     if (multi) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));
-    // boundary partials per half-tile
+    // replicas of W in the lane quarters, and the column unit of the SUM walk / boundary partials
     const int half_n = tile_n / 2;
-    int64_t max_halves = 1;
-    for (auto& b : p.br) max_halves = std::max<int64_t>(max_halves, ceil_div(b.m, half_n));
-    RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * max_halves));
+    int rep = m_blocks == 1 ? (p.d_out <= 32 ? 4 : (p.d_out <= 64 ? 2 : 1)) : 1;
+    while (rep > 1 && half_n / rep < 32) rep /= 2;
+    const int unit = half_n / rep;
+    int64_t max_units = 1;
+    for (auto& b : p.br) max_units = std::max<int64_t>(max_units, ceil_div(b.m, unit));
+    RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * max_units));
     const int rows_pad = m_blocks * 128;
     const size_t wp_elems = (size_t)rows_pad * L.n_kb * 64;
     RELNN_TRY(p.wpack.alloc(wp_elems * 2 + 256));
@@ -565,7 +578,7 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         if (b.m == 0) continue;
-        { pack_w_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, rows_pad, L.n_kb, d_meta,
+        { pack_w_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, rows_pad, rows_pad / rep, L.n_kb, d_meta,
                                           d_meta + kMaxKb, p.wpack.as<uint16_t>()); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
         TcArgs a{};
@@ -597,6 +610,7 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         a.n_kb = L.n_kb;
         a.tile_n = tile_n;
         a.m_blocks = m_blocks;
+        a.rep = rep;
         a.stages = stages;
         a.idesc = tc::idesc_bf16_f32(128, tile_n);
         a.tmem_cols = (uint32_t)(2 * m_blocks * tile_n) <= 256 ? 256u : 512u;
@@ -610,7 +624,7 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
         { ProfToken pt = prof_begin(RELNN_PROF_FWD_TC, st); fwd_tc_kernel<<<grid, kThreads, smem, st>>>(wmap, a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
-        launch_fixup(a.seg, a.m, half_n, ceil_div(a.m, half_n), a.carry, out, p.d_out, multi, p.kahan, st);
+        launch_fixup(a.seg, a.m, unit, ceil_div(a.m, unit), a.carry, out, p.d_out, multi, p.kahan, st);
         RELNN_CUDA(cudaGetLastError());
     }
     return RELNN_OK;
