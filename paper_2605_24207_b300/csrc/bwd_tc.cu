@@ -36,6 +36,7 @@ constexpr int kThreads = 416;
 constexpr int kProducerThreads = 256;
 constexpr int kMmaWarp = 8;
 constexpr int kMaxKb = 4;  // input-feature K blocks (d_in <= 256)
+constexpr int kMaxMbk = 2; // GEMM A row blocks of 128 (d_in <= 256)
 constexpr int kSmemLimit = 227 * 1024;
 
 struct BwArgs {
@@ -57,20 +58,79 @@ struct BwArgs {
     int z_bf16, r_bf16, d, d_r, d_in, d_out, concat_dst, mask_words;
     int n_kb, d_in_pad, mbk, tile_n, stages;
     int x_blocks;           // K blocks of X staged per tile (n_kb in the dst pass, 0 in the src pass)
+    int dy_blocks;          // blocks of 64 outputs in dY (d_out <= 64: 1; GEMM B then computes dW rows
+                            // 64-127 from whatever follows the dY block and they are never read)
     int src_pass;           // 1: tuples in src order; hd then holds each tuple's row in output order
                             // (its ReLU mask row), hs the src H rows (non-decreasing), seg their output rows
     uint32_t idesc_dx, idesc_dw, tmem_cols, d2_col;
     int kb_src[kMaxKb], kb_col[kMaxKb], kb_width[kMaxKb];
+    // GEMM A rows of this pass: TMEM lane quarter i (block i / 4) holds Concat part qpart[i] (0 z_src,
+    // 1 z_dst, 2 r, -1 none) from column qcol0[i]; with rep > 1 the quarters repeat rep times and
+    // the warps of equal rows share the tile's columns
+    int qpart[4 * kMaxMbk], qcol0[4 * kMaxMbk];
+    int rep;
     int need_arr[3];
 };
+
+// dY rows of one producer thread (rows row_base .. row_base + rpt - 1, 16-byte chunk `chunk` of each
+// 64-output block): dOut[seg_t] masked by the ReLU mask of tuple t, rounded to bf16 into the
+// 128B-swizzled dY blocks, and added to the thread's db partial. RB rows' loads are issued before
+// any is used; OB = blocks of 64 outputs.
+template <int RB, int OB>
+__device__ __forceinline__ void build_dy(const BwArgs& a, const int32_t* islot, int N, int64_t t0, int row_base,
+                                         int rpt, int chunk, uint32_t dyb, float (&dbacc)[2][8]) {
+#pragma unroll
+    for (int j0 = 0; j0 < 4; j0 += RB) {
+        if (j0 >= rpt) break;
+        float4 u[RB][OB][2];
+        uint32_t bits[RB][OB];
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+            const int row = row_base + j0 + jj;
+            const bool in = j0 + jj < rpt;
+            const bool tv = in && (t0 + row < a.m);
+            const int sg = tv ? islot[3 * N + row] : 0;
+            const int64_t mrow = a.src_pass ? (int64_t)(in ? islot[N + row] : 0) : t0 + row;
+#pragma unroll
+            for (int ob = 0; ob < OB; ++ob) {
+                const int o0 = ob * 64 + chunk * 8;
+                const bool ld = tv && o0 < a.d_out;
+                const float4* q = reinterpret_cast<const float4*>(a.dout + (int64_t)sg * a.d_out + o0);
+                u[jj][ob][0] = ld ? __ldg(q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                u[jj][ob][1] = ld ? __ldg(q + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                bits[jj][ob] = (ld && a.mask) ? __ldg(a.mask + mrow * a.mask_words + (o0 >> 5)) >> (o0 & 31)
+                                              : 0xffffffffu;
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+            if (j0 + jj >= rpt) break;
+            const int row = row_base + j0 + jj;
+#pragma unroll
+            for (int ob = 0; ob < OB; ++ob) {
+                float v[8] = {u[jj][ob][0].x, u[jj][ob][0].y, u[jj][ob][0].z, u[jj][ob][0].w,
+                              u[jj][ob][1].x, u[jj][ob][1].y, u[jj][ob][1].z, u[jj][ob][1].w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    v[k] = ((bits[jj][ob] >> k) & 1u) ? v[k] : 0.f;
+                    dbacc[ob][k] += v[k];
+                }
+                const uint32_t dst = dyb + (uint32_t)ob * N * 128u + (uint32_t)row * 128u +
+                                     ((uint32_t)(chunk ^ (row & 7)) << 4);
+                st_shared_v4(dst, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                             pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+            }
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
 bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__ BwArgs a) {
     extern __shared__ uint8_t dyn_smem[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~(uintptr_t)1023);
     const int N = a.tile_n;
-    const uint32_t wt_bytes = (uint32_t)a.mbk * 2u * 16384u;          // W^T: mbk x 2 blocks of 128 x 64
-    const uint32_t dy_bytes = 2u * (uint32_t)N * 128u;                  // dY: 2 blocks of 64 outputs
+    const uint32_t wt_bytes = (uint32_t)(a.mbk * a.dy_blocks) * 16384u;   // W^T: mbk x dy_blocks of 128 x 64
+    const uint32_t dy_bytes = (uint32_t)a.dy_blocks * N * 128u;             // dY: blocks of 64 outputs
     const uint32_t x_bytes = (uint32_t)a.x_blocks * (uint32_t)N * 128u; // X: x_blocks blocks of 64 inputs
     const uint32_t stage_bytes = dy_bytes + x_bytes;
     uint8_t* wt_smem = base;
@@ -153,50 +213,10 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                     uint8_t* stg = st_smem + (size_t)s * stage_bytes;
                     const uint32_t dyb = smem_u32(stg);
                     const uint32_t xb = smem_u32(stg + dy_bytes);
-                    // dY rows: dOut[seg_t] masked by the stored ReLU mask, as bf16; 2 blocks of 64 outputs.
-                    // All loads of this thread's rows are issued before any is used.
-#pragma unroll
-                    for (int j0 = 0; j0 < 4; j0 += 2) {
-                        if (j0 >= rpt) break;
-                        float4 u[2][2][2];
-                        uint32_t bits[2][2];
-#pragma unroll
-                        for (int jj = 0; jj < 2; ++jj) {
-                            const int row = row_base + j0 + jj;
-                            const bool tv = (j0 + jj < rpt) && (t0 + row < a.m);
-                            const int sg = tv ? islot[3 * N + row] : 0;
-                            const int64_t mrow = a.src_pass ? (int64_t)islot[N + row] : t0 + row;
-#pragma unroll
-                            for (int ob = 0; ob < 2; ++ob) {
-                                const int o0 = ob * 64 + chunk * 8;
-                                const bool ld = tv && o0 < a.d_out;
-                                const float4* q = reinterpret_cast<const float4*>(a.dout + (int64_t)sg * a.d_out + o0);
-                                u[jj][ob][0] = ld ? __ldg(q) : make_float4(0.f, 0.f, 0.f, 0.f);
-                                u[jj][ob][1] = ld ? __ldg(q + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-                                bits[jj][ob] = (ld && a.mask) ? __ldg(a.mask + mrow * a.mask_words + (o0 >> 5)) >> (o0 & 31)
-                                                              : 0xffffffffu;
-                            }
-                        }
-#pragma unroll
-                        for (int jj = 0; jj < 2; ++jj) {
-                            if (j0 + jj >= rpt) break;
-                            const int row = row_base + j0 + jj;
-#pragma unroll
-                            for (int ob = 0; ob < 2; ++ob) {
-                                float v[8] = {u[jj][ob][0].x, u[jj][ob][0].y, u[jj][ob][0].z, u[jj][ob][0].w,
-                                              u[jj][ob][1].x, u[jj][ob][1].y, u[jj][ob][1].z, u[jj][ob][1].w};
-#pragma unroll
-                                for (int k = 0; k < 8; ++k) {
-                                    v[k] = ((bits[jj][ob] >> k) & 1u) ? v[k] : 0.f;
-                                    dbacc[ob][k] += v[k];
-                                }
-                                const uint32_t dst = dyb + (uint32_t)ob * N * 128u + (uint32_t)row * 128u +
-                                                     ((uint32_t)(chunk ^ (row & 7)) << 4);
-                                st_shared_v4(dst, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                                             pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-                            }
-                        }
-                    }
+                    // dY rows: dOut[seg_t] masked by the stored ReLU mask, as bf16, in blocks of 64
+                    // outputs; up to 4 rows' loads in flight before any is used
+                    if (a.dy_blocks == 1) build_dy<4, 1>(a, islot, N, t0, row_base, rpt, chunk, dyb, dbacc);
+                    else build_dy<2, 2>(a, islot, N, t0, row_base, rpt, chunk, dyb, dbacc);
                     // X rows, K-block by K-block (as in the forward); the src pass needs no dW
                     for (int kb = 0; kb < a.x_blocks; ++kb) {
                         const int src = a.kb_src[kb];
@@ -260,7 +280,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
             for (int ob = 0; ob < 2; ++ob)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    float v = dbacc[ob][k];
+                    float v = ob < a.dy_blocks ? dbacc[ob][k] : 0.f;
                     v += __shfl_xor_sync(0xffffffffu, v, 8);
                     v += __shfl_xor_sync(0xffffffffu, v, 16);
                     if (lane < 8) db_smem[warp * 128 + ob * 64 + chunk * 8 + k] = v;
@@ -278,8 +298,8 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
             const uint32_t wb = smem_u32(wbar);
             mbar_arrive_expect_tx(wb, wt_bytes);
             for (int mb = 0; mb < a.mbk; ++mb)
-                for (int kk = 0; kk < 2; ++kk)
-                    tma_load_2d(smem_u32(wt_smem + (size_t)(mb * 2 + kk) * 16384u), &wtmap, kk * 64, mb * 128, wb);
+                for (int kk = 0; kk < a.dy_blocks; ++kk)
+                    tma_load_2d(smem_u32(wt_smem + (size_t)(mb * a.dy_blocks + kk) * 16384u), &wtmap, kk * 64, mb * 128, wb);
             bool ok = mbar_wait(wb, 0, a.status, abort_flag);
             tc_fence_after();
             int lt = 0;
@@ -297,10 +317,10 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                 // GEMM A: dX^T for this tile
                 const uint32_t d2 = tmem_base + a.d2_col + (uint32_t)acc * d2_stride;
                 for (int mb = 0; mb < a.mbk; ++mb)
-                    for (int kk = 0; kk < 2; ++kk)
+                    for (int kk = 0; kk < a.dy_blocks; ++kk)
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            const uint64_t ad = sw128_kmajor_desc(smem_u32(wt_smem + (size_t)(mb * 2 + kk) * 16384u) + k * 32);
+                            const uint64_t ad = sw128_kmajor_desc(smem_u32(wt_smem + (size_t)(mb * a.dy_blocks + kk) * 16384u) + k * 32);
                             const uint64_t bd = sw128_kmajor_desc(dyb + (uint32_t)kk * N * 128u + k * 32);
                             mma_bf16(d2 + (uint32_t)mb * N, ad, bd, a.idesc_dx, (kk | k) != 0);
                         }
@@ -321,18 +341,20 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
     } else {
         // ------------------------------------------------------------------ epilogue
         const int q = warp & 3;
-        int32_t* wix = epi_smem + (warp - kMmaWarp - 1) * 3 * N;  // hs, hd, er of the tile
+        const int span = N / a.rep;                     // columns of each tile this warp reduces
+        const int c0 = (q / (4 / a.rep)) * span;        // the first of them
+        int32_t* wix = epi_smem + (warp - kMmaWarp - 1) * 3 * N;  // hs, hd, er of those columns
         int lt = 0;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
-            const int64_t t0 = tile * N;
-            const int nt = (int)imin64(N, a.m - t0);
+            const int64_t t0 = tile * N + c0;
+            const int ntl = (int)imin64(span, a.m - t0);  // <= 0: nothing in this warp's columns
             __syncwarp();
-            for (int rr = lane; rr < N; rr += 32) {
-                const bool v = rr < nt;
+            for (int rr = lane; rr < span; rr += 32) {
+                const bool v = rr < ntl;
                 wix[rr] = v ? __ldg(a.hs + t0 + rr) : 0;
-                wix[N + rr] = (v && a.concat_dst) ? __ldg(a.hd + t0 + rr) : -1;
-                wix[2 * N + rr] = (v && a.d_r > 0) ? __ldg(a.er + t0 + rr) : 0;
+                wix[N + rr] = (v && a.concat_dst && !a.src_pass) ? __ldg(a.hd + t0 + rr) : -1;
+                wix[2 * N + rr] = (v && a.dr) ? __ldg(a.er + t0 + rr) : 0;
             }
             __syncwarp();
             const int acc = lt & 1;
@@ -343,48 +365,42 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
             }
             tc_fence_after();
             for (int mb = 0; mb < a.mbk; ++mb) {
-                const int kbase = mb * 128 + 32 * q;  // padded K row of lane 0
-                if (kbase >= a.d_in_pad) continue;
-                // which Concat slice (and column in it) this lane's padded K row holds
-                const int kr = kbase + lane;
-                const int kblk = kr >> 6;
-                const int part = a.kb_src[kblk < a.n_kb ? kblk : 0];
-                const int kk = a.kb_col[kblk < a.n_kb ? kblk : 0] + (kr & 63);
-                const bool k_ok = kblk < a.n_kb && kk < a.kb_width[kblk];
+                const int part = a.qpart[mb * 4 + q];  // warp-uniform
+                if (part < 0) continue;
+                const int kk = a.qcol0[mb * 4 + q] + lane;  // this lane's column of the part
+                const bool k_ok = kk < (part == 2 ? a.d_r : a.d);
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + a.d2_col + (uint32_t)acc * d2_stride +
-                                       (uint32_t)mb * N;
-                for (int c = 0; c * 32 < nt; ++c) {
+                                       (uint32_t)(mb * N + c0);
+                for (int c = 0; c * 32 < ntl; ++c) {
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
                     tmem_ld_wait();
-                    const int cnt = min(32, nt - c * 32);
-                    if ((part == 1 && !a.src_pass) || (part == 0 && a.src_pass)) {
+                    const int cnt = min(32, ntl - c * 32);
+                    if (part != 2) {
                         // runs of equal dst (dst pass) or src (src pass) H rows inside the chunk (the
                         // tuples are sorted by it): a segmented running sum in registers, then one
                         // add per run end
-                        const int32_t* keyv = part == 1 ? wix + N : wix;
-                        const int li = c * 32 + lane;
-                        const int h = keyv[li];
+                        const int32_t* keyv = (part == 1 ? wix + N : wix) + c * 32;
+                        const int h = keyv[lane];
                         const bool tvalid = lane < cnt;
-                        const bool nx_diff = (lane == cnt - 1) || (li + 1 < N && keyv[li + 1] != h);
+                        const bool nx_diff = (lane == cnt - 1) || (lane + 1 < cnt && keyv[lane + 1] != h);
                         const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && nx_diff);
                         const unsigned startmask = (endmask << 1) | 1u;
                         float sum = 0.f, comp = 0.f;
                         uint32_t mword = 0;
                         seg_scan<false, false, false>(v, 0.f, startmask, sum, comp, mword, lane);
-                        for (unsigned em = endmask; em; em &= em - 1u) {
-                            const int j = __ffs(em) - 1;
-                            const float val = __uint_as_float(select32(v, j));
-                            const int hj = keyv[c * 32 + j];
-                            if (k_ok && a.dz) atomicAdd(a.dz + (int64_t)hj * a.d + kk, val);
-                        }
-                    } else if (a.src_pass || part == 0) {
-                        // the other pass adds this slice
-                    } else {
+                        float* dzc = a.dz + kk;
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
-                            if (j < cnt && k_ok && a.dr)
-                                atomicAdd(a.dr + (int64_t)wix[2 * N + c * 32 + j] * a.d_r + kk, __uint_as_float(v[j]));
+                            if ((endmask >> j) & 1u) {
+                                if (k_ok) atomicAdd(dzc + (int64_t)keyv[j] * a.d, __uint_as_float(v[j]));
+                            }
+                    } else {
+                        const int32_t* erv = wix + 2 * N + c * 32;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < cnt && k_ok)
+                                atomicAdd(a.dr + (int64_t)erv[j] * a.d_r + kk, __uint_as_float(v[j]));
                     }
                 }
             }
@@ -501,41 +517,99 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
     if (p.concat_dst) add_part(1, p.d, p.d);
     if (p.br[0].d_r) add_part(2, p.br[0].d_r, p.d * (p.concat_dst ? 2 : 1));
     const int d_in_pad = n_kb * 64;
-    const int mbk = (d_in_pad + 127) / 128;
-    while ((int)row_src.size() < mbk * 128) row_src.push_back(-1);
-    // Tile size per pass: 128 tuples when three stages fit, else 64. The src pass stages only dY.
-    const uint32_t wt_bytes = (uint32_t)mbk * 2u * 16384u;
     const uint32_t d2_col = (uint32_t)((d_in_pad + 31) / 32 * 32);
+    // GEMM A rows of each pass: the dst pass needs dX for the z_dst and r slices, the src pass for
+    // the z_src slice. Each part fills whole 32-row lane quarters; one or two quarters are repeated
+    // to fill the 128 lanes (so every epilogue warp has work).
+    struct PassMap {
+        std::vector<int> rows;  // input feature of each GEMM A row (-1 = padding), mbk * 128
+        int mbk = 1, rep = 1;
+        int qpart[4 * kMaxMbk], qcol0[4 * kMaxMbk];
+    };
+    auto make_map = [&](bool src_slice) {
+        PassMap m;
+        std::vector<std::pair<int, int>> qs;  // (part, first column) per quarter
+        std::vector<int> rows;
+        auto add = [&](int part, int width, int kofs) {
+            for (int c = 0; c < width; c += 32) {
+                qs.push_back({part, c});
+                for (int i = 0; i < 32; ++i) rows.push_back(c + i < width ? kofs + c + i : -1);
+            }
+        };
+        if (src_slice) add(0, p.d, 0);
+        else {
+            if (p.concat_dst) add(1, p.d, p.d);
+            if (p.br[0].d_r) add(2, p.br[0].d_r, p.d * (p.concat_dst ? 2 : 1));
+        }
+        if (qs.empty()) {
+            qs.push_back({-1, 0});
+            rows.assign(32, -1);
+        }
+        const int nq = (int)qs.size();
+        m.rep = nq == 1 ? 4 : (nq == 2 ? 2 : 1);
+        const int per = m.rep > 1 ? 4 / m.rep : 4 * ((nq + 3) / 4);  // quarters of one copy
+        while ((int)qs.size() < per) {
+            qs.push_back({-1, 0});
+            rows.insert(rows.end(), 32, -1);
+        }
+        for (int r = 1; r < m.rep; ++r)
+            for (int i = 0; i < per; ++i) {
+                qs.push_back(qs[i]);
+                rows.insert(rows.end(), rows.begin() + 32 * i, rows.begin() + 32 * (i + 1));
+            }
+        m.mbk = (int)qs.size() / 4;
+        for (int i = 0; i < 4 * kMaxMbk; ++i) {
+            m.qpart[i] = i < (int)qs.size() ? qs[i].first : -1;
+            m.qcol0[i] = i < (int)qs.size() ? qs[i].second : 0;
+        }
+        m.rows = rows;
+        return m;
+    };
+    const PassMap dmap = make_map(false), smap = make_map(true);
+    const int dy_blocks = (p.d_out + 63) / 64;
+    // quarter table of a pass at the tile's replication (copies beyond it are switched off, so no
+    // two warps reduce the same rows over the same columns)
+    auto fill_quarters = [](BwArgs& a, const PassMap& pm, int rep) {
+        for (int k = 0; k < 4 * kMaxMbk; ++k) {
+            const bool on = (k % 4) % (4 / rep) < 4 / pm.rep;
+            a.qpart[k] = on ? pm.qpart[k] : -1;
+            a.qcol0[k] = pm.qcol0[k];
+        }
+        a.rep = rep;
+    };
+    if (dmap.mbk > kMaxMbk || smap.mbk > kMaxMbk) return backward_fp32(p, io_in, g, st);
+    // Tile size per pass: 128 tuples when three stages and the TMEM columns fit, else 64. The src
+    // pass stages only dY.
     struct PassCfg {
-        int N = 0, stages = 0;
-        uint32_t tmem_cols = 0;
+        int N = 0, stages = 0, rep = 1;
+        uint32_t tmem_cols = 0, wt_bytes = 0;
         size_t smem = 0;
     };
-    auto pass_cfg = [&](int x_blocks) {
+    auto pass_cfg = [&](int x_blocks, const PassMap& pm) {
         PassCfg c;
-        auto stage_of = [&](int N) { return 2u * N * 128u + (uint32_t)x_blocks * N * 128u; };
+        c.wt_bytes = (uint32_t)(pm.mbk * dy_blocks) * 16384u;
+        auto stage_of = [&](int N) { return (uint32_t)dy_blocks * N * 128u + (uint32_t)x_blocks * N * 128u; };
         auto aux_of = [&](int N) { return (uint32_t)(20 * N * 4 + (kProducerThreads / 32) * 128 * 4); };
         auto stages_at = [&](int N) {
-            return (int)((kSmemLimit - 1024 - 256 - (int)wt_bytes - (int)aux_of(N)) / (int)stage_of(N));
+            return (int)((kSmemLimit - 1024 - 256 - (int)c.wt_bytes - (int)aux_of(N)) / (int)stage_of(N));
         };
         c.N = 128;
         c.stages = stages_at(128);
-        if (c.stages < 3 || d2_col + 2u * mbk * 128u > 512u) {
+        if (c.stages < 3 || d2_col + 2u * pm.mbk * 128u > 512u) {
             c.N = 64;
             c.stages = stages_at(64);
         }
         c.stages = std::min(c.stages, 6);
-        const uint32_t cols_needed = d2_col + 2u * mbk * c.N;
+        c.rep = std::min(pm.rep, c.N / 32);
+        const uint32_t cols_needed = d2_col + 2u * pm.mbk * c.N;
         if (c.stages < 2 || cols_needed > 512) c.stages = 0;  // not runnable
         c.tmem_cols = cols_needed <= 256 ? 256u : 512u;
-        c.smem = 1024 + wt_bytes + (size_t)c.stages * stage_of(c.N) + aux_of(c.N) + 256;
+        c.smem = 1024 + c.wt_bytes + (size_t)c.stages * stage_of(c.N) + aux_of(c.N) + 256;
         return c;
     };
-    const PassCfg dcfg = pass_cfg(n_kb), scfg = pass_cfg(0);
+    const PassCfg dcfg = pass_cfg(n_kb, dmap), scfg = pass_cfg(0, smap);
     if (dcfg.stages == 0 || scfg.stages == 0) return backward_fp32(p, io_in, g, st);
-    const int N = dcfg.N, stages = dcfg.stages;
-    const uint32_t tmem_cols = dcfg.tmem_cols;
-    const size_t smem = dcfg.smem;
+    const int N = dcfg.N;
 
     // f32 z is gathered as a bf16 copy (the rounding the kernel applies anyway), by cp.async
     CallIO io;
@@ -552,7 +626,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
     }
     if (g.dz) RELNN_CUDA(cudaMemsetAsync(g.dz, 0, sizeof(float) * p.n_h * p.d, st));
     const int grid_max = num_sms();
-    const size_t wt_elems = (size_t)mbk * 128 * 128;
+    const size_t wt_d_elems = (size_t)dmap.mbk * 128 * 128, wt_s_elems = (size_t)smap.mbk * 128 * 128;
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         float* dW = g.dW.size() > i ? g.dW[i] : nullptr;
@@ -570,31 +644,45 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         }
         const int64_t n_tiles = ceil_div(b.m, N);
         const int grid = (int)std::min<int64_t>(n_tiles, grid_max);
-        // scratch: W^T (bf16), row map, dW partials
+        // scratch: W^T row blocks of the two passes (bf16), their row maps, the X column map, and
+        // the dW / db partials
         const size_t part_elems = (size_t)grid * p.d_out * p.d_in;
         const size_t dbp_elems = (size_t)grid * p.d_out;
-        const size_t bytes = wt_elems * 2 + sizeof(int) * row_src.size() + 256 + sizeof(float) * (part_elems + dbp_elems);
-        RELNN_TRY(p.scratch.alloc(bytes));
-        uint16_t* wt = p.scratch.as<uint16_t>();
-        int* d_rows = reinterpret_cast<int*>(p.scratch.as<uint8_t>() + wt_elems * 2);
-        float* part = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + ((wt_elems * 2 + sizeof(int) * row_src.size() + 255) & ~(size_t)255));
+        const size_t n_maps = dmap.rows.size() + smap.rows.size() + row_src.size();
+        const size_t head = ((wt_d_elems + wt_s_elems) * 2 + sizeof(int) * n_maps + 255) & ~(size_t)255;
+        RELNN_TRY(p.scratch.alloc(head + sizeof(float) * (part_elems + dbp_elems)));
+        uint16_t* wt_d = p.scratch.as<uint16_t>();
+        uint16_t* wt_s = wt_d + wt_d_elems;
+        int* d_maps = reinterpret_cast<int*>(wt_s + wt_s_elems);
+        int* d_rows = d_maps + dmap.rows.size() + smap.rows.size();
+        float* part = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + head);
         float* db_part = part + part_elems;
-        RELNN_CUDA(cudaMemcpyAsync(d_rows, row_src.data(), sizeof(int) * row_src.size(), cudaMemcpyHostToDevice, st));
-        { pack_wt_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, mbk * 128, d_rows, wt); note_launch(); }
-        CUtensorMap wtmap;
         {
+            std::vector<int> maps(dmap.rows);
+            maps.insert(maps.end(), smap.rows.begin(), smap.rows.end());
+            maps.insert(maps.end(), row_src.begin(), row_src.end());
+            RELNN_CUDA(cudaMemcpyAsync(d_maps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, st));
+        }
+        { pack_wt_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, dmap.mbk * 128, d_maps, wt_d); note_launch(); }
+        if (g.dz) { pack_wt_kernel<<<64, 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, smap.mbk * 128,
+                                                       d_maps + dmap.rows.size(), wt_s); note_launch(); }
+        auto make_tmap = [&](CUtensorMap& m, uint16_t* wt, int mbk) -> relnn_status {
             cuuint64_t gdim[2] = {128, (cuuint64_t)mbk * 128};
             cuuint64_t gstride[1] = {128 * 2};
             cuuint32_t box[2] = {64, 128};
             cuuint32_t estr[2] = {1, 1};
-            CUresult r = enc(&wtmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, wt, gdim, gstride, box, estr,
+            CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, wt, gdim, gstride, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) {
                 set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
                 return RELNN_ECUDA;
             }
-        }
+            return RELNN_OK;
+        };
+        CUtensorMap wtmap_d, wtmap_s;
+        RELNN_TRY(make_tmap(wtmap_d, wt_d, dmap.mbk));
+        RELNN_TRY(make_tmap(wtmap_s, wt_s, smap.mbk));
         BwArgs a{};
         a.z = io.z;
         a.r = io.br[i].r;
@@ -622,13 +710,15 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         a.mask_words = ((p.d_out + 127) / 128) * 4;
         a.n_kb = n_kb;
         a.d_in_pad = d_in_pad;
-        a.mbk = mbk;
+        a.mbk = dmap.mbk;
+        fill_quarters(a, dmap, dcfg.rep);
         a.tile_n = N;
-        a.stages = stages;
+        a.stages = dcfg.stages;
         a.x_blocks = n_kb;
+        a.dy_blocks = dy_blocks;
         a.idesc_dx = tc::idesc_bf16_f32(128, N);
         a.idesc_dw = tc::idesc_bf16_f32(128, d_in_pad, true, true);
-        a.tmem_cols = tmem_cols;
+        a.tmem_cols = dcfg.tmem_cols;
         a.d2_col = d2_col;
         a.need_arr[0] = a.need_arr[1] = a.need_arr[2] = 0;
         for (int k = 0; k < n_kb; ++k) {
@@ -637,7 +727,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
             a.kb_width[k] = kb_width[k];
             a.need_arr[kb_src[k]] = 1;
         }
-        { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<grid, kThreads, smem, st>>>(wtmap, a); note_launch(); prof_end(pt, st); }
+        { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<grid, kThreads, dcfg.smem, st>>>(wtmap_d, a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
         if (g.dz) {
             // src pass: the src slice of dX over the tuples in src order, one add per run
@@ -647,6 +737,8 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
             s2.x_blocks = 0;
             s2.tile_n = scfg.N;
             s2.stages = scfg.stages;
+            s2.mbk = smap.mbk;
+            fill_quarters(s2, smap, scfg.rep);
             s2.n_tiles = ceil_div(b.m, scfg.N);
             s2.idesc_dx = tc::idesc_bf16_f32(128, scfg.N);
             s2.tmem_cols = scfg.tmem_cols;
@@ -660,7 +752,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
             s2.need_arr[0] = 1;
             s2.need_arr[1] = relu ? 1 : 0;
             s2.need_arr[2] = 0;
-            { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<sgrid, kThreads, scfg.smem, st>>>(wtmap, s2); note_launch(); prof_end(pt, st); }
+            { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<sgrid, kThreads, scfg.smem, st>>>(wtmap_s, s2); note_launch(); prof_end(pt, st); }
             RELNN_CUDA(cudaGetLastError());
         }
         if (dW) {
