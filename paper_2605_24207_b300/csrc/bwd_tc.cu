@@ -390,11 +390,21 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                         uint32_t mword = 0;
                         seg_scan<false, false, false>(v, 0.f, startmask, sum, comp, mword, lane);
                         float* dzc = a.dz + kk;
+                        // one add per run end, four ends at a time (independent selects and adds)
+                        for (unsigned em = endmask; em;) {
+                            int jj[4];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if ((endmask >> j) & 1u) {
-                                if (k_ok) atomicAdd(dzc + (int64_t)keyv[j] * a.d, __uint_as_float(v[j]));
+                            for (int g = 0; g < 4; ++g) {
+                                jj[g] = em ? __ffs(em) - 1 : -1;
+                                em &= em - 1u;
                             }
+#pragma unroll
+                            for (int g = 0; g < 4; ++g) {
+                                const uint32_t val = select32(v, jj[g] & 31);
+                                const int hj = keyv[jj[g] & 31];
+                                if (jj[g] >= 0 && k_ok) atomicAdd(dzc + (int64_t)hj * a.d, __uint_as_float(val));
+                            }
+                        }
                     } else {
                         const int32_t* erv = wix + 2 * N + c * 32;
 #pragma unroll

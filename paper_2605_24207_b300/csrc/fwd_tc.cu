@@ -150,6 +150,9 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
             const int32_t* islot = idx_smem + (lt % kIdxSlots) * 3 * a.tile_n;
             // indices two tiles ahead (that slot was last read two tiles ago, before a barrier)
             issue_idx(tile + 2 * (int64_t)gridDim.x, (lt + 2) % kIdxSlots);
+            // this thread's row indices, reloaded only when the K block reads another Concat part
+            int32_t ridx[kMaxRows];
+            int ridx_src = -1;
             for (int kb = 0; kb < a.n_kb; ++kb) {
                 if (!ok) break;
                 const int s = it % a.stages;
@@ -163,11 +166,13 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 const uint32_t sbase = smem_u32(st_smem + (size_t)s * stage_bytes);
                 const int col = a.kb_col[kb] + chunk * 8;
                 const bool in_part = col < a.kb_width[kb];
-                int32_t ridx[kMaxRows];
+                if (src != ridx_src) {
 #pragma unroll
-                for (int k = 0; k < kMaxRows; ++k) {
-                    const int row = rg + k * kRowGroups;
-                    ridx[k] = row < a.tile_n ? rows_idx[row] : 0;
+                    for (int k = 0; k < kMaxRows; ++k) {
+                        const int row = rg + k * kRowGroups;
+                        ridx[k] = row < a.tile_n ? rows_idx[row] : 0;
+                    }
+                    ridx_src = src;
                 }
                 // destination of row `row`: 128-byte line, 16-byte chunk swizzled by the row (SW128)
                 auto dst_of = [&](int row) {
@@ -369,19 +374,33 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         else if (relu) seg_scan<true, false, false>(v, bo, startmask, sum, comp, mword, lane);
                         else seg_scan<false, false, false>(v, bo, startmask, sum, comp, mword, lane);
                     }
-                    // one store per piece end (uniform loop over the set bits)
-                    for (unsigned em = endmask; em; em &= em - 1u) {
-                        const int j = __ffs(em) - 1;
-                        const float val = __uint_as_float(select32(v, j));
-                        const int s = wseg[c * 32 + j];
-                        const bool last = (c * 32 + j == nt - 1);
-                        const int sn = last ? ((nt == unit) ? after_seg : -1) : s + 1;
-                        const bool split = (first && prev_seg == s) || (last && sn == s);
-                        if (o_ok) {
-                            if (split) __stcg(a.carry + (vtile * 2 + (first ? 0 : 1)) * a.d_out + o, val);
-                            else emit_out(a.out + (int64_t)s * a.d_out + o, val, a.accumulate);
+                    // one store per piece end (uniform loop over the set bits, four ends at a time so
+                    // that their register selects and stores overlap)
+                    for (unsigned em = endmask; em;) {
+                        int jj[4];
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            jj[g] = em ? __ffs(em) - 1 : -1;
+                            em &= em - 1u;
                         }
-                        first = false;
+                        uint32_t vv[4];
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) vv[g] = select32(v, jj[g] & 31);
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            if (jj[g] < 0) break;
+                            const int j = jj[g];
+                            const float val = __uint_as_float(vv[g]);
+                            const int s = wseg[c * 32 + j];
+                            const bool last = (c * 32 + j == nt - 1);
+                            const int sn = last ? ((nt == unit) ? after_seg : -1) : s + 1;
+                            const bool split = (first && prev_seg == s) || (last && sn == s);
+                            if (o_ok) {
+                                if (split) __stcg(a.carry + (vtile * 2 + (first ? 0 : 1)) * a.d_out + o, val);
+                                else emit_out(a.out + (int64_t)s * a.d_out + o, val, a.accumulate);
+                            }
+                            first = false;
+                        }
                     }
                     if (mask && tvalid) a.relu_mask[(t0 + li) * a.mask_words + mb * 4 + fq] = mword;
                 }
