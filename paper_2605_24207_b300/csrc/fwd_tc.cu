@@ -374,8 +374,13 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         else if (relu) seg_scan<true, false, false>(v, bo, startmask, sum, comp, mword, lane);
                         else seg_scan<false, false, false>(v, bo, startmask, sum, comp, mword, lane);
                     }
-                    // one store per piece end (uniform loop over the set bits, four ends at a time so
-                    // that their register selects and stores overlap)
+                    // one store per piece end: the running sums go back to TMEM and each end's column is
+                    // read back (four ends per round trip), instead of selecting registers by a run-time
+                    // index
+                    if (endmask) {
+                        tmem_st_32x32b_x32(taddr + (uint32_t)c * 32, v);
+                        tmem_st_wait();
+                    }
                     for (unsigned em = endmask; em;) {
                         int jj[4];
 #pragma unroll
@@ -385,7 +390,11 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         }
                         uint32_t vv[4];
 #pragma unroll
-                        for (int g = 0; g < 4; ++g) vv[g] = select32(v, jj[g] & 31);
+                        for (int g = 0; g < 4; ++g)
+                            vv[g] = jj[g] >= 0 ? tmem_ld_32x32b_x1(taddr + (uint32_t)(c * 32 + jj[g])) : 0u;
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) tmem_ld_after(vv[g]);
 #pragma unroll
                         for (int g = 0; g < 4; ++g) {
                             if (jj[g] < 0) break;
