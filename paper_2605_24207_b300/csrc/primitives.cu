@@ -6,10 +6,11 @@
 // Radix sort: the key bits are split into passes of equal width of at most 11 bits (a 20-bit key
 // takes two passes of 10). Each block owns a tile of 4096 keys split into 8 warp sub-tiles of 512
 // keys that a warp visits in 16 steps of 32. Pass = (1) per-block digit histogram with
-// warp-aggregated shared-memory counts, (2) exclusive scan of the digit-major histogram, (3) stable
-// scatter: a key's destination is digit base + (keys of its digit in earlier blocks) + (in earlier
-// warps of its block) + (in earlier steps of its warp) + (in lower lanes of its step), the last two
-// found with __match_any_sync / popc.
+// shared-memory atomics, (2) exclusive scan of the digit-major histogram, (3) stable scatter: a
+// key's destination is digit base + (keys of its digit in earlier blocks) + (in earlier warps of
+// its block) + (in earlier steps of its warp) + (in lower lanes of its step), the lanes of equal
+// digit found with one ballot per digit bit; the block reorders its tile by digit in shared memory
+// first, so each digit's keys are stored as one contiguous run.
 #include "primitives.cuh"
 
 #include <algorithm>
@@ -98,7 +99,8 @@ constexpr int kSortTile = kSortThreads * kSortSteps;  // 4096
 constexpr int kMaxDigitBits = 11;
 
 // Per-block digit counts of one pass (digit = (key >> shift) & mask, bins = mask + 1), stored
-// digit-major: hist[d * nblocks + block].
+// digit-major: hist[d * nblocks + block]. Shared-memory atomics per key (with 2^11 bins the lanes of
+// a warp rarely share a digit).
 template <class K>
 __global__ void rs_hist_kernel(const K* __restrict__ keys, int64_t n, int shift, unsigned mask,
                                int32_t* __restrict__ hist, int nblocks) {
@@ -110,26 +112,56 @@ __global__ void rs_hist_kernel(const K* __restrict__ keys, int64_t n, int shift,
     const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortSteps);
     for (int s = 0; s < kSortSteps; ++s) {
         int64_t i = base + s * 32 + lane;
-        bool valid = i < n;
-        unsigned d = valid ? (unsigned)((keys[i] >> shift) & mask) : 0xffffffffu - lane;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
+        if (i < n) atomicAdd(&h[(unsigned)((keys[i] >> shift) & mask)], 1);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < bins; i += kSortThreads) hist[(int64_t)i * nblocks + blockIdx.x] = h[i];
 }
 
+// Exclusive scan of v[0..count) in place by one block of kSortThreads threads (count <= 8 x 256).
+__device__ void block_excl_scan_small(int32_t* v, int count, int32_t* warp_tot) {
+    const int per = (count + kSortThreads - 1) / kSortThreads;
+    const int b0 = threadIdx.x * per;
+    int32_t run = 0;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < count) run += v[b0 + i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int32_t woff = 0;
+    for (int w = 0; w < warp; ++w) woff += warp_tot[w];
+    int32_t off = woff + incl - run;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < count) {
+            const int32_t t = v[b0 + i];
+            v[b0 + i] = off;
+            off += t;
+        }
+    __syncthreads();
+}
+
 // Stable scatter of one pass: a key's destination is its digit's base for this block (scanned
 // histogram) + the keys of that digit in earlier warps of the block + in earlier steps of its warp
-// + in lower lanes of its step (__match_any_sync / popc).
+// + in lower lanes of its step (__match_any_sync / popc). The block first reorders its tile by
+// digit in shared memory, so that each digit's keys leave as one contiguous run (coalesced stores).
 template <class K, class V>
 __global__ void rs_scatter_kernel(const K* __restrict__ keys, const V* __restrict__ vals,
                                   K* __restrict__ okeys, V* __restrict__ ovals, int64_t n,
                                   int shift, unsigned mask, const int32_t* __restrict__ offs, int nblocks) {
-    extern __shared__ int32_t sm[];
+    extern __shared__ __align__(16) int32_t sm[];
     const int bins = (int)mask + 1;
-    int32_t* gbase = sm;          // [bins]
-    int32_t* wcnt = sm + bins;    // [kSortWarps][bins]
+    int32_t* gbase = sm;                               // [bins]
+    int32_t* wcnt = sm + bins;                         // [kSortWarps][bins]
+    int32_t* dstart = wcnt + kSortWarps * bins;        // [bins] block-local start of each digit
+    int32_t* wtot = dstart + bins;                     // [kSortWarps]
+    K* tk = reinterpret_cast<K*>(sm + ((bins * (kSortWarps + 2) + kSortWarps + 3) & ~3));  // [kSortTile]
+    V* tv = reinterpret_cast<V*>(tk + kSortTile);                                        // [kSortTile]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < bins; i += kSortThreads) {
         gbase[i] = offs[(int64_t)i * nblocks + blockIdx.x];
@@ -152,15 +184,19 @@ __global__ void rs_scatter_kernel(const K* __restrict__ keys, const V* __restric
     for (int s = 0; s < kSortSteps; ++s) {
         int64_t i = base + s * 32 + lane;
         bool valid = i < n;
-        unsigned d = valid ? (unsigned)((k[s] >> shift) & mask) : 0xffffffffu - lane;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int leader = __ffs(peers) - 1;
-        int old = 0;
-        if (valid && lane == leader) {
-            old = wcnt[warp * bins + d];
-            wcnt[warp * bins + d] = old + __popc(peers);
+        unsigned d = valid ? (unsigned)((k[s] >> shift) & mask) : 0u;
+        // lanes with this lane's digit: one ballot per digit bit
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < kMaxDigitBits; ++b) {
+            if ((mask >> b) & 1u) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bb : ~bb;
+            }
         }
-        old = __shfl_sync(0xffffffffu, old, leader);
+        const int old = valid ? wcnt[warp * bins + d] : 0;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp * bins + d] = old + __popc(peers);
         rank[s] = old + __popc(peers & lanemask_lt());
         __syncwarp();
     }
@@ -173,17 +209,29 @@ __global__ void rs_scatter_kernel(const K* __restrict__ keys, const V* __restric
             wcnt[w * bins + i] = run;
             run += t;
         }
+        dstart[i] = run;  // the block's count of digit i, scanned next
     }
     __syncthreads();
+    block_excl_scan_small(dstart, bins, wtot);
 #pragma unroll
     for (int s = 0; s < kSortSteps; ++s) {
         int64_t i = base + s * 32 + lane;
         if (i < n) {
             unsigned d = (unsigned)((k[s] >> shift) & mask);
-            int64_t pos = (int64_t)gbase[d] + wcnt[warp * bins + d] + rank[s];
-            okeys[pos] = k[s];
-            ovals[pos] = v[s];
+            const int lp = dstart[d] + wcnt[warp * bins + d] + rank[s];
+            tk[lp] = k[s];
+            tv[lp] = v[s];
         }
+    }
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
+    const int cnt = (int)(n - t0 < kSortTile ? n - t0 : kSortTile);
+    for (int i = threadIdx.x; i < cnt; i += kSortThreads) {
+        const K key = tk[i];
+        const unsigned d = (unsigned)((key >> shift) & mask);
+        const int64_t pos = (int64_t)gbase[d] + (i - dstart[d]);
+        okeys[pos] = key;
+        ovals[pos] = tv[i];
     }
 }
 
@@ -229,11 +277,15 @@ relnn_status radix_sort_pairs(K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_
     const int bins = (int)mask + 1;
     RELNN_CHECK_ARG(nb64 * bins < (1ll << 31), "radix sort: too many keys");
     const int nb = (int)nb64;
-    const size_t scatter_smem = sizeof(int32_t) * (size_t)bins * (kSortWarps + 1);
+    auto smem_of = [](int nbins) {
+        return sizeof(int32_t) * (size_t)((nbins * (kSortWarps + 2) + kSortWarps + 3) & ~3) +
+               (sizeof(K) + sizeof(V)) * (size_t)kSortTile;
+    };
+    const size_t scatter_smem = smem_of(bins);
     static bool attr_set = false;
     if (!attr_set) {
-        const int max_smem = (int)(sizeof(int32_t) * (1u << kMaxDigitBits) * (kSortWarps + 1));
-        RELNN_CUDA(cudaFuncSetAttribute(rs_scatter_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        RELNN_CUDA(cudaFuncSetAttribute(rs_scatter_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_of(1 << kMaxDigitBits)));
         attr_set = true;
     }
     int32_t* hist = nullptr;
