@@ -40,6 +40,13 @@ constexpr int kEpiWarps = 8;
 constexpr int kIdxSlots = 3;    // row-index ring: the tile in production and the next two
 constexpr int kRowGroups = kProducerThreads / 8;                 // 28 rows per pass of the producers
 constexpr int kMaxRows = (256 + kRowGroups - 1) / kRowGroups;    // rows per producer thread per stage
+// Staged row indices: in row order (16-byte copies; each producer thread then reads its rows'
+// indices one by one, once per Concat part), or transposed when every part is a single K block
+// (entry (row group rg, k) = index of row rg + 28 k at rg * kIdxPitch + k, staged by 4-byte copies,
+// so a producer thread reads its rows' indices with three 16-byte loads).
+constexpr int kIdxPitch = 12;
+constexpr int kIdxArr = kRowGroups * kIdxPitch;                  // ints per staged index array
+static_assert(kMaxRows <= kIdxPitch && kIdxPitch % 4 == 0 && kIdxArr >= 256, "index layout");
 constexpr int kMaxKb = 12;
 constexpr int kSmemLimit = 227 * 1024;
 
@@ -68,6 +75,7 @@ struct TcArgs {
     int need_arr[3];      // which of hs, hd, er the K blocks read
 };
 
+template <bool IDX_T>
 __global__ void __launch_bounds__(kThreads, 1)
 fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ TcArgs a) {
     extern __shared__ uint8_t dyn_smem[];
@@ -80,7 +88,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
     int32_t* idx_smem = reinterpret_cast<int32_t*>(st_smem + (size_t)a.stages * stage_bytes);
     // output rows of the half-tile being reduced, one copy per epilogue warp
     const int half_n = a.tile_n / 2;
-    int32_t* seg_smem = idx_smem + kIdxSlots * 3 * a.tile_n;
+    int32_t* seg_smem = idx_smem + kIdxSlots * 3 * kIdxArr;
     uint64_t* bars = reinterpret_cast<uint64_t*>(seg_smem + kEpiWarps * half_n);
     uint64_t* full = bars;
     uint64_t* empty = bars + a.stages;
@@ -122,19 +130,33 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
         // warp instruction); the row indices of a stage are all loaded before the copies are issued.
         const int chunk = tid & 7;
         const int rg = tid >> 3;
-        // cp.async of one tile's hs / hd / er entries (16 bytes each, zero-filled past m) into a slot;
-        // committed as one group
-        const int q_per_arr = a.tile_n / 4;
+        // cp.async of one tile's hs / hd / er entries (4 bytes each, zero-filled past m) into a slot
+        // in the transposed layout; committed as one group
         auto issue_idx = [&](int64_t tile, int slot) {
-            int32_t* dstb = idx_smem + slot * 3 * a.tile_n;
-            for (int e = tid; e < 3 * q_per_arr; e += kProducerThreads) {
-                const int r = e / q_per_arr, qq = e - r * q_per_arr;
+            int32_t* dstb = idx_smem + slot * 3 * kIdxArr;
+            if (!IDX_T) {
+                const int q_per_arr = a.tile_n / 4;
+                for (int e = tid; e < 3 * q_per_arr; e += kProducerThreads) {
+                    const int r = e / q_per_arr, qq = e - r * q_per_arr;
+                    if (!a.need_arr[r]) continue;
+                    const int32_t* arr = r == 0 ? a.hs : (r == 1 ? a.hd : a.er);
+                    const int64_t t = tile * a.tile_n + 4 * qq;
+                    const int64_t left = (tile < a.n_tiles) ? a.m - t : 0;
+                    const uint32_t bytes = left >= 4 ? 16u : (left > 0 ? (uint32_t)left * 4u : 0u);
+                    cp_async_16_stream(smem_u32(dstb + r * kIdxArr + 4 * qq), bytes ? arr + t : arr, bytes);
+                }
+                cp_async_commit();
+                return;
+            }
+            for (int e = tid; e < 3 * a.tile_n; e += kProducerThreads) {
+                const int r = e >= 2 * a.tile_n ? 2 : (e >= a.tile_n ? 1 : 0);
                 if (!a.need_arr[r]) continue;
+                const int row = e - r * a.tile_n;
                 const int32_t* arr = r == 0 ? a.hs : (r == 1 ? a.hd : a.er);
-                const int64_t t = tile * a.tile_n + 4 * qq;
-                const int64_t left = (tile < a.n_tiles) ? a.m - t : 0;
-                const uint32_t bytes = left >= 4 ? 16u : (left > 0 ? (uint32_t)left * 4u : 0u);
-                cp_async_16_stream(smem_u32(dstb + r * a.tile_n + 4 * qq), bytes ? arr + t : arr, bytes);
+                const int64_t t = tile * a.tile_n + row;
+                const bool valid = tile < a.n_tiles && t < a.m;
+                cp_async_4(smem_u32(dstb + r * kIdxArr + (row % kRowGroups) * kIdxPitch + row / kRowGroups),
+                           valid ? arr + t : arr, valid ? 4u : 0u);
             }
             cp_async_commit();
         };
@@ -147,7 +169,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int64_t t0 = tile * a.tile_n;
-            const int32_t* islot = idx_smem + (lt % kIdxSlots) * 3 * a.tile_n;
+            const int32_t* islot = idx_smem + (lt % kIdxSlots) * 3 * kIdxArr;
             // indices two tiles ahead (that slot was last read two tiles ago, before a barrier)
             issue_idx(tile + 2 * (int64_t)gridDim.x, (lt + 2) % kIdxSlots);
             // this thread's row indices, reloaded only when the K block reads another Concat part
@@ -159,19 +181,26 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 const uint32_t ph = (uint32_t)((it / a.stages) & 1);
                 if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.status, abort_flag)) { ok = false; break; }
                 const int src = a.kb_src[kb];
-                const int32_t* rows_idx = islot + src * a.tile_n;
+                const int32_t* rows_idx = islot + src * kIdxArr;
                 const void* tbl = src == 2 ? a.r : a.z;
                 const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
                 const int row_elems = src == 2 ? a.d_r : a.d;
                 const uint32_t sbase = smem_u32(st_smem + (size_t)s * stage_bytes);
                 const int col = a.kb_col[kb] + chunk * 8;
                 const bool in_part = col < a.kb_width[kb];
-                if (src != ridx_src) {
+                if (src != ridx_src && !IDX_T) {
 #pragma unroll
                     for (int k = 0; k < kMaxRows; ++k) {
                         const int row = rg + k * kRowGroups;
                         ridx[k] = row < a.tile_n ? rows_idx[row] : 0;
                     }
+                    ridx_src = src;
+                } else if (src != ridx_src) {
+                    const int4* rp = reinterpret_cast<const int4*>(rows_idx + rg * kIdxPitch);
+                    const int4 i0 = rp[0], i1 = rp[1], i2 = rp[2];
+                    const int32_t all[12] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w, i2.x, i2.y, i2.z, i2.w};
+#pragma unroll
+                    for (int k = 0; k < kMaxRows; ++k) ridx[k] = all[k];  // rows past tile_n are never copied
                     ridx_src = src;
                 }
                 // destination of row `row`: 128-byte line, 16-byte chunk swizzled by the row (SW128)
@@ -549,7 +578,7 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     const uint32_t stage_bytes = (uint32_t)tile_n * 128u;
     const int bar_bytes = 256;
     // staged row indices (kIdxSlots x 3 x tile_n) + epilogue rows (kEpiWarps x tile_n / 2)
-    const int aux_bytes = 4 * (kIdxSlots * 3 * tile_n + kEpiWarps * tile_n / 2);
+    const int aux_bytes = 4 * (kIdxSlots * 3 * kIdxArr + kEpiWarps * tile_n / 2);
     int stages = (int)((kSmemLimit - 1024 - bar_bytes - aux_bytes - (int)w_bytes) / (int)stage_bytes);
     stages = std::min(stages, 8);
     if (stages < 2) {
@@ -598,7 +627,8 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     }
     static bool attr_set = false;
     if (!attr_set) {
-        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
     const bool want_mask = p.act == RELNN_ACT_RELU && (p.flags & RELNN_FLAG_RELU_MASK);
@@ -650,7 +680,15 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
             a.kb_width[k] = L.width[k];
         }
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
-        { ProfToken pt = prof_begin(RELNN_PROF_FWD_TC, st); fwd_tc_kernel<<<grid, kThreads, smem, st>>>(wmap, a); note_launch(); prof_end(pt, st); }
+        // every Concat part a single K block: indices staged transposed (see kIdxPitch)
+        const bool idx_t = p.d <= 64 && b.d_r <= 64;
+        {
+            ProfToken pt = prof_begin(RELNN_PROF_FWD_TC, st);
+            if (idx_t) fwd_tc_kernel<true><<<grid, kThreads, smem, st>>>(wmap, a);
+            else fwd_tc_kernel<false><<<grid, kThreads, smem, st>>>(wmap, a);
+            note_launch();
+            prof_end(pt, st);
+        }
         RELNN_CUDA(cudaGetLastError());
         launch_fixup(a.seg, a.m, unit, ceil_div(a.m, unit), a.carry, out, p.d_out, multi, p.kahan, st);
         RELNN_CUDA(cudaGetLastError());
