@@ -76,9 +76,23 @@ struct BwArgs {
 // 64-output block): dOut[seg_t] masked by the ReLU mask of tuple t, rounded to bf16 into the
 // 128B-swizzled dY blocks, and added to the thread's db partial. RB rows' loads are issued before
 // any is used; OB = blocks of 64 outputs.
+// The staged entries of rows row_base .. row_base + rpt - 1 (rpt = 2 or 4) with one shared load.
+__device__ __forceinline__ void load_rows(const int32_t* p, int rpt, int32_t (&o)[4]) {
+    if (rpt == 4) {
+        const int4 v = *reinterpret_cast<const int4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        const int2 v = *reinterpret_cast<const int2*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = 0; o[3] = 0;
+    }
+}
+
 template <int RB, int OB>
 __device__ __forceinline__ void build_dy(const BwArgs& a, const int32_t* islot, int N, int64_t t0, int row_base,
                                          int rpt, int chunk, uint32_t dyb, float (&dbacc)[2][8]) {
+    int32_t sgv[4], mrv[4];
+    load_rows(islot + 3 * N + row_base, rpt, sgv);
+    if (a.src_pass) load_rows(islot + N + row_base, rpt, mrv);
 #pragma unroll
     for (int j0 = 0; j0 < 4; j0 += RB) {
         if (j0 >= rpt) break;
@@ -89,8 +103,8 @@ __device__ __forceinline__ void build_dy(const BwArgs& a, const int32_t* islot, 
             const int row = row_base + j0 + jj;
             const bool in = j0 + jj < rpt;
             const bool tv = in && (t0 + row < a.m);
-            const int sg = tv ? islot[3 * N + row] : 0;
-            const int64_t mrow = a.src_pass ? (int64_t)(in ? islot[N + row] : 0) : t0 + row;
+            const int sg = tv ? sgv[j0 + jj] : 0;
+            const int64_t mrow = a.src_pass ? (int64_t)(in ? mrv[j0 + jj] : 0) : t0 + row;
 #pragma unroll
             for (int ob = 0; ob < OB; ++ob) {
                 const int o0 = ob * 64 + chunk * 8;
@@ -217,23 +231,31 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                     // outputs; up to 4 rows' loads in flight before any is used
                     if (a.dy_blocks == 1) build_dy<4, 1>(a, islot, N, t0, row_base, rpt, chunk, dyb, dbacc);
                     else build_dy<2, 2>(a, islot, N, t0, row_base, rpt, chunk, dyb, dbacc);
-                    // X rows, K-block by K-block (as in the forward); the src pass needs no dW
+                    // X rows, K-block by K-block (as in the forward); the src pass needs no dW. The
+                    // rows' indices are loaded once per Concat part.
+                    int32_t rix[4];
+                    int rix_src = -1;
                     for (int kb = 0; kb < a.x_blocks; ++kb) {
                         const int src = a.kb_src[kb];
                         const int col = a.kb_col[kb] + chunk * 8;
                         const bool in_part = col < a.kb_width[kb];
-                        const int32_t* rows_idx = islot + src * N;
+                        if (src != rix_src) {
+                            load_rows(islot + src * N + row_base, rpt, rix);
+                            rix_src = src;
+                        }
                         const void* tbl = src == 2 ? a.r : a.z;
                         const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
                         const int row_elems = src == 2 ? a.d_r : a.d;
                         const uint32_t kbase = xb + (uint32_t)kb * N * 128u;
                         if (tbl_bf16) {
                             const uint16_t* p = reinterpret_cast<const uint16_t*>(tbl);
-                            for (int j = 0; j < rpt; ++j) {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (j >= rpt) break;
                                 const int row = row_base + j;
                                 const uint32_t dst = kbase + (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
                                 const bool valid = (t0 + row < a.m) && in_part;
-                                const int64_t ridx = rows_idx[row];
+                                const int64_t ridx = rix[j];
                                 cp_async_16(dst, valid ? p + ridx * row_elems + col : p, valid ? 16u : 0u);
                             }
                         } else {
@@ -243,7 +265,7 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                             for (int j = 0; j < 4; ++j) {
                                 const int row = row_base + j;
                                 const bool valid = j < rpt && (t0 + row < a.m) && in_part;
-                                const int64_t ridx = valid ? rows_idx[row] : 0;
+                                const int64_t ridx = valid ? rix[j] : 0;
                                 const float4* q = reinterpret_cast<const float4*>(
                                     reinterpret_cast<const float*>(tbl) + ridx * row_elems + col);
                                 u[j] = valid ? __ldg(q) : make_float4(0.f, 0.f, 0.f, 0.f);
