@@ -43,6 +43,7 @@ struct BwArgs {
     const void* z;
     const void* r;
     const float* dout;
+    const uint16_t* dout_bf;  // bf16 copy of dout (src pass), or nullptr
     const uint32_t* mask;   // [m][mask_words] or nullptr (no ReLU)
     const int32_t* hs;
     const int32_t* hd;
@@ -133,6 +134,53 @@ __device__ __forceinline__ void build_dy(const BwArgs& a, const int32_t* islot, 
                                      ((uint32_t)(chunk ^ (row & 7)) << 4);
                 st_shared_v4(dst, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
                              pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+            }
+        }
+    }
+}
+
+// The same dY rows from the bf16 copy of dOut (the rounding dY gets anyway; no db partial): one
+// 16-byte load per row and block, the ReLU mask applied to the packed pairs.
+template <int RB, int OB>
+__device__ __forceinline__ void build_dy_bf(const BwArgs& a, const int32_t* islot, int N, int64_t t0, int row_base,
+                                            int rpt, int chunk, uint32_t dyb) {
+    int32_t sgv[4], mrv[4];
+    load_rows(islot + 3 * N + row_base, rpt, sgv);
+    if (a.src_pass) load_rows(islot + N + row_base, rpt, mrv);
+#pragma unroll
+    for (int j0 = 0; j0 < 4; j0 += RB) {
+        if (j0 >= rpt) break;
+        uint4 u[RB][OB];
+        uint32_t bits[RB][OB];
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+            const int row = row_base + j0 + jj;
+            const bool in = j0 + jj < rpt;
+            const bool tv = in && (t0 + row < a.m);
+            const int sg = tv ? sgv[j0 + jj] : 0;
+            const int64_t mrow = a.src_pass ? (int64_t)(in ? mrv[j0 + jj] : 0) : t0 + row;
+#pragma unroll
+            for (int ob = 0; ob < OB; ++ob) {
+                const int o0 = ob * 64 + chunk * 8;
+                const bool ld = tv && o0 < a.d_out;
+                u[jj][ob] = ld ? __ldg(reinterpret_cast<const uint4*>(a.dout_bf + (int64_t)sg * a.d_out + o0))
+                               : make_uint4(0u, 0u, 0u, 0u);
+                bits[jj][ob] = (ld && a.mask) ? __ldg(a.mask + mrow * a.mask_words + (o0 >> 5)) >> (o0 & 31)
+                                              : 0xffffffffu;
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+            if (j0 + jj >= rpt) break;
+            const int row = row_base + j0 + jj;
+#pragma unroll
+            for (int ob = 0; ob < OB; ++ob) {
+                const uint32_t b = bits[jj][ob];
+                auto keep = [&](int k) { return ((b >> k) & 1u ? 0x0000ffffu : 0u) | ((b >> (k + 1)) & 1u ? 0xffff0000u : 0u); };
+                const uint32_t dst = dyb + (uint32_t)ob * N * 128u + (uint32_t)row * 128u +
+                                     ((uint32_t)(chunk ^ (row & 7)) << 4);
+                st_shared_v4(dst, u[jj][ob].x & keep(0), u[jj][ob].y & keep(2), u[jj][ob].z & keep(4),
+                             u[jj][ob].w & keep(6));
             }
         }
     }
@@ -229,8 +277,14 @@ bwd_tc_kernel(const __grid_constant__ CUtensorMap wtmap, const __grid_constant__
                     const uint32_t xb = smem_u32(stg + dy_bytes);
                     // dY rows: dOut[seg_t] masked by the stored ReLU mask, as bf16, in blocks of 64
                     // outputs; up to 4 rows' loads in flight before any is used
-                    if (a.dy_blocks == 1) build_dy<4, 1>(a, islot, N, t0, row_base, rpt, chunk, dyb, dbacc);
-                    else build_dy<2, 2>(a, islot, N, t0, row_base, rpt, chunk, dyb, dbacc);
+                    if (a.dout_bf) {
+                        if (a.dy_blocks == 1) build_dy_bf<4, 1>(a, islot, N, t0, row_base, rpt, chunk, dyb);
+                        else build_dy_bf<4, 2>(a, islot, N, t0, row_base, rpt, chunk, dyb);
+                    } else if (a.dy_blocks == 1) {
+                        build_dy<4, 1>(a, islot, N, t0, row_base, rpt, chunk, dyb, dbacc);
+                    } else {
+                        build_dy<2, 2>(a, islot, N, t0, row_base, rpt, chunk, dyb, dbacc);
+                    }
                     // X rows, K-block by K-block (as in the forward); the src pass needs no dW. The
                     // rows' indices are loaded once per Concat part.
                     int32_t rix[4];
@@ -657,6 +711,15 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         attr_set = true;
     }
     if (g.dz) RELNN_CUDA(cudaMemsetAsync(g.dz, 0, sizeof(float) * p.n_h * p.d, st));
+    // the src pass gathers dOut rows in H-row order: from a bf16 copy (half the bytes, the rounding
+    // dY gets anyway)
+    const uint16_t* dout_bf = nullptr;
+    if (g.dz && (reinterpret_cast<uintptr_t>(g.dout) & 15u) == 0 && p.n_out > 0) {
+        RELNN_TRY(p.doutbf.alloc(sizeof(uint16_t) * (size_t)p.n_out * p.d_out));
+        f32_to_bf16(g.dout, p.n_out * (int64_t)p.d_out, p.doutbf.as<uint16_t>(), st);
+        RELNN_CUDA(cudaGetLastError());
+        dout_bf = p.doutbf.as<uint16_t>();
+    }
     const int grid_max = num_sms();
     const size_t wt_d_elems = (size_t)dmap.mbk * 128 * 128, wt_s_elems = (size_t)smap.mbk * 128 * 128;
     for (size_t i = 0; i < p.br.size(); ++i) {
@@ -780,6 +843,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
             s2.seg = b.seg_src.as<int32_t>();
             s2.dr = nullptr;
             s2.db_part = nullptr;
+            s2.dout_bf = dout_bf;
             s2.dw_part = nullptr;
             s2.need_arr[0] = 1;
             s2.need_arr[1] = relu ? 1 : 0;

@@ -29,6 +29,9 @@ struct CallIO {
 // when it is bf16 already. Returns the CallIO to use.
 relnn_status with_bf16_z(Plan& p, const CallIO& io, CallIO& out, cudaStream_t st);
 
+// dst[i] = bf16(src[i]) (nearest even) for n elements; n % 4 == 0, both pointers 16- and 8-byte aligned.
+void f32_to_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st);
+
 relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 

@@ -535,6 +535,13 @@ static bool make_layout(const Plan& p, KbLayout& L) {
     return true;
 }
 
+void f32_to_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st) {
+    const int64_t n4 = n / 4;
+    if (n4 == 0) return;
+    const int blocks = (int)std::min<int64_t>(ceil_div(n4, 256), (int64_t)num_sms() * 16);
+    { z_to_bf16_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(src), n4, reinterpret_cast<uint2*>(dst)); note_launch(); }
+}
+
 relnn_status with_bf16_z(Plan& p, const CallIO& io, CallIO& out, cudaStream_t st) {
     out = io;
     // (an f32 table that is not 16-byte aligned keeps the kernels' convert-as-you-gather path)
