@@ -39,7 +39,7 @@ METRIC = "rule tuples/s"
 UNIT = "tuples/s"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fwd_tc_kernel launch on the
 # default 16M-tuple single-rule workload, from one ncu capture of the kernel as it is now
-# (824,533,248 read + 538,527,744 written); reported only for that workload.
+# (824,710,912 read + 538,213,632 written); reported only for that workload.
 NCU_TRAFFIC_PER_LAUNCH = 824_710_912 + 538_213_632
 
 
