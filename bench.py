@@ -94,8 +94,8 @@ class Clocks:
         self.f.flush()
         rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
         os.unlink(self.f.name)
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        parsed = []
         for r in rows:
             r = [x.strip() for x in r]
             try:
@@ -103,15 +103,21 @@ class Clocks:
                 f_sm, f_mx = float(r[2]), float(r[3])
             except (ValueError, IndexError):
                 continue
-            if not (t0 <= ts <= t1):
-                continue
-            sm.append(f_sm)
-            mx.append(f_mx)
-            for n, v in zip(names, r[6:10]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            parsed.append((ts, f_sm, f_mx, {n for n, v in zip(names, r[6:10]) if v.lower().startswith("active")}))
+        inside = [p for p in parsed if t0 <= p[0] <= t1]
+        out = {}
+        if not inside:
+            # a timed region shorter than the sampling period: the samples just before and after it
+            before = [p for p in parsed if t0 - 0.25 <= p[0] < t0][-1:]
+            after = [p for p in parsed if t1 < p[0] <= t1 + 0.25][:1]
+            inside = before + after
+            out["window"] = "nearest samples around the timed region"
+        sm = [p[1] for p in inside]
+        mx = [p[2] for p in inside]
+        reasons = set().union(*[p[3] for p in inside]) if inside else set()
+        out.update({"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                    "reasons": sorted(reasons), "samples": len(sm)})
+        return out
 
 
 def cores():
@@ -384,6 +390,7 @@ class C4:
         self.flags = R.FLAG_BF16 | R.FLAG_KAHAN
         p = R.RulePlan(self.t["h"], self.brs, 64, 96, flags=self.flags, d_r=64)
         self.matched, self.n_out = p.n_matched, p.n_out
+        self.n_h = int(rel.h_ids.size)
         self.plan0 = p
         self.out = torch.empty((self.n_out, 96), dtype=torch.float32, device=dev)
 
@@ -395,7 +402,14 @@ class C4:
 
     def roofline_kernel(self):
         from paper_2605_24207_b300 import relnn as R
-        return R.PROF_FWD_TC, "fwd_tc_kernel", 2.0 * 192 * 96 * self.matched
+        # HBM-bound (about 115 FLOP per byte): algorithmic bytes of the three launches = per tuple its
+        # r row (64 x f32) and its four 4-byte indices, each H row once (f32[64]) and each output row
+        # once (f32[96])
+        by = self.matched * (64 * 4 + 16) + self.n_h * 64 * 4 + self.n_out * 96 * 4
+        return R.PROF_FWD_TC, "fwd_tc_kernel", float(by)
+
+    def roofline_peak(self):
+        return "hbm", None, None
 
     def e2e_setup(self):
         import torch
@@ -796,7 +810,7 @@ def run_relnn(args):
     R.profile_enable(False)
     clocks = clk.stop(t_epoch0, t_epoch1)
     value, t_step = job_throughput(e0.elapsed_time(e1) / args.steps, wl.matched, dev)
-    kid, kname, flops = wl.roofline_kernel()  # algorithmic FLOP of the kernel's launches in one step
+    kid, kname, flops = wl.roofline_kernel()  # algorithmic FLOP (or bytes) of the kernel's launches in one step
     k_ms, k_n = R.profile_read(kid)
     plan_ms, plan_n = R.profile_read(R.PROF_PLAN)
     del keep
@@ -804,10 +818,12 @@ def run_relnn(args):
     pk, pk_src = peaks()
     k_avg = k_ms / max(k_n, 1)
     achieved = flops / (k_ms / args.steps * 1e-3) / 1e12
-    bound, peak, peak_src = "tensor", pk["bf16_tflops_sustained"], f"{pk_src} bf16 sustained"
+    bound, peak, peak_src, r_unit = "tensor", pk["bf16_tflops_sustained"], f"{pk_src} bf16 sustained", "TFLOP/s"
     if hasattr(wl, "roofline_peak"):
         bound, peak, peak_src = wl.roofline_peak()
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    if bound == "hbm":  # the work is algorithmic bytes
+        achieved, peak, peak_src, r_unit = achieved * 1e3, pk["hbm_gbs"], f"{pk_src} HBM copy bandwidth", "GB/s"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": r_unit, "frac": achieved / peak,
                 "traffic": NCU_TRAFFIC_PER_LAUNCH if (wl.name == "c2" and args.n_tuples is None
                                                      and args.n_keys is None) else None, "kernel": kname,
                 "kernel_ms": k_avg, "kernel_launches_per_step": k_n / args.steps, "peak_source": peak_src}
