@@ -520,7 +520,7 @@ class C1B:
 
     def roofline_kernel(self):
         from paper_2605_24207_b300 import relnn as R
-        return R.PROF_FWD_FP32, "fwd_fp32_kernel", 2.0 * 32 * 16 * self.matched
+        return R.PROF_FWD_FP32, "fwd_fp32_lane_kernel", 2.0 * 32 * 16 * self.matched
 
     def roofline_peak(self):
         # f32 FMA on CUDA cores: 148 SMs x 128 lanes x 2 FLOP x 2.032 GHz (no measured figure exists)
