@@ -206,13 +206,12 @@ __device__ __forceinline__ float bf16_to_f32(uint16_t h) {
 }
 
 // Writes one output element. Single-branch rules write every output row exactly once (streaming
-// store); unions add the later branches into rows the earlier ones wrote, so only that path reads
-// the old value (the read is volatile asm so that it is never hoisted onto the store-only path).
+// store); unions add every branch into the zeroed output with a reduction (no load on the path).
 __device__ __forceinline__ void emit_out(float* dst, float v, int accumulate) {
     if (accumulate) {
-        float old;
-        asm volatile("ld.global.f32 %0, [%1];" : "=f"(old) : "l"(dst) : "memory");
-        __stcg(dst, old + v);
+        // one add per element per launch and the launches are stream-ordered, so the sum over the
+        // branches is taken in branch order (a fire-and-forget reduction: no load on the path)
+        atomicAdd(dst, v);
     } else {
         __stcs(dst, v);
     }

@@ -36,7 +36,7 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
 relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 
 // Adds the carried partials of tile-split segments into `out` (see file comment).
-void launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,
-                  float* out, int d_out, bool accumulate, bool kahan, cudaStream_t st);
+relnn_status launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,
+                          float* out, int d_out, bool accumulate, bool kahan, DevBuf& jobs_buf, cudaStream_t st);
 
 }  // namespace relnn

@@ -306,9 +306,13 @@ __global__ void __launch_bounds__(256) fwd_fp32_lane_kernel(Fp32Args a) {
 // segment adds that segment's pieces in tile order and writes the output row. The five seg values
 // the decision needs are fetched by five lanes at once; the last tile whose first row lies in the
 // segment is the next tile unless the segment reaches past it (then one lane binary-searches).
+// A segment cut into more than kLongPieces pieces is not summed by its first boundary's warp:
+// that warp records it (first boundary, last tile, first slot, output row) for long_fixup_kernel.
+constexpr int kLongPieces = 64;
+
 __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int tile, int64_t n_tiles,
                              const float* __restrict__ carry, float* __restrict__ out, int d_out,
-                             int accumulate, int kahan, int vec4) {
+                             int accumulate, int kahan, int vec4, int* __restrict__ jobs, int max_jobs) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t b = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) + 1; b < n_tiles; b += nwarps) {
@@ -340,6 +344,16 @@ __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int til
                 last = lo;
             }
             e = __shfl_sync(0xffffffffu, last, 0) / tile;
+        }
+        if (vec4 && jobs && e - b + 2 > kLongPieces) {
+            if (lane == 0) {
+                const int k = atomicAdd(jobs, 1);
+                if (k < max_jobs) {
+                    int4* jb = reinterpret_cast<int4*>(jobs + 4) + k;
+                    *jb = make_int4((int)b, (int)e, first_slot, s);
+                }
+            }
+            continue;
         }
         const float* c0 = carry + ((b - 1) * 2 + first_slot) * (int64_t)d_out;
         float* dst = out + (int64_t)s * d_out;
@@ -386,6 +400,73 @@ __global__ void fixup_kernel(const int32_t* __restrict__ seg, int64_t m, int til
     }
 }
 
+// One block of 8 warps per recorded long segment: warp w adds the w-th eighth of the segment's
+// pieces in order (8 loads in flight), the 8 partials are then added in warp order (compensated
+// when kahan): a fixed order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) long_fixup_kernel(const int* __restrict__ jobs, int max_jobs,
+                                                         const float* __restrict__ carry, float* __restrict__ out,
+                                                         int d_out, int accumulate, int kahan) {
+    __shared__ float4 part[8][64];  // d_out <= 256
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int njobs = min(jobs[0], max_jobs);
+    for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+        const int4 J = reinterpret_cast<const int4*>(jobs + 4)[jb];
+        const int64_t b = J.x, e = J.y;
+        const int first_slot = J.z, s = J.w;
+        // piece 0 = the first tile's cut piece, piece i >= 1 = slot 0 of tile b + i - 1
+        const int64_t P = e - b + 2;
+        const int64_t p0 = P * warp / 8, p1 = P * (warp + 1) / 8;
+        auto piece = [&](int64_t i) -> const float* {
+            return i == 0 ? carry + ((b - 1) * 2 + first_slot) * (int64_t)d_out
+                          : carry + ((b + i - 1) * 2) * (int64_t)d_out;
+        };
+        for (int q = lane; q * 4 < d_out; q += 32) {
+            const int o = q * 4;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), comp = make_float4(0.f, 0.f, 0.f, 0.f);
+            auto add4 = [&](const float4& x) {
+                if (kahan) {
+                    kahan_add(acc.x, comp.x, x.x); kahan_add(acc.y, comp.y, x.y);
+                    kahan_add(acc.z, comp.z, x.z); kahan_add(acc.w, comp.w, x.w);
+                } else {
+                    acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
+                }
+            };
+            int64_t i = p0;
+            for (; i + 7 < p1; i += 8) {
+                float4 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) x[u] = *reinterpret_cast<const float4*>(piece(i + u) + o);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) add4(x[u]);
+            }
+            for (; i < p1; ++i) add4(*reinterpret_cast<const float4*>(piece(i) + o));
+            part[warp][q] = acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            float* dst = out + (int64_t)s * d_out;
+            for (int q = lane; q * 4 < d_out; q += 32) {
+                float4 acc = part[0][q], comp = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int w = 1; w < 8; ++w) {
+                    const float4 x = part[w][q];
+                    if (kahan) {
+                        kahan_add(acc.x, comp.x, x.x); kahan_add(acc.y, comp.y, x.y);
+                        kahan_add(acc.z, comp.z, x.z); kahan_add(acc.w, comp.w, x.w);
+                    } else {
+                        acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
+                    }
+                }
+                if (accumulate) {
+                    const float4 old = *reinterpret_cast<const float4*>(dst + q * 4);
+                    acc.x += old.x; acc.y += old.y; acc.z += old.z; acc.w += old.w;
+                }
+                __stcg(reinterpret_cast<float4*>(dst + q * 4), acc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Wt[k][o] = W[o][k] in f32.
 __global__ void transpose_w_kernel(const void* W, int w_bf16, int d_out, int d_in, float* Wt) {
     const int n = d_out * d_in;
@@ -398,17 +479,32 @@ __global__ void transpose_w_kernel(const void* W, int w_bf16, int d_out, int d_i
 
 }  // namespace
 
-void launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,
-                  float* out, int d_out, bool accumulate, bool kahan, cudaStream_t st) {
-    if (n_tiles <= 1) return;
+relnn_status launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,
+                          float* out, int d_out, bool accumulate, bool kahan, DevBuf& jobs_buf, cudaStream_t st) {
+    if (n_tiles <= 1) return RELNN_OK;
     // one warp per boundary, 8 warps per block
     const int blocks = (int)std::min<int64_t>(ceil_div(n_tiles - 1, 8), (int64_t)num_sms() * 8);
-    const bool vec4 = d_out % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0 &&
+    const bool vec4 = d_out % 4 == 0 && d_out <= 256 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0 &&
                       (reinterpret_cast<uintptr_t>(carry) & 15u) == 0;
+    // segments longer than kLongPieces pieces go to long_fixup_kernel (at most one per kLongPieces tiles)
+    const bool split = vec4 && n_tiles > kLongPieces;
+    const int max_jobs = split ? (int)(n_tiles / kLongPieces + 1) : 0;
+    int* jobs = nullptr;
+    if (split) {
+        RELNN_TRY(jobs_buf.alloc(sizeof(int) * (4 + 4 * (size_t)max_jobs)));
+        jobs = jobs_buf.as<int>();
+        RELNN_CUDA(cudaMemsetAsync(jobs, 0, sizeof(int), st));
+    }
     ProfToken pt = prof_begin(RELNN_PROF_FIXUP, st);
     { fixup_kernel<<<blocks, 256, 0, st>>>(seg, m, tile, n_tiles, carry, out, d_out, accumulate ? 1 : 0,
-                                         kahan ? 1 : 0, vec4 ? 1 : 0); note_launch(); }
+                                         kahan ? 1 : 0, vec4 ? 1 : 0, jobs, max_jobs); note_launch(); }
+    if (split) {
+        { long_fixup_kernel<<<num_sms(), 256, 0, st>>>(jobs, max_jobs, carry, out, d_out, accumulate ? 1 : 0,
+                                                      kahan ? 1 : 0); note_launch(); }
+    }
     prof_end(pt, st);
+    RELNN_CUDA(cudaGetLastError());
+    return RELNN_OK;
 }
 
 relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
@@ -493,7 +589,7 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
             { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); fwd_fp32_kernel<<<grid, threads, smem, st>>>(a); note_launch(); prof_end(pt, st); }
         }
         RELNN_CUDA(cudaGetLastError());
-        launch_fixup(a.seg, a.m, (int)fix_tile, fix_n, a.carry, out, p.d_out, multi, p.kahan, st);
+        RELNN_TRY(launch_fixup(a.seg, a.m, (int)fix_tile, fix_n, a.carry, out, p.d_out, multi, p.kahan, p.fixjobs, st));
         RELNN_CUDA(cudaGetLastError());
     }
     return RELNN_OK;
