@@ -73,7 +73,6 @@ struct TcArgs {
     int kb_col[kMaxKb];   // first element of the block within its part
     int kb_width[kMaxKb]; // width of that part
     int need_arr[3];      // which of hs, hd, er the K blocks read
-    int r_seq;            // r rows are already in tuple order (row of tuple t = t): no er lookup
 };
 
 template <bool IDX_T>
@@ -189,11 +188,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 const uint32_t sbase = smem_u32(st_smem + (size_t)s * stage_bytes);
                 const int col = a.kb_col[kb] + chunk * 8;
                 const bool in_part = col < a.kb_width[kb];
-                if (src != ridx_src && src == 2 && a.r_seq) {
-#pragma unroll
-                    for (int k = 0; k < kMaxRows; ++k) ridx[k] = (int32_t)(t0 + rg + k * kRowGroups);
-                    ridx_src = src;
-                } else if (src != ridx_src && !IDX_T) {
+                if (src != ridx_src && !IDX_T) {
 #pragma unroll
                     for (int k = 0; k < kMaxRows; ++k) {
                         const int row = rg + k * kRowGroups;
@@ -461,20 +456,6 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
     }
 }
 
-// rs[t][c] = bf16(r[er[t]][c]) (nearest even): the per-tuple rows in tuple order, 4 elements per
-// thread and step (d_r % 4 == 0).
-__global__ void gather_r_bf16_kernel(const float* __restrict__ r, const int32_t* __restrict__ er, int64_t m, int d_r,
-                                     uint2* __restrict__ rs) {
-    const int q = d_r / 4;
-    const int64_t n = m * q;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / q;
-        const int c = (int)(i - t * q) * 4;
-        const float4 v = __ldg(reinterpret_cast<const float4*>(r + (int64_t)er[t] * d_r + c));
-        rs[i] = make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
-    }
-}
-
 // out[i] = bf16(z[i]) (round to nearest even), 4 elements per thread and step.
 __global__ void z_to_bf16_kernel(const float4* __restrict__ z, int64_t n4, uint2* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
@@ -669,18 +650,6 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         a.z = io.z;
         a.r = io.br[i].r;
         a.r_bf16 = io.r_bf16;
-        // f32 per-tuple rows: gathered into tuple order as bf16 once, then streamed by cp.async
-        if (b.d_r > 0 && !io.r_bf16 && (reinterpret_cast<uintptr_t>(io.br[i].r) & 15u) == 0) {
-            RELNN_TRY(p.rbf.alloc(sizeof(uint16_t) * (size_t)b.m * b.d_r));
-            const int64_t n4 = b.m * (int64_t)(b.d_r / 4);
-            const int blocks = (int)std::min<int64_t>(ceil_div(n4, 256), (int64_t)num_sms() * 16);
-            { gather_r_bf16_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float*>(io.br[i].r), b.er.as<int32_t>(),
-                                                           b.m, b.d_r, p.rbf.as<uint2>()); note_launch(); }
-            RELNN_CUDA(cudaGetLastError());
-            a.r = p.rbf.p;
-            a.r_bf16 = 1;
-            a.r_seq = 1;
-        }
         a.hs = b.hs.as<int32_t>();
         a.hd = b.hd.as<int32_t>();
         a.er = b.er.as<int32_t>();
@@ -712,7 +681,7 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         a.tmem_cols = (uint32_t)(2 * m_blocks * tile_n) <= 256 ? 256u : 512u;
         a.need_arr[0] = a.need_arr[1] = a.need_arr[2] = 0;
         for (int k = 0; k < L.n_kb; ++k) {
-            a.need_arr[L.src[k]] = (L.src[k] == 2 && a.r_seq) ? 0 : 1;
+            a.need_arr[L.src[k]] = 1;
             a.kb_src[k] = L.src[k];
             a.kb_col[k] = L.col[k];
             a.kb_width[k] = L.width[k];

@@ -48,7 +48,6 @@ struct Plan {
     DevBuf scratch;   // misc per-call scratch
     DevBuf zbf;       // bf16 copy of an f32 H embedding for the tensor-core kernels
     DevBuf doutbf;    // bf16 copy of the output gradient for the backward's src pass
-    DevBuf rbf;       // bf16 per-tuple rows of a branch in tuple order (f32 r, tensor-core forward)
     DevBuf fixjobs;   // long segments handed from the fix-up to its block-per-segment pass
     int64_t total_matched() const {
         int64_t s = 0;
@@ -59,7 +58,7 @@ struct Plan {
     // a synchronising cudaFree), for plans whose work all ran on s.
     void retire_on(cudaStream_t s) {
         DevBuf* bufs[] = {&H.rows_sorted, &H.run_start, &H.uid_of_pos, &H.ukeys, &H.slot_keys, &H.slot_vals,
-                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &rbf, &fixjobs};
+                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs};
         for (DevBuf* b : bufs) {
             b->ordered = true;
             b->st = s;
