@@ -61,6 +61,13 @@ typedef enum relnn_act_t { RELNN_ACT_NONE = 0, RELNN_ACT_RELU = 1 } relnn_act_t;
 #define RELNN_FLAG_NO_CONCAT_DST 0x10u /* join H(dst) (it filters tuples) but leave z_dst out of Concat */
 #define RELNN_FLAG_RELU_MASK 0x20u    /* forward stores the per-tuple ReLU mask for a later backward   */
 #define RELNN_FLAG_TILE128 0x40u      /* BF16 forward: 128 matched tuples per tile instead of 256      */
+#define RELNN_FLAG_PUSHDOWN 0x80u     /* forward with the Linear pushed below the join (paper Sec. 6):
+                                         P = Z W_src^T, Q = Z W_dst^T + b once per H row on tensor
+                                         cores (bf16 operands, f32 accumulate), then Out[k] = SUM
+                                         over the tuples of k of act(P[src] + Q[dst]) in f32. No
+                                         per-tuple embedding; d_out a multiple of 32, at most 128.
+                                         The backward is the per-tuple one (RELNN_FLAG_RELU_MASK is
+                                         honoured).                                                */
 
 /* Device status codes (relnn_last_device_error) */
 #define RELNN_DEV_OK 0

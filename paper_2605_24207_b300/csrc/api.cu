@@ -170,7 +170,8 @@ relnn_status relnn_rule_forward(relnn_plan_t p, const relnn_rule_params* prm, vo
     CallIO io;
     RELNN_TRY(resolve_io(P, prm, io));
     if (P.n_out > 0) {
-        if (P.bf16) RELNN_TRY(forward_tc(P, io, d_out_z, st));
+        if (P.flags & RELNN_FLAG_PUSHDOWN) RELNN_TRY(forward_pushdown(P, io, d_out_z, st));
+        else if (P.bf16) RELNN_TRY(forward_tc(P, io, d_out_z, st));
         else RELNN_TRY(forward_fp32(P, io, d_out_z, st));
     }
     RELNN_TRY(copy_out_keys(P, d_out_keys, st));

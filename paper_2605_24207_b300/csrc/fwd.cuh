@@ -34,6 +34,8 @@ void f32_to_bf16(const float* src, int64_t n, uint16_t* dst, cudaStream_t st);
 
 relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st);
+// RELNN_FLAG_PUSHDOWN: the Linear once per H row, then per-tuple gathers and the SUM walk.
+relnn_status forward_pushdown(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 
 // Adds the carried partials of tile-split segments into `out` (see file comment).
 relnn_status launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,

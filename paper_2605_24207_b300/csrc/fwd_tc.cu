@@ -75,7 +75,7 @@ struct TcArgs {
     int need_arr[3];      // which of hs, hd, er the K blocks read
 };
 
-template <bool IDX_T>
+template <bool IDX_T, bool DENSE>
 __global__ void __launch_bounds__(kThreads, 1)
 fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ TcArgs a) {
     extern __shared__ uint8_t dyn_smem[];
@@ -383,6 +383,15 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
                     tmem_ld_wait();
+                    if (DENSE) {
+                        // every tuple is its own output row (row t of a dense product): one
+                        // coalesced 128-byte store per tuple, no SUM walk
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (c * 32 + j < nt && o_ok)
+                                __stcg(a.out + (t0 + c * 32 + j) * a.d_out + o, __uint_as_float(v[j]) + bo);
+                        continue;
+                    }
                     const int li = c * 32 + lane;  // this lane's row in the half-tile
                     const bool tvalid = li < nt;
                     // a piece ends at row j if the next row has another output row or j is the
@@ -634,8 +643,10 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     }
     static bool attr_set = false;
     if (!attr_set) {
-        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
     const bool want_mask = p.act == RELNN_ACT_RELU && (p.flags & RELNN_FLAG_RELU_MASK);
@@ -691,13 +702,20 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         const bool idx_t = p.d <= 64 && b.d_r <= 64;
         {
             ProfToken pt = prof_begin(RELNN_PROF_FWD_TC, st);
-            if (idx_t) fwd_tc_kernel<true><<<grid, kThreads, smem, st>>>(wmap, a);
-            else fwd_tc_kernel<false><<<grid, kThreads, smem, st>>>(wmap, a);
+            const bool dense = (p.flags & kPlanDense) != 0;
+            if (dense) {
+                if (idx_t) fwd_tc_kernel<true, true><<<grid, kThreads, smem, st>>>(wmap, a);
+                else fwd_tc_kernel<false, true><<<grid, kThreads, smem, st>>>(wmap, a);
+            } else {
+                if (idx_t) fwd_tc_kernel<true, false><<<grid, kThreads, smem, st>>>(wmap, a);
+                else fwd_tc_kernel<false, false><<<grid, kThreads, smem, st>>>(wmap, a);
+            }
             note_launch();
             prof_end(pt, st);
         }
         RELNN_CUDA(cudaGetLastError());
-        RELNN_TRY(launch_fixup(a.seg, a.m, unit, ceil_div(a.m, unit), a.carry, out, p.d_out, multi, p.kahan, p.fixjobs, st));
+        if (!(p.flags & kPlanDense))
+            RELNN_TRY(launch_fixup(a.seg, a.m, unit, ceil_div(a.m, unit), a.carry, out, p.d_out, multi, p.kahan, p.fixjobs, st));
         RELNN_CUDA(cudaGetLastError());
     }
     return RELNN_OK;

@@ -15,6 +15,7 @@
 //   seg_src[m]  int32  its output row
 #pragma once
 
+#include <memory>
 #include <vector>
 
 #include "join.cuh"
@@ -29,6 +30,10 @@ struct BranchPlan {
     DevBuf src_perm, hs_src, seg_src;
     DevBuf relu_mask;  // uint32 [m][ceil(d_out/32)] when RELNN_FLAG_RELU_MASK
 };
+
+// Internal plan flag (above the public RELNN_FLAG_* bits): every tuple is its own output row (the
+// identity plan of a dense per-row product), so the forward stores rows without a SUM walk.
+constexpr uint32_t kPlanDense = 1u << 30;
 
 struct Plan {
     int kt = RELNN_I32;
@@ -49,6 +54,10 @@ struct Plan {
     DevBuf zbf;       // bf16 copy of an f32 H embedding for the tensor-core kernels
     DevBuf doutbf;    // bf16 copy of the output gradient for the backward's src pass
     DevBuf fixjobs;   // long segments handed from the fix-up to its block-per-segment pass
+    // transformation push-down (RELNN_FLAG_PUSHDOWN): the identity plan of the per-H-row products,
+    // the products P = Z W_src^T and Q = Z W_dst^T + b, and one column block of W
+    std::unique_ptr<Plan> pd;
+    DevBuf pdP, pdQ, pdW;
     int64_t total_matched() const {
         int64_t s = 0;
         for (auto& b : br) s += b.m;
@@ -58,11 +67,12 @@ struct Plan {
     // a synchronising cudaFree), for plans whose work all ran on s.
     void retire_on(cudaStream_t s) {
         DevBuf* bufs[] = {&H.rows_sorted, &H.run_start, &H.uid_of_pos, &H.ukeys, &H.slot_keys, &H.slot_vals,
-                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs};
+                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &pdP, &pdQ, &pdW};
         for (DevBuf* b : bufs) {
             b->ordered = true;
             b->st = s;
         }
+        if (pd) pd->retire_on(s);
         for (auto& b : br) {
             DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.src_perm, &b.hs_src, &b.seg_src, &b.relu_mask};
             for (DevBuf* x : bb) {
