@@ -68,6 +68,9 @@ typedef enum relnn_act_t { RELNN_ACT_NONE = 0, RELNN_ACT_RELU = 1 } relnn_act_t;
                                          per-tuple embedding; d_out a multiple of 32, at most 128.
                                          The backward is the per-tuple one (RELNN_FLAG_RELU_MASK is
                                          honoured).                                                */
+#define RELNN_FLAG_MEAN 0x100u        /* aggregator MEAN instead of SUM (paper Sec. 2.2 alpha): each
+                                         output row is the SUM divided by its number of matched
+                                         tuples; single-branch rules only (EINVAL otherwise)       */
 
 /* Device status codes (relnn_last_device_error) */
 #define RELNN_DEV_OK 0

@@ -11,7 +11,7 @@ Definitions followed (paper sections):
   * embedded relation (r, eta): content tuples plus one embedding per tuple          -- Sec. 2.1
   * join: natural join on shared attributes; embedding = concatenation eta1 (+) eta2   -- Sec. 2.2
   * projected union with aggregator alpha: group by the projected key, alpha over the
-    multiset B_t of contributing tuples (alpha = SUM here)                            -- Sec. 2.2
+    multiset B_t of contributing tuples (alpha = SUM, or MEAN = SUM / |B_t|)           -- Sec. 2.2
   * transformation T_tau: tau applied to each tuple embedding independently            -- Sec. 2.2
   * join rule R(x; alpha(tau)) :- R1,...,Rk  ==  U_{alpha,x}(T_tau(R1 |><| ... |><| Rk)) -- Sec. 3.1
   * union rule / "|..." replicator: branch results added by the head's sum             -- Sec. 3.1, 3.7
@@ -130,29 +130,37 @@ def _tau(X, W, b, act):
 
 
 def rule_forward(h_ids, z, branches, act: str = "none", join_dst: bool = True,
-                 concat_dst: bool = True):
-    """Evaluate H'(dst; SUM(tau(Concat(...)))) :- E_i(src, dst[; r]), H(src; z_src), H(dst; z_dst)
+                 concat_dst: bool = True, agg: str = "sum"):
+    """Evaluate H'(dst; alpha(tau(Concat(...)))) :- E_i(src, dst[; r]), H(src; z_src), H(dst; z_dst)
     for every branch i and add the branch results (Sec. 3.1 join rule; union rule and the "|..."
-    replicator of Sec. 3.7 for several branches).
+    replicator of Sec. 3.7 for several branches). alpha = SUM, or MEAN: each branch's per-key sum
+    divided by that branch's number of contributing tuples of the key (Sec. 2.2).
 
     ``branches``: sequence of objects with fields src, dst, r (or None), W (or None = identity), b.
     Returns (out_keys sorted ascending, out_z float64 [n_out, d_out], join sizes per branch)."""
+    assert agg in ("sum", "mean")
     acc: dict = {}
     sizes = []
     for br in branches:
         e, hs, hd = join(br.src, br.dst, h_ids, join_dst)
         sizes.append(int(e.size))
         dst = np.asarray(br.dst)
+        bacc: dict = {}
+        bcnt: dict = {}
         for lo in range(0, e.size, CHUNK):
             sl = slice(lo, lo + CHUNK)
             X = concat_rows(z, br.r, e[sl], hs[sl], hd[sl], concat_dst)
             Y = _tau(X, br.W, br.b, act)
             uk, part = group_sum(dst[e[sl]], Y)
+            ck, cn = np.unique(dst[e[sl]], return_counts=True)
+            for k, c in zip(ck.tolist(), cn.tolist()):
+                bcnt[k] = bcnt.get(k, 0) + c
             for k, row in zip(uk.tolist(), part):
-                if k in acc:
-                    acc[k] = acc[k] + row
-                else:
-                    acc[k] = row
+                bacc[k] = bacc[k] + row if k in bacc else row
+        for k, row in bacc.items():
+            if agg == "mean":
+                row = row / bcnt[k]
+            acc[k] = acc[k] + row if k in acc else row
     keys = sorted(acc)
     d_out = _out_dim(z, branches, concat_dst)
     out = np.stack([acc[k] for k in keys]) if keys else np.zeros((0, d_out))
@@ -169,11 +177,12 @@ def _out_dim(z, branches, concat_dst):
 
 
 def rule_backward(h_ids, z, branches, dout_keys, dout, act: str = "none", join_dst: bool = True,
-                  concat_dst: bool = True):
+                  concat_dst: bool = True, agg: str = "sum"):
     """Chain rule through the rule of ``rule_forward`` in float64 (the fit of Sec. 2.3 optimises the
     weights and the per-tuple embeddings, Sec. 3.6).
 
-    SUM backward broadcasts dOut[dst] to every contributing tuple; ReLU masks by the recomputed
+    SUM backward broadcasts dOut[dst] to every contributing tuple (MEAN: dOut[dst] divided by the
+    branch's number of contributing tuples of dst); ReLU masks by the recomputed
     pre-activation; Linear gives dW = dY^T X, db = sum dY, dX = dY W; Concat backward splits dX and
     adds each slice to the embedding row it was gathered from.
 
@@ -191,11 +200,16 @@ def rule_backward(h_ids, z, branches, dout_keys, dout, act: str = "none", join_d
         dW = None if W is None else np.zeros_like(W)
         db = None if W is None else np.zeros(W.shape[0])
         dr = None if br.r is None else np.zeros(np.asarray(br.r).shape, np.float64)
+        if agg == "mean":
+            ck, cn = np.unique(dst[e], return_counts=True)
+            cnt = dict(zip(ck.tolist(), cn.tolist()))
         for lo in range(0, e.size, CHUNK):
             sl = slice(lo, lo + CHUNK)
             X = concat_rows(z, br.r, e[sl], hs[sl], hd[sl], concat_dst)
             rows = np.asarray([pos[k] for k in dst[e[sl]].tolist()], np.int64)
             G = dout[rows]
+            if agg == "mean":
+                G = G / np.asarray([cnt[k] for k in dst[e[sl]].tolist()], np.float64)[:, None]
             if act == "relu":
                 pre = _tau(X, W, br.b, "none")
                 G = G * (pre > 0.0)

@@ -4,6 +4,7 @@
 #include <string>
 
 #include "bwd.cuh"
+#include "mean.cuh"
 #include "primitives.cuh"
 
 namespace relnn {
@@ -169,10 +170,13 @@ relnn_status relnn_rule_forward(relnn_plan_t p, const relnn_rule_params* prm, vo
     cudaStream_t st = (cudaStream_t)stream;
     CallIO io;
     RELNN_TRY(resolve_io(P, prm, io));
+    const bool mean = (P.flags & RELNN_FLAG_MEAN) != 0;
+    if (mean) RELNN_TRY(ensure_inv_count(P, st));
     if (P.n_out > 0) {
         if (P.flags & RELNN_FLAG_PUSHDOWN) RELNN_TRY(forward_pushdown(P, io, d_out_z, st));
         else if (P.bf16) RELNN_TRY(forward_tc(P, io, d_out_z, st));
         else RELNN_TRY(forward_fp32(P, io, d_out_z, st));
+        if (mean) RELNN_TRY(scale_rows(d_out_z, P.inv_cnt.as<float>(), P.n_out, P.d_out, d_out_z, st));
     }
     RELNN_TRY(copy_out_keys(P, d_out_keys, st));
     if (d_out_count)
@@ -200,6 +204,12 @@ relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, c
         if (d_dr) g.dr[i] = d_dr[i];
     }
     RELNN_CHECK_ARG(P.n_out == 0 || d_dout, "backward: null output gradient");
+    if ((P.flags & RELNN_FLAG_MEAN) && P.n_out > 0) {  // MEAN: the SUM backward of dOut[k] / n_k
+        RELNN_TRY(ensure_inv_count(P, st));
+        RELNN_TRY(P.mean_dout.alloc(sizeof(float) * (size_t)P.n_out * P.d_out));
+        RELNN_TRY(scale_rows(d_dout, P.inv_cnt.as<float>(), P.n_out, P.d_out, P.mean_dout.as<float>(), st));
+        g.dout = P.mean_dout.as<float>();
+    }
     if (P.bf16) return backward_tc(P, io, g, st);
     return backward_fp32(P, io, g, st);
 }

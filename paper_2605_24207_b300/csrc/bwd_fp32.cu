@@ -3,7 +3,7 @@
 //                  from the regathered Concat), stored to scratch; dX = dY W scattered into dz / dr
 //                  with f32 atomics.
 //   bw_dw_kernel : dW = dY^T X as a split-K SIMT GEMM over tuple chunks (X regathered), plus the
-//                  db = sum_t dY[t] partials; bw_reduce_kernel adds the chunk partials in order.
+//                  db = sum_t dY[t] partials (2048-tuple chunks); bw_reduce_kernel adds the chunk partials in order, compensated.
 #include "bwd.cuh"
 
 #include <algorithm>
@@ -132,7 +132,7 @@ __global__ void bw_identity_kernel(BwArgs a) {
 
 // Split-K SIMT GEMM: block (ob, kb, chunk) computes a 32x32 tile of dW over one tuple chunk.
 constexpr int kDwTile = 32;
-constexpr int kDwChunk = 8192;
+constexpr int kDwChunk = 2048;  // short f32 chains per partial; partials added compensated
 
 __global__ void bw_dw_kernel(BwArgs a, float* part, float* dbpart) {
     __shared__ float Ys[16][kDwTile + 1];
@@ -174,8 +174,8 @@ __global__ void bw_dw_kernel(BwArgs a, float* part, float* dbpart) {
 
 __global__ void bw_reduce_kernel(const float* part, int nchunks, int64_t n, float* out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * n + i];
+        float s = 0.f, c = 0.f;
+        for (int k = 0; k < nchunks; ++k) kahan_add(s, c, part[(int64_t)k * n + i]);
         out[i] = s;
     }
 }

@@ -1,0 +1,13 @@
+// MEAN aggregator helpers (see mean.cu).
+#pragma once
+
+#include "plan.cuh"
+
+namespace relnn {
+
+// 1 / (matched tuples of each output row) of a single-branch plan, built once into p.inv_cnt.
+relnn_status ensure_inv_count(Plan& p, cudaStream_t st);
+// dst[k][:] = src[k][:] * inv[k] for n rows of width d (dst may equal src).
+relnn_status scale_rows(const float* src, const float* inv, int64_t n, int d, float* dst, cudaStream_t st);
+
+}  // namespace relnn

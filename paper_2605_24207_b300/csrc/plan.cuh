@@ -58,6 +58,8 @@ struct Plan {
     // the products P = Z W_src^T and Q = Z W_dst^T + b, and one column block of W
     std::unique_ptr<Plan> pd;
     DevBuf pdP, pdQ, pdW;
+    // MEAN aggregator (RELNN_FLAG_MEAN): 1 / matched tuples per output row, and the scaled dOut
+    DevBuf inv_cnt, mean_dout;
     int64_t total_matched() const {
         int64_t s = 0;
         for (auto& b : br) s += b.m;
@@ -67,7 +69,7 @@ struct Plan {
     // a synchronising cudaFree), for plans whose work all ran on s.
     void retire_on(cudaStream_t s) {
         DevBuf* bufs[] = {&H.rows_sorted, &H.run_start, &H.uid_of_pos, &H.ukeys, &H.slot_keys, &H.slot_vals,
-                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &pdP, &pdQ, &pdW};
+                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &pdP, &pdQ, &pdW, &inv_cnt, &mean_dout};
         for (DevBuf* b : bufs) {
             b->ordered = true;
             b->st = s;

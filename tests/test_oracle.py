@@ -388,3 +388,63 @@ def test_pins_detect_planted_mistakes(monkeypatch):
     e, _, _ = O.join(br.src, br.dst, h)
     assert e.size != len(g["triples"])
     monkeypatch.setattr(O, "key_index", orig_index)
+
+
+# ----------------------------------------------------------------------------- MEAN aggregator
+def brute_mean(h_ids, z, br, act="none"):
+    """Per-key average of the brute-force tuple outputs (explicit loops, one branch)."""
+    sums, cnts = {}, {}
+    for (e, a, c) in brute_join(br.src, br.dst, h_ids):
+        x = list(z[a]) + list(z[c])
+        y = [br.b[o] + sum(br.W[o][k] * x[k] for k in range(len(x))) for o in range(len(br.W))]
+        if act == "relu":
+            y = [v if v > 0 else 0.0 for v in y]
+        key = br.dst[e]
+        sums[key] = [p + q for p, q in zip(sums.get(key, [0.0] * len(y)), y)]
+        cnts[key] = cnts.get(key, 0) + 1
+    keys = sorted(sums)
+    return keys, np.array([[v / cnts[k] for v in sums[k]] for k in keys])
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("act", ["none", "relu"])
+def test_mean_matches_brute_force(seed, act):
+    h_ids, z, br = tiny(seed + 70)
+    keys, out, _ = O.rule_forward(h_ids, z, [br], act=act, agg="mean")
+    bk, bo = brute_mean(h_ids, z, br, act)
+    assert list(keys) == bk
+    np.testing.assert_allclose(out, bo, rtol=1e-12, atol=1e-12)
+
+
+def test_mean_times_count_is_sum():
+    h_ids, z, br = tiny(80, n_e=60)
+    keys, mean, _ = O.rule_forward(h_ids, z, [br], agg="mean")
+    keys_s, total, _ = O.rule_forward(h_ids, z, [br])
+    e, hs, hd = O.join(br.src, br.dst, h_ids)
+    cnt = {k: c for k, c in zip(*np.unique(np.asarray(br.dst)[e], return_counts=True))}
+    assert np.array_equal(keys, keys_s)
+    np.testing.assert_allclose(mean * np.array([cnt[k] for k in keys])[:, None], total, rtol=1e-12, atol=1e-12)
+
+
+def test_mean_backward_finite_differences():
+    h_ids, z, br = tiny(81, n_e=30, n_h=10, d=3, d_out=4)
+    keys, out, _ = O.rule_forward(h_ids, z, [br], agg="mean")
+    C = np.random.default_rng(5).standard_normal(out.shape)
+    dW, db, dz, _ = O.rule_backward(h_ids, z, [br], keys, C, agg="mean")
+    h = 1e-3
+
+    def loss():
+        k2, o2, _ = O.rule_forward(h_ids, z, [br], agg="mean")
+        return float(np.sum(o2 * C))
+
+    rng = np.random.default_rng(11)
+    for arr, grad in ((br.W, dW[0]), (br.b, db[0]), (z, dz)):
+        for _ in range(4):
+            i = tuple(rng.integers(0, s) for s in arr.shape)
+            old = arr[i]
+            arr[i] = old + h
+            lp = loss()
+            arr[i] = old - h
+            lm = loss()
+            arr[i] = old
+            assert (lp - lm) / (2 * h) == pytest.approx(grad[i], rel=1e-6, abs=1e-8)
