@@ -116,11 +116,28 @@ relnn_status relnn_join_destroy(relnn_join_t j);
 /* ---------------------------------------------------------------------------------------------
  * Rules (paper Sec. 3.1 join rule, union rule; Sec. 3.7 "|..." replicator).
  * ------------------------------------------------------------------------------------------- */
+/* Selection (paper Sec. 3.1 filter expressions, Sec. 4.2 sigma): an atomic predicate
+ * lhs op rhs over the tuple's content variables (its src and dst keys) and integer constants; a
+ * branch's predicates are conjunctive. A tuple that fails one is dropped before the join. */
+typedef enum relnn_term_t { RELNN_TERM_SRC = 0, RELNN_TERM_DST = 1, RELNN_TERM_CONST = 2 } relnn_term_t;
+typedef enum relnn_cmp_t {
+    RELNN_CMP_EQ = 0, RELNN_CMP_NE = 1, RELNN_CMP_LT = 2, RELNN_CMP_LE = 3, RELNN_CMP_GT = 4, RELNN_CMP_GE = 5
+} relnn_cmp_t;
+#define RELNN_MAX_FILTERS 4
+typedef struct relnn_filter {
+    int32_t lhs, op, rhs;  /* relnn_term_t, relnn_cmp_t, relnn_term_t                             */
+    int32_t reserved;      /* 0                                                                    */
+    int64_t lhs_const;     /* value of lhs when lhs == RELNN_TERM_CONST (compared as signed keys)  */
+    int64_t rhs_const;     /* value of rhs when rhs == RELNN_TERM_CONST                            */
+} relnn_filter;
+
 typedef struct relnn_branch_desc {
     const void* d_src;     /* [n_tuples] keys of E.src (device)                                   */
     const void* d_dst;     /* [n_tuples] keys of E.dst (device)                                   */
     int64_t n_tuples;      /* rows of this E relation (< 2^31)                                     */
     int32_t d_r;           /* width of the per-tuple embedding r (0 = none)                        */
+    int32_t n_filters;     /* 0..RELNN_MAX_FILTERS predicates in `filters`                         */
+    const relnn_filter* filters;  /* host array [n_filters] or NULL                               */
 } relnn_branch_desc;
 
 typedef struct relnn_rule_desc {

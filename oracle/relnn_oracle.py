@@ -13,6 +13,9 @@ Definitions followed (paper sections):
   * projected union with aggregator alpha: group by the projected key, alpha over the
     multiset B_t of contributing tuples (alpha = SUM, or MEAN = SUM / |B_t|)           -- Sec. 2.2
   * transformation T_tau: tau applied to each tuple embedding independently            -- Sec. 2.2
+  * selection: a conjunctive filter expression of atomic predicates e1 theta e2 over the
+    body's content variables (here a tuple's src and dst keys) and constants; a tuple
+    that fails it does not take part in the join                                       -- Sec. 3.1, 4.2
   * join rule R(x; alpha(tau)) :- R1,...,Rk  ==  U_{alpha,x}(T_tau(R1 |><| ... |><| Rk)) -- Sec. 3.1
   * union rule / "|..." replicator: branch results added by the head's sum             -- Sec. 3.1, 3.7
   * fit: parameters (weights and per-tuple embeddings) minimise a loss relation        -- Sec. 2.3, 3.2, 3.6
@@ -32,7 +35,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "key_index", "join", "join_pairs", "join_cardinality", "concat_rows", "group_sum",
+    "key_index", "join", "join_pairs", "join_cardinality", "concat_rows", "group_sum", "selected_rows",
+    "selected_join",
     "rule_forward", "rule_backward", "mse", "mse_grad", "stacked_forward", "stacked_backward",
 ]
 
@@ -129,6 +133,31 @@ def _tau(X, W, b, act):
     return Y
 
 
+_CMP = {"==": np.equal, "!=": np.not_equal, "<": np.less, "<=": np.less_equal, ">": np.greater,
+        ">=": np.greater_equal}
+
+
+def selected_rows(br):
+    """Boolean mask of the E rows that satisfy the branch's filter expression (all predicates;
+    ``br.filters`` is absent or a list of (lhs, op, rhs), lhs / rhs = "src", "dst" or an int)."""
+    src = np.asarray(br.src)
+    keep = np.ones(src.size, bool)
+    for lhs, op, rhs in getattr(br, "filters", None) or []:
+        def term(x):
+            if isinstance(x, str):
+                return np.asarray({"src": br.src, "dst": br.dst}[x]).astype(np.int64)
+            return np.int64(x)
+        keep &= _CMP[op](term(lhs), term(rhs))
+    return keep
+
+
+def selected_join(br, h_ids, join_dst):
+    """The join triples (e, hs, hd) of the branch's E rows that pass its selection."""
+    e, hs, hd = join(br.src, br.dst, h_ids, join_dst)
+    keep = selected_rows(br)[e]
+    return e[keep], hs[keep], hd[keep]
+
+
 def rule_forward(h_ids, z, branches, act: str = "none", join_dst: bool = True,
                  concat_dst: bool = True, agg: str = "sum"):
     """Evaluate H'(dst; alpha(tau(Concat(...)))) :- E_i(src, dst[; r]), H(src; z_src), H(dst; z_dst)
@@ -142,7 +171,7 @@ def rule_forward(h_ids, z, branches, act: str = "none", join_dst: bool = True,
     acc: dict = {}
     sizes = []
     for br in branches:
-        e, hs, hd = join(br.src, br.dst, h_ids, join_dst)
+        e, hs, hd = selected_join(br, h_ids, join_dst)
         sizes.append(int(e.size))
         dst = np.asarray(br.dst)
         bacc: dict = {}
@@ -194,7 +223,7 @@ def rule_backward(h_ids, z, branches, dout_keys, dout, act: str = "none", join_d
     dout = np.asarray(dout, np.float64)
     dWs, dbs, drs = [], [], []
     for br in branches:
-        e, hs, hd = join(br.src, br.dst, h_ids, join_dst)
+        e, hs, hd = selected_join(br, h_ids, join_dst)
         dst = np.asarray(br.dst)
         W = None if br.W is None else np.asarray(br.W, np.float64)
         dW = None if W is None else np.zeros_like(W)

@@ -14,14 +14,42 @@ inline int grid_for(int64_t n, int threads = 256) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 16));
 }
 
-// Pass 1 over E: distinct-key indices of src and dst, matches per tuple, per-warp totals.
+// Conjunctive selection over a tuple's src and dst keys (relnn_filter), passed by value.
+struct FilterSet {
+    int n = 0;
+    bool uses_dst = false;
+    relnn_filter f[RELNN_MAX_FILTERS];
+    __device__ __forceinline__ bool pass(int64_t s, int64_t d) const {
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < RELNN_MAX_FILTERS; ++i) {
+            if (i >= n) break;
+            const int64_t a = f[i].lhs == RELNN_TERM_SRC ? s : (f[i].lhs == RELNN_TERM_DST ? d : f[i].lhs_const);
+            const int64_t b = f[i].rhs == RELNN_TERM_SRC ? s : (f[i].rhs == RELNN_TERM_DST ? d : f[i].rhs_const);
+            switch (f[i].op) {
+                case RELNN_CMP_EQ: ok = ok && a == b; break;
+                case RELNN_CMP_NE: ok = ok && a != b; break;
+                case RELNN_CMP_LT: ok = ok && a < b; break;
+                case RELNN_CMP_LE: ok = ok && a <= b; break;
+                case RELNN_CMP_GT: ok = ok && a > b; break;
+                default: ok = ok && a >= b; break;
+            }
+        }
+        return ok;
+    }
+};
+
+// Pass 1 over E: distinct-key indices of src and dst, matches per tuple, per-warp totals. A tuple
+// that fails the selection counts as unmatched.
 __global__ void tri_count_kernel(JoinView j, const void* src, const void* dst, int64_t T, int kt,
-                                 bool join_dst, int32_t* us, int32_t* ud, int64_t* warp_tot) {
+                                 bool join_dst, FilterSet flt, int32_t* us, int32_t* ud, int64_t* warp_tot) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t m = 0;
     if (e < T) {
-        int32_t a = j.lookup(load_key(src, kt, e));
-        int32_t b = join_dst ? j.lookup(load_key(dst, kt, e)) : 0;
+        const int64_t ks = load_key(src, kt, e);
+        const int64_t kd = (join_dst || flt.uses_dst) ? load_key(dst, kt, e) : 0;
+        int32_t a = flt.pass(ks, kd) ? j.lookup(ks) : -1;
+        int32_t b = join_dst ? j.lookup(kd) : 0;
         us[e] = a;
         ud[e] = b;
         if (a >= 0 && b >= 0) {
@@ -100,7 +128,7 @@ constexpr unsigned long long kTileAgg = 1ull << 62, kTileInc = 2ull << 62, kTile
 
 template <class K, class V>
 __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
-    JoinView j, const void* src, const void* dst, int64_t T, int kt, bool join_dst, uint64_t omin,
+    JoinView j, const void* src, const void* dst, int64_t T, int kt, bool join_dst, FilterSet flt, uint64_t omin,
     unsigned* tile_ctr, unsigned long long* tile_state, unsigned long long* total, int* status, K* t_key, V* t_val) {
     __shared__ int tile_s;
     __shared__ int warp_tot[kEmitThreads / 32];
@@ -115,7 +143,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
     for (int i = 0; i < kEmitItems; ++i) {
         const int64_t e = e0 + i;
         ks[i] = e < T ? load_key(src, kt, e) : 0;
-        kd[i] = (e < T && join_dst) ? load_key(dst, kt, e) : 0;
+        kd[i] = (e < T && (join_dst || flt.uses_dst)) ? load_key(dst, kt, e) : 0;
     }
     int32_t a[kEmitItems], bb[kEmitItems];
     int cnt = 0;
@@ -135,7 +163,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
     }
 #pragma unroll
     for (int i = 0; i < kEmitItems; ++i) {
-        if (e0 + i >= T) a[i] = -1;
+        if (e0 + i >= T || (flt.n && !flt.pass(ks[i], kd[i]))) a[i] = -1;
         cnt += (a[i] >= 0 && bb[i] >= 0) ? 1 : 0;
     }
     // block-wide exclusive scan of the per-thread counts
@@ -292,6 +320,17 @@ struct Tmp {
     DevBuf& sorted_val() { return in_tmp ? val_tmp : val; }
 };
 
+// The branch's selection predicates as a kernel argument.
+FilterSet filters_of(const relnn_branch_desc& bd) {
+    FilterSet fs;
+    fs.n = bd.filters ? bd.n_filters : 0;
+    for (int i = 0; i < fs.n; ++i) {
+        fs.f[i] = bd.filters[i];
+        fs.uses_dst = fs.uses_dst || fs.f[i].lhs == RELNN_TERM_DST || fs.f[i].rhs == RELNN_TERM_DST;
+    }
+    return fs;
+}
+
 // Emits the matched tuples as (group key, payload) pairs into t.key / t.val and returns their count
 // in *M. Unique H keys: one pass (buffers sized for every E row); otherwise a counting pass first.
 template <class K, class V>
@@ -313,7 +352,7 @@ relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M
             RELNN_CUDA(cudaMemsetAsync(ctl.p, 0, ctl_bytes, st));
             unsigned long long* st_words = ctl.as<unsigned long long>();
             { emit_unique_kernel<K, V><<<(unsigned)n_tiles, kEmitThreads, 0, st>>>(
-                v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst, t.omin, reinterpret_cast<unsigned*>(st_words + n_tiles),
+                v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst, filters_of(bd), t.omin, reinterpret_cast<unsigned*>(st_words + n_tiles),
                 st_words, st_words + n_tiles + 1, p.status.as<int>(), t.key.as<K>(), t.val.as<V>()); note_launch(); }
             RELNN_CUDA(cudaGetLastError());
             unsigned long long Mu = 0;
@@ -330,7 +369,7 @@ relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M
         RELNN_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(int64_t) * (nwarps + 1), st));
         const int blocks = (int)ceil_div(std::max<int64_t>(T, 1), 256);
         if (T > 0)
-            { tri_count_kernel<<<blocks, 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst,
+            { tri_count_kernel<<<blocks, 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst, filters_of(bd),
                                                      us.as<int32_t>(), ud.as<int32_t>(), wt.as<int64_t>()); note_launch(); }
         RELNN_TRY(exclusive_scan<int64_t>(wt.as<int64_t>(), wt.as<int64_t>(), nwarps, wt.as<int64_t>() + nwarps, st));
         RELNN_CUDA(cudaMemcpyAsync(&M, wt.as<int64_t>() + nwarps, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -464,6 +503,14 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         RELNN_CHECK_ARG(b.n_tuples == 0 || (b.d_src && b.d_dst), "rule plan: null E column");
         RELNN_CHECK_ARG(b.d_r >= 0 && b.d_r <= 4096, "rule plan: bad d_r");
         RELNN_CHECK_ARG(b.d_r == d_r0, "rule plan: branches must share the Concat width");
+        RELNN_CHECK_ARG(b.n_filters >= 0 && b.n_filters <= RELNN_MAX_FILTERS && (b.n_filters == 0 || b.filters),
+                        "rule plan: bad filter list");
+        for (int k = 0; k < b.n_filters; ++k) {
+            const relnn_filter& f = b.filters[k];
+            RELNN_CHECK_ARG(f.lhs >= RELNN_TERM_SRC && f.lhs <= RELNN_TERM_CONST && f.rhs >= RELNN_TERM_SRC &&
+                                f.rhs <= RELNN_TERM_CONST && f.op >= RELNN_CMP_EQ && f.op <= RELNN_CMP_GE,
+                            "rule plan: bad filter");
+        }
     }
     p.d_in = p.d * (p.concat_dst ? 2 : 1) + d_r0;
     p.d_out = p.identity ? p.d_in : desc->d_out;

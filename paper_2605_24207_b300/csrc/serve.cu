@@ -127,7 +127,7 @@ relnn_status run_batch(relnn_server_s* S, std::vector<Query*>& batch, cudaStream
         }
     }
     RELNN_CUDA(cudaGetLastError());
-    relnn_branch_desc bd{sk.p, dk.p, T, 0};
+    relnn_branch_desc bd{sk.p, dk.p, T, 0, 0, nullptr};
     relnn_rule_desc desc{};
     desc.key_type = RELNN_I64;
     desc.d_h_ids = hk.p;

@@ -39,8 +39,35 @@ class RelnnError(RuntimeError):
         self.status = status
 
 
+class Filter(C.Structure):
+    _fields_ = [("lhs", C.c_int32), ("op", C.c_int32), ("rhs", C.c_int32), ("reserved", C.c_int32),
+                ("lhs_const", C.c_int64), ("rhs_const", C.c_int64)]
+
+
 class BranchDesc(C.Structure):
-    _fields_ = [("d_src", C.c_void_p), ("d_dst", C.c_void_p), ("n_tuples", C.c_int64), ("d_r", C.c_int32)]
+    _fields_ = [("d_src", C.c_void_p), ("d_dst", C.c_void_p), ("n_tuples", C.c_int64), ("d_r", C.c_int32),
+                ("n_filters", C.c_int32), ("filters", C.POINTER(Filter))]
+
+
+TERM_SRC, TERM_DST, TERM_CONST = 0, 1, 2
+_CMP = {"==": 0, "!=": 1, "<": 2, "<=": 3, ">": 4, ">=": 5}
+MAX_FILTERS = 4
+
+
+def _filters(preds):
+    """A relnn_filter array from (lhs, op, rhs) triples: lhs / rhs are "src", "dst" or an int."""
+    if not preds:
+        return None, 0
+    assert len(preds) <= MAX_FILTERS, "at most 4 predicates per branch"
+    arr = (Filter * len(preds))()
+    for i, (lhs, op, rhs) in enumerate(preds):
+        def term(x):
+            if isinstance(x, str):
+                return {"src": TERM_SRC, "dst": TERM_DST}[x], 0
+            return TERM_CONST, int(x)
+        (lt, lc), (rt, rc) = term(lhs), term(rhs)
+        arr[i] = Filter(lt, _CMP[op], rt, 0, lc, rc)
+    return arr, len(preds)
 
 
 class RuleDesc(C.Structure):
@@ -215,8 +242,10 @@ class RulePlan:
     H'(dst; SUM tau(Concat(z_src, z_dst[, r]))) :- E_i(src, dst[; r]), H(src; z_src), H(dst; z_dst)."""
 
     def __init__(self, h_ids: torch.Tensor, branches: Sequence, d: int, d_out: int, act: int = ACT_NONE,
-                 flags: int = 0, d_r: int = 0, stream=None):
-        """``branches``: sequence of (src, dst) device key tensors."""
+                 flags: int = 0, d_r: int = 0, stream=None, filters=None):
+        """``branches``: sequence of (src, dst) device key tensors. ``filters``: per branch, None or a
+        list of up to 4 conjunctive predicates (lhs, op, rhs) with lhs / rhs "src", "dst" or an integer
+        constant and op one of == != < <= > >= (the rule's selection on its content variables)."""
         self.kt = _key_type(h_ids)
         self.key_dtype = h_ids.dtype
         self.device = h_ids.device
@@ -224,9 +253,13 @@ class RulePlan:
         self.flags, self.act, self.d, self.d_r = flags, act, d, d_r
         self.n_tuples = [int(s.numel()) for s, _ in branches]
         arr = (BranchDesc * len(branches))()
+        self._filters = []
         for i, (s, t) in enumerate(branches):
             assert s.dtype == self.key_dtype and t.dtype == self.key_dtype
-            arr[i] = BranchDesc(_ptr(s), _ptr(t), s.numel(), d_r)
+            farr, nf = _filters(filters[i] if filters else None)
+            self._filters.append(farr)
+            arr[i] = BranchDesc(_ptr(s), _ptr(t), s.numel(), d_r, nf,
+                                C.cast(farr, C.POINTER(Filter)) if farr is not None else None)
         desc = RuleDesc(self.kt, _ptr(h_ids), h_ids.numel(), d, d_out, len(branches), arr, act, flags)
         self._h = C.c_void_p()
         _check(lib().relnn_rule_plan(C.byref(desc), _stream(stream), C.byref(self._h)))

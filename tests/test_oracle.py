@@ -448,3 +448,48 @@ def test_mean_backward_finite_differences():
             lm = loss()
             arr[i] = old
             assert (lp - lm) / (2 * h) == pytest.approx(grad[i], rel=1e-6, abs=1e-8)
+
+
+# ----------------------------------------------------------------------------- selection
+FILTER_SETS = [[("src", "<", "dst")], [("dst", "!=", 3), ("src", ">=", 2)], [(4, ">", "src")],
+               [("src", "==", "dst")]]
+
+
+@pytest.mark.parametrize("filters", FILTER_SETS)
+def test_selection_matches_brute_force(filters):
+    h_ids, z, br = tiny(90, n_e=50)
+    br.filters = filters
+    ops = {"==": lambda a, b: a == b, "!=": lambda a, b: a != b, "<": lambda a, b: a < b,
+           "<=": lambda a, b: a <= b, ">": lambda a, b: a > b, ">=": lambda a, b: a >= b}
+    keep = []
+    for e in range(len(br.src)):
+        ok = True
+        for lhs, op, rhs in filters:
+            val = lambda x: br.src[e] if x == "src" else (br.dst[e] if x == "dst" else x)
+            ok = ok and ops[op](val(lhs), val(rhs))
+        keep.append(ok)
+    keep = np.array(keep)
+    sub = Br(br.src[keep], br.dst[keep], br.W, br.b)
+    bk, bo = brute_rule(h_ids, z, [sub])
+    keys, out, _ = O.rule_forward(h_ids, z, [br])
+    assert list(keys) == bk
+    np.testing.assert_allclose(out, bo, rtol=1e-12, atol=1e-12)
+
+
+def test_selection_is_the_rule_over_the_kept_rows():
+    h_ids, z, br = tiny(91, n_e=60, d_r=2)
+    br.filters = [("src", "<=", "dst"), ("dst", ">", 1)]
+    keep = O.selected_rows(br)
+    sub = Br(br.src[keep], br.dst[keep], br.W, br.b, br.r[keep])
+    k1, o1, s1 = O.rule_forward(h_ids, z, [br])
+    k2, o2, s2 = O.rule_forward(h_ids, z, [sub])
+    assert np.array_equal(k1, k2) and s1 == s2
+    np.testing.assert_allclose(o1, o2, rtol=1e-12, atol=1e-12)
+    C = np.random.default_rng(7).standard_normal(o1.shape)
+    g1 = O.rule_backward(h_ids, z, [br], k1, C)
+    g2 = O.rule_backward(h_ids, z, [sub], k2, C)
+    np.testing.assert_allclose(g1[0][0], g2[0][0], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g1[2], g2[2], rtol=1e-12, atol=1e-12)
+    # dr keeps the full E shape: rows that fail the selection get no gradient
+    assert np.all(g1[3][0][~keep] == 0)
+    np.testing.assert_allclose(g1[3][0][keep], g2[3][0], rtol=1e-12, atol=1e-12)
