@@ -86,10 +86,9 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
     uint8_t* st_smem = base + w_bytes;
     // row indices of the tiles being gathered (kIdxSlots x {hs, hd, er} x tile_n)
     int32_t* idx_smem = reinterpret_cast<int32_t*>(st_smem + (size_t)a.stages * stage_bytes);
-    // output rows of the half-tile being reduced, one copy per epilogue warp
+    // each epilogue warp walks the columns of one half of a tile (or 1/rep of it)
     const int half_n = a.tile_n / 2;
-    int32_t* seg_smem = idx_smem + kIdxSlots * 3 * kIdxArr;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(seg_smem + kEpiWarps * half_n);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(idx_smem + kIdxSlots * 3 * kIdxArr);
     uint64_t* full = bars;
     uint64_t* empty = bars + a.stages;
     uint64_t* tfull = bars + 2 * a.stages;
@@ -327,7 +326,6 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
         const int unit = half_n / a.rep;             // columns per warp and tile
         const int ucol = hh * half_n + (q / n_fq) * unit;  // first column of this warp's unit
         const int n_unit_chunks = unit / 32;
-        int32_t* wseg = seg_smem + ew * half_n;
         const bool relu = a.act == RELNN_ACT_RELU;
         const bool mask = relu && a.relu_mask != nullptr;
         float bias_r[2];
@@ -354,13 +352,10 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int acc = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
-            __syncwarp();
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (c < n_unit_chunks) wseg[32 * c + lane] = pf[c];
+            // output rows of this warp's columns: chunk c, lane l -> row of column 32 c + l
+            const int cs0 = pf[0], cs1 = pf[1], cs2 = pf[2], cs3 = pf[3];
             const int prev_seg = pf_prev;
             const int after_seg = pf_after;
-            __syncwarp();
             prefetch(tile + gridDim.x);
             // warp-uniform outcome of the bounded wait, so no lane runs the .sync.aligned loads alone
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), use & 1u, a.status, abort_flag))) break;
@@ -396,8 +391,11 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                     const bool tvalid = li < nt;
                     // a piece ends at row j if the next row has another output row or j is the
                     // half-tile's last row; it starts at j if row j-1 ended one
-                    const int sg = wseg[li];
-                    const int nx = (li + 1 < unit) ? wseg[li + 1] : after_seg;
+                    const int sg = c == 0 ? cs0 : (c == 1 ? cs1 : (c == 2 ? cs2 : cs3));
+                    const int sgn = c == 0 ? cs1 : (c == 1 ? cs2 : cs3);  // next chunk's (lane 0 used)
+                    int nx = __shfl_down_sync(0xffffffffu, sg, 1);
+                    const int nx31 = __shfl_sync(0xffffffffu, sgn, 0);
+                    if (lane == 31) nx = (li + 1 < unit) ? nx31 : after_seg;
                     const unsigned endmask = __ballot_sync(0xffffffffu, tvalid && (sg != nx || li == nt - 1));
                     const unsigned startmask = (endmask << 1) | prev_end;
                     prev_end = endmask >> 31;
@@ -438,7 +436,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                             if (jj[g] < 0) break;
                             const int j = jj[g];
                             const float val = __uint_as_float(vv[g]);
-                            const int s = wseg[c * 32 + j];
+                            const int s = __shfl_sync(0xffffffffu, sg, j);
                             const bool last = (c * 32 + j == nt - 1);
                             const int sn = last ? ((nt == unit) ? after_seg : -1) : s + 1;
                             const bool split = (first && prev_seg == s) || (last && sn == s);
@@ -593,8 +591,8 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     const uint32_t w_bytes = (uint32_t)L.n_kb * m_blocks * 16384u;
     const uint32_t stage_bytes = (uint32_t)tile_n * 128u;
     const int bar_bytes = 256;
-    // staged row indices (kIdxSlots x 3 x tile_n) + epilogue rows (kEpiWarps x tile_n / 2)
-    const int aux_bytes = 4 * (kIdxSlots * 3 * kIdxArr + kEpiWarps * tile_n / 2);
+    // staged row indices (kIdxSlots x 3 arrays)
+    const int aux_bytes = 4 * (kIdxSlots * 3 * kIdxArr);
     int stages = (int)((kSmemLimit - 1024 - bar_bytes - aux_bytes - (int)w_bytes) / (int)stage_bytes);
     stages = std::min(stages, 8);
     if (stages < 2) {
