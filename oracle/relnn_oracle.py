@@ -11,7 +11,8 @@ Definitions followed (paper sections):
   * embedded relation (r, eta): content tuples plus one embedding per tuple          -- Sec. 2.1
   * join: natural join on shared attributes; embedding = concatenation eta1 (+) eta2   -- Sec. 2.2
   * projected union with aggregator alpha: group by the projected key, alpha over the
-    multiset B_t of contributing tuples (alpha = SUM, or MEAN = SUM / |B_t|)           -- Sec. 2.2
+    multiset B_t of contributing tuples (alpha = SUM, MEAN = SUM / |B_t|, or MAX per
+    feature; the union compiles to a scatter reduction chosen by alpha)              -- Sec. 2.2, 4.2
   * transformation T_tau: tau applied to each tuple embedding independently            -- Sec. 2.2
   * selection: a conjunctive filter expression of atomic predicates e1 theta e2 over the
     body's content variables (here a tuple's src and dst keys) and constants; a tuple
@@ -26,6 +27,8 @@ Readings where the paper is silent (each is listed with its reason in the design
   * output keys are exactly the keys with >= 1 contributing tuple, sorted ascending;
   * Concat order is (z_src, z_dst[, r_edge]); Linear is y = x W^T + b with W [d_out, d_in];
   * ReLU (when present) is applied per tuple, inside the SUM.
+  * MAX: the gradient of a row's maximum goes to one tuple, the first that attains it in the
+    order (dst H row, E row, src H row) within the row; ReLU' is taken at that tuple.
 
 Parity status: every function here is pinned by ``tests/test_oracle.py`` (nested-loop brute force,
 closed forms, invariants, finite differences, a hand-derived golden fixture).
@@ -35,7 +38,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "key_index", "join", "join_pairs", "join_cardinality", "concat_rows", "group_sum", "selected_rows",
+    "key_index", "join", "join_pairs", "join_cardinality", "concat_rows", "group_sum", "group_max",
+    "max_tie_order", "selected_rows",
     "selected_join",
     "rule_forward", "rule_backward", "mse", "mse_grad", "stacked_forward", "stacked_backward",
 ]
@@ -120,6 +124,33 @@ def group_sum(keys, values):
     return uk, out
 
 
+def max_tie_order(keys, e, hs, hd):
+    """Permutation listing the join triples by output key, and within a key by dst H row, then E
+    row, then src H row: the order in which MAX keeps the first tuple attaining a maximum."""
+    return np.lexsort((np.asarray(hs), np.asarray(e), np.asarray(hd), np.asarray(keys)))
+
+
+def group_max(keys, values, order):
+    """Projected union with alpha = MAX (Sec. 2.2), per column. ``order`` lists the rows of
+    ``values`` grouped by key (``max_tie_order``). Returns the sorted distinct keys, the per-key
+    column maxima, and for each (key, column) the row that attains the maximum first in ``order``."""
+    order = np.asarray(order, np.int64)
+    k_sorted = np.asarray(keys)[order]
+    uk, start = np.unique(k_sorted, return_index=True)
+    bounds = list(start) + [order.size]
+    n_col = values.shape[1]
+    out = np.zeros((uk.size, n_col), np.float64)
+    win = np.zeros((uk.size, n_col), np.int64)
+    cols = np.arange(n_col)
+    for g in range(uk.size):
+        rows = order[bounds[g]:bounds[g + 1]]
+        block = values[rows]
+        first = np.argmax(block, axis=0)  # the first occurrence of each column's maximum
+        out[g] = block[first, cols]
+        win[g] = rows[first]
+    return uk, out, win
+
+
 def _tau(X, W, b, act):
     """T_tau with tau = [ReLU o] Linear (Sec. 2.2 Transformation): y = x W^T + b per tuple."""
     if W is None:
@@ -167,7 +198,10 @@ def rule_forward(h_ids, z, branches, act: str = "none", join_dst: bool = True,
 
     ``branches``: sequence of objects with fields src, dst, r (or None), W (or None = identity), b.
     Returns (out_keys sorted ascending, out_z float64 [n_out, d_out], join sizes per branch)."""
-    assert agg in ("sum", "mean")
+    assert agg in ("sum", "mean", "max")
+    if agg == "max":
+        keys, out, _, sizes = _max_forward(h_ids, z, branches, act, join_dst, concat_dst)
+        return keys, out, sizes
     acc: dict = {}
     sizes = []
     for br in branches:
@@ -197,6 +231,24 @@ def rule_forward(h_ids, z, branches, act: str = "none", join_dst: bool = True,
     return np.asarray(keys, key_dtype), out, sizes
 
 
+def _max_forward(h_ids, z, branches, act, join_dst, concat_dst):
+    """alpha = MAX for a single-branch rule: per output key and feature, the maximum of tau over the
+    key's join tuples. Also returns the winners (row of the join triples per key and feature) and the
+    triples, for the backward."""
+    assert len(branches) == 1, "MAX: single-branch rules"
+    br = branches[0]
+    e, hs, hd = selected_join(br, h_ids, join_dst)
+    dst = np.asarray(br.dst)
+    X = concat_rows(z, br.r, e, hs, hd, concat_dst)
+    Y = _tau(X, br.W, br.b, act)
+    gk = dst[e]
+    uk, out, win = group_max(gk, Y, max_tie_order(gk, e, hs, hd))
+    if uk.size == 0:
+        out = np.zeros((0, _out_dim(z, branches, concat_dst)))
+    key_dtype = np.asarray(h_ids).dtype if join_dst else dst.dtype
+    return np.asarray(uk, key_dtype), out, (win, e, hs, hd, X), [int(e.size)]
+
+
 def _out_dim(z, branches, concat_dst):
     br = branches[0]
     if br.W is not None:
@@ -221,6 +273,8 @@ def rule_backward(h_ids, z, branches, dout_keys, dout, act: str = "none", join_d
     dz = np.zeros_like(z64)
     pos = {k: i for i, k in enumerate(np.asarray(dout_keys).tolist())}
     dout = np.asarray(dout, np.float64)
+    if agg == "max":
+        return _max_backward(h_ids, z64, branches[0], pos, dout, act, join_dst, concat_dst)
     dWs, dbs, drs = [], [], []
     for br in branches:
         e, hs, hd = selected_join(br, h_ids, join_dst)
@@ -259,6 +313,36 @@ def rule_backward(h_ids, z, branches, dout_keys, dout, act: str = "none", join_d
         dbs.append(db)
         drs.append(dr)
     return dWs, dbs, dz, drs
+
+
+def _max_backward(h_ids, z64, br, pos, dout, act, join_dst, concat_dst):
+    """MAX backward: dOut[k][o] goes to the winner of (k, o) alone (ReLU' taken there)."""
+    uk, _, (win, e, hs, hd, X), _ = _max_forward(h_ids, z64, [br], act, join_dst, concat_dst)
+    W = None if br.W is None else np.asarray(br.W, np.float64)
+    G = np.zeros((e.size, W.shape[0] if W is not None else X.shape[1]))
+    for g, k in enumerate(uk.tolist()):
+        G[win[g], np.arange(win.shape[1])] = dout[pos[k]]
+    if act == "relu":
+        G = G * (_tau(X, W, br.b, "none") > 0.0)
+    d = z64.shape[1]
+    dz = np.zeros_like(z64)
+    dW = db = None
+    if W is not None:
+        dW = G.T @ X
+        db = G.sum(axis=0)
+        dX = G @ W
+    else:
+        dX = G
+    np.add.at(dz, hs, dX[:, :d])
+    off = d
+    if concat_dst:
+        np.add.at(dz, hd, dX[:, d:2 * d])
+        off = 2 * d
+    dr = None
+    if br.r is not None:
+        dr = np.zeros(np.asarray(br.r).shape, np.float64)
+        np.add.at(dr, e, dX[:, off:])
+    return [dW], [db], dz, [dr]
 
 
 def mse(pred_keys, pred, target_keys, target):

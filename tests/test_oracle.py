@@ -493,3 +493,150 @@ def test_selection_is_the_rule_over_the_kept_rows():
     # dr keeps the full E shape: rows that fail the selection get no gradient
     assert np.all(g1[3][0][~keep] == 0)
     np.testing.assert_allclose(g1[3][0][keep], g2[3][0], rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- MAX aggregator
+def brute_max(h_ids, z, br, dout=None, act="none", join_dst=True, concat_dst=True):
+    """Per-key, per-feature maximum of the brute-force tuple outputs with explicit loops, the winner
+    being the first tuple attaining it when a key's tuples are listed by (dst H row, E row, src H
+    row); with ``dout`` (rows in key order) also the gradients (dW, db, dz) by explicit loops."""
+    per_key = {}
+    for (e, a, c) in brute_join(br.src, br.dst, h_ids, join_dst):
+        x = list(z[a]) + (list(z[c]) if concat_dst else [])
+        pre = [br.b[o] + sum(br.W[o][k] * x[k] for k in range(len(x))) for o in range(len(br.W))]
+        y = [v if (act != "relu" or v > 0) else 0.0 for v in pre]
+        per_key.setdefault(br.dst[e], []).append(((c, e, a), x, pre, y, a, c))
+    keys = sorted(per_key)
+    d_out, d_in, d = len(br.W), len(br.W[0]), z.shape[1]
+    out = np.zeros((len(keys), d_out))
+    dW, db, dz = np.zeros((d_out, d_in)), np.zeros(d_out), np.zeros_like(z)
+    for i, k in enumerate(keys):
+        tuples = sorted(per_key[k], key=lambda t: t[0])
+        for o in range(d_out):
+            best = None
+            for t in tuples:
+                if best is None or t[3][o] > best[3][o]:
+                    best = t
+            out[i, o] = best[3][o]
+            if dout is None or (act == "relu" and not best[2][o] > 0):
+                continue
+            g = dout[i][o]
+            _, x, _, _, a, c = best
+            db[o] += g
+            for kk in range(d_in):
+                dW[o][kk] += g * x[kk]
+                if kk < d:
+                    dz[a][kk] += g * br.W[o][kk]
+                elif concat_dst:
+                    dz[c][kk - d] += g * br.W[o][kk]
+    return keys, out, (dW, db, dz)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("act", ["none", "relu"])
+def test_max_matches_brute_force(seed, act):
+    h_ids, z, br = tiny(seed + 100, n_e=50)
+    keys, out, _ = O.rule_forward(h_ids, z, [br], act=act, agg="max")
+    C = np.random.default_rng(seed).standard_normal(out.shape)
+    bk, bo, (bW, bb, bz) = brute_max(h_ids, z, br, C, act)
+    assert list(keys) == bk
+    np.testing.assert_allclose(out, bo, rtol=1e-12, atol=1e-12)
+    dW, db, dz, _ = O.rule_backward(h_ids, z, [br], keys, C, act=act, agg="max")
+    np.testing.assert_allclose(dW[0], bW, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(db[0], bb, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(dz, bz, rtol=1e-12, atol=1e-12)
+
+
+def test_max_brute_force_with_ties():
+    """Quantised inputs make many tuples tie; the brute-force walk (first in the tie order wins)
+    and the oracle must still agree exactly, also without a dst join (readout form)."""
+    h_ids, z, br = tiny(110, n_e=80, n_h=14)
+    rng = np.random.default_rng(3)
+    z[:] = rng.integers(-2, 3, size=z.shape)
+    br.W = rng.integers(-1, 2, size=br.W.shape).astype(float)
+    br.b = np.zeros(br.W.shape[0])
+    for join_dst in (True, False):
+        b2 = Br(br.src, br.dst, br.W if join_dst else br.W[:, :z.shape[1]], br.b)
+        keys, out, _ = O.rule_forward(h_ids, z, [b2], act="relu", join_dst=join_dst, concat_dst=join_dst,
+                                      agg="max")
+        C = rng.integers(-3, 4, size=out.shape).astype(float)
+        bk, bo, (bW, bb, bz) = brute_max(h_ids, z, b2, C, "relu", join_dst, join_dst)
+        assert list(keys) == bk
+        assert np.array_equal(out, bo)
+        dW, db, dz, _ = O.rule_backward(h_ids, z, [b2], keys, C, act="relu", join_dst=join_dst,
+                                        concat_dst=join_dst, agg="max")
+        assert np.array_equal(dW[0], bW) and np.array_equal(db[0], bb) and np.array_equal(dz, bz)
+
+
+def test_max_tie_goes_to_the_first_tuple_by_hand():
+    """Hand-derived: d = 1, W = [[1, 0]], b = 0, so y = z[src row].
+    H rows: 0 key 9 (z 1), 1 key 9 (z 1), 2 key 1 (z 0), 3 key 2 (z 5), 4 key 1 (z 5).
+    E: e0 = (1, 9), e1 = (2, 9). Key 9's tuples (dst row, E row, src row): (0,0,2) y 0, (0,0,4) y 5,
+    (0,1,3) y 5, (1,0,2) y 0, (1,0,4) y 5, (1,1,3) y 5. Max 5; the first in that order is
+    (dst 0, e0, src 4), so with dOut = 2: dz[4] = 2 * W[0][0] = 2, dz[0] = 2 * W[0][1] = 0, every
+    other row 0; dW = 2 * x = [[10, 2]], db = [2]. An order that put the src row before the E row
+    would pick (0, 1, 3) and send the gradient to row 3; the last occurrence would pick (1, 1, 3)."""
+    h_ids = np.array([9, 9, 1, 2, 1])
+    z = np.array([[1.0], [1.0], [0.0], [5.0], [5.0]])
+    br = Br(np.array([1, 2]), np.array([9, 9]), np.array([[1.0, 0.0]]), np.array([0.0]))
+    keys, out, _ = O.rule_forward(h_ids, z, [br], agg="max")
+    assert keys.tolist() == [9] and out.tolist() == [[5.0]]
+    dW, db, dz, _ = O.rule_backward(h_ids, z, [br], keys, np.array([[2.0]]), agg="max")
+    assert dW[0].tolist() == [[10.0, 2.0]] and db[0].tolist() == [2.0]
+    assert dz[:, 0].tolist() == [0.0, 0.0, 0.0, 0.0, 2.0]
+
+
+def test_max_of_single_tuple_rows_is_sum():
+    """Keys that receive exactly one tuple: MAX = SUM, forward and backward."""
+    rng = np.random.default_rng(12)
+    h_ids = np.arange(30)
+    z = rng.standard_normal((30, 3))
+    br = Br(rng.integers(0, 30, size=25), rng.permutation(30)[:25], rng.standard_normal((4, 6)),
+            rng.standard_normal(4))
+    k1, o1, _ = O.rule_forward(h_ids, z, [br], act="relu", agg="max")
+    k2, o2, _ = O.rule_forward(h_ids, z, [br], act="relu")
+    assert np.array_equal(k1, k2)
+    np.testing.assert_allclose(o1, o2, rtol=1e-12, atol=1e-12)
+    C = rng.standard_normal(o1.shape)
+    g1 = O.rule_backward(h_ids, z, [br], k1, C, act="relu", agg="max")
+    g2 = O.rule_backward(h_ids, z, [br], k2, C, act="relu")
+    for a, b in ((g1[0][0], g2[0][0]), (g1[1][0], g2[1][0]), (g1[2], g2[2])):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_max_bounds_every_member_and_is_attained():
+    h_ids, z, br = tiny(120, n_e=60)
+    keys, out, _ = O.rule_forward(h_ids, z, [br], agg="max")
+    e, hs, hd = O.join(br.src, br.dst, h_ids)
+    Y = O.concat_rows(z, None, e, hs, hd) @ br.W.T + br.b
+    gk = np.asarray(br.dst)[e]
+    for i, k in enumerate(keys.tolist()):
+        Yk = Y[gk == k]
+        assert np.all(Yk <= out[i] + 0.0)
+        assert np.all(np.any(Yk == out[i], axis=0))
+
+
+@pytest.mark.parametrize("act", ["none", "relu"])
+def test_max_backward_finite_differences(act):
+    """MAX is piecewise linear: away from ties (continuous random inputs) central differences with a
+    small step reproduce the backward exactly up to rounding."""
+    h_ids, z, br = tiny(130, n_e=30, n_h=10, d=3, d_out=4)
+    keys, out, _ = O.rule_forward(h_ids, z, [br], act=act, agg="max")
+    C = np.random.default_rng(9).standard_normal(out.shape)
+    dW, db, dz, _ = O.rule_backward(h_ids, z, [br], keys, C, act=act, agg="max")
+    h = 1e-6
+
+    def loss():
+        return float(np.sum(O.rule_forward(h_ids, z, [br], act=act, agg="max")[1] * C))
+
+    rng = np.random.default_rng(13)
+    for arr, grad in ((br.W, dW[0]), (br.b, db[0]), (z, dz)):
+        for _ in range(5):
+            i = tuple(rng.integers(0, s) for s in arr.shape)
+            old = arr[i]
+            arr[i] = old + h
+            lp = loss()
+            arr[i] = old - h
+            lm = loss()
+            arr[i] = old
+            assert (lp - lm) / (2 * h) == pytest.approx(grad[i], rel=1e-6, abs=1e-7)
