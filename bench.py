@@ -214,11 +214,17 @@ class C2:
         ppd = R.RulePlan(t["h"], [(t["src"], t["dst"])], self.d, self.d_out, flags=self.flags | R.FLAG_PUSHDOWN)
         ms_pd = timer(lambda: ppd.forward(t["z"], [t["W"]], [t["b"]], out=self.out), max(3, steps))
         del ppd
+        pmx = R.RulePlan(t["h"], [(t["src"], t["dst"])], self.d, self.d_out, flags=self.flags | R.FLAG_MAX)
+        ms_mx = timer(lambda: pmx.forward(t["z"], [t["W"]], [t["b"]], out=self.out), max(3, steps))
+        del pmx
         return {"warm_forward_tuples_per_s": self.matched / (ms_f * 1e-3), "warm_forward_ms": ms_f,
                 "warm_fwd_bwd_tuples_per_s": self.matched / (ms_fb * 1e-3), "warm_fwd_bwd_ms": ms_fb,
                 "pushdown_warm_forward": {"tuples_per_s": self.matched / (ms_pd * 1e-3), "ms": ms_pd,
                                           "what": "RELNN_FLAG_PUSHDOWN: P = Z W_src^T, Q = Z W_dst^T + b per H row "
                                                   "(tensor cores), then per-tuple f32 row gathers + SUM"},
+                "max_warm_forward": {"tuples_per_s": self.matched / (ms_mx * 1e-3), "ms": ms_mx,
+                                     "what": "RELNN_FLAG_MAX: the same fused forward with a MAX group-by (per-feature "
+                                             "maximum and the position of its first tuple, kept for the backward)"},
                 "torch_fp32_unfused": {"tuples_per_s": self.matched / (ms_torch * 1e-3), "ms_per_step": ms_torch,
                                        "what": "sort+searchsorted join, index_select, cat, F.linear f32 (TF32 off), "
                                                "unique + index_add_; same step (join + forward)"}}

@@ -71,6 +71,14 @@ typedef enum relnn_act_t { RELNN_ACT_NONE = 0, RELNN_ACT_RELU = 1 } relnn_act_t;
 #define RELNN_FLAG_MEAN 0x100u        /* aggregator MEAN instead of SUM (paper Sec. 2.2 alpha): each
                                          output row is the SUM divided by its number of matched
                                          tuples; single-branch rules only (EINVAL otherwise)       */
+#define RELNN_FLAG_MAX 0x200u         /* aggregator MAX instead of SUM (paper Sec. 2.2 alpha; Sec. 4.2
+                                         scatter-max): per output row and feature, the maximum of
+                                         tau(...) over its matched tuples. Single-branch rules; not
+                                         with MEAN or PUSHDOWN (EINVAL). The forward records, per row
+                                         and feature, the first tuple reaching the maximum in the
+                                         plan's order (dst H row, then E row, then src H row); the
+                                         backward sends dOut there only (times ReLU' at it), so it
+                                         needs a forward of the same plan first.                   */
 
 /* Device status codes (relnn_last_device_error) */
 #define RELNN_DEV_OK 0
@@ -181,8 +189,8 @@ typedef struct relnn_rule_params {
 } relnn_rule_params;
 
 /* async. Forward of the rule: d_out_z [n_out, d_out] f32 receives, for each output key (sorted as
- * relnn_plan_out_keys), the SUM over every branch's matched tuples with that dst key of
- * tau(Concat(...)). d_out_keys (may be NULL) receives the keys; d_out_count (device int64, may be
+ * relnn_plan_out_keys), the SUM (MEAN, MAX with those flags) over every branch's matched tuples with
+ * that dst key of tau(Concat(...)). d_out_keys (may be NULL) receives the keys; d_out_count (device int64, may be
  * NULL) receives n_out. d_out_z is fully overwritten. Concat widths: the BF16 form needs d and d_r
  * to be multiples of 8 and d_in, d_out <= 256; the FP32 form needs d_in, d_out <= 256. */
 relnn_status relnn_rule_forward(relnn_plan_t p, const relnn_rule_params* prm, void* d_out_keys,
@@ -191,8 +199,9 @@ relnn_status relnn_rule_forward(relnn_plan_t p, const relnn_rule_params* prm, vo
 /* async. Backward of relnn_rule_forward for the output gradient d_dout [n_out, d_out] f32:
  * d_dW[i] [d_out, d_in] f32, d_db[i] [d_out] f32, d_dz [n_h, d] f32 and d_dr[i] [n_tuples_i, d_r]
  * f32 are OVERWRITTEN with the gradients (any of the host arrays or entries may be NULL to skip).
- * The gathered Concat rows are recomputed, not stored. With act = RELU the plan's forward must have
- * run with RELNN_FLAG_RELU_MASK (the mask is kept in the plan). */
+ * The gathered Concat rows are recomputed, not stored. With act = RELU the BF16 form's forward must
+ * have run with RELNN_FLAG_RELU_MASK (the mask is kept in the plan); with RELNN_FLAG_MAX the plan's
+ * last forward must have run (its argmax is kept in the plan), ENOTSUP otherwise. */
 relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, const float* d_dout,
                                  float* const* d_dW, float* const* d_db, float* d_dz,
                                  float* const* d_dr, void* stream);

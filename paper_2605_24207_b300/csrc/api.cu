@@ -4,6 +4,7 @@
 #include <string>
 
 #include "bwd.cuh"
+#include "maxagg.cuh"
 #include "mean.cuh"
 #include "primitives.cuh"
 
@@ -178,6 +179,7 @@ relnn_status relnn_rule_forward(relnn_plan_t p, const relnn_rule_params* prm, vo
         else RELNN_TRY(forward_fp32(P, io, d_out_z, st));
         if (mean) RELNN_TRY(scale_rows(d_out_z, P.inv_cnt.as<float>(), P.n_out, P.d_out, d_out_z, st));
     }
+    if (P.flags & RELNN_FLAG_MAX) P.max_ready = true;
     RELNN_TRY(copy_out_keys(P, d_out_keys, st));
     if (d_out_count)
         RELNN_CUDA(cudaMemcpyAsync(d_out_count, &P.n_out, sizeof(int64_t), cudaMemcpyHostToDevice, st));
@@ -210,6 +212,7 @@ relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, c
         RELNN_TRY(scale_rows(d_dout, P.inv_cnt.as<float>(), P.n_out, P.d_out, P.mean_dout.as<float>(), st));
         g.dout = P.mean_dout.as<float>();
     }
+    if (P.flags & RELNN_FLAG_MAX) RELNN_TRY(build_win_mask(P, st));  // MAX: dOut to the argmax only
     if (P.bf16) return backward_tc(P, io, g, st);
     return backward_fp32(P, io, g, st);
 }

@@ -62,8 +62,9 @@ __global__ void bw_dy_kernel(BwArgs a) {
             Yg[idx] = a.dout[(int64_t)a.seg[t0 + t] * a.d_out + o];
         }
         __syncthreads();
-        if (a.act == RELNN_ACT_RELU && a.mask) {
-            // the mask the forward used (keeps a BF16-form forward and this backward consistent)
+        if (a.mask) {
+            // the ReLU mask the forward used (keeps a BF16-form forward and this backward
+            // consistent), or the MAX aggregator's winner mask
             for (int idx = tid; idx < nt * a.d_out; idx += blockDim.x) {
                 const int t = idx / a.d_out, o = idx - t * a.d_out;
                 if (!((a.mask[(t0 + t) * a.mask_words + (o >> 5)] >> (o & 31)) & 1u)) Yg[idx] = 0.f;
@@ -222,12 +223,14 @@ relnn_status backward_fp32(Plan& p, const CallIO& io, const GradIO& g, cudaStrea
         a.d_out = p.d_out;
         a.concat_dst = p.concat_dst;
         a.act = p.act;
-        a.mask = b.relu_mask.p ? b.relu_mask.as<uint32_t>() : nullptr;
+        const bool maxagg = (p.flags & RELNN_FLAG_MAX) != 0;
+        a.mask = maxagg ? p.win_mask.as<uint32_t>()
+                        : ((p.act == RELNN_ACT_RELU && b.relu_mask.p) ? b.relu_mask.as<uint32_t>() : nullptr);
         a.mask_words = ((p.d_out + 127) / 128) * 4;
         // identity without ReLU: a straight gather of dOut rows into the gradients
         const bool aligned16 = ((reinterpret_cast<uintptr_t>(g.dout) | reinterpret_cast<uintptr_t>(g.dz) |
                                  reinterpret_cast<uintptr_t>(a.dr)) & 15u) == 0;
-        if (p.identity && p.act != RELNN_ACT_RELU && p.d % 4 == 0 && b.d_r % 4 == 0 && aligned16) {
+        if (p.identity && p.act != RELNN_ACT_RELU && !maxagg && p.d % 4 == 0 && b.d_r % 4 == 0 && aligned16) {
             const int blocks = (int)std::min<int64_t>(ceil_div(b.m * (p.d_in / 4), 256), (int64_t)num_sms() * 16);
             { ProfToken pt = prof_begin(RELNN_PROF_BWD_FP32, st); bw_identity_kernel<<<blocks, 256, 0, st>>>(a); note_launch(); prof_end(pt, st); }
             RELNN_CUDA(cudaGetLastError());

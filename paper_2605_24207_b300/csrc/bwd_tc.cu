@@ -733,7 +733,9 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
             if (dW) RELNN_CUDA(cudaMemsetAsync(dW, 0, sizeof(float) * p.d_out * p.d_in, st));
             continue;
         }
-        if (relu && !b.relu_mask.p) {
+        // MAX: the winner mask (argmax and ReLU' in one) replaces the ReLU mask
+        const bool maxagg = (p.flags & RELNN_FLAG_MAX) != 0;
+        if (relu && !maxagg && !b.relu_mask.p) {
             set_error("BF16 backward with ReLU needs the forward's mask (plan flag RELNN_FLAG_RELU_MASK)");
             return RELNN_EINVAL;
         }
@@ -782,7 +784,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         a.z = io.z;
         a.r = io.br[i].r;
         a.dout = g.dout;
-        a.mask = relu ? b.relu_mask.as<uint32_t>() : nullptr;
+        a.mask = maxagg ? p.win_mask.as<uint32_t>() : (relu ? b.relu_mask.as<uint32_t>() : nullptr);
         a.hs = b.hs.as<int32_t>();
         a.hd = b.hd.as<int32_t>();
         a.er = b.er.as<int32_t>();
@@ -846,7 +848,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
             s2.dout_bf = dout_bf;
             s2.dw_part = nullptr;
             s2.need_arr[0] = 1;
-            s2.need_arr[1] = relu ? 1 : 0;
+            s2.need_arr[1] = a.mask ? 1 : 0;  // each tuple's mask row (its position in output order)
             s2.need_arr[2] = 0;
             { ProfToken pt = prof_begin(RELNN_PROF_BWD_TC, st); bwd_tc_kernel<<<sgrid, kThreads, scfg.smem, st>>>(wtmap_s, s2); note_launch(); prof_end(pt, st); }
             RELNN_CUDA(cudaGetLastError());

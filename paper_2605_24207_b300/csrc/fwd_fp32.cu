@@ -3,6 +3,7 @@
 // output feature o and keeps y[t][o] for the tile's 32 tuples in registers, so the SUM over a run of
 // equal output rows is a sequential walk in registers (Sec. 2.2 projected union with SUM).
 #include "fwd.cuh"
+#include "maxagg.cuh"
 
 #include <algorithm>
 
@@ -25,8 +26,11 @@ struct Fp32Args {
     int range_tiles;
     int vec_in;          // widths multiples of 4 and rows aligned: 4-element loads
     int concat_dst, d_in, d_out, act, kahan, accumulate, w_in_smem;
+    int maxagg;          // MAX aggregator (fwd_fp32_kernel only)
     float* out;
     float* carry;
+    int32_t* arg;        // MAX: [n_out][d_out] plan position of each maximum (-1: ReLU'd zero)
+    int32_t* carry_pos;  // MAX: positions of the boundary partials
 };
 
 __device__ __forceinline__ float load_elem(const void* base, int bf16, int64_t idx) {
@@ -96,25 +100,42 @@ __global__ void __launch_bounds__(256) fwd_fp32_kernel(Fp32Args a) {
         const int prev_seg = t0 > 0 ? a.seg[t0 - 1] : -1;
         const int next_seg = t0 + nt < a.m ? a.seg[t0 + nt] : -1;
         float acc = 0.f, comp = 0.f;
+        int rpos = 0;       // MAX: position of the piece's running maximum (first occurrence)
+        bool fresh = true;  // the next tuple starts a piece
         bool first = true;
 #pragma unroll
         for (int t = 0; t < kTT; ++t) {
             if (t < nt) {
-                if (a.kahan) kahan_add(acc, comp, y[t]);
-                else acc += y[t];
+                if (a.maxagg) {
+                    if (fresh || y[t] > acc) {
+                        acc = y[t];
+                        rpos = (int)(t0 + t);
+                    }
+                } else if (a.kahan) {
+                    kahan_add(acc, comp, y[t]);
+                } else {
+                    acc += y[t];
+                }
+                fresh = false;
                 const int s = seg_s[t];
                 const bool last = (t == nt - 1);
                 const int sn = last ? next_seg : seg_s[t + 1 < kTT ? t + 1 : t];
                 if (sn != s || last) {
                     const bool split = (first && prev_seg == s) || (last && sn == s);
                     if (split) {
-                        a.carry[(tile * 2 + (first ? 0 : 1)) * a.d_out + o] = acc;
+                        const int64_t ci = (tile * 2 + (first ? 0 : 1)) * a.d_out + o;
+                        a.carry[ci] = acc;
+                        if (a.maxagg) a.carry_pos[ci] = rpos;
+                    } else if (a.maxagg) {
+                        a.out[(int64_t)s * a.d_out + o] = acc;
+                        a.arg[(int64_t)s * a.d_out + o] = (a.act == RELNN_ACT_RELU && !(acc > 0.f)) ? -1 : rpos;
                     } else {
                         float* dst = a.out + (int64_t)s * a.d_out + o;
                         emit_out(dst, acc, a.accumulate);
                     }
                     acc = 0.f;
                     comp = 0.f;
+                    fresh = true;
                     first = false;
                 }
             }
@@ -515,6 +536,12 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
     int64_t max_tiles = 1;
     for (auto& b : p.br) max_tiles = std::max<int64_t>(max_tiles, ceil_div(b.m, kTT));
     RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * max_tiles));
+    const bool maxagg = (p.flags & RELNN_FLAG_MAX) != 0;
+    if (maxagg) {
+        RELNN_CHECK_ARG(!multi, "MAX aggregator: single-branch rules only");
+        RELNN_TRY(p.carry_pos.alloc(sizeof(int32_t) * 2 * p.d_out * max_tiles));
+        RELNN_TRY(p.max_arg.alloc(sizeof(int32_t) * (size_t)p.n_out * p.d_out));
+    }
     const size_t wt_bytes = sizeof(float) * p.d_in * p.d_out;
     RELNN_TRY(p.scratch.alloc(wt_bytes));
     const bool w_in_smem = !p.identity && wt_bytes <= 160 * 1024;
@@ -557,6 +584,11 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
                        (b.d_r == 0 || (b.d_r % 4 == 0 && (ra & rmask) == 0));
         }
         a.carry = p.carry.as<float>();
+        if (maxagg) {
+            a.maxagg = 1;
+            a.arg = p.max_arg.as<int32_t>();
+            a.carry_pos = p.carry_pos.as<int32_t>();
+        }
         // narrow widths: the lane-per-tuple kernel (its in-tile sums are 5-level trees, whose error
         // bound is below that of a compensated 32-term walk; the fix-up compensates across tiles)
         // one wave of warps, each over an equal range of tiles
@@ -581,7 +613,8 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
             return true;
         };
         static int bps64x64[2], bps32x32[2], bps64x16[2];
-        const bool lane_done = p.identity ? lane_launch(fwd_fp32_lane_kernel<64, 64>, 64, 64, bps64x64)
+        // (MAX runs in the feature-per-thread kernel: a sequential walk keeps the first maximum)
+        const bool lane_done = maxagg ? false : p.identity ? lane_launch(fwd_fp32_lane_kernel<64, 64>, 64, 64, bps64x64)
                                           : (lane_launch(fwd_fp32_lane_kernel<32, 32>, 32, 32, bps32x32) ||
                                              lane_launch(fwd_fp32_lane_kernel<64, 16>, 64, 16, bps64x16));
         if (!lane_done) {
@@ -589,7 +622,11 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
             { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); fwd_fp32_kernel<<<grid, threads, smem, st>>>(a); note_launch(); prof_end(pt, st); }
         }
         RELNN_CUDA(cudaGetLastError());
-        RELNN_TRY(launch_fixup(a.seg, a.m, (int)fix_tile, fix_n, a.carry, out, p.d_out, multi, p.kahan, p.fixjobs, st));
+        if (maxagg)
+            RELNN_TRY(launch_fixup_max(a.seg, a.m, (int)fix_tile, fix_n, a.carry, a.carry_pos, out, a.arg, p.d_out,
+                                       p.act == RELNN_ACT_RELU, p.fixjobs, st));
+        else
+            RELNN_TRY(launch_fixup(a.seg, a.m, (int)fix_tile, fix_n, a.carry, out, p.d_out, multi, p.kahan, p.fixjobs, st));
         RELNN_CUDA(cudaGetLastError());
     }
     return RELNN_OK;

@@ -21,6 +21,7 @@
 // copies): every quarter then holds all features of the tile, and each of the rep warps sharing a
 // feature quarter walks 1/rep of the half-tile's columns (the unit shrinks to half_n / rep).
 #include "fwd.cuh"
+#include "maxagg.cuh"
 #include "segscan.cuh"
 #include "tc.cuh"
 
@@ -60,6 +61,8 @@ struct TcArgs {
     const float* bias;
     float* out;
     float* carry;
+    int32_t* arg;         // MAX: [n_out][d_out] plan position of each maximum (-1: ReLU'd zero)
+    int32_t* carry_pos;   // MAX: the positions of the boundary partials in `carry`
     int* status;
     uint32_t* relu_mask;
     int64_t m;
@@ -75,7 +78,10 @@ struct TcArgs {
     int need_arr[3];      // which of hs, hd, er the K blocks read
 };
 
-template <bool IDX_T, bool DENSE>
+// Aggregation of the epilogue: SUM walk, one row per tuple (dense product), or MAX with argmax.
+constexpr int kAggSum = 0, kAggDense = 1, kAggMax = 2;
+
+template <bool IDX_T, int AGG>
 __global__ void __launch_bounds__(kThreads, 1)
 fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ TcArgs a) {
     extern __shared__ uint8_t dyn_smem[];
@@ -370,6 +376,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 const bool o_ok = o < a.d_out;
                 const float bo = mb == 0 ? bias_r[0] : bias_r[1];
                 float sum = 0.f, comp = 0.f;
+                int rpos = 0;  // MAX: plan position of the running maximum
                 bool first = true;
                 unsigned prev_end = 1u;  // did the tuple before this chunk end a piece? (half start: yes)
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_stride +
@@ -378,7 +385,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(taddr + (uint32_t)c * 32, v);
                     tmem_ld_wait();
-                    if (DENSE) {
+                    if (AGG == kAggDense) {
                         // every tuple is its own output row (row t of a dense product): one
                         // coalesced 128-byte store per tuple, no SUM walk
 #pragma unroll
@@ -400,8 +407,13 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                     const unsigned startmask = (endmask << 1) | prev_end;
                     prev_end = endmask >> 31;
                     uint32_t mword = 0;
-                    // segmented running sum over the chunk: v[j] <- sum of its piece up to row j
-                    if (a.kahan) {
+                    unsigned takemask = 0;  // MAX: rows where the piece's running maximum was taken
+                    // segmented running sum (maximum) over the chunk: v[j] <- sum (maximum) of its
+                    // piece up to row j
+                    if (AGG == kAggMax) {
+                        if (relu) seg_scan_max<true>(v, bo, startmask, sum, takemask);
+                        else seg_scan_max<false>(v, bo, startmask, sum, takemask);
+                    } else if (a.kahan) {
                         if (mask) seg_scan<true, true, true>(v, bo, startmask, sum, comp, mword, lane);
                         else if (relu) seg_scan<true, true, false>(v, bo, startmask, sum, comp, mword, lane);
                         else seg_scan<false, true, false>(v, bo, startmask, sum, comp, mword, lane);
@@ -440,13 +452,29 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                             const bool last = (c * 32 + j == nt - 1);
                             const int sn = last ? ((nt == unit) ? after_seg : -1) : s + 1;
                             const bool split = (first && prev_seg == s) || (last && sn == s);
-                            if (o_ok) {
+                            if (AGG == kAggMax) {
+                                // the piece's maximum was first reached at its last take up to row j
+                                const unsigned tk = takemask & (0xffffffffu >> (31 - j));
+                                const int pos = tk ? (int)(t0 + c * 32 + 31 - __clz(tk)) : rpos;
+                                if (o_ok) {
+                                    if (split) {
+                                        const int64_t ci = (vtile * 2 + (first ? 0 : 1)) * a.d_out + o;
+                                        __stcg(a.carry + ci, val);
+                                        __stcg(a.carry_pos + ci, pos);
+                                    } else {
+                                        __stcs(a.out + (int64_t)s * a.d_out + o, val);
+                                        __stcs(a.arg + (int64_t)s * a.d_out + o, (relu && !(val > 0.f)) ? -1 : pos);
+                                    }
+                                }
+                            } else if (o_ok) {
                                 if (split) __stcg(a.carry + (vtile * 2 + (first ? 0 : 1)) * a.d_out + o, val);
                                 else emit_out(a.out + (int64_t)s * a.d_out + o, val, a.accumulate);
                             }
                             first = false;
                         }
                     }
+                    // MAX: the open piece's position carried into the next chunk
+                    if (AGG == kAggMax && takemask) rpos = (int)(t0 + c * 32 + 31 - __clz(takemask));
                     if (mask && tvalid) a.relu_mask[(t0 + li) * a.mask_words + mb * 4 + fq] = mword;
                 }
             }
@@ -641,13 +669,22 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     }
     static bool attr_set = false;
     if (!attr_set) {
-        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false, kAggSum>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true, kAggSum>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false, kAggDense>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true, kAggDense>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<false, kAggMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(fwd_tc_kernel<true, kAggMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
-    const bool want_mask = p.act == RELNN_ACT_RELU && (p.flags & RELNN_FLAG_RELU_MASK);
+    const bool maxagg = (p.flags & RELNN_FLAG_MAX) != 0;
+    // MAX: the backward routes dOut through the recorded argmax instead of a ReLU mask
+    const bool want_mask = p.act == RELNN_ACT_RELU && (p.flags & RELNN_FLAG_RELU_MASK) && !maxagg;
+    if (maxagg) {
+        RELNN_CHECK_ARG(!multi, "MAX aggregator: single-branch rules only");
+        RELNN_TRY(p.carry_pos.alloc(sizeof(int32_t) * 2 * p.d_out * max_units));
+        RELNN_TRY(p.max_arg.alloc(sizeof(int32_t) * (size_t)p.n_out * p.d_out));
+    }
     const int mask_words = m_blocks * 4;
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
@@ -666,6 +703,10 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         a.bias = io.br[i].b;
         a.out = out;
         a.carry = p.carry.as<float>();
+        if (maxagg) {
+            a.carry_pos = p.carry_pos.as<int32_t>();
+            a.arg = p.max_arg.as<int32_t>();
+        }
         a.status = p.status.as<int>();
         if (want_mask) {
             RELNN_TRY(b.relu_mask.alloc(sizeof(uint32_t) * (size_t)b.m * mask_words));
@@ -702,17 +743,23 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
             ProfToken pt = prof_begin(RELNN_PROF_FWD_TC, st);
             const bool dense = (p.flags & kPlanDense) != 0;
             if (dense) {
-                if (idx_t) fwd_tc_kernel<true, true><<<grid, kThreads, smem, st>>>(wmap, a);
-                else fwd_tc_kernel<false, true><<<grid, kThreads, smem, st>>>(wmap, a);
+                if (idx_t) fwd_tc_kernel<true, kAggDense><<<grid, kThreads, smem, st>>>(wmap, a);
+                else fwd_tc_kernel<false, kAggDense><<<grid, kThreads, smem, st>>>(wmap, a);
+            } else if (maxagg) {
+                if (idx_t) fwd_tc_kernel<true, kAggMax><<<grid, kThreads, smem, st>>>(wmap, a);
+                else fwd_tc_kernel<false, kAggMax><<<grid, kThreads, smem, st>>>(wmap, a);
             } else {
-                if (idx_t) fwd_tc_kernel<true, false><<<grid, kThreads, smem, st>>>(wmap, a);
-                else fwd_tc_kernel<false, false><<<grid, kThreads, smem, st>>>(wmap, a);
+                if (idx_t) fwd_tc_kernel<true, kAggSum><<<grid, kThreads, smem, st>>>(wmap, a);
+                else fwd_tc_kernel<false, kAggSum><<<grid, kThreads, smem, st>>>(wmap, a);
             }
             note_launch();
             prof_end(pt, st);
         }
         RELNN_CUDA(cudaGetLastError());
-        if (!(p.flags & kPlanDense))
+        if (maxagg)
+            RELNN_TRY(launch_fixup_max(a.seg, a.m, unit, ceil_div(a.m, unit), a.carry, a.carry_pos, out, a.arg, p.d_out,
+                                       p.act == RELNN_ACT_RELU, p.fixjobs, st));
+        else if (!(p.flags & kPlanDense))
             RELNN_TRY(launch_fixup(a.seg, a.m, unit, ceil_div(a.m, unit), a.carry, out, p.d_out, multi, p.kahan, p.fixjobs, st));
         RELNN_CUDA(cudaGetLastError());
     }

@@ -496,6 +496,11 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     p.bf16 = (desc->flags & RELNN_FLAG_BF16) != 0;
     p.kahan = (desc->flags & RELNN_FLAG_KAHAN) != 0;
     RELNN_CHECK_ARG(p.join_dst || desc->n_branches == 1, "rule plan: a union needs the dst join (shared key space)");
+    if (desc->flags & RELNN_FLAG_MAX) {
+        RELNN_CHECK_ARG(desc->n_branches == 1, "rule plan: MAX aggregator: single-branch rules only");
+        RELNN_CHECK_ARG(!(desc->flags & (RELNN_FLAG_MEAN | RELNN_FLAG_PUSHDOWN)),
+                        "rule plan: MAX aggregator excludes MEAN and PUSHDOWN");
+    }
     const int d_r0 = desc->branches[0].d_r;
     for (int i = 0; i < desc->n_branches; ++i) {
         const relnn_branch_desc& b = desc->branches[i];

@@ -60,6 +60,11 @@ struct Plan {
     DevBuf pdP, pdQ, pdW;
     // MEAN aggregator (RELNN_FLAG_MEAN): 1 / matched tuples per output row, and the scaled dOut
     DevBuf inv_cnt, mean_dout;
+    // MAX aggregator (RELNN_FLAG_MAX): int32 [n_out][d_out] plan position of each maximum's first
+    // tuple (-1: no gradient), the positions of the boundary partials (twin of carry), and the
+    // winner mask the backward reads in place of a ReLU mask (uint32 [m][mask_words])
+    DevBuf max_arg, carry_pos, win_mask;
+    bool max_ready = false;  // a forward has filled max_arg
     int64_t total_matched() const {
         int64_t s = 0;
         for (auto& b : br) s += b.m;
@@ -69,7 +74,8 @@ struct Plan {
     // a synchronising cudaFree), for plans whose work all ran on s.
     void retire_on(cudaStream_t s) {
         DevBuf* bufs[] = {&H.rows_sorted, &H.run_start, &H.uid_of_pos, &H.ukeys, &H.slot_keys, &H.slot_vals,
-                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &pdP, &pdQ, &pdW, &inv_cnt, &mean_dout};
+                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &pdP, &pdQ, &pdW, &inv_cnt, &mean_dout,
+                          &max_arg, &carry_pos, &win_mask};
         for (DevBuf* b : bufs) {
             b->ordered = true;
             b->st = s;

@@ -35,6 +35,26 @@ __device__ __forceinline__ void seg_scan(uint32_t (&v)[32], float bo, unsigned s
     }
 }
 
+// Segmented running maximum over the same 32 tuples: v[j] <- the maximum of its piece up to row j;
+// bit j of `takemask` is set where row j becomes the piece's maximum (a piece start, or a value
+// strictly above the running maximum), so the first position attaining the maximum of the piece
+// up to row j is the highest set bit at or below j (or, with none, the carried position).
+template <bool RELU>
+__device__ __forceinline__ void seg_scan_max(uint32_t (&v)[32], float bo, unsigned startmask, float& run,
+                                             unsigned& takemask) {
+    unsigned tm = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        float y = __uint_as_float(v[j]) + bo;
+        if (RELU) y = fmaxf(y, 0.f);
+        const bool take = ((startmask >> j) & 1u) || y > run;
+        run = take ? y : run;
+        tm |= take ? (1u << j) : 0u;
+        v[j] = __float_as_uint(run);
+    }
+    takemask = tm;
+}
+
 // v[j] for a warp-uniform run-time j without local-memory indexing (a 5-level select tree).
 __device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], int j) {
     uint32_t t16[16], t8[8], t4[4];

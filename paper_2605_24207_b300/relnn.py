@@ -28,6 +28,7 @@ FLAG_RELU_MASK = 0x20
 FLAG_TILE128 = 0x40
 FLAG_PUSHDOWN = 0x80
 FLAG_MEAN = 0x100
+FLAG_MAX = 0x200
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOSPC", 4: "EAGAIN", 5: "ETIMEDOUT", 6: "ECUDA",
           7: "EDEVICE", 8: "ENOTSUP"}
