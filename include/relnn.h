@@ -89,6 +89,7 @@ typedef enum relnn_act_t { RELNN_ACT_NONE = 0, RELNN_ACT_RELU = 1 } relnn_act_t;
 typedef struct relnn_join_s* relnn_join_t;
 typedef struct relnn_plan_s* relnn_plan_t;
 typedef struct relnn_server_s* relnn_server_t;
+typedef struct relnn_stream_s* relnn_stream_t;
 
 /* ---------------------------------------------------------------------------------------------
  * Library
@@ -294,6 +295,54 @@ relnn_status relnn_serve_poll(relnn_server_t s, uint64_t ticket, relnn_result* r
 relnn_status relnn_serve_release(relnn_server_t s, uint64_t ticket);
 /* Stops accepting queries, finishes the queued ones, joins the workers and frees everything. */
 relnn_status relnn_server_destroy(relnn_server_t s);
+
+/* ---------------------------------------------------------------------------------------------
+ * Streaming a relation larger than device memory (paper Sec. 6, future work on scaling for memory:
+ * streaming the data from the database to the GPU in mini-batches). E (src, dst and the optional
+ * per-tuple embedding r) stays in HOST memory; H (ids, z) is device-resident. A forward or backward
+ * walks E in chunks: the next chunk's columns are copied while the current one is planned (join
+ * against the shared H build side, grouping) and evaluated, and every chunk adds its rows into one
+ * device accumulator indexed by H's distinct keys, so the result equals the unchunked rule's up to
+ * the order of f32 additions (chunks are added in order: deterministic). Single branch, dst joined
+ * (the output key space is H's), SUM or MEAN; no MAX, no PUSHDOWN.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct relnn_stream_desc {
+    relnn_key_t key_type;       /* type of H.id, E.src, E.dst                                       */
+    const void* d_h_ids;        /* [n_h] keys of H (device; used by relnn_stream_create only)      */
+    int64_t n_h;
+    int32_t d;                  /* width of H.z                                                     */
+    int32_t d_out;              /* output width (ignored with RELNN_FLAG_IDENTITY)                  */
+    relnn_act_t act;
+    uint32_t flags;             /* RELNN_FLAG_BF16, KAHAN, IDENTITY, NO_CONCAT_DST, MEAN, TILE128   */
+    const void* h_src;          /* [n_tuples] keys of E.src (HOST; pinned memory overlaps copies)   */
+    const void* h_dst;          /* [n_tuples] keys of E.dst (HOST); both must outlive the stream    */
+    int64_t n_tuples;           /* any size (chunks hold < 2^31 tuples each)                        */
+    int32_t d_r;                /* width of the per-tuple embedding r (0 = none)                    */
+    int32_t n_filters;          /* selection predicates (as relnn_branch_desc)                      */
+    const relnn_filter* filters;
+    int64_t chunk_tuples;       /* E rows per chunk; 0: from mem_budget_bytes                       */
+    int64_t mem_budget_bytes;   /* device bytes the chunk pipeline may hold; 0: a quarter of free   */
+} relnn_stream_desc;
+
+/* sync. Builds the H side (join build over H.id) and the device accumulators ([U, d_out] f32 per
+ * role, U = distinct keys of H). Errors: EINVAL (unsupported flags / shapes), ENOMEM. */
+relnn_status relnn_stream_create(const relnn_stream_desc* desc, void* stream, relnn_stream_t* out);
+/* Distinct keys of H (the output capacity a forward needs), tuples per chunk and chunks per pass. */
+relnn_status relnn_stream_info(relnn_stream_t s, int64_t* max_out_rows, int64_t* chunk_tuples, int64_t* n_chunks);
+/* sync. Forward over all of E: d_out_keys [max_out_rows] (may be NULL) and d_out_z
+ * [max_out_rows, d_out] f32 receive the n_out (*h_n_out) output rows, keys ascending, as
+ * relnn_rule_forward would for the whole E. prm holds z, W, b as for a rule (one branch); its r
+ * entry, if any, is a HOST pointer [n_tuples, d_r] (streamed with the keys). */
+relnn_status relnn_stream_forward(relnn_stream_t s, const relnn_rule_params* prm, void* d_out_keys, float* d_out_z,
+                                  int64_t* h_n_out, void* stream);
+/* sync. Backward of the last relnn_stream_forward for d_dout [n_out, d_out] f32 (rows as that
+ * forward returned them): d_dW [d_out, d_in], d_db [d_out], d_dz [n_h, d] (device, OVERWRITTEN) and
+ * h_dr [n_tuples, d_r] (HOST, overwritten; may be NULL), each may be NULL to skip. The chunks are
+ * re-planned; a BF16 rule with ReLU re-runs each chunk's forward for its ReLU mask. */
+relnn_status relnn_stream_backward(relnn_stream_t s, const relnn_rule_params* prm, const float* d_dout, float* d_dW,
+                                   float* d_db, float* d_dz, float* h_dr, void* stream);
+/* Frees the stream's device memory (waits for the device first). */
+relnn_status relnn_stream_destroy(relnn_stream_t s);
 
 /* ---------------------------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to report roofline fractions).

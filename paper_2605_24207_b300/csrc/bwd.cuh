@@ -12,6 +12,7 @@ struct GradIO {
     const float* dout = nullptr;          // [n_out, d_out]
     std::vector<float*> dW, db, dr;       // per branch (entries may be null)
     float* dz = nullptr;                  // [n_h, d]
+    bool accumulate_dz = false;           // add into dz instead of overwriting it (stream chunks)
 };
 
 relnn_status backward_fp32(Plan& p, const CallIO& io, const GradIO& g, cudaStream_t st);

@@ -186,7 +186,7 @@ __global__ void bw_reduce_kernel(const float* part, int nchunks, int64_t n, floa
 relnn_status backward_fp32(Plan& p, const CallIO& io, const GradIO& g, cudaStream_t st) {
     RELNN_CHECK_ARG(g.dout, "backward: null output gradient");
     RELNN_CHECK_ARG(p.d_in <= 1024 && p.d_out <= 1024, "backward: widths too large");
-    if (g.dz) RELNN_CUDA(cudaMemsetAsync(g.dz, 0, sizeof(float) * p.n_h * p.d, st));
+    if (g.dz && !g.accumulate_dz) RELNN_CUDA(cudaMemsetAsync(g.dz, 0, sizeof(float) * p.n_h * p.d, st));
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         const bool need_w = !p.identity && (g.dW.size() > i && (g.dW[i] || g.db[i]));

@@ -710,7 +710,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         RELNN_CUDA(cudaFuncSetAttribute(bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
-    if (g.dz) RELNN_CUDA(cudaMemsetAsync(g.dz, 0, sizeof(float) * p.n_h * p.d, st));
+    if (g.dz && !g.accumulate_dz) RELNN_CUDA(cudaMemsetAsync(g.dz, 0, sizeof(float) * p.n_h * p.d, st));
     // the src pass gathers dOut rows in H-row order: from a bf16 copy (half the bytes, the rounding
     // dY gets anyway)
     const uint16_t* dout_bf = nullptr;

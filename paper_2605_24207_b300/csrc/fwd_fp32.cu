@@ -530,8 +530,9 @@ relnn_status launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_til
 
 relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
     RELNN_CHECK_ARG(p.d_in <= 1024 && p.d_out <= 256, "FP32 form: d_in <= 1024 and d_out <= 256 required");
-    const bool multi = p.br.size() > 1;
-    if (multi) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));
+    // several branches add into one output; a stream chunk adds into the stream's accumulator
+    const bool multi = p.br.size() > 1 || p.acc_out;
+    if (p.br.size() > 1 && !p.acc_out) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));
     const int threads = std::max(32, ((p.d_out + 31) / 32) * 32);
     int64_t max_tiles = 1;
     for (auto& b : p.br) max_tiles = std::max<int64_t>(max_tiles, ceil_div(b.m, kTT));

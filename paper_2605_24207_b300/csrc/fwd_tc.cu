@@ -633,8 +633,9 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         set_error("cuTensorMapEncodeTiled unavailable");
         return RELNN_ECUDA;
     }
-    const bool multi = p.br.size() > 1;
-    if (multi) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));
+    // several branches add into one output; a stream chunk adds into the stream's accumulator
+    const bool multi = p.br.size() > 1 || p.acc_out;
+    if (p.br.size() > 1 && !p.acc_out) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));
     // replicas of W in the lane quarters, and the column unit of the SUM walk / boundary partials
     const int half_n = tile_n / 2;
     int rep = m_blocks == 1 ? (p.d_out <= 32 ? 4 : (p.d_out <= 64 ? 2 : 1)) : 1;

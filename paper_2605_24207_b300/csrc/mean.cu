@@ -49,6 +49,13 @@ relnn_status ensure_inv_count(Plan& p, cudaStream_t st) {
     return RELNN_OK;
 }
 
+relnn_status count_rows_into(const int32_t* seg, int64_t m, int32_t* cnt, cudaStream_t st) {
+    if (m == 0) return RELNN_OK;
+    { count_rows_kernel<<<grid_for(m), 256, 0, st>>>(seg, m, cnt); note_launch(); }
+    RELNN_CUDA(cudaGetLastError());
+    return RELNN_OK;
+}
+
 relnn_status scale_rows(const float* src, const float* inv, int64_t n, int d, float* dst, cudaStream_t st) {
     if (n == 0) return RELNN_OK;
     { scale_rows_kernel<<<grid_for(n * d), 256, 0, st>>>(src, inv, n, d, dst); note_launch(); }

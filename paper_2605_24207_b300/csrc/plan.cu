@@ -336,9 +336,9 @@ FilterSet filters_of(const relnn_branch_desc& bd) {
 template <class K, class V>
 relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M_out, cudaStream_t st) {
     const int64_t T = bd.n_tuples;
-    const JoinView v = p.H.view();
+    const JoinView v = p.Ht().view();
     int64_t M = 0;
-    if (p.H.n_unique == p.n_h) {
+    if (p.Ht().n_unique == p.n_h) {
         const int64_t cap = std::max<int64_t>(T, 1);
         RELNN_TRY(t.key.alloc_tmp(sizeof(K) * cap, st));
         RELNN_TRY(t.key_tmp.alloc_tmp(sizeof(K) * cap, st));
@@ -483,7 +483,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     RELNN_CHECK_ARG(desc->key_type == RELNN_I32 || desc->key_type == RELNN_I64, "rule plan: bad key type");
     RELNN_CHECK_ARG(desc->n_branches >= 1 && desc->branches, "rule plan: need >= 1 branch");
     RELNN_CHECK_ARG(desc->d > 0 && desc->d <= 4096, "rule plan: bad embedding width d");
-    RELNN_CHECK_ARG(desc->n_h >= 0 && (desc->n_h == 0 || desc->d_h_ids), "rule plan: bad H");
+    RELNN_CHECK_ARG(desc->n_h >= 0 && (desc->n_h == 0 || desc->d_h_ids || p.Hx), "rule plan: bad H");
     RELNN_CHECK_ARG(desc->act == RELNN_ACT_NONE || desc->act == RELNN_ACT_RELU, "rule plan: bad act");
     p.kt = desc->key_type;
     p.flags = desc->flags;
@@ -524,8 +524,9 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     RELNN_CUDA(cudaMemsetAsync(p.status.p, 0, sizeof(int), st));
 
     // a1: build side over H.id
-    RELNN_TRY(join_table_build(p.H, desc->d_h_ids, desc->n_h, p.kt, st));
-    const int64_t U = p.H.n_unique;
+    if (!p.Hx) RELNN_TRY(join_table_build(p.H, desc->d_h_ids, desc->n_h, p.kt, st));
+    const JoinTable& HT = p.Ht();
+    const int64_t U = HT.n_unique;
 
     // a2: probe and emit per branch; a3: sort by group key
     p.br.clear();
@@ -539,7 +540,19 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
 
     // output key set and output row of every matched tuple
     int32_t nout_join = 0;
-    if (p.join_dst) {
+    if (p.join_dst && p.dense_out) {
+        // stream chunk: output row = distinct index of the dst key; presence kept by the stream
+        for (auto i = 0u; i < p.br.size(); ++i)
+            if (p.br[i].m > 0) {
+                { mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                    tmp[i].keys<uint32_t>(), p.br[i].m, HT.uid_of_pos.as<int32_t>(), p.present_ext); note_launch(); }
+                { finalize_dst_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                    tmp[i].keys<uint32_t>(), p.br[i].m, HT.rows_sorted.as<int32_t>(), HT.uid_of_pos.as<int32_t>(),
+                    p.iota_ext, p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>()); note_launch(); }
+            }
+        RELNN_CUDA(cudaGetLastError());
+        nout_join = (int32_t)U;
+    } else if (p.join_dst) {
         DevBuf present;
         RELNN_TRY(present.alloc_tmp(sizeof(int32_t) * (U + 1), st));
         RELNN_CUDA(cudaMemsetAsync(present.p, 0, sizeof(int32_t) * (U + 1), st));
@@ -548,18 +561,18 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
                 { mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
-                    tmp[i].keys<uint32_t>(), p.br[i].m, p.H.uid_of_pos.as<int32_t>(), present.as<int32_t>()); note_launch(); }
+                    tmp[i].keys<uint32_t>(), p.br[i].m, HT.uid_of_pos.as<int32_t>(), present.as<int32_t>()); note_launch(); }
         RELNN_TRY(exclusive_scan<int32_t>(present.as<int32_t>(), out_row.as<int32_t>(), U, out_row.as<int32_t>() + U, st));
         // the output-row count arrives with the final synchronisation; U bounds it
         RELNN_CUDA(cudaMemcpyAsync(&nout_join, out_row.as<int32_t>() + U, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         RELNN_TRY(p.out_keys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(U, 1), st));
         if (U > 0)
             { out_keys_kernel<<<grid_for(U), 256, 0, st>>>(present.as<int32_t>(), out_row.as<int32_t>(),
-                                                         p.H.ukeys.as<int64_t>(), U, p.out_keys.as<int64_t>()); note_launch(); }
+                                                         HT.ukeys.as<int64_t>(), U, p.out_keys.as<int64_t>()); note_launch(); }
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
                 { finalize_dst_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
-                    tmp[i].keys<uint32_t>(), p.br[i].m, p.H.rows_sorted.as<int32_t>(), p.H.uid_of_pos.as<int32_t>(),
+                    tmp[i].keys<uint32_t>(), p.br[i].m, HT.rows_sorted.as<int32_t>(), HT.uid_of_pos.as<int32_t>(),
                     out_row.as<int32_t>(), p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>()); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
     } else {

@@ -65,6 +65,15 @@ struct Plan {
     // winner mask the backward reads in place of a ReLU mask (uint32 [m][mask_words])
     DevBuf max_arg, carry_pos, win_mask;
     bool max_ready = false;  // a forward has filled max_arg
+    // Chunk of a streamed relation: the H build side is the stream's (Hx); with dense_out the
+    // output rows are H's distinct-key indices (n_out = U, seg = distinct index, the present flags
+    // go to present_ext, iota_ext is the identity map 0..U); with acc_out the forward adds into its
+    // output instead of overwriting it
+    const JoinTable* Hx = nullptr;
+    bool dense_out = false, acc_out = false;
+    int32_t* present_ext = nullptr;
+    const int32_t* iota_ext = nullptr;
+    const JoinTable& Ht() const { return Hx ? *Hx : H; }
     int64_t total_matched() const {
         int64_t s = 0;
         for (auto& b : br) s += b.m;

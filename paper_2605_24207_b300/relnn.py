@@ -77,6 +77,13 @@ class RuleDesc(C.Structure):
                 ("act", C.c_int), ("flags", C.c_uint32)]
 
 
+class StreamDesc(C.Structure):
+    _fields_ = [("key_type", C.c_int), ("d_h_ids", C.c_void_p), ("n_h", C.c_int64), ("d", C.c_int32),
+                ("d_out", C.c_int32), ("act", C.c_int), ("flags", C.c_uint32), ("h_src", C.c_void_p),
+                ("h_dst", C.c_void_p), ("n_tuples", C.c_int64), ("d_r", C.c_int32), ("n_filters", C.c_int32),
+                ("filters", C.POINTER(Filter)), ("chunk_tuples", C.c_int64), ("mem_budget_bytes", C.c_int64)]
+
+
 class RuleParams(C.Structure):
     _fields_ = [("d_z", C.c_void_p), ("z_dtype", C.c_int), ("d_r", C.POINTER(C.c_void_p)), ("r_dtype", C.c_int),
                 ("d_W", C.POINTER(C.c_void_p)), ("w_dtype", C.c_int), ("d_b", C.POINTER(C.c_void_p))]
@@ -121,6 +128,14 @@ def lib():
     L.relnn_rule_forward_noalloc.restype = C.c_int
     L.relnn_mse_loss.argtypes = [vp, vp, i64, vp, vp, i64, C.c_int32, C.c_int, vp, vp, vp]
     L.relnn_mse_loss.restype = C.c_int
+    L.relnn_stream_create.argtypes = [C.POINTER(StreamDesc), vp, C.POINTER(vp)]
+    L.relnn_stream_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    L.relnn_stream_forward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, C.POINTER(i64), vp]
+    L.relnn_stream_backward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp, vp, vp]
+    L.relnn_stream_destroy.argtypes = [vp]
+    for name in ("relnn_stream_create", "relnn_stream_info", "relnn_stream_forward", "relnn_stream_backward",
+                 "relnn_stream_destroy"):
+        getattr(L, name).restype = C.c_int
     L.relnn_profile_enable.argtypes = [C.c_int32]
     L.relnn_profile_read.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(i64)]
     for name in EXPORTS[4:-1]:
@@ -322,6 +337,78 @@ class RulePlan:
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value and _LIB is not None:
             _LIB.relnn_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+
+class StreamRule:
+    """relnn_stream_*: a single-branch rule whose E (src, dst and the optional per-tuple r) stays in
+    host memory and is streamed to the device in chunks; H (ids, z) is on the device."""
+
+    def __init__(self, h_ids: torch.Tensor, src: torch.Tensor, dst: torch.Tensor, d: int, d_out: int,
+                 act: int = ACT_NONE, flags: int = 0, d_r: int = 0, chunk_tuples: int = 0, mem_budget: int = 0,
+                 filters=None, stream=None):
+        """``src`` / ``dst``: CPU key tensors (pinned memory lets the copies overlap the compute);
+        they are kept referenced for the stream's lifetime."""
+        assert not src.is_cuda and not dst.is_cuda, "E stays in host memory"
+        self.kt = _key_type(h_ids)
+        self.key_dtype = h_ids.dtype
+        self.device = h_ids.device
+        self.src, self.dst = src.contiguous(), dst.contiguous()
+        assert self.src.dtype == self.key_dtype and self.dst.dtype == self.key_dtype
+        self.flags, self.act, self.d, self.d_r = flags, act, d, d_r
+        self.n_tuples = int(self.src.numel())
+        self._farr, nf = _filters(filters)
+        desc = StreamDesc(self.kt, _ptr(h_ids), h_ids.numel(), d, d_out, act, flags, self.src.data_ptr(),
+                          self.dst.data_ptr(), self.n_tuples, d_r, nf,
+                          C.cast(self._farr, C.POINTER(Filter)) if self._farr is not None else None,
+                          chunk_tuples, mem_budget)
+        self._h = C.c_void_p()
+        _check(lib().relnn_stream_create(C.byref(desc), _stream(stream), C.byref(self._h)))
+        u, ch, nc = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().relnn_stream_info(self._h, C.byref(u), C.byref(ch), C.byref(nc)))
+        self.max_out, self.chunk_tuples, self.n_chunks = u.value, ch.value, nc.value
+        concat = d * (1 if flags & FLAG_NO_CONCAT_DST else 2) + d_r
+        self.d_in = concat
+        self.d_out = concat if flags & FLAG_IDENTITY else d_out
+        self.n_out = None
+
+    def _params(self, z, W, b, r):
+        Ws = (C.c_void_p * 1)(_ptr(W)) if W is not None else None
+        bs = (C.c_void_p * 1)(_ptr(b)) if b is not None else None
+        rs = None
+        if r is not None:
+            assert not r.is_cuda and r.is_contiguous(), "r is streamed from host memory"
+            rs = (C.c_void_p * 1)(r.data_ptr())
+        prm = RuleParams(_ptr(z), _float_type(z), rs, _float_type(r) if r is not None else F32, Ws,
+                         _float_type(W) if W is not None else F32, bs)
+        return prm, (Ws, bs, rs)
+
+    def forward(self, z, W=None, b=None, r=None, stream=None):
+        """(output keys [n_out], output embeddings [n_out, d_out] f32), keys ascending."""
+        keys = torch.empty(max(self.max_out, 1), dtype=self.key_dtype, device=self.device)
+        out = torch.empty((max(self.max_out, 1), self.d_out), dtype=torch.float32, device=self.device)
+        prm, keep = self._params(z, W, b, r)
+        n = C.c_int64()
+        _check(lib().relnn_stream_forward(self._h, C.byref(prm), _ptr(keys), _ptr(out), C.byref(n), _stream(stream)))
+        self.n_out = n.value
+        return keys[: self.n_out], out[: self.n_out]
+
+    def backward(self, dout, z, W=None, b=None, r=None, need_dz=True, stream=None):
+        """(dW, db, dz, dr) for the output gradient of the last forward; dr is a CPU tensor."""
+        dev = self.device
+        dW = torch.empty((self.d_out, self.d_in), dtype=torch.float32, device=dev) if W is not None else None
+        db = torch.empty(self.d_out, dtype=torch.float32, device=dev) if W is not None else None
+        dz = torch.empty(z.shape, dtype=torch.float32, device=dev) if need_dz else None
+        dr = torch.empty((self.n_tuples, self.d_r), dtype=torch.float32) if (r is not None and self.d_r > 0) else None
+        prm, keep = self._params(z, W, b, r)
+        dout = dout.contiguous()
+        _check(lib().relnn_stream_backward(self._h, C.byref(prm), _ptr(dout), _ptr(dW), _ptr(db), _ptr(dz),
+                                           dr.data_ptr() if dr is not None else None, _stream(stream)))
+        return dW, db, dz, dr
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value and _LIB is not None:
+            _LIB.relnn_stream_destroy(self._h)
             self._h = C.c_void_p()
 
 
