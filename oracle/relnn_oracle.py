@@ -20,6 +20,10 @@ Definitions followed (paper sections):
   * join rule R(x; alpha(tau)) :- R1,...,Rk  ==  U_{alpha,x}(T_tau(R1 |><| ... |><| Rk)) -- Sec. 3.1
   * union rule / "|..." replicator: branch results added by the head's sum             -- Sec. 3.1, 3.7
   * fit: parameters (weights and per-tuple embeddings) minimise a loss relation        -- Sec. 2.3, 3.2, 3.6
+  * attention over a join: Score(p, t; q*k) :- E(t, p), Q(p; q), K(t; k) and
+    Attention(p; sum(a*v)) :- Score(p, t; a), V(t; v) (element-wise product head), and the
+    HGT head: per head, softmax over t of the scaled dot product q . k, then the weighted
+    sum of v                                                                          -- Sec. 1, Sec. 5 (HGT)
 
 Readings where the paper is silent (each is listed with its reason in the design notes):
   * bag semantics: every E row is a distinct tuple, duplicate H keys each match;
@@ -42,6 +46,7 @@ __all__ = [
     "max_tie_order", "selected_rows",
     "selected_join",
     "rule_forward", "rule_backward", "mse", "mse_grad", "stacked_forward", "stacked_backward",
+    "attention_forward", "attention_backward",
 ]
 
 CHUNK = 1 << 20  # join triples processed per NumPy block in the Linear/SUM steps
@@ -405,3 +410,81 @@ def stacked_backward(h_ids, z, src, dst, W1, b1, W2, b2, g_keys, g_groups, t_gro
     (dW1,), (db1,), dz, _ = rule_backward(h_ids, z, [_Br(src, dst, W1, b1)], f["k1"], d_h1,
                                           act="relu")
     return dict(dW1=dW1, db1=db1, dW2=dW2, db2=db2, dz=dz, d_h1=d_h1, d_h2=d_h2, d_ho=d_ho)
+
+
+# ----------------------------------------------------------------------------- attention over a join
+def _attn_parts(h_ids, src, dst):
+    """Join triples of E(t = src, p = dst) with H on both sides; the output key of a tuple is p."""
+    e, hs, hd = join(src, dst, h_ids)
+    keys = np.asarray(dst)[e]
+    uk, inv = np.unique(keys, return_inverse=True)
+    return e, hs, hd, uk, inv.reshape(-1)
+
+
+def _scores(q, k, hs, hd, n_heads, scale):
+    """s[t, h] = scale * sum over head h's features of q[hd_t] * k[hs_t]."""
+    d = q.shape[1]
+    prod = (q[hd] * k[hs]).reshape(hs.size, n_heads, d // n_heads)
+    return scale * prod.sum(axis=2)
+
+
+def attention_forward(h_ids, q, k, v, src, dst, n_heads=1, scale=1.0, mode="softmax"):
+    """Attention of each output key p over its join tuples t (E rows with dst = p; q from the dst
+    side's H row, k and v from the src side's H row), in float64.
+
+    mode "product" (the Sec. 1 program): Out[p] = sum_t q_t * k_t * v_t element-wise (d_v = d).
+    mode "softmax" (the HGT head of Sec. 5): per head h, a_t = exp(s_t) / sum_t' exp(s_t') with
+    s_t = scale * q_t . k_t over the head's features, and Out[p][h] = sum_t a_t v_t[h].
+    Returns (sorted output keys, Out [n_out, d_v], logsumexp [n_out, n_heads] or None)."""
+    q = np.asarray(q, np.float64)
+    k = np.asarray(k, np.float64)
+    v = np.asarray(v, np.float64)
+    e, hs, hd, uk, inv = _attn_parts(h_ids, src, dst)
+    d_v = v.shape[1]
+    out = np.zeros((uk.size, d_v))
+    if mode == "product":
+        np.add.at(out, inv, q[hd] * k[hs] * v[hs])
+        return uk, out, None
+    s = _scores(q, k, hs, hd, n_heads, scale)
+    lse = np.full((uk.size, n_heads), -np.inf)
+    for g in range(uk.size):
+        rows = np.nonzero(inv == g)[0]
+        sg = s[rows]
+        m = sg.max(axis=0)
+        w = np.exp(sg - m)
+        lse[g] = m + np.log(w.sum(axis=0))
+        a = w / w.sum(axis=0)
+        vg = v[hs[rows]].reshape(rows.size, n_heads, d_v // n_heads)
+        out[g] = (a[:, :, None] * vg).sum(axis=0).reshape(d_v)
+    return uk, out, lse
+
+
+def attention_backward(h_ids, q, k, v, src, dst, dout, n_heads=1, scale=1.0, mode="softmax"):
+    """Gradients (dq, dk, dv) of sum(dout * Out) for ``attention_forward`` (rows of dout in its key
+    order); each tuple's contribution is added to the H rows it was gathered from."""
+    q = np.asarray(q, np.float64)
+    k = np.asarray(k, np.float64)
+    v = np.asarray(v, np.float64)
+    dout = np.asarray(dout, np.float64)
+    e, hs, hd, uk, inv = _attn_parts(h_ids, src, dst)
+    dq, dk, dv = np.zeros_like(q), np.zeros_like(k), np.zeros_like(v)
+    G = dout[inv]
+    if mode == "product":
+        np.add.at(dq, hd, G * k[hs] * v[hs])
+        np.add.at(dk, hs, G * q[hd] * v[hs])
+        np.add.at(dv, hs, G * q[hd] * k[hs])
+        return dq, dk, dv
+    _, out, lse = attention_forward(h_ids, q, k, v, src, dst, n_heads, scale, mode)
+    d, d_v = q.shape[1], v.shape[1]
+    s = _scores(q, k, hs, hd, n_heads, scale)
+    a = np.exp(s - lse[inv])                                   # [T, heads]
+    Gh = G.reshape(-1, n_heads, d_v // n_heads)
+    vh = v[hs].reshape(-1, n_heads, d_v // n_heads)
+    np.add.at(dv, hs, (a[:, :, None] * Gh).reshape(-1, d_v))
+    da = (Gh * vh).sum(axis=2)                                 # dL/da_t per head
+    D = (dout.reshape(-1, n_heads, d_v // n_heads) * out.reshape(-1, n_heads, d_v // n_heads)).sum(axis=2)
+    ds = a * (da - D[inv]) * scale                             # dL/d(q . k) per head
+    dsf = np.repeat(ds, d // n_heads, axis=1)
+    np.add.at(dq, hd, dsf * k[hs])
+    np.add.at(dk, hs, dsf * q[hd])
+    return dq, dk, dv

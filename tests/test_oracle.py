@@ -640,3 +640,110 @@ def test_max_backward_finite_differences(act):
             lm = loss()
             arr[i] = old
             assert (lp - lm) / (2 * h) == pytest.approx(grad[i], rel=1e-6, abs=1e-7)
+
+
+# ----------------------------------------------------------------------------- attention over a join
+def _attn_case(seed, n_h=12, n_e=50, d=8, key_range=10, dup=True):
+    rng = np.random.default_rng(seed)
+    h_ids = rng.integers(0, key_range, size=n_h) if dup else rng.permutation(key_range)[:n_h]
+    q, k, v = (rng.standard_normal((n_h, d)) for _ in range(3))
+    src = rng.integers(0, key_range + 2, size=n_e)
+    dst = rng.integers(0, key_range + 2, size=n_e)
+    return h_ids, q, k, v, src, dst
+
+
+def brute_attention(h_ids, q, k, v, src, dst, n_heads, scale, mode):
+    """Explicit loops over E x H x H: per output key, the list of (q row, k row, v row) of its
+    tuples, then the product head or the per-head softmax written out term by term."""
+    groups = {}
+    for (e, a, c) in brute_join(src, dst, h_ids):
+        groups.setdefault(dst[e], []).append((c, a))
+    keys = sorted(groups)
+    d, d_v = q.shape[1], v.shape[1]
+    out = np.zeros((len(keys), d_v))
+    for i, key in enumerate(keys):
+        tuples = groups[key]
+        if mode == "product":
+            for (c, a) in tuples:
+                for f in range(d_v):
+                    out[i][f] += q[c][f] * k[a][f] * v[a][f]
+            continue
+        hq, hv = d // n_heads, d_v // n_heads
+        for h in range(n_heads):
+            sc = []
+            for (c, a) in tuples:
+                sc.append(scale * sum(q[c][h * hq + j] * k[a][h * hq + j] for j in range(hq)))
+            mx = max(sc)
+            w = [np.exp(x - mx) for x in sc]
+            tot = sum(w)
+            for (c, a), wt in zip(tuples, w):
+                for j in range(hv):
+                    out[i][h * hv + j] += wt / tot * v[a][h * hv + j]
+    return keys, out
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("mode,heads", [("product", 1), ("softmax", 1), ("softmax", 2), ("softmax", 4)])
+def test_attention_matches_brute_force(seed, mode, heads):
+    h_ids, q, k, v, src, dst = _attn_case(seed + 200)
+    keys, out, _ = O.attention_forward(h_ids, q, k, v, src, dst, heads, 0.7, mode)
+    bk, bo = brute_attention(h_ids, q, k, v, src, dst, heads, 0.7, mode)
+    assert list(keys) == bk
+    np.testing.assert_allclose(out, bo, rtol=1e-12, atol=1e-12)
+
+
+def test_attention_uniform_weights_is_the_mean_aggregator():
+    """k = 0 makes every score 0, so the softmax weights are uniform: the output is the MEAN of the
+    group's v rows, i.e. the identity rule with alpha = MEAN over z = v (no z_dst)."""
+    h_ids, q, k, v, src, dst = _attn_case(210)
+    keys, out, _ = O.attention_forward(h_ids, q, np.zeros_like(k), v, src, dst, 2, 1.0, "softmax")
+    br = Br(src, dst, None, None)
+    k2, mean, _ = O.rule_forward(h_ids, v, [br], concat_dst=False, agg="mean")
+    assert np.array_equal(keys, k2)
+    np.testing.assert_allclose(out, mean, rtol=1e-12, atol=1e-12)
+
+
+def test_attention_is_invariant_to_a_shift_of_the_keys():
+    """With unique H keys every tuple of output key p uses the same q row, so adding one vector c to
+    every k row shifts all of p's scores by the same scale * q_p . c: the softmax is unchanged."""
+    h_ids, q, k, v, src, dst = _attn_case(211, dup=False)
+    c = np.random.default_rng(1).standard_normal(k.shape[1])
+    _, o1, _ = O.attention_forward(h_ids, q, k, v, src, dst, 2, 0.5)
+    _, o2, _ = O.attention_forward(h_ids, q, k + c, v, src, dst, 2, 0.5)
+    np.testing.assert_allclose(o1, o2, rtol=1e-10, atol=1e-12)
+
+
+def test_attention_single_tuple_keys_return_v():
+    rng = np.random.default_rng(4)
+    h_ids = np.arange(30)
+    q, k, v = (rng.standard_normal((30, 8)) for _ in range(3))
+    src, dst = rng.integers(0, 30, size=20), rng.permutation(30)[:20]
+    keys, out, lse = O.attention_forward(h_ids, q, k, v, src, dst, 4, 0.3)
+    order = np.argsort(dst)
+    np.testing.assert_allclose(out, v[src[order]], rtol=1e-12, atol=1e-12)
+    s = 0.3 * (q[dst[order]] * k[src[order]]).reshape(20, 4, 2).sum(axis=2)
+    np.testing.assert_allclose(lse, s, rtol=1e-12, atol=1e-12)  # log of a single exp
+
+
+@pytest.mark.parametrize("mode,heads", [("product", 1), ("softmax", 2)])
+def test_attention_backward_finite_differences(mode, heads):
+    h_ids, q, k, v, src, dst = _attn_case(220, n_e=30, d=4)
+    keys, out, _ = O.attention_forward(h_ids, q, k, v, src, dst, heads, 0.8, mode)
+    C = np.random.default_rng(5).standard_normal(out.shape)
+    dq, dk, dv = O.attention_backward(h_ids, q, k, v, src, dst, C, heads, 0.8, mode)
+    h = 1e-6
+
+    def loss():
+        return float(np.sum(O.attention_forward(h_ids, q, k, v, src, dst, heads, 0.8, mode)[1] * C))
+
+    rng = np.random.default_rng(6)
+    for arr, grad in ((q, dq), (k, dk), (v, dv)):
+        for _ in range(6):
+            i = tuple(rng.integers(0, s) for s in arr.shape)
+            old = arr[i]
+            arr[i] = old + h
+            lp = loss()
+            arr[i] = old - h
+            lm = loss()
+            arr[i] = old
+            assert (lp - lm) / (2 * h) == pytest.approx(grad[i], rel=1e-6, abs=1e-7)
