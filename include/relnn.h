@@ -207,6 +207,40 @@ relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, c
                                  float* const* d_dW, float* const* d_db, float* d_dz,
                                  float* const* d_dr, void* stream);
 
+/* Attention over a rule's join (paper Sec. 1: Score(p, t; q*k) :- Treat(p, t), Queries(p; q),
+ * Keys(t; k) and Attention(p; sum(a*v)) :- Score(p, t; a), Values(t; v); Sec. 5: the HGT head).
+ * On a single-branch plan with a dst join and no per-tuple embedding, E(src = t, dst = p): every
+ * output key p attends over its matched tuples, with q from the dst side's H row and k, v from the
+ * src side's H row (rows of d_q, d_k, d_v are aligned with H's rows).
+ *   RELNN_ATTN_PRODUCT: Out[p] = sum_t q_t * k_t * v_t (element-wise).
+ *   RELNN_ATTN_SOFTMAX: per head h (features [h d/H, (h+1) d/H)), a_t = softmax over p's tuples of
+ *                       scale * q_t . k_t, Out[p][h] = sum_t a_t v_t[h]; lse[p][h] = log sum_t exp. */
+#define RELNN_ATTN_SOFTMAX 0
+#define RELNN_ATTN_PRODUCT 1
+typedef struct relnn_attn_params {
+    const void* d_q;         /* [n_h, d] (device, 16-byte aligned)                                 */
+    const void* d_k;         /* [n_h, d]                                                           */
+    const void* d_v;         /* [n_h, d_val]                                                       */
+    relnn_float_t dtype;     /* of q, k and v                                                      */
+    int32_t d;               /* 32, 64, 128 or 256                                                 */
+    int32_t d_val;           /* width of v; = d                                                    */
+    int32_t n_heads;         /* softmax: a power of two <= 32 (ignored by the product head)        */
+    float scale;             /* softmax: multiplies q . k (e.g. 1 / sqrt(d / n_heads))             */
+    int32_t mode;            /* RELNN_ATTN_SOFTMAX or RELNN_ATTN_PRODUCT                           */
+} relnn_attn_params;
+
+/* async. d_out [n_out, d] f32 (rows in relnn_plan_out_keys order, 16-byte aligned) and, for the
+ * softmax head, d_lse [n_out, n_heads] f32 (may be NULL when no backward follows). Deterministic.
+ * Errors: EINVAL (plan or shape outside the above). */
+relnn_status relnn_attention_forward(relnn_plan_t p, const relnn_attn_params* prm, float* d_out, float* d_lse,
+                                     void* stream);
+/* async. Gradients of sum(d_dout * Out) for the forward's inputs: d_dq, d_dk, d_dv [n_h, d] f32 are
+ * OVERWRITTEN (each may be NULL to skip); the softmax head needs that forward's d_out and d_lse.
+ * Contributions are added with f32 atomics (run order may vary in the last bits). */
+relnn_status relnn_attention_backward(relnn_plan_t p, const relnn_attn_params* prm, const float* d_fwd_out,
+                                      const float* d_lse, const float* d_dout, float* d_dq, float* d_dk, float* d_dv,
+                                      void* stream);
+
 /* Releases the plan's device memory (waits for the device first). */
 relnn_status relnn_plan_destroy(relnn_plan_t p);
 

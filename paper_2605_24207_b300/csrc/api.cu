@@ -217,6 +217,19 @@ relnn_status relnn_rule_backward(relnn_plan_t p, const relnn_rule_params* prm, c
     return backward_fp32(P, io, g, st);
 }
 
+relnn_status relnn_attention_forward(relnn_plan_t p, const relnn_attn_params* prm, float* d_out, float* d_lse,
+                                     void* stream) {
+    RELNN_CHECK_ARG(p, "attention: null plan");
+    return attention_forward(p->p, prm, d_out, d_lse, (cudaStream_t)stream);
+}
+
+relnn_status relnn_attention_backward(relnn_plan_t p, const relnn_attn_params* prm, const float* d_fwd_out,
+                                      const float* d_lse, const float* d_dout, float* d_dq, float* d_dk, float* d_dv,
+                                      void* stream) {
+    RELNN_CHECK_ARG(p, "attention backward: null plan");
+    return attention_backward(p->p, prm, d_fwd_out, d_lse, d_dout, d_dq, d_dk, d_dv, (cudaStream_t)stream);
+}
+
 relnn_status relnn_plan_destroy(relnn_plan_t p) {
     if (!p) return RELNN_OK;
     cudaDeviceSynchronize();

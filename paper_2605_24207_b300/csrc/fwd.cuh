@@ -37,6 +37,11 @@ relnn_status forward_tc(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 // RELNN_FLAG_PUSHDOWN: the Linear once per H row, then per-tuple gathers and the SUM walk.
 relnn_status forward_pushdown(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 
+// Attention over the plan's tuples (relnn_attention_forward / _backward; attention.cu).
+relnn_status attention_forward(Plan& p, const relnn_attn_params* prm, float* out, float* lse, cudaStream_t st);
+relnn_status attention_backward(Plan& p, const relnn_attn_params* prm, const float* fout, const float* flse,
+                                const float* dout, float* dq, float* dk, float* dv, cudaStream_t st);
+
 // Adds the carried partials of tile-split segments into `out` (see file comment).
 relnn_status launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_tiles, const float* carry,
                           float* out, int d_out, bool accumulate, bool kahan, DevBuf& jobs_buf, cudaStream_t st);

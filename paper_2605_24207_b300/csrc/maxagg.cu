@@ -10,6 +10,7 @@
 // earliest maximum wins as in a sequential walk. The backward reuses the ReLU-mask path: the winner
 // mask has bit o of tuple t set iff t = arg[seg_t][o].
 #include "maxagg.cuh"
+#include "segfix.cuh"
 
 #include <algorithm>
 
@@ -18,44 +19,6 @@ namespace relnn {
 namespace {
 
 constexpr int kLongPieces = 64;  // segments with more pieces go to the block-per-segment pass
-
-// Boundary b (1 <= b < n_tiles, tiles of `tile` rows) is the first boundary that cuts segment s:
-// returns true with s, the carry slot of s's piece in tile b - 1 and the last tile e whose first
-// row lies in s. Warp-collective (all lanes return the same).
-__device__ __forceinline__ bool first_cut(const int32_t* __restrict__ seg, int64_t m, int tile, int64_t b, int lane,
-                                          int& s, int& first_slot, int64_t& e) {
-    const int64_t row = b * tile;  // < m
-    int v = -1;
-    if (lane == 0) v = seg[row];
-    else if (lane == 1) v = seg[row - 1];
-    else if (lane == 2) v = seg[(b - 1) * tile];
-    else if (lane == 3 && b >= 2) v = seg[(b - 1) * tile - 1];
-    else if (lane == 4 && row + tile < m) v = seg[row + tile];
-    s = __shfl_sync(0xffffffffu, v, 0);
-    if (__shfl_sync(0xffffffffu, v, 1) != s) return false;          // b cuts no segment
-    if (b >= 2 && __shfl_sync(0xffffffffu, v, 3) == s) return false;  // s was cut before b
-    first_slot = __shfl_sync(0xffffffffu, v, 2) == s ? 0 : 1;
-    e = b;
-    if (__shfl_sync(0xffffffffu, v, 4) == s) {  // s reaches past tile b: find its last row
-        int64_t last = 0;
-        if (lane == 0) {
-            int64_t lo = row + tile, hi = m;
-            while (lo + 1 < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (seg[mid] == s) lo = mid;
-                else hi = mid;
-            }
-            last = lo;
-        }
-        e = __shfl_sync(0xffffffffu, last, 0) / tile;
-    }
-    return true;
-}
-
-// piece i of the segment first cut at b: 0 = its piece in tile b - 1, i >= 1 = slot 0 of tile b + i - 1
-__device__ __forceinline__ int64_t piece_slot(int64_t b, int first_slot, int64_t i) {
-    return i == 0 ? (b - 1) * 2 + first_slot : (b + i - 1) * 2;
-}
 
 __device__ __forceinline__ void max_take(float& v, int& p, float x, int xp) {
     const bool t = x > v;

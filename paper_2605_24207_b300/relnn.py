@@ -77,6 +77,14 @@ class RuleDesc(C.Structure):
                 ("act", C.c_int), ("flags", C.c_uint32)]
 
 
+ATTN_SOFTMAX, ATTN_PRODUCT = 0, 1
+
+
+class AttnParams(C.Structure):
+    _fields_ = [("d_q", C.c_void_p), ("d_k", C.c_void_p), ("d_v", C.c_void_p), ("dtype", C.c_int), ("d", C.c_int32),
+                ("d_val", C.c_int32), ("n_heads", C.c_int32), ("scale", C.c_float), ("mode", C.c_int32)]
+
+
 class StreamDesc(C.Structure):
     _fields_ = [("key_type", C.c_int), ("d_h_ids", C.c_void_p), ("n_h", C.c_int64), ("d", C.c_int32),
                 ("d_out", C.c_int32), ("act", C.c_int), ("flags", C.c_uint32), ("h_src", C.c_void_p),
@@ -128,6 +136,10 @@ def lib():
     L.relnn_rule_forward_noalloc.restype = C.c_int
     L.relnn_mse_loss.argtypes = [vp, vp, i64, vp, vp, i64, C.c_int32, C.c_int, vp, vp, vp]
     L.relnn_mse_loss.restype = C.c_int
+    L.relnn_attention_forward.argtypes = [vp, C.POINTER(AttnParams), vp, vp, vp]
+    L.relnn_attention_backward.argtypes = [vp, C.POINTER(AttnParams), vp, vp, vp, vp, vp, vp, vp]
+    L.relnn_attention_forward.restype = C.c_int
+    L.relnn_attention_backward.restype = C.c_int
     L.relnn_stream_create.argtypes = [C.POINTER(StreamDesc), vp, C.POINTER(vp)]
     L.relnn_stream_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     L.relnn_stream_forward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, C.POINTER(i64), vp]
@@ -307,6 +319,31 @@ class RulePlan:
         keep = (Ws, bs, rs)
         prm = RuleParams(_ptr(z), _float_type(z), rs, r_dt, Ws, w_dt, bs)
         return prm, keep
+
+    @staticmethod
+    def _attn(q, k, v, n_heads, scale, mode):
+        return AttnParams(_ptr(q), _ptr(k), _ptr(v), _float_type(q), q.shape[1], v.shape[1], n_heads, float(scale),
+                          {"softmax": ATTN_SOFTMAX, "product": ATTN_PRODUCT}[mode])
+
+    def attention(self, q, k, v, n_heads: int = 1, scale: float = 1.0, mode: str = "softmax", stream=None):
+        """relnn_attention_forward: (Out [n_out, d] f32, log-sum-exp [n_out, n_heads] or None). q is read at
+        each tuple's dst H row, k and v at its src H row."""
+        out = torch.empty((max(self.n_out, 1), v.shape[1]), dtype=torch.float32, device=self.device)
+        lse = torch.empty((max(self.n_out, 1), n_heads), dtype=torch.float32, device=self.device) \
+            if mode == "softmax" else None
+        prm = self._attn(q, k, v, n_heads, scale, mode)
+        _check(lib().relnn_attention_forward(self._h, C.byref(prm), _ptr(out), _ptr(lse), _stream(stream)))
+        return out[: self.n_out], (lse[: self.n_out] if lse is not None else None)
+
+    def attention_backward(self, dout, out, lse, q, k, v, n_heads: int = 1, scale: float = 1.0,
+                           mode: str = "softmax", stream=None):
+        """relnn_attention_backward: (dq, dk, dv) [n_h, d] f32."""
+        dq, dk, dv = (torch.empty(x.shape, dtype=torch.float32, device=self.device) for x in (q, k, v))
+        prm = self._attn(q, k, v, n_heads, scale, mode)
+        dout = dout.contiguous()
+        _check(lib().relnn_attention_backward(self._h, C.byref(prm), _ptr(out), _ptr(lse), _ptr(dout), _ptr(dq),
+                                              _ptr(dk), _ptr(dv), _stream(stream)))
+        return dq, dk, dv
 
     def forward(self, z, W=None, b=None, r=None, out=None, stream=None) -> torch.Tensor:
         """Output embeddings [n_out, d_out] f32 (rows in out_keys() order)."""
