@@ -227,6 +227,19 @@ class C2:
         host_keys = torch.cat([src_h, dst_h]).pin_memory()
         ms_cp = timer(lambda: dev_keys.copy_(host_keys, non_blocking=True), 3)
         del stm, dev_keys, host_keys
+        # attention over the same join (HGT softmax head, 8 heads, bf16 rows q = k = v = z; product head)
+        zq = t["z"] if t["z"].dtype == torch.bfloat16 else t["z"].to(torch.bfloat16)
+        sc = 1.0 / (self.d // 8) ** 0.5
+        ms_at = timer(lambda: p.attention(zq, zq, zq, 8, sc, "softmax"), max(3, steps))
+        ao, al = p.attention(zq, zq, zq, 8, sc, "softmax")
+        dd = torch.ones_like(ao)
+        ms_atb = timer(lambda: p.attention_backward(dd, ao, al, zq, zq, zq, 8, sc, "softmax"), 3)
+        ms_ap = timer(lambda: p.attention(zq, zq, zq, 1, 1.0, "product"), max(3, steps))
+        del ao, al, dd
+        # algorithmic bytes of the softmax forward: 3 index arrays per tuple, q / k / v rows once,
+        # the output rows and their log-sum-exp once
+        n_h = t["h"].numel()
+        at_bytes = 12 * self.matched + 3 * n_h * self.d * 2 + self.n_out * (self.d + 8) * 4
         return {"warm_forward_tuples_per_s": self.matched / (ms_f * 1e-3), "warm_forward_ms": ms_f,
                 "warm_fwd_bwd_tuples_per_s": self.matched / (ms_fb * 1e-3), "warm_fwd_bwd_ms": ms_fb,
                 "pushdown_warm_forward": {"tuples_per_s": self.matched / (ms_pd * 1e-3), "ms": ms_pd,
@@ -237,6 +250,13 @@ class C2:
                                    "what": "relnn_stream_forward: E keys in pinned host memory, 4 chunks, each "
                                            "planned against the shared H side and evaluated while the next is "
                                            "copied; h2d_copy_ms is one plain pinned copy of the same key bytes"},
+                "attention": {"softmax_forward_ms": ms_at, "softmax_forward_tuples_per_s": self.matched / (ms_at * 1e-3),
+                              "softmax_backward_ms": ms_atb, "product_forward_ms": ms_ap,
+                              "softmax_forward_algorithmic_bytes": at_bytes,
+                              "softmax_forward_gbs": at_bytes / (ms_at * 1e-3) / 1e9,
+                              "what": "relnn_attention_* on this join: HGT softmax head (8 heads of 16, bf16 "
+                                      "q = k = v = z) and the product head; bytes = indices + q, k, v rows once "
+                                      "+ output rows and log-sum-exp"},
                 "max_warm_forward": {"tuples_per_s": self.matched / (ms_mx * 1e-3), "ms": ms_mx,
                                      "what": "RELNN_FLAG_MAX: the same fused forward with a MAX group-by (per-feature "
                                              "maximum and the position of its first tuple, kept for the backward)"},
