@@ -24,6 +24,8 @@ Definitions followed (paper sections):
     Attention(p; sum(a*v)) :- Score(p, t; a), V(t; v) (element-wise product head), and the
     HGT head: per head, softmax over t of the scaled dot product q . k, then the weighted
     sum of v                                                                          -- Sec. 1, Sec. 5 (HGT)
+  * cyclic self-join (DHN triangle homomorphisms): Out(n; sum(a_n * b_v * c_w)) :-
+    E(n, v), E(v, w), E(w, n), H(n; a), H(v; b), H(w; c), element-wise products      -- Sec. 5 (DHN)
 
 Readings where the paper is silent (each is listed with its reason in the design notes):
   * bag semantics: every E row is a distinct tuple, duplicate H keys each match;
@@ -46,7 +48,7 @@ __all__ = [
     "max_tie_order", "selected_rows",
     "selected_join",
     "rule_forward", "rule_backward", "mse", "mse_grad", "stacked_forward", "stacked_backward",
-    "attention_forward", "attention_backward",
+    "attention_forward", "attention_backward", "triangle_forward", "triangle_backward",
 ]
 
 CHUNK = 1 << 20  # join triples processed per NumPy block in the Linear/SUM steps
@@ -488,3 +490,60 @@ def attention_backward(h_ids, q, k, v, src, dst, dout, n_heads=1, scale=1.0, mod
     np.add.at(dq, hd, dsf * k[hs])
     np.add.at(dk, hs, dsf * q[hd])
     return dq, dk, dv
+
+
+# ----------------------------------------------------------------------------- triangle (cyclic) join
+def triangle_matches(h_ids, src, dst):
+    """All matches of E(n, v), E(v, w), E(w, n) joined with H on n, v and w (bag semantics: every E
+    row is a tuple and every H row of a key matches). Returns int64 arrays (n_key, row_n, row_v,
+    row_w), one entry per match, ordered by the three E rows (e1, e2, e3) then the H rows."""
+    idx = key_index(h_ids)
+    src = np.asarray(src).tolist()
+    dst = np.asarray(dst).tolist()
+    out_of: dict = {}
+    for e, (a, b) in enumerate(zip(src, dst)):
+        out_of.setdefault(a, []).append(e)
+    keys, rn, rv, rw = [], [], [], []
+    for e1, (n, v) in enumerate(zip(src, dst)):
+        if n not in idx or v not in idx:
+            continue
+        for e2 in out_of.get(v, []):
+            w = dst[e2]
+            if w not in idx:
+                continue
+            for e3 in out_of.get(w, []):
+                if dst[e3] != n:
+                    continue
+                for a in idx[n]:
+                    for b in idx[v]:
+                        for c in idx[w]:
+                            keys.append(n)
+                            rn.append(a)
+                            rv.append(b)
+                            rw.append(c)
+    return (np.asarray(keys, np.int64), np.asarray(rn, np.int64), np.asarray(rv, np.int64),
+            np.asarray(rw, np.int64))
+
+
+def triangle_forward(h_ids, a, b, c, src, dst):
+    """Out(n; sum(a_n * b_v * c_w)) over the triangle matches, grouped by the key of n (ascending;
+    only keys with at least one match). Returns (keys, Out [n_out, d]) in float64."""
+    a, b, c = (np.asarray(x, np.float64) for x in (a, b, c))
+    keys, rn, rv, rw = triangle_matches(h_ids, src, dst)
+    uk, inv = np.unique(keys, return_inverse=True)
+    out = np.zeros((uk.size, a.shape[1]))
+    np.add.at(out, inv.reshape(-1), a[rn] * b[rv] * c[rw])
+    return uk.astype(np.asarray(h_ids).dtype), out
+
+
+def triangle_backward(h_ids, a, b, c, src, dst, dout):
+    """Gradients (da, db, dc) of sum(dout * Out) for ``triangle_forward`` (dout rows in its key order)."""
+    a, b, c = (np.asarray(x, np.float64) for x in (a, b, c))
+    keys, rn, rv, rw = triangle_matches(h_ids, src, dst)
+    uk, inv = np.unique(keys, return_inverse=True)
+    G = np.asarray(dout, np.float64)[inv.reshape(-1)]
+    da, db, dc = np.zeros_like(a), np.zeros_like(b), np.zeros_like(c)
+    np.add.at(da, rn, G * b[rv] * c[rw])
+    np.add.at(db, rv, G * a[rn] * c[rw])
+    np.add.at(dc, rw, G * a[rn] * b[rv])
+    return da, db, dc

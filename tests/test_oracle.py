@@ -747,3 +747,96 @@ def test_attention_backward_finite_differences(mode, heads):
             lm = loss()
             arr[i] = old
             assert (lp - lm) / (2 * h) == pytest.approx(grad[i], rel=1e-6, abs=1e-7)
+
+
+# ----------------------------------------------------------------------------- triangle (cyclic) join
+def _tri_case(seed, n_keys=9, n_e=40, n_h=11, d=3):
+    rng = np.random.default_rng(seed)
+    h_ids = rng.integers(0, n_keys, size=n_h)  # duplicate keys and keys without a row
+    src = rng.integers(0, n_keys + 1, size=n_e)
+    dst = rng.integers(0, n_keys + 1, size=n_e)
+    a, b, c = (rng.standard_normal((n_h, d)) for _ in range(3))
+    return h_ids, a, b, c, src, dst
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_triangle_matches_brute_force_over_edge_triples(seed):
+    """Explicit loops over all E x E x E triples and the H rows of their three keys."""
+    h_ids, a, b, c, src, dst = _tri_case(300 + seed)
+    acc = {}
+    E = list(zip(src.tolist(), dst.tolist()))
+    for (n, v) in E:
+        for (v2, w) in E:
+            if v2 != v:
+                continue
+            for (w2, n2) in E:
+                if w2 != w or n2 != n:
+                    continue
+                for ra in range(len(h_ids)):
+                    if h_ids[ra] != n:
+                        continue
+                    for rb in range(len(h_ids)):
+                        if h_ids[rb] != v:
+                            continue
+                        for rc in range(len(h_ids)):
+                            if h_ids[rc] != w:
+                                continue
+                            acc[n] = acc.get(n, 0) + a[ra] * b[rb] * c[rc]
+    keys, out = O.triangle_forward(h_ids, a, b, c, src, dst)
+    assert list(keys) == sorted(acc)
+    np.testing.assert_allclose(out, np.array([acc[k] for k in sorted(acc)]).reshape(out.shape), rtol=1e-12,
+                               atol=1e-12)
+
+
+def test_triangle_closed_form_diag_of_matrix_products():
+    """With unique H keys 0..K-1, feature f of Out[n] is a_n * (M D_b M D_c M)[n][n], where M is
+    the edge multiplicity matrix and D_x = diag(x[:, f]): a closed form independent of the walk."""
+    rng = np.random.default_rng(11)
+    K = 12
+    h_ids = np.arange(K)
+    src, dst = rng.integers(0, K, size=70), rng.integers(0, K, size=70)
+    a, b, c = (rng.standard_normal((K, 2)) for _ in range(3))
+    M = np.zeros((K, K))
+    np.add.at(M, (src, dst), 1.0)
+    keys, out = O.triangle_forward(h_ids, a, b, c, src, dst)
+    for f in range(2):
+        diag = np.diag(M @ np.diag(b[:, f]) @ M @ np.diag(c[:, f]) @ M) * a[:, f]
+        nz = np.nonzero(np.diag(M @ M @ M))[0]
+        np.testing.assert_allclose(out[:, f], diag[keys], rtol=1e-12, atol=1e-12)
+        assert set(keys.tolist()) == set(nz.tolist())
+
+
+def test_triangle_counts_with_unit_embeddings():
+    """a = b = c = 1, d = 1: Out[n] counts the closed directed 3-walks from n, edge multiplicities
+    multiplying. Hand graph: the 3-cycle 0->1->2->0 with the edge 1->2 doubled gives 2 matches at
+    each of 0, 1 and 2 (either copy of 1->2), and the self-loop 3->3 gives 1 match at 3."""
+    h_ids = np.arange(4)
+    src = np.array([0, 1, 1, 2, 3])
+    dst = np.array([1, 2, 2, 0, 3])
+    ones = np.ones((4, 1))
+    keys, out = O.triangle_forward(h_ids, ones, ones, ones, src, dst)
+    assert keys.tolist() == [0, 1, 2, 3]
+    assert out[:, 0].tolist() == [2.0, 2.0, 2.0, 1.0]
+
+
+def test_triangle_backward_finite_differences():
+    h_ids, a, b, c, src, dst = _tri_case(320, n_e=50)
+    keys, out = O.triangle_forward(h_ids, a, b, c, src, dst)
+    C = np.random.default_rng(2).standard_normal(out.shape)
+    da, db, dc = O.triangle_backward(h_ids, a, b, c, src, dst, C)
+    h = 1e-6
+
+    def loss():
+        return float(np.sum(O.triangle_forward(h_ids, a, b, c, src, dst)[1] * C))
+
+    rng = np.random.default_rng(3)
+    for arr, grad in ((a, da), (b, db), (c, dc)):
+        for _ in range(6):
+            i = tuple(rng.integers(0, s) for s in arr.shape)
+            old = arr[i]
+            arr[i] = old + h
+            lp = loss()
+            arr[i] = old - h
+            lm = loss()
+            arr[i] = old
+            assert (lp - lm) / (2 * h) == pytest.approx(grad[i], rel=1e-6, abs=1e-7)
