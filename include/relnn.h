@@ -90,6 +90,7 @@ typedef struct relnn_join_s* relnn_join_t;
 typedef struct relnn_plan_s* relnn_plan_t;
 typedef struct relnn_server_s* relnn_server_t;
 typedef struct relnn_stream_s* relnn_stream_t;
+typedef struct relnn_tri_s* relnn_tri_t;
 
 /* ---------------------------------------------------------------------------------------------
  * Library
@@ -329,6 +330,42 @@ relnn_status relnn_serve_poll(relnn_server_t s, uint64_t ticket, relnn_result* r
 relnn_status relnn_serve_release(relnn_server_t s, uint64_t ticket);
 /* Stops accepting queries, finishes the queued ones, joins the workers and frees everything. */
 relnn_status relnn_server_destroy(relnn_server_t s);
+
+/* ---------------------------------------------------------------------------------------------
+ * Cyclic self-join (paper Sec. 5, DHN: a triangle homomorphism as a cyclic join over an edge
+ * relation, the per-position transformations Mu applied to the node embeddings beforehand):
+ *     Out(n; sum(a_n * b_v * c_w)) :- E(n, v), E(v, w), E(w, n), H(n; a), H(v; b), H(w; c)
+ * with element-wise products and bag semantics (every E row is a tuple, every H row of a key
+ * matches; edges with a key outside H are dropped). Output keys: the n with at least one match,
+ * ascending. The plan intersects sorted adjacency lists per edge (a worst-case-optimal join).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct relnn_tri_desc {
+    relnn_key_t key_type;   /* type of H.id, E.src, E.dst                                           */
+    const void* d_h_ids;    /* [n_h] (device)                                                       */
+    int64_t n_h;
+    const void* d_src;      /* [n_edges] E.src = n of E(n, v) (device)                              */
+    const void* d_dst;      /* [n_edges] E.dst                                                      */
+    int64_t n_edges;        /* < 2^31                                                               */
+} relnn_tri_desc;
+
+/* sync. Builds the cached match records (n, v, w, multiplicity) grouped by n. Errors: EINVAL,
+ * ENOMEM, ENOTSUP (2^31 records or more), EDEVICE (a multiplicity above 2^31). */
+relnn_status relnn_triangle_plan(const relnn_tri_desc* desc, void* stream, relnn_tri_t* out);
+/* Output rows, match records (distinct (n, v, w)) and the edges kept by the join with H. */
+relnn_status relnn_triangle_info(relnn_tri_t t, int64_t* n_out, int64_t* n_records, int64_t* n_edges_kept);
+/* async. The output keys [n_out] (plan key type). */
+relnn_status relnn_triangle_out_keys(relnn_tri_t t, void* d_out_keys, void* stream);
+/* async. d_a, d_b, d_c [n_h, d] rows aligned with H (dtype f32 or bf16; d in {32, 64, 128, 256});
+ * d_out [n_out, d] f32 (16-byte aligned), fully overwritten. Deterministic. */
+relnn_status relnn_triangle_forward(relnn_tri_t t, const void* d_a, const void* d_b, const void* d_c,
+                                    relnn_float_t dtype, int32_t d, float* d_out, void* stream);
+/* async. Gradients of sum(d_dout * Out): d_da, d_db, d_dc [n_h, d] f32 OVERWRITTEN (each may be
+ * NULL). Contributions are added with f32 atomics. */
+relnn_status relnn_triangle_backward(relnn_tri_t t, const void* d_a, const void* d_b, const void* d_c,
+                                     relnn_float_t dtype, int32_t d, const float* d_dout, float* d_da,
+                                     float* d_db, float* d_dc, void* stream);
+/* Frees the plan (waits for the device first). */
+relnn_status relnn_triangle_destroy(relnn_tri_t t);
 
 /* ---------------------------------------------------------------------------------------------
  * Streaming a relation larger than device memory (paper Sec. 6, future work on scaling for memory:

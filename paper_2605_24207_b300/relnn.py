@@ -85,6 +85,11 @@ class AttnParams(C.Structure):
                 ("d_val", C.c_int32), ("n_heads", C.c_int32), ("scale", C.c_float), ("mode", C.c_int32)]
 
 
+class TriDesc(C.Structure):
+    _fields_ = [("key_type", C.c_int), ("d_h_ids", C.c_void_p), ("n_h", C.c_int64), ("d_src", C.c_void_p),
+                ("d_dst", C.c_void_p), ("n_edges", C.c_int64)]
+
+
 class StreamDesc(C.Structure):
     _fields_ = [("key_type", C.c_int), ("d_h_ids", C.c_void_p), ("n_h", C.c_int64), ("d", C.c_int32),
                 ("d_out", C.c_int32), ("act", C.c_int), ("flags", C.c_uint32), ("h_src", C.c_void_p),
@@ -140,6 +145,15 @@ def lib():
     L.relnn_attention_backward.argtypes = [vp, C.POINTER(AttnParams), vp, vp, vp, vp, vp, vp, vp]
     L.relnn_attention_forward.restype = C.c_int
     L.relnn_attention_backward.restype = C.c_int
+    L.relnn_triangle_plan.argtypes = [C.POINTER(TriDesc), vp, C.POINTER(vp)]
+    L.relnn_triangle_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    L.relnn_triangle_out_keys.argtypes = [vp, vp, vp]
+    L.relnn_triangle_forward.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int32, vp, vp]
+    L.relnn_triangle_backward.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int32, vp, vp, vp, vp, vp]
+    L.relnn_triangle_destroy.argtypes = [vp]
+    for name in ("relnn_triangle_plan", "relnn_triangle_info", "relnn_triangle_out_keys", "relnn_triangle_forward",
+                 "relnn_triangle_backward", "relnn_triangle_destroy"):
+        getattr(L, name).restype = C.c_int
     L.relnn_stream_create.argtypes = [C.POINTER(StreamDesc), vp, C.POINTER(vp)]
     L.relnn_stream_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     L.relnn_stream_forward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, C.POINTER(i64), vp]
@@ -374,6 +388,46 @@ class RulePlan:
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value and _LIB is not None:
             _LIB.relnn_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+
+class TrianglePlan:
+    """relnn_triangle_*: Out(n; sum(a_n * b_v * c_w)) :- E(n, v), E(v, w), E(w, n), H(n; a), H(v; b),
+    H(w; c) (the cyclic self-join of a triangle homomorphism), with cached match records."""
+
+    def __init__(self, h_ids: torch.Tensor, src: torch.Tensor, dst: torch.Tensor, stream=None):
+        self.kt = _key_type(h_ids)
+        self.key_dtype = h_ids.dtype
+        self.device = h_ids.device
+        assert src.dtype == self.key_dtype and dst.dtype == self.key_dtype
+        desc = TriDesc(self.kt, _ptr(h_ids), h_ids.numel(), _ptr(src), _ptr(dst), src.numel())
+        self._h = C.c_void_p()
+        _check(lib().relnn_triangle_plan(C.byref(desc), _stream(stream), C.byref(self._h)))
+        n_out, n_rec, n_kept = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().relnn_triangle_info(self._h, C.byref(n_out), C.byref(n_rec), C.byref(n_kept)))
+        self.n_out, self.n_records, self.n_edges_kept = n_out.value, n_rec.value, n_kept.value
+
+    def out_keys(self, stream=None) -> torch.Tensor:
+        k = torch.empty(max(self.n_out, 1), dtype=self.key_dtype, device=self.device)
+        _check(lib().relnn_triangle_out_keys(self._h, _ptr(k), _stream(stream)))
+        return k[: self.n_out]
+
+    def forward(self, a, b, c, stream=None) -> torch.Tensor:
+        out = torch.empty((max(self.n_out, 1), a.shape[1]), dtype=torch.float32, device=self.device)
+        _check(lib().relnn_triangle_forward(self._h, _ptr(a), _ptr(b), _ptr(c), _float_type(a), a.shape[1],
+                                            _ptr(out), _stream(stream)))
+        return out[: self.n_out]
+
+    def backward(self, dout, a, b, c, stream=None):
+        da, db, dc = (torch.empty(x.shape, dtype=torch.float32, device=self.device) for x in (a, b, c))
+        dout = dout.contiguous()
+        _check(lib().relnn_triangle_backward(self._h, _ptr(a), _ptr(b), _ptr(c), _float_type(a), a.shape[1],
+                                             _ptr(dout), _ptr(da), _ptr(db), _ptr(dc), _stream(stream)))
+        return da, db, dc
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value and _LIB is not None:
+            _LIB.relnn_triangle_destroy(self._h)
             self._h = C.c_void_p()
 
 

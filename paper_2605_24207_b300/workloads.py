@@ -185,3 +185,36 @@ def serving_query(seed: int, q: int, n_tuples: int, d: int = 64):
     dst = draw_tuples(rng, int(n_tuples), keys)
     z = _normal(rng, (k, d), 1.0)
     return keys, src, dst, z
+
+
+def graph_batch(seed: int, n_graphs: int, n_nodes: int, d: int, near: int = 3, p_back: float = 0.5,
+                key_dtype=np.int32, dup_edges: float = 0.0, dup_rows: float = 0.0, missing: float = 0.0):
+    """A batch of small directed graphs for the cyclic (triangle) join: graph g's node i has key
+    g * n_nodes + i (keys in shuffled H order); every node points to its next `near` nodes on a ring
+    and each such edge is also present reversed with probability p_back, so short cycles close.
+    ``dup_edges`` repeats a fraction of the edges (bag semantics), ``dup_rows`` repeats H rows with
+    fresh embeddings, ``missing`` points a fraction of the edges at keys outside H. Returns
+    (h_ids, a, b, c, src, dst) with a, b, c f32 [n_h, d] (N(0, 1))."""
+    rng = rng_for(seed, 7)
+    g = np.repeat(np.arange(n_graphs, dtype=np.int64), n_nodes * near)
+    i = np.tile(np.repeat(np.arange(n_nodes, dtype=np.int64), near), n_graphs)
+    k = np.tile(np.arange(1, near + 1, dtype=np.int64), n_graphs * n_nodes)
+    j = (i + k) % n_nodes
+    src, dst = g * n_nodes + i, g * n_nodes + j
+    back = rng.random(src.size) < p_back
+    src = np.concatenate([src, dst[back]])
+    dst = np.concatenate([dst, (g * n_nodes + i)[back]])
+    if dup_edges > 0:
+        pick = rng.integers(0, src.size, size=int(src.size * dup_edges))
+        src, dst = np.concatenate([src, src[pick]]), np.concatenate([dst, dst[pick]])
+    if missing > 0:
+        m = rng.random(src.size) < missing
+        dst[m] = n_graphs * n_nodes + rng.integers(0, 1000, size=int(m.sum()))
+    perm = rng.permutation(src.size)
+    src, dst = src[perm], dst[perm]
+    h_ids = np.arange(n_graphs * n_nodes, dtype=np.int64)
+    if dup_rows > 0:
+        h_ids = np.concatenate([h_ids, rng.integers(0, h_ids.size, size=int(h_ids.size * dup_rows))])
+    h_ids = h_ids[rng.permutation(h_ids.size)]
+    a, b, c = (_normal(rng, (h_ids.size, d), 1.0) for _ in range(3))
+    return (h_ids.astype(key_dtype), a, b, c, src.astype(key_dtype), dst.astype(key_dtype))
