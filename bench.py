@@ -236,6 +236,32 @@ class C2:
         ms_atb = timer(lambda: p.attention_backward(dd, ao, al, zq, zq, zq, 8, sc, "softmax"), 3)
         ms_ap = timer(lambda: p.attention(zq, zq, zq, 1, 1.0, "product"), max(3, steps))
         del ao, al, dd
+        # cyclic self-join on a batch of small graphs (a separate synthetic workload): plan, forward,
+        # backward; the walk's algorithmic bytes are the records (16 B) + the B and C key rows once +
+        # the A rows and output rows once
+        from paper_2605_24207_b300 import workloads as WL
+        gh, ga, gb, gc, gs, gd = WL.graph_batch(11, 50_000, 32, 64)
+        dv = t["src"].device
+        th, ts, td = (torch.from_numpy(x).to(dv) for x in (gh, gs, gd))
+        tA, tB, tC = (torch.from_numpy(x).to(dv) for x in (ga, gb, gc))
+        tri_holder = {}
+
+        def tri_plan():
+            tri_holder["T"] = None
+            tri_holder["T"] = R.TrianglePlan(th, ts, td)
+        ms_tp = timer(tri_plan, 3)
+        T3 = tri_holder["T"]
+        ms_tf = timer(lambda: T3.forward(tA, tB, tC), max(3, steps))
+        to = T3.forward(tA, tB, tC)
+        ms_tb = timer(lambda: T3.backward(torch.ones_like(to), tA, tB, tC), 3)
+        tri_bytes = 16 * T3.n_records + 4 * 64 * (3 * gh.size + T3.n_out)
+        tri = {"edges": int(gs.size), "records": T3.n_records, "n_out": T3.n_out, "plan_ms": ms_tp,
+               "forward_ms": ms_tf, "backward_ms": ms_tb, "forward_algorithmic_bytes": tri_bytes,
+               "forward_gbs": tri_bytes / (ms_tf * 1e-3) / 1e9,
+               "what": "relnn_triangle_*: 50,000 ring graphs of 32 nodes (3 forward edges per node, each "
+                       "reversed with p 0.5), d = 64 f32; plan = join with H, two edge sorts, per-edge "
+                       "sorted-list intersection into records"}
+        del T3, tri_holder, to
         # algorithmic bytes of the softmax forward: 3 index arrays per tuple, q / k / v rows once,
         # the output rows and their log-sum-exp once
         n_h = t["h"].numel()
@@ -257,6 +283,7 @@ class C2:
                               "what": "relnn_attention_* on this join: HGT softmax head (8 heads of 16, bf16 "
                                       "q = k = v = z) and the product head; bytes = indices + q, k, v rows once "
                                       "+ output rows and log-sum-exp"},
+                "triangle": tri,
                 "max_warm_forward": {"tuples_per_s": self.matched / (ms_mx * 1e-3), "ms": ms_mx,
                                      "what": "RELNN_FLAG_MAX: the same fused forward with a MAX group-by (per-feature "
                                              "maximum and the position of its first tuple, kept for the backward)"},
