@@ -12,9 +12,11 @@
 // state as a boundary partial; the fix-up merges a row's partials in range order (rescaling by the
 // running maxima) and writes the row and its log-sum-exp, which the backward uses to rebuild a_t.
 //
-// Backward (atomics into dq, dk, dv): dv_t += a_t dOut_p, da_t = dOut_p . v_t, D_p = dOut_p . Out_p
-// (per head), ds_t = scale a_t (da_t - D_p), dk_t += ds_t q_p, dq_p += ds_t k_t (summed in registers
-// over a run of equal q rows); the product head's gradients are the three two-factor products.
+// Backward: dv_t += a_t dOut_p, da_t = dOut_p . v_t, D_p = dOut_p . Out_p (per head), ds_t =
+// scale a_t (da_t - D_p), dk_t += ds_t q_p, dq_p += ds_t k_t; the product head's gradients are the
+// three two-factor products. Two walks: in output order dq is summed over runs of equal q rows; in
+// src order (the plan's cached permutation) dk and dv are summed over runs of equal k / v rows, so
+// each run, not each tuple, adds into the gradients.
 #include "fwd.cuh"
 #include "segfix.cuh"
 
@@ -48,6 +50,10 @@ struct AttnArgs {
     const float* flse;     // forward log-sum-exp (softmax)
     const float* dout;
     float *dq, *dk, *dv;
+    // src pass: the same tuples in src order (k and v rows non-decreasing), their q rows and
+    // output rows, and D[p][h] = dOut_p . Out_p per head
+    const int32_t *k_src, *q_src, *seg_src;
+    const float* Dh;
 };
 
 // F consecutive elements of row `row` starting at column c (bf16 or f32), as f32.
@@ -349,6 +355,113 @@ __global__ void __launch_bounds__(256) attn_bwd_kernel(AttnArgs a) {
     }
 }
 
+// D[p][h] = dOut_p . Out_p over head h's features (one warp per output row).
+template <int F>
+__global__ void attn_dterm_kernel(AttnArgs a, int64_t n_out, float* D) {
+    const int lane = threadIdx.x & 31;
+    const int c0 = lane * F, head = lane / a.lph;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_out; p += nw) {
+        float g[F], o[F];
+        load_f<F, false>(a.dout, p, a.d, c0, g);
+        load_f<F, false>(a.fout, p, a.d, c0, o);
+        float x = 0.f;
+#pragma unroll
+        for (int i = 0; i < F; ++i) x = fmaf(g[i], o[i], x);
+        x = head_sum(x, a.lph);
+        if (lane % a.lph == 0) D[p * a.n_heads + head] = x;
+    }
+}
+
+__global__ void gather_rows_kernel(const int32_t* idx, const int32_t* perm, int64_t m, int32_t* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = idx[perm[i]];
+}
+
+// Backward, src pass: the tuples in src order, so a k / v row stays in registers over its run and
+// dk, dv receive one atomic add per run; per tuple the q row, the dOut row and (softmax) the row's
+// log-sum-exp and D are gathered.
+template <int F, bool BF16, int MODE>
+__global__ void __launch_bounds__(256) attn_bwd_src_kernel(AttnArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const int64_t span = (int64_t)a.range_tiles * 32;
+    const int c0 = lane * F, head = lane / a.lph;
+    for (int64_t rg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; rg < a.n_ranges; rg += warps_total) {
+        const int64_t r0 = rg * span, r1 = imin64(a.m, r0 + span);
+        int curk = -1;
+        float kf[F], vf[F], dka[F], dva[F];
+#pragma unroll
+        for (int i = 0; i < F; ++i) kf[i] = vf[i] = dka[i] = dva[i] = 0.f;
+        auto flush = [&]() {
+            if (curk >= 0) {
+                if (a.dk) atomic_add_f<F>(a.dk + (int64_t)curk * a.d + c0, dka);
+                if (a.dv) atomic_add_f<F>(a.dv + (int64_t)curk * a.d + c0, dva);
+            }
+#pragma unroll
+            for (int i = 0; i < F; ++i) dka[i] = dva[i] = 0.f;
+        };
+        for (int64_t b0 = r0; b0 < r1; b0 += 32) {
+            const int nb = (int)imin64(32, r1 - b0);
+            const bool tv = lane < nb;
+            const int sv = tv ? a.seg_src[b0 + lane] : 0;
+            const int kv = tv ? a.k_src[b0 + lane] : 0;
+            const int qv = tv ? a.q_src[b0 + lane] : 0;
+            for (int j0 = 0; j0 < nb; j0 += 4) {
+                float qf[4][F], gf[4][F], Lj[4], Dj[4];
+                int kj[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u < nb ? j0 + u : nb - 1;
+                    const int sj = __shfl_sync(0xffffffffu, sv, j);
+                    kj[u] = __shfl_sync(0xffffffffu, kv, j);
+                    load_f<F, BF16>(a.q, __shfl_sync(0xffffffffu, qv, j), a.d, c0, qf[u]);
+                    load_f<F, false>(a.dout, sj, a.d, c0, gf[u]);
+                    if (MODE == kSoftmax) {
+                        Lj[u] = __ldg(a.flse + (int64_t)sj * a.n_heads + head);
+                        Dj[u] = __ldg(a.Dh + (int64_t)sj * a.n_heads + head);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (j0 + u >= nb) break;
+                    if (kj[u] != curk) {
+                        flush();
+                        curk = kj[u];
+                        load_f<F, BF16>(a.k, curk, a.d, c0, kf);
+                        load_f<F, BF16>(a.v, curk, a.d, c0, vf);
+                    }
+                    if (MODE == kProduct) {
+#pragma unroll
+                        for (int i = 0; i < F; ++i) {
+                            const float gq = gf[u][i] * qf[u][i];
+                            dva[i] = fmaf(gq, kf[i], dva[i]);
+                            dka[i] = fmaf(gq, vf[i], dka[i]);
+                        }
+                    } else {
+                        float p = 0.f, pv = 0.f;
+#pragma unroll
+                        for (int i = 0; i < F; ++i) {
+                            p = fmaf(qf[u][i], kf[i], p);
+                            pv = fmaf(gf[u][i], vf[i], pv);
+                        }
+                        const float sc = head_sum(p, a.lph) * a.scale;
+                        const float da = head_sum(pv, a.lph);
+                        const float at = __expf(sc - Lj[u]);
+                        const float ds = at * (da - Dj[u]) * a.scale;
+#pragma unroll
+                        for (int i = 0; i < F; ++i) {
+                            dva[i] = fmaf(at, gf[u][i], dva[i]);
+                            dka[i] = fmaf(ds, qf[u][i], dka[i]);
+                        }
+                    }
+                }
+            }
+        }
+        flush();
+    }
+}
+
 template <class K>
 void range_launch(K kern, AttnArgs& a, cudaStream_t st, int& bps_cache) {
     if (bps_cache <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_cache, kern, 256, 0) != cudaSuccess) {
@@ -398,18 +511,58 @@ relnn_status attn_forward_t(Plan& p, AttnArgs& a, int mode, cudaStream_t st) {
     return RELNN_OK;
 }
 
+// Two walks: the dst pass (output order) sums dq over runs of equal q rows; the src pass (src order)
+// sums dk and dv over runs of equal k / v rows, so no per-tuple atomics remain.
 template <int F, bool BF16>
-relnn_status attn_backward_t(AttnArgs& a, int mode, cudaStream_t st) {
-    static int bps[2] = {0, 0};
-    ProfToken pt = prof_begin(RELNN_PROF_BWD_FP32, st);
-    if (mode == kSoftmax) {
-        range_launch(attn_bwd_kernel<F, BF16, kSoftmax>, a, st, bps[0]);
-        attn_bwd_kernel<F, BF16, kSoftmax><<<(int)std::min<int64_t>(ceil_div(a.n_ranges, 8), num_sms() * 8), 256, 0, st>>>(a);
-    } else {
-        range_launch(attn_bwd_kernel<F, BF16, kProduct>, a, st, bps[1]);
-        attn_bwd_kernel<F, BF16, kProduct><<<(int)std::min<int64_t>(ceil_div(a.n_ranges, 8), num_sms() * 8), 256, 0, st>>>(a);
+relnn_status attn_backward_t(Plan& p, AttnArgs& a, int mode, cudaStream_t st) {
+    static int bps[4] = {0, 0, 0, 0};
+    const int cap = num_sms() * 8;
+    BranchPlan& b = p.br[0];
+    const bool need_kv = a.dk || a.dv;
+    float* dk = a.dk;
+    float* dv = a.dv;
+    if (need_kv) {
+        RELNN_TRY(ensure_src_order(p, b, st));
+        const size_t dbytes = mode == kSoftmax ? sizeof(float) * (size_t)p.n_out * a.n_heads : 0;
+        RELNN_TRY(p.scratch.alloc(sizeof(int32_t) * (size_t)b.m + dbytes + 256));
+        int32_t* q_src = p.scratch.as<int32_t>();
+        { gather_rows_kernel<<<(int)std::min<int64_t>(ceil_div(b.m, 256), cap), 256, 0, st>>>(
+              b.hd.as<int32_t>(), b.src_perm.as<int32_t>(), b.m, q_src); note_launch(); }
+        a.q_src = q_src;
+        a.k_src = b.hs_src.as<int32_t>();
+        a.seg_src = b.seg_src.as<int32_t>();
+        if (mode == kSoftmax) {
+            float* D = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + ((sizeof(int32_t) * (size_t)b.m + 255) & ~(size_t)255));
+            { attn_dterm_kernel<F><<<(int)std::min<int64_t>(ceil_div(p.n_out, 8), cap), 256, 0, st>>>(a, p.n_out, D); note_launch(); }
+            a.Dh = D;
+        }
     }
-    note_launch();
+    ProfToken pt = prof_begin(RELNN_PROF_BWD_FP32, st);
+    // dst pass: dq only
+    a.dk = a.dv = nullptr;
+    if (a.dq) {
+        if (mode == kSoftmax) {
+            range_launch(attn_bwd_kernel<F, BF16, kSoftmax>, a, st, bps[0]);
+            attn_bwd_kernel<F, BF16, kSoftmax><<<(int)std::min<int64_t>(ceil_div(a.n_ranges, 8), cap), 256, 0, st>>>(a);
+        } else {
+            range_launch(attn_bwd_kernel<F, BF16, kProduct>, a, st, bps[1]);
+            attn_bwd_kernel<F, BF16, kProduct><<<(int)std::min<int64_t>(ceil_div(a.n_ranges, 8), cap), 256, 0, st>>>(a);
+        }
+        note_launch();
+    }
+    // src pass: dk, dv
+    a.dk = dk;
+    a.dv = dv;
+    if (need_kv) {
+        if (mode == kSoftmax) {
+            range_launch(attn_bwd_src_kernel<F, BF16, kSoftmax>, a, st, bps[2]);
+            attn_bwd_src_kernel<F, BF16, kSoftmax><<<(int)std::min<int64_t>(ceil_div(a.n_ranges, 8), cap), 256, 0, st>>>(a);
+        } else {
+            range_launch(attn_bwd_src_kernel<F, BF16, kProduct>, a, st, bps[3]);
+            attn_bwd_src_kernel<F, BF16, kProduct><<<(int)std::min<int64_t>(ceil_div(a.n_ranges, 8), cap), 256, 0, st>>>(a);
+        }
+        note_launch();
+    }
     prof_end(pt, st);
     RELNN_CUDA(cudaGetLastError());
     return RELNN_OK;
@@ -459,12 +612,12 @@ relnn_status dispatch_fwd(Plan& p, AttnArgs& a, int mode, cudaStream_t st) {
 }
 
 template <bool BF16>
-relnn_status dispatch_bwd(AttnArgs& a, int mode, cudaStream_t st) {
+relnn_status dispatch_bwd(Plan& p, AttnArgs& a, int mode, cudaStream_t st) {
     switch (a.d / 32) {
-        case 1: return attn_backward_t<1, BF16>(a, mode, st);
-        case 2: return attn_backward_t<2, BF16>(a, mode, st);
-        case 4: return attn_backward_t<4, BF16>(a, mode, st);
-        default: return attn_backward_t<8, BF16>(a, mode, st);
+        case 1: return attn_backward_t<1, BF16>(p, a, mode, st);
+        case 2: return attn_backward_t<2, BF16>(p, a, mode, st);
+        case 4: return attn_backward_t<4, BF16>(p, a, mode, st);
+        default: return attn_backward_t<8, BF16>(p, a, mode, st);
     }
 }
 
@@ -500,7 +653,7 @@ relnn_status attention_backward(Plan& p, const relnn_attn_params* prm, const flo
     a.dq = dq;
     a.dk = dk;
     a.dv = dv;
-    return prm->dtype == RELNN_BF16 ? dispatch_bwd<true>(a, prm->mode, st) : dispatch_bwd<false>(a, prm->mode, st);
+    return prm->dtype == RELNN_BF16 ? dispatch_bwd<true>(p, a, prm->mode, st) : dispatch_bwd<false>(p, a, prm->mode, st);
 }
 
 }  // namespace relnn
