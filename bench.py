@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="tuples in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip warm / comparator extras")
+    ap.add_argument("--agg", default="sum", choices=["sum", "mean", "max"],
+                    help="c2: aggregator of the rule (extras only with sum)")
     return ap.parse_args()
 
 
@@ -143,12 +145,14 @@ class C2:
         from paper_2605_24207_b300 import workloads as W
         self.n_tuples = args.n_tuples or 16_000_000
         self.n_keys = args.n_keys or 1_000_000
+        self.agg = args.agg
         self.rel = W.config2(seed=0, n_tuples=self.n_tuples, n_keys=self.n_keys)
 
     def describe(self):
-        return (f"single rule H'(dst; SUM Linear(Concat(z_src, z_dst))), E {self.n_tuples} tuples over "
+        A = self.agg.upper()
+        return (f"single rule H'(dst; {A} Linear(Concat(z_src, z_dst))), E {self.n_tuples} tuples over "
                 f"{self.n_keys} int64 keys (src Zipf 1.1, dst uniform), z bf16[128], Linear 256->128 "
-                f"bf16/f32-acc, SUM by dst; step = plan (join build+probe+group) + fused forward")
+                f"bf16/f32-acc, {A} by dst; step = plan (join build+probe+group) + fused forward")
 
     def to_device(self, dev):
         import torch
@@ -158,7 +162,7 @@ class C2:
                       dst=torch.from_numpy(br.dst).to(dev), z=torch.from_numpy(rel.z).to(dev).to(torch.bfloat16),
                       W=torch.from_numpy(br.W).to(dev), b=torch.from_numpy(br.b).to(dev))
         self.d, self.d_out = rel.z.shape[1], br.W.shape[0]
-        self.flags = R.FLAG_BF16
+        self.flags = R.FLAG_BF16 | {"sum": 0, "mean": R.FLAG_MEAN, "max": R.FLAG_MAX}[self.agg]
         p = R.RulePlan(self.t["h"], [(self.t["src"], self.t["dst"])], self.d, self.d_out, flags=self.flags)
         self.matched, self.n_out = p.n_matched, p.n_out
         self.plan0 = p
@@ -199,6 +203,8 @@ class C2:
     def extras(self, timer, steps):
         """Warm forward (content cached), warm forward + backward, and the unfused FP32 torch form."""
         import torch
+        if self.agg != "sum":
+            return {}
         t, p = self.t, self.plan0
         fwd = lambda: p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
         ms_f = timer(fwd, max(3, steps))
@@ -319,7 +325,7 @@ class C2:
         ob = _Br(br.src[:n], br.dst[:n], _bf16(br.W), br.b)
         z = _bf16(self.rel.z)
         t0 = time.perf_counter()
-        _, _, sizes = O.rule_forward(self.rel.h_ids, z, [ob])
+        _, _, sizes = O.rule_forward(self.rel.h_ids, z, [ob], agg=self.agg)
         dt = time.perf_counter() - t0
         return sizes[0] / dt, f"first {n} of {self.n_tuples} E rows with the full H ({sizes[0]} matched tuples, {dt:.1f} s)"
 
