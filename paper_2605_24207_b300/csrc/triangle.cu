@@ -12,8 +12,10 @@
 // records come out grouped by n (edge order), so the output rows are a segmented sum.
 //
 // Because H rows of one key all match, the sum factorises per key: with A_k = sum of a over the
-// rows of key k (likewise B, C), Out[n] = A_n * sum over records of mult * B_v * C_w. The forward
-// folds a, b, c to key rows, walks the records (warp per range, lane = d / 32 features), multiplies a
+// rows of key k (likewise B, C), Out[n] = A_n * sum over records of mult * B_v * C_w. With unique H
+// keys (A_k is one row) the records name H rows and a, b, c are read in place; otherwise the forward
+// folds a, b, c to key rows first. It walks the records (warp per range, lane = d / 32 features, 4 records'
+// rows in flight), multiplies a
 // row's sum by A_n when it is emitted, and the SUM fix-up adds rows cut by range edges. The
 // backward walks the records again: dB_v += mult g * C_w, dC_w += mult g * B_v (g = dOut_n * A_n)
 // by f32 atomics, dA_n = dOut_n * (the row's sum); the key gradients are then broadcast to H rows.
@@ -34,7 +36,7 @@ struct relnn_tri_s {
     DevBuf fold;                             // f32 [3][U][d] key rows of a, b, c
     DevBuf gkey;                             // f32 [3][U][d] key-row gradients
     DevBuf carry, jobs, status;
-    int fold_d = 0;
+    bool direct = false;  // H keys unique: the records name H rows and a, b, c are read in place
 };
 
 namespace relnn {
@@ -138,6 +140,15 @@ __global__ void rec_seg_kernel(const int32_t* rn, int64_t r, const int32_t* out_
         seg[i] = out_row[rn[i]];
 }
 
+__global__ void uid_to_row_kernel(const int32_t* rows_sorted, const int32_t* run_start, int64_t r, int32_t* rn,
+                                  int32_t* rv, int32_t* rw) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < r; i += (int64_t)gridDim.x * blockDim.x) {
+        rn[i] = rows_sorted[run_start[rn[i]]];
+        rv[i] = rows_sorted[run_start[rv[i]]];
+        rw[i] = rows_sorted[run_start[rw[i]]];
+    }
+}
+
 __global__ void tri_keys_kernel(const int32_t* present, const int32_t* out_row, const int64_t* ukeys, int64_t U,
                                 int64_t* keys) {
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U; u += (int64_t)gridDim.x * blockDim.x)
@@ -179,7 +190,8 @@ __global__ void unfold_kernel(const float* G, const int32_t* rows_sorted, const 
 }
 
 struct TriArgs {
-    const float *A, *B, *C;        // key rows [U][d]
+    const void *A, *B, *C;         // rows of a, b, c: folded key rows (f32) or, with unique H keys, the
+                                   // caller's rows (the records then name H rows)
     const int32_t *rn, *rv, *rw, *rm, *seg;
     int64_t r;
     int d;
@@ -231,13 +243,47 @@ __device__ __forceinline__ void add4(float* p, const float (&x)[F]) {
     }
 }
 
+// F consecutive elements of a row of a, b or c, as f32.
+template <int F, bool BF16>
+__device__ __forceinline__ void ldrow(const void* base, int64_t row, int d, int c0, float (&x)[F]) {
+    if (!BF16) {
+        ld4<F>(reinterpret_cast<const float*>(base) + row * d + c0, x);
+        return;
+    }
+    const uint16_t* p = reinterpret_cast<const uint16_t*>(base) + row * d + c0;
+    if (F == 8) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = __uint_as_float(w[i] << 16);
+            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    } else if (F == 4) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+        x[0] = __uint_as_float(u.x << 16);
+        x[1] = __uint_as_float(u.x & 0xffff0000u);
+        x[2] = __uint_as_float(u.y << 16);
+        x[3] = __uint_as_float(u.y & 0xffff0000u);
+    } else if (F == 2) {
+        const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(p));
+        x[0] = __uint_as_float(u << 16);
+        x[1] = __uint_as_float(u & 0xffff0000u);
+    } else {
+        x[0] = __uint_as_float((uint32_t)__ldg(p) << 16);
+    }
+}
+
 __global__ void narrow_keys_kernel(const int64_t* k, int64_t n, int32_t* out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (int32_t)k[i];
 }
 
+// Records whose B and C rows are loaded before any is used.
+constexpr int kInFlight = 4;
+
 // Forward walk (BWD = false) or backward walk (BWD = true) over the records of a range.
-template <int F, bool BWD>
+template <int F, bool BWD, bool BF16>
 __global__ void __launch_bounds__(256) tri_walk_kernel(TriArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
@@ -279,22 +325,22 @@ __global__ void __launch_bounds__(256) tri_walk_kernel(TriArgs a) {
             const int vv = tv ? a.rv[b0 + lane] : 0;
             const int wv = tv ? a.rw[b0 + lane] : 0;
             const float mv = tv ? (float)a.rm[b0 + lane] : 0.f;
-            for (int j0 = 0; j0 < nb; j0 += 4) {
-                float bf[4][F], cf[4][F], mj[4];
-                int sj[4], nj[4], vj[4], wj[4];
+            for (int j0 = 0; j0 < nb; j0 += kInFlight) {
+                float bf[kInFlight][F], cf[kInFlight][F], mj[kInFlight];
+                int sj[kInFlight], nj[kInFlight], vj[kInFlight], wj[kInFlight];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kInFlight; ++u) {
                     const int j = j0 + u < nb ? j0 + u : nb - 1;
                     sj[u] = __shfl_sync(0xffffffffu, sv, j);
                     nj[u] = __shfl_sync(0xffffffffu, nv, j);
                     vj[u] = __shfl_sync(0xffffffffu, vv, j);
                     wj[u] = __shfl_sync(0xffffffffu, wv, j);
                     mj[u] = __shfl_sync(0xffffffffu, mv, j);
-                    ld4<F>(a.B + (int64_t)vj[u] * a.d + c0, bf[u]);
-                    ld4<F>(a.C + (int64_t)wj[u] * a.d + c0, cf[u]);
+                    ldrow<F, BF16>(a.B, vj[u], a.d, c0, bf[u]);
+                    ldrow<F, BF16>(a.C, wj[u], a.d, c0, cf[u]);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kInFlight; ++u) {
                     if (j0 + u >= nb) break;
                     if (sj[u] != cur) {
                         if (cur >= 0) flush(false);
@@ -303,11 +349,11 @@ __global__ void __launch_bounds__(256) tri_walk_kernel(TriArgs a) {
                         if (BWD) {
                             float dn[F];
                             ld4<F>(a.dout + (int64_t)cur * a.d + c0, dn);
-                            ld4<F>(a.A + (int64_t)curn * a.d + c0, an);
+                            ldrow<F, BF16>(a.A, curn, a.d, c0, an);
 #pragma unroll
                             for (int i = 0; i < F; ++i) g[i] = dn[i];
                         } else {
-                            ld4<F>(a.A + (int64_t)curn * a.d + c0, an);
+                            ldrow<F, BF16>(a.A, curn, a.d, c0, an);
                         }
                     }
                     if (BWD) {
@@ -332,10 +378,10 @@ __global__ void __launch_bounds__(256) tri_walk_kernel(TriArgs a) {
     }
 }
 
-template <int F>
+template <int F, bool BF16>
 void size_ranges(TriArgs& a) {
     static int bps = 0;
-    if (bps <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tri_walk_kernel<F, false>, 256, 0) != cudaSuccess) {
+    if (bps <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tri_walk_kernel<F, false, BF16>, 256, 0) != cudaSuccess) {
         (void)cudaGetLastError();
         bps = 1;
     }
@@ -345,30 +391,35 @@ void size_ranges(TriArgs& a) {
     a.n_ranges = ceil_div(n32, a.range_tiles);
 }
 
-template <int F>
+template <int F, bool BF16>
 relnn_status walk(relnn_tri_s* T, TriArgs& a, bool bwd, cudaStream_t st) {
-    size_ranges<F>(a);
+    size_ranges<F, BF16>(a);
     const int grid = (int)std::min<int64_t>(ceil_div(a.n_ranges, 8), (int64_t)num_sms() * 8);
     if (!bwd) {
         RELNN_TRY(T->carry.alloc(sizeof(float) * 2 * (size_t)a.d * a.n_ranges));
         a.carry = T->carry.as<float>();
-        { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); tri_walk_kernel<F, false><<<grid, 256, 0, st>>>(a); note_launch(); prof_end(pt, st); }
+        { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); tri_walk_kernel<F, false, BF16><<<grid, 256, 0, st>>>(a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
         RELNN_TRY(launch_fixup(a.seg, a.r, a.range_tiles * 32, a.n_ranges, a.carry, a.out, a.d, false, false, T->jobs, st));
     } else {
-        { ProfToken pt = prof_begin(RELNN_PROF_BWD_FP32, st); tri_walk_kernel<F, true><<<grid, 256, 0, st>>>(a); note_launch(); prof_end(pt, st); }
+        { ProfToken pt = prof_begin(RELNN_PROF_BWD_FP32, st); tri_walk_kernel<F, true, BF16><<<grid, 256, 0, st>>>(a); note_launch(); prof_end(pt, st); }
         RELNN_CUDA(cudaGetLastError());
     }
     return RELNN_OK;
 }
 
-relnn_status run_walk(relnn_tri_s* T, TriArgs& a, bool bwd, cudaStream_t st) {
+template <bool BF16>
+relnn_status run_walk_t(relnn_tri_s* T, TriArgs& a, bool bwd, cudaStream_t st) {
     switch (a.d / 32) {  // lane = F = d / 32 consecutive features
-        case 1: return walk<1>(T, a, bwd, st);
-        case 2: return walk<2>(T, a, bwd, st);
-        case 4: return walk<4>(T, a, bwd, st);
-        default: return walk<8>(T, a, bwd, st);
+        case 1: return walk<1, BF16>(T, a, bwd, st);
+        case 2: return walk<2, BF16>(T, a, bwd, st);
+        case 4: return walk<4, BF16>(T, a, bwd, st);
+        default: return walk<8, BF16>(T, a, bwd, st);
     }
+}
+
+relnn_status run_walk(relnn_tri_s* T, TriArgs& a, bool bwd, bool bf16_rows, cudaStream_t st) {
+    return bf16_rows ? run_walk_t<true>(T, a, bwd, st) : run_walk_t<false>(T, a, bwd, st);
 }
 
 relnn_status check_rows(relnn_tri_s* T, const void* a, const void* b, const void* c, relnn_float_t dtype, int d) {
@@ -376,6 +427,8 @@ relnn_status check_rows(relnn_tri_s* T, const void* a, const void* b, const void
     RELNN_CHECK_ARG(d == 32 || d == 64 || d == 128 || d == 256, "triangle: d in {32, 64, 128, 256}");
     RELNN_CHECK_ARG(dtype == RELNN_F32 || dtype == RELNN_BF16, "triangle: bad dtype");
     RELNN_CHECK_ARG(T->n_h == 0 || (a && b && c), "triangle: null rows");
+    RELNN_CHECK_ARG(((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c)) & 15u) == 0,
+                    "triangle: rows must be 16-byte aligned");
     return RELNN_OK;
 }
 
@@ -389,12 +442,20 @@ relnn_status fold_rows(relnn_tri_s* T, const void* a, const void* b, const void*
     return RELNN_OK;
 }
 
-TriArgs base_args(relnn_tri_s* T, int d) {
+// Rows the walk reads: the caller's (records name H rows when H's keys are unique) or the folded
+// key rows.
+TriArgs base_args(relnn_tri_s* T, int d, const void* a, const void* b, const void* c) {
     TriArgs t{};
-    const float* f = T->fold.as<float>();
-    t.A = f;
-    t.B = f + (size_t)T->U * d;
-    t.C = f + 2 * (size_t)T->U * d;
+    if (T->direct) {
+        t.A = a;
+        t.B = b;
+        t.C = c;
+    } else {
+        const float* f = T->fold.as<float>();
+        t.A = f;
+        t.B = f + (size_t)T->U * d;
+        t.C = f + 2 * (size_t)T->U * d;
+    }
     t.rn = T->rec_n.as<int32_t>();
     t.rv = T->rec_v.as<int32_t>();
     t.rw = T->rec_w.as<int32_t>();
@@ -544,6 +605,13 @@ relnn_status relnn_triangle_plan(const relnn_tri_desc* desc, void* stream, relnn
     { tri_keys_kernel<<<grid_of(U), 256, 0, st>>>(present.as<int32_t>(), orow.as<int32_t>(), T->H.ukeys.as<int64_t>(), U,
                                                   T->out_keys.as<int64_t>()); note_launch(); }
     if (R > 0) { rec_seg_kernel<<<grid_of(R), 256, 0, st>>>(T->rec_n.as<int32_t>(), R, orow.as<int32_t>(), T->seg.as<int32_t>()); note_launch(); }
+    // unique H keys: a key's rows are one row, so the records can name H rows and the forward reads
+    // a, b, c in place (no folding)
+    T->direct = (U == T->n_h);
+    if (T->direct && R > 0)
+        { uid_to_row_kernel<<<grid_of(R), 256, 0, st>>>(T->H.rows_sorted.as<int32_t>(), T->H.run_start.as<int32_t>(), R,
+                                                       T->rec_n.as<int32_t>(), T->rec_v.as<int32_t>(),
+                                                       T->rec_w.as<int32_t>()); note_launch(); }
     int dev_status = 0;
     TRI_CUDA(cudaMemcpyAsync(&dev_status, T->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     TRI_CUDA(cudaStreamSynchronize(st));
@@ -587,10 +655,10 @@ relnn_status relnn_triangle_forward(relnn_tri_t T, const void* d_a, const void* 
     if (T->n_out == 0) return RELNN_OK;
     RELNN_CHECK_ARG(d_out && (reinterpret_cast<uintptr_t>(d_out) & 15u) == 0, "triangle: null or unaligned output");
     cudaStream_t st = (cudaStream_t)stream;
-    RELNN_TRY(fold_rows(T, d_a, d_b, d_c, dtype, d, st));
-    TriArgs a = base_args(T, d);
+    if (!T->direct) RELNN_TRY(fold_rows(T, d_a, d_b, d_c, dtype, d, st));
+    TriArgs a = base_args(T, d, d_a, d_b, d_c);
     a.out = d_out;
-    return run_walk(T, a, false, st);
+    return run_walk(T, a, false, T->direct && dtype == RELNN_BF16, st);
 }
 
 relnn_status relnn_triangle_backward(relnn_tri_t T, const void* d_a, const void* d_b, const void* d_c, relnn_float_t dtype,
@@ -604,16 +672,37 @@ relnn_status relnn_triangle_backward(relnn_tri_t T, const void* d_a, const void*
         return RELNN_OK;
     }
     RELNN_CHECK_ARG(d_dout && (reinterpret_cast<uintptr_t>(d_dout) & 15u) == 0, "triangle: null or unaligned dOut");
+    if (T->direct) {
+        // the walk adds straight into the H-row gradients (scratch rows for the skipped ones)
+        RELNN_CHECK_ARG(((reinterpret_cast<uintptr_t>(d_da) | reinterpret_cast<uintptr_t>(d_db) |
+                          reinterpret_cast<uintptr_t>(d_dc)) & 15u) == 0, "triangle: gradients must be 16-byte aligned");
+        const int missing = (d_da ? 0 : 1) + (d_db ? 0 : 1) + (d_dc ? 0 : 1);
+        if (missing) RELNN_TRY(T->gkey.alloc(rows * missing));
+        float* spare = T->gkey.as<float>();
+        float* g[3] = {d_da, d_db, d_dc};
+        for (float*& x : g)
+            if (!x) {
+                x = spare;
+                spare += (size_t)T->n_h * d;
+            }
+        for (float* x : g) RELNN_CUDA(cudaMemsetAsync(x, 0, rows, st));
+        TriArgs a = base_args(T, d, d_a, d_b, d_c);
+        a.dout = d_dout;
+        a.dA = g[0];
+        a.dB = g[1];
+        a.dC = g[2];
+        return run_walk(T, a, true, dtype == RELNN_BF16, st);
+    }
     RELNN_TRY(fold_rows(T, d_a, d_b, d_c, dtype, d, st));
     const size_t keyrows = sizeof(float) * 3 * (size_t)T->U * d;
     RELNN_TRY(T->gkey.alloc(keyrows));
     RELNN_CUDA(cudaMemsetAsync(T->gkey.p, 0, keyrows, st));
-    TriArgs a = base_args(T, d);
+    TriArgs a = base_args(T, d, d_a, d_b, d_c);
     a.dout = d_dout;
     a.dA = T->gkey.as<float>();
     a.dB = a.dA + (size_t)T->U * d;
     a.dC = a.dA + 2 * (size_t)T->U * d;
-    RELNN_TRY(run_walk(T, a, true, st));
+    RELNN_TRY(run_walk(T, a, true, false, st));
     { unfold_kernel<<<grid_of(3 * T->n_h * d), 256, 0, st>>>(T->gkey.as<float>(), T->H.rows_sorted.as<int32_t>(),
                                                             T->H.uid_of_pos.as<int32_t>(), T->n_h, T->U, d, d_da, d_db,
                                                             d_dc); note_launch(); }

@@ -109,3 +109,27 @@ def test_triangle_without_matches_and_bad_width(gpu):
     with pytest.raises(R.RelnnError):
         T.forward(torch.zeros((10, 48), device="cuda"), torch.zeros((10, 48), device="cuda"),
                   torch.zeros((10, 48), device="cuda"))
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("d", [32, 128])
+def test_triangle_unique_keys_read_rows_in_place(gpu, bf16, d):
+    """Unique H keys: the records name H rows and the walk reads a, b, c (f32 or bf16) in place;
+    forward and backward against the oracle."""
+    h, a, b, c, src, dst = W.graph_batch(54, 300, 20, d, dup_edges=0.05, missing=0.02)
+    T = _plan(h, src, dst)
+    dt = torch.bfloat16 if bf16 else torch.float32
+    ta, tb, tc = to_dev(a, dt), to_dev(b, dt), to_dev(c, dt)
+    out = T.forward(ta, tb, tc)
+    dout = np.random.default_rng(8).standard_normal(tuple(out.shape)).astype(np.float32)
+    da, db, dc = T.backward(to_dev(dout), ta, tb, tc)
+    torch.cuda.synchronize()
+    if bf16:
+        a, b, c = bf16_round(a), bf16_round(b), bf16_round(c)
+    ok, oo = O.triangle_forward(h, a, b, c, src, dst)
+    assert np.array_equal(T.out_keys().cpu().numpy(), ok)
+    assert rel_frob(out.cpu().numpy(), oo) <= 1e-5
+    oa, ob, oc = O.triangle_backward(h, a, b, c, src, dst, dout)
+    assert rel_frob(da.cpu().numpy(), oa) <= 1e-5
+    assert rel_frob(db.cpu().numpy(), ob) <= 1e-5
+    assert rel_frob(dc.cpu().numpy(), oc) <= 1e-5
