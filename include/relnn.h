@@ -244,6 +244,10 @@ relnn_status relnn_attention_backward(relnn_plan_t p, const relnn_attn_params* p
 
 /* Releases the plan's device memory (waits for the device first). */
 relnn_status relnn_plan_destroy(relnn_plan_t p);
+/* Releases the plan without waiting: its device memory is freed in the order of `stream`, after
+ * the work already queued there. Every call that used the plan must have been issued on that
+ * stream (or be complete); the handle is invalid on return. */
+relnn_status relnn_plan_release(relnn_plan_t p, void* stream);
 
 /* async. Loss relation of content arity 0 (paper Sec. 3.2 fit statement; Sec. 3.6 loss rule):
  *     L(; mean((z_p - z_t)^2)) :- Pred(g; z_p), Target(g; z_t)

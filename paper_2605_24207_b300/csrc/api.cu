@@ -230,6 +230,13 @@ relnn_status relnn_attention_backward(relnn_plan_t p, const relnn_attn_params* p
     return attention_backward(p->p, prm, d_fwd_out, d_lse, d_dout, d_dq, d_dk, d_dv, (cudaStream_t)stream);
 }
 
+relnn_status relnn_plan_release(relnn_plan_t p, void* stream) {
+    if (!p) return RELNN_OK;
+    p->p.retire_on((cudaStream_t)stream);
+    delete p;
+    return RELNN_OK;
+}
+
 relnn_status relnn_plan_destroy(relnn_plan_t p) {
     if (!p) return RELNN_OK;
     cudaDeviceSynchronize();

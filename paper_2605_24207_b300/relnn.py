@@ -137,6 +137,8 @@ def lib():
     L.relnn_rule_forward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp]
     L.relnn_rule_backward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp, vp, vp]
     L.relnn_plan_destroy.argtypes = [vp]
+    L.relnn_plan_release.argtypes = [vp, vp]
+    L.relnn_plan_release.restype = C.c_int
     L.relnn_rule_forward_noalloc.argtypes = [vp, C.c_int32, vp, vp, vp, i64, vp, vp, C.c_int32, C.c_int, vp, vp]
     L.relnn_rule_forward_noalloc.restype = C.c_int
     L.relnn_mse_loss.argtypes = [vp, vp, i64, vp, vp, i64, C.c_int32, C.c_int, vp, vp, vp]
@@ -384,6 +386,13 @@ class RulePlan:
         _check(lib().relnn_rule_backward(self._h, C.byref(prm), _ptr(dout), dWp, dbp, _ptr(dz), drp,
                                          _stream(stream)))
         return dW, db, dz, dr
+
+    def release(self, stream=None):
+        """Frees the plan in the order of ``stream`` (no device-wide wait); every call that used
+        the plan must have been issued on that stream."""
+        if getattr(self, "_h", None) and self._h.value:
+            _check(lib().relnn_plan_release(self._h, _stream(stream)))
+            self._h = C.c_void_p()
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value and _LIB is not None:
