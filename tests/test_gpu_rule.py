@@ -212,3 +212,21 @@ def test_bf16_backward_matches_oracle(gpu, shape):
         if dr is not None:
             assert rel_frob(dr[i].cpu().numpy(), orr[i]) <= BF16_TOL
     assert rel_frob(dz.cpu().numpy(), oz) <= BF16_TOL
+
+
+def test_plan_release_in_stream_order(gpu):
+    """relnn_plan_release frees the plan after the work queued on its stream, without a device-wide
+    wait: a forward issued on a side stream, then the release, then the result read back."""
+    rel = W.make_rule(97, 20_000, 2000, 16, 16, np.int32)
+    br = rel.branches[0]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan = R.RulePlan(to_dev(rel.h_ids), [(to_dev(br.src), to_dev(br.dst))], 16, 16)
+        out = plan.forward(to_dev(rel.z), [to_dev(br.W)], [to_dev(br.b)])
+        keys = plan.out_keys()
+        plan.release()
+    s.synchronize()
+    ok, oo, _ = oracle_rule(rel)
+    assert np.array_equal(keys.cpu().numpy(), ok)
+    assert rel_frob(out.cpu().numpy(), oo) <= 1e-5
+    plan.release()  # a second release is a no-op
