@@ -613,10 +613,11 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
             { ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st); kern<<<lgrid, 256, lsmem, st>>>(a); note_launch(); prof_end(pt, st); }
             return true;
         };
-        static int bps64x64[2], bps32x32[2], bps64x16[2];
+        static int bps64x64[2], bps32x16[2], bps32x32[2], bps64x16[2];
         // (MAX runs in the feature-per-thread kernel: a sequential walk keeps the first maximum)
         const bool lane_done = maxagg ? false : p.identity ? lane_launch(fwd_fp32_lane_kernel<64, 64>, 64, 64, bps64x64)
-                                          : (lane_launch(fwd_fp32_lane_kernel<32, 32>, 32, 32, bps32x32) ||
+                                          : (lane_launch(fwd_fp32_lane_kernel<32, 16>, 32, 16, bps32x16) ||
+                                             lane_launch(fwd_fp32_lane_kernel<32, 32>, 32, 32, bps32x32) ||
                                              lane_launch(fwd_fp32_lane_kernel<64, 16>, 64, 16, bps64x16));
         if (!lane_done) {
             const int grid = (int)std::min<int64_t>(a.n_tiles, (int64_t)num_sms() * (smem > 100 * 1024 ? 1 : 4));
