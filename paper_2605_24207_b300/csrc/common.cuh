@@ -91,9 +91,7 @@ struct DevBuf {
         p = nullptr;
         bytes = 0;
     }
-    // (without a stream, the allocation is ordered on the calling thread's default stream, which
-    // does not wait for other streams' work, so growing a buffer does not drain the device)
-    relnn_status alloc(size_t n, cudaStream_t s = cudaStreamPerThread) {
+    relnn_status alloc(size_t n, cudaStream_t s = nullptr) {
         if (n <= bytes && p) return RELNN_OK;
         release();
         if (n == 0) n = 16;
