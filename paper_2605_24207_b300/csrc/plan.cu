@@ -215,13 +215,15 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
             base_s = excl;
         }
     }
-    __syncthreads();
-    int64_t pos = base_s + woff + (incl - cnt);
     // unique keys: a key's distinct index is its sorted position, so rd = run_start[b] = b and the
-    // src H row is rows_sorted[a]
+    // src H row is rows_sorted[a]. The tile's pairs are staged in shared memory in output order and
+    // then stored by consecutive threads (the block's output range is contiguous).
+    __shared__ K sk[kEmitTile];
+    __shared__ V sv[kEmitTile];
     int32_t hsv[kEmitItems];
 #pragma unroll
     for (int i = 0; i < kEmitItems; ++i) hsv[i] = (a[i] >= 0 && bb[i] >= 0) ? __ldg(j.rows_sorted + a[i]) : 0;
+    int lp = woff + (incl - cnt);
 #pragma unroll
     for (int i = 0; i < kEmitItems; ++i) {
         if (a[i] < 0 || bb[i] < 0) continue;
@@ -230,10 +232,15 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
         V val;
         if (sizeof(V) == 8) val = (V)(((uint64_t)(uint32_t)hs << 32) | (uint32_t)e);
         else val = (V)hs;
-        if (join_dst) t_key[pos] = (K)bb[i];
-        else t_key[pos] = (K)(ordered64(load_key(dst, kt, e)) - omin);
-        t_val[pos] = val;
-        ++pos;
+        sk[lp] = join_dst ? (K)bb[i] : (K)(ordered64(load_key(dst, kt, e)) - omin);
+        sv[lp] = val;
+        ++lp;
+    }
+    __syncthreads();
+    const int64_t base = base_s;
+    for (int i = threadIdx.x; i < btot; i += kEmitThreads) {
+        t_key[base + i] = sk[i];
+        t_val[base + i] = sv[i];
     }
 }
 
