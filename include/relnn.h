@@ -44,7 +44,7 @@ typedef enum relnn_status {
     RELNN_ETIMEDOUT = 5,  /* a bounded wait ran out                                                */
     RELNN_ECUDA = 6,      /* a CUDA runtime/driver call failed                                     */
     RELNN_EDEVICE = 7,    /* a device-side check failed; code in relnn_last_device_error()         */
-    RELNN_ENOTSUP = 8     /* feature/shape combination not supported by this build                 */
+    RELNN_ENOTSUP = 8     /* feature/shape combination the library does not support               */
 } relnn_status;
 
 typedef enum relnn_key_t { RELNN_I32 = 0, RELNN_I64 = 1 } relnn_key_t;
