@@ -1,7 +1,8 @@
 """GPU parity at the full sizes of the measured workloads, in the launch configurations bench.py times:
 the single-rule workload (16M tuples over 1M int64 keys, BF16 form), the union workload (three
-relations of 2M / 1M / 0.5M tuples with a per-tuple embedding, BF16 form, Kahan) and the first rule
-of the stacked program (4M tuples over 500k keys, ReLU, f32 z). The oracle evaluates sampled
+relations of 2M / 1M / 0.5M tuples with a per-tuple embedding, BF16 form, Kahan), the first rule
+of the stacked program (4M tuples over 500k keys, ReLU, f32 z) and the 4,096 small FP32 rules in
+one plan. The oracle evaluates sampled
 output keys one by one: the E rows whose dst is a sampled key, joined with the full H, give exactly
 those keys' rows. Properties that hold at any size are checked on the whole output: the output
 key set is the set of dst keys with a matched tuple, and every branch's matched-tuple count is the
@@ -99,3 +100,27 @@ def test_single_rule_full_size_max(gpu):
     _, all_keys = _matched_keys(rel)
     assert np.array_equal(keys.astype(np.int64), all_keys.astype(np.int64))
     _sampled_parity(rel, keys, out, R.FLAG_BF16 | R.FLAG_MAX, "none", 4, agg="max")
+
+
+def test_many_small_rules_full_size(gpu):
+    """4,096 independent instances of the small FP32 rule in one plan and one FP32-form launch (the
+    bench's many-small-rules workload): sampled output keys against the oracle."""
+    hs, zs, ss, ds = [], [], [], []
+    for i in range(4096):
+        r = W.config1(seed=i)
+        br = r.branches[0]
+        off = np.int32(i * 1024)
+        hs.append(r.h_ids + off)
+        zs.append(r.z)
+        ss.append(br.src + off)
+        ds.append(br.dst + off)
+        if i == 0:
+            Wn, bn = br.W, br.b
+    rel = W.Relations(h_ids=np.concatenate(hs), z=np.concatenate(zs),
+                      branches=[W.Branch(src=np.concatenate(ss), dst=np.concatenate(ds), W=Wn, b=bn, r=None)],
+                      act="none")
+    plan, keys, out = _run(rel, 0, "none", torch.float32)
+    counts, all_keys = _matched_keys(rel)
+    assert plan.matched == counts
+    assert np.array_equal(keys, all_keys)
+    _sampled_parity(rel, keys, out, 0, "none", 5, round_=False, tol=1e-5)
