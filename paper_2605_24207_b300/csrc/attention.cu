@@ -128,15 +128,29 @@ __device__ __forceinline__ float head_sum(float x, int lph) {
     return x;
 }
 
-template <int F, bool BF16, int MODE>
+// Sum over the lph lanes of a head within the lanes of `mask` (aligned groups of lph lanes).
+__device__ __forceinline__ float head_sum_m(float x, int lph, unsigned mask) {
+    for (int o = lph >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o);
+    return x;
+}
+
+// Each group of G lanes (a warp, or a half-warp for narrow rows) owns one range of tuples; lane j of
+// a group holds features [F j, F j + F) (F = d / G), and KIN tuples' k and v rows are loaded before
+// any is used.
+template <int F, bool BF16, int MODE, int G>
 __global__ void __launch_bounds__(256) attn_fwd_kernel(AttnArgs a) {
+    constexpr int KIN = G == 32 ? 4 : 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const int gl = lane % G, grp = lane / G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (16 * grp));
+    const int64_t groups_total = (int64_t)gridDim.x * (blockDim.x >> 5) * (32 / G);
     const int64_t span = (int64_t)a.range_tiles * 32;
-    const int c0 = lane * F;                // this lane's first feature
-    const int head = lane / a.lph;          // its head
-    const bool head_lead = (lane % a.lph) == 0;
-    for (int64_t rg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; rg < a.n_ranges; rg += warps_total) {
+    const int lph = G / a.n_heads;          // lanes per head within the group
+    const int c0 = gl * F;                  // this lane's first feature
+    const int head = gl / lph;              // its head
+    const bool head_lead = (gl % lph) == 0;
+    for (int64_t rg = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * (32 / G) + grp; rg < a.n_ranges;
+         rg += groups_total) {
         const int64_t r0 = rg * span, r1 = imin64(a.m, r0 + span);
         const int prev_seg = r0 > 0 ? a.seg[r0 - 1] : -1;
         const int next_seg = r1 < a.m ? a.seg[r1] : -1;
@@ -177,26 +191,26 @@ __global__ void __launch_bounds__(256) attn_fwd_kernel(AttnArgs a) {
             l = 0.f;
             first = false;
         };
-        for (int64_t b0 = r0; b0 < r1; b0 += 32) {
-            const int nb = (int)imin64(32, r1 - b0);
-            const bool tv = lane < nb;
-            const int sv = tv ? a.seg[b0 + lane] : -1;
-            const int kv = tv ? a.hs[b0 + lane] : 0;
-            const int qv = tv ? a.hd[b0 + lane] : 0;
-            for (int j0 = 0; j0 < nb; j0 += 4) {
-                float kf[4][F], vf[4][F];
-                int sj[4], qj[4];
+        for (int64_t b0 = r0; b0 < r1; b0 += G) {
+            const int nb = (int)imin64(G, r1 - b0);
+            const bool tv = gl < nb;
+            const int sv = tv ? a.seg[b0 + gl] : -1;
+            const int kv = tv ? a.hs[b0 + gl] : 0;
+            const int qv = tv ? a.hd[b0 + gl] : 0;
+            for (int j0 = 0; j0 < nb; j0 += KIN) {
+                float kf[KIN][F], vf[KIN][F];
+                int sj[KIN], qj[KIN];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < KIN; ++u) {
                     const int j = j0 + u < nb ? j0 + u : nb - 1;
-                    sj[u] = __shfl_sync(0xffffffffu, sv, j);
-                    qj[u] = __shfl_sync(0xffffffffu, qv, j);
-                    const int kr = __shfl_sync(0xffffffffu, kv, j);
+                    sj[u] = __shfl_sync(gmask, sv, j, G);
+                    qj[u] = __shfl_sync(gmask, qv, j, G);
+                    const int kr = __shfl_sync(gmask, kv, j, G);
                     load_f<F, BF16>(a.k, kr, a.d, c0, kf[u]);
                     load_f<F, BF16>(a.v, kr, a.d, c0, vf[u]);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < KIN; ++u) {
                     if (j0 + u >= nb) break;
                     if (sj[u] != cur) {
                         if (cur >= 0) flush(cur, false);
@@ -213,7 +227,7 @@ __global__ void __launch_bounds__(256) attn_fwd_kernel(AttnArgs a) {
                         float p = 0.f;
 #pragma unroll
                         for (int i = 0; i < F; ++i) p = fmaf(qf[i], kf[u][i], p);
-                        const float sc = head_sum(p, a.lph) * a.scale;
+                        const float sc = head_sum_m(p, lph, gmask) * a.scale;
                         const float mn = fmaxf(mx, sc);
                         const float corr = __expf(mx - mn);
                         const float e = __expf(sc - mn);
@@ -463,36 +477,47 @@ __global__ void __launch_bounds__(256) attn_bwd_src_kernel(AttnArgs a) {
 }
 
 template <class K>
-void range_launch(K kern, AttnArgs& a, cudaStream_t st, int& bps_cache) {
+void range_launch(K kern, AttnArgs& a, cudaStream_t st, int& bps_cache, int groups_per_warp = 1) {
     if (bps_cache <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_cache, kern, 256, 0) != cudaSuccess) {
         (void)cudaGetLastError();  // sizes the ranges only: assume one block per SM
         bps_cache = 1;
     }
     const int bps = std::max(1, bps_cache);
     const int64_t n32 = ceil_div(a.m, 32);
-    const int64_t resident = (int64_t)bps * num_sms() * 8;
+    const int64_t resident = (int64_t)bps * num_sms() * 8 * groups_per_warp;
     a.range_tiles = (int)std::min<int64_t>(ceil_div(n32, resident), 1 << 20);
     a.n_ranges = ceil_div(n32, a.range_tiles);
 }
 
+// F = d / 32 (the fix-up's warp layout); the walk runs half-warp groups (2F features per lane) for
+// rows of up to 128 features with at most 16 heads, whole warps otherwise.
 template <int F, bool BF16>
 relnn_status attn_forward_t(Plan& p, AttnArgs& a, int mode, cudaStream_t st) {
-    static int bps[2] = {0, 0};
+    static int bps[4] = {0, 0, 0, 0};
     const int grid_cap = num_sms() * 8;
+    constexpr int FH = F <= 4 ? 2 * F : F;  // features per lane in a half-warp group
+    const bool half = F <= 4 && (mode == kProduct || a.n_heads <= 16);
     if (mode == kSoftmax) {
-        range_launch(attn_fwd_kernel<F, BF16, kSoftmax>, a, st, bps[0]);
+        if (half) range_launch(attn_fwd_kernel<FH, BF16, kSoftmax, 16>, a, st, bps[0], 2);
+        else range_launch(attn_fwd_kernel<F, BF16, kSoftmax, 32>, a, st, bps[1]);
         a.hdr = (2 * a.n_heads + 3) & ~3;
     } else {
-        range_launch(attn_fwd_kernel<F, BF16, kProduct>, a, st, bps[1]);
+        if (half) range_launch(attn_fwd_kernel<FH, BF16, kProduct, 16>, a, st, bps[2], 2);
+        else range_launch(attn_fwd_kernel<F, BF16, kProduct, 32>, a, st, bps[3]);
         a.hdr = 0;
     }
     a.cs = a.hdr + a.d;  // d is a multiple of 32, so cs is a multiple of 4 floats
     RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * (size_t)a.cs * a.n_ranges));
     a.carry = p.carry.as<float>();
-    const int grid = (int)std::min<int64_t>(ceil_div(a.n_ranges, 8), grid_cap);
+    const int grid = (int)std::min<int64_t>(ceil_div(a.n_ranges, half ? 16 : 8), grid_cap);
     ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st);
-    if (mode == kSoftmax) attn_fwd_kernel<F, BF16, kSoftmax><<<grid, 256, 0, st>>>(a);
-    else attn_fwd_kernel<F, BF16, kProduct><<<grid, 256, 0, st>>>(a);
+    if (mode == kSoftmax) {
+        if (half) attn_fwd_kernel<FH, BF16, kSoftmax, 16><<<grid, 256, 0, st>>>(a);
+        else attn_fwd_kernel<F, BF16, kSoftmax, 32><<<grid, 256, 0, st>>>(a);
+    } else {
+        if (half) attn_fwd_kernel<FH, BF16, kProduct, 16><<<grid, 256, 0, st>>>(a);
+        else attn_fwd_kernel<F, BF16, kProduct, 32><<<grid, 256, 0, st>>>(a);
+    }
     note_launch();
     prof_end(pt, st);
     RELNN_CUDA(cudaGetLastError());
