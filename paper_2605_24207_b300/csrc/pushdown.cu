@@ -136,6 +136,92 @@ __global__ void __launch_bounds__(256) pd_sum_kernel(PdArgs a) {
     }
 }
 
+// The same walk in half-warp groups when no ReLU mask is kept and d_out is 64 or 128: each group of
+// 16 lanes owns a range, lane j holds outputs [F j, F j + F) (16-byte loads of the P and Q rows),
+// so every warp instruction serves two tuples.
+template <int F>
+__global__ void __launch_bounds__(256) pd_sum_half_kernel(PdArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane & 15, grp = lane >> 4;
+    const unsigned gmask = 0xffffu << (16 * grp);
+    const int64_t groups_total = (int64_t)gridDim.x * (blockDim.x >> 5) * 2;
+    const int64_t span = (int64_t)a.range_tiles * 32;
+    const bool relu = a.act == RELNN_ACT_RELU;
+    const int c0 = gl * F;
+    float qb[F];
+#pragma unroll
+    for (int i = 0; i < F; ++i) qb[i] = (!a.Q && a.bias) ? a.bias[c0 + i] : 0.f;
+    for (int64_t rg = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 2 + grp; rg < a.n_ranges;
+         rg += groups_total) {
+        const int64_t r0 = rg * span, r1 = imin64(a.m, r0 + span);
+        const int prev_seg = r0 > 0 ? a.seg[r0 - 1] : -1;
+        const int next_seg = r1 < a.m ? a.seg[r1] : -1;
+        int cur = -1;
+        bool first = true;
+        float acc[F], comp[F];
+#pragma unroll
+        for (int i = 0; i < F; ++i) acc[i] = comp[i] = 0.f;
+        auto flush = [&](int s, bool last) {
+            const bool split = (first && prev_seg == s) || (last && next_seg == s);
+            float* dst = (split ? a.carry + (rg * 2 + (first ? 0 : 1)) * a.d_out : a.out + (int64_t)s * a.d_out) + c0;
+            if (split || !a.accumulate) {
+#pragma unroll
+                for (int i = 0; i < F; i += 4)
+                    __stcg(reinterpret_cast<float4*>(dst + i), make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < F; ++i) atomicAdd(dst + i, acc[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < F; ++i) acc[i] = comp[i] = 0.f;
+            first = false;
+        };
+        for (int64_t b0 = r0; b0 < r1; b0 += 16) {
+            const int nb = (int)imin64(16, r1 - b0);
+            const bool tv = gl < nb;
+            const int sv = tv ? a.seg[b0 + gl] : -1;
+            const int hv = tv ? a.hs[b0 + gl] : 0;
+            const int dv = (tv && a.Q) ? a.hd[b0 + gl] : 0;
+            for (int j0 = 0; j0 < nb; j0 += 4) {
+                float y[4][F];
+                int sj[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u < nb ? j0 + u : nb - 1;
+                    sj[u] = __shfl_sync(gmask, sv, j, 16);
+                    const int64_t ph = (int64_t)__shfl_sync(gmask, hv, j, 16) * a.d_out + c0;
+                    const int64_t qh = (int64_t)__shfl_sync(gmask, dv, j, 16) * a.d_out + c0;
+#pragma unroll
+                    for (int i = 0; i < F; i += 4) {
+                        const float4 pv = __ldg(reinterpret_cast<const float4*>(a.P + ph + i));
+                        const float4 qv = a.Q ? __ldg(reinterpret_cast<const float4*>(a.Q + qh + i))
+                                              : make_float4(qb[i], qb[i + 1], qb[i + 2], qb[i + 3]);
+                        y[u][i] = pv.x + qv.x;
+                        y[u][i + 1] = pv.y + qv.y;
+                        y[u][i + 2] = pv.z + qv.z;
+                        y[u][i + 3] = pv.w + qv.w;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (j0 + u >= nb) break;
+                    if (sj[u] != cur) {
+                        if (cur >= 0) flush(cur, false);
+                        cur = sj[u];
+                    }
+#pragma unroll
+                    for (int i = 0; i < F; ++i) {
+                        const float v = relu ? fmaxf(y[u][i], 0.f) : y[u][i];
+                        if (a.kahan) kahan_add(acc[i], comp[i], v);
+                        else acc[i] += v;
+                    }
+                }
+            }
+        }
+        if (cur >= 0) flush(cur, true);
+    }
+}
+
 }  // namespace
 
 relnn_status forward_pushdown(Plan& p, const CallIO& io_in, float* out, cudaStream_t st) {
@@ -232,10 +318,21 @@ relnn_status forward_pushdown(Plan& p, const CallIO& io_in, float* out, cudaStre
         a.n_ranges = ceil_div(n32, a.range_tiles);
         RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * (size_t)a.n_ranges));
         a.carry = p.carry.as<float>();
-        const int grid = (int)std::min<int64_t>(ceil_div(a.n_ranges, 8), (int64_t)bps * num_sms());
+        const bool half = !want_mask && (p.d_out == 64 || p.d_out == 128) &&
+                          (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+        if (half) {
+            // half-warp groups: two ranges per warp
+            a.range_tiles = (int)std::min<int64_t>(ceil_div(n32, 2 * resident), 1 << 20);
+            a.n_ranges = ceil_div(n32, a.range_tiles);
+            RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * (size_t)a.n_ranges));
+            a.carry = p.carry.as<float>();
+        }
+        const int grid = (int)std::min<int64_t>(ceil_div(a.n_ranges, half ? 16 : 8), (int64_t)bps * num_sms());
         {
             ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st);
-            switch (F) {
+            if (half && p.d_out == 128) pd_sum_half_kernel<8><<<grid, 256, 0, st>>>(a);
+            else if (half) pd_sum_half_kernel<4><<<grid, 256, 0, st>>>(a);
+            else switch (F) {
                 case 1: pd_sum_kernel<1><<<grid, 256, 0, st>>>(a); break;
                 case 2: pd_sum_kernel<2><<<grid, 256, 0, st>>>(a); break;
                 case 3: pd_sum_kernel<3><<<grid, 256, 0, st>>>(a); break;
