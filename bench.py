@@ -37,10 +37,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rule tuples/s"
 UNIT = "tuples/s"
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fwd_tc_kernel launch on the
-# default 16M-tuple single-rule workload, from one ncu capture of the kernel as it is now
-# (824,585,216 read + 538,345,472 written); reported only for that workload.
-NCU_TRAFFIC_PER_LAUNCH = 824_585_216 + 538_345_472
 
 
 def parse():
@@ -60,6 +56,12 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip warm / comparator extras")
     ap.add_argument("--agg", default="sum", choices=["sum", "mean", "max"],
                     help="c2: aggregator of the rule (extras only with sum)")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="c2: skip the c3 / c4 / c1b / c5 records appended to the line")
+    ap.add_argument("--no-serving", action="store_true", help="c2: skip the shortened c5 record")
+    ap.add_argument("--sub-queries", type=int, default=2000, help="queries of the shortened c5 record")
+    ap.add_argument("--sub-cmp-queries", type=int, default=300,
+                    help="queries the torch comparator serves in the shortened c5 record")
     return ap.parse_args()
 
 
@@ -167,6 +169,12 @@ class C2:
         self.matched, self.n_out = p.n_matched, p.n_out
         self.plan0 = p
         self.out = torch.empty((max(self.n_out, 1), self.d_out), dtype=torch.float32, device=dev)
+        # the SUM rule has no activation: the library evaluates it aggregate-first (one virtual row
+        # per output row, or per 32 tuples of a heavier row)
+        self.agg_form = self.agg == "sum"
+        cnt = np.bincount(np.searchsorted(np.sort(self.rel.h_ids), self.rel.branches[0].dst),
+                          minlength=self.rel.h_ids.size)
+        self.n_vrows = int(np.maximum(1, (cnt[cnt > 0] + 31) // 32).sum())
 
     def step(self):
         from paper_2605_24207_b300 import relnn as R
@@ -175,9 +183,18 @@ class C2:
         p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
         return p
 
-    def roofline_kernel(self):
+    def kernels(self):
+        """Library kernels of a step: id -> (name, algorithmic work per step, bound)."""
         from paper_2605_24207_b300 import relnn as R
-        return R.PROF_FWD_TC, "fwd_tc_kernel", 2.0 * (2 * self.d) * self.d_out * self.matched
+        # aggregate-first form (HBM): per matched tuple its two 4-byte row indices, per virtual row
+        # its 16-byte descriptor (read by the producers and the epilogue), each H row once (bf16) and
+        # each output row once (f32). Per-tuple form (tensor): 2 d_in d_out FLOP per tuple.
+        return {R.PROF_AGG_FWD: ("agg_tc_kernel<fwd>", float(self.agg_bytes()), "hbm"),
+                R.PROF_FWD_TC: ("fwd_tc_kernel", 2.0 * (2 * self.d) * self.d_out * self.matched, "tensor")}
+
+    def agg_bytes(self):
+        n_h = int(self.t["h"].numel())
+        return 8 * self.matched + 2 * 16 * self.n_vrows + n_h * self.d * 2 + self.n_out * self.d_out * 4
 
     def e2e_setup(self):
         # two slots (device inputs, device output, pinned result, stream) used in turn, so that one
@@ -242,15 +259,40 @@ class C2:
         import torch
         if self.agg != "sum":
             return {}
+        from paper_2605_24207_b300 import relnn as R
         t, p = self.t, self.plan0
+
+        def ktime(fn, reps, kid):
+            """(ms per call, ms per launch of library kernel kid)."""
+            R.profile_reset()
+            R.profile_enable(True)
+            ms = timer(fn, reps)
+            R.profile_enable(False)
+            k_ms, k_n = R.profile_read(kid)
+            return ms, (k_ms / k_n if k_n else None)
+
         fwd = lambda: p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
-        ms_f = timer(fwd, max(3, steps))
-        dout = torch.ones_like(self.out[: self.n_out])
+        ms_f, k_f = ktime(fwd, max(3, steps), R.PROF_AGG_FWD)
+        dout = torch.randn_like(self.out[: self.n_out])
+        bwd = lambda: p.backward(dout, t["z"], [t["W"]], [t["b"]])
+        ms_b, k_b = ktime(bwd, max(3, steps), R.PROF_AGG_BWD)
 
         def fb():
             fwd()
-            p.backward(dout, t["z"], [t["W"]], [t["b"]])
-        ms_fb = timer(fb, 3)
+            bwd()
+        ms_fb = timer(fb, max(3, steps))
+        # the per-tuple form of the same rule (the Linear on every matched tuple, then the SUM walk)
+        ppt = R.RulePlan(t["h"], [(t["src"], t["dst"])], self.d, self.d_out, flags=self.flags | R.FLAG_PER_TUPLE)
+        ms_pt, k_pt = ktime(lambda: ppt.forward(t["z"], [t["W"]], [t["b"]], out=self.out), max(3, steps), R.PROF_FWD_TC)
+        ms_ptb, k_ptb = ktime(lambda: ppt.backward(dout, t["z"], [t["W"]], [t["b"]]), 3, R.PROF_BWD_TC)
+        del ppt
+        pk, _ = peaks()
+        pt_flop = 2.0 * (2 * self.d) * self.d_out * self.matched
+        # backward bytes: per pass and tuple one 4-byte index, per H row its descriptor (twice), the
+        # dOut rows (bf16) and H rows (bf16) once per pass, dz written by the src pass and read and
+        # written by the dst pass
+        n_h = int(t["h"].numel())
+        b_bytes = 2 * (4 * self.matched + 32 * n_h + self.n_out * self.d_out * 2 + n_h * self.d * 2) + n_h * self.d * 4 * 3
         ms_torch = timer(self.torch_step, 3)
         # the push-down rewrite (Linear once per H row, then per-tuple gathers of the f32 products)
         from paper_2605_24207_b300 import relnn as R
@@ -310,7 +352,19 @@ class C2:
         n_h = t["h"].numel()
         at_bytes = 12 * self.matched + 3 * n_h * self.d * 2 + self.n_out * (self.d + 8) * 4
         return {"warm_forward_tuples_per_s": self.matched / (ms_f * 1e-3), "warm_forward_ms": ms_f,
+                "warm_forward_kernel_ms": k_f,
+                "warm_backward_ms": ms_b, "warm_backward_kernel_ms_per_pass": k_b,
+                "warm_backward_roofline": {"bound": "hbm", "algorithmic_bytes": b_bytes,
+                                           "achieved_gbs": b_bytes / (2 * k_b * 1e-3) / 1e9 if k_b else None,
+                                           "frac": (b_bytes / (2 * k_b * 1e-3) / 1e9 / pk["hbm_gbs"]) if k_b else None,
+                                           "kernel": "agg_tc_kernel<bwd> (two passes)"},
                 "warm_fwd_bwd_tuples_per_s": self.matched / (ms_fb * 1e-3), "warm_fwd_bwd_ms": ms_fb,
+                "per_tuple_form": {"warm_forward_ms": ms_pt, "fwd_tc_kernel_ms": k_pt,
+                                   "tensor_tflops": pt_flop / (k_pt * 1e-3) / 1e12 if k_pt else None,
+                                   "frac_of_bf16_burst": (pt_flop / (k_pt * 1e-3) / 1e12 / pk["bf16_tflops"]) if k_pt else None,
+                                   "warm_backward_ms": ms_ptb, "bwd_tc_kernel_ms": k_ptb,
+                                   "what": "RELNN_FLAG_PER_TUPLE: the Linear on every matched tuple (tcgen05), "
+                                           "then the SUM walk; backward: two tcgen05 passes"},
                 "pushdown_warm_forward": {"tuples_per_s": self.matched / (ms_pd * 1e-3), "ms": ms_pd,
                                           "what": "RELNN_FLAG_PUSHDOWN: P = Z W_src^T, Q = Z W_dst^T + b per H row "
                                                   "(tensor cores), then per-tuple f32 row gathers + SUM"},
@@ -400,11 +454,24 @@ class C3:
         t = self.t
         return self.prog.step(t["z"], t["W1"], t["b1"], t["W2"], t["b2"])
 
-    def roofline_kernel(self):
+    def kernels(self):
         from paper_2605_24207_b300 import relnn as R
-        # the backward's two GEMMs (dX, dW): 2 x 2 x 128 x 64 FLOP per rule tuple and step (the src
-        # pass recomputes dX for the src slice; that is not counted as algorithmic work)
-        return R.PROF_BWD_TC, "bwd_tc_kernel", 2.0 * 2.0 * 128 * 64 * self.matched
+        pr = self.prog
+        m1, m2 = pr.p1.n_matched, pr.p2.n_matched
+        n_h, n1, n2 = int(self.t["h"].numel()), pr.p1.n_out, pr.p2.n_out
+        # rule 1 (ReLU) runs per tuple on the tensor cores: forward 2 x 128 x 64 FLOP per tuple, the
+        # backward's two GEMMs (dX, dW) twice that (the src pass's recomputed dX slice not counted).
+        # Rule 2 (linear) runs aggregate-first and is HBM-bound: forward = per tuple two 4-byte
+        # indices, per output row its descriptor (twice), H1 rows once (bf16) and output rows once;
+        # backward = per pass and tuple one 4-byte index, per H1 row its descriptor (twice), dOut rows
+        # (bf16) and H1 rows (bf16) once, dz rows written (src pass) or read and written (dst pass).
+        agg_f = 8 * m2 + 32 * n2 + n1 * 64 * 2 + n2 * 64 * 4
+        agg_b = 2 * (4 * m2 + 32 * n1 + n2 * 64 * 2 + n1 * 64 * 2) + n1 * 64 * 4 * 3
+        return {R.PROF_BWD_TC: ("bwd_tc_kernel (rule 1)", 2.0 * 2.0 * 128 * 64 * m1, "tensor"),
+                R.PROF_FWD_TC: ("fwd_tc_kernel (rule 1)", 2.0 * 128 * 64 * m1, "tensor"),
+                R.PROF_AGG_FWD: ("agg_tc_kernel<fwd> (rule 2)", float(agg_f), "hbm"),
+                R.PROF_AGG_BWD: ("agg_tc_kernel<bwd> (rule 2)", float(agg_b), "hbm"),
+                R.PROF_FWD_FP32: ("fwd_fp32_lane_kernel (readout)", float(n2 * 64 * 4 + n2 * 4), "hbm")}
 
     def e2e_setup(self):
         import torch
@@ -519,16 +586,13 @@ class C4:
         p.forward(self.t["z"], self.W, self.b, self.r, out=self.out)
         return p
 
-    def roofline_kernel(self):
+    def kernels(self):
         from paper_2605_24207_b300 import relnn as R
         # HBM-bound (about 115 FLOP per byte): algorithmic bytes of the three launches = per tuple its
         # r row (64 x f32) and its four 4-byte indices, each H row once (f32[64]) and each output row
         # once (f32[96])
         by = self.matched * (64 * 4 + 16) + self.n_h * 64 * 4 + self.n_out * 96 * 4
-        return R.PROF_FWD_TC, "fwd_tc_kernel", float(by)
-
-    def roofline_peak(self):
-        return "hbm", None, None
+        return {R.PROF_FWD_TC: ("fwd_tc_kernel", float(by), "hbm")}
 
     def e2e_setup(self):
         import torch
@@ -637,13 +701,10 @@ class C1B:
         p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
         return p
 
-    def roofline_kernel(self):
+    def kernels(self):
         from paper_2605_24207_b300 import relnn as R
-        return R.PROF_FWD_FP32, "fwd_fp32_lane_kernel", 2.0 * 32 * 16 * self.matched
-
-    def roofline_peak(self):
-        # f32 FMA on CUDA cores: 148 SMs x 128 lanes x 2 FLOP x 2.032 GHz (no measured figure exists)
-        return "alu", 148 * 128 * 2 * 2.032e9 / 1e12, "derived f32 CUDA-core peak (148 SM x 128 FMA/clk x 2.032 GHz)"
+        # f32 FMA on CUDA cores: 2 x 32 x 16 FLOP per tuple against the measured FMA probe
+        return {R.PROF_FWD_FP32: ("fwd_fp32_lane_kernel", 2.0 * 32 * 16 * self.matched, "alu")}
 
     def e2e_setup(self):
         import torch
@@ -700,10 +761,12 @@ def _torch_query(h, z, src, dst, Wt, bt):
     return uk, torch.zeros((uk.numel(), Y.shape[1]), device=Y.device).index_add_(0, inv, Y)
 
 
-def run_serving(args):
-    """--config c5: a stream of rule queries (T ~ logU[1k, 1M], K = T/8, z bf16[64], shared Linear
-    128 -> 64) arriving as a Poisson process at 2,000 queries/s, served by relnn_server_* with
-    memory-admitted continuous batching; latency = arrival -> results ready."""
+def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True) -> dict:
+    """A stream of rule queries (T ~ logU[1k, 1M], K = T/8, z bf16[64], shared Linear 128 -> 64)
+    arriving as a Poisson process at 2,000 queries/s, served by relnn_server_* with memory-admitted
+    continuous batching; latency = arrival -> results ready. Paced run (clocks sampled), saturation
+    run (arrivals as fast as admission allows), and the unfused FP32 torch form on the first n_cmp
+    queries of the same trace."""
     import threading
 
     import torch
@@ -712,7 +775,6 @@ def run_serving(args):
     from paper_2605_24207_b300 import workloads as W
 
     torch.backends.cuda.matmul.allow_tf32 = False
-    nq = args.n_queries
     arrivals, sizes = W.serving_trace(0, nq, 2000.0)
     grid = np.unique(np.round(np.exp(np.linspace(np.log(1000), np.log(1_000_000), 24))).astype(np.int64))
     qsize = grid[np.argmin(np.abs(np.log(grid)[None, :] - np.log(sizes)[:, None]), axis=1)]
@@ -772,11 +834,15 @@ def run_serving(args):
         srv.close()
         return np.array(lat), wall, float(np.mean(batch_q))
 
+    clk = Clocks(local)
+    te0 = time.time()
     lat, wall, mean_batch = serve(True, nq)
-    lat_s, wall_s, _ = serve(False, nq)
+    te1 = time.time()
+    clocks = clk.stop(te0, te1)
+    lat_s, wall_s, mean_batch_s = serve(False, nq)
 
     # comparator: the unfused FP32 form, one query at a time in arrival order, same trace prefix
-    n_cmp = min(nq, args.cmp_queries)
+    n_cmp = min(nq, n_cmp)
     for g in grid[:3].tolist():
         _torch_query(*pool[g], Wt, bt)
     torch.cuda.synchronize()
@@ -786,37 +852,48 @@ def run_serving(args):
         wait = t0 + arrivals[i] - time.perf_counter()
         if wait > 0:
             time.sleep(wait)
-        h, z, s, d = pool[int(qsize[i])]
-        _torch_query(h, z, s, d, Wt, bt)
+        h, z, s_, d_ = pool[int(qsize[i])]
+        _torch_query(h, z, s_, d_, Wt, bt)
         torch.cuda.synchronize()
         lat_t.append((time.perf_counter() - (t0 + arrivals[i])) * 1e3)
     lat_t = np.array(lat_t)
 
-    # CPU oracle on one query of median size
-    from oracle import relnn_oracle as O
-    gm = int(np.median(qsize))
-    keys, src, dst, z = W.serving_query(0, gm, gm, 64)
-    t1 = time.perf_counter()
-    _, _, sz = O.rule_forward(keys, _bf16(z), [_Br(src, dst, _bf16(Wt.cpu().numpy()), bt.cpu().numpy())])
-    cpu_rate = sz[0] / (time.perf_counter() - t1)
+    cpu = None
+    if with_cpu:
+        # CPU oracle on one query of median size
+        from oracle import relnn_oracle as O
+        gm = int(np.median(qsize))
+        keys, src, dst, z = W.serving_query(0, gm, gm, 64)
+        t1 = time.perf_counter()
+        _, _, sz = O.rule_forward(keys, _bf16(z), [_Br(src, dst, _bf16(Wt.cpu().numpy()), bt.cpu().numpy())])
+        cpu = {"value": sz[0] / (time.perf_counter() - t1), "unit": UNIT, "cores": cores(), "kind": "oracle",
+               "sample": f"one query of {gm} tuples"}
 
     pct = lambda a, q: float(np.percentile(a, q))
-    line = {"metric": METRIC, "value": tuples / wall_s, "unit": UNIT, "n_gpus": 1, "steps": nq, "warmup": 4,
-            "ms_per_step": 1e3 * wall_s / nq, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16", "data": "synthetic (seeded serving trace; no dataset)",
+    return {"value": tuples / wall_s, "unit": UNIT, "queries": nq, "tuples": tuples,
             "config": {"workload": f"serving stream of {nq} rule queries, T ~ logU[1k,1M] (24 size classes), "
                                    f"K = T/8, int32 keys, z bf16[64], shared Linear 128->64, Poisson arrivals "
                                    f"2000/s; value = saturation tuples/s", "tile128_below": thr},
             "serving": {"paced_p50_ms": pct(lat, 50), "paced_p99_ms": pct(lat, 99),
                         "paced_queries_per_s": nq / wall, "mean_queries_per_batch": mean_batch,
                         "saturation_queries_per_s": nq / wall_s, "saturation_tuples_per_s": tuples / wall_s,
+                        "saturation_mean_queries_per_batch": mean_batch_s,
                         "saturation_p50_ms": pct(lat_s, 50), "saturation_p99_ms": pct(lat_s, 99),
                         "first_n_paced_p50_ms": pct(lat[:n_cmp], 50), "first_n_paced_p99_ms": pct(lat[:n_cmp], 99),
                         "torch_fp32_unfused_first_n_p50_ms": pct(lat_t, 50),
                         "torch_fp32_unfused_first_n_p99_ms": pct(lat_t, 99), "first_n": n_cmp},
-            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores(), "kind": "oracle",
-                             "sample": f"one query of {gm} tuples"},
-            "roofline": None, "e2e": None}
+            "clocks": clocks, "cpu_baseline": cpu}
+
+
+def run_serving(args):
+    """--config c5: the serving stream on its own (one JSON line)."""
+    st = serving_stats(args.n_queries, args.cmp_queries)
+    nq = st["queries"]
+    line = {"metric": METRIC, "value": st["value"], "unit": UNIT, "n_gpus": 1, "steps": nq, "warmup": 4,
+            "ms_per_step": 1e3 * st["tuples"] / st["value"] / nq, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded serving trace; no dataset)",
+            "config": st["config"], "serving": st["serving"], "cpu_baseline": st["cpu_baseline"],
+            "clocks": st["clocks"], "roofline": None, "e2e": None}
     print(json.dumps(line), flush=True)
 
 
@@ -867,6 +944,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def choose_peak(bound: str, pk: dict, pk_src: str, region_s: float, clocks: dict, fp32: dict | None):
+    """Roofline denominator of a kernel: (peak, unit, source, the other bf16 peak or None). A bf16
+    contraction timed in a region shorter than a second with the SM clock at its maximum is compared
+    with the burst GEMM peak, otherwise with the sustained (power-capped) one."""
+    if bound == "hbm":
+        return pk["hbm_gbs"], "GB/s", f"{pk_src} HBM copy bandwidth", None
+    if bound == "alu":
+        if fp32 and fp32.get("tflops"):
+            return fp32["tflops"], "TFLOP/s", "f32 FMA probe (relnn_peak_fma_f32) measured in this run", None
+        return 148 * 128 * 2 * 2.032, "TFLOP/s", "derived f32 peak (148 SM x 128 FMA/clk x 2.032 GHz)", None
+    burst, sust = pk["bf16_tflops"], pk["bf16_tflops_sustained"]
+    sm, mx = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    at_max = bool(sm and mx and sm >= 0.95 * mx)
+    if region_s < 1.0 and at_max:
+        return burst, "TFLOP/s", f"{pk_src} bf16 burst (timed region {region_s:.3f} s at the maximum SM clock)", sust
+    return sust, "TFLOP/s", f"{pk_src} bf16 sustained", burst
+
+
 def run_relnn(args):
     import torch
     import torch.distributed as dist
@@ -889,6 +984,7 @@ def run_relnn(args):
 
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pk, pk_src = peaks()
 
     def timer(fn, reps):
         fn()
@@ -900,55 +996,87 @@ def run_relnn(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    def measure(wl, steps, warmup):
+        """Device time per step (CUDA events on the launching stream, max over ranks), the library
+        kernels' CUDA-event times, launches and the clocks sampled during the timed region."""
+        clk = Clocks(local)
+        for _ in range(warmup):
+            wl.step()
+        torch.cuda.synchronize()
+        barrier()
+        R.profile_reset()
+        R.profile_enable(True)
+        n0 = R.launch_count()
+        torch.cuda.synchronize()
+        barrier()
+        tw0, te0 = time.perf_counter(), time.time()
+        e0.record(stream)
+        keep = None
+        for _ in range(steps):
+            keep = wl.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tw, te1 = time.perf_counter() - tw0, time.time()
+        barrier()
+        launches = R.launch_count() - n0
+        R.profile_enable(False)
+        clocks = clk.stop(te0, te1)
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        ks = {kid: R.profile_read(kid) for kid in wl.kernels()}
+        plan_ms, plan_n = R.profile_read(R.PROF_PLAN)
+        del keep
+        return dict(ms=ms, clocks=clocks, launches=launches, wall=tw, region_s=te1 - te0, ks=ks,
+                    plan_ms=plan_ms / plan_n if plan_n else None)
+
+    def roofline(wl, m, steps, fp32, traffic=None):
+        """Roofline of the step's dominant library kernel (the largest device time), and the same
+        figures for every kernel of the step."""
+        table = wl.kernels()
+        rows = {}
+        for kid, (name, work, bound) in table.items():
+            k_ms, k_n = m["ks"][kid]
+            if k_n == 0:
+                continue
+            peak, unit, src, other = choose_peak(bound, pk, pk_src, m["region_s"], m["clocks"], fp32)
+            per_step = k_ms / steps
+            achieved = work / (per_step * 1e-3) / (1e9 if unit == "GB/s" else 1e12)
+            r = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                 "kernel": name, "kernel_ms": k_ms / k_n, "kernel_launches_per_step": k_n / steps,
+                 "kernel_ms_per_step": per_step, "peak_source": src}
+            if other is not None:
+                r["frac_other_bf16_peak"] = achieved / other
+                r["other_bf16_peak"] = other
+            rows[kid] = r
+        if not rows:
+            return None, []
+        dom = max(rows, key=lambda k: rows[k]["kernel_ms_per_step"])
+        main = dict(rows[dom])
+        main["traffic"] = traffic.get(dom) if traffic else None
+        return main, [rows[k] for k in sorted(rows, key=lambda k: -rows[k]["kernel_ms_per_step"])]
+
+    # FP32 CUDA-core peak (the FP32 form's roofline denominator), clocks sampled around it
+    fp32 = None
+    if rank == 0:
+        clk = Clocks(local)
+        R.peak_fma_f32(1 << 14)
+        te0 = time.time()
+        tf, fms = R.peak_fma_f32(1 << 20)
+        te1 = time.time()
+        fp32 = {"tflops": tf, "ms": fms, "clocks": clk.stop(te0, te1),
+                "what": "relnn_peak_fma_f32: 296 blocks x 1024 threads x 8 independent FMA chains x 2^20 steps"}
+
     wl = WORKLOADS[args.config](args)
     wl.to_device(dev)
 
     # ------------------------------------------------------------ timed region (device inputs)
-    clk = Clocks(local)
-    for _ in range(args.warmup):
-        wl.step()
-    torch.cuda.synchronize()
-    barrier()
-    R.profile_reset()
-    R.profile_enable(True)
-    n_launch0 = R.launch_count()
-    torch.cuda.synchronize()
-    barrier()
-    t_wall0 = time.perf_counter()
-    t_epoch0 = time.time()
-    e0.record(stream)
-    keep = None
-    for _ in range(args.steps):
-        keep = wl.step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall0
-    t_epoch1 = time.time()
-    barrier()
-    gpu_launches = R.launch_count() - n_launch0
-    R.profile_enable(False)
-    clocks = clk.stop(t_epoch0, t_epoch1)
-    value, t_step = job_throughput(e0.elapsed_time(e1) / args.steps, wl.matched, dev)
-    kid, kname, flops = wl.roofline_kernel()  # algorithmic FLOP (or bytes) of the kernel's launches in one step
-    k_ms, k_n = R.profile_read(kid)
-    plan_ms, plan_n = R.profile_read(R.PROF_PLAN)
-    del keep
-
-    pk, pk_src = peaks()
-    k_avg = k_ms / max(k_n, 1)
-    achieved = flops / (k_ms / args.steps * 1e-3) / 1e12
-    bound, peak, peak_src, r_unit = "tensor", pk["bf16_tflops_sustained"], f"{pk_src} bf16 sustained", "TFLOP/s"
-    if hasattr(wl, "roofline_peak"):
-        bound, peak, peak_src = wl.roofline_peak()
-    if bound == "hbm":  # the work is algorithmic bytes
-        achieved, peak, peak_src, r_unit = achieved * 1e3, pk["hbm_gbs"], f"{pk_src} HBM copy bandwidth", "GB/s"
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": r_unit, "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC_PER_LAUNCH if (wl.name == "c2" and args.n_tuples is None
-                                                     and args.n_keys is None) else None, "kernel": kname,
-                "kernel_ms": k_avg, "kernel_launches_per_step": k_n / args.steps, "peak_source": peak_src}
+    m = measure(wl, args.steps, args.warmup)
+    value, t_step = job_throughput(m["ms"], wl.matched, dev)
+    traffic = getattr(wl, "ncu_traffic", lambda: None)()
+    rl, rl_all = roofline(wl, m, args.steps, fp32, traffic)
 
     extras = {} if args.no_extras else wl.extras(timer, args.steps)
-    extras["plan_ms"] = plan_ms / plan_n if plan_n else None
+    extras["plan_ms"] = m["plan_ms"]
+    extras["kernels"] = rl_all
 
     # ------------------------------------------------------------ end to end (host buffers)
     h2d, d2h = wl.e2e_setup()
@@ -976,21 +1104,51 @@ def run_relnn(args):
     if rank == 0 and not args.no_cpu_baseline:
         rate, desc = wl.cpu_rate(args.cpu_sample)
         cpu = {"value": rate, "unit": UNIT, "cores": cores(), "kind": "oracle", "sample": desc}
+    describe, matched = wl.describe(), wl.matched
+    del wl
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------------------ the other configurations
+    subs = {}
+    if rank == 0 and args.config == "c2" and not args.no_subrecords:
+        for name, steps in (("c3", 40), ("c4", 40), ("c1b", 40)):
+            sa = argparse.Namespace(**vars(args))
+            sa.n_tuples = sa.n_keys = None
+            sw = WORKLOADS[name](sa)
+            sw.to_device(dev)
+            sm = measure(sw, steps, 3)
+            srl, srl_all = roofline(sw, sm, steps, fp32)
+            rec = {"value": sw.matched / (sm["ms"] * 1e-3), "unit": UNIT, "ms_per_step": sm["ms"], "steps": steps,
+                   "warmup": 3, "config": {"workload": sw.describe(), "matched_tuples_per_step": sw.matched},
+                   "roofline": srl, "kernels": srl_all, "clocks": sm["clocks"], "gpu_launches": sm["launches"],
+                   "plan_ms": sm["plan_ms"]}
+            rec.update(sw.extras(timer, steps))
+            subs[name] = rec
+            del sw
+            torch.cuda.empty_cache()
+        if not args.no_serving:
+            st = serving_stats(args.sub_queries, args.sub_cmp_queries, local, with_cpu=False)
+            st["config"]["workload"] += (f" (shortened to the first {args.sub_queries} queries of the trace; the "
+                                         f"torch comparator on the first {args.sub_cmp_queries})")
+            subs["c5"] = st
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded Zipf/uniform relations; no dataset)",
-            "config": {"workload": wl.describe(), "matched_tuples_per_step": wl.matched,
+            "config": {"workload": describe, "matched_tuples_per_step": matched,
                        "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": world * wl.matched / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "roofline": rl, "cpu_baseline": cpu,
+            "e2e": {"value": world * matched / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": gpu_launches, "clocks": clocks, "wall_s_timed": t_wall,
+            "gpu_launches": m["launches"], "clocks": m["clocks"], "wall_s_timed": m["wall"],
+            "fp32_peak": fp32,
         }
         line.update(extras)
+        if subs:
+            line["subrecords"] = subs
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

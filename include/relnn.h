@@ -80,6 +80,15 @@ typedef enum relnn_act_t { RELNN_ACT_NONE = 0, RELNN_ACT_RELU = 1 } relnn_act_t;
                                          backward sends dOut there only (times ReLU' at it), so it
                                          needs a forward of the same plan first.                   */
 
+#define RELNN_FLAG_PER_TUPLE 0x400u   /* BF16 form without an activation: apply the Linear to every
+                                         matched tuple and then SUM (the order of the rule as
+                                         written), instead of the default for such rules, which
+                                         sums each output row's Concat rows first and applies the
+                                         Linear once per row (SUM commutes with a linear map;
+                                         paper Sec. 2.2 alpha, Sec. 6 hybrid rewrites). Both give
+                                         the rule's result; they differ in the order of f32
+                                         additions and in speed.                                   */
+
 /* Device status codes (relnn_last_device_error) */
 #define RELNN_DEV_OK 0
 #define RELNN_DEV_TIMEOUT 1           /* a bounded spin/mbarrier wait gave up                         */
@@ -428,6 +437,8 @@ relnn_status relnn_stream_destroy(relnn_stream_t s);
 #define RELNN_PROF_BWD_TC 3      /* tensor-core backward kernels                                   */
 #define RELNN_PROF_BWD_FP32 4    /* FP32-form backward kernels                                     */
 #define RELNN_PROF_PLAN 5        /* content track (whole relnn_rule_plan)                          */
+#define RELNN_PROF_AGG_FWD 6     /* aggregate-first forward kernel (linear SUM rules)              */
+#define RELNN_PROF_AGG_BWD 7     /* aggregate-first backward kernel (one launch per pass)          */
 
 /* Number of kernels this library has launched since it was loaded (host counter). */
 uint64_t relnn_launch_count(void);
@@ -438,6 +449,11 @@ relnn_status relnn_profile_enable(int32_t on);
  * accumulated since the last reset. */
 relnn_status relnn_profile_read(int32_t id, double* total_ms, int64_t* launches);
 relnn_status relnn_profile_reset(void);
+/* sync. FP32 CUDA-core throughput probe: one launch of 2 x SMs blocks of 1024 threads, each thread
+ * running 8 independent FMA chains for `iters` steps, timed by CUDA events on `stream` after one
+ * warm-up launch. *tflops = 16 x iters x threads / time (FMA = 2 FLOP); *ms (may be NULL) = the
+ * launch's time. The denominator of the FP32 form's roofline. Errors: EINVAL, ECUDA. */
+relnn_status relnn_peak_fma_f32(int32_t iters, double* tflops, double* ms, void* stream);
 
 #ifdef __cplusplus
 }

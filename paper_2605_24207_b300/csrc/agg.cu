@@ -1,0 +1,1091 @@
+// Aggregate-first evaluation of linear SUM rules on tcgen05 tensor cores (sm_103a).
+//
+// A join rule without an activation, H'(dst; SUM(W Concat(z_src, z_dst) + b)) (Sec. 3.1 join rule:
+// T_tau with tau = Linear, then alpha = SUM over the tuples B_t of a key, Sec. 2.2), is linear in its
+// Concat rows, so the SUM commutes with the transformation:
+//     Out[k] = sum_{t in B_k} (W X_t + b) = W S[k] + n_k b,     S[k] = sum_{t in B_k} X_t,
+// with S[k] = [sum z[hs_t] | sum z[hd_t]]. It is one of the hybrid content/embedding rewrites the
+// paper lists as future work (Sec. 6: transformations applied once per node instead of once per
+// edge): the tensor cores run once per output row instead of once per matched tuple, and the
+// per-tuple work is a gather-sum of bf16 rows. The BF16 form's precision is kept: the f32 sums are
+// split into a bf16 pair S = S_hi + S_lo (about 16 significant bits) and both halves are multiplied
+// by the bf16 W with f32 accumulation.
+//
+// The same kernel evaluates the linear backward (the fit of Sec. 2.3; embeddings are parameters,
+// Sec. 3.6). With dY_t = dOut[seg_t] (SUM broadcasts the row gradient to its tuples):
+//     dz[h] = G_s[h] W_s + G_d[h] W_d,    G_s[h] = sum_{t: hs_t = h} dOut[seg_t]
+//                                         G_d[h] = sum_{t: hd_t = h} dOut[seg_t]
+//     dW_s = G_s^T Z,  dW_d = G_d^T Z,    db = sum_k n_k dOut[k]
+// (W_s, W_d: the column blocks of W that multiply z_src and z_dst). A pass takes the tuples in src
+// order (G_s; every H row, so dz is written once) or in dst order (G_d; runs of equal dst H rows,
+// added): per H row a gather-sum of dOut rows and one GEMM row of dz; G^T Z is a second GEMM whose
+// K dimension is the H rows, accumulated over all tiles of the CTA in TMEM. db is summed in f32 from
+// the unrounded dOut by the pass that makes its bf16 copy.
+//
+// Virtual rows: the tuples of a destination row are cut into chunks of at most kChunk tuples (one
+// virtual row each), which bounds a producer warp's unit of work; a row cut into several chunks
+// leaves one partial per chunk, added in chunk order by the fix-up (two levels for rows with many
+// chunks). Summation order: a chunk's tuples are summed in L-strided groups (fixed), the groups by a
+// butterfly, the chunks in order: results are deterministic.
+//
+// Roles (512 threads, one CTA per SM, persistent over tiles of N virtual rows):
+//   warps 0-6, 12-15  producers: take the tile's virtual rows one at a time from a shared counter,
+//                     gather-sum the rows' Concat parts in f32, write S_hi / S_lo into 128B-swizzled
+//                     K-major stages; in a backward pass also the row's z (B operand of G^T Z)
+//   warp 7            TMEM allocation; lane 0 stages A (W, or a W^T block) once by TMA and issues
+//                     tcgen05.mma: D[f][row] = sum_k A[f][k] S[row][k] over both halves
+//   warps 8-11        epilogue (TMEM lane quarter = warp % 4): Out row = D + n b (or the chunk's
+//                     partial); after the last tile of a backward pass, the CTA's dW and db partials
+#include "agg.cuh"
+#include "primitives.cuh"
+#include "tc.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace relnn {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 512;
+constexpr int kMmaWarp = 7;
+constexpr int kEpiWarp0 = 8;
+constexpr int kEpiWarps = 4;
+constexpr int kProdWarps = 11;                 // warps 0-6 and 12-15
+constexpr int kProdThreads = kProdWarps * 32;
+constexpr int kMaxParts = 2;
+constexpr int kMaxMeta = 4;                    // tile rows / 32 (N <= 128)
+constexpr int kUnroll = 8;                     // row loads in flight per lane
+constexpr int kChunk = 32;                     // tuples per virtual row (one index per lane)
+constexpr int kFixChunk = 256;                 // chunk partials one fix-up block adds
+constexpr int kSmemLimit = 227 * 1024;
+
+struct AggArgs {
+    const int4* vr;                            // virtual rows {t0, n, row, part}
+    int64_t nv, n_tiles;
+    // Concat parts, in processing order: gather index per tuple, bf16 table, width, kind (0: a
+    // different row per tuple; 1: few distinct rows per virtual row, summed as count x row), and
+    // the part's first column in A's K dimension (a multiple of 64)
+    const int32_t* gidx[kMaxParts];
+    const uint16_t* tbl[kMaxParts];
+    int width[kMaxParts], kind[kMaxParts], kofs[kMaxParts];
+    int n_parts, n_kb, m_blocks, n_feat;
+    const float* bias;                         // forward: + n * bias[f]
+    float* out;                                // [rows][n_feat] (nullptr: no output rows)
+    float* vpart;                              // [partials][n_feat]
+    int accumulate, tile_n, stages;
+    uint32_t idesc, tmem_cols;
+    int* status;
+    // backward pass: dW_part += G^T Z[row]
+    const uint16_t* zrows;                     // bf16 [rows][d_z]
+    int d_z, z_blocks, m_dw;
+    float* dw_part;                            // [grid][n_g][d_z]
+    int n_g;
+    uint32_t idesc_dw, dw_col;
+};
+
+__device__ __forceinline__ void add8(float (&acc)[8], float (&cmp)[8], const uint4& u, bool kahan) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float lo = __uint_as_float(w[i] << 16), hi = __uint_as_float(w[i] & 0xffff0000u);
+        if (kahan) {
+            kahan_add(acc[2 * i], cmp[2 * i], lo);
+            kahan_add(acc[2 * i + 1], cmp[2 * i + 1], hi);
+        } else {
+            acc[2 * i] += lo;
+            acc[2 * i + 1] += hi;
+        }
+    }
+}
+
+// Sum over the virtual row's tuples of table rows (bf16, `w` elements) for this lane's 16-byte
+// chunk: `ix` holds lane j's tuple index (j < n). Returns the f32 sums of the chunk's 8 elements in
+// every lane of the chunk (groups of w / 8 lanes share nothing but the final butterfly).
+template <bool KAHAN>
+__device__ __forceinline__ void part_sum(const uint16_t* __restrict__ tbl, int w, int kind, int ix, int n, int lane,
+                                         float (&acc)[8]) {
+    const int L = w >> 3;  // lanes per table row (a power of two <= 32)
+    const int G = 32 / L;  // tuples per warp step
+    const int grp = lane / L, ch = lane - grp * L;
+    const uint4* __restrict__ base = reinterpret_cast<const uint4*>(tbl) + ch;
+    float cmp[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = cmp[i] = 0.f;
+    if (kind == 0) {
+        for (int j0 = 0; j0 < n; j0 += kUnroll * G) {
+            uint4 u[kUnroll];
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) {
+                const int j = j0 + q * G + grp;
+                const int r = __shfl_sync(0xffffffffu, ix, j & 31);
+                u[q] = j < n ? __ldg(base + (int64_t)r * L) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) add8(acc, cmp, u[q], KAHAN);
+        }
+    } else {
+        // distinct rows among the tuples, each loaded once and weighted by its multiplicity
+        const bool valid = lane < n;
+        unsigned rem = __ballot_sync(0xffffffffu, valid);
+        while (rem) {
+            const int r = __shfl_sync(0xffffffffu, ix, __ffs(rem) - 1);
+            const unsigned mm = __ballot_sync(0xffffffffu, valid && ix == r);
+            rem &= ~mm;
+            if (grp == 0) {
+                const uint4 u = __ldg(base + (int64_t)r * L);
+                const float c = (float)__popc(mm);
+                const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    // c <= 32 times a bf16 value is exact in f32
+                    const float lo = c * __uint_as_float(wd[i] << 16), hi = c * __uint_as_float(wd[i] & 0xffff0000u);
+                    if (KAHAN) {
+                        kahan_add(acc[2 * i], cmp[2 * i], lo);
+                        kahan_add(acc[2 * i + 1], cmp[2 * i + 1], hi);
+                    } else {
+                        acc[2 * i] += lo;
+                        acc[2 * i + 1] += hi;
+                    }
+                }
+            }
+        }
+    }
+    // groups of the warp: butterfly (each pairwise add is commutative, so every lane of a chunk
+    // ends with the same value)
+    for (int off = L; off < 32; off <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (KAHAN) {
+                const float s2 = __shfl_xor_sync(0xffffffffu, acc[i], off);
+                const float c2 = __shfl_xor_sync(0xffffffffu, cmp[i], off);
+                // (s1 - c1) + (s2 - c2), compensated; symmetric in the two operands
+                const float a1 = acc[i] - cmp[i], a2 = s2 - c2;
+                acc[i] = a1 + a2;
+                cmp[i] = 0.f;
+            } else {
+                acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+            }
+        }
+    }
+    if (KAHAN) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] -= cmp[i];
+    }
+}
+
+template <bool BWD, bool KAHAN>
+__global__ void __launch_bounds__(kThreads, 1)
+agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ AggArgs a) {
+    extern __shared__ uint8_t dyn_smem[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~(uintptr_t)1023);
+    const int N = a.tile_n;
+    const uint32_t a_bytes = (uint32_t)a.n_kb * a.m_blocks * 16384u;
+    const uint32_t blk = (uint32_t)N * 128u;  // one 64-column block of a stage
+    const uint32_t stage_bytes = (uint32_t)(2 * a.n_kb + a.z_blocks) * blk;
+    uint8_t* a_smem = base;
+    uint8_t* st_smem = base + a_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(st_smem + (size_t)a.stages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + a.stages;
+    uint64_t* tfull = bars + 2 * a.stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wbar = tempty + 2;
+    uint64_t* drain = wbar + 1;
+    int* ctr = reinterpret_cast<int*>(drain + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctr + a.stages);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(smem_u32(&full[s]), kProdThreads);
+            mbar_init(smem_u32(&empty[s]), 1);
+            ctr[s] = 0;
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&tfull[i]), 1);
+            mbar_init(smem_u32(&tempty[i]), 32 * kEpiWarps);
+        }
+        mbar_init(smem_u32(wbar), 1);
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    // zero the stages (columns a part does not fill stay zero)
+    for (uint32_t i = tid; i < (uint32_t)a.stages * stage_bytes / 16u; i += kThreads)
+        st_shared_v4(smem_u32(st_smem) + i * 16u, 0u, 0u, 0u, 0u);
+    fence_proxy_async();
+    if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t acc_stride = (uint32_t)a.m_blocks * N;
+    const bool producer = warp < kMmaWarp || warp >= kEpiWarp0 + kEpiWarps;
+
+    if (producer) {
+        // ------------------------------------------------------------------ producers
+        const int meta_n = N / 32;
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
+            const int s = lt % a.stages;
+            const uint32_t use = (uint32_t)(lt / a.stages);
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&empty[s]), (use & 1u) ^ 1u, a.status, abort_flag))) break;
+            const uint32_t sb = smem_u32(st_smem + (size_t)s * stage_bytes);
+            const int64_t v0 = tile * N;
+            // the tile's virtual rows: lane l of register c holds row 32 c + l
+            int4 meta[kMaxMeta];
+#pragma unroll
+            for (int c = 0; c < kMaxMeta; ++c) {
+                const int64_t v = v0 + 32 * c + lane;
+                meta[c] = (c < meta_n && v < a.nv) ? __ldg(a.vr + v) : make_int4(0, 0, -1, -1);
+            }
+            // rows are taken one at a time; each warp's last take fails, so a tile use consumes
+            // exactly N + kProdWarps values of the stage's counter
+            const int cbase = (int)use * (N + kProdWarps);
+            auto take = [&]() {
+                int r = 0;
+                if (lane == 0) r = atomicAdd(ctr + s, 1) - cbase;
+                return __shfl_sync(0xffffffffu, r, 0);
+            };
+            auto row_meta = [&](int r) {
+                const int c = r >> 5, l = r & 31;
+                int4 m;
+                m.x = __shfl_sync(0xffffffffu, c == 0 ? meta[0].x : c == 1 ? meta[1].x : c == 2 ? meta[2].x : meta[3].x, l);
+                m.y = __shfl_sync(0xffffffffu, c == 0 ? meta[0].y : c == 1 ? meta[1].y : c == 2 ? meta[2].y : meta[3].y, l);
+                m.z = __shfl_sync(0xffffffffu, c == 0 ? meta[0].z : c == 1 ? meta[1].z : c == 2 ? meta[2].z : meta[3].z, l);
+                return m;
+            };
+            // the next row's tuple indices are loaded while the current row is summed
+            auto load_idx = [&](const int4& m, int (&ix)[kMaxParts]) {
+#pragma unroll
+                for (int p = 0; p < kMaxParts; ++p)
+                    ix[p] = (p < a.n_parts && m.z >= 0 && lane < m.y) ? __ldg(a.gidx[p] + m.x + lane) : -1;
+            };
+            int r_next = take();
+            int4 m_next = make_int4(0, 0, -1, -1);
+            int ix_next[kMaxParts];
+            if (r_next < N) m_next = row_meta(r_next);
+            load_idx(m_next, ix_next);
+            while (r_next < N) {
+                const int r = r_next;
+                const int4 m = m_next;
+                int ix[kMaxParts];
+#pragma unroll
+                for (int p = 0; p < kMaxParts; ++p) ix[p] = ix_next[p];
+                r_next = take();
+                m_next = r_next < N ? row_meta(r_next) : make_int4(0, 0, -1, -1);
+                load_idx(m_next, ix_next);
+                const uint32_t rsw = (uint32_t)(r & 7);
+                if (m.z < 0) {
+                    // past the last virtual row: zero the row's S blocks (stale rows would add into dW)
+                    for (int i = lane; i < 2 * a.n_kb * 8; i += 32)
+                        st_shared_v4(sb + (uint32_t)(i >> 3) * blk + (uint32_t)r * 128u + (uint32_t)(i & 7) * 16u, 0u, 0u,
+                                     0u, 0u);
+                    continue;
+                }
+                // backward: the row's z (B operand of G^T Z), loaded now and stored at the end
+                uint4 zc = make_uint4(0u, 0u, 0u, 0u);
+                const int zch = BWD ? a.d_z >> 3 : 0;
+                if (BWD && lane < zch) zc = __ldg(reinterpret_cast<const uint4*>(a.zrows + (int64_t)m.z * a.d_z) + lane);
+#pragma unroll
+                for (int p = 0; p < kMaxParts; ++p) {
+                    if (p >= a.n_parts) break;
+                    float acc[8];
+                    part_sum<KAHAN>(a.tbl[p], a.width[p], a.kind[p], ix[p], m.y, lane, acc);
+                    const int L = a.width[p] >> 3;
+                    if (lane < L) {
+                        // S = S_hi + S_lo, each rounded to bf16 (nearest even)
+                        uint32_t hi[4], lo[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            hi[i] = pack_bf16x2(acc[2 * i], acc[2 * i + 1]);
+                            const float h0 = __uint_as_float(hi[i] << 16), h1 = __uint_as_float(hi[i] & 0xffff0000u);
+                            lo[i] = pack_bf16x2(acc[2 * i] - h0, acc[2 * i + 1] - h1);
+                        }
+                        const int k = a.kofs[p] + 8 * lane;  // first element of this lane's chunk in K
+                        const uint32_t off = (uint32_t)(k >> 6) * blk + (uint32_t)r * 128u +
+                                             ((((uint32_t)(k >> 3) & 7u) ^ rsw) << 4);
+                        st_shared_v4(sb + off, hi[0], hi[1], hi[2], hi[3]);
+                        st_shared_v4(sb + (uint32_t)a.n_kb * blk + off, lo[0], lo[1], lo[2], lo[3]);
+                    }
+                }
+                if (BWD && lane < zch)
+                    st_shared_v4(sb + (uint32_t)(2 * a.n_kb + (lane >> 3)) * blk + (uint32_t)r * 128u +
+                                     ((((uint32_t)lane & 7u) ^ rsw) << 4),
+                                 zc.x, zc.y, zc.z, zc.w);
+            }
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&full[s]));
+        }
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t wb = smem_u32(wbar);
+            mbar_arrive_expect_tx(wb, a_bytes);
+            for (int kb = 0; kb < a.n_kb; ++kb)
+                for (int mb = 0; mb < a.m_blocks; ++mb)
+                    tma_load_2d(smem_u32(a_smem + (size_t)(kb * a.m_blocks + mb) * 16384u), &amap, kb * 64, mb * 128, wb);
+            bool ok = mbar_wait(wb, 0, a.status, abort_flag);
+            tc_fence_after();
+            int lt = 0;
+            for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++lt) {
+                const int s = lt % a.stages;
+                const uint32_t use = (uint32_t)(lt / a.stages);
+                const int acc = lt & 1;
+                const uint32_t ause = (uint32_t)(lt >> 1);
+                if (!mbar_wait(smem_u32(&tempty[acc]), (ause & 1u) ^ 1u, a.status, abort_flag)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&full[s]), use & 1u, a.status, abort_flag)) { ok = false; break; }
+                fence_proxy_async();
+                tc_fence_after();
+                const uint32_t sb = smem_u32(st_smem + (size_t)s * stage_bytes);
+                const uint32_t d_acc = tmem_base + (uint32_t)acc * acc_stride;
+                for (int mb = 0; mb < a.m_blocks; ++mb) {
+                    uint32_t accum = 0;
+                    for (int kb = 0; kb < a.n_kb; ++kb) {
+                        const uint32_t ab = smem_u32(a_smem + (size_t)(kb * a.m_blocks + mb) * 16384u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint64_t adesc = sw128_kmajor_desc(ab + k * 32);
+#pragma unroll
+                            for (int hl = 0; hl < 2; ++hl) {
+                                const uint64_t bdesc = sw128_kmajor_desc(sb + (uint32_t)(hl * a.n_kb + kb) * blk + k * 32);
+                                mma_bf16(d_acc + (uint32_t)mb * N, adesc, bdesc, a.idesc, accum);
+                                accum = 1;
+                            }
+                        }
+                    }
+                }
+                if (BWD) {
+                    // G^T Z: K = the tile's rows (16 per instruction), both operands read MN-major
+                    // from the staged rows
+                    const uint32_t zb = sb + (uint32_t)(2 * a.n_kb) * blk;
+                    for (int step = 0; step < N / 16; ++step) {
+                        for (int mbw = 0; mbw < a.m_dw; ++mbw) {
+#pragma unroll
+                            for (int hl = 0; hl < 2; ++hl) {
+                                const uint32_t accw = (lt > 0 || step > 0 || hl > 0) ? 1u : 0u;
+                                const uint64_t ad = sw128_mnmajor_desc(
+                                    sb + (uint32_t)(hl * a.n_kb + 2 * mbw) * blk + (uint32_t)step * 2048u, blk);
+                                const uint64_t bd = sw128_mnmajor_desc(zb + (uint32_t)step * 2048u, blk);
+                                mma_bf16(tmem_base + a.dw_col + (uint32_t)mbw * a.d_z, ad, bd, a.idesc_dw, accw);
+                            }
+                        }
+                    }
+                }
+                mma_commit(smem_u32(&empty[s]));
+                mma_commit(smem_u32(&tfull[acc]));
+            }
+            // every issued MMA has finished before the dW read-out and the TMEM release
+            mma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0, a.status, abort_flag);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------ epilogue
+        const int q = warp & 3;
+        float bias_r[2];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+            const int o = mb * 128 + 32 * q + lane;
+            bias_r[mb] = (a.bias && mb < a.m_blocks && o < a.n_feat) ? a.bias[o] : 0.f;
+        }
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            const uint32_t ause = (uint32_t)(lt >> 1);
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), ause & 1u, a.status, abort_flag))) break;
+            tc_fence_after();
+            const int64_t v0 = tile * N;
+            for (int c = 0; c < N / 32; ++c) {
+                const int64_t vb = v0 + 32 * c;
+                if (vb >= a.nv) break;
+                const int4 mt = vb + lane < a.nv ? __ldg(a.vr + vb + lane) : make_int4(0, 0, -1, -1);
+                for (int mb = 0; mb < a.m_blocks; ++mb) {
+                    if (mb * 128 + 32 * q >= a.n_feat) continue;
+                    const int o = mb * 128 + 32 * q + lane;
+                    const bool o_ok = o < a.n_feat && a.out != nullptr;
+                    const float bo = mb == 0 ? bias_r[0] : bias_r[1];
+                    uint32_t v[32];
+                    tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_stride +
+                                           (uint32_t)mb * N + (uint32_t)(32 * c), v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int row = __shfl_sync(0xffffffffu, mt.z, j);
+                        const int part = __shfl_sync(0xffffffffu, mt.w, j);
+                        const int nj = __shfl_sync(0xffffffffu, mt.y, j);
+                        if (row < 0) break;  // past the last virtual row (warp-uniform)
+                        if (o_ok) {
+                            const float y = __uint_as_float(v[j]) + (float)nj * bo;
+                            if (part >= 0) __stcg(a.vpart + (int64_t)part * a.n_feat + o, y);
+                            else emit_out(a.out + (int64_t)row * a.n_feat + o, y, a.accumulate);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&tempty[acc]));
+        }
+        if (BWD) {
+            // this CTA's dW (TMEM lane = G feature, columns = z features)
+            if (__all_sync(0xffffffffu, mbar_wait(smem_u32(drain), 0, a.status, abort_flag))) {
+                tc_fence_after();
+                for (int mbw = 0; mbw < a.m_dw; ++mbw) {
+                    const int g = mbw * 128 + 32 * q + lane;
+                    float* dst = a.dw_part + ((int64_t)blockIdx.x * a.n_g + g) * a.d_z;
+                    for (int c = 0; c < a.d_z / 32; ++c) {
+                        uint32_t v[32];
+                        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * q) << 16) + a.dw_col + (uint32_t)mbw * a.d_z +
+                                               (uint32_t)(32 * c), v);
+                        tmem_ld_wait();
+                        if (g < a.n_g) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                *reinterpret_cast<float4*>(dst + 32 * c + j) =
+                                    make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, a.tmem_cols);
+    }
+}
+
+// ------------------------------------------------------------------------------ virtual rows
+// Sorted keys (values in [0, R)): beg[k] / end[k] = the tuple range of row k (0 / 0 when absent).
+__global__ void vr_bounds_kernel(const int32_t* __restrict__ key, int64_t m, int32_t* beg, int32_t* end) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = key[t];
+        if (t == 0 || key[t - 1] != k) beg[k] = (int32_t)t;
+        if (t == m - 1 || key[t + 1] != k) end[k] = (int32_t)(t + 1);
+    }
+}
+
+// Unsorted keys: 1 at the first tuple of every run of equal keys.
+__global__ void vr_run_flags_kernel(const int32_t* __restrict__ key, int64_t m, int32_t* flag) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+        flag[t] = (t == 0 || key[t - 1] != key[t]) ? 1 : 0;
+}
+
+// Run r (exclusive scan of the flags gives the run of each start): its tuple range and key.
+__global__ void vr_runs_kernel(const int32_t* __restrict__ key, int64_t m, const int32_t* __restrict__ rid_excl,
+                               int32_t* beg, int32_t* end, int32_t* rkey) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = key[t];
+        const bool start = t == 0 || key[t - 1] != k;
+        const int32_t r = rid_excl[t] - (start ? 0 : 1);
+        if (start) {
+            beg[r] = (int32_t)t;
+            rkey[r] = k;
+        }
+        if (t == m - 1 || key[t + 1] != k) end[r] = (int32_t)(t + 1);
+    }
+}
+
+// Chunks per row (every row of a sorted list gets one, empty or not), chunk partials per row (rows
+// of one chunk need none), and the split flag.
+__global__ void vr_count_kernel(const int32_t* __restrict__ beg, const int32_t* __restrict__ end, int64_t R,
+                                int32_t* nch, int32_t* npart, int32_t* split, int32_t* cnt_out) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t cnt = end[r] - beg[r];
+        if (cnt_out) cnt_out[r] = cnt;
+        const int32_t c = cnt > kChunk ? (cnt + kChunk - 1) / kChunk : 1;
+        nch[r] = c;
+        npart[r] = c > 1 ? c : 0;
+        split[r] = c > 1 ? 1 : 0;
+    }
+}
+
+__global__ void vr_fill_kernel(const int32_t* __restrict__ beg, const int32_t* __restrict__ end,
+                               const int32_t* __restrict__ rkey, int64_t R, const int32_t* __restrict__ voff,
+                               const int32_t* __restrict__ poff, const int32_t* __restrict__ soff, int4* vr, int4* splits) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = beg[r], cnt = end[r] - b;
+        const int32_t c = cnt > kChunk ? (cnt + kChunk - 1) / kChunk : 1;
+        const int32_t row = rkey ? rkey[r] : (int32_t)r;
+        for (int32_t i = 0; i < c; ++i)
+            vr[voff[r] + i] = make_int4(b + i * kChunk, max(0, min(kChunk, cnt - i * kChunk)), row, c > 1 ? poff[r] + i : -1);
+        if (c > 1) splits[soff[r]] = make_int4(row, poff[r], c, -1);
+    }
+}
+
+// ------------------------------------------------------------------------------ fix-up
+// One block per job {row, first partial, count, level-2 slot or -1}: the partials are added in
+// order (8 warps take every 8th, then the warps' sums are added in warp order), into the level-2
+// slot or the output row.
+__global__ void __launch_bounds__(256) agg_fix_kernel(const int4* __restrict__ jobs, int64_t n_jobs,
+                                                      const float* __restrict__ part, float* part2, float* out, int F,
+                                                      int accumulate, int kahan) {
+    __shared__ float4 red[8][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int F4 = F >> 2;
+    for (int64_t jb = blockIdx.x; jb < n_jobs; jb += gridDim.x) {
+        const int4 j = jobs[jb];
+        for (int c4 = lane; c4 < F4; c4 += 32) {
+            float s[4] = {0.f, 0.f, 0.f, 0.f}, cm[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int i = warp; i < j.z; i += 8) {
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(part + (int64_t)(j.y + i) * F) + c4);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (kahan) kahan_add(s[e], cm[e], vv[e]);
+                    else s[e] += vv[e];
+                }
+            }
+            red[warp][c4] = make_float4(s[0] - cm[0], s[1] - cm[1], s[2] - cm[2], s[3] - cm[3]);
+        }
+        __syncthreads();
+        for (int c4 = threadIdx.x; c4 < F4; c4 += blockDim.x) {
+            float s[4] = {0.f, 0.f, 0.f, 0.f}, cm[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int w = 0; w < 8; ++w) {
+                const float4 v = red[w][c4];
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (kahan) kahan_add(s[e], cm[e], vv[e]);
+                    else s[e] += vv[e];
+                }
+            }
+            float4 res = make_float4(s[0] - cm[0], s[1] - cm[1], s[2] - cm[2], s[3] - cm[3]);
+            if (j.w >= 0) {
+                reinterpret_cast<float4*>(part2 + (int64_t)j.w * F)[c4] = res;
+            } else {
+                float4* dst = reinterpret_cast<float4*>(out + (int64_t)j.x * F) + c4;
+                if (accumulate) {
+                    const float4 o = *dst;
+                    res = make_float4(o.x + res.x, o.y + res.y, o.z + res.z, o.w + res.w);
+                }
+                *dst = res;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------ operands
+// A of the forward: A[o][k] = W[o][col(k)] with every Concat part padded to `kpad` columns.
+__global__ void pack_a_fwd_kernel(const void* W, int w_bf16, int d_out, int d_in, int d, int kpad, int rows_pad,
+                                  int cols, uint16_t* out) {
+    const int n = rows_pad * cols;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int o = i / cols, k = i - o * cols;
+        const int part = k / kpad, kk = k - part * kpad;
+        uint16_t v = 0;
+        if (o < d_out && kk < d && part * d + kk < d_in) {
+            const int col = part * d + kk;
+            v = w_bf16 ? reinterpret_cast<const uint16_t*>(W)[o * d_in + col]
+                       : __bfloat16_as_ushort(__float2bfloat16_rn(reinterpret_cast<const float*>(W)[o * d_in + col]));
+        }
+        out[i] = v;
+    }
+}
+
+// A of a backward pass: A[i][o] = W[o][col0 + i] (i < d, o < d_out), zero-padded.
+__global__ void pack_a_bwd_kernel(const void* W, int w_bf16, int d_out, int d_in, int col0, int d, int rows_pad,
+                                  int cols, uint16_t* out) {
+    const int n = rows_pad * cols;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int r = i / cols, o = i - r * cols;
+        uint16_t v = 0;
+        if (r < d && o < d_out) {
+            const int idx = o * d_in + col0 + r;
+            v = w_bf16 ? reinterpret_cast<const uint16_t*>(W)[idx]
+                       : __bfloat16_as_ushort(__float2bfloat16_rn(reinterpret_cast<const float*>(W)[idx]));
+        }
+        out[i] = v;
+    }
+}
+
+// dW[g][col0 + i] = sum over CTAs (in order) of part[c][g][i].
+__global__ void agg_reduce_dw_kernel(const float* __restrict__ part, int grid, int n_g, int d_z, float* dW, int d_in,
+                                     int col0) {
+    const int64_t n = (int64_t)n_g * d_z;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int c = 0; c < grid; ++c) s += part[(int64_t)c * n + i];
+        const int64_t g = i / d_z, k = i - g * d_z;
+        dW[g * d_in + col0 + k] = s;
+    }
+}
+
+
+// dOut -> its bf16 copy (round to nearest even), and per block the partial of
+// db_b = sum_k cnt_b[k] dOut[k] (the SUM backward's bias gradient, f32 from the unrounded dOut) for up
+// to kDbBranches branches. Block i takes a contiguous range of rows; lanes hold float4 columns; the
+// warps' partials are added in warp order, the blocks' later in block order (deterministic).
+constexpr int kDbBranches = 4;
+struct CntSet {
+    const int32_t* c[kDbBranches];
+    int n;
+};
+
+__global__ void __launch_bounds__(256) dout_prep_kernel(const float* __restrict__ dout, int64_t n_out, int d_out,
+                                                        CntSet cs, int64_t rows_per_block, uint16_t* __restrict__ out_bf,
+                                                        float* __restrict__ db_part) {
+    __shared__ float4 red[8][kDbBranches][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int F4 = d_out >> 2;               // float4 per row (2..64)
+    const int LR = F4 < 32 ? F4 : 32;        // lanes per row
+    const int RPW = 32 / LR;                 // rows per warp step
+    const int FPL = F4 / LR;                 // float4 per lane (1 or 2)
+    const int g = lane / LR, c0 = lane - g * LR;
+    float4 acc[kDbBranches][2];
+#pragma unroll
+    for (int b = 0; b < kDbBranches; ++b) acc[b][0] = acc[b][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t r0 = blockIdx.x * rows_per_block, r1 = imin64(n_out, r0 + rows_per_block);
+    for (int64_t r = r0 + warp * RPW + g; r < r1; r += 8 * RPW) {
+        int32_t cnt[kDbBranches];
+#pragma unroll
+        for (int b = 0; b < kDbBranches; ++b) cnt[b] = b < cs.n ? __ldg(cs.c[b] + r) : 0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (j >= FPL) break;
+            const int c = c0 + j * LR;
+            const float4 v = __ldg(reinterpret_cast<const float4*>(dout + r * d_out) + c);
+            *reinterpret_cast<uint2*>(out_bf + r * d_out + 4 * c) = make_uint2(tc::pack_bf16x2(v.x, v.y), tc::pack_bf16x2(v.z, v.w));
+#pragma unroll
+            for (int b = 0; b < kDbBranches; ++b) {
+                const float w = (float)cnt[b];
+                acc[b][j].x = fmaf(w, v.x, acc[b][j].x);
+                acc[b][j].y = fmaf(w, v.y, acc[b][j].y);
+                acc[b][j].z = fmaf(w, v.z, acc[b][j].z);
+                acc[b][j].w = fmaf(w, v.w, acc[b][j].w);
+            }
+        }
+    }
+    // the row groups of the warp, then the warps
+    for (int off = LR; off < 32; off <<= 1) {
+#pragma unroll
+        for (int b = 0; b < kDbBranches; ++b)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                acc[b][j].x += __shfl_xor_sync(0xffffffffu, acc[b][j].x, off);
+                acc[b][j].y += __shfl_xor_sync(0xffffffffu, acc[b][j].y, off);
+                acc[b][j].z += __shfl_xor_sync(0xffffffffu, acc[b][j].z, off);
+                acc[b][j].w += __shfl_xor_sync(0xffffffffu, acc[b][j].w, off);
+            }
+    }
+    if (g == 0) {
+#pragma unroll
+        for (int b = 0; b < kDbBranches; ++b)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (j < FPL) red[warp][b][c0 + j * LR] = acc[b][j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cs.n * F4; i += blockDim.x) {
+        const int b = i / F4, c = i - b * F4;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int w = 0; w < 8; ++w) {
+            const float4 v = red[w][b][c];
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+        reinterpret_cast<float4*>(db_part + ((int64_t)blockIdx.x * kDbBranches + b) * d_out)[c] = s;
+    }
+}
+
+// db_b[f] = sum over blocks (in order, compensated) of the partials.
+__global__ void db_reduce_kernel(const float* __restrict__ part, int blocks, int d_out, int b, float* db) {
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d_out; f += gridDim.x * blockDim.x) {
+        float s = 0.f, c = 0.f;
+        for (int k = 0; k < blocks; ++k) kahan_add(s, c, part[((int64_t)k * kDbBranches + b) * d_out + f]);
+        db[f] = s - c;
+    }
+}
+
+inline int grid_for(int64_t n, int threads = 256) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 16));
+}
+
+inline bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+// Builds (once) the virtual rows of an ordered tuple list: `sorted` = the keys ascend over rows
+// 0..R-1 and every row gets at least one virtual row (an empty row writes zeros); otherwise the
+// rows are the runs of equal keys in list order.
+relnn_status ensure_vrows(VRows& V, const int32_t* key, int64_t m, int64_t R, bool sorted, cudaStream_t st) {
+    if (V.nv >= 0) return RELNN_OK;
+    DevBuf beg, end, rkey, flag;
+    int64_t rows = R;
+    if (!sorted) {
+        RELNN_TRY(flag.alloc_tmp(sizeof(int32_t) * (m + 1), st));
+        if (m > 0) { vr_run_flags_kernel<<<grid_for(m), 256, 0, st>>>(key, m, flag.as<int32_t>()); note_launch(); }
+        RELNN_TRY(exclusive_scan<int32_t>(flag.as<int32_t>(), flag.as<int32_t>(), m, flag.as<int32_t>() + m, st));
+        int32_t nr = 0;
+        RELNN_CUDA(cudaMemcpyAsync(&nr, flag.as<int32_t>() + m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RELNN_CUDA(cudaStreamSynchronize(st));
+        rows = nr;
+    }
+    const int64_t r1 = std::max<int64_t>(rows, 1);
+    RELNN_TRY(beg.alloc_tmp(sizeof(int32_t) * r1, st));
+    RELNN_TRY(end.alloc_tmp(sizeof(int32_t) * r1, st));
+    if (sorted) {
+        RELNN_CUDA(cudaMemsetAsync(beg.p, 0, sizeof(int32_t) * r1, st));
+        RELNN_CUDA(cudaMemsetAsync(end.p, 0, sizeof(int32_t) * r1, st));
+        if (m > 0) { vr_bounds_kernel<<<grid_for(m), 256, 0, st>>>(key, m, beg.as<int32_t>(), end.as<int32_t>()); note_launch(); }
+    } else {
+        RELNN_TRY(rkey.alloc_tmp(sizeof(int32_t) * r1, st));
+        if (m > 0) { vr_runs_kernel<<<grid_for(m), 256, 0, st>>>(key, m, flag.as<int32_t>(), beg.as<int32_t>(), end.as<int32_t>(),
+                                                               rkey.as<int32_t>()); note_launch(); }
+    }
+    DevBuf cnts;  // nch | npart | split, each rows + 1 (exclusive scans in place)
+    RELNN_TRY(cnts.alloc_tmp(sizeof(int32_t) * 3 * (rows + 1), st));
+    int32_t* nch = cnts.as<int32_t>();
+    int32_t* npart = nch + rows + 1;
+    int32_t* split = npart + rows + 1;
+    if (sorted) RELNN_TRY(V.cnt.alloc(sizeof(int32_t) * r1, st));
+    if (rows > 0) { vr_count_kernel<<<grid_for(rows), 256, 0, st>>>(beg.as<int32_t>(), end.as<int32_t>(), rows, nch, npart, split,
+                                                                   sorted ? V.cnt.as<int32_t>() : nullptr); note_launch(); }
+    RELNN_TRY(exclusive_scan<int32_t>(nch, nch, rows, nch + rows, st));
+    RELNN_TRY(exclusive_scan<int32_t>(npart, npart, rows, npart + rows, st));
+    RELNN_TRY(exclusive_scan<int32_t>(split, split, rows, split + rows, st));
+    int32_t tot[3] = {0, 0, 0};
+    RELNN_CUDA(cudaMemcpyAsync(&tot[0], nch + rows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaMemcpyAsync(&tot[1], npart + rows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaMemcpyAsync(&tot[2], split + rows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    const int64_t nv = tot[0], n_split = tot[2];
+    RELNN_TRY(V.vr.alloc(sizeof(int4) * std::max<int64_t>(nv, 1), st));
+    DevBuf splits;
+    RELNN_TRY(splits.alloc_tmp(sizeof(int4) * std::max<int64_t>(n_split, 1), st));
+    if (rows > 0) { vr_fill_kernel<<<grid_for(rows), 256, 0, st>>>(beg.as<int32_t>(), end.as<int32_t>(),
+                                                                  sorted ? nullptr : rkey.as<int32_t>(), rows, nch, npart,
+                                                                  split, V.vr.as<int4>(), splits.as<int4>()); note_launch(); }
+    RELNN_CUDA(cudaGetLastError());
+    // fix-up jobs of split rows (a few per heavy row): built on the host
+    std::vector<int4> sp((size_t)n_split);
+    if (n_split > 0)
+        RELNN_CUDA(cudaMemcpyAsync(sp.data(), splits.p, sizeof(int4) * n_split, cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    std::vector<int4> j1, j2;
+    int64_t l2 = 0;
+    for (const int4& s : sp) {
+        if (s.z <= kFixChunk) {
+            j1.push_back(make_int4(s.x, s.y, s.z, -1));
+        } else {
+            const int nc = (s.z + kFixChunk - 1) / kFixChunk;
+            for (int c = 0; c < nc; ++c)
+                j1.push_back(make_int4(s.x, s.y + c * kFixChunk, std::min(kFixChunk, s.z - c * kFixChunk), (int)(l2 + c)));
+            j2.push_back(make_int4(s.x, (int)l2, nc, -1));
+            l2 += nc;
+        }
+    }
+    V.n_fix1 = (int64_t)j1.size();
+    V.n_fix2 = (int64_t)j2.size();
+    V.n_l2 = l2;
+    if (!j1.empty()) {
+        RELNN_TRY(V.fix1.alloc(sizeof(int4) * j1.size(), st));
+        RELNN_CUDA(cudaMemcpyAsync(V.fix1.p, j1.data(), sizeof(int4) * j1.size(), cudaMemcpyHostToDevice, st));
+    }
+    if (!j2.empty()) {
+        RELNN_TRY(V.fix2.alloc(sizeof(int4) * j2.size(), st));
+        RELNN_CUDA(cudaMemcpyAsync(V.fix2.p, j2.data(), sizeof(int4) * j2.size(), cudaMemcpyHostToDevice, st));
+    }
+    if (!j1.empty()) RELNN_CUDA(cudaStreamSynchronize(st));  // the job vectors are copied from
+    V.n_parts = tot[1];
+    V.nv = nv;
+    return RELNN_OK;
+}
+
+// Tile rows and pipeline depth: the largest N (128, 64, 32) that leaves two stages in shared
+// memory and fits TMEM.
+struct AggCfg {
+    int N = 0, stages = 0;
+    uint32_t tmem_cols = 0, dw_col = 0;
+    size_t smem = 0;
+};
+
+AggCfg agg_config(int n_kb, int m_blocks, bool bwd, int z_blocks, int m_dw, int d_z) {
+    AggCfg c;
+    const uint32_t a_bytes = (uint32_t)n_kb * m_blocks * 16384u;
+    // two stages at the largest N; a single stage of 32 rows as the last resort (wide A operands)
+    const int tries[4][2] = {{128, 2}, {64, 2}, {32, 2}, {32, 1}};
+    for (const auto& tr : tries) {
+        const int N = tr[0];
+        const size_t stage = (size_t)(2 * n_kb + z_blocks) * N * 128;
+        const size_t fixed = 1024 + a_bytes + 512;
+        if (fixed + stage > (size_t)kSmemLimit) continue;
+        const int stages = (int)std::min<size_t>(4, (kSmemLimit - fixed) / stage);
+        const uint32_t cols = 2u * m_blocks * N + (bwd ? (uint32_t)(m_dw * d_z) : 0u);
+        if (stages >= tr[1] && cols <= 512) {
+            c.N = N;
+            c.stages = stages;
+            c.dw_col = 2u * m_blocks * N;
+            uint32_t t = 32;
+            while (t < cols) t <<= 1;
+            c.tmem_cols = t;
+            c.smem = fixed + (size_t)stages * stage;
+            return c;
+        }
+    }
+    return c;
+}
+
+template <bool BWD, bool KAHAN>
+relnn_status launch_agg(const CUtensorMap& amap, const AggArgs& a, size_t smem, int grid, cudaStream_t st, int prof) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        RELNN_CUDA(cudaFuncSetAttribute(agg_tc_kernel<BWD, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        attr_set = true;
+    }
+    ProfToken pt = prof_begin(prof, st);
+    { agg_tc_kernel<BWD, KAHAN><<<grid, kThreads, smem, st>>>(amap, a); note_launch(); }
+    prof_end(pt, st);
+    RELNN_CUDA(cudaGetLastError());
+    return RELNN_OK;
+}
+
+// Fix-up of the split rows of one launch: partial rows in p.vpart (level-2 sums after them).
+relnn_status agg_fixup(const VRows& V, const float* vpart, float* vpart2, float* out, int F, bool accumulate, bool kahan,
+                       cudaStream_t st) {
+    if (!out || V.n_fix1 == 0) return RELNN_OK;
+    ProfToken pt = prof_begin(RELNN_PROF_FIXUP, st);
+    { agg_fix_kernel<<<(int)std::min<int64_t>(V.n_fix1, 65535), 256, 0, st>>>(V.fix1.as<int4>(), V.n_fix1, vpart, vpart2, out, F,
+                                                                            accumulate ? 1 : 0, kahan ? 1 : 0); note_launch(); }
+    if (V.n_fix2 > 0)
+        { agg_fix_kernel<<<(int)std::min<int64_t>(V.n_fix2, 65535), 256, 0, st>>>(V.fix2.as<int4>(), V.n_fix2, vpart2, nullptr, out,
+                                                                                F, accumulate ? 1 : 0, kahan ? 1 : 0); note_launch(); }
+    prof_end(pt, st);
+    RELNN_CUDA(cudaGetLastError());
+    return RELNN_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Forward: A = W with each Concat part padded to 64 columns; M = output features.
+AggCfg fwd_cfg(const Plan& p) {
+    const int n_parts = p.concat_dst ? 2 : 1;
+    const int kpad = ((p.d + 63) / 64) * 64;
+    return agg_config(n_parts * kpad / 64, (p.d_out + 127) / 128, false, 0, 0, 0);
+}
+
+// Backward pass: A = a W^T block (M = z features, K = output features), B of G^T Z = z rows.
+AggCfg bwd_cfg(const Plan& p) {
+    return agg_config((p.d_out + 63) / 64, (p.d + 127) / 128, true, (p.d + 63) / 64, (p.d_out + 127) / 128, p.d);
+}
+
+}  // namespace
+
+bool agg_forward_ok(const Plan& p, const CallIO& io, const float* out) {
+    if (!aligned16(out)) return false;  // the fix-up adds partial rows as float4
+    if (!p.bf16 || p.identity || p.act != RELNN_ACT_NONE) return false;
+    if (p.flags & (RELNN_FLAG_MAX | RELNN_FLAG_PUSHDOWN | RELNN_FLAG_PER_TUPLE | kPlanDense)) return false;
+    if (p.Hx || p.dense_out || p.acc_out) return false;
+    for (auto& b : p.br)
+        if (b.d_r > 0) return false;
+    if (!pow2_in(p.d, 8, 256) || p.d_out > 256 || p.d_out % 4 != 0) return false;
+    // the gathered table is bf16 (given, or the plan's copy of an aligned f32 table)
+    return aligned16(io.z) && fwd_cfg(p).N > 0;
+}
+
+bool agg_backward_ok(const Plan& p, const CallIO& io, const GradIO& g) {
+    if (!agg_forward_ok(p, io, g.dz)) return false;
+    if (!pow2_in(p.d_out, 8, 256) || p.d % 32 != 0) return false;
+    return g.dout != nullptr && aligned16(g.dout) && bwd_cfg(p).N > 0;
+}
+
+relnn_status forward_agg(Plan& p, const CallIO& io_in, float* out, cudaStream_t st) {
+    CallIO io;
+    RELNN_TRY(with_bf16_z(p, io_in, io, st));
+    const int n_parts = p.concat_dst ? 2 : 1;
+    const int kpad = ((p.d + 63) / 64) * 64;
+    const int n_kb = n_parts * kpad / 64;
+    const int m_blocks = (p.d_out + 127) / 128;
+    const AggCfg cfg = fwd_cfg(p);
+    if (cfg.N == 0) {
+        set_error("aggregate-first forward: operands too large for shared memory");
+        return RELNN_ENOTSUP;
+    }
+    const int rows_pad = m_blocks * 128, cols = n_kb * 64;
+    RELNN_TRY(p.wpack.alloc(sizeof(uint16_t) * (size_t)rows_pad * cols));
+    CUtensorMap amap;
+    RELNN_TRY(encode_bf16_tile_map(&amap, p.wpack.p, cols, rows_pad));
+    size_t vp_max = 0;
+    for (auto& b : p.br) {
+        RELNN_TRY(ensure_vrows(b.vr_out, b.seg.as<int32_t>(), b.m, p.n_out, true, st));
+        vp_max = std::max(vp_max, (size_t)(b.vr_out.n_parts + b.vr_out.n_l2) * p.d_out);
+    }
+    if (vp_max) RELNN_TRY(p.vpart.alloc(sizeof(float) * vp_max));
+    for (size_t i = 0; i < p.br.size(); ++i) {
+        BranchPlan& b = p.br[i];
+        const VRows& V = b.vr_out;
+        if (V.nv == 0) continue;
+        { pack_a_fwd_kernel<<<grid_for((int64_t)rows_pad * cols), 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, p.d,
+                                                                               kpad, rows_pad, cols, p.wpack.as<uint16_t>()); note_launch(); }
+        AggArgs a{};
+        a.vr = V.vr.as<int4>();
+        a.nv = V.nv;
+        a.n_tiles = ceil_div(V.nv, cfg.N);
+        // the dst part first (one or a few rows per virtual row: its load overlaps the src part's)
+        int pi = 0;
+        if (p.concat_dst) {
+            a.gidx[pi] = b.hd.as<int32_t>();
+            a.tbl[pi] = reinterpret_cast<const uint16_t*>(io.z);
+            a.width[pi] = p.d;
+            a.kind[pi] = 1;
+            a.kofs[pi] = kpad;
+            ++pi;
+        }
+        a.gidx[pi] = b.hs.as<int32_t>();
+        a.tbl[pi] = reinterpret_cast<const uint16_t*>(io.z);
+        a.width[pi] = p.d;
+        a.kind[pi] = 0;
+        a.kofs[pi] = 0;
+        a.n_parts = pi + 1;
+        a.n_kb = n_kb;
+        a.m_blocks = m_blocks;
+        a.n_feat = p.d_out;
+        a.bias = io.br[i].b;
+        a.out = out;
+        a.vpart = p.vpart.as<float>();
+        a.accumulate = i > 0 ? 1 : 0;  // every branch covers every output row: the first one stores
+        a.tile_n = cfg.N;
+        a.stages = cfg.stages;
+        a.idesc = tc::idesc_bf16_f32(128, cfg.N);
+        a.tmem_cols = cfg.tmem_cols;
+        a.status = p.status.as<int>();
+        const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
+        if (p.kahan) RELNN_TRY((launch_agg<false, true>(amap, a, cfg.smem, grid, st, RELNN_PROF_AGG_FWD)));
+        else RELNN_TRY((launch_agg<false, false>(amap, a, cfg.smem, grid, st, RELNN_PROF_AGG_FWD)));
+        RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d_out, out, p.d_out, i > 0,
+                            p.kahan, st));
+    }
+    return RELNN_OK;
+}
+
+relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStream_t st) {
+    CallIO io;
+    RELNN_TRY(with_bf16_z(p, io_in, io, st));
+    const int n_kb = (p.d_out + 63) / 64;       // K of the dz GEMM: the G features
+    const int m_blocks = (p.d + 127) / 128;     // dz features
+    const int z_blocks = (p.d + 63) / 64;
+    const int m_dw = (p.d_out + 127) / 128;     // dW rows (G features)
+    const AggCfg cfg = bwd_cfg(p);
+    if (cfg.N == 0) {
+        set_error("aggregate-first backward: operands too large for shared memory");
+        return RELNN_ENOTSUP;
+    }
+    const int rows_pad = m_blocks * 128, cols = n_kb * 64;
+    const int grid_max = num_sms();
+    const int pblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(p.n_out, 64), 4 * (int64_t)num_sms()));
+    // scratch: A (bf16), the CTAs' dW partials, the blocks' db partials
+    const size_t a_elems = (size_t)rows_pad * cols;
+    const size_t a_bytes = (a_elems * 2 + 255) & ~(size_t)255;
+    const size_t dwp = (size_t)grid_max * p.d_out * p.d, dbp = (size_t)pblocks * kDbBranches * p.d_out;
+    RELNN_TRY(p.scratch.alloc(a_bytes + sizeof(float) * (dwp + dbp)));
+    uint16_t* abuf = p.scratch.as<uint16_t>();
+    float* dw_part = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + a_bytes);
+    float* db_part = dw_part + dwp;
+    // dOut rows are gathered as bf16 (the rounding the tensor cores give dY in the per-tuple form);
+    // the sums G are split into a bf16 pair like S in the forward. db comes from the f32 dOut, in
+    // the pass that makes the bf16 copy (tuples per output row from the forward's virtual rows).
+    for (auto& b : p.br) RELNN_TRY(ensure_vrows(b.vr_out, b.seg.as<int32_t>(), b.m, p.n_out, true, st));
+    if (p.n_out > 0) {
+        RELNN_TRY(p.doutbf.alloc(sizeof(uint16_t) * (size_t)p.n_out * p.d_out));
+        const int64_t rpb = ceil_div(p.n_out, pblocks);
+        for (size_t b0 = 0; b0 < p.br.size(); b0 += kDbBranches) {
+            CntSet cs{};
+            cs.n = (int)std::min<size_t>(kDbBranches, p.br.size() - b0);
+            for (int k = 0; k < cs.n; ++k) cs.c[k] = p.br[b0 + k].vr_out.cnt.as<int32_t>();
+            { dout_prep_kernel<<<pblocks, 256, 0, st>>>(g.dout, p.n_out, p.d_out, cs, rpb, p.doutbf.as<uint16_t>(),
+                                                       db_part); note_launch(); }
+            for (int k = 0; k < cs.n; ++k) {
+                float* db = g.db.size() > b0 + k ? g.db[b0 + k] : nullptr;
+                if (db) { db_reduce_kernel<<<grid_for(p.d_out, 128), 128, 0, st>>>(db_part, pblocks, p.d_out, k, db); note_launch(); }
+            }
+        }
+        RELNN_CUDA(cudaGetLastError());
+    } else {
+        for (size_t i = 0; i < p.br.size(); ++i)
+            if (g.db.size() > i && g.db[i]) RELNN_CUDA(cudaMemsetAsync(g.db[i], 0, sizeof(float) * p.d_out, st));
+    }
+    CUtensorMap amap;
+    RELNN_TRY(encode_bf16_tile_map(&amap, abuf, cols, rows_pad));
+    // virtual rows of both passes of every branch first, so the partial rows are allocated once
+    const int n_pass = p.concat_dst ? 2 : 1;
+    size_t vp_max = 0;
+    for (auto& b : p.br) {
+        RELNN_TRY(ensure_src_order(p, b, st));
+        RELNN_TRY(ensure_vrows(b.vr_src, b.hs_src.as<int32_t>(), b.m, p.n_h, true, st));
+        if (n_pass > 1) RELNN_TRY(ensure_vrows(b.vr_dst, b.hd.as<int32_t>(), b.m, 0, false, st));
+        vp_max = std::max(vp_max, (size_t)(b.vr_src.n_parts + b.vr_src.n_l2) * p.d);
+        if (n_pass > 1) vp_max = std::max(vp_max, (size_t)(b.vr_dst.n_parts + b.vr_dst.n_l2) * p.d);
+    }
+    if (vp_max) RELNN_TRY(p.vpart.alloc(sizeof(float) * vp_max));
+    for (size_t i = 0; i < p.br.size(); ++i) {
+        BranchPlan& b = p.br[i];
+        float* dW = g.dW.size() > i ? g.dW[i] : nullptr;
+        for (int pass = 0; pass < n_pass; ++pass) {
+            VRows& V = pass == 0 ? b.vr_src : b.vr_dst;
+            const int col0 = pass == 0 ? 0 : p.d;
+            if (V.nv == 0) {
+                if (dW) {
+                    // no tuples: this slice of dW is zero
+                    RELNN_CUDA(cudaMemset2DAsync(dW + col0, sizeof(float) * p.d_in, 0, sizeof(float) * p.d, p.d_out, st));
+                }
+                continue;
+            }
+            { pack_a_bwd_kernel<<<grid_for((int64_t)a_elems), 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, col0, p.d,
+                                                                           rows_pad, cols, abuf); note_launch(); }
+            const bool accumulate = pass > 0 || i > 0 || g.accumulate_dz;
+            AggArgs a{};
+            a.vr = V.vr.as<int4>();
+            a.nv = V.nv;
+            a.n_tiles = ceil_div(V.nv, cfg.N);
+            a.gidx[0] = pass == 0 ? b.seg_src.as<int32_t>() : b.seg.as<int32_t>();
+            a.tbl[0] = p.doutbf.as<uint16_t>();
+            a.width[0] = p.d_out;
+            a.kind[0] = pass == 0 ? 0 : 1;
+            a.kofs[0] = 0;
+            a.n_parts = 1;
+            a.n_kb = n_kb;
+            a.m_blocks = m_blocks;
+            a.n_feat = p.d;
+            a.bias = nullptr;
+            a.out = g.dz;
+            a.vpart = p.vpart.as<float>();
+            a.accumulate = accumulate ? 1 : 0;
+            a.tile_n = cfg.N;
+            a.stages = cfg.stages;
+            a.idesc = tc::idesc_bf16_f32(128, cfg.N);
+            a.tmem_cols = cfg.tmem_cols;
+            a.status = p.status.as<int>();
+            a.zrows = reinterpret_cast<const uint16_t*>(io.z);
+            a.d_z = p.d;
+            a.z_blocks = z_blocks;
+            a.m_dw = m_dw;
+            a.dw_part = dw_part;
+            a.n_g = p.d_out;
+            a.idesc_dw = tc::idesc_bf16_f32(128, p.d, true, true);
+            a.dw_col = cfg.dw_col;
+            const int grid = (int)std::min<int64_t>(a.n_tiles, grid_max);
+            if (p.kahan) RELNN_TRY((launch_agg<true, true>(amap, a, cfg.smem, grid, st, RELNN_PROF_AGG_BWD)));
+            else RELNN_TRY((launch_agg<true, false>(amap, a, cfg.smem, grid, st, RELNN_PROF_AGG_BWD)));
+            RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d, g.dz, p.d, accumulate,
+                                p.kahan, st));
+            if (dW) {
+                const int64_t nw = (int64_t)p.d_out * p.d;
+                { agg_reduce_dw_kernel<<<grid_for(nw), 256, 0, st>>>(dw_part, grid, p.d_out, p.d, dW, p.d_in, col0); note_launch(); }
+            }
+            RELNN_CUDA(cudaGetLastError());
+        }
+    }
+    return RELNN_OK;
+}
+
+}  // namespace relnn

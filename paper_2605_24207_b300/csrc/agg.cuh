@@ -1,0 +1,25 @@
+// Aggregate-first evaluation of linear SUM rules on tcgen05 tensor cores (agg.cu).
+#pragma once
+
+#include <cuda.h>
+
+#include "bwd.cuh"
+
+namespace relnn {
+
+// Whether the forward of the plan runs aggregate-first with these inputs: BF16 form, no activation,
+// SUM or MEAN, no per-tuple embedding, d a power of two in [8, 256], d_out <= 256 and a multiple
+// of 4, not a streamed chunk, RELNN_FLAG_PER_TUPLE not set, z and out 16-byte aligned.
+bool agg_forward_ok(const Plan& p, const CallIO& io, const float* out);
+// The same for the backward (also: no MAX, d_out a power of two in [8, 256], d a multiple of 32,
+// dOut and dz 16-byte aligned).
+bool agg_backward_ok(const Plan& p, const CallIO& io, const GradIO& g);
+
+relnn_status forward_agg(Plan& p, const CallIO& io, float* out, cudaStream_t st);
+relnn_status backward_agg(Plan& p, const CallIO& io, const GradIO& g, cudaStream_t st);
+
+// 2-D bf16 tensor map over a row-major [rows][cols] matrix, box 64 x 128, 128-byte swizzle (the
+// layout the tensor-core kernels stage their A operands in).
+relnn_status encode_bf16_tile_map(CUtensorMap* m, void* base, uint64_t cols, uint64_t rows);
+
+}  // namespace relnn

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "agg.cuh"
 #include "bwd.cuh"
 #include "segscan.cuh"
 #include "tc.cuh"
@@ -584,6 +585,8 @@ static bool tc_backward_supported(const Plan& p) {
 }
 
 relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStream_t st) {
+    // linear SUM / MEAN rules: per-H-row sums of dOut, then dense GEMM rows (agg.cu)
+    if (agg_backward_ok(p, io_in, g)) return backward_agg(p, io_in, g, st);
     if (!tc_backward_supported(p)) return backward_fp32(p, io_in, g, st);
     RELNN_CHECK_ARG(g.dout, "backward: null output gradient");
     const bool relu = p.act == RELNN_ACT_RELU;

@@ -20,6 +20,7 @@
 // Narrow outputs (d_out <= 64) leave lane quarters empty, so W is replicated into them (2 or 4
 // copies): every quarter then holds all features of the tile, and each of the rep warps sharing a
 // feature quarter walks 1/rep of the half-tile's columns (the unit shrinks to half_n / rep).
+#include "agg.cuh"
 #include "fwd.cuh"
 #include "maxagg.cuh"
 #include "segscan.cuh"
@@ -542,6 +543,25 @@ EncodeTiledFn get_encode_fn() {
 
 }  // namespace
 
+relnn_status encode_bf16_tile_map(CUtensorMap* m, void* base, uint64_t cols, uint64_t rows) {
+    EncodeTiledFn enc = get_encode_fn();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return RELNN_ECUDA;
+    }
+    cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+        return RELNN_ECUDA;
+    }
+    return RELNN_OK;
+}
+
 // Concat layout for the tensor-core path: every part (z_src, z_dst, r) starts on a 64-column
 // K block; K blocks never straddle parts.
 struct KbLayout {
@@ -593,6 +613,8 @@ relnn_status with_bf16_z(Plan& p, const CallIO& io, CallIO& out, cudaStream_t st
 }
 
 relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t st) {
+    // linear SUM / MEAN rules: sum each output row's Concat rows first, then one GEMM row (agg.cu)
+    if (agg_forward_ok(p, io_in, out)) return forward_agg(p, io_in, out, st);
     if (p.identity) {
         set_error("BF16 form needs a Linear (identity rules run in the FP32 form)");
         return RELNN_ENOTSUP;

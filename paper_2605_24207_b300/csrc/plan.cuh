@@ -22,6 +22,18 @@
 
 namespace relnn {
 
+// Virtual rows of an ordered tuple list for the aggregate-first kernels (agg.cu): the tuples of
+// one destination row (a run of equal keys) cut into chunks of at most a fixed number of tuples.
+//   vr[v]    int4 {first tuple, tuples, destination row, partial slot (-1: the row is one chunk)}
+//   fix1/2   fix-up jobs of rows cut into several chunks (int4 {row, first slot, count, level-2 slot
+//            or -1}), level 2 only for rows with more chunks than one fix-up block adds
+//   cnt[r]   int32 tuples of row r (lists whose keys ascend over rows 0..R-1)
+// Built once per list and cached (nv < 0: not built yet).
+struct VRows {
+    int64_t nv = -1, n_parts = 0, n_l2 = 0, n_fix1 = 0, n_fix2 = 0;
+    DevBuf vr, fix1, fix2, cnt;
+};
+
 struct BranchPlan {
     int64_t n_tuples = 0;
     int64_t m = 0;  // matched tuples
@@ -29,6 +41,9 @@ struct BranchPlan {
     DevBuf hs, hd, er, seg;
     DevBuf src_perm, hs_src, seg_src;
     DevBuf relu_mask;  // uint32 [m][ceil(d_out/32)] when RELNN_FLAG_RELU_MASK
+    // aggregate-first evaluation: output rows (forward), H rows in src order and runs of equal dst H
+    // rows (backward)
+    VRows vr_out, vr_src, vr_dst;
 };
 
 // Internal plan flag (above the public RELNN_FLAG_* bits): every tuple is its own output row (the
@@ -54,6 +69,7 @@ struct Plan {
     DevBuf zbf;       // bf16 copy of an f32 H embedding for the tensor-core kernels
     DevBuf doutbf;    // bf16 copy of the output gradient for the backward's src pass
     DevBuf fixjobs;   // long segments handed from the fix-up to its block-per-segment pass
+    DevBuf vpart;     // aggregate-first: f32 partial rows of chunks (and their level-2 sums)
     // transformation push-down (RELNN_FLAG_PUSHDOWN): the identity plan of the per-H-row products,
     // the products P = Z W_src^T and Q = Z W_dst^T + b, and one column block of W
     std::unique_ptr<Plan> pd;
@@ -83,7 +99,7 @@ struct Plan {
     // a synchronising cudaFree), for plans whose work all ran on s.
     void retire_on(cudaStream_t s) {
         DevBuf* bufs[] = {&H.rows_sorted, &H.run_start, &H.uid_of_pos, &H.ukeys, &H.slot_keys, &H.slot_vals,
-                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &pdP, &pdQ, &pdW, &inv_cnt, &mean_dout,
+                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &vpart, &pdP, &pdQ, &pdW, &inv_cnt, &mean_dout,
                           &max_arg, &carry_pos, &win_mask};
         for (DevBuf* b : bufs) {
             b->ordered = true;
@@ -91,7 +107,10 @@ struct Plan {
         }
         if (pd) pd->retire_on(s);
         for (auto& b : br) {
-            DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.src_perm, &b.hs_src, &b.seg_src, &b.relu_mask};
+            DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.src_perm, &b.hs_src, &b.seg_src, &b.relu_mask,
+                            &b.vr_out.vr, &b.vr_out.fix1, &b.vr_out.fix2, &b.vr_out.cnt, &b.vr_src.vr, &b.vr_src.fix1,
+                            &b.vr_src.fix2, &b.vr_src.cnt, &b.vr_dst.vr, &b.vr_dst.fix1, &b.vr_dst.fix2,
+                            &b.vr_dst.cnt};
             for (DevBuf* x : bb) {
                 x->ordered = true;
                 x->st = s;

@@ -78,11 +78,58 @@ void prof_end(ProfToken& tok, cudaStream_t st) {
     tok.ev = nullptr;
 }
 
+// FP32 FMA throughput probe: every thread runs kFmaChains independent chains x <- x * a + b (a and b
+// are run-time values, so nothing folds), enough independent work per warp to issue an FMA every
+// cycle; the sum of the chains is stored only if it equals a value it cannot take, which keeps the
+// chains live without a store per thread.
+constexpr int kFmaChains = 8;
+__global__ void __launch_bounds__(1024) fma_peak_kernel(float* out, int iters, float a, float b) {
+    float x[kFmaChains];
+#pragma unroll
+    for (int i = 0; i < kFmaChains; ++i) x[i] = (float)threadIdx.x * 1e-3f + (float)i;
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int i = 0; i < kFmaChains; ++i) x[i] = fmaf(x[i], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < kFmaChains; ++i) s += x[i];
+    if (s == -1.2345e30f) out[blockIdx.x] = s;
+}
+
 }  // namespace relnn
 
 using namespace relnn;
 
 extern "C" {
+
+relnn_status relnn_peak_fma_f32(int32_t iters, double* tflops, double* ms, void* stream) {
+    RELNN_CHECK_ARG(iters > 0 && tflops, "peak fma: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int blocks = 2 * num_sms(), threads = 1024;
+    float* sink = nullptr;
+    RELNN_CUDA(cudaMallocAsync(&sink, sizeof(float) * blocks, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RELNN_CUDA(cudaEventCreate(&e0));
+    RELNN_CUDA(cudaEventCreate(&e1));
+    // a = 1 - 2^-20 and b = 2^-10 keep the chains bounded (x converges to b / (1 - a) = 1024)
+    const float a = 1.0f - 9.5367431640625e-07f, b = 9.765625e-04f;
+    { fma_peak_kernel<<<blocks, threads, 0, st>>>(sink, iters, a, b); note_launch(); }
+    cudaEventRecord(e0, st);
+    { fma_peak_kernel<<<blocks, threads, 0, st>>>(sink, iters, a, b); note_launch(); }
+    cudaEventRecord(e1, st);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(sink, st);
+    RELNN_CUDA(err);
+    const double flop = 2.0 * kFmaChains * (double)iters * blocks * threads;
+    *tflops = flop / (t * 1e-3) / 1e12;
+    if (ms) *ms = t;
+    return RELNN_OK;
+}
 
 uint64_t relnn_launch_count(void) { return g_launches.load(); }
 

@@ -29,6 +29,7 @@ FLAG_TILE128 = 0x40
 FLAG_PUSHDOWN = 0x80
 FLAG_MEAN = 0x100
 FLAG_MAX = 0x200
+FLAG_PER_TUPLE = 0x400
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOSPC", 4: "EAGAIN", 5: "ETIMEDOUT", 6: "ECUDA",
           7: "EDEVICE", 8: "ENOTSUP"}
@@ -111,7 +112,7 @@ EXPORTS = [
     "relnn_rule_forward", "relnn_rule_backward", "relnn_plan_destroy",
     "relnn_profile_enable", "relnn_profile_read", "relnn_profile_reset", "relnn_launch_count",
 ]
-PROF_FWD_TC, PROF_FWD_FP32, PROF_FIXUP, PROF_BWD_TC, PROF_BWD_FP32, PROF_PLAN = range(6)
+PROF_FWD_TC, PROF_FWD_FP32, PROF_FIXUP, PROF_BWD_TC, PROF_BWD_FP32, PROF_PLAN, PROF_AGG_FWD, PROF_AGG_BWD = range(8)
 
 
 def lib():
@@ -169,6 +170,8 @@ def lib():
     for name in EXPORTS[4:-1]:
         getattr(L, name).restype = C.c_int
     L.relnn_launch_count.restype = C.c_uint64
+    L.relnn_peak_fma_f32.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+    L.relnn_peak_fma_f32.restype = C.c_int
     _LIB = L
     return L
 
@@ -218,6 +221,13 @@ def profile_enable(on: bool = True):
 
 def profile_reset():
     _check(lib().relnn_profile_reset())
+
+
+def peak_fma_f32(iters: int = 1 << 15, stream=None):
+    """(TFLOP/s, ms) of the library's FP32 FMA throughput probe (relnn_peak_fma_f32)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().relnn_peak_fma_f32(int(iters), C.byref(tf), C.byref(ms), _stream(stream)))
+    return tf.value, ms.value
 
 
 def profile_read(kernel_id: int):

@@ -1,0 +1,190 @@
+"""GPU parity of the aggregate-first evaluation of linear SUM rules (the BF16 form's default for rules
+without an activation: each output row's Concat rows are summed first and the Linear is applied once
+per row, since SUM commutes with a linear map, paper Sec. 2.2 and the hybrid rewrites of Sec. 6).
+
+Bars as for the BF16 form: join output and key sets bit-exact, <= 2e-2 relative Frobenius error
+against the FP64 oracle on the original inputs, and <= 1e-4 against the oracle fed the same
+bf16-rounded operands (the per-row sums are kept as a bf16 pair, about 16 significant bits). The
+per-tuple form (RELNN_FLAG_PER_TUPLE) computes the same rule and is compared as well. Shapes cover
+virtual rows cut into chunks (heavy rows), the two-level fix-up (rows of more than 256 chunks), the
+backward's src-order hubs, unions, MEAN, Kahan, every supported width and the fallbacks."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import relnn_oracle as O
+from paper_2605_24207_b300 import relnn as R
+from paper_2605_24207_b300 import workloads as W
+
+from rule_cases import OBr, bf16_round, oracle_rule, rel_frob, run_rule, to_dev
+
+pytestmark = pytest.mark.gpu
+
+BF16_TOL = 2e-2
+SAME_INPUT_TOL = 1e-4
+
+
+def _fwd(rel, flags=0, z_dtype=torch.bfloat16, **kw):
+    keys, out, plan, t = run_rule(rel, flags=flags | R.FLAG_BF16, z_dtype=z_dtype, **kw)
+    ok, oo, sizes = oracle_rule(rel)
+    assert np.array_equal(keys, ok)
+    assert plan.matched == sizes
+    assert rel_frob(out, oo) <= BF16_TOL
+    _, oo_r, _ = oracle_rule(rel, round_z=True, round_w=True)
+    err = rel_frob(out, oo_r)
+    assert err <= SAME_INPUT_TOL, err
+    return keys, out, plan, t
+
+
+@pytest.mark.parametrize("d,d_out", [(128, 128), (64, 64), (32, 96), (256, 64), (8, 16), (16, 256), (64, 200)])
+def test_forward_widths(gpu, d, d_out):
+    rel = W.make_rule(101, 20_011, 1500, d, d_out, np.int32, src_dist="zipf", src_s=1.1)
+    _fwd(rel)
+
+
+def test_forward_same_as_per_tuple(gpu):
+    rel = W.make_rule(102, 50_000, 4000, 128, 128, np.int64, src_dist="zipf", src_s=1.1)
+    keys, out, _, _ = _fwd(rel)
+    keys2, out2, _, _ = run_rule(rel, flags=R.FLAG_BF16 | R.FLAG_PER_TUPLE, z_dtype=torch.bfloat16)
+    assert np.array_equal(keys, keys2)
+    assert rel_frob(out, out2.astype(np.float64)) <= SAME_INPUT_TOL
+
+
+@pytest.mark.parametrize("kahan", [False, True])
+def test_forward_heavy_rows_two_level_fixup(gpu, kahan):
+    """Zipf(2.0) dst over 200 keys: the largest row holds most of the 40k tuples, i.e. more than 256
+    chunks of 32, so its chunk partials go through both fix-up levels."""
+    rel = W.make_rule(103, 40_000, 200, 64, 64, np.int32, dst_dist="zipf", dst_s=2.0)
+    _fwd(rel, flags=R.FLAG_KAHAN if kahan else 0)
+
+
+def test_forward_f32_table_and_duplicate_keys(gpu):
+    """f32 z (the plan's bf16 copy is gathered) and duplicate H keys (a row's tuples name several
+    dst H rows: the dst part sums distinct rows with their multiplicities)."""
+    rel = W.make_rule(104, 8000, 600, 64, 64, np.int64, dup_frac=0.3, missing_frac=0.1, sparse_keys=True)
+    _fwd(rel, z_dtype=torch.float32)
+
+
+def test_forward_union_without_edge_embedding(gpu):
+    rel = W.make_rule(105, 0, 3000, 64, 96, np.int32, dst_dist="zipf", dst_s=1.0,
+                      branch_tuples=[20_000, 10_000, 5000])
+    _fwd(rel)
+
+
+def test_forward_no_concat_dst_and_readout_shape(gpu):
+    rel = W.make_rule(106, 10_000, 900, 64, 64, np.int32)
+    rel.branches[0].W = np.ascontiguousarray(rel.branches[0].W[:, :64])  # Concat = z_src only
+    keys, out, plan, _ = run_rule(rel, flags=R.FLAG_BF16 | R.FLAG_NO_CONCAT_DST, z_dtype=torch.bfloat16)
+    ok, oo, _ = oracle_rule(rel, round_z=True, round_w=True, concat_dst=False)
+    assert np.array_equal(keys, ok)
+    assert rel_frob(out, oo) <= SAME_INPUT_TOL
+
+
+def test_forward_mean(gpu):
+    rel = W.make_rule(107, 30_000, 2500, 64, 64, np.int32, src_dist="zipf", src_s=1.2, dst_dist="zipf", dst_s=1.3)
+    keys, out, plan, _ = run_rule(rel, flags=R.FLAG_BF16 | R.FLAG_MEAN, z_dtype=torch.bfloat16)
+    brs = [OBr(b.src, b.dst, bf16_round(b.W), b.b, None) for b in rel.branches]
+    ok, oo, _ = O.rule_forward(rel.h_ids, bf16_round(rel.z), brs, agg="mean")
+    assert np.array_equal(keys, ok)
+    assert rel_frob(out, oo) <= SAME_INPUT_TOL
+
+
+def test_forward_unaligned_output_takes_per_tuple_form(gpu):
+    """An output pointer that is not 16-byte aligned runs the per-tuple form (same result)."""
+    rel = W.make_rule(108, 6000, 500, 64, 64, np.int32)
+    br = rel.branches[0]
+    plan = R.RulePlan(to_dev(rel.h_ids), [(to_dev(br.src), to_dev(br.dst))], 64, 64, flags=R.FLAG_BF16)
+    buf = torch.empty(plan.n_out * 64 + 1, dtype=torch.float32, device="cuda")
+    out = buf[1:].view(plan.n_out, 64)
+    plan.forward(to_dev(rel.z, torch.bfloat16), [to_dev(br.W)], [to_dev(br.b)], out=out)
+    torch.cuda.synchronize()
+    plan.check()
+    _, oo, _ = oracle_rule(rel, round_z=True, round_w=True)
+    assert rel_frob(out.cpu().numpy(), oo) <= SAME_INPUT_TOL
+
+
+def test_empty_branch_in_union(gpu):
+    """A union whose first branch matches nothing: the first launch still writes every output row."""
+    rel = W.make_rule(109, 0, 800, 64, 64, np.int32, branch_tuples=[3000, 4000])
+    b0 = rel.branches[0]
+    b0.src = np.full_like(b0.src, 10 ** 6)  # no H key matches
+    _fwd(rel)
+
+
+# ------------------------------------------------------------------------------ backward
+def _bwd(rel, flags=0, z_dtype=torch.bfloat16, seed=3):
+    keys, out, plan, t = run_rule(rel, flags=flags | R.FLAG_BF16, z_dtype=z_dtype)
+    dout = np.random.default_rng(seed).standard_normal(out.shape).astype(np.float32)
+    dW, db, dz, _ = plan.backward(to_dev(dout), t["z"], t["W"], t["b"], t["r"])
+    torch.cuda.synchronize()
+    plan.check()
+    agg = "mean" if flags & R.FLAG_MEAN else "sum"
+    brs = [OBr(b.src, b.dst, bf16_round(b.W), b.b, None) for b in rel.branches]
+    oW, ob, oz, _ = O.rule_backward(rel.h_ids, bf16_round(rel.z), brs, keys, dout, act=rel.act, agg=agg)
+    return (dW, db, dz), (oW, ob, oz), (plan, t, dout)
+
+
+@pytest.mark.parametrize("d,d_out,src_s", [(128, 128, 1.1), (64, 64, 1.2), (32, 8, 1.1), (256, 128, 1.1), (64, 256, 1.3)])
+def test_backward_matches_oracle(gpu, d, d_out, src_s):
+    rel = W.make_rule(111, 30_011, 3000, d, d_out, np.int32, src_dist="zipf", src_s=src_s)
+    (dW, db, dz), (oW, ob, oz), _ = _bwd(rel)
+    # dOut is gathered as bf16 (the per-tuple form's dY rounding); the sums are a bf16 pair
+    assert rel_frob(dW[0].cpu().numpy(), oW[0]) <= 5e-3
+    assert rel_frob(db[0].cpu().numpy(), ob[0]) <= 5e-3
+    assert rel_frob(dz.cpu().numpy(), oz) <= 5e-3
+
+
+def test_backward_same_as_per_tuple(gpu):
+    rel = W.make_rule(112, 40_000, 3000, 128, 128, np.int64, src_dist="zipf", src_s=1.1)
+    (dW, db, dz), _, (plan, t, dout) = _bwd(rel)
+    keys, out, plan2, t2 = run_rule(rel, flags=R.FLAG_BF16 | R.FLAG_PER_TUPLE, z_dtype=torch.bfloat16)
+    dW2, db2, dz2, _ = plan2.backward(to_dev(dout), t2["z"], t2["W"], t2["b"], t2["r"])
+    torch.cuda.synchronize()
+    assert rel_frob(dW[0].cpu().numpy(), dW2[0].cpu().numpy().astype(np.float64)) <= 2e-2
+    assert rel_frob(db[0].cpu().numpy(), db2[0].cpu().numpy().astype(np.float64)) <= 1e-4
+    assert rel_frob(dz.cpu().numpy(), dz2.cpu().numpy().astype(np.float64)) <= 2e-2
+
+
+def test_backward_src_hub_two_level_fixup(gpu):
+    """Zipf(2.5) src over 2000 keys: the top src row holds most of the 60k tuples (more than 256
+    chunks), so the src pass's dz row of that hub goes through both fix-up levels."""
+    rel = W.make_rule(113, 60_000, 2000, 64, 64, np.int32, src_dist="zipf", src_s=2.5)
+    (dW, db, dz), (oW, ob, oz), _ = _bwd(rel)
+    assert rel_frob(dW[0].cpu().numpy(), oW[0]) <= 5e-3
+    assert rel_frob(dz.cpu().numpy(), oz) <= 5e-3
+
+
+@pytest.mark.parametrize("kind", ["union", "mean", "kahan", "dup_keys"])
+def test_backward_variants(gpu, kind):
+    flags = 0
+    if kind == "union":
+        rel = W.make_rule(114, 0, 2000, 64, 64, np.int32, dst_dist="zipf", dst_s=1.0, branch_tuples=[9000, 5000, 2500])
+    elif kind == "mean":
+        rel = W.make_rule(115, 20_000, 1500, 64, 64, np.int32, dst_dist="zipf", dst_s=1.3)
+        flags = R.FLAG_MEAN
+    elif kind == "kahan":
+        rel = W.make_rule(116, 20_000, 1500, 64, 64, np.int32, src_dist="zipf", src_s=1.5)
+        flags = R.FLAG_KAHAN
+    else:
+        rel = W.make_rule(117, 8000, 600, 64, 64, np.int64, dup_frac=0.3, missing_frac=0.1, sparse_keys=True)
+    (dW, db, dz), (oW, ob, oz), _ = _bwd(rel, flags=flags)
+    for i in range(len(rel.branches)):
+        assert rel_frob(dW[i].cpu().numpy(), oW[i]) <= 5e-3
+        assert rel_frob(db[i].cpu().numpy(), ob[i]) <= 5e-3
+    assert rel_frob(dz.cpu().numpy(), oz) <= 5e-3
+
+
+def test_backward_repeat_is_deterministic(gpu):
+    rel = W.make_rule(118, 30_000, 2000, 64, 64, np.int32, src_dist="zipf", src_s=1.4)
+    (dW, db, dz), _, (plan, t, dout) = _bwd(rel)
+    dW2, db2, dz2, _ = plan.backward(to_dev(dout), t["z"], t["W"], t["b"], t["r"])
+    torch.cuda.synchronize()
+    assert torch.equal(dW[0], dW2[0]) and torch.equal(db[0], db2[0]) and torch.equal(dz, dz2)
+
+
+def test_forward_repeat_is_deterministic(gpu):
+    rel = W.make_rule(119, 30_000, 200, 64, 64, np.int32, dst_dist="zipf", dst_s=2.0)
+    keys, out, plan, t = run_rule(rel, flags=R.FLAG_BF16, z_dtype=torch.bfloat16)
+    out2 = plan.forward(t["z"], t["W"], t["b"])
+    torch.cuda.synchronize()
+    assert np.array_equal(out, out2.cpu().numpy())
