@@ -439,6 +439,7 @@ relnn_status relnn_stream_destroy(relnn_stream_t s);
 #define RELNN_PROF_PLAN 5        /* content track (whole relnn_rule_plan)                          */
 #define RELNN_PROF_AGG_FWD 6     /* aggregate-first forward kernel (linear SUM rules)              */
 #define RELNN_PROF_AGG_BWD 7     /* aggregate-first backward kernel (one launch per pass)          */
+#define RELNN_PROF_AGG_SUM 8     /* aggregate-first gather-sum kernel (per-row sums of the src rows) */
 
 /* Number of kernels this library has launched since it was loaded (host counter). */
 uint64_t relnn_launch_count(void);
@@ -449,6 +450,19 @@ relnn_status relnn_profile_enable(int32_t on);
  * accumulated since the last reset. */
 relnn_status relnn_profile_read(int32_t id, double* total_ms, int64_t* launches);
 relnn_status relnn_profile_reset(void);
+/* Process-wide tuning knobs (no counterpart in the paper): choices of the kernels' host code that
+ * change speed, never results beyond the order of f32 additions. Set by the autotuner or the
+ * caller; thread-safe; a value outside the knob's range is rejected with EINVAL.
+ *   RELNN_TUNE_SORT_BITS   widest digit of a radix-sort pass (4..11, default 8): the content track's
+ *                          group sort takes ceil(key bits / this) passes of equal width; narrower
+ *                          digits make longer runs per 4096-key tile in the scatter
+ *   RELNN_TUNE_AGG_ROWS    output rows per tile of the aggregate-first kernel (0 = the largest that
+ *                          fits, or 32 / 64 / 128)                                                 */
+#define RELNN_TUNE_SORT_BITS 0
+#define RELNN_TUNE_AGG_ROWS 1
+relnn_status relnn_tune_set(int32_t knob, int64_t value);
+relnn_status relnn_tune_get(int32_t knob, int64_t* value);
+
 /* sync. FP32 CUDA-core throughput probe: one launch of 2 x SMs blocks of 1024 threads, each thread
  * running 8 independent FMA chains for `iters` steps, timed by CUDA events on `stream` after one
  * warm-up launch. *tflops = 16 x iters x threads / time (FMA = 2 FLOP); *ms (may be NULL) = the

@@ -59,6 +59,9 @@ constexpr int kMaxParts = 2;
 constexpr int kMaxMeta = 4;                    // tile rows / 32 (N <= 128)
 constexpr int kUnroll = 8;                     // row loads in flight per lane
 constexpr int kChunk = 32;                     // tuples per virtual row (one index per lane)
+constexpr int kMaxG = 8;                       // rows per warp in group mode (row width >= 4 chunks)
+constexpr int kRound = 16;                     // tuples of a row loaded together (two rounds per row)
+constexpr int kMaxZ = 2;                       // z-row chunks per lane loaded with the row (the rest after)
 constexpr int kFixChunk = 256;                 // chunk partials one fix-up block adds
 constexpr int kSmemLimit = 227 * 1024;
 
@@ -176,7 +179,24 @@ __device__ __forceinline__ void part_sum(const uint16_t* __restrict__ tbl, int w
     }
 }
 
-template <bool BWD, bool KAHAN>
+// S = S_hi + S_lo of one 8-element chunk into the stage (lanes < L of the part write).
+__device__ __forceinline__ void store_pair(uint32_t sb, uint32_t blk, int n_kb, int kofs, int r, int lane,
+                                           const float (&acc)[8]) {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        hi[i] = pack_bf16x2(acc[2 * i], acc[2 * i + 1]);
+        const float h0 = __uint_as_float(hi[i] << 16), h1 = __uint_as_float(hi[i] & 0xffff0000u);
+        lo[i] = pack_bf16x2(acc[2 * i] - h0, acc[2 * i + 1] - h1);
+    }
+    const int k = kofs + 8 * lane;  // first element of this lane's chunk in K
+    const uint32_t off = (uint32_t)(k >> 6) * blk + (uint32_t)r * 128u +
+                         ((((uint32_t)(k >> 3) & 7u) ^ ((uint32_t)r & 7u)) << 4);
+    st_shared_v4(sb + off, hi[0], hi[1], hi[2], hi[3]);
+    st_shared_v4(sb + (uint32_t)n_kb * blk + off, lo[0], lo[1], lo[2], lo[3]);
+}
+
+template <bool BWD, bool KAHAN, int K1, int K0>
 __global__ void __launch_bounds__(kThreads, 1)
 agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ AggArgs a) {
     extern __shared__ uint8_t dyn_smem[];
@@ -229,7 +249,16 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 
     if (producer) {
         // ------------------------------------------------------------------ producers
-        const int meta_n = N / 32;
+        // Group mode (every part L = width / 8 >= 4 lanes wide): a warp takes G = 32 / L rows at once
+        // and lane group g sums row g alone (lane = one 16-byte chunk of the row), so a row needs no
+        // cross-group reduction and the per-row work is shared by G rows. Other widths: one row at a
+        // time with the general part sums.
+        const int Lw = a.width[0] >> 3;  // a power of two
+        const int lsh = 31 - __clz(Lw);   // log2(Lw): no integer division in the loops below
+        const bool gmode = Lw >= 4 && (a.n_parts == 1 || a.width[1] == a.width[0]);
+        const int G = gmode ? 32 >> lsh : 1;
+        const int grp = gmode ? lane >> lsh : 0, ch = gmode ? (lane & (Lw - 1)) : lane;
+        const int zch = BWD ? a.d_z >> 3 : 0;  // 16-byte chunks of a z row
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int s = lt % a.stages;
@@ -237,87 +266,197 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&empty[s]), (use & 1u) ^ 1u, a.status, abort_flag))) break;
             const uint32_t sb = smem_u32(st_smem + (size_t)s * stage_bytes);
             const int64_t v0 = tile * N;
-            // the tile's virtual rows: lane l of register c holds row 32 c + l
-            int4 meta[kMaxMeta];
-#pragma unroll
-            for (int c = 0; c < kMaxMeta; ++c) {
-                const int64_t v = v0 + 32 * c + lane;
-                meta[c] = (c < meta_n && v < a.nv) ? __ldg(a.vr + v) : make_int4(0, 0, -1, -1);
-            }
-            // rows are taken one at a time; each warp's last take fails, so a tile use consumes
-            // exactly N + kProdWarps values of the stage's counter
-            const int cbase = (int)use * (N + kProdWarps);
+            // rows are taken G at a time from the stage's counter; each warp's last take fails, so a
+            // tile use consumes exactly G * (ceil(N / G) + kProdWarps) values
+            const int cbase = (int)use * G * ((N + G - 1) / G + kProdWarps);
+            bool done = false;
             auto take = [&]() {
+                if (done) return N;
                 int r = 0;
-                if (lane == 0) r = atomicAdd(ctr + s, 1) - cbase;
-                return __shfl_sync(0xffffffffu, r, 0);
+                if (lane == 0) r = atomicAdd(ctr + s, G) - cbase;
+                r = __shfl_sync(0xffffffffu, r, 0);
+                if (r >= N) done = true;
+                return r;
             };
-            auto row_meta = [&](int r) {
-                const int c = r >> 5, l = r & 31;
-                int4 m;
-                m.x = __shfl_sync(0xffffffffu, c == 0 ? meta[0].x : c == 1 ? meta[1].x : c == 2 ? meta[2].x : meta[3].x, l);
-                m.y = __shfl_sync(0xffffffffu, c == 0 ? meta[0].y : c == 1 ? meta[1].y : c == 2 ? meta[2].y : meta[3].y, l);
-                m.z = __shfl_sync(0xffffffffu, c == 0 ? meta[0].z : c == 1 ? meta[1].z : c == 2 ? meta[2].z : meta[3].z, l);
-                return m;
+            auto meta_of = [&](int r) {
+                return (r < N && v0 + r < a.nv) ? __ldg(a.vr + v0 + r) : make_int4(0, 0, -1, -1);
             };
-            // the next row's tuple indices are loaded while the current row is summed
-            auto load_idx = [&](const int4& m, int (&ix)[kMaxParts]) {
-#pragma unroll
-                for (int p = 0; p < kMaxParts; ++p)
-                    ix[p] = (p < a.n_parts && m.z >= 0 && lane < m.y) ? __ldg(a.gidx[p] + m.x + lane) : -1;
+            // past the last virtual row: zero the row's S blocks (stale rows would add into dW)
+            auto zero_row = [&](int r, int l0, int nl) {
+                for (int i = l0; i < 2 * a.n_kb * 8; i += nl)
+                    st_shared_v4(sb + (uint32_t)(i >> 3) * blk + (uint32_t)r * 128u + (uint32_t)(i & 7) * 16u, 0u, 0u, 0u, 0u);
             };
-            int r_next = take();
-            int4 m_next = make_int4(0, 0, -1, -1);
-            int ix_next[kMaxParts];
-            if (r_next < N) m_next = row_meta(r_next);
-            load_idx(m_next, ix_next);
-            while (r_next < N) {
-                const int r = r_next;
-                const int4 m = m_next;
-                int ix[kMaxParts];
+            auto z_store = [&](int r, int c, const uint4& zc) {
+                st_shared_v4(sb + (uint32_t)(2 * a.n_kb + (c >> 3)) * blk + (uint32_t)r * 128u +
+                                 ((((uint32_t)c & 7u) ^ ((uint32_t)r & 7u)) << 4),
+                             zc.x, zc.y, zc.z, zc.w);
+            };
+            if (!gmode) {
+                // ---------------------------------------------------------------- one row at a time
+                for (int r = take(); r < N; r = take()) {
+                    const int4 m = meta_of(r);
+                    if (m.z < 0) {
+                        zero_row(r, lane, 32);
+                        continue;
+                    }
+                    int ix[kMaxParts];
 #pragma unroll
-                for (int p = 0; p < kMaxParts; ++p) ix[p] = ix_next[p];
-                r_next = take();
-                m_next = r_next < N ? row_meta(r_next) : make_int4(0, 0, -1, -1);
-                load_idx(m_next, ix_next);
-                const uint32_t rsw = (uint32_t)(r & 7);
-                if (m.z < 0) {
-                    // past the last virtual row: zero the row's S blocks (stale rows would add into dW)
-                    for (int i = lane; i < 2 * a.n_kb * 8; i += 32)
-                        st_shared_v4(sb + (uint32_t)(i >> 3) * blk + (uint32_t)r * 128u + (uint32_t)(i & 7) * 16u, 0u, 0u,
-                                     0u, 0u);
-                    continue;
-                }
-                // backward: the row's z (B operand of G^T Z), loaded now and stored at the end
-                uint4 zc = make_uint4(0u, 0u, 0u, 0u);
-                const int zch = BWD ? a.d_z >> 3 : 0;
-                if (BWD && lane < zch) zc = __ldg(reinterpret_cast<const uint4*>(a.zrows + (int64_t)m.z * a.d_z) + lane);
+                    for (int p = 0; p < kMaxParts; ++p)
+                        ix[p] = (p < a.n_parts && lane < m.y) ? __ldg(a.gidx[p] + m.x + lane) : -1;
+                    for (int c = lane; c < zch; c += 32)
+                        z_store(r, c, __ldg(reinterpret_cast<const uint4*>(a.zrows + (int64_t)m.z * a.d_z) + c));
 #pragma unroll
-                for (int p = 0; p < kMaxParts; ++p) {
-                    if (p >= a.n_parts) break;
-                    float acc[8];
-                    part_sum<KAHAN>(a.tbl[p], a.width[p], a.kind[p], ix[p], m.y, lane, acc);
-                    const int L = a.width[p] >> 3;
-                    if (lane < L) {
-                        // S = S_hi + S_lo, each rounded to bf16 (nearest even)
-                        uint32_t hi[4], lo[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            hi[i] = pack_bf16x2(acc[2 * i], acc[2 * i + 1]);
-                            const float h0 = __uint_as_float(hi[i] << 16), h1 = __uint_as_float(hi[i] & 0xffff0000u);
-                            lo[i] = pack_bf16x2(acc[2 * i] - h0, acc[2 * i + 1] - h1);
-                        }
-                        const int k = a.kofs[p] + 8 * lane;  // first element of this lane's chunk in K
-                        const uint32_t off = (uint32_t)(k >> 6) * blk + (uint32_t)r * 128u +
-                                             ((((uint32_t)(k >> 3) & 7u) ^ rsw) << 4);
-                        st_shared_v4(sb + off, hi[0], hi[1], hi[2], hi[3]);
-                        st_shared_v4(sb + (uint32_t)a.n_kb * blk + off, lo[0], lo[1], lo[2], lo[3]);
+                    for (int p = 0; p < kMaxParts; ++p) {
+                        if (p >= a.n_parts) break;
+                        float acc[8];
+                        part_sum<KAHAN>(a.tbl[p], a.width[p], a.kind[p], ix[p], m.y, lane, acc);
+                        if (lane < (a.width[p] >> 3)) store_pair(sb, blk, a.n_kb, a.kofs[p], r, lane, acc);
                     }
                 }
-                if (BWD && lane < zch)
-                    st_shared_v4(sb + (uint32_t)(2 * a.n_kb + (lane >> 3)) * blk + (uint32_t)r * 128u +
-                                     ((((uint32_t)lane & 7u) ^ rsw) << 4),
-                                 zc.x, zc.y, zc.z, zc.w);
+            } else {
+                // ---------------------------------------------------------------- G rows at a time
+                // lane (g, c) holds tuple c + L i of row g's part indices, i < G (rows <= 32 tuples)
+                int r_n = take();
+                int4 m_n = meta_of(r_n + grp);
+                int ix_n[kMaxParts][kMaxG];
+                auto load_idx = [&](const int4& m, int (&ix)[kMaxParts][kMaxG]) {
+#pragma unroll
+                    for (int p = 0; p < kMaxParts; ++p)
+#pragma unroll
+                        for (int i = 0; i < kMaxG; ++i) {
+                            const int t = ch + Lw * i;
+                            ix[p][i] = (p < a.n_parts && i < G && m.z >= 0 && t < m.y) ? __ldg(a.gidx[p] + m.x + t) : -1;
+                        }
+                };
+                load_idx(m_n, ix_n);
+                while (r_n < N) {
+                    const int r0 = r_n;
+                    const int4 m = m_n;
+                    int ix[kMaxParts][kMaxG];
+#pragma unroll
+                    for (int p = 0; p < kMaxParts; ++p)
+#pragma unroll
+                        for (int i = 0; i < kMaxG; ++i) ix[p][i] = ix_n[p][i];
+                    const int rr = r0 + grp;  // this lane group's row
+                    const bool row_ok = rr < N && m.z >= 0;
+                    const int nmax = __reduce_max_sync(0xffffffffu, row_ok ? m.y : 0);
+                    // the single-row part: every tuple of a row names the same table row (else the
+                    // warp takes the general path for its rows)
+                    int first1 = -1;
+                    bool single = true;
+                    if (K1) {
+                        first1 = __shfl_sync(0xffffffffu, ix[0][0], grp << lsh);
+#pragma unroll
+                        for (int i = 0; i < kMaxG; ++i)
+                            single = single && (i >= G || ix[0][i] < 0 || ix[0][i] == first1);
+                        single = __all_sync(0xffffffffu, single);
+                    }
+                    // the next rows' descriptors and indices load while these rows are summed
+                    r_n = take();
+                    m_n = meta_of(r_n + grp);
+                    load_idx(m_n, ix_n);
+                    if (!single) {
+                        // general path, row by row (indices reloaded in row layout)
+                        for (int g = 0; g < G; ++g) {
+                            const int r = r0 + g;
+                            if (r >= N) break;
+                            const int4 mg = meta_of(r);
+                            if (mg.z < 0) {
+                                zero_row(r, lane, 32);
+                                continue;
+                            }
+                            int ixr[kMaxParts];
+#pragma unroll
+                            for (int p = 0; p < kMaxParts; ++p)
+                                ixr[p] = (p < a.n_parts && lane < mg.y) ? __ldg(a.gidx[p] + mg.x + lane) : -1;
+                            for (int c = lane; c < zch; c += 32)
+                                z_store(r, c, __ldg(reinterpret_cast<const uint4*>(a.zrows + (int64_t)mg.z * a.d_z) + c));
+#pragma unroll
+                            for (int p = 0; p < kMaxParts; ++p) {
+                                if (p >= a.n_parts) break;
+                                float acc[8];
+                                part_sum<KAHAN>(a.tbl[p], a.width[p], a.kind[p], ixr[p], mg.y, lane, acc);
+                                if (lane < (a.width[p] >> 3)) store_pair(sb, blk, a.n_kb, a.kofs[p], r, lane, acc);
+                            }
+                        }
+                        continue;
+                    }
+                    // every load of the rows' first 16 tuples (and the single-row part, and z) in flight
+                    // before any is summed
+                    uint4 zc[kMaxZ];
+#pragma unroll
+                    for (int i = 0; i < kMaxZ; ++i) {
+                        const int c = ch + Lw * i;
+                        zc[i] = (BWD && row_ok && c < zch)
+                                    ? __ldg(reinterpret_cast<const uint4*>(a.zrows + (int64_t)m.z * a.d_z) + c)
+                                    : make_uint4(0u, 0u, 0u, 0u);
+                    }
+                    uint4 d1 = make_uint4(0u, 0u, 0u, 0u);
+                    if (K1 && row_ok && m.y > 0)
+                        d1 = __ldg(reinterpret_cast<const uint4*>(a.tbl[0]) + (int64_t)first1 * Lw + ch);
+                    float acc[8], cmp[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[i] = cmp[i] = 0.f;
+                    if (K0) {
+                        const uint4* __restrict__ base = reinterpret_cast<const uint4*>(a.tbl[K1]) + ch;
+                        // round 0: tuples 0..15, round 1: 16..31 (rows of more than 16 tuples)
+#pragma unroll
+                        for (int round = 0; round < 2; ++round) {
+                            if (round == 1 && nmax <= kRound) break;
+                            uint4 u[kRound];
+#pragma unroll
+                            for (int q = 0; q < kRound; ++q) {
+                                const int j = round * kRound + q;  // compile-time
+                                const int src = (grp << lsh) + (j & (Lw - 1));
+                                // register j / L of the group's lanes holds tuple j
+                                const int jr = j >> lsh;
+                                int v = -1;
+#pragma unroll
+                                for (int i = 0; i < kMaxG; ++i)
+                                    if (i == jr) v = ix[K1][i];
+                                const int r = __shfl_sync(0xffffffffu, v, src);
+                                u[q] = (row_ok && j < m.y) ? __ldg(base + (int64_t)r * Lw) : make_uint4(0u, 0u, 0u, 0u);
+                            }
+#pragma unroll
+                            for (int q = 0; q < kRound; ++q) {
+                                if (round * kRound + q >= nmax) break;
+                                add8(acc, cmp, u[q], KAHAN);
+                            }
+                        }
+                    }
+                    if (rr < N) {
+                        if (!row_ok) {
+                            zero_row(rr, ch, Lw);
+                        } else {
+                            if (K1) {
+                                // count x a bf16 value is exact in f32 (count <= 32)
+                                float a1[8];
+                                const float c1 = (float)m.y;
+                                const uint32_t w[4] = {d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    a1[2 * i] = c1 * __uint_as_float(w[i] << 16);
+                                    a1[2 * i + 1] = c1 * __uint_as_float(w[i] & 0xffff0000u);
+                                }
+                                store_pair(sb, blk, a.n_kb, a.kofs[0], rr, ch, a1);
+                            }
+                            if (K0) {
+                                if (KAHAN) {
+#pragma unroll
+                                    for (int i = 0; i < 8; ++i) acc[i] -= cmp[i];
+                                }
+                                store_pair(sb, blk, a.n_kb, a.kofs[K1], rr, ch, acc);
+                            }
+#pragma unroll
+                            for (int i = 0; i < kMaxZ; ++i) {
+                                const int c = ch + Lw * i;
+                                if (BWD && c < zch) z_store(rr, c, zc[i]);
+                            }
+                            for (int c = ch + Lw * kMaxZ; BWD && c < zch; c += Lw)
+                                z_store(rr, c, __ldg(reinterpret_cast<const uint4*>(a.zrows + (int64_t)m.z * a.d_z) + c));
+                        }
+                    }
+                }
             }
             fence_proxy_async();
             mbar_arrive(smem_u32(&full[s]));
@@ -459,6 +598,312 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
     tc_fence_before();
     __syncthreads();
     if (warp == kMmaWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, a.tmem_cols);
+    }
+}
+
+// ------------------------------------------------------------------------------ two-kernel forward
+// For a plan whose H keys are unique, the forward runs as two kernels:
+//   seg_sum_kernel  S_src[v] = sum over virtual row v's tuples of z[hs_t] (f32 on CUDA cores, high
+//                   occupancy, the next row's tuple indices loading while a row is summed), stored
+//                   as a bf16 pair S_hi | S_lo per row;
+//   agg_gemm_kernel D1 = W_src [S_hi; S_lo] with S staged by TMA, D2 = W_dst z[hd(v)] with the dst rows
+//                   (exact bf16) copied by cp.async, and Out = D1 + n_v (D2 + b) in the epilogue (the
+//                   dst part of S is n_v z[hd(v)], so scaling D2 gives it exactly).
+
+// S[v][0, w) = S_hi, S[v][kpad, kpad + w) = S_lo of the sum of the tuples' table rows; the other
+// columns of the row zero. A warp takes 32 virtual rows at a time (their descriptors in one load);
+// lane groups of L = w / 8 lanes take every G-th tuple (a lane = one 16-byte chunk of a row).
+template <bool KAHAN>
+__global__ void __launch_bounds__(256) seg_sum_kernel(const int4* __restrict__ vr, int64_t nv,
+                                                      const int32_t* __restrict__ gidx,
+                                                      const uint16_t* __restrict__ tbl, int w, int kpad,
+                                                      uint16_t* __restrict__ S) {
+    const int lane = threadIdx.x & 31;
+    const int L = w >> 3, lsh = 31 - __clz(L), G = 32 >> lsh;
+    const int grp = lane >> lsh, ch = lane & (L - 1);
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint4* __restrict__ base = reinterpret_cast<const uint4*>(tbl) + ch;
+    const int pitch = 2 * kpad;
+    for (int64_t vb = warp0 * 32; vb < nv; vb += nw * 32) {
+        const int4 mine = vb + lane < nv ? __ldg(vr + vb + lane) : make_int4(0, 0, -1, -1);
+        const int nrows = (int)imin64(32, nv - vb);
+        int ix;
+        {
+            const int x0 = __shfl_sync(0xffffffffu, mine.x, 0), y0 = __shfl_sync(0xffffffffu, mine.y, 0);
+            ix = lane < y0 ? __ldg(gidx + x0 + lane) : -1;
+        }
+        for (int j = 0; j < nrows; ++j) {
+            const int n = __shfl_sync(0xffffffffu, mine.y, j);
+            // the next row's tuple indices load while this row is summed
+            const int xn = __shfl_sync(0xffffffffu, mine.x, (j + 1) & 31);
+            const int yn = j + 1 < nrows ? __shfl_sync(0xffffffffu, mine.y, (j + 1) & 31) : 0;
+            const int ixn = lane < yn ? __ldg(gidx + xn + lane) : -1;
+            float acc[8], cmp[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = cmp[i] = 0.f;
+            for (int j0 = 0; j0 < n; j0 += kUnroll * G) {
+                uint4 u[kUnroll];
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) {
+                    const int jj = j0 + q * G + grp;
+                    const int r = __shfl_sync(0xffffffffu, ix, jj & 31);
+                    u[q] = jj < n ? __ldg(base + (int64_t)r * L) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) add8(acc, cmp, u[q], KAHAN);
+            }
+            for (int off = L; off < 32; off <<= 1) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (KAHAN) {
+                        const float s2 = __shfl_xor_sync(0xffffffffu, acc[i], off);
+                        const float c2 = __shfl_xor_sync(0xffffffffu, cmp[i], off);
+                        acc[i] = (acc[i] - cmp[i]) + (s2 - c2);
+                        cmp[i] = 0.f;
+                    } else {
+                        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+                    }
+                }
+            }
+            if (KAHAN) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] -= cmp[i];
+            }
+            if (lane < (kpad >> 3)) {
+                uint32_t hi[4] = {0u, 0u, 0u, 0u}, lo[4] = {0u, 0u, 0u, 0u};
+                if (lane < L) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        hi[i] = pack_bf16x2(acc[2 * i], acc[2 * i + 1]);
+                        const float h0 = __uint_as_float(hi[i] << 16), h1 = __uint_as_float(hi[i] & 0xffff0000u);
+                        lo[i] = pack_bf16x2(acc[2 * i] - h0, acc[2 * i + 1] - h1);
+                    }
+                }
+                uint16_t* row = S + (vb + j) * pitch + 8 * lane;
+                *reinterpret_cast<uint4*>(row) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4*>(row + kpad) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            }
+            ix = ixn;
+        }
+    }
+}
+
+// Dst H row of every virtual row (the first tuple's; all tuples of a row share it when H keys are
+// unique), or -1 for an empty row.
+__global__ void vr_first_kernel(const int4* __restrict__ vr, int64_t nv, const int32_t* __restrict__ hd, int32_t* d1) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        const int4 m = vr[v];
+        d1[v] = m.y > 0 ? hd[m.x] : -1;
+    }
+}
+
+constexpr int kGemmThreads = 256;   // warps 0-2 loaders, 3 MMA, 4-7 epilogue
+constexpr int kGemmLoaders = 96;
+constexpr int kGemmMma = 3;
+constexpr int kGemmEpi0 = 4;
+
+struct GemmArgs {
+    const int4* vr;
+    int64_t nv, n_tiles;
+    const int32_t* d1;        // per virtual row: the dst table row (-1: zeros)
+    const uint16_t* rtbl;     // dst table, bf16 rows of w_r elements
+    int w_r;                  // 0: no dst part
+    int n_kb_s, n_kb_r, kpad_s, m_blocks, n_feat;
+    const float* bias;
+    float* out;
+    float* vpart;
+    int accumulate, tile_n, stages;
+    uint32_t idesc, tmem_cols;
+    int* status;
+};
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap smap,
+                const __grid_constant__ GemmArgs a) {
+    extern __shared__ uint8_t dyn_smem[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~(uintptr_t)1023);
+    const int N = a.tile_n;
+    const int n_kb = a.n_kb_s + a.n_kb_r;
+    const uint32_t a_bytes = (uint32_t)n_kb * a.m_blocks * 16384u;
+    const uint32_t blk = (uint32_t)N * 128u;
+    const uint32_t stage_bytes = (uint32_t)(2 * a.n_kb_s + a.n_kb_r) * blk;
+    const uint32_t s_bytes = (uint32_t)(2 * a.n_kb_s) * blk;  // TMA bytes of one stage
+    uint8_t* a_smem = base;
+    uint8_t* st_smem = base + a_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(st_smem + (size_t)a.stages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + a.stages;
+    uint64_t* tfull = bars + 2 * a.stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wbar = tempty + 2;
+    uint64_t* drain = wbar + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(smem_u32(&full[s]), kGemmLoaders + 1);  // the loaders' copies + the TMA's bytes
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&tfull[i]), 1);
+            mbar_init(smem_u32(&tempty[i]), 32 * kEpiWarps);
+        }
+        mbar_init(smem_u32(wbar), 1);
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == kGemmMma) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t buf_cols = 2u * a.m_blocks * N;  // D1 and D2 of one accumulator buffer
+
+    if (tid < kGemmLoaders) {
+        // ------------------------------------------------------------------ loaders
+        const int rch = a.w_r >> 3;  // 16-byte chunks of a dst row
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
+            const int s = lt % a.stages;
+            const uint32_t use = (uint32_t)(lt / a.stages);
+            if (!mbar_wait(smem_u32(&empty[s]), (use & 1u) ^ 1u, a.status, abort_flag)) break;
+            const uint32_t sb = smem_u32(st_smem + (size_t)s * stage_bytes);
+            const int64_t v0 = tile * N;
+            if (tid == 0) {
+                mbar_arrive_expect_tx(smem_u32(&full[s]), s_bytes);
+                for (int hl = 0; hl < 2; ++hl)
+                    for (int kb = 0; kb < a.n_kb_s; ++kb)
+                        tma_load_2d(sb + (uint32_t)(hl * a.n_kb_s + kb) * blk, &smap, hl * a.kpad_s + kb * 64, (int)v0,
+                                    smem_u32(&full[s]));
+            }
+            // dst rows: (row, chunk) pairs over the loader threads; rows past the end and empty rows
+            // are zero-filled by the copy
+            const uint32_t rb = sb + (uint32_t)(2 * a.n_kb_s) * blk;
+            for (int i = tid; i < N * rch; i += kGemmLoaders) {
+                const int r = i / rch, c = i - r * rch;
+                const int64_t v = v0 + r;
+                const int hrow = v < a.nv ? __ldg(a.d1 + v) : -1;
+                const uint32_t dst = rb + (uint32_t)(c >> 3) * blk + (uint32_t)r * 128u +
+                                     ((((uint32_t)c & 7u) ^ ((uint32_t)r & 7u)) << 4);
+                const uint16_t* src = hrow >= 0 ? a.rtbl + (int64_t)hrow * a.w_r + 8 * c : a.rtbl;
+                cp_async_16(dst, src, hrow >= 0 ? 16u : 0u);
+            }
+            cp_async_mbar_arrive_noinc(smem_u32(&full[s]));
+        }
+        cp_async_wait<0>();
+    } else if (warp == kGemmMma) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t wb = smem_u32(wbar);
+            mbar_arrive_expect_tx(wb, a_bytes);
+            for (int kb = 0; kb < n_kb; ++kb)
+                for (int mb = 0; mb < a.m_blocks; ++mb)
+                    tma_load_2d(smem_u32(a_smem + (size_t)(kb * a.m_blocks + mb) * 16384u), &amap, kb * 64, mb * 128, wb);
+            bool ok = mbar_wait(wb, 0, a.status, abort_flag);
+            tc_fence_after();
+            int lt = 0;
+            for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++lt) {
+                const int s = lt % a.stages;
+                const uint32_t use = (uint32_t)(lt / a.stages);
+                const int acc = lt & 1;
+                const uint32_t ause = (uint32_t)(lt >> 1);
+                if (!mbar_wait(smem_u32(&tempty[acc]), (ause & 1u) ^ 1u, a.status, abort_flag)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&full[s]), use & 1u, a.status, abort_flag)) { ok = false; break; }
+                fence_proxy_async();  // the cp.async rows were written through the generic proxy
+                tc_fence_after();
+                const uint32_t sb = smem_u32(st_smem + (size_t)s * stage_bytes);
+                const uint32_t d1 = tmem_base + (uint32_t)acc * buf_cols;
+                for (int mb = 0; mb < a.m_blocks; ++mb) {
+                    uint32_t acc1 = 0, acc2 = 0;
+                    for (int kb = 0; kb < n_kb; ++kb) {
+                        const uint32_t ab = smem_u32(a_smem + (size_t)(kb * a.m_blocks + mb) * 16384u);
+                        const bool src = kb < a.n_kb_s;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint64_t adesc = sw128_kmajor_desc(ab + k * 32);
+                            if (src) {
+#pragma unroll
+                                for (int hl = 0; hl < 2; ++hl) {
+                                    const uint64_t bdesc =
+                                        sw128_kmajor_desc(sb + (uint32_t)(hl * a.n_kb_s + kb) * blk + k * 32);
+                                    mma_bf16(d1 + (uint32_t)mb * N, adesc, bdesc, a.idesc, acc1);
+                                    acc1 = 1;
+                                }
+                            } else {
+                                const uint64_t bdesc = sw128_kmajor_desc(
+                                    sb + (uint32_t)(2 * a.n_kb_s + kb - a.n_kb_s) * blk + k * 32);
+                                mma_bf16(d1 + (uint32_t)(a.m_blocks + mb) * N, adesc, bdesc, a.idesc, acc2);
+                                acc2 = 1;
+                            }
+                        }
+                    }
+                }
+                mma_commit(smem_u32(&empty[s]));
+                mma_commit(smem_u32(&tfull[acc]));
+            }
+            mma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0, a.status, abort_flag);
+        }
+        __syncwarp();
+    } else if (warp >= kGemmEpi0) {
+        // ------------------------------------------------------------------ epilogue
+        const int q = warp & 3;
+        const bool has_r = a.n_kb_r > 0;
+        float bias_r[2];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+            const int o = mb * 128 + 32 * q + lane;
+            bias_r[mb] = (a.bias && mb < a.m_blocks && o < a.n_feat) ? a.bias[o] : 0.f;
+        }
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            const uint32_t ause = (uint32_t)(lt >> 1);
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), ause & 1u, a.status, abort_flag))) break;
+            tc_fence_after();
+            const int64_t v0 = tile * N;
+            for (int c = 0; c < N / 32; ++c) {
+                const int64_t vb = v0 + 32 * c;
+                if (vb >= a.nv) break;
+                const int4 mt = vb + lane < a.nv ? __ldg(a.vr + vb + lane) : make_int4(0, 0, -1, -1);
+                for (int mb = 0; mb < a.m_blocks; ++mb) {
+                    if (mb * 128 + 32 * q >= a.n_feat) continue;
+                    const int o = mb * 128 + 32 * q + lane;
+                    const bool o_ok = o < a.n_feat;
+                    const float bo = mb == 0 ? bias_r[0] : bias_r[1];
+                    const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * buf_cols +
+                                        (uint32_t)mb * N + (uint32_t)(32 * c);
+                    uint32_t v1[32], v2[32];
+                    tmem_ld_32x32b_x32(ta, v1);
+                    if (has_r) tmem_ld_32x32b_x32(ta + (uint32_t)a.m_blocks * N, v2);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int row = __shfl_sync(0xffffffffu, mt.z, j);
+                        const int part = __shfl_sync(0xffffffffu, mt.w, j);
+                        const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
+                        if (row < 0) break;
+                        if (o_ok) {
+                            const float d2 = has_r ? __uint_as_float(v2[j]) : 0.f;
+                            const float y = __uint_as_float(v1[j]) + nj * (d2 + bo);
+                            if (part >= 0) __stcg(a.vpart + (int64_t)part * a.n_feat + o, y);
+                            else emit_out(a.out + (int64_t)row * a.n_feat + o, y, a.accumulate);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&tempty[acc]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kGemmMma) {
         tc_fence_after();
         tmem_dealloc(tmem_base, a.tmem_cols);
     }
@@ -715,9 +1160,44 @@ inline int grid_for(int64_t n, int threads = 256) {
 
 inline bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
+// Fix-up jobs of the split rows {row, first partial, chunks} (host copy): one job per row of at most
+// kFixChunk chunks, otherwise one per kFixChunk chunks into level-2 slots plus one level-2 job.
+relnn_status make_fix_jobs(VRows& V, const int4* d_splits, int64_t n_split, cudaStream_t st) {
+    V.n_fix1 = V.n_fix2 = V.n_l2 = 0;
+    if (n_split == 0) return RELNN_OK;
+    std::vector<int4> sp((size_t)n_split);
+    RELNN_CUDA(cudaMemcpyAsync(sp.data(), d_splits, sizeof(int4) * n_split, cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    std::vector<int4> j1, j2;
+    int64_t l2 = 0;
+    for (const int4& sj : sp) {
+        if (sj.z <= kFixChunk) {
+            j1.push_back(make_int4(sj.x, sj.y, sj.z, -1));
+        } else {
+            const int nc = (sj.z + kFixChunk - 1) / kFixChunk;
+            for (int c = 0; c < nc; ++c)
+                j1.push_back(make_int4(sj.x, sj.y + c * kFixChunk, std::min(kFixChunk, sj.z - c * kFixChunk), (int)(l2 + c)));
+            j2.push_back(make_int4(sj.x, (int)l2, nc, -1));
+            l2 += nc;
+        }
+    }
+    RELNN_TRY(V.fix1.alloc_nosync(sizeof(int4) * j1.size(), st));
+    RELNN_CUDA(cudaMemcpyAsync(V.fix1.p, j1.data(), sizeof(int4) * j1.size(), cudaMemcpyHostToDevice, st));
+    if (!j2.empty()) {
+        RELNN_TRY(V.fix2.alloc_nosync(sizeof(int4) * j2.size(), st));
+        RELNN_CUDA(cudaMemcpyAsync(V.fix2.p, j2.data(), sizeof(int4) * j2.size(), cudaMemcpyHostToDevice, st));
+    }
+    RELNN_CUDA(cudaStreamSynchronize(st));  // the job vectors are copied from, and the buffers are shared
+    V.n_fix1 = (int64_t)j1.size();
+    V.n_fix2 = (int64_t)j2.size();
+    V.n_l2 = l2;
+    return RELNN_OK;
+}
+
 // Builds (once) the virtual rows of an ordered tuple list: `sorted` = the keys ascend over rows
 // 0..R-1 and every row gets at least one virtual row (an empty row writes zeros); otherwise the
-// rows are the runs of equal keys in list order.
+// rows are the runs of equal keys in list order. A sorted list takes one synchronisation (the
+// totals; buffers are sized by bounds and allocated before it), plus one when rows were cut.
 relnn_status ensure_vrows(VRows& V, const int32_t* key, int64_t m, int64_t R, bool sorted, cudaStream_t st) {
     if (V.nv >= 0) return RELNN_OK;
     DevBuf beg, end, rkey, flag;
@@ -732,6 +1212,10 @@ relnn_status ensure_vrows(VRows& V, const int32_t* key, int64_t m, int64_t R, bo
         rows = nr;
     }
     const int64_t r1 = std::max<int64_t>(rows, 1);
+    // every row gives ceil(cnt / kChunk) virtual rows (at least one), and a row is cut only when it
+    // holds more than kChunk tuples
+    const int64_t nv_max = rows + m / kChunk + 1;
+    const int64_t ns_max = std::min<int64_t>(r1, m / (kChunk + 1) + 1);
     RELNN_TRY(beg.alloc_tmp(sizeof(int32_t) * r1, st));
     RELNN_TRY(end.alloc_tmp(sizeof(int32_t) * r1, st));
     if (sorted) {
@@ -743,62 +1227,31 @@ relnn_status ensure_vrows(VRows& V, const int32_t* key, int64_t m, int64_t R, bo
         if (m > 0) { vr_runs_kernel<<<grid_for(m), 256, 0, st>>>(key, m, flag.as<int32_t>(), beg.as<int32_t>(), end.as<int32_t>(),
                                                                rkey.as<int32_t>()); note_launch(); }
     }
-    DevBuf cnts;  // nch | npart | split, each rows + 1 (exclusive scans in place)
-    RELNN_TRY(cnts.alloc_tmp(sizeof(int32_t) * 3 * (rows + 1), st));
+    DevBuf cnts;  // nch | npart | split, each rows + 1 (exclusive scans in place), then the 3 totals
+    RELNN_TRY(cnts.alloc_tmp(sizeof(int32_t) * (3 * (rows + 1) + 4), st));
     int32_t* nch = cnts.as<int32_t>();
     int32_t* npart = nch + rows + 1;
     int32_t* split = npart + rows + 1;
-    if (sorted) RELNN_TRY(V.cnt.alloc(sizeof(int32_t) * r1, st));
+    int32_t* tot_d = split + rows + 1;
+    if (sorted) RELNN_TRY(V.cnt.alloc_nosync(sizeof(int32_t) * r1, st));
+    RELNN_TRY(V.vr.alloc_nosync(sizeof(int4) * nv_max, st));
+    DevBuf splits;
+    RELNN_TRY(splits.alloc_tmp(sizeof(int4) * ns_max, st));
     if (rows > 0) { vr_count_kernel<<<grid_for(rows), 256, 0, st>>>(beg.as<int32_t>(), end.as<int32_t>(), rows, nch, npart, split,
                                                                    sorted ? V.cnt.as<int32_t>() : nullptr); note_launch(); }
-    RELNN_TRY(exclusive_scan<int32_t>(nch, nch, rows, nch + rows, st));
-    RELNN_TRY(exclusive_scan<int32_t>(npart, npart, rows, npart + rows, st));
-    RELNN_TRY(exclusive_scan<int32_t>(split, split, rows, split + rows, st));
-    int32_t tot[3] = {0, 0, 0};
-    RELNN_CUDA(cudaMemcpyAsync(&tot[0], nch + rows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    RELNN_CUDA(cudaMemcpyAsync(&tot[1], npart + rows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    RELNN_CUDA(cudaMemcpyAsync(&tot[2], split + rows, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    RELNN_CUDA(cudaStreamSynchronize(st));
-    const int64_t nv = tot[0], n_split = tot[2];
-    RELNN_TRY(V.vr.alloc(sizeof(int4) * std::max<int64_t>(nv, 1), st));
-    DevBuf splits;
-    RELNN_TRY(splits.alloc_tmp(sizeof(int4) * std::max<int64_t>(n_split, 1), st));
+    RELNN_TRY(exclusive_scan<int32_t>(nch, nch, rows, tot_d, st));
+    RELNN_TRY(exclusive_scan<int32_t>(npart, npart, rows, tot_d + 1, st));
+    RELNN_TRY(exclusive_scan<int32_t>(split, split, rows, tot_d + 2, st));
     if (rows > 0) { vr_fill_kernel<<<grid_for(rows), 256, 0, st>>>(beg.as<int32_t>(), end.as<int32_t>(),
                                                                   sorted ? nullptr : rkey.as<int32_t>(), rows, nch, npart,
                                                                   split, V.vr.as<int4>(), splits.as<int4>()); note_launch(); }
     RELNN_CUDA(cudaGetLastError());
-    // fix-up jobs of split rows (a few per heavy row): built on the host
-    std::vector<int4> sp((size_t)n_split);
-    if (n_split > 0)
-        RELNN_CUDA(cudaMemcpyAsync(sp.data(), splits.p, sizeof(int4) * n_split, cudaMemcpyDeviceToHost, st));
+    int32_t tot[3] = {0, 0, 0};
+    RELNN_CUDA(cudaMemcpyAsync(tot, tot_d, sizeof(tot), cudaMemcpyDeviceToHost, st));
     RELNN_CUDA(cudaStreamSynchronize(st));
-    std::vector<int4> j1, j2;
-    int64_t l2 = 0;
-    for (const int4& s : sp) {
-        if (s.z <= kFixChunk) {
-            j1.push_back(make_int4(s.x, s.y, s.z, -1));
-        } else {
-            const int nc = (s.z + kFixChunk - 1) / kFixChunk;
-            for (int c = 0; c < nc; ++c)
-                j1.push_back(make_int4(s.x, s.y + c * kFixChunk, std::min(kFixChunk, s.z - c * kFixChunk), (int)(l2 + c)));
-            j2.push_back(make_int4(s.x, (int)l2, nc, -1));
-            l2 += nc;
-        }
-    }
-    V.n_fix1 = (int64_t)j1.size();
-    V.n_fix2 = (int64_t)j2.size();
-    V.n_l2 = l2;
-    if (!j1.empty()) {
-        RELNN_TRY(V.fix1.alloc(sizeof(int4) * j1.size(), st));
-        RELNN_CUDA(cudaMemcpyAsync(V.fix1.p, j1.data(), sizeof(int4) * j1.size(), cudaMemcpyHostToDevice, st));
-    }
-    if (!j2.empty()) {
-        RELNN_TRY(V.fix2.alloc(sizeof(int4) * j2.size(), st));
-        RELNN_CUDA(cudaMemcpyAsync(V.fix2.p, j2.data(), sizeof(int4) * j2.size(), cudaMemcpyHostToDevice, st));
-    }
-    if (!j1.empty()) RELNN_CUDA(cudaStreamSynchronize(st));  // the job vectors are copied from
+    RELNN_TRY(make_fix_jobs(V, splits.as<int4>(), tot[2], st));
     V.n_parts = tot[1];
-    V.nv = nv;
+    V.nv = tot[0];
     return RELNN_OK;
 }
 
@@ -815,8 +1268,10 @@ AggCfg agg_config(int n_kb, int m_blocks, bool bwd, int z_blocks, int m_dw, int 
     const uint32_t a_bytes = (uint32_t)n_kb * m_blocks * 16384u;
     // two stages at the largest N; a single stage of 32 rows as the last resort (wide A operands)
     const int tries[4][2] = {{128, 2}, {64, 2}, {32, 2}, {32, 1}};
+    const int64_t want = tune_get(RELNN_TUNE_AGG_ROWS);  // 0: the largest that fits
     for (const auto& tr : tries) {
         const int N = tr[0];
+        if (want != 0 && N > want) continue;
         const size_t stage = (size_t)(2 * n_kb + z_blocks) * N * 128;
         const size_t fixed = 1024 + a_bytes + 512;
         if (fixed + stage > (size_t)kSmemLimit) continue;
@@ -836,18 +1291,37 @@ AggCfg agg_config(int n_kb, int m_blocks, bool bwd, int z_blocks, int m_dw, int 
     return c;
 }
 
-template <bool BWD, bool KAHAN>
-relnn_status launch_agg(const CUtensorMap& amap, const AggArgs& a, size_t smem, int grid, cudaStream_t st, int prof) {
+template <bool BWD, bool KAHAN, int K1, int K0>
+relnn_status launch_agg_t(const CUtensorMap& amap, const AggArgs& a, size_t smem, int grid, cudaStream_t st, int prof) {
     static bool attr_set = false;
     if (!attr_set) {
-        RELNN_CUDA(cudaFuncSetAttribute(agg_tc_kernel<BWD, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(agg_tc_kernel<BWD, KAHAN, K1, K0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kSmemLimit));
         attr_set = true;
     }
     ProfToken pt = prof_begin(prof, st);
-    { agg_tc_kernel<BWD, KAHAN><<<grid, kThreads, smem, st>>>(amap, a); note_launch(); }
+    { agg_tc_kernel<BWD, KAHAN, K1, K0><<<grid, kThreads, smem, st>>>(amap, a); note_launch(); }
     prof_end(pt, st);
     RELNN_CUDA(cudaGetLastError());
     return RELNN_OK;
+}
+
+// The instantiation for the launch's parts: forward (a single-row dst part, then a per-tuple src
+// part, or the src part alone), backward src pass (per-tuple dOut rows), backward dst pass (a
+// single dOut row per run).
+template <bool BWD>
+relnn_status launch_agg(const CUtensorMap& amap, const AggArgs& a, bool kahan, size_t smem, int grid, cudaStream_t st,
+                        int prof) {
+    const bool k1 = a.n_parts == 2 || a.kind[0] == 1;
+    const bool k0 = a.n_parts == 2 || a.kind[0] == 0;
+    if constexpr (!BWD) {
+        if (k1 && k0) return kahan ? launch_agg_t<false, true, 1, 1>(amap, a, smem, grid, st, prof)
+                                   : launch_agg_t<false, false, 1, 1>(amap, a, smem, grid, st, prof);
+    }
+    if (k1) return kahan ? launch_agg_t<BWD, true, 1, 0>(amap, a, smem, grid, st, prof)
+                         : launch_agg_t<BWD, false, 1, 0>(amap, a, smem, grid, st, prof);
+    return kahan ? launch_agg_t<BWD, true, 0, 1>(amap, a, smem, grid, st, prof)
+                 : launch_agg_t<BWD, false, 0, 1>(amap, a, smem, grid, st, prof);
 }
 
 // Fix-up of the split rows of one launch: partial rows in p.vpart (level-2 sums after them).
@@ -866,6 +1340,35 @@ relnn_status agg_fixup(const VRows& V, const float* vpart, float* vpart2, float*
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Two-kernel forward: tile rows and stages of agg_gemm_kernel (two stages at the largest N).
+AggCfg gemm_config(int n_kb_s, int n_kb_r, int m_blocks) {
+    AggCfg c;
+    const uint32_t a_bytes = (uint32_t)(n_kb_s + n_kb_r) * m_blocks * 16384u;
+    const int64_t want = tune_get(RELNN_TUNE_AGG_ROWS);
+    for (int N : {128, 64, 32}) {
+        if (want != 0 && N > want) continue;
+        const size_t stage = (size_t)(2 * n_kb_s + n_kb_r) * N * 128;
+        const size_t fixed = 1024 + a_bytes + 512;
+        if (fixed + 2 * stage > (size_t)kSmemLimit) continue;
+        const uint32_t cols = 4u * m_blocks * N;
+        if (cols > 512) continue;
+        c.N = N;
+        c.stages = (int)std::min<size_t>(4, (kSmemLimit - fixed) / stage);
+        uint32_t t = 32;
+        while (t < cols) t <<= 1;
+        c.tmem_cols = t;
+        c.smem = fixed + (size_t)c.stages * stage;
+        return c;
+    }
+    return c;
+}
+
+bool two_kernel_forward(const Plan& p) {
+    const int kpad = ((p.d + 63) / 64) * 64;
+    return (!p.concat_dst || p.Ht().n_unique == p.n_h) && p.d % 8 == 0 && kpad <= 256 &&
+           gemm_config(kpad / 64, p.concat_dst ? kpad / 64 : 0, (p.d_out + 127) / 128).N > 0;
+}
 
 // Forward: A = W with each Concat part padded to 64 columns; M = output features.
 AggCfg fwd_cfg(const Plan& p) {
@@ -899,9 +1402,95 @@ bool agg_backward_ok(const Plan& p, const CallIO& io, const GradIO& g) {
     return g.dout != nullptr && aligned16(g.dout) && bwd_cfg(p).N > 0;
 }
 
+// Two-kernel forward (unique H keys or no dst part): gather-sum into S, then the TMA-fed GEMM.
+relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
+    const int kpad = ((p.d + 63) / 64) * 64;
+    const int n_kb_s = kpad / 64, n_kb_r = p.concat_dst ? kpad / 64 : 0;
+    const int m_blocks = (p.d_out + 127) / 128;
+    const AggCfg cfg = gemm_config(n_kb_s, n_kb_r, m_blocks);
+    const int rows_pad = m_blocks * 128, cols = (n_kb_s + n_kb_r) * 64;
+    RELNN_TRY(p.wpack.alloc(sizeof(uint16_t) * (size_t)rows_pad * cols));
+    CUtensorMap amap;
+    RELNN_TRY(encode_bf16_tile_map(&amap, p.wpack.p, cols, rows_pad));
+    size_t vp_max = 0;
+    int64_t nv_max = 0;
+    for (auto& b : p.br) {
+        VRows& V = b.vr_out;
+        RELNN_TRY(ensure_vrows(V, b.seg.as<int32_t>(), b.m, p.n_out, true, st));
+        if (p.concat_dst && !V.has_d1) {
+            RELNN_TRY(V.d1.alloc(sizeof(int32_t) * std::max<int64_t>(V.nv, 1), st));
+            if (V.nv > 0) { vr_first_kernel<<<grid_for(V.nv), 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hd.as<int32_t>(), V.d1.as<int32_t>()); note_launch(); }
+            RELNN_CUDA(cudaGetLastError());
+            V.has_d1 = true;
+        }
+        vp_max = std::max(vp_max, (size_t)(V.n_parts + V.n_l2) * p.d_out);
+        nv_max = std::max(nv_max, V.nv);
+    }
+    if (vp_max) RELNN_TRY(p.vpart.alloc(sizeof(float) * vp_max));
+    RELNN_TRY(p.sbuf.alloc(sizeof(uint16_t) * 2 * (size_t)kpad * std::max<int64_t>(nv_max, 1)));
+    static bool attr_set = false;
+    if (!attr_set) {
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        attr_set = true;
+    }
+    const int ss_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nv_max, 32 * 8), (int64_t)num_sms() * 8));
+    for (size_t i = 0; i < p.br.size(); ++i) {
+        BranchPlan& b = p.br[i];
+        const VRows& V = b.vr_out;
+        if (V.nv == 0) continue;
+        uint16_t* S = p.sbuf.as<uint16_t>();
+        {
+            ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
+            if (p.kahan) seg_sum_kernel<true><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(),
+                                                                         reinterpret_cast<const uint16_t*>(io.z), p.d, kpad, S);
+            else seg_sum_kernel<false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(),
+                                                                   reinterpret_cast<const uint16_t*>(io.z), p.d, kpad, S);
+            note_launch();
+            prof_end(pt, st);
+        }
+        RELNN_CUDA(cudaGetLastError());
+        { pack_a_fwd_kernel<<<grid_for((int64_t)rows_pad * cols), 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, p.d,
+                                                                               kpad, rows_pad, cols, p.wpack.as<uint16_t>()); note_launch(); }
+        CUtensorMap smap;
+        RELNN_TRY(encode_bf16_tile_map(&smap, S, 2 * kpad, V.nv, cfg.N));
+        GemmArgs a{};
+        a.vr = V.vr.as<int4>();
+        a.nv = V.nv;
+        a.n_tiles = ceil_div(V.nv, cfg.N);
+        a.d1 = p.concat_dst ? V.d1.as<int32_t>() : nullptr;
+        a.rtbl = reinterpret_cast<const uint16_t*>(io.z);
+        a.w_r = p.concat_dst ? p.d : 0;
+        a.n_kb_s = n_kb_s;
+        a.n_kb_r = n_kb_r;
+        a.kpad_s = kpad;
+        a.m_blocks = m_blocks;
+        a.n_feat = p.d_out;
+        a.bias = io.br[i].b;
+        a.out = out;
+        a.vpart = p.vpart.as<float>();
+        a.accumulate = i > 0 ? 1 : 0;  // every branch covers every output row: the first one stores
+        a.tile_n = cfg.N;
+        a.stages = cfg.stages;
+        a.idesc = tc::idesc_bf16_f32(128, cfg.N);
+        a.tmem_cols = cfg.tmem_cols;
+        a.status = p.status.as<int>();
+        const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
+        {
+            ProfToken pt = prof_begin(RELNN_PROF_AGG_FWD, st);
+            { agg_gemm_kernel<<<grid, kGemmThreads, cfg.smem, st>>>(amap, smap, a); note_launch(); }
+            prof_end(pt, st);
+        }
+        RELNN_CUDA(cudaGetLastError());
+        RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d_out, out, p.d_out, i > 0,
+                            p.kahan, st));
+    }
+    return RELNN_OK;
+}
+
 relnn_status forward_agg(Plan& p, const CallIO& io_in, float* out, cudaStream_t st) {
     CallIO io;
     RELNN_TRY(with_bf16_z(p, io_in, io, st));
+    if (two_kernel_forward(p)) return forward_two_kernel(p, io, out, st);
     const int n_parts = p.concat_dst ? 2 : 1;
     const int kpad = ((p.d + 63) / 64) * 64;
     const int n_kb = n_parts * kpad / 64;
@@ -960,8 +1549,7 @@ relnn_status forward_agg(Plan& p, const CallIO& io_in, float* out, cudaStream_t 
         a.tmem_cols = cfg.tmem_cols;
         a.status = p.status.as<int>();
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
-        if (p.kahan) RELNN_TRY((launch_agg<false, true>(amap, a, cfg.smem, grid, st, RELNN_PROF_AGG_FWD)));
-        else RELNN_TRY((launch_agg<false, false>(amap, a, cfg.smem, grid, st, RELNN_PROF_AGG_FWD)));
+        RELNN_TRY(launch_agg<false>(amap, a, p.kahan, cfg.smem, grid, st, RELNN_PROF_AGG_FWD));
         RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d_out, out, p.d_out, i > 0,
                             p.kahan, st));
     }
@@ -1074,8 +1662,7 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             a.idesc_dw = tc::idesc_bf16_f32(128, p.d, true, true);
             a.dw_col = cfg.dw_col;
             const int grid = (int)std::min<int64_t>(a.n_tiles, grid_max);
-            if (p.kahan) RELNN_TRY((launch_agg<true, true>(amap, a, cfg.smem, grid, st, RELNN_PROF_AGG_BWD)));
-            else RELNN_TRY((launch_agg<true, false>(amap, a, cfg.smem, grid, st, RELNN_PROF_AGG_BWD)));
+            RELNN_TRY(launch_agg<true>(amap, a, p.kahan, cfg.smem, grid, st, RELNN_PROF_AGG_BWD));
             RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d, g.dz, p.d, accumulate,
                                 p.kahan, st));
             if (dW) {

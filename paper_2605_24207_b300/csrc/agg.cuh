@@ -18,8 +18,9 @@ bool agg_backward_ok(const Plan& p, const CallIO& io, const GradIO& g);
 relnn_status forward_agg(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 relnn_status backward_agg(Plan& p, const CallIO& io, const GradIO& g, cudaStream_t st);
 
-// 2-D bf16 tensor map over a row-major [rows][cols] matrix, box 64 x 128, 128-byte swizzle (the
-// layout the tensor-core kernels stage their A operands in).
-relnn_status encode_bf16_tile_map(CUtensorMap* m, void* base, uint64_t cols, uint64_t rows);
+// 2-D bf16 tensor map over a row-major [rows][cols] matrix, box 64 columns x box_rows rows, 128-byte
+// swizzle (the K-major layout the tensor-core kernels stage their operands in); rows past the end
+// load as zeros.
+relnn_status encode_bf16_tile_map(CUtensorMap* m, void* base, uint64_t cols, uint64_t rows, uint32_t box_rows = 128);
 
 }  // namespace relnn

@@ -50,6 +50,9 @@ void prof_end(ProfToken& tok, cudaStream_t st);
         if (s_ != RELNN_OK) return s_;      \
     } while (0)
 
+// Current value of a tuning knob (RELNN_TUNE_*; relnn_tune_set).
+int64_t tune_get(int knob);
+
 // Keeps freed blocks of the device's default memory pool cached (no return to the OS at syncs), so
 // repeated plan builds reuse memory instead of mapping it again.
 void ensure_pool_cached();

@@ -151,8 +151,19 @@ extern "C" relnn_status relnn_rule_forward_noalloc(const float* d_z, int32_t d, 
                   std::to_string(kNaScratchFloats * 4) + " (split the call or use relnn_rule_forward)");
         return RELNN_ENOSPC;
     }
+    // 32 x 2d floats of the gathered Concat rows: up to 128 KB (2d = 1024), above the 48 KB a launch
+    // gets without asking, so the kernel's dynamic shared-memory limit is raised (an attribute of
+    // the function, not an allocation)
     const size_t smem = sizeof(float) * kNaTile * d_in;
-    RELNN_CHECK_ARG(smem <= 48 * 1024, "noalloc forward: 32 x 2d floats must fit in 48 KB of shared memory");
+    if (smem > 48 * 1024) {
+        static std::once_flag once;
+        static cudaError_t attr_err = cudaSuccess;
+        std::call_once(once, [] {
+            attr_err = cudaFuncSetAttribute(na_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(float) * kNaTile * 1024));
+        });
+        RELNN_CUDA(attr_err);
+    }
     float* scratch = nullptr;
     RELNN_TRY(scratch_ptr(&scratch));
     float* Wt = scratch;

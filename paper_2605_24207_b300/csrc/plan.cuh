@@ -28,10 +28,12 @@ namespace relnn {
 //   fix1/2   fix-up jobs of rows cut into several chunks (int4 {row, first slot, count, level-2 slot
 //            or -1}), level 2 only for rows with more chunks than one fix-up block adds
 //   cnt[r]   int32 tuples of row r (lists whose keys ascend over rows 0..R-1)
+//   d1[v]    int32 dst H row of virtual row v (forward lists of plans with unique H keys), or -1
 // Built once per list and cached (nv < 0: not built yet).
 struct VRows {
     int64_t nv = -1, n_parts = 0, n_l2 = 0, n_fix1 = 0, n_fix2 = 0;
-    DevBuf vr, fix1, fix2, cnt;
+    DevBuf vr, fix1, fix2, cnt, d1;
+    bool has_d1 = false;
 };
 
 struct BranchPlan {
@@ -70,6 +72,7 @@ struct Plan {
     DevBuf doutbf;    // bf16 copy of the output gradient for the backward's src pass
     DevBuf fixjobs;   // long segments handed from the fix-up to its block-per-segment pass
     DevBuf vpart;     // aggregate-first: f32 partial rows of chunks (and their level-2 sums)
+    DevBuf sbuf;      // aggregate-first: per virtual row the bf16 pair of its src sums
     // transformation push-down (RELNN_FLAG_PUSHDOWN): the identity plan of the per-H-row products,
     // the products P = Z W_src^T and Q = Z W_dst^T + b, and one column block of W
     std::unique_ptr<Plan> pd;
@@ -99,7 +102,7 @@ struct Plan {
     // a synchronising cudaFree), for plans whose work all ran on s.
     void retire_on(cudaStream_t s) {
         DevBuf* bufs[] = {&H.rows_sorted, &H.run_start, &H.uid_of_pos, &H.ukeys, &H.slot_keys, &H.slot_vals,
-                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &vpart, &pdP, &pdQ, &pdW, &inv_cnt, &mean_dout,
+                          &H.status, &out_keys, &status, &carry, &wpack, &scratch, &zbf, &doutbf, &fixjobs, &vpart, &sbuf, &pdP, &pdQ, &pdW, &inv_cnt, &mean_dout,
                           &max_arg, &carry_pos, &win_mask};
         for (DevBuf* b : bufs) {
             b->ordered = true;
@@ -108,7 +111,7 @@ struct Plan {
         if (pd) pd->retire_on(s);
         for (auto& b : br) {
             DevBuf* bb[] = {&b.hs, &b.hd, &b.er, &b.seg, &b.src_perm, &b.hs_src, &b.seg_src, &b.relu_mask,
-                            &b.vr_out.vr, &b.vr_out.fix1, &b.vr_out.fix2, &b.vr_out.cnt, &b.vr_src.vr, &b.vr_src.fix1,
+                            &b.vr_out.vr, &b.vr_out.fix1, &b.vr_out.fix2, &b.vr_out.cnt, &b.vr_out.d1, &b.vr_src.vr, &b.vr_src.fix1,
                             &b.vr_src.fix2, &b.vr_src.cnt, &b.vr_dst.vr, &b.vr_dst.fix1, &b.vr_dst.fix2,
                             &b.vr_dst.cnt};
             for (DevBuf* x : bb) {

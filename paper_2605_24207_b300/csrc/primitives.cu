@@ -3,8 +3,9 @@
 // Scan: reduce-then-scan. A block owns 4096 consecutive items (512 threads x 8 items in blocked
 // order); the block sums are scanned recursively and added back.
 //
-// Radix sort: the key bits are split into passes of equal width of at most 11 bits (a 20-bit key
-// takes two passes of 10). Each block owns a tile of 4096 keys split into 8 warp sub-tiles of 512
+// Radix sort: the key bits are split into passes of equal width of at most RELNN_TUNE_SORT_BITS
+// bits (default 8: a 20-bit key takes three passes of 7, so each digit of a 4096-key tile leaves as
+// a run of about 32 keys). Each block owns a tile of 4096 keys split into 8 warp sub-tiles of 512
 // keys that a warp visits in 16 steps of 32. Pass = (1) per-block digit histogram with
 // shared-memory atomics, (2) exclusive scan of the digit-major histogram, (3) stable scatter: a
 // key's destination is digit base + (keys of its digit in earlier blocks) + (in earlier warps of
@@ -270,8 +271,9 @@ relnn_status radix_sort_pairs(K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_
     if (result_in_tmp) *result_in_tmp = false;
     if (n <= 1 || nbits <= 0) return RELNN_OK;
     const int64_t nb64 = ceil_div(n, kSortTile);
-    // passes of equal width, at most kMaxDigitBits bits each
-    const int passes = (nbits + kMaxDigitBits - 1) / kMaxDigitBits;
+    // passes of equal width, at most RELNN_TUNE_SORT_BITS (<= kMaxDigitBits) bits each
+    const int max_bits = (int)std::min<int64_t>(kMaxDigitBits, std::max<int64_t>(4, tune_get(RELNN_TUNE_SORT_BITS)));
+    const int passes = (nbits + max_bits - 1) / max_bits;
     const int bits = (nbits + passes - 1) / passes;
     const unsigned mask = (1u << bits) - 1u;
     const int bins = (int)mask + 1;

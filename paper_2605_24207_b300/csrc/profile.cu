@@ -43,6 +43,20 @@ EvPair* take() {
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+constexpr int kKnobs = 2;
+std::atomic<int64_t> g_knobs[kKnobs] = {{8}, {0}};
+bool knob_ok(int knob, int64_t v) {
+    switch (knob) {
+        case RELNN_TUNE_SORT_BITS: return v >= 4 && v <= 11;
+        case RELNN_TUNE_AGG_ROWS: return v == 0 || v == 32 || v == 64 || v == 128;
+    }
+    return false;
+}
+}  // namespace
+
+int64_t tune_get(int knob) { return knob >= 0 && knob < kKnobs ? g_knobs[knob].load() : 0; }
+
 void ensure_pool_cached() {
     static std::atomic<uint64_t> done_mask{0};
     int dev = 0;
@@ -102,6 +116,18 @@ __global__ void __launch_bounds__(1024) fma_peak_kernel(float* out, int iters, f
 using namespace relnn;
 
 extern "C" {
+
+relnn_status relnn_tune_set(int32_t knob, int64_t value) {
+    RELNN_CHECK_ARG(knob_ok(knob, value), "tune: unknown knob or value out of range");
+    g_knobs[knob].store(value);
+    return RELNN_OK;
+}
+
+relnn_status relnn_tune_get(int32_t knob, int64_t* value) {
+    RELNN_CHECK_ARG(knob >= 0 && knob < kKnobs && value, "tune: unknown knob");
+    *value = g_knobs[knob].load();
+    return RELNN_OK;
+}
 
 relnn_status relnn_peak_fma_f32(int32_t iters, double* tflops, double* ms, void* stream) {
     RELNN_CHECK_ARG(iters > 0 && tflops, "peak fma: bad arguments");

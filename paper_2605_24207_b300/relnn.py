@@ -112,7 +112,8 @@ EXPORTS = [
     "relnn_rule_forward", "relnn_rule_backward", "relnn_plan_destroy",
     "relnn_profile_enable", "relnn_profile_read", "relnn_profile_reset", "relnn_launch_count",
 ]
-PROF_FWD_TC, PROF_FWD_FP32, PROF_FIXUP, PROF_BWD_TC, PROF_BWD_FP32, PROF_PLAN, PROF_AGG_FWD, PROF_AGG_BWD = range(8)
+(PROF_FWD_TC, PROF_FWD_FP32, PROF_FIXUP, PROF_BWD_TC, PROF_BWD_FP32, PROF_PLAN, PROF_AGG_FWD, PROF_AGG_BWD,
+ PROF_AGG_SUM) = range(9)
 
 
 def lib():
@@ -170,6 +171,10 @@ def lib():
     for name in EXPORTS[4:-1]:
         getattr(L, name).restype = C.c_int
     L.relnn_launch_count.restype = C.c_uint64
+    L.relnn_tune_set.argtypes = [C.c_int32, i64]
+    L.relnn_tune_set.restype = C.c_int
+    L.relnn_tune_get.argtypes = [C.c_int32, C.POINTER(i64)]
+    L.relnn_tune_get.restype = C.c_int
     L.relnn_peak_fma_f32.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     L.relnn_peak_fma_f32.restype = C.c_int
     _LIB = L
@@ -221,6 +226,20 @@ def profile_enable(on: bool = True):
 
 def profile_reset():
     _check(lib().relnn_profile_reset())
+
+
+TUNE_SORT_BITS, TUNE_AGG_ROWS = 0, 1
+
+
+def tune_set(knob: int, value: int):
+    """Sets a process-wide tuning knob (relnn_tune_set)."""
+    _check(lib().relnn_tune_set(int(knob), int(value)))
+
+
+def tune_get(knob: int) -> int:
+    v = C.c_int64()
+    _check(lib().relnn_tune_get(int(knob), C.byref(v)))
+    return v.value
 
 
 def peak_fma_f32(iters: int = 1 << 15, stream=None):
