@@ -105,6 +105,10 @@ typedef struct relnn_tri_s* relnn_tri_t;
  * Library
  * ------------------------------------------------------------------------------------------- */
 int32_t relnn_version(void);                      /* 100 * major + minor                          */
+int32_t relnn_build_flags(void);                  /* bit 0: the checked build (-DRELNN_CHECKED:
+                                                     gathered indices and output rows are tested
+                                                     on the device, a failing one raises
+                                                     RELNN_DEV_BOUNDS and the access is skipped)  */
 const char* relnn_status_string(relnn_status s);  /* static string                                */
 const char* relnn_last_error(void);               /* calling thread's last error message          */
 int32_t relnn_last_device_error(void);            /* RELNN_DEV_* of the last RELNN_EDEVICE        */
@@ -462,6 +466,14 @@ relnn_status relnn_profile_reset(void);
 #define RELNN_TUNE_AGG_ROWS 1
 relnn_status relnn_tune_set(int32_t knob, int64_t value);
 relnn_status relnn_tune_get(int32_t knob, int64_t* value);
+
+/* sync. Test of the bounded waits (no counterpart in the paper): one CTA waits, with the bounded
+ * mbarrier wait every tensor-core kernel of the library uses, on a barrier that nothing arrives at,
+ * under a budget of budget_us microseconds (0 < budget_us <= 1e6) instead of the kernels' 2 s. The
+ * wait gives up, the kernel returns and RELNN_EDEVICE is returned with relnn_last_device_error() ==
+ * RELNN_DEV_TIMEOUT after about budget_us; the device and the context stay usable. Errors: EINVAL,
+ * ECUDA. */
+relnn_status relnn_test_wait_timeout(int32_t budget_us, void* stream);
 
 /* sync. FP32 CUDA-core throughput probe: one launch of 2 x SMs blocks of 1024 threads, each thread
  * running 8 independent FMA chains for `iters` steps, timed by CUDA events on `stream` after one

@@ -73,6 +73,7 @@ struct AggArgs {
     // the part's first column in A's K dimension (a multiple of 64)
     const int32_t* gidx[kMaxParts];
     const uint16_t* tbl[kMaxParts];
+    int64_t tbl_rows[kMaxParts];
     int width[kMaxParts], kind[kMaxParts], kofs[kMaxParts];
     int n_parts, n_kb, m_blocks, n_feat;
     const float* bias;                         // forward: + n * bias[f]
@@ -108,8 +109,8 @@ __device__ __forceinline__ void add8(float (&acc)[8], float (&cmp)[8], const uin
 // chunk: `ix` holds lane j's tuple index (j < n). Returns the f32 sums of the chunk's 8 elements in
 // every lane of the chunk (groups of w / 8 lanes share nothing but the final butterfly).
 template <bool KAHAN>
-__device__ __forceinline__ void part_sum(const uint16_t* __restrict__ tbl, int w, int kind, int ix, int n, int lane,
-                                         float (&acc)[8]) {
+__device__ __forceinline__ void part_sum(const uint16_t* __restrict__ tbl, int64_t rows, int* status, int w, int kind,
+                                         int ix, int n, int lane, float (&acc)[8]) {
     const int L = w >> 3;  // lanes per table row (a power of two <= 32)
     const int G = 32 / L;  // tuples per warp step
     const int grp = lane / L, ch = lane - grp * L;
@@ -124,7 +125,7 @@ __device__ __forceinline__ void part_sum(const uint16_t* __restrict__ tbl, int w
             for (int q = 0; q < kUnroll; ++q) {
                 const int j = j0 + q * G + grp;
                 const int r = __shfl_sync(0xffffffffu, ix, j & 31);
-                u[q] = j < n ? __ldg(base + (int64_t)r * L) : make_uint4(0u, 0u, 0u, 0u);
+                u[q] = (j < n && in_bounds(r, rows, status)) ? __ldg(base + (int64_t)r * L) : make_uint4(0u, 0u, 0u, 0u);
             }
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) add8(acc, cmp, u[q], KAHAN);
@@ -137,7 +138,7 @@ __device__ __forceinline__ void part_sum(const uint16_t* __restrict__ tbl, int w
             const int r = __shfl_sync(0xffffffffu, ix, __ffs(rem) - 1);
             const unsigned mm = __ballot_sync(0xffffffffu, valid && ix == r);
             rem &= ~mm;
-            if (grp == 0) {
+            if (grp == 0 && in_bounds(r, rows, status)) {
                 const uint4 u = __ldg(base + (int64_t)r * L);
                 const float c = (float)__popc(mm);
                 const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
@@ -309,7 +310,7 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
                     for (int p = 0; p < kMaxParts; ++p) {
                         if (p >= a.n_parts) break;
                         float acc[8];
-                        part_sum<KAHAN>(a.tbl[p], a.width[p], a.kind[p], ix[p], m.y, lane, acc);
+                        part_sum<KAHAN>(a.tbl[p], a.tbl_rows[p], a.status, a.width[p], a.kind[p], ix[p], m.y, lane, acc);
                         if (lane < (a.width[p] >> 3)) store_pair(sb, blk, a.n_kb, a.kofs[p], r, lane, acc);
                     }
                 }
@@ -375,7 +376,7 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
                             for (int p = 0; p < kMaxParts; ++p) {
                                 if (p >= a.n_parts) break;
                                 float acc[8];
-                                part_sum<KAHAN>(a.tbl[p], a.width[p], a.kind[p], ixr[p], mg.y, lane, acc);
+                                part_sum<KAHAN>(a.tbl[p], a.tbl_rows[p], a.status, a.width[p], a.kind[p], ixr[p], mg.y, lane, acc);
                                 if (lane < (a.width[p] >> 3)) store_pair(sb, blk, a.n_kb, a.kofs[p], r, lane, acc);
                             }
                         }
@@ -392,7 +393,7 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
                                     : make_uint4(0u, 0u, 0u, 0u);
                     }
                     uint4 d1 = make_uint4(0u, 0u, 0u, 0u);
-                    if (K1 && row_ok && m.y > 0)
+                    if (K1 && row_ok && m.y > 0 && in_bounds(first1, a.tbl_rows[0], a.status))
                         d1 = __ldg(reinterpret_cast<const uint4*>(a.tbl[0]) + (int64_t)first1 * Lw + ch);
                     float acc[8], cmp[8];
 #pragma unroll
@@ -415,7 +416,9 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
                                 for (int i = 0; i < kMaxG; ++i)
                                     if (i == jr) v = ix[K1][i];
                                 const int r = __shfl_sync(0xffffffffu, v, src);
-                                u[q] = (row_ok && j < m.y) ? __ldg(base + (int64_t)r * Lw) : make_uint4(0u, 0u, 0u, 0u);
+                                u[q] = (row_ok && j < m.y && in_bounds(r, a.tbl_rows[K1], a.status))
+                                           ? __ldg(base + (int64_t)r * Lw)
+                                           : make_uint4(0u, 0u, 0u, 0u);
                             }
 #pragma unroll
                             for (int q = 0; q < kRound; ++q) {
@@ -615,11 +618,13 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 // S[v][0, w) = S_hi, S[v][kpad, kpad + w) = S_lo of the sum of the tuples' table rows; the other
 // columns of the row zero. A warp takes 32 virtual rows at a time (their descriptors in one load);
 // lane groups of L = w / 8 lanes take every G-th tuple (a lane = one 16-byte chunk of a row).
-template <bool KAHAN>
-__global__ void __launch_bounds__(256) seg_sum_kernel(const int4* __restrict__ vr, int64_t nv,
+// SINGLE: every tuple of a virtual row names the same table row (the backward's runs of equal dst
+// rows): the row is loaded once and multiplied by the tuple count (exact in f32, count <= 32).
+template <bool KAHAN, bool SINGLE>
+__global__ void __launch_bounds__(256, 3) seg_sum_kernel(const int4* __restrict__ vr, int64_t nv,
                                                       const int32_t* __restrict__ gidx,
-                                                      const uint16_t* __restrict__ tbl, int w, int kpad,
-                                                      uint16_t* __restrict__ S) {
+                                                      const uint16_t* __restrict__ tbl, int64_t tbl_rows, int w,
+                                                      int kpad, uint16_t* __restrict__ S, int* status) {
     const int lane = threadIdx.x & 31;
     const int L = w >> 3, lsh = 31 - __clz(L), G = 32 >> lsh;
     const int grp = lane >> lsh, ch = lane & (L - 1);
@@ -644,16 +649,36 @@ __global__ void __launch_bounds__(256) seg_sum_kernel(const int4* __restrict__ v
             float acc[8], cmp[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) acc[i] = cmp[i] = 0.f;
-            for (int j0 = 0; j0 < n; j0 += kUnroll * G) {
+            if (SINGLE) {
+                const int r = __shfl_sync(0xffffffffu, ix, 0);
+                if (n > 0 && grp == 0 && in_bounds(r, tbl_rows, status)) {
+                    const uint4 u = __ldg(base + (int64_t)r * L);
+                    const float c = (float)n;
+                    const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        acc[2 * i] = c * __uint_as_float(wd[i] << 16);
+                        acc[2 * i + 1] = c * __uint_as_float(wd[i] & 0xffff0000u);
+                    }
+                }
+            }
+            for (int j0 = 0; !SINGLE && j0 < n; j0 += kUnroll * G) {
+                // slots of this batch that hold a tuple of the row (warp-uniform): short rows skip the rest
+                const int slots = min(kUnroll, (n - j0 + G - 1) >> (5 - lsh));
                 uint4 u[kUnroll];
 #pragma unroll
                 for (int q = 0; q < kUnroll; ++q) {
+                    if (q >= slots) break;
                     const int jj = j0 + q * G + grp;
                     const int r = __shfl_sync(0xffffffffu, ix, jj & 31);
-                    u[q] = jj < n ? __ldg(base + (int64_t)r * L) : make_uint4(0u, 0u, 0u, 0u);
+                    u[q] = (jj < n && in_bounds(r, tbl_rows, status)) ? __ldg(base + (int64_t)r * L)
+                                                                       : make_uint4(0u, 0u, 0u, 0u);
                 }
 #pragma unroll
-                for (int q = 0; q < kUnroll; ++q) add8(acc, cmp, u[q], KAHAN);
+                for (int q = 0; q < kUnroll; ++q) {
+                    if (q >= slots) break;
+                    add8(acc, cmp, u[q], KAHAN);
+                }
             }
             for (int off = L; off < 32; off <<= 1) {
 #pragma unroll
@@ -708,9 +733,15 @@ constexpr int kGemmEpi0 = 4;
 struct GemmArgs {
     const int4* vr;
     int64_t nv, n_tiles;
-    const int32_t* d1;        // per virtual row: the dst table row (-1: zeros)
-    const uint16_t* rtbl;     // dst table, bf16 rows of w_r elements
-    int w_r;                  // 0: no dst part
+    const int32_t* ridx;      // per virtual row v: ridx[v * ridx_stride] = the R-part table row (-1: zeros)
+    int ridx_stride;
+    const uint16_t* rtbl;     // R-part table (forward: the dst rows z; backward: the rows z of dW), bf16
+    int64_t rtbl_rows, out_rows;
+    int w_r;                  // R-part width (0: none)
+    // backward pass: dW_part += S^T R over all rows of the CTA
+    float* dw_part;           // [grid][n_g][w_r]
+    int n_g, m_dw;
+    uint32_t idesc_dw, dw_col;
     int n_kb_s, n_kb_r, kpad_s, m_blocks, n_feat;
     const float* bias;
     float* out;
@@ -720,13 +751,17 @@ struct GemmArgs {
     int* status;
 };
 
+// Forward: D1 = A_src [S_hi; S_lo], D2 = A_dst R (the dst rows), Out = D1 + n (D2 + b).
+// Backward pass: D1 = A [S_hi; S_lo] is a dz row (A = a W^T block), and dW += S^T R with R = the
+// rows' z, both operands read MN-major from the staged rows, accumulated in TMEM over the CTA's tiles.
+template <bool BWD>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap smap,
                 const __grid_constant__ GemmArgs a) {
     extern __shared__ uint8_t dyn_smem[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~(uintptr_t)1023);
     const int N = a.tile_n;
-    const int n_kb = a.n_kb_s + a.n_kb_r;
+    const int n_kb = a.n_kb_s + (BWD ? 0 : a.n_kb_r);  // K blocks of A (the backward's R feeds dW only)
     const uint32_t a_bytes = (uint32_t)n_kb * a.m_blocks * 16384u;
     const uint32_t blk = (uint32_t)N * 128u;
     const uint32_t stage_bytes = (uint32_t)(2 * a.n_kb_s + a.n_kb_r) * blk;
@@ -762,15 +797,34 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const uint32_t buf_cols = 2u * a.m_blocks * N;  // D1 and D2 of one accumulator buffer
+    const uint32_t buf_cols = (BWD ? 1u : 2u) * a.m_blocks * N;  // D1 (and D2) of one accumulator buffer
 
     if (tid < kGemmLoaders) {
         // ------------------------------------------------------------------ loaders
-        const int rch = a.w_r >> 3;  // 16-byte chunks of a dst row
+        // dst rows: a row is copied by rch = w_r / 8 lanes (16 bytes each, at most 32); the tile's
+        // dst row indices are loaded for the next tile while this one's copies are issued
+        const int rch = a.w_r >> 3;
+        const int rsh = rch > 0 ? 31 - __clz(rch) : 0;  // rch is a power of two
+        const int lw = tid >> 5;                         // loader warp 0..2
+        const int rpw = rch > 0 ? 32 >> rsh : 0;         // rows per warp instruction
+        const int rsub = rch > 0 ? lane >> rsh : 0, c = rch > 0 ? lane & (rch - 1) : 0;
+        int hrow_n[kMaxMeta];                            // lane l: dst row of tile row 32 i + l
+        auto load_rows = [&](int64_t tile) {
+#pragma unroll
+            for (int i = 0; i < kMaxMeta; ++i) {
+                const int64_t v = tile * N + 32 * i + lane;
+                hrow_n[i] = (rch > 0 && tile < a.n_tiles && 32 * i < N && v < a.nv) ? __ldg(a.ridx + v * a.ridx_stride) : -1;
+            }
+        };
+        load_rows(blockIdx.x);
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int s = lt % a.stages;
             const uint32_t use = (uint32_t)(lt / a.stages);
+            int hrow[kMaxMeta];
+#pragma unroll
+            for (int i = 0; i < kMaxMeta; ++i) hrow[i] = hrow_n[i];
+            load_rows(tile + gridDim.x);
             if (!mbar_wait(smem_u32(&empty[s]), (use & 1u) ^ 1u, a.status, abort_flag)) break;
             const uint32_t sb = smem_u32(st_smem + (size_t)s * stage_bytes);
             const int64_t v0 = tile * N;
@@ -781,17 +835,23 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                         tma_load_2d(sb + (uint32_t)(hl * a.n_kb_s + kb) * blk, &smap, hl * a.kpad_s + kb * 64, (int)v0,
                                     smem_u32(&full[s]));
             }
-            // dst rows: (row, chunk) pairs over the loader threads; rows past the end and empty rows
-            // are zero-filled by the copy
+            // rows past the end and empty rows are zero-filled by the copy
             const uint32_t rb = sb + (uint32_t)(2 * a.n_kb_s) * blk;
-            for (int i = tid; i < N * rch; i += kGemmLoaders) {
-                const int r = i / rch, c = i - r * rch;
-                const int64_t v = v0 + r;
-                const int hrow = v < a.nv ? __ldg(a.d1 + v) : -1;
-                const uint32_t dst = rb + (uint32_t)(c >> 3) * blk + (uint32_t)r * 128u +
-                                     ((((uint32_t)c & 7u) ^ ((uint32_t)r & 7u)) << 4);
-                const uint16_t* src = hrow >= 0 ? a.rtbl + (int64_t)hrow * a.w_r + 8 * c : a.rtbl;
-                cp_async_16(dst, src, hrow >= 0 ? 16u : 0u);
+            if (rch > 0) {
+                for (int r0 = lw * rpw; r0 < N; r0 += 3 * rpw) {
+                    const int r = r0 + rsub;
+                    int hr = -1;
+#pragma unroll
+                    for (int i = 0; i < kMaxMeta; ++i) {
+                        const int h = __shfl_sync(0xffffffffu, hrow[i], r & 31);
+                        if (i == (r >> 5)) hr = h;
+                    }
+                    const uint32_t dst = rb + (uint32_t)(c >> 3) * blk + (uint32_t)r * 128u +
+                                         ((((uint32_t)c & 7u) ^ ((uint32_t)r & 7u)) << 4);
+                    const bool ok = hr >= 0 && in_bounds(hr, a.rtbl_rows, a.status);
+                    const uint16_t* src = ok ? a.rtbl + (int64_t)hr * a.w_r + 8 * c : a.rtbl;
+                    cp_async_16(dst, src, ok ? 16u : 0u);
+                }
             }
             cp_async_mbar_arrive_noinc(smem_u32(&full[s]));
         }
@@ -843,6 +903,21 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                         }
                     }
                 }
+                if (BWD) {
+                    // dW += S^T R: K = the tile's rows (16 per instruction), M = S features (128 per
+                    // block: two 64-column blocks of S), N = the R width
+                    const uint32_t rb = sb + (uint32_t)(2 * a.n_kb_s) * blk;
+                    for (int step = 0; step < N / 16; ++step)
+                        for (int mbw = 0; mbw < a.m_dw; ++mbw)
+#pragma unroll
+                            for (int hl = 0; hl < 2; ++hl) {
+                                const uint32_t accw = (lt > 0 || step > 0 || hl > 0) ? 1u : 0u;
+                                const uint64_t ad = sw128_mnmajor_desc(
+                                    sb + (uint32_t)(hl * a.n_kb_s + 2 * mbw) * blk + (uint32_t)step * 2048u, blk);
+                                const uint64_t bd = sw128_mnmajor_desc(rb + (uint32_t)step * 2048u, blk);
+                                mma_bf16(tmem_base + a.dw_col + (uint32_t)mbw * a.w_r, ad, bd, a.idesc_dw, accw);
+                            }
+                }
                 mma_commit(smem_u32(&empty[s]));
                 mma_commit(smem_u32(&tfull[acc]));
             }
@@ -853,24 +928,39 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
     } else if (warp >= kGemmEpi0) {
         // ------------------------------------------------------------------ epilogue
         const int q = warp & 3;
-        const bool has_r = a.n_kb_r > 0;
+        const bool has_r = !BWD && a.n_kb_r > 0;
         float bias_r[2];
 #pragma unroll
         for (int mb = 0; mb < 2; ++mb) {
             const int o = mb * 128 + 32 * q + lane;
             bias_r[mb] = (a.bias && mb < a.m_blocks && o < a.n_feat) ? a.bias[o] : 0.f;
         }
+        // the virtual rows of the next tile (lane l of register c: row 32 c + l) load during this one
+        int4 meta_n[kMaxMeta];
+        auto load_meta = [&](int64_t tile) {
+#pragma unroll
+            for (int c = 0; c < kMaxMeta; ++c) {
+                const int64_t v = tile * N + 32 * c + lane;
+                meta_n[c] = (tile < a.n_tiles && 32 * c < N && v < a.nv) ? __ldg(a.vr + v) : make_int4(0, 0, -1, -1);
+            }
+        };
+        load_meta(blockIdx.x);
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int acc = lt & 1;
             const uint32_t ause = (uint32_t)(lt >> 1);
+            int4 meta[kMaxMeta];
+#pragma unroll
+            for (int c = 0; c < kMaxMeta; ++c) meta[c] = meta_n[c];
+            load_meta(tile + gridDim.x);
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), ause & 1u, a.status, abort_flag))) break;
             tc_fence_after();
             const int64_t v0 = tile * N;
-            for (int c = 0; c < N / 32; ++c) {
+#pragma unroll
+            for (int c = 0; c < kMaxMeta; ++c) {
                 const int64_t vb = v0 + 32 * c;
-                if (vb >= a.nv) break;
-                const int4 mt = vb + lane < a.nv ? __ldg(a.vr + vb + lane) : make_int4(0, 0, -1, -1);
+                if (32 * c >= N || vb >= a.nv) break;
+                const int4 mt = meta[c];
                 for (int mb = 0; mb < a.m_blocks; ++mb) {
                     if (mb * 128 + 32 * q >= a.n_feat) continue;
                     const int o = mb * 128 + 32 * q + lane;
@@ -888,9 +978,9 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                         const int part = __shfl_sync(0xffffffffu, mt.w, j);
                         const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
                         if (row < 0) break;
-                        if (o_ok) {
+                        if (o_ok && a.out && in_bounds(part >= 0 ? 0 : row, a.out_rows, a.status)) {
                             const float d2 = has_r ? __uint_as_float(v2[j]) : 0.f;
-                            const float y = __uint_as_float(v1[j]) + nj * (d2 + bo);
+                            const float y = BWD ? __uint_as_float(v1[j]) : __uint_as_float(v1[j]) + nj * (d2 + bo);
                             if (part >= 0) __stcg(a.vpart + (int64_t)part * a.n_feat + o, y);
                             else emit_out(a.out + (int64_t)row * a.n_feat + o, y, a.accumulate);
                         }
@@ -899,6 +989,29 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
             }
             tc_fence_before();
             mbar_arrive(smem_u32(&tempty[acc]));
+        }
+        if (BWD) {
+            // this CTA's dW partial (TMEM lane = S feature, columns = R features)
+            if (__all_sync(0xffffffffu, mbar_wait(smem_u32(drain), 0, a.status, abort_flag))) {
+                tc_fence_after();
+                for (int mbw = 0; mbw < a.m_dw; ++mbw) {
+                    const int g = mbw * 128 + 32 * q + lane;
+                    float* dst = a.dw_part + ((int64_t)blockIdx.x * a.n_g + g) * a.w_r;
+                    for (int c = 0; c < a.w_r / 32; ++c) {
+                        uint32_t v[32];
+                        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * q) << 16) + a.dw_col + (uint32_t)mbw * a.w_r +
+                                               (uint32_t)(32 * c), v);
+                        tmem_ld_wait();
+                        if (g < a.n_g) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                *reinterpret_cast<float4*>(dst + 32 * c + j) =
+                                    make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+                        }
+                    }
+                }
+            }
         }
     }
     tc_fence_before();
@@ -973,7 +1086,7 @@ __global__ void vr_fill_kernel(const int32_t* __restrict__ beg, const int32_t* _
 // slot or the output row.
 __global__ void __launch_bounds__(256) agg_fix_kernel(const int4* __restrict__ jobs, int64_t n_jobs,
                                                       const float* __restrict__ part, float* part2, float* out, int F,
-                                                      int accumulate, int kahan) {
+                                                      int accumulate, int kahan, int64_t out_rows, int* status) {
     __shared__ float4 red[8][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int F4 = F >> 2;
@@ -1007,7 +1120,7 @@ __global__ void __launch_bounds__(256) agg_fix_kernel(const int4* __restrict__ j
             float4 res = make_float4(s[0] - cm[0], s[1] - cm[1], s[2] - cm[2], s[3] - cm[3]);
             if (j.w >= 0) {
                 reinterpret_cast<float4*>(part2 + (int64_t)j.w * F)[c4] = res;
-            } else {
+            } else if (in_bounds(j.x, out_rows, status)) {
                 float4* dst = reinterpret_cast<float4*>(out + (int64_t)j.x * F) + c4;
                 if (accumulate) {
                     const float4 o = *dst;
@@ -1326,14 +1439,14 @@ relnn_status launch_agg(const CUtensorMap& amap, const AggArgs& a, bool kahan, s
 
 // Fix-up of the split rows of one launch: partial rows in p.vpart (level-2 sums after them).
 relnn_status agg_fixup(const VRows& V, const float* vpart, float* vpart2, float* out, int F, bool accumulate, bool kahan,
-                       cudaStream_t st) {
+                       int64_t out_rows, int* status, cudaStream_t st) {
     if (!out || V.n_fix1 == 0) return RELNN_OK;
     ProfToken pt = prof_begin(RELNN_PROF_FIXUP, st);
     { agg_fix_kernel<<<(int)std::min<int64_t>(V.n_fix1, 65535), 256, 0, st>>>(V.fix1.as<int4>(), V.n_fix1, vpart, vpart2, out, F,
-                                                                            accumulate ? 1 : 0, kahan ? 1 : 0); note_launch(); }
+                                                                            accumulate ? 1 : 0, kahan ? 1 : 0, out_rows, status); note_launch(); }
     if (V.n_fix2 > 0)
         { agg_fix_kernel<<<(int)std::min<int64_t>(V.n_fix2, 65535), 256, 0, st>>>(V.fix2.as<int4>(), V.n_fix2, vpart2, nullptr, out,
-                                                                                F, accumulate ? 1 : 0, kahan ? 1 : 0); note_launch(); }
+                                                                                F, accumulate ? 1 : 0, kahan ? 1 : 0, out_rows, status); note_launch(); }
     prof_end(pt, st);
     RELNN_CUDA(cudaGetLastError());
     return RELNN_OK;
@@ -1341,19 +1454,21 @@ relnn_status agg_fixup(const VRows& V, const float* vpart, float* vpart2, float*
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Two-kernel forward: tile rows and stages of agg_gemm_kernel (two stages at the largest N).
-AggCfg gemm_config(int n_kb_s, int n_kb_r, int m_blocks) {
+// Tile rows and stages of agg_gemm_kernel (two stages at the largest N). Backward: A holds only the
+// S part's K blocks, and TMEM also holds dW (m_dw blocks of w_r columns).
+AggCfg gemm_config(int n_kb_s, int n_kb_r, int m_blocks, bool bwd = false, int m_dw = 0, int w_r = 0) {
     AggCfg c;
-    const uint32_t a_bytes = (uint32_t)(n_kb_s + n_kb_r) * m_blocks * 16384u;
+    const uint32_t a_bytes = (uint32_t)(n_kb_s + (bwd ? 0 : n_kb_r)) * m_blocks * 16384u;
     const int64_t want = tune_get(RELNN_TUNE_AGG_ROWS);
     for (int N : {128, 64, 32}) {
         if (want != 0 && N > want) continue;
         const size_t stage = (size_t)(2 * n_kb_s + n_kb_r) * N * 128;
         const size_t fixed = 1024 + a_bytes + 512;
         if (fixed + 2 * stage > (size_t)kSmemLimit) continue;
-        const uint32_t cols = 4u * m_blocks * N;
+        const uint32_t cols = bwd ? 2u * m_blocks * N + (uint32_t)(m_dw * w_r) : 4u * m_blocks * N;
         if (cols > 512) continue;
         c.N = N;
+        c.dw_col = 2u * m_blocks * N;
         c.stages = (int)std::min<size_t>(4, (kSmemLimit - fixed) / stage);
         uint32_t t = 32;
         while (t < cols) t <<= 1;
@@ -1399,7 +1514,8 @@ bool agg_forward_ok(const Plan& p, const CallIO& io, const float* out) {
 bool agg_backward_ok(const Plan& p, const CallIO& io, const GradIO& g) {
     if (!agg_forward_ok(p, io, g.dz)) return false;
     if (!pow2_in(p.d_out, 8, 256) || p.d % 32 != 0) return false;
-    return g.dout != nullptr && aligned16(g.dout) && bwd_cfg(p).N > 0;
+    return g.dout != nullptr && aligned16(g.dout) &&
+           gemm_config((p.d_out + 63) / 64, (p.d + 63) / 64, (p.d + 127) / 128, true, (p.d_out + 127) / 128, p.d).N > 0;
 }
 
 // Two-kernel forward (unique H keys or no dst part): gather-sum into S, then the TMA-fed GEMM.
@@ -1430,7 +1546,7 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
     RELNN_TRY(p.sbuf.alloc(sizeof(uint16_t) * 2 * (size_t)kpad * std::max<int64_t>(nv_max, 1)));
     static bool attr_set = false;
     if (!attr_set) {
-        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
     const int ss_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nv_max, 32 * 8), (int64_t)num_sms() * 8));
@@ -1441,10 +1557,11 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         uint16_t* S = p.sbuf.as<uint16_t>();
         {
             ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
-            if (p.kahan) seg_sum_kernel<true><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(),
-                                                                         reinterpret_cast<const uint16_t*>(io.z), p.d, kpad, S);
-            else seg_sum_kernel<false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(),
-                                                                   reinterpret_cast<const uint16_t*>(io.z), p.d, kpad, S);
+            const uint16_t* zt = reinterpret_cast<const uint16_t*>(io.z);
+            if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
+                                                                                p.n_h, p.d, kpad, S, p.status.as<int>());
+            else seg_sum_kernel<false, false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
+                                                                          p.n_h, p.d, kpad, S, p.status.as<int>());
             note_launch();
             prof_end(pt, st);
         }
@@ -1457,8 +1574,11 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         a.vr = V.vr.as<int4>();
         a.nv = V.nv;
         a.n_tiles = ceil_div(V.nv, cfg.N);
-        a.d1 = p.concat_dst ? V.d1.as<int32_t>() : nullptr;
+        a.ridx = p.concat_dst ? V.d1.as<int32_t>() : nullptr;
+        a.ridx_stride = 1;
         a.rtbl = reinterpret_cast<const uint16_t*>(io.z);
+        a.rtbl_rows = p.n_h;
+        a.out_rows = p.n_out;
         a.w_r = p.concat_dst ? p.d : 0;
         a.n_kb_s = n_kb_s;
         a.n_kb_r = n_kb_r;
@@ -1477,12 +1597,12 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
         {
             ProfToken pt = prof_begin(RELNN_PROF_AGG_FWD, st);
-            { agg_gemm_kernel<<<grid, kGemmThreads, cfg.smem, st>>>(amap, smap, a); note_launch(); }
+            { agg_gemm_kernel<false><<<grid, kGemmThreads, cfg.smem, st>>>(amap, smap, a); note_launch(); }
             prof_end(pt, st);
         }
         RELNN_CUDA(cudaGetLastError());
         RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d_out, out, p.d_out, i > 0,
-                            p.kahan, st));
+                            p.kahan, p.n_out, p.status.as<int>(), st));
     }
     return RELNN_OK;
 }
@@ -1525,6 +1645,7 @@ relnn_status forward_agg(Plan& p, const CallIO& io_in, float* out, cudaStream_t 
         if (p.concat_dst) {
             a.gidx[pi] = b.hd.as<int32_t>();
             a.tbl[pi] = reinterpret_cast<const uint16_t*>(io.z);
+            a.tbl_rows[pi] = p.n_h;
             a.width[pi] = p.d;
             a.kind[pi] = 1;
             a.kofs[pi] = kpad;
@@ -1532,6 +1653,7 @@ relnn_status forward_agg(Plan& p, const CallIO& io_in, float* out, cudaStream_t 
         }
         a.gidx[pi] = b.hs.as<int32_t>();
         a.tbl[pi] = reinterpret_cast<const uint16_t*>(io.z);
+        a.tbl_rows[pi] = p.n_h;
         a.width[pi] = p.d;
         a.kind[pi] = 0;
         a.kofs[pi] = 0;
@@ -1551,7 +1673,7 @@ relnn_status forward_agg(Plan& p, const CallIO& io_in, float* out, cudaStream_t 
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
         RELNN_TRY(launch_agg<false>(amap, a, p.kahan, cfg.smem, grid, st, RELNN_PROF_AGG_FWD));
         RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d_out, out, p.d_out, i > 0,
-                            p.kahan, st));
+                            p.kahan, p.n_out, p.status.as<int>(), st));
     }
     return RELNN_OK;
 }
@@ -1563,7 +1685,8 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
     const int m_blocks = (p.d + 127) / 128;     // dz features
     const int z_blocks = (p.d + 63) / 64;
     const int m_dw = (p.d_out + 127) / 128;     // dW rows (G features)
-    const AggCfg cfg = bwd_cfg(p);
+    const int kpad_g = ((p.d_out + 63) / 64) * 64;  // S row: the bf16 pair of a G row
+    const AggCfg cfg = gemm_config(n_kb, z_blocks, m_blocks, true, m_dw, p.d);
     if (cfg.N == 0) {
         set_error("aggregate-first backward: operands too large for shared memory");
         return RELNN_ENOTSUP;
@@ -1604,17 +1727,28 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
     }
     CUtensorMap amap;
     RELNN_TRY(encode_bf16_tile_map(&amap, abuf, cols, rows_pad));
-    // virtual rows of both passes of every branch first, so the partial rows are allocated once
+    // virtual rows of both passes of every branch first, so the partial rows and sums are allocated once
     const int n_pass = p.concat_dst ? 2 : 1;
     size_t vp_max = 0;
+    int64_t nv_max = 0;
     for (auto& b : p.br) {
         RELNN_TRY(ensure_src_order(p, b, st));
         RELNN_TRY(ensure_vrows(b.vr_src, b.hs_src.as<int32_t>(), b.m, p.n_h, true, st));
         if (n_pass > 1) RELNN_TRY(ensure_vrows(b.vr_dst, b.hd.as<int32_t>(), b.m, 0, false, st));
         vp_max = std::max(vp_max, (size_t)(b.vr_src.n_parts + b.vr_src.n_l2) * p.d);
-        if (n_pass > 1) vp_max = std::max(vp_max, (size_t)(b.vr_dst.n_parts + b.vr_dst.n_l2) * p.d);
+        nv_max = std::max(nv_max, b.vr_src.nv);
+        if (n_pass > 1) {
+            vp_max = std::max(vp_max, (size_t)(b.vr_dst.n_parts + b.vr_dst.n_l2) * p.d);
+            nv_max = std::max(nv_max, b.vr_dst.nv);
+        }
     }
     if (vp_max) RELNN_TRY(p.vpart.alloc(sizeof(float) * vp_max));
+    RELNN_TRY(p.sbuf.alloc(sizeof(uint16_t) * 2 * (size_t)kpad_g * std::max<int64_t>(nv_max, 1)));
+    static bool attr_set = false;
+    if (!attr_set) {
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        attr_set = true;
+    }
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         float* dW = g.dW.size() > i ? g.dW[i] : nullptr;
@@ -1628,20 +1762,46 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
                 }
                 continue;
             }
+            // G rows: sums of dOut rows per virtual row (src order: a row per tuple; dst order: one
+            // row times the run's length), as bf16 pairs
+            uint16_t* S = p.sbuf.as<uint16_t>();
+            const int ss_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(V.nv, 32 * 8), (int64_t)num_sms() * 8));
+            const int32_t* gi = pass == 0 ? b.seg_src.as<int32_t>() : b.seg.as<int32_t>();
+            {
+                ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
+                const uint16_t* tb = p.doutbf.as<uint16_t>();
+                int* stw = p.status.as<int>();
+                if (pass == 0) {
+                    if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
+                                                                                        p.d_out, kpad_g, S, stw);
+                    else seg_sum_kernel<false, false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
+                                                                                  p.d_out, kpad_g, S, stw);
+                } else {
+                    seg_sum_kernel<false, true><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out,
+                                                                            kpad_g, S, stw);
+                }
+                note_launch();
+                prof_end(pt, st);
+            }
+            RELNN_CUDA(cudaGetLastError());
             { pack_a_bwd_kernel<<<grid_for((int64_t)a_elems), 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, col0, p.d,
                                                                            rows_pad, cols, abuf); note_launch(); }
+            CUtensorMap smap;
+            RELNN_TRY(encode_bf16_tile_map(&smap, S, 2 * kpad_g, V.nv, cfg.N));
             const bool accumulate = pass > 0 || i > 0 || g.accumulate_dz;
-            AggArgs a{};
+            GemmArgs a{};
             a.vr = V.vr.as<int4>();
             a.nv = V.nv;
             a.n_tiles = ceil_div(V.nv, cfg.N);
-            a.gidx[0] = pass == 0 ? b.seg_src.as<int32_t>() : b.seg.as<int32_t>();
-            a.tbl[0] = p.doutbf.as<uint16_t>();
-            a.width[0] = p.d_out;
-            a.kind[0] = pass == 0 ? 0 : 1;
-            a.kofs[0] = 0;
-            a.n_parts = 1;
-            a.n_kb = n_kb;
+            a.ridx = reinterpret_cast<const int32_t*>(V.vr.as<int4>()) + 2;  // the row id field (an H row)
+            a.ridx_stride = 4;
+            a.rtbl = reinterpret_cast<const uint16_t*>(io.z);
+            a.rtbl_rows = p.n_h;
+            a.out_rows = p.n_h;
+            a.w_r = p.d;
+            a.n_kb_s = n_kb;
+            a.n_kb_r = z_blocks;
+            a.kpad_s = kpad_g;
             a.m_blocks = m_blocks;
             a.n_feat = p.d;
             a.bias = nullptr;
@@ -1653,18 +1813,20 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             a.idesc = tc::idesc_bf16_f32(128, cfg.N);
             a.tmem_cols = cfg.tmem_cols;
             a.status = p.status.as<int>();
-            a.zrows = reinterpret_cast<const uint16_t*>(io.z);
-            a.d_z = p.d;
-            a.z_blocks = z_blocks;
-            a.m_dw = m_dw;
             a.dw_part = dw_part;
             a.n_g = p.d_out;
+            a.m_dw = m_dw;
             a.idesc_dw = tc::idesc_bf16_f32(128, p.d, true, true);
             a.dw_col = cfg.dw_col;
             const int grid = (int)std::min<int64_t>(a.n_tiles, grid_max);
-            RELNN_TRY(launch_agg<true>(amap, a, p.kahan, cfg.smem, grid, st, RELNN_PROF_AGG_BWD));
+            {
+                ProfToken pt = prof_begin(RELNN_PROF_AGG_BWD, st);
+                { agg_gemm_kernel<true><<<grid, kGemmThreads, cfg.smem, st>>>(amap, smap, a); note_launch(); }
+                prof_end(pt, st);
+            }
+            RELNN_CUDA(cudaGetLastError());
             RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d, g.dz, p.d, accumulate,
-                                p.kahan, st));
+                                p.kahan, p.n_h, p.status.as<int>(), st));
             if (dW) {
                 const int64_t nw = (int64_t)p.d_out * p.d;
                 { agg_reduce_dw_kernel<<<grid_for(nw), 256, 0, st>>>(dw_part, grid, p.d_out, p.d, dW, p.d_in, col0); note_launch(); }

@@ -69,6 +69,8 @@ extern "C" {
 
 int32_t relnn_version(void) { return 100; }
 
+int32_t relnn_build_flags(void) { return kChecked ? 1 : 0; }
+
 const char* relnn_status_string(relnn_status s) {
     switch (s) {
         case RELNN_OK: return "ok";

@@ -167,6 +167,15 @@ __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { retur
 // Wall-clock budget for any spin or mbarrier wait inside a kernel (nanoseconds).
 constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
 
+// A kernel's device status word is two ints: [0] the status code it raises (RELNN_DEV_*), [1] the
+// budget of its bounded waits in microseconds (0: kWaitBudgetNs). Only the wait-timeout test entry
+// point sets [1]; every other status word keeps it 0.
+constexpr int kStatusInts = 2;
+__device__ __forceinline__ unsigned long long wait_budget_ns(const int* status) {
+    const int us = status ? *reinterpret_cast<const volatile int*>(status + 1) : 0;
+    return us > 0 ? (unsigned long long)us * 1000ull : kWaitBudgetNs;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -175,6 +184,22 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 __device__ __forceinline__ void raise_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
+}
+
+// Checked build (compiled with -DRELNN_CHECKED, librelnn_checked.so): gathered row indices and output
+// rows are tested on the device; one outside [0, n) raises RELNN_DEV_BOUNDS in the status word and the
+// access is skipped (a zero row is read, nothing is written), so a bad plan or input ends as
+// RELNN_EDEVICE instead of a fault. In the regular build the test compiles away.
+#ifdef RELNN_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t n, int* status) {
+    if (!kChecked) return true;
+    if (i >= 0 && i < n) return true;
+    raise_status(status, RELNN_DEV_BOUNDS);
+    return false;
 }
 
 // Order-preserving maps from signed keys to unsigned integers (for radix sorting).

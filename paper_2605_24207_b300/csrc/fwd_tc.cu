@@ -68,6 +68,7 @@ struct TcArgs {
     uint32_t* relu_mask;
     int64_t m;
     int64_t n_tiles;
+    int64_t z_rows, r_rows;  // rows of z and r (the checked build tests the gathered indices)
     int z_bf16, r_bf16, d, d_r;
     int d_out, act, kahan, accumulate;
     int n_kb, tile_n, m_blocks, stages, mask_words;
@@ -189,6 +190,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                 const int src = a.kb_src[kb];
                 const int32_t* rows_idx = islot + src * kIdxArr;
                 const void* tbl = src == 2 ? a.r : a.z;
+                const int64_t tbl_rows = src == 2 ? a.r_rows : a.z_rows;
                 const int tbl_bf16 = src == 2 ? a.r_bf16 : a.z_bf16;
                 const int row_elems = src == 2 ? a.d_r : a.d;
                 const uint32_t sbase = smem_u32(st_smem + (size_t)s * stage_bytes);
@@ -220,7 +222,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         for (int k = 0; k < kMaxRows; ++k) {
                             const int row = rg + k * kRowGroups;
                             if (row >= a.tile_n) break;
-                            const bool valid = (t0 + row < a.m) && in_part;
+                            const bool valid = (t0 + row < a.m) && in_part && in_bounds(ridx[k], tbl_rows, a.status);
                             cp_async_16_stream(dst_of(row), valid ? p + (int64_t)ridx[k] * row_elems + col : p,
                                                valid ? 16u : 0u);
                         }
@@ -229,7 +231,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
                         for (int k = 0; k < kMaxRows; ++k) {
                             const int row = rg + k * kRowGroups;
                             if (row >= a.tile_n) break;
-                            const bool valid = (t0 + row < a.m) && in_part;
+                            const bool valid = (t0 + row < a.m) && in_part && in_bounds(ridx[k], tbl_rows, a.status);
                             cp_async_16(dst_of(row), valid ? p + (int64_t)ridx[k] * row_elems + col : p,
                                         valid ? 16u : 0u);
                         }
@@ -243,7 +245,8 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ 
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
                             const int row = rg + (k0 + k) * kRowGroups;
-                            const bool valid = k0 + k < kMaxRows && row < a.tile_n && (t0 + row < a.m) && in_part;
+                            const bool valid = k0 + k < kMaxRows && row < a.tile_n && (t0 + row < a.m) && in_part &&
+                                               in_bounds(ridx[k0 + k < kMaxRows ? k0 + k : 0], tbl_rows, a.status);
                             const float4* qp = reinterpret_cast<const float4*>(
                                 pf32 + (valid ? (int64_t)ridx[k0 + k < kMaxRows ? k0 + k : 0] * row_elems + col : 0));
                             u[k] = valid ? __ldg(qp) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -738,6 +741,8 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         a.mask_words = mask_words;
         a.m = b.m;
         a.n_tiles = ceil_div(b.m, tile_n);
+        a.z_rows = p.n_h;
+        a.r_rows = b.n_tuples;
         a.z_bf16 = io.z_bf16;
         a.d = p.d;
         a.d_r = b.d_r;

@@ -180,8 +180,8 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     RELNN_CHECK_ARG(n == 0 || keys, "join build: null keys");
     jt.kt = kt;
     jt.n = n;
-    RELNN_TRY(jt.status.alloc_nosync(sizeof(int), st));
-    RELNN_CUDA(cudaMemsetAsync(jt.status.p, 0, sizeof(int), st));
+    RELNN_TRY(jt.status.alloc_nosync(sizeof(int) * kStatusInts, st));
+    RELNN_CUDA(cudaMemsetAsync(jt.status.p, 0, sizeof(int) * kStatusInts, st));
     RELNN_TRY(jt.rows_sorted.alloc_nosync(sizeof(int32_t) * std::max<int64_t>(n, 1), st));
     RELNN_TRY(jt.uid_of_pos.alloc_nosync(sizeof(int32_t) * std::max<int64_t>(n, 1), st));
     if (n == 0) {

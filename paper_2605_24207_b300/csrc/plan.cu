@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
         if (lane == 0) atomicExch(&tile_state[tile], (tile == 0 ? kTileInc : kTileAgg) | (unsigned long long)btot);
         int window = tile - 1;
         const unsigned long long t_start = globaltimer_ns();
+        const unsigned long long budget = wait_budget_ns(status);
         unsigned spins = 0;
         while (window >= 0) {
             const int idx = window - lane;
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
             if (idx >= 0) w = *reinterpret_cast<volatile unsigned long long*>(&tile_state[idx]);
             const unsigned flag = (unsigned)(w >> 62);
             if (__any_sync(0xffffffffu, flag == 0)) {  // a predecessor is still counting
-                if ((++spins & 63u) == 0 && globaltimer_ns() - t_start > kWaitBudgetNs) {
+                if ((++spins & 63u) == 0 && globaltimer_ns() - t_start > budget) {
                     if (lane == 0) raise_status(status, RELNN_DEV_TIMEOUT);
                     break;
                 }
@@ -527,8 +528,8 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     p.d_in = p.d * (p.concat_dst ? 2 : 1) + d_r0;
     p.d_out = p.identity ? p.d_in : desc->d_out;
     RELNN_CHECK_ARG(p.d_out > 0 && p.d_out <= 4096, "rule plan: bad d_out");
-    RELNN_TRY(p.status.alloc_nosync(sizeof(int), st));
-    RELNN_CUDA(cudaMemsetAsync(p.status.p, 0, sizeof(int), st));
+    RELNN_TRY(p.status.alloc_nosync(sizeof(int) * kStatusInts, st));
+    RELNN_CUDA(cudaMemsetAsync(p.status.p, 0, sizeof(int) * kStatusInts, st));
 
     // a1: build side over H.id
     if (!p.Hx) RELNN_TRY(join_table_build(p.H, desc->d_h_ids, desc->n_h, p.kt, st));

@@ -2,10 +2,12 @@
 // Events are recorded on the stream the kernel is launched on, so the elapsed time is that of the
 // launch as the device ran it inside the caller's stream order.
 #include <atomic>
+#include <string>
 #include <mutex>
 #include <vector>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace relnn {
 
@@ -111,11 +113,50 @@ __global__ void __launch_bounds__(1024) fma_peak_kernel(float* out, int iters, f
     if (s == -1.2345e30f) out[blockIdx.x] = s;
 }
 
+// One CTA waits, with the library's bounded mbarrier wait, on a barrier nothing arrives at; the wait
+// gives up after the budget in the status word, raises RELNN_DEV_TIMEOUT and the kernel returns.
+__global__ void wait_timeout_kernel(int* status) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(tc::smem_u32(&bar), 1);
+        abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    tc::mbar_wait(tc::smem_u32(&bar), 0, status, &abort_flag);  // phase 0 never completes
+}
+
 }  // namespace relnn
 
 using namespace relnn;
 
 extern "C" {
+
+relnn_status relnn_test_wait_timeout(int32_t budget_us, void* stream) {
+    RELNN_CHECK_ARG(budget_us > 0 && budget_us <= 1000000, "wait timeout test: budget must be in (0, 1 s]");
+    cudaStream_t st = (cudaStream_t)stream;
+    int* d = nullptr;
+    RELNN_CUDA(cudaMallocAsync(&d, sizeof(int) * kStatusInts, st));
+    const int h[kStatusInts] = {0, budget_us};
+    int code = 0;
+    cudaError_t e = cudaMemcpyAsync(d, h, sizeof(h), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        wait_timeout_kernel<<<1, 32, 0, st>>>(d);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&code, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d, st);
+    RELNN_CUDA(e);
+    if (code != 0) {
+        set_device_error(code);
+        set_error("wait timeout test: the bounded wait gave up (device code " + std::to_string(code) + ")");
+        return RELNN_EDEVICE;
+    }
+    return RELNN_OK;
+}
 
 relnn_status relnn_tune_set(int32_t knob, int64_t value) {
     RELNN_CHECK_ARG(knob_ok(knob, value), "tune: unknown knob or value out of range");

@@ -247,8 +247,8 @@ relnn_status forward_pushdown(Plan& p, const CallIO& io_in, float* out, cudaStre
         b.n_tuples = b.m = p.n_h;
         RELNN_TRY(b.hs.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(p.n_h, 1)));
         RELNN_TRY(b.seg.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(p.n_h, 1)));
-        RELNN_TRY(g.status.alloc(sizeof(int)));
-        RELNN_CUDA(cudaMemsetAsync(g.status.p, 0, sizeof(int), st));
+        RELNN_TRY(g.status.alloc(sizeof(int) * kStatusInts));
+        RELNN_CUDA(cudaMemsetAsync(g.status.p, 0, sizeof(int) * kStatusInts, st));
         const int blocks = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(p.n_h, 1), 256), (int64_t)num_sms() * 8);
         { iota_kernel<<<blocks, 256, 0, st>>>(b.hs.as<int32_t>(), p.n_h); note_launch(); }
         { iota_kernel<<<blocks, 256, 0, st>>>(b.seg.as<int32_t>(), p.n_h); note_launch(); }

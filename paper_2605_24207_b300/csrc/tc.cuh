@@ -49,12 +49,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
     for (int i = 0; i < 4; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
+    const unsigned long long budget = wait_budget_ns(status);
     unsigned iter = 0;
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((++iter & 15u) == 0) {
             if (*abort) return false;
-            if (globaltimer_ns() - t0 > kWaitBudgetNs) {
+            if (globaltimer_ns() - t0 > budget) {
                 raise_status(status, RELNN_DEV_TIMEOUT);
                 *abort = 1;
                 return false;

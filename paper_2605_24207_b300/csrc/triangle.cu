@@ -502,8 +502,8 @@ relnn_status relnn_triangle_plan(const relnn_tri_desc* desc, void* stream, relnn
     T->kt = desc->key_type;
     T->n_h = desc->n_h;
     T->n_edges = desc->n_edges;
-    TRI_TRY(T->status.alloc(sizeof(int)));
-    TRI_CUDA(cudaMemsetAsync(T->status.p, 0, sizeof(int), st));
+    TRI_TRY(T->status.alloc(sizeof(int) * kStatusInts));
+    TRI_CUDA(cudaMemsetAsync(T->status.p, 0, sizeof(int) * kStatusInts, st));
     TRI_TRY(join_table_build(T->H, desc->d_h_ids, desc->n_h, desc->key_type, st));
     T->U = T->H.n_unique;
     const int64_t E = desc->n_edges, U = T->U;

@@ -14,7 +14,8 @@ from typing import Sequence
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "librelnn.so")
+# RELNN_LIB=checked selects the checked build (device-side bounds checks, librelnn_checked.so)
+LIB_PATH = os.path.join(HERE, "librelnn_checked.so" if os.environ.get("RELNN_LIB") == "checked" else "librelnn.so")
 
 I32, I64 = 0, 1
 F32, BF16 = 0, 1
@@ -122,7 +123,7 @@ def lib():
     if _LIB is not None:
         return _LIB
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"librelnn.so not built at {LIB_PATH}; run paper_2605_24207_b300/build_lib.py")
+        raise RuntimeError(f"{os.path.basename(LIB_PATH)} not built at {LIB_PATH}; run paper_2605_24207_b300/build_lib.py")
     L = C.CDLL(LIB_PATH)
     L.relnn_version.restype = C.c_int32
     L.relnn_status_string.restype = C.c_char_p
@@ -175,6 +176,9 @@ def lib():
     L.relnn_tune_set.restype = C.c_int
     L.relnn_tune_get.argtypes = [C.c_int32, C.POINTER(i64)]
     L.relnn_tune_get.restype = C.c_int
+    L.relnn_build_flags.restype = C.c_int32
+    L.relnn_test_wait_timeout.argtypes = [C.c_int32, vp]
+    L.relnn_test_wait_timeout.restype = C.c_int
     L.relnn_peak_fma_f32.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     L.relnn_peak_fma_f32.restype = C.c_int
     _LIB = L
