@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip warm / comparator extras")
     ap.add_argument("--agg", default="sum", choices=["sum", "mean", "max"],
                     help="c2: aggregator of the rule (extras only with sum)")
+    ap.add_argument("--no-tune", action="store_true", help="time the library defaults (no autotuning)")
     ap.add_argument("--no-subrecords", action="store_true",
                     help="c2: skip the c3 / c4 / c1b / c5 records appended to the line")
     ap.add_argument("--no-serving", action="store_true", help="c2: skip the shortened c5 record")
@@ -176,6 +177,16 @@ class C2:
                           minlength=self.rel.h_ids.size)
         self.n_vrows = int(np.maximum(1, (cnt[cnt > 0] + 31) // 32).sum())
 
+    def tune(self):
+        """The autotuner's choice for this rule (plan + forward of this relation), applied to the
+        library's knobs and this workload's flags before anything is timed."""
+        if self.agg != "sum":
+            return None
+        from paper_2605_24207_b300 import autotune as A
+        c = A.tune_rule(self.d, self.d_out, self.n_tuples, rel=self.rel, backward=False, cache=None, reps=3)
+        self.flags = (self.flags & ~(A.R.FLAG_PER_TUPLE | A.R.FLAG_PUSHDOWN | A.R.FLAG_TILE128)) | A.apply(c)
+        return c
+
     def step(self):
         from paper_2605_24207_b300 import relnn as R
         t = self.t
@@ -186,15 +197,31 @@ class C2:
     def kernels(self):
         """Library kernels of a step: id -> (name, algorithmic work per step, bound)."""
         from paper_2605_24207_b300 import relnn as R
-        # aggregate-first form (HBM): per matched tuple its two 4-byte row indices, per virtual row
-        # its 16-byte descriptor (read by the producers and the epilogue), each H row once (bf16) and
-        # each output row once (f32). Per-tuple form (tensor): 2 d_in d_out FLOP per tuple.
-        return {R.PROF_AGG_FWD: ("agg_tc_kernel<fwd>", float(self.agg_bytes()), "hbm"),
+        # aggregate-first form, two kernels (HBM): the gather-sum reads per matched tuple its 4-byte
+        # src row index, per virtual row its 16-byte descriptor, each H row once (bf16) and writes
+        # per virtual row the bf16 pair of its sums (2 x 2 x kpad bytes); the GEMM reads those pairs,
+        # the descriptors and dst row indices (16 + 4 bytes per virtual row), the dst H row of each
+        # output row (bf16) and writes each output row once (f32). Per-tuple form (tensor):
+        # 2 d_in d_out FLOP per tuple.
+        sb, gb = self.agg_bytes()
+        return {R.PROF_AGG_SUM: ("seg_sum_kernel (gather-sum)", float(sb), "hbm"),
+                R.PROF_AGG_FWD: ("agg_gemm_kernel (TMA + tcgen05 GEMM)", float(gb), "hbm"),
                 R.PROF_FWD_TC: ("fwd_tc_kernel", 2.0 * (2 * self.d) * self.d_out * self.matched, "tensor")}
 
     def agg_bytes(self):
+        """(gather-sum bytes, GEMM bytes) per forward."""
         n_h = int(self.t["h"].numel())
-        return 8 * self.matched + 2 * 16 * self.n_vrows + n_h * self.d * 2 + self.n_out * self.d_out * 4
+        kpad = (self.d + 63) // 64 * 64
+        pair = 2 * 2 * kpad * self.n_vrows
+        sb = 4 * self.matched + 16 * self.n_vrows + n_h * self.d * 2 + pair
+        gb = pair + 20 * self.n_vrows + self.n_out * self.d * 2 + self.n_out * self.d_out * 4
+        return sb, gb
+
+    def forward_bytes(self):
+        """Compulsory bytes of the whole forward (no intermediate): per matched tuple its src row and
+        output row indices, each H row once, each output row once."""
+        n_h = int(self.t["h"].numel())
+        return 8 * self.matched + n_h * self.d * 2 + self.n_out * self.d_out * 4
 
     def e2e_setup(self):
         # two slots (device inputs, device output, pinned result, stream) used in turn, so that one
@@ -273,9 +300,11 @@ class C2:
 
         fwd = lambda: p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
         ms_f, k_f = ktime(fwd, max(3, steps), R.PROF_AGG_FWD)
+        _, k_fs = ktime(fwd, max(3, steps), R.PROF_AGG_SUM)
         dout = torch.randn_like(self.out[: self.n_out])
         bwd = lambda: p.backward(dout, t["z"], [t["W"]], [t["b"]])
         ms_b, k_b = ktime(bwd, max(3, steps), R.PROF_AGG_BWD)
+        _, k_bs = ktime(bwd, max(3, steps), R.PROF_AGG_SUM)
 
         def fb():
             fwd()
@@ -288,11 +317,11 @@ class C2:
         del ppt
         pk, _ = peaks()
         pt_flop = 2.0 * (2 * self.d) * self.d_out * self.matched
-        # backward bytes: per pass and tuple one 4-byte index, per H row its descriptor (twice), the
-        # dOut rows (bf16) and H rows (bf16) once per pass, dz written by the src pass and read and
-        # written by the dst pass
+        # backward compulsory bytes: per pass and tuple one 4-byte index, the dOut rows (bf16) and
+        # H rows (bf16) once per pass, dz written by the src pass and read and written by the dst pass
         n_h = int(t["h"].numel())
-        b_bytes = 2 * (4 * self.matched + 32 * n_h + self.n_out * self.d_out * 2 + n_h * self.d * 2) + n_h * self.d * 4 * 3
+        b_bytes = 2 * (4 * self.matched + self.n_out * self.d_out * 2 + n_h * self.d * 2) + n_h * self.d * 4 * 3
+        f_bytes = self.forward_bytes()
         ms_torch = timer(self.torch_step, 3)
         # the push-down rewrite (Linear once per H row, then per-tuple gathers of the f32 products)
         from paper_2605_24207_b300 import relnn as R
@@ -352,12 +381,20 @@ class C2:
         n_h = t["h"].numel()
         at_bytes = 12 * self.matched + 3 * n_h * self.d * 2 + self.n_out * (self.d + 8) * 4
         return {"warm_forward_tuples_per_s": self.matched / (ms_f * 1e-3), "warm_forward_ms": ms_f,
-                "warm_forward_kernel_ms": k_f,
-                "warm_backward_ms": ms_b, "warm_backward_kernel_ms_per_pass": k_b,
+                "warm_forward_kernels_ms": {"seg_sum": k_fs, "agg_gemm": k_f},
+                "warm_forward_roofline": {"bound": "hbm", "algorithmic_bytes": f_bytes,
+                                          "achieved_gbs": f_bytes / (ms_f * 1e-3) / 1e9,
+                                          "frac": f_bytes / (ms_f * 1e-3) / 1e9 / pk["hbm_gbs"],
+                                          "what": "the whole warm forward (both kernels, fix-ups, launches) "
+                                                  "against its compulsory bytes (no intermediate)"},
+                "warm_backward_ms": ms_b,
+                "warm_backward_kernels_ms_per_pass": {"seg_sum": k_bs, "agg_gemm": k_b},
                 "warm_backward_roofline": {"bound": "hbm", "algorithmic_bytes": b_bytes,
-                                           "achieved_gbs": b_bytes / (2 * k_b * 1e-3) / 1e9 if k_b else None,
-                                           "frac": (b_bytes / (2 * k_b * 1e-3) / 1e9 / pk["hbm_gbs"]) if k_b else None,
-                                           "kernel": "agg_tc_kernel<bwd> (two passes)"},
+                                           "achieved_gbs": b_bytes / (ms_b * 1e-3) / 1e9,
+                                           "frac": b_bytes / (ms_b * 1e-3) / 1e9 / pk["hbm_gbs"],
+                                           "what": "the whole warm backward (two passes of gather-sum + "
+                                                   "GEMM, dOut preparation, fix-ups) against its compulsory "
+                                                   "bytes"},
                 "warm_fwd_bwd_tuples_per_s": self.matched / (ms_fb * 1e-3), "warm_fwd_bwd_ms": ms_fb,
                 "per_tuple_form": {"warm_forward_ms": ms_pt, "fwd_tc_kernel_ms": k_pt,
                                    "tensor_tflops": pt_flop / (k_pt * 1e-3) / 1e12 if k_pt else None,
@@ -579,6 +616,16 @@ class C4:
         self.n_h = int(rel.h_ids.size)
         self.plan0 = p
         self.out = torch.empty((self.n_out, 96), dtype=torch.float32, device=dev)
+
+    def tune(self):
+        """The autotuner's tile choice of the per-tuple form (the rule has a per-tuple embedding),
+        timed on the first branch, applied before anything is timed."""
+        from paper_2605_24207_b300 import autotune as A
+        import torch
+        c = A.tune_rule(64, 96, int(self.sizes[0]), rel=self.rel, z_dtype=torch.float32, kahan=True,
+                        backward=False, cache=None, reps=3)
+        self.flags = (self.flags & ~A.R.FLAG_TILE128) | A.apply(c)
+        return c
 
     def step(self):
         from paper_2605_24207_b300 import relnn as R
@@ -1067,6 +1114,7 @@ def run_relnn(args):
 
     wl = WORKLOADS[args.config](args)
     wl.to_device(dev)
+    tuned = wl.tune() if hasattr(wl, "tune") and not args.no_tune else None
 
     # ------------------------------------------------------------ timed region (device inputs)
     m = measure(wl, args.steps, args.warmup)
@@ -1116,12 +1164,17 @@ def run_relnn(args):
             sa.n_tuples = sa.n_keys = None
             sw = WORKLOADS[name](sa)
             sw.to_device(dev)
+            from paper_2605_24207_b300 import autotune as A
+            A.apply(None)  # library defaults, then this configuration's own tuning
+            s_tuned = sw.tune() if hasattr(sw, "tune") and not args.no_tune else None
             sm = measure(sw, steps, 3)
             srl, srl_all = roofline(sw, sm, steps, fp32)
             rec = {"value": sw.matched / (sm["ms"] * 1e-3), "unit": UNIT, "ms_per_step": sm["ms"], "steps": steps,
                    "warmup": 3, "config": {"workload": sw.describe(), "matched_tuples_per_step": sw.matched},
                    "roofline": srl, "kernels": srl_all, "clocks": sm["clocks"], "gpu_launches": sm["launches"],
                    "plan_ms": sm["plan_ms"]}
+            if s_tuned:
+                rec["tuned"] = s_tuned
             rec.update(sw.extras(timer, steps))
             subs[name] = rec
             del sw
@@ -1146,6 +1199,11 @@ def run_relnn(args):
             "gpu_launches": m["launches"], "clocks": m["clocks"], "wall_s_timed": m["wall"],
             "fp32_peak": fp32,
         }
+        if tuned:
+            line["tuned"] = dict(tuned, what="autotune.tune_rule on this relation (plan + forward): the "
+                                             "configuration timed here; ms / default_ms are the tuner's "
+                                             "forward times with it and with the library defaults, plan_ms / "
+                                             "default_plan_ms the plan times")
         line.update(extras)
         if subs:
             line["subrecords"] = subs

@@ -193,6 +193,14 @@ relnn_status relnn_plan_out_keys(relnn_plan_t p, void* d_out_keys, void* stream)
  * RELNN_EDEVICE (and clears it). */
 relnn_status relnn_plan_check(relnn_plan_t p, void* stream);
 
+/* sync (host only). The caller's promise about H.z for the following calls on this plan: an f32 table
+ * passed at the same address with the same nonzero `version` holds the same values. The BF16 form
+ * then converts the table to bf16 once per version and reuses the copy across forwards and
+ * backwards (a training step's forward and backward share one conversion). version 0 (the default)
+ * promises nothing: the table is converted on every call. Changing the table without changing the
+ * version gives results computed from the stale copy. */
+relnn_status relnn_plan_set_z_version(relnn_plan_t p, uint64_t version);
+
 typedef struct relnn_rule_params {
     const void* d_z;               /* H.z [n_h, d]                                                 */
     relnn_float_t z_dtype;
@@ -460,10 +468,20 @@ relnn_status relnn_profile_reset(void);
  *   RELNN_TUNE_SORT_BITS   widest digit of a radix-sort pass (4..11, default 8): the content track's
  *                          group sort takes ceil(key bits / this) passes of equal width; narrower
  *                          digits make longer runs per 4096-key tile in the scatter
- *   RELNN_TUNE_AGG_ROWS    output rows per tile of the aggregate-first kernel (0 = the largest that
- *                          fits, or 32 / 64 / 128)                                                 */
+ *   RELNN_TUNE_AGG_ROWS    output rows per tile of the aggregate-first GEMM (0 = the largest that
+ *                          fits, or 32 / 64 / 128)
+ *   RELNN_TUNE_AGG_STAGES  shared-memory pipeline stages of that GEMM (0 = as many as fit, at most
+ *                          4; or 2..4, capped at what fits)
+ *   RELNN_TUNE_AGG_EPI     epilogue warps of that GEMM: 4 (one per TMEM lane quarter) or 8 (two per
+ *                          quarter, each on every other 32-row chunk); 0 = 8
+ *   RELNN_TUNE_KAHAN_MIN   with RELNN_FLAG_KAHAN, the gather-sum of the aggregate-first form
+ *                          compensates only rows of at least this many tuples (rows cut into chunks
+ *                          always); 0 = every row (default)                                         */
 #define RELNN_TUNE_SORT_BITS 0
 #define RELNN_TUNE_AGG_ROWS 1
+#define RELNN_TUNE_AGG_STAGES 2
+#define RELNN_TUNE_AGG_EPI 3
+#define RELNN_TUNE_KAHAN_MIN 4
 relnn_status relnn_tune_set(int32_t knob, int64_t value);
 relnn_status relnn_tune_get(int32_t knob, int64_t* value);
 

@@ -617,41 +617,65 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 
 // S[v][0, w) = S_hi, S[v][kpad, kpad + w) = S_lo of the sum of the tuples' table rows; the other
 // columns of the row zero. A warp takes 32 virtual rows at a time (their descriptors in one load);
-// lane groups of L = w / 8 lanes take every G-th tuple (a lane = one 16-byte chunk of a row).
+// their tuples are one contiguous range of gidx (at most 32 x 32 indices), staged in shared memory.
+// Lane groups of L = w / 8 lanes each own one row at a time (a lane = one 16-byte chunk of the row,
+// so a group needs no reduction across lanes): G = 32 / L rows are summed side by side, each group
+// walking its row's tuples in order with up to kUnroll row loads in flight.
 // SINGLE: every tuple of a virtual row names the same table row (the backward's runs of equal dst
 // rows): the row is loaded once and multiplied by the tuple count (exact in f32, count <= 32).
+constexpr int kSegWarps = 8;
+constexpr int kSegIdx = 32 * kChunk;  // tuple indices of a warp's 32 virtual rows
+
 template <bool KAHAN, bool SINGLE>
-__global__ void __launch_bounds__(256, 3) seg_sum_kernel(const int4* __restrict__ vr, int64_t nv,
-                                                      const int32_t* __restrict__ gidx,
-                                                      const uint16_t* __restrict__ tbl, int64_t tbl_rows, int w,
-                                                      int kpad, uint16_t* __restrict__ S, int* status) {
+__global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* __restrict__ vr, int64_t nv,
+                                                                 const int32_t* __restrict__ gidx,
+                                                                 const uint16_t* __restrict__ tbl, int64_t tbl_rows,
+                                                                 int w, int kpad, uint16_t* __restrict__ S,
+                                                                 int* status, int kahan_min) {
+    __shared__ int32_t s_idx[SINGLE ? 1 : kSegWarps][SINGLE ? 1 : kSegIdx];
     const int lane = threadIdx.x & 31;
     const int L = w >> 3, lsh = 31 - __clz(L), G = 32 >> lsh;
     const int grp = lane >> lsh, ch = lane & (L - 1);
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const uint4* __restrict__ base = reinterpret_cast<const uint4*>(tbl) + ch;
-    const int pitch = 2 * kpad;
+    const int pitch = 2 * kpad, nck = kpad >> 3;
+    int32_t* sidx = s_idx[SINGLE ? 0 : threadIdx.x >> 5];
     for (int64_t vb = warp0 * 32; vb < nv; vb += nw * 32) {
         const int4 mine = vb + lane < nv ? __ldg(vr + vb + lane) : make_int4(0, 0, -1, -1);
         const int nrows = (int)imin64(32, nv - vb);
-        int ix;
-        {
-            const int x0 = __shfl_sync(0xffffffffu, mine.x, 0), y0 = __shfl_sync(0xffffffffu, mine.y, 0);
-            ix = lane < y0 ? __ldg(gidx + x0 + lane) : -1;
+        const int myn = mine.y > 0 ? mine.y : 0;
+        int x0 = 0;
+        bool ok = true;
+        if (!SINGLE) {
+            x0 = (int)__reduce_min_sync(0xffffffffu, (unsigned)(myn > 0 ? mine.x : INT_MAX));
+            const int cnt = (int)__reduce_add_sync(0xffffffffu, (unsigned)myn);
+            const int x1 = (int)__reduce_max_sync(0xffffffffu, (unsigned)(myn > 0 ? mine.x + myn : 0));
+            // the non-empty rows' tuples must tile [x0, x0 + cnt) (virtual rows are in tuple order)
+            ok = cnt == 0 || (x1 - x0 == cnt && cnt <= kSegIdx);
+            if (!ok && lane == 0) raise_status(status, RELNN_DEV_BOUNDS);
+            __syncwarp();
+            if (ok)
+                for (int i = lane; i < cnt; i += 32) sidx[i] = __ldg(gidx + x0 + i);
+            __syncwarp();
         }
-        for (int j = 0; j < nrows; ++j) {
-            const int n = __shfl_sync(0xffffffffu, mine.y, j);
-            // the next row's tuple indices load while this row is summed
-            const int xn = __shfl_sync(0xffffffffu, mine.x, (j + 1) & 31);
-            const int yn = j + 1 < nrows ? __shfl_sync(0xffffffffu, mine.y, (j + 1) & 31) : 0;
-            const int ixn = lane < yn ? __ldg(gidx + xn + lane) : -1;
+        for (int j0 = 0; j0 < nrows; j0 += G) {
+            const int j = j0 + grp;  // this group's row of the batch
+            const int jj = j < nrows ? j : 0;
+            // every lane takes part in every shuffle (none under a condition)
+            const int n_j = __shfl_sync(0xffffffffu, myn, jj);
+            const int x_j = __shfl_sync(0xffffffffu, mine.x, jj);
+            const int p_j = __shfl_sync(0xffffffffu, mine.w, jj);
+            const int n = (j < nrows && ok) ? n_j : 0;
+            const int xo = x_j - x0;
+            // KAHAN: compensated for rows of at least kahan_min tuples and for chunks of cut rows
+            const bool kh = KAHAN && (n >= kahan_min || p_j >= 0);
             float acc[8], cmp[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) acc[i] = cmp[i] = 0.f;
             if (SINGLE) {
-                const int r = __shfl_sync(0xffffffffu, ix, 0);
-                if (n > 0 && grp == 0 && in_bounds(r, tbl_rows, status)) {
+                const int r = n > 0 ? __ldg(gidx + xo) : -1;
+                if (n > 0 && in_bounds(r, tbl_rows, status)) {
                     const uint4 u = __ldg(base + (int64_t)r * L);
                     const float c = (float)n;
                     const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
@@ -661,35 +685,24 @@ __global__ void __launch_bounds__(256, 3) seg_sum_kernel(const int4* __restrict_
                         acc[2 * i + 1] = c * __uint_as_float(wd[i] & 0xffff0000u);
                     }
                 }
-            }
-            for (int j0 = 0; !SINGLE && j0 < n; j0 += kUnroll * G) {
-                // slots of this batch that hold a tuple of the row (warp-uniform): short rows skip the rest
-                const int slots = min(kUnroll, (n - j0 + G - 1) >> (5 - lsh));
-                uint4 u[kUnroll];
+            } else {
+                const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)n);
+                for (int t0 = 0; t0 < nmax; t0 += kUnroll) {
+                    const int slots = min(kUnroll, nmax - t0);  // warp-uniform
+                    uint4 u[kUnroll];
 #pragma unroll
-                for (int q = 0; q < kUnroll; ++q) {
-                    if (q >= slots) break;
-                    const int jj = j0 + q * G + grp;
-                    const int r = __shfl_sync(0xffffffffu, ix, jj & 31);
-                    u[q] = (jj < n && in_bounds(r, tbl_rows, status)) ? __ldg(base + (int64_t)r * L)
-                                                                       : make_uint4(0u, 0u, 0u, 0u);
-                }
+                    for (int q = 0; q < kUnroll; ++q) {
+                        if (q >= slots) break;
+                        u[q] = make_uint4(0u, 0u, 0u, 0u);
+                        if (t0 + q < n) {
+                            const int r = sidx[xo + t0 + q];
+                            if (in_bounds(r, tbl_rows, status)) u[q] = __ldg(base + (int64_t)r * L);
+                        }
+                    }
 #pragma unroll
-                for (int q = 0; q < kUnroll; ++q) {
-                    if (q >= slots) break;
-                    add8(acc, cmp, u[q], KAHAN);
-                }
-            }
-            for (int off = L; off < 32; off <<= 1) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (KAHAN) {
-                        const float s2 = __shfl_xor_sync(0xffffffffu, acc[i], off);
-                        const float c2 = __shfl_xor_sync(0xffffffffu, cmp[i], off);
-                        acc[i] = (acc[i] - cmp[i]) + (s2 - c2);
-                        cmp[i] = 0.f;
-                    } else {
-                        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+                    for (int q = 0; q < kUnroll; ++q) {
+                        if (q >= slots) break;
+                        add8(acc, cmp, u[q], kh);
                     }
                 }
             }
@@ -697,23 +710,40 @@ __global__ void __launch_bounds__(256, 3) seg_sum_kernel(const int4* __restrict_
 #pragma unroll
                 for (int i = 0; i < 8; ++i) acc[i] -= cmp[i];
             }
-            if (lane < (kpad >> 3)) {
-                uint32_t hi[4] = {0u, 0u, 0u, 0u}, lo[4] = {0u, 0u, 0u, 0u};
-                if (lane < L) {
+            if (j < nrows) {
+                uint32_t hi[4], lo[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        hi[i] = pack_bf16x2(acc[2 * i], acc[2 * i + 1]);
-                        const float h0 = __uint_as_float(hi[i] << 16), h1 = __uint_as_float(hi[i] & 0xffff0000u);
-                        lo[i] = pack_bf16x2(acc[2 * i] - h0, acc[2 * i + 1] - h1);
-                    }
+                for (int i = 0; i < 4; ++i) {
+                    hi[i] = pack_bf16x2(acc[2 * i], acc[2 * i + 1]);
+                    const float h0 = __uint_as_float(hi[i] << 16), h1 = __uint_as_float(hi[i] & 0xffff0000u);
+                    lo[i] = pack_bf16x2(acc[2 * i] - h0, acc[2 * i + 1] - h1);
                 }
-                uint16_t* row = S + (vb + j) * pitch + 8 * lane;
-                *reinterpret_cast<uint4*>(row) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<uint4*>(row + kpad) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                uint16_t* row = S + (vb + j) * pitch;
+                for (int c = ch; c < nck; c += L) {
+                    const bool data = c < L;  // chunks past w are the zero padding of each half
+                    *reinterpret_cast<uint4*>(row + 8 * c) =
+                        data ? make_uint4(hi[0], hi[1], hi[2], hi[3]) : make_uint4(0u, 0u, 0u, 0u);
+                    *reinterpret_cast<uint4*>(row + kpad + 8 * c) =
+                        data ? make_uint4(lo[0], lo[1], lo[2], lo[3]) : make_uint4(0u, 0u, 0u, 0u);
+                }
             }
-            ix = ixn;
         }
     }
+}
+
+// Grid of the gather-sum: every block resident (the warps stride over the 32-row batches).
+template <bool KAHAN, bool SINGLE>
+int seg_sum_grid(int64_t nv) {
+    static int per_sm = 0;
+    if (per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_sum_kernel<KAHAN, SINGLE>, 32 * kSegWarps, 0) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            per_sm = 0;
+        }
+        per_sm = std::max(1, per_sm);
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nv, 32 * kSegWarps), (int64_t)num_sms() * per_sm));
 }
 
 // Dst H row of every virtual row (the first tuple's; all tuples of a row share it when H keys are
@@ -725,10 +755,12 @@ __global__ void vr_first_kernel(const int4* __restrict__ vr, int64_t nv, const i
     }
 }
 
-constexpr int kGemmThreads = 256;   // warps 0-2 loaders, 3 MMA, 4-7 epilogue
+// warps 0-2 loaders, 3 MMA, 4.. epilogue: EPI = 4 (one per TMEM lane quarter) or 8 (two per quarter,
+// each on every other 32-row chunk of a tile)
 constexpr int kGemmLoaders = 96;
 constexpr int kGemmMma = 3;
 constexpr int kGemmEpi0 = 4;
+constexpr int gemm_threads(int epi) { return 32 * (kGemmEpi0 + epi); }
 
 struct GemmArgs {
     const int4* vr;
@@ -754,8 +786,8 @@ struct GemmArgs {
 // Forward: D1 = A_src [S_hi; S_lo], D2 = A_dst R (the dst rows), Out = D1 + n (D2 + b).
 // Backward pass: D1 = A [S_hi; S_lo] is a dz row (A = a W^T block), and dW += S^T R with R = the
 // rows' z, both operands read MN-major from the staged rows, accumulated in TMEM over the CTA's tiles.
-template <bool BWD>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+template <bool BWD, int EPI>
+__global__ void __launch_bounds__(gemm_threads(EPI), 1)
 agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap smap,
                 const __grid_constant__ GemmArgs a) {
     extern __shared__ uint8_t dyn_smem[];
@@ -785,7 +817,7 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(&tfull[i]), 1);
-            mbar_init(smem_u32(&tempty[i]), 32 * kEpiWarps);
+            mbar_init(smem_u32(&tempty[i]), 32 * EPI);
         }
         mbar_init(smem_u32(wbar), 1);
         mbar_init(smem_u32(drain), 1);
@@ -927,7 +959,10 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
         __syncwarp();
     } else if (warp >= kGemmEpi0) {
         // ------------------------------------------------------------------ epilogue
+        // EH warps per TMEM lane quarter, warp eh taking 32-row chunks eh, eh + EH, ... of a tile
+        constexpr int EH = EPI / 4;
         const int q = warp & 3;
+        const int eh = (warp - kGemmEpi0) >> 2;
         const bool has_r = !BWD && a.n_kb_r > 0;
         float bias_r[2];
 #pragma unroll
@@ -935,13 +970,15 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
             const int o = mb * 128 + 32 * q + lane;
             bias_r[mb] = (a.bias && mb < a.m_blocks && o < a.n_feat) ? a.bias[o] : 0.f;
         }
-        // the virtual rows of the next tile (lane l of register c: row 32 c + l) load during this one
-        int4 meta_n[kMaxMeta];
+        // this warp's chunks of the next tile (lane l of register c: row 32 (EH c + eh) + l) load
+        // during this one
+        int4 meta_n[kMaxMeta / EH];
         auto load_meta = [&](int64_t tile) {
 #pragma unroll
-            for (int c = 0; c < kMaxMeta; ++c) {
-                const int64_t v = tile * N + 32 * c + lane;
-                meta_n[c] = (tile < a.n_tiles && 32 * c < N && v < a.nv) ? __ldg(a.vr + v) : make_int4(0, 0, -1, -1);
+            for (int c = 0; c < kMaxMeta / EH; ++c) {
+                const int rr = 32 * (EH * c + eh);
+                const int64_t v = tile * N + rr + lane;
+                meta_n[c] = (tile < a.n_tiles && rr < N && v < a.nv) ? __ldg(a.vr + v) : make_int4(0, 0, -1, -1);
             }
         };
         load_meta(blockIdx.x);
@@ -949,29 +986,47 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
         for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
             const int acc = lt & 1;
             const uint32_t ause = (uint32_t)(lt >> 1);
-            int4 meta[kMaxMeta];
+            int4 meta[kMaxMeta / EH];
 #pragma unroll
-            for (int c = 0; c < kMaxMeta; ++c) meta[c] = meta_n[c];
+            for (int c = 0; c < kMaxMeta / EH; ++c) meta[c] = meta_n[c];
             load_meta(tile + gridDim.x);
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), ause & 1u, a.status, abort_flag))) break;
             tc_fence_after();
             const int64_t v0 = tile * N;
 #pragma unroll
-            for (int c = 0; c < kMaxMeta; ++c) {
-                const int64_t vb = v0 + 32 * c;
-                if (32 * c >= N || vb >= a.nv) break;
+            for (int c = 0; c < kMaxMeta / EH; ++c) {
+                const int rr = 32 * (EH * c + eh);
+                const int64_t vb = v0 + rr;
+                if (rr >= N || vb >= a.nv) break;
                 const int4 mt = meta[c];
+                // chunks of consecutive whole rows (no chunk partial, no row past the end) store row after
+                // row without per-row bookkeeping
+                const int row0 = __shfl_sync(0xffffffffu, mt.z, 0);
+                const bool simple = __all_sync(0xffffffffu, mt.w < 0 && mt.z == row0 + lane);
                 for (int mb = 0; mb < a.m_blocks; ++mb) {
                     if (mb * 128 + 32 * q >= a.n_feat) continue;
                     const int o = mb * 128 + 32 * q + lane;
                     const bool o_ok = o < a.n_feat;
                     const float bo = mb == 0 ? bias_r[0] : bias_r[1];
                     const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * buf_cols +
-                                        (uint32_t)mb * N + (uint32_t)(32 * c);
+                                        (uint32_t)mb * N + (uint32_t)rr;
                     uint32_t v1[32], v2[32];
                     tmem_ld_32x32b_x32(ta, v1);
                     if (has_r) tmem_ld_32x32b_x32(ta + (uint32_t)a.m_blocks * N, v2);
                     tmem_ld_wait();
+                    if (simple && a.out && in_bounds(row0 + 31, a.out_rows, a.status) && in_bounds(row0, a.out_rows, a.status)) {
+                        float* dst = a.out + (int64_t)row0 * a.n_feat + o;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            float y = __uint_as_float(v1[j]);
+                            if (!BWD) {
+                                const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
+                                y += nj * ((has_r ? __uint_as_float(v2[j]) : 0.f) + bo);
+                            }
+                            if (o_ok) emit_out(dst + (int64_t)j * a.n_feat, y, a.accumulate);
+                        }
+                        continue;
+                    }
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int row = __shfl_sync(0xffffffffu, mt.z, j);
@@ -990,7 +1045,7 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
             tc_fence_before();
             mbar_arrive(smem_u32(&tempty[acc]));
         }
-        if (BWD) {
+        if (BWD && eh == 0) {
             // this CTA's dW partial (TMEM lane = S feature, columns = R features)
             if (__all_sync(0xffffffffu, mbar_wait(smem_u32(drain), 0, a.status, abort_flag))) {
                 tc_fence_after();
@@ -1454,6 +1509,9 @@ relnn_status agg_fixup(const VRows& V, const float* vpart, float* vpart2, float*
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Epilogue warps of agg_gemm_kernel (RELNN_TUNE_AGG_EPI; 8 by default).
+int gemm_epi() { return tune_get(RELNN_TUNE_AGG_EPI) == 4 ? 4 : 8; }
+
 // Tile rows and stages of agg_gemm_kernel (two stages at the largest N). Backward: A holds only the
 // S part's K blocks, and TMEM also holds dW (m_dw blocks of w_r columns).
 AggCfg gemm_config(int n_kb_s, int n_kb_r, int m_blocks, bool bwd = false, int m_dw = 0, int w_r = 0) {
@@ -1469,7 +1527,8 @@ AggCfg gemm_config(int n_kb_s, int n_kb_r, int m_blocks, bool bwd = false, int m
         if (cols > 512) continue;
         c.N = N;
         c.dw_col = 2u * m_blocks * N;
-        c.stages = (int)std::min<size_t>(4, (kSmemLimit - fixed) / stage);
+        const int64_t want_st = tune_get(RELNN_TUNE_AGG_STAGES);
+        c.stages = (int)std::min<size_t>(want_st ? (size_t)want_st : 4, (kSmemLimit - fixed) / stage);
         uint32_t t = 32;
         while (t < cols) t <<= 1;
         c.tmem_cols = t;
@@ -1490,11 +1549,6 @@ AggCfg fwd_cfg(const Plan& p) {
     const int n_parts = p.concat_dst ? 2 : 1;
     const int kpad = ((p.d + 63) / 64) * 64;
     return agg_config(n_parts * kpad / 64, (p.d_out + 127) / 128, false, 0, 0, 0);
-}
-
-// Backward pass: A = a W^T block (M = z features, K = output features), B of G^T Z = z rows.
-AggCfg bwd_cfg(const Plan& p) {
-    return agg_config((p.d_out + 63) / 64, (p.d + 127) / 128, true, (p.d + 63) / 64, (p.d_out + 127) / 128, p.d);
 }
 
 }  // namespace
@@ -1546,10 +1600,12 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
     RELNN_TRY(p.sbuf.alloc(sizeof(uint16_t) * 2 * (size_t)kpad * std::max<int64_t>(nv_max, 1)));
     static bool attr_set = false;
     if (!attr_set) {
-        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
-    const int ss_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nv_max, 32 * 8), (int64_t)num_sms() * 8));
+    const int ss_blocks = p.kahan ? seg_sum_grid<true, false>(nv_max) : seg_sum_grid<false, false>(nv_max);
+    const int kmin = (int)tune_get(RELNN_TUNE_KAHAN_MIN);
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         const VRows& V = b.vr_out;
@@ -1558,10 +1614,10 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         {
             ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
             const uint16_t* zt = reinterpret_cast<const uint16_t*>(io.z);
-            if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
-                                                                                p.n_h, p.d, kpad, S, p.status.as<int>());
-            else seg_sum_kernel<false, false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
-                                                                          p.n_h, p.d, kpad, S, p.status.as<int>());
+            if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
+                                                                                p.n_h, p.d, kpad, S, p.status.as<int>(), kmin);
+            else seg_sum_kernel<false, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
+                                                                          p.n_h, p.d, kpad, S, p.status.as<int>(), kmin);
             note_launch();
             prof_end(pt, st);
         }
@@ -1597,7 +1653,9 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
         {
             ProfToken pt = prof_begin(RELNN_PROF_AGG_FWD, st);
-            { agg_gemm_kernel<false><<<grid, kGemmThreads, cfg.smem, st>>>(amap, smap, a); note_launch(); }
+            if (gemm_epi() == 4) agg_gemm_kernel<false, 4><<<grid, gemm_threads(4), cfg.smem, st>>>(amap, smap, a);
+            else agg_gemm_kernel<false, 8><<<grid, gemm_threads(8), cfg.smem, st>>>(amap, smap, a);
+            note_launch();
             prof_end(pt, st);
         }
         RELNN_CUDA(cudaGetLastError());
@@ -1746,7 +1804,8 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
     RELNN_TRY(p.sbuf.alloc(sizeof(uint16_t) * 2 * (size_t)kpad_g * std::max<int64_t>(nv_max, 1)));
     static bool attr_set = false;
     if (!attr_set) {
-        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
     for (size_t i = 0; i < p.br.size(); ++i) {
@@ -1765,20 +1824,22 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             // G rows: sums of dOut rows per virtual row (src order: a row per tuple; dst order: one
             // row times the run's length), as bf16 pairs
             uint16_t* S = p.sbuf.as<uint16_t>();
-            const int ss_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(V.nv, 32 * 8), (int64_t)num_sms() * 8));
+            const int ss_blocks = pass == 1 ? seg_sum_grid<false, true>(V.nv)
+                                  : p.kahan ? seg_sum_grid<true, false>(V.nv) : seg_sum_grid<false, false>(V.nv);
             const int32_t* gi = pass == 0 ? b.seg_src.as<int32_t>() : b.seg.as<int32_t>();
+            const int kmin = (int)tune_get(RELNN_TUNE_KAHAN_MIN);
             {
                 ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
                 const uint16_t* tb = p.doutbf.as<uint16_t>();
                 int* stw = p.status.as<int>();
                 if (pass == 0) {
-                    if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
-                                                                                        p.d_out, kpad_g, S, stw);
-                    else seg_sum_kernel<false, false><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
-                                                                                  p.d_out, kpad_g, S, stw);
+                    if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
+                                                                                        p.d_out, kpad_g, S, stw, kmin);
+                    else seg_sum_kernel<false, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
+                                                                                  p.d_out, kpad_g, S, stw, kmin);
                 } else {
-                    seg_sum_kernel<false, true><<<ss_blocks, 256, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out,
-                                                                            kpad_g, S, stw);
+                    seg_sum_kernel<false, true><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out,
+                                                                            kpad_g, S, stw, 0);
                 }
                 note_launch();
                 prof_end(pt, st);
@@ -1821,7 +1882,9 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             const int grid = (int)std::min<int64_t>(a.n_tiles, grid_max);
             {
                 ProfToken pt = prof_begin(RELNN_PROF_AGG_BWD, st);
-                { agg_gemm_kernel<true><<<grid, kGemmThreads, cfg.smem, st>>>(amap, smap, a); note_launch(); }
+                if (gemm_epi() == 4) agg_gemm_kernel<true, 4><<<grid, gemm_threads(4), cfg.smem, st>>>(amap, smap, a);
+                else agg_gemm_kernel<true, 8><<<grid, gemm_threads(8), cfg.smem, st>>>(amap, smap, a);
+                note_launch();
                 prof_end(pt, st);
             }
             RELNN_CUDA(cudaGetLastError());

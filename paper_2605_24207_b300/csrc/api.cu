@@ -165,6 +165,12 @@ relnn_status relnn_plan_check(relnn_plan_t p, void* stream) {
     return RELNN_OK;
 }
 
+relnn_status relnn_plan_set_z_version(relnn_plan_t p, uint64_t version) {
+    RELNN_CHECK_ARG(p, "set z version: null plan");
+    p->p.z_version = version;
+    return RELNN_OK;
+}
+
 relnn_status relnn_rule_forward(relnn_plan_t p, const relnn_rule_params* prm, void* d_out_keys, float* d_out_z,
                                 int64_t* d_out_count, void* stream) {
     RELNN_CHECK_ARG(p, "forward: null plan");

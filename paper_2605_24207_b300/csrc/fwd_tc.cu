@@ -605,7 +605,14 @@ relnn_status with_bf16_z(Plan& p, const CallIO& io, CallIO& out, cudaStream_t st
     // (an f32 table that is not 16-byte aligned keeps the kernels' convert-as-you-gather path)
     if (io.z_bf16 || p.n_h == 0 || (reinterpret_cast<uintptr_t>(io.z) & 15u)) return RELNN_OK;
     const int64_t n = p.n_h * (int64_t)p.d;  // d % 8 == 0 on the tensor-core path
+    out.z = p.zbf.p;
+    out.z_bf16 = 1;
+    if (p.z_version != 0 && p.zbf.p && p.zbf_src == io.z && p.zbf_version == p.z_version &&
+        p.zbf.bytes >= sizeof(uint16_t) * (size_t)n)
+        return RELNN_OK;  // the copy converted for this table version
     RELNN_TRY(p.zbf.alloc(sizeof(uint16_t) * n));
+    p.zbf_src = io.z;
+    p.zbf_version = p.z_version;
     const int64_t n4 = n / 4;
     const int blocks = (int)std::min<int64_t>(ceil_div(n4, 256), (int64_t)num_sms() * 16);
     { z_to_bf16_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(io.z), n4, p.zbf.as<uint2>()); note_launch(); }

@@ -10,6 +10,7 @@ namespace relnn {
 namespace {
 
 __global__ void key_minmax_kernel(const void* keys, int64_t n, int kt, unsigned long long* mm) {
+    __shared__ unsigned long long wl[8], wh[8];
     unsigned long long lo = ~0ull, hi = 0ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -24,7 +25,17 @@ __global__ void key_minmax_kernel(const void* keys, int64_t n, int kt, unsigned 
         lo = a < lo ? a : lo;
         hi = b > hi ? b : hi;
     }
+    // one pair of atomics per block (per-warp atomics on two words serialise)
     if ((threadIdx.x & 31) == 0) {
+        wl[threadIdx.x >> 5] = lo;
+        wh[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = wl[w] < lo ? wl[w] : lo;
+            hi = wh[w] > hi ? wh[w] : hi;
+        }
         atomicMin(&mm[0], lo);
         atomicMax(&mm[1], hi);
     }
@@ -103,6 +114,73 @@ __global__ void hash_insert_kernel(const int64_t* ukeys, int64_t U, uint64_t mas
     }
 }
 
+// ---- dense build: when the key span is small (at most 4n, or 2^20), a key's slot is key - key_min
+// and the sort becomes a counting pass, one scan and a placement pass.
+constexpr int kDenseRun = 64;  // longest run of equal keys the dense build orders itself
+
+__global__ void dense_count_kernel(const void* keys, int64_t n, int kt, int64_t kmin, int32_t* cnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[(uint64_t)load_key(keys, kt, i) - (uint64_t)kmin], 1);
+}
+
+// packed[s] = count | (count > 0) << 32, so that one exclusive scan gives each slot's first sorted
+// position (low half) and distinct-key index (high half); *maxc = the largest count.
+__global__ void dense_pack_kernel(const int32_t* cnt, int64_t S, int64_t* packed, int* maxc) {
+    int m = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cnt[s];
+        packed[s] = (int64_t)c | ((int64_t)(c > 0) << 32);
+        m = c > m ? c : m;
+    }
+    m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(maxc, m);
+}
+
+__global__ void dense_slots_kernel(const int32_t* cnt, const int64_t* excl, int64_t S, int64_t kmin, int64_t n,
+                                   int64_t U, int32_t* slot_vals, int32_t* run_start, int64_t* ukeys) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = excl[s];
+        const int32_t u = (int32_t)(e >> 32);
+        if (cnt[s] > 0) {
+            slot_vals[s] = u;
+            run_start[u] = (int32_t)(uint32_t)e;
+            ukeys[u] = (int64_t)((uint64_t)kmin + (uint64_t)s);
+        } else {
+            slot_vals[s] = -1;
+        }
+        if (s == 0) run_start[U] = (int32_t)n;
+    }
+}
+
+// Row i goes to its key's run (unique keys: the run's only position; else the next free one, in
+// no particular order until dense_fix_kernel sorts the run).
+__global__ void dense_place_kernel(const void* keys, int64_t n, int kt, int64_t kmin, const int64_t* excl,
+                                   int32_t* cursor, int32_t* rows_sorted, int32_t* uid_of_pos) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = (uint64_t)load_key(keys, kt, i) - (uint64_t)kmin;
+        const int64_t e = excl[s];
+        const int32_t pos = (int32_t)(uint32_t)e + (cursor ? atomicAdd(&cursor[s], 1) : 0);
+        rows_sorted[pos] = (int32_t)i;
+        uid_of_pos[pos] = (int32_t)(e >> 32);
+    }
+}
+
+// Runs of equal keys in ascending row order (insertion sort; runs are at most kDenseRun long).
+__global__ void dense_fix_kernel(const int32_t* run_start, int64_t U, int32_t* rows_sorted) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U; u += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = run_start[u], e = run_start[u + 1];
+        for (int32_t i = b + 1; i < e; ++i) {
+            const int32_t v = rows_sorted[i];
+            int32_t j = i - 1;
+            while (j >= b && rows_sorted[j] > v) {
+                rows_sorted[j + 1] = rows_sorted[j];
+                --j;
+            }
+            rows_sorted[j + 1] = v;
+        }
+    }
+}
+
 // Standalone probe, pass 1: distinct-key index and match count per probe row; per-warp totals.
 __global__ void probe_count_kernel(JoinView j, const void* keys, int64_t m, int kt, int32_t* uarr,
                                    int64_t* warp_tot) {
@@ -165,7 +243,7 @@ relnn_status key_range(const void* keys, int64_t n, int kt, int64_t* kmin, int64
     RELNN_CUDA(cudaMallocAsync(&mm, 16, st));
     unsigned long long init[2] = {~0ull, 0ull};
     cudaMemcpyAsync(mm, init, 16, cudaMemcpyHostToDevice, st);
-    { key_minmax_kernel<<<grid_for(n), 256, 0, st>>>(keys, n, kt, mm); note_launch(); }
+    { key_minmax_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256 * 8), num_sms() * 4)), 256, 0, st>>>(keys, n, kt, mm); note_launch(); }
     unsigned long long h[2];
     cudaMemcpyAsync(h, mm, 16, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(mm, st);
@@ -174,6 +252,52 @@ relnn_status key_range(const void* keys, int64_t n, int kt, int64_t* kmin, int64
     *kmax = (int64_t)(h[1] ^ 0x8000000000000000ull);
     return RELNN_OK;
 }
+
+namespace {
+
+// The dense build over S = span + 1 slots; *done = false (nothing changed) when a key repeats more
+// than kDenseRun times, which the sort path handles.
+relnn_status dense_build(JoinTable& jt, const void* keys, int64_t n, int kt, int64_t kmin, int64_t S, bool* done,
+                         cudaStream_t st) {
+    *done = false;
+    DevBuf cnt, packed;
+    RELNN_TRY(cnt.alloc_tmp(sizeof(int32_t) * (S + 1), st));
+    RELNN_TRY(packed.alloc_tmp(sizeof(int64_t) * (S + 1), st));
+    int32_t* maxc = cnt.as<int32_t>() + S;
+    RELNN_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (S + 1), st));
+    const int gn = grid_for(n), gs = grid_for(S);
+    { dense_count_kernel<<<gn, 256, 0, st>>>(keys, n, kt, kmin, cnt.as<int32_t>()); note_launch(); }
+    { dense_pack_kernel<<<gs, 256, 0, st>>>(cnt.as<int32_t>(), S, packed.as<int64_t>(), maxc); note_launch(); }
+    RELNN_TRY(exclusive_scan<int64_t>(packed.as<int64_t>(), packed.as<int64_t>(), S, packed.as<int64_t>() + S, st));
+    int64_t total = 0;
+    int32_t mc = 0;
+    RELNN_CUDA(cudaMemcpyAsync(&total, packed.as<int64_t>() + S, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaMemcpyAsync(&mc, maxc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    if (mc > kDenseRun) return RELNN_OK;
+    const int64_t U = total >> 32;
+    jt.n_unique = U;
+    jt.mode = 1;
+    jt.direct_size = S;
+    jt.cap = 0;
+    RELNN_TRY(jt.run_start.alloc_nosync(sizeof(int32_t) * (U + 1), st));
+    RELNN_TRY(jt.ukeys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(U, 1), st));
+    RELNN_TRY(jt.slot_vals.alloc_nosync(sizeof(int32_t) * S, st));
+    { dense_slots_kernel<<<gs, 256, 0, st>>>(cnt.as<int32_t>(), packed.as<int64_t>(), S, kmin, n, U,
+                                             jt.slot_vals.as<int32_t>(), jt.run_start.as<int32_t>(),
+                                             jt.ukeys.as<int64_t>()); note_launch(); }
+    const bool dup = U < n;
+    if (dup) RELNN_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * S, st));
+    { dense_place_kernel<<<gn, 256, 0, st>>>(keys, n, kt, kmin, packed.as<int64_t>(), dup ? cnt.as<int32_t>() : nullptr,
+                                             jt.rows_sorted.as<int32_t>(), jt.uid_of_pos.as<int32_t>()); note_launch(); }
+    if (dup) { dense_fix_kernel<<<grid_for(U), 256, 0, st>>>(jt.run_start.as<int32_t>(), U, jt.rows_sorted.as<int32_t>()); note_launch(); }
+    RELNN_CUDA(cudaGetLastError());
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    *done = true;
+    return RELNN_OK;
+}
+
+}  // namespace
 
 relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt, cudaStream_t st) {
     RELNN_CHECK_ARG(n >= 0 && n < (1ll << 31) - 1, "join build: n out of range");
@@ -202,6 +326,11 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     jt.key_max = kmax;
     const uint64_t omin = (uint64_t)kmin ^ 0x8000000000000000ull;
     const uint64_t span = ((uint64_t)kmax ^ 0x8000000000000000ull) - omin;
+    if (span < (uint64_t)std::max<int64_t>(4 * n, 1 << 20)) {
+        bool done = false;
+        RELNN_TRY(dense_build(jt, keys, n, kt, kmin, (int64_t)span + 1, &done, st));
+        if (done) return RELNN_OK;
+    }
     const int nbits = bit_length(span);
     const bool narrow = nbits <= 32;
     const size_t kb = narrow ? 4 : 8;

@@ -10,6 +10,10 @@ namespace relnn {
 
 namespace {
 
+// One thread per kIlp items, no grid-stride loop.
+constexpr int kIlp = 4;
+inline unsigned ilp_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, ceil_div(n, 256 * kIlp)); }
+
 inline int grid_for(int64_t n, int threads = 256) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 16));
 }
@@ -245,6 +249,48 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
     }
 }
 
+// Unique H keys, no selection: if every tuple matches, tuple e's pair goes to position e. This pass
+// assumes so (plain streaming, no look-back) and counts the tuples that do not match; when the count
+// is not zero, the caller runs emit_unique_kernel over the same outputs.
+template <class K, class V>
+__global__ void emit_all_kernel(JoinView j, const void* src, const void* dst, int64_t T, int kt, bool join_dst,
+                                uint64_t omin, unsigned long long* misses, K* t_key, V* t_val) {
+    const int64_t e0 = (blockIdx.x * (int64_t)blockDim.x) * kIlp + threadIdx.x;
+    int64_t ks[kIlp], kd[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+        const int64_t e = e0 + (int64_t)k * blockDim.x;
+        ks[k] = e < T ? load_key(src, kt, e) : 0;
+        kd[k] = e < T ? load_key(dst, kt, e) : 0;
+    }
+    int32_t a[kIlp], b[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+        a[k] = j.lookup(ks[k]);
+        b[k] = join_dst ? j.lookup(kd[k]) : 0;
+    }
+    int32_t hs[kIlp];
+    unsigned miss = 0;
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+        const bool in = e0 + (int64_t)k * blockDim.x < T;
+        const bool ok = a[k] >= 0 && b[k] >= 0;
+        miss += (in && !ok) ? 1u : 0u;
+        hs[k] = in && ok ? __ldg(j.rows_sorted + a[k]) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+        const int64_t e = e0 + (int64_t)k * blockDim.x;
+        if (e < T) {
+            t_key[e] = join_dst ? (K)b[k] : (K)(ordered64(kd[k]) - omin);
+            if (sizeof(V) == 8) t_val[e] = (V)(((uint64_t)(uint32_t)hs[k] << 32) | (uint32_t)e);
+            else t_val[e] = (V)hs[k];
+        }
+    }
+    miss = __reduce_add_sync(0xffffffffu, miss);
+    if ((threadIdx.x & 31) == 0 && miss) atomicAdd(misses, (unsigned long long)miss);
+}
+
 // Splits (src H row << 32 | E row) payloads into hs / er.
 __global__ void split_pair_kernel(const int64_t* val, int64_t m, int32_t* hs, int32_t* er) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
@@ -255,22 +301,51 @@ __global__ void split_pair_kernel(const int64_t* val, int64_t m, int32_t* hs, in
     }
 }
 
-// After grouping by dst position: the dst H row and the output row of every matched tuple.
+// After grouping by dst position: the dst H row and the output row of every matched tuple. Each
+// thread takes kIlp tuples with all of their loads issued before the first use (the lookups are
+// dependent loads; one tuple at a time leaves the memory system idle).
+
 __global__ void finalize_dst_kernel(const uint32_t* pos_d, int64_t m, const int32_t* rows_sorted,
                                     const int32_t* uid_of_pos, const int32_t* out_row, int32_t* hd, int32_t* seg) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t p = pos_d[i];
-        hd[i] = rows_sorted[p];
-        seg[i] = out_row[uid_of_pos[p]];
+    const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x) * kIlp + threadIdx.x;
+    uint32_t p[kIlp];
+    int32_t h[kIlp], u[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        p[k] = i < m ? __ldg(pos_d + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+        const bool ok = i0 + (int64_t)k * blockDim.x < m;
+        h[k] = ok ? __ldg(rows_sorted + p[k]) : 0;
+        u[k] = ok ? __ldg(uid_of_pos + p[k]) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        if (i < m) {
+            hd[i] = h[k];
+            seg[i] = __ldg(out_row + u[k]);
+        }
     }
 }
 
 __global__ void mark_present_kernel(const uint32_t* pos_d, int64_t m, const int32_t* uid_of_pos,
                                     int32_t* present) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x)
-        present[uid_of_pos[pos_d[i]]] = 1;
+    const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x) * kIlp + threadIdx.x;
+    uint32_t p[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        p[k] = i < m ? __ldg(pos_d + i) : 0u;
+    }
+    int32_t u[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) u[k] = i0 + (int64_t)k * blockDim.x < m ? __ldg(uid_of_pos + p[k]) : -1;
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k)
+        if (u[k] >= 0) present[u[k]] = 1;
 }
 
 // present / out_row: exclusive scan of the presence flags; writes the output keys.
@@ -352,7 +427,21 @@ relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M
         RELNN_TRY(t.key_tmp.alloc_tmp(sizeof(K) * cap, st));
         RELNN_TRY(t.val.alloc_tmp(sizeof(V) * cap, st));
         RELNN_TRY(t.val_tmp.alloc_tmp(sizeof(V) * cap, st));
-        if (T > 0) {
+        bool all_matched = false;
+        if (T > 0 && filters_of(bd).n == 0) {
+            DevBuf miss;
+            RELNN_TRY(miss.alloc_tmp(sizeof(unsigned long long), st));
+            RELNN_CUDA(cudaMemsetAsync(miss.p, 0, sizeof(unsigned long long), st));
+            { emit_all_kernel<K, V><<<ilp_grid(T), 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst, t.omin,
+                                                              miss.as<unsigned long long>(), t.key.as<K>(), t.val.as<V>()); note_launch(); }
+            RELNN_CUDA(cudaGetLastError());
+            unsigned long long mu = 0;
+            RELNN_CUDA(cudaMemcpyAsync(&mu, miss.p, sizeof(mu), cudaMemcpyDeviceToHost, st));
+            RELNN_CUDA(cudaStreamSynchronize(st));
+            all_matched = mu == 0;
+            if (all_matched) M = T;
+        }
+        if (T > 0 && !all_matched) {
             const int64_t n_tiles = ceil_div(T, kEmitTile);
             DevBuf ctl;  // tile states, tile counter, total
             const size_t ctl_bytes = sizeof(unsigned long long) * (n_tiles + 2);
@@ -552,9 +641,9 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         // stream chunk: output row = distinct index of the dst key; presence kept by the stream
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0) {
-                { mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                { mark_present_kernel<<<ilp_grid(p.br[i].m), 256, 0, st>>>(
                     tmp[i].keys<uint32_t>(), p.br[i].m, HT.uid_of_pos.as<int32_t>(), p.present_ext); note_launch(); }
-                { finalize_dst_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                { finalize_dst_kernel<<<ilp_grid(p.br[i].m), 256, 0, st>>>(
                     tmp[i].keys<uint32_t>(), p.br[i].m, HT.rows_sorted.as<int32_t>(), HT.uid_of_pos.as<int32_t>(),
                     p.iota_ext, p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>()); note_launch(); }
             }
@@ -568,7 +657,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         RELNN_TRY(out_row.alloc_tmp(sizeof(int32_t) * (U + 1), st));
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
-                { mark_present_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                { mark_present_kernel<<<ilp_grid(p.br[i].m), 256, 0, st>>>(
                     tmp[i].keys<uint32_t>(), p.br[i].m, HT.uid_of_pos.as<int32_t>(), present.as<int32_t>()); note_launch(); }
         RELNN_TRY(exclusive_scan<int32_t>(present.as<int32_t>(), out_row.as<int32_t>(), U, out_row.as<int32_t>() + U, st));
         // the output-row count arrives with the final synchronisation; U bounds it
@@ -579,7 +668,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
                                                          HT.ukeys.as<int64_t>(), U, p.out_keys.as<int64_t>()); note_launch(); }
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
-                { finalize_dst_kernel<<<grid_for(p.br[i].m), 256, 0, st>>>(
+                { finalize_dst_kernel<<<ilp_grid(p.br[i].m), 256, 0, st>>>(
                     tmp[i].keys<uint32_t>(), p.br[i].m, HT.rows_sorted.as<int32_t>(), HT.uid_of_pos.as<int32_t>(),
                     out_row.as<int32_t>(), p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>()); note_launch(); }
         RELNN_CUDA(cudaGetLastError());

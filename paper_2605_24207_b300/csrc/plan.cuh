@@ -69,6 +69,10 @@ struct Plan {
     DevBuf wpack;     // bf16 packed/padded weights for the tensor-core kernels
     DevBuf scratch;   // misc per-call scratch
     DevBuf zbf;       // bf16 copy of an f32 H embedding for the tensor-core kernels
+    // the caller's promise (relnn_plan_set_z_version): an f32 H.z passed at the same address with the
+    // same nonzero version is unchanged, so zbf (converted from zbf_src at zbf_version) is reused
+    uint64_t z_version = 0, zbf_version = 0;
+    const void* zbf_src = nullptr;
     DevBuf doutbf;    // bf16 copy of the output gradient for the backward's src pass
     DevBuf fixjobs;   // long segments handed from the fix-up to its block-per-segment pass
     DevBuf vpart;     // aggregate-first: f32 partial rows of chunks (and their level-2 sums)

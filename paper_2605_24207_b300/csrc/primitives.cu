@@ -111,10 +111,16 @@ __global__ void rs_hist_kernel(const K* __restrict__ keys, int64_t n, int shift,
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortSteps);
+    // all of the thread's keys are loaded before the first atomic (one memory round trip, not 16)
+    K k[kSortSteps];
+#pragma unroll
     for (int s = 0; s < kSortSteps; ++s) {
-        int64_t i = base + s * 32 + lane;
-        if (i < n) atomicAdd(&h[(unsigned)((keys[i] >> shift) & mask)], 1);
+        const int64_t i = base + s * 32 + lane;
+        k[s] = i < n ? __ldg(keys + i) : K(0);
     }
+#pragma unroll
+    for (int s = 0; s < kSortSteps; ++s)
+        if (base + s * 32 + lane < n) atomicAdd(&h[(unsigned)((k[s] >> shift) & mask)], 1);
     __syncthreads();
     for (int i = threadIdx.x; i < bins; i += kSortThreads) hist[(int64_t)i * nblocks + blockIdx.x] = h[i];
 }

@@ -312,21 +312,16 @@ relnn_status forward_pushdown(Plan& p, const CallIO& io_in, float* out, cudaStre
             }
             bps = std::max(1, bps);
         }
+        // half-warp groups (two ranges per warp, 16-byte row accesses) when no mask is kept, d_out is 64
+        // or 128 and out is 16-byte aligned; otherwise one range per warp
+        const bool half = !want_mask && (p.d_out == 64 || p.d_out == 128) &&
+                          (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
         const int64_t n32 = ceil_div(b.m, 32);
-        const int64_t resident = (int64_t)bps * num_sms() * 8;
+        const int64_t resident = (int64_t)bps * num_sms() * 8 * (half ? 2 : 1);
         a.range_tiles = (int)std::min<int64_t>(ceil_div(n32, resident), 1 << 20);
         a.n_ranges = ceil_div(n32, a.range_tiles);
         RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * (size_t)a.n_ranges));
         a.carry = p.carry.as<float>();
-        const bool half = !want_mask && (p.d_out == 64 || p.d_out == 128) &&
-                          (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
-        if (half) {
-            // half-warp groups: two ranges per warp
-            a.range_tiles = (int)std::min<int64_t>(ceil_div(n32, 2 * resident), 1 << 20);
-            a.n_ranges = ceil_div(n32, a.range_tiles);
-            RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * (size_t)a.n_ranges));
-            a.carry = p.carry.as<float>();
-        }
         const int grid = (int)std::min<int64_t>(ceil_div(a.n_ranges, half ? 16 : 8), (int64_t)bps * num_sms());
         {
             ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st);

@@ -201,18 +201,33 @@ void worker_main(relnn_server_s* S) {
                        (!S->queue.empty() && S->mem_in_use + S->queue.front()->mem <= S->budget);
             });
             if (S->queue.empty()) break;  // stopping and drained
+            // the device's free memory now (other batches and other processes hold some of it): a
+            // batch is admitted only while its estimate fits in 90 % of it as well as in the budget
+            lk.unlock();
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+                (void)cudaGetLastError();
+                free_b = (size_t)S->budget;
+            }
+            const int64_t avail = (int64_t)(0.9 * (double)free_b);
+            lk.lock();
+            if (S->queue.empty()) continue;
             while (!S->queue.empty()) {
                 Query* q = S->queue.front();
                 if (!batch.empty() && ((int)batch.size() >= S->cfg.max_batch_queries ||
                                        btup + q->q.n_tuples > S->cfg.max_batch_tuples))
                     break;
                 if (S->mem_in_use + bmem + q->mem > S->budget) break;
+                // the first query of a batch always goes (its estimate fits the budget, and a
+                // smaller free figure only means other batches still hold memory they will free)
+                if (!batch.empty() && bmem + q->mem > avail) break;
                 S->queue.pop_front();
                 q->state = 1;
                 batch.push_back(q);
                 bmem += q->mem;
                 btup += q->q.n_tuples;
             }
+            if (batch.empty()) continue;  // another worker took the front query meanwhile
             S->mem_in_use += bmem;
         }
         relnn_status s = run_batch(S, batch, st);

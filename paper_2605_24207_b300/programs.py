@@ -9,7 +9,8 @@ loss relation (a program of the kind of the paper's Sec. 3.6 example):
     L(; mean((z_o - z_t)^2))                   :- Out(g; z_o), T(g; z_t)
 
 The content track of each rule is planned once (relnn_rule_plan) and reused by every forward and
-backward, as the paper caches content across training iterations.
+backward, as the paper caches content across training iterations; an f32 embedding table is
+converted to bf16 once per tensor version (relnn_plan_set_z_version), not once per call.
 """
 from __future__ import annotations
 
@@ -38,8 +39,8 @@ class StackedReadout:
 
     def forward(self, z, W1, b1, W2, b2, stream=None):
         """Loss (device f32 [1]) and the intermediate relations (kept for backward)."""
-        h1 = self.p1.forward(z, [W1], [b1], stream=stream)
-        h2 = self.p2.forward(h1, [W2], [b2], stream=stream)
+        h1 = self.p1.forward(z, [W1], [b1], stream=stream, z_version="auto")
+        h2 = self.p2.forward(h1, [W2], [b2], stream=stream, z_version="auto")
         ho = self.p3.forward(h2, stream=stream)
         loss, d_ho = R.mse_loss(ho, self.ko, self.targets, self.t_keys, stream=stream)
         self._saved = (z, W1, b1, W2, b2, h1, h2, d_ho)
@@ -49,8 +50,8 @@ class StackedReadout:
         """Gradients of the last forward's loss: dict with dW1, db1, dW2, db2, dz."""
         z, W1, b1, W2, b2, h1, h2, d_ho = self._saved
         _, _, d_h2, _ = self.p3.backward(d_ho, h2, stream=stream)
-        (dW2,), (db2,), d_h1, _ = self.p2.backward(d_h2, h1, [W2], [b2], stream=stream)
-        (dW1,), (db1,), dz, _ = self.p1.backward(d_h1, z, [W1], [b1], stream=stream)
+        (dW2,), (db2,), d_h1, _ = self.p2.backward(d_h2, h1, [W2], [b2], stream=stream, z_version="auto")
+        (dW1,), (db1,), dz, _ = self.p1.backward(d_h1, z, [W1], [b1], stream=stream, z_version="auto")
         return dict(dW1=dW1, db1=db1, dW2=dW2, db2=db2, dz=dz)
 
     def step(self, z, W1, b1, W2, b2, stream=None):

@@ -8,6 +8,7 @@ never falls back to another implementation: if the shared library is missing the
 from __future__ import annotations
 
 import ctypes as C
+import itertools
 import os
 from typing import Sequence
 
@@ -109,7 +110,7 @@ _LIB = None
 EXPORTS = [
     "relnn_version", "relnn_status_string", "relnn_last_error", "relnn_last_device_error",
     "relnn_join_build", "relnn_join_probe", "relnn_join_destroy",
-    "relnn_rule_plan", "relnn_plan_info", "relnn_plan_out_keys", "relnn_plan_check",
+    "relnn_rule_plan", "relnn_plan_info", "relnn_plan_out_keys", "relnn_plan_check", "relnn_plan_set_z_version",
     "relnn_rule_forward", "relnn_rule_backward", "relnn_plan_destroy",
     "relnn_profile_enable", "relnn_profile_read", "relnn_profile_reset", "relnn_launch_count",
 ]
@@ -137,6 +138,7 @@ def lib():
     L.relnn_plan_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     L.relnn_plan_out_keys.argtypes = [vp, vp, vp]
     L.relnn_plan_check.argtypes = [vp, vp]
+    L.relnn_plan_set_z_version.argtypes = [vp, C.c_uint64]
     L.relnn_rule_forward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp]
     L.relnn_rule_backward.argtypes = [vp, C.POINTER(RuleParams), vp, vp, vp, vp, vp, vp]
     L.relnn_plan_destroy.argtypes = [vp]
@@ -232,7 +234,7 @@ def profile_reset():
     _check(lib().relnn_profile_reset())
 
 
-TUNE_SORT_BITS, TUNE_AGG_ROWS = 0, 1
+TUNE_SORT_BITS, TUNE_AGG_ROWS, TUNE_AGG_STAGES, TUNE_AGG_EPI, TUNE_KAHAN_MIN = 0, 1, 2, 3, 4
 
 
 def tune_set(knob: int, value: int):
@@ -394,17 +396,30 @@ class RulePlan:
                                               _ptr(dk), _ptr(dv), _stream(stream)))
         return dq, dk, dv
 
-    def forward(self, z, W=None, b=None, r=None, out=None, stream=None) -> torch.Tensor:
-        """Output embeddings [n_out, d_out] f32 (rows in out_keys() order)."""
+    def _set_z_version(self, z, z_version):
+        v = 0
+        if z_version == "auto":
+            v = _auto_z_version(z)
+        elif z_version is not None:
+            v = int(z_version)
+        _check(lib().relnn_plan_set_z_version(self._h, v))
+
+    def forward(self, z, W=None, b=None, r=None, out=None, stream=None, z_version=None) -> torch.Tensor:
+        """Output embeddings [n_out, d_out] f32 (rows in out_keys() order). z_version: None (an f32 z
+        is converted to bf16 on every call of the BF16 form), "auto" (the tensor object and its
+        in-place version counter key the plan's bf16 copy) or a caller-managed nonzero int."""
         if out is None:
             out = torch.empty((max(self.n_out, 1), self.d_out), dtype=torch.float32, device=self.device)
+        self._set_z_version(z, z_version)
         prm, keep = self._params(z, W, b, r)
         _check(lib().relnn_rule_forward(self._h, C.byref(prm), None, _ptr(out), None, _stream(stream)))
         return out[: self.n_out]
 
-    def backward(self, dout, z, W=None, b=None, r=None, need_dz=True, stream=None):
-        """Gradients (dW list, db list, dz, dr list) of the forward for output gradient ``dout``."""
+    def backward(self, dout, z, W=None, b=None, r=None, need_dz=True, stream=None, z_version=None):
+        """Gradients (dW list, db list, dz, dr list) of the forward for output gradient ``dout``
+        (z_version as for forward)."""
         dev, n = self.device, self.n_branches
+        self._set_z_version(z, z_version)
         dW = [torch.empty((self.d_out, self.d_in), dtype=torch.float32, device=dev) for _ in range(n)] \
             if W is not None else None
         db = [torch.empty(self.d_out, dtype=torch.float32, device=dev) for _ in range(n)] if W is not None else None
@@ -545,6 +560,19 @@ class StreamRule:
             self._h = C.c_void_p()
 
 
+_Z_SERIAL = itertools.count(1)
+
+
+def _auto_z_version(z) -> int:
+    """A nonzero version for tensor object ``z``: a serial number given to the object on first use
+    (a new tensor at a reused address gets a new one) and its in-place version counter."""
+    s = getattr(z, "_relnn_z_serial", None)
+    if s is None:
+        s = next(_Z_SERIAL)
+        z._relnn_z_serial = s
+    return ((s & 0xFFFFFFFFFF) << 24) | (z._version & 0xFFFFFF)
+
+
 class RelnnRule(torch.autograd.Function):
     """Autograd wrapper: forward = relnn_rule_forward, backward = relnn_rule_backward (the gathered
     Concat is recomputed in the backward, not stored). Single-branch rules; for a union use the
@@ -555,14 +583,14 @@ class RelnnRule(torch.autograd.Function):
         ctx.plan = plan
         ctx.save_for_backward(z, W, b, r)
         return plan.forward(z, [W] if W is not None else None, [b] if b is not None else None,
-                            [r] if r is not None else None)
+                            [r] if r is not None else None, z_version="auto")
 
     @staticmethod
     def backward(ctx, dout):
         z, W, b, r = ctx.saved_tensors
         dW, db, dz, dr = ctx.plan.backward(dout, z, [W] if W is not None else None,
                                            [b] if b is not None else None, [r] if r is not None else None,
-                                           need_dz=ctx.needs_input_grad[1])
+                                           need_dz=ctx.needs_input_grad[1], z_version="auto")
         return (None, dz, dW[0] if dW else None, db[0] if db else None, dr[0] if dr else None)
 
 

@@ -76,3 +76,22 @@ def test_pushdown_rejects_per_tuple_embedding(gpu):
     rel = W.make_rule(60, 1000, 100, 64, 64, np.int32, d_r=64)
     with pytest.raises(R.RelnnError):
         run_rule(rel, flags=PD, z_dtype=torch.bfloat16)
+
+
+@pytest.mark.parametrize("d_out", [64, 128])
+def test_pushdown_unaligned_output_takes_warp_form(gpu, d_out):
+    """An output 4 bytes off a 16-byte boundary cannot take the half-warp walk (16-byte row stores):
+    the one-range-per-warp walk runs instead and gives the same rows."""
+    rel = W.make_rule(61, 20_000, 1500, 64, d_out, np.int32, src_dist="zipf", src_s=1.2)
+    br = rel.branches[0]
+    plan = R.RulePlan(to_dev(rel.h_ids), [(to_dev(br.src), to_dev(br.dst))], 64, d_out, flags=PD)
+    buf = torch.empty(plan.n_out * d_out + 1, dtype=torch.float32, device="cuda")
+    out = buf[1:].view(plan.n_out, d_out)
+    assert out.data_ptr() % 16 == 4
+    plan.forward(to_dev(rel.z, torch.bfloat16), [to_dev(br.W)], [to_dev(br.b)], out=out)
+    torch.cuda.synchronize()
+    plan.check()
+    _, oo, _ = oracle_rule(rel, round_z=True, round_w=True)
+    assert rel_frob(out.cpu().numpy(), oo) <= 1e-4
+    _, out_a, _, _ = run_rule(rel, flags=PD, z_dtype=torch.bfloat16)
+    assert rel_frob(out.cpu().numpy(), out_a) <= 1e-5
