@@ -74,15 +74,25 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler (every 20 ms, timestamped), started before the warm-up so that it is
-    running when the timed region begins; stop() keeps the samples taken inside [t0, t1]."""
+    """Clock sampler for a timed region: an NVML thread (the library nvidia-smi reads, queried
+    in-process every 2 ms, so that even a region of a few tens of milliseconds holds samples) on the
+    GPU with the CUDA device's PCI bus id; nvidia-smi every 20 ms if NVML is unavailable. Started
+    before the warm-up; stop() keeps the samples taken inside [t0, t1]."""
 
     Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
+        self.samples, self.p, self.thread = [], None, None
+        try:
+            self._start_nvml(gpu_index)
+            return
+        except Exception:  # no NVML: the nvidia-smi command line of the profiling recipe
+            self.thread = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.source = "nvidia-smi, 20 ms"
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
@@ -90,16 +100,48 @@ class Clocks:
         except OSError:
             self.p = None
 
-    def stop(self, t0: float, t1: float):
-        """Summary of the samples whose timestamp lies in [t0, t1] (time.time() seconds)."""
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+    def _start_nvml(self, gpu_index: int):
+        """NVML through ctypes (libnvidia-ml.so.1, the driver's library; read-only queries)."""
+        import ctypes as C
+        import threading
+        import torch
+        nv = C.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit_v2 failed")
+        pr = torch.cuda.get_device_properties(gpu_index)
+        bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+        h = C.c_void_p()
+        if nv.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(h)) != 0:
+            raise OSError("no NVML device at " + bus.decode())
+        SM = 1  # NVML_CLOCK_SM
+        mx = C.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, SM, C.byref(mx)) != 0:
+            raise OSError("nvmlDeviceGetMaxClockInfo failed")
+        # clocks event reason bits (nvml.h): hw slowdown 0x8, sw thermal 0x20, hw thermal 0x40, sw power cap 0x4
+        bits = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
+        self.stop_ev = threading.Event()
+
+        def run():
+            clk, rs = C.c_uint(), C.c_ulonglong()
+            while not self.stop_ev.is_set():
+                if nv.nvmlDeviceGetClockInfo(h, SM, C.byref(clk)) != 0:
+                    break
+                if nv.nvmlDeviceGetCurrentClocksEventReasons(h, C.byref(rs)) != 0:
+                    rs.value = 0
+                self.samples.append((time.time(), float(clk.value), float(mx.value),
+                                     {n for n, bt in bits.items() if rs.value & bt}))
+                self.stop_ev.wait(0.002)
+        self.source = f"NVML, 2 ms, GPU {bus.decode()}"
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+        time.sleep(0.01)
+
+    def _smi_samples(self):
         self.p.terminate()
         self.p.wait(timeout=10)
         self.f.flush()
         rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
         os.unlink(self.f.name)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         parsed = []
         for r in rows:
             r = [x.strip() for x in r]
@@ -108,9 +150,21 @@ class Clocks:
                 f_sm, f_mx = float(r[2]), float(r[3])
             except (ValueError, IndexError):
                 continue
-            parsed.append((ts, f_sm, f_mx, {n for n, v in zip(names, r[6:10]) if v.lower().startswith("active")}))
+            parsed.append((ts, f_sm, f_mx, {n for n, v in zip(self.NAMES, r[6:10]) if v.lower().startswith("active")}))
+        return parsed
+
+    def stop(self, t0: float, t1: float):
+        """Summary of the samples whose timestamp lies in [t0, t1] (time.time() seconds)."""
+        if self.thread is not None:
+            self.stop_ev.set()
+            self.thread.join(timeout=5)
+            parsed = list(self.samples)
+        elif self.p is not None:
+            parsed = self._smi_samples()
+        else:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"], "samples": 0}
         inside = [p for p in parsed if t0 <= p[0] <= t1]
-        out = {}
+        out = {"source": self.source}
         if not inside:
             # a timed region shorter than the sampling period: the samples just before and after it
             before = [p for p in parsed if t0 - 0.25 <= p[0] < t0][-1:]

@@ -476,12 +476,18 @@ relnn_status relnn_profile_reset(void);
  *                          quarter, each on every other 32-row chunk); 0 = 8
  *   RELNN_TUNE_KAHAN_MIN   with RELNN_FLAG_KAHAN, the gather-sum of the aggregate-first form
  *                          compensates only rows of at least this many tuples (rows cut into chunks
- *                          always); 0 = every row (default)                                         */
+ *                          always); 0 = every row (default)
+ *   RELNN_TUNE_GROUP_SORT  group-by of a single-branch plan over unique H keys: 0 = the stable radix
+ *                          sort (groups in E order; default); 1 = by counting (a count per group key
+ *                          during the emission, one scan, an atomic scatter, each group then ordered
+ *                          by src H row), falling back to the radix sort when a tuple does not match
+ *                          or a group holds more than 4096 tuples                                   */
 #define RELNN_TUNE_SORT_BITS 0
 #define RELNN_TUNE_AGG_ROWS 1
 #define RELNN_TUNE_AGG_STAGES 2
 #define RELNN_TUNE_AGG_EPI 3
 #define RELNN_TUNE_KAHAN_MIN 4
+#define RELNN_TUNE_GROUP_SORT 5
 relnn_status relnn_tune_set(int32_t knob, int64_t value);
 relnn_status relnn_tune_get(int32_t knob, int64_t* value);
 

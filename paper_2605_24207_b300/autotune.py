@@ -10,7 +10,8 @@ a BF16 linear rule and the knobs of the kernels it runs:
   - for the aggregate-first GEMM: tile rows (RELNN_TUNE_AGG_ROWS), pipeline stages
     (RELNN_TUNE_AGG_STAGES) and epilogue warps (RELNN_TUNE_AGG_EPI: 4 or 8, two kernel instances);
   - with Kahan summation, the degree below which rows are summed plainly (RELNN_TUNE_KAHAN_MIN);
-  - for the plan, the radix digit width of the group sort (RELNN_TUNE_SORT_BITS).
+  - for the plan, the radix digit width of the group sort (RELNN_TUNE_SORT_BITS), or the counting
+    group-by instead of the radix sort (RELNN_TUNE_GROUP_SORT).
 It times forward + backward (or forward alone) on a synthetic relation of the bucket's shape and
 keeps the fastest; apply() sets the knobs and returns the flags to add.
 
@@ -32,7 +33,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "relnn_b300", "a
 
 # the library's defaults (what every knob is when nothing is tuned)
 DEFAULTS = {"form": "agg", "agg_rows": 0, "agg_stages": 0, "agg_epi": 8, "kahan_min": 0, "sort_bits": 8,
-            "tile128": False}
+            "tile128": False, "group_sort": 0}
 _FORM_FLAG = {"agg": 0, "per_tuple": R.FLAG_PER_TUPLE, "pushdown": R.FLAG_PUSHDOWN}
 
 
@@ -66,6 +67,7 @@ def apply(cfg: dict) -> int:
     R.tune_set(R.TUNE_AGG_EPI, int(c["agg_epi"]))
     R.tune_set(R.TUNE_KAHAN_MIN, int(c["kahan_min"]))
     R.tune_set(R.TUNE_SORT_BITS, int(c["sort_bits"]))
+    R.tune_set(R.TUNE_GROUP_SORT, int(c["group_sort"]))
     return _FORM_FLAG[c["form"]] | (R.FLAG_TILE128 if c["tile128"] else 0)
 
 
@@ -155,16 +157,16 @@ def tune_rule(d: int, d_out: int, n_tuples: int, n_keys: int | None = None, z_dt
         # the plan's sort digit width, timed on plan builds with the best numeric configuration
         best_ms, best = min(results, key=lambda x: x[0])
         plan_t = []
-        for bits in (7, 8, 10, 11):
-            flags = base | apply(dict(best, sort_bits=bits))
+        for bits, gsort in ((7, 0), (8, 0), (10, 0), (11, 0), (8, 1)):
+            flags = base | apply(dict(best, sort_bits=bits, group_sort=gsort))
             plan_t.append((_event_ms(lambda: R.RulePlan(h, [(s_, t_)], d, d_out, act=act, flags=flags, d_r=d_r), 3),
-                           bits))
-        plan_ms, bits = min(plan_t)
+                           bits, gsort))
+        plan_ms, bits, gsort = min(plan_t)
         # the library's own choice without tuning: aggregate-first for linear rules, else per-tuple
         default_cfg = dict(DEFAULTS) if linear else dict(DEFAULTS, form="per_tuple")
         default_ms = next((ms for ms, c in results if c == default_cfg), None)
-        choice = dict(best, sort_bits=bits, ms=best_ms, default_ms=default_ms, plan_ms=plan_ms,
-                      default_plan_ms=next((ms for ms, b in plan_t if b == DEFAULTS["sort_bits"]), None))
+        choice = dict(best, sort_bits=bits, group_sort=gsort, ms=best_ms, default_ms=default_ms, plan_ms=plan_ms,
+                      default_plan_ms=next((ms for ms, b, g in plan_t if b == DEFAULTS["sort_bits"] and g == 0), None))
     finally:
         for k, v in saved.items():
             R.tune_set(k, v)

@@ -626,13 +626,25 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 constexpr int kSegWarps = 8;
 constexpr int kSegIdx = 32 * kChunk;  // tuple indices of a warp's 32 virtual rows
 
-template <bool KAHAN, bool SINGLE>
+// MASK (the backward of a ReLU rule): every tuple's row is taken through its ReLU mask bits (the
+// forward's per-tuple mask, uint32 [m][mask_words], bit o of word o / 32 = feature o active). The
+// src pass finds a tuple's mask through perm (src order -> plan order); the dst pass (SINGLE) counts,
+// per feature, the active tuples of the run (plan positions x .. x + n - 1) and also sums its rows,
+// from the f32 table tbl_f32 (16-byte aligned rows), into this block's db partial db_part[block][w]
+// (the warps' sums added in warp order).
+template <bool KAHAN, bool SINGLE, bool MASK = false>
 __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* __restrict__ vr, int64_t nv,
                                                                  const int32_t* __restrict__ gidx,
                                                                  const uint16_t* __restrict__ tbl, int64_t tbl_rows,
                                                                  int w, int kpad, uint16_t* __restrict__ S,
-                                                                 int* status, int kahan_min) {
+                                                                 int* status, int kahan_min,
+                                                                 const uint32_t* __restrict__ mask = nullptr,
+                                                                 int mask_words = 0,
+                                                                 const int32_t* __restrict__ perm = nullptr,
+                                                                 float* __restrict__ db_part = nullptr,
+                                                                 const float* __restrict__ tbl_f32 = nullptr) {
     __shared__ int32_t s_idx[SINGLE ? 1 : kSegWarps][SINGLE ? 1 : kSegIdx];
+    __shared__ float s_db[MASK && SINGLE ? kSegWarps : 1][MASK && SINGLE ? 256 : 1];
     const int lane = threadIdx.x & 31;
     const int L = w >> 3, lsh = 31 - __clz(L), G = 32 >> lsh;
     const int grp = lane >> lsh, ch = lane & (L - 1);
@@ -641,6 +653,10 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
     const uint4* __restrict__ base = reinterpret_cast<const uint4*>(tbl) + ch;
     const int pitch = 2 * kpad, nck = kpad >> 3;
     int32_t* sidx = s_idx[SINGLE ? 0 : threadIdx.x >> 5];
+    const int mword = (8 * ch) >> 5, msh = (8 * ch) & 31;  // this lane's 8 features in the mask
+    float dbacc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dbacc[i] = 0.f;
     for (int64_t vb = warp0 * 32; vb < nv; vb += nw * 32) {
         const int4 mine = vb + lane < nv ? __ldg(vr + vb + lane) : make_int4(0, 0, -1, -1);
         const int nrows = (int)imin64(32, nv - vb);
@@ -677,12 +693,38 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
                 const int r = n > 0 ? __ldg(gidx + xo) : -1;
                 if (n > 0 && in_bounds(r, tbl_rows, status)) {
                     const uint4 u = __ldg(base + (int64_t)r * L);
-                    const float c = (float)n;
+                    float c[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) c[i] = (float)n;
+                    if (MASK) {
+                        // per feature, the run's tuples whose ReLU was active
+                        int ci[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                        for (int t = 0; t < n; ++t) {
+                            const uint32_t mw = __ldg(mask + (int64_t)(xo + t) * mask_words + mword) >> msh;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) ci[i] += (mw >> i) & 1u;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) c[i] = (float)ci[i];
+                    }
                     const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        acc[2 * i] = c * __uint_as_float(wd[i] << 16);
-                        acc[2 * i + 1] = c * __uint_as_float(wd[i] & 0xffff0000u);
+                        acc[2 * i] = c[2 * i] * __uint_as_float(wd[i] << 16);
+                        acc[2 * i + 1] = c[2 * i + 1] * __uint_as_float(wd[i] & 0xffff0000u);
+                    }
+                    if (MASK) {
+                        // db from the f32 rows (the bf16 copy feeds only the tensor cores)
+                        const float4* fr = reinterpret_cast<const float4*>(tbl_f32 + (int64_t)r * w + 8 * ch);
+                        const float4 f0 = __ldg(fr), f1 = __ldg(fr + 1);
+                        dbacc[0] += c[0] * f0.x;
+                        dbacc[1] += c[1] * f0.y;
+                        dbacc[2] += c[2] * f0.z;
+                        dbacc[3] += c[3] * f0.w;
+                        dbacc[4] += c[4] * f1.x;
+                        dbacc[5] += c[5] * f1.y;
+                        dbacc[6] += c[6] * f1.z;
+                        dbacc[7] += c[7] * f1.w;
                     }
                 }
             } else {
@@ -690,18 +732,29 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
                 for (int t0 = 0; t0 < nmax; t0 += kUnroll) {
                     const int slots = min(kUnroll, nmax - t0);  // warp-uniform
                     uint4 u[kUnroll];
+                    uint32_t mk[kUnroll];
 #pragma unroll
                     for (int q = 0; q < kUnroll; ++q) {
                         if (q >= slots) break;
                         u[q] = make_uint4(0u, 0u, 0u, 0u);
+                        mk[q] = 0u;
                         if (t0 + q < n) {
                             const int r = sidx[xo + t0 + q];
                             if (in_bounds(r, tbl_rows, status)) u[q] = __ldg(base + (int64_t)r * L);
+                            if (MASK) mk[q] = __ldg(mask + (int64_t)__ldg(perm + x0 + xo + t0 + q) * mask_words + mword) >> msh;
                         }
                     }
 #pragma unroll
                     for (int q = 0; q < kUnroll; ++q) {
                         if (q >= slots) break;
+                        if (MASK) {
+                            // a bf16 element whose ReLU was inactive becomes +0
+                            const uint32_t m8 = mk[q];
+                            u[q].x &= ((m8 & 1u) ? 0x0000ffffu : 0u) | ((m8 & 2u) ? 0xffff0000u : 0u);
+                            u[q].y &= ((m8 & 4u) ? 0x0000ffffu : 0u) | ((m8 & 8u) ? 0xffff0000u : 0u);
+                            u[q].z &= ((m8 & 16u) ? 0x0000ffffu : 0u) | ((m8 & 32u) ? 0xffff0000u : 0u);
+                            u[q].w &= ((m8 & 64u) ? 0x0000ffffu : 0u) | ((m8 & 128u) ? 0xffff0000u : 0u);
+                        }
                         add8(acc, cmp, u[q], kh);
                     }
                 }
@@ -729,14 +782,33 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
             }
         }
     }
+    if (MASK && SINGLE) {
+        // db partial of this block: groups of the warp in group order (butterfly over lanes with the
+        // same column chunk), then warps in warp order
+        for (int off = L; off < 32; off <<= 1) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dbacc[i] += __shfl_xor_sync(0xffffffffu, dbacc[i], off);
+        }
+        const int wib = threadIdx.x >> 5;
+        if (lane < L) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s_db[wib][8 * lane + i] = dbacc[i];
+        }
+        __syncthreads();
+        for (int f = threadIdx.x; f < w; f += blockDim.x) {
+            float sacc = 0.f;
+            for (int k = 0; k < kSegWarps; ++k) sacc += s_db[k][f];
+            db_part[(int64_t)blockIdx.x * w + f] = sacc;
+        }
+    }
 }
 
 // Grid of the gather-sum: every block resident (the warps stride over the 32-row batches).
-template <bool KAHAN, bool SINGLE>
+template <bool KAHAN, bool SINGLE, bool MASK = false>
 int seg_sum_grid(int64_t nv) {
     static int per_sm = 0;
     if (per_sm <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_sum_kernel<KAHAN, SINGLE>, 32 * kSegWarps, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_sum_kernel<KAHAN, SINGLE, MASK>, 32 * kSegWarps, 0) !=
             cudaSuccess) {
             (void)cudaGetLastError();
             per_sm = 0;
@@ -1079,11 +1151,24 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
 
 // ------------------------------------------------------------------------------ virtual rows
 // Sorted keys (values in [0, R)): beg[k] / end[k] = the tuple range of row k (0 / 0 when absent).
-__global__ void vr_bounds_kernel(const int32_t* __restrict__ key, int64_t m, int32_t* beg, int32_t* end) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t k = key[t];
-        if (t == 0 || key[t - 1] != k) beg[k] = (int32_t)t;
-        if (t == m - 1 || key[t + 1] != k) end[k] = (int32_t)(t + 1);
+// One thread per 4 tuples, all loads issued before the first store (one memory round trip).
+__global__ void vr_bounds_kernel(const int32_t* __restrict__ key, int64_t m, int32_t* __restrict__ beg,
+                                 int32_t* __restrict__ end) {
+    const int64_t t0 = (blockIdx.x * (int64_t)blockDim.x) * 4 + threadIdx.x;
+    int32_t k[4], kp[4], kn[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t t = t0 + (int64_t)i * blockDim.x;
+        k[i] = t < m ? __ldg(key + t) : 0;
+        kp[i] = (t < m && t > 0) ? __ldg(key + t - 1) : ~k[i];
+        kn[i] = t + 1 < m ? __ldg(key + t + 1) : ~k[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t t = t0 + (int64_t)i * blockDim.x;
+        if (t >= m) continue;
+        if (kp[i] != k[i]) beg[k[i]] = (int32_t)t;
+        if (kn[i] != k[i]) end[k[i]] = (int32_t)(t + 1);
     }
 }
 
@@ -1111,7 +1196,7 @@ __global__ void vr_runs_kernel(const int32_t* __restrict__ key, int64_t m, const
 // Chunks per row (every row of a sorted list gets one, empty or not), chunk partials per row (rows
 // of one chunk need none), and the split flag.
 __global__ void vr_count_kernel(const int32_t* __restrict__ beg, const int32_t* __restrict__ end, int64_t R,
-                                int32_t* nch, int32_t* npart, int32_t* split, int32_t* cnt_out) {
+                                int32_t* nch, int32_t* npart, int32_t* split, int32_t* cnt_out, int32_t* long_rows) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t cnt = end[r] - beg[r];
         if (cnt_out) cnt_out[r] = cnt;
@@ -1119,6 +1204,7 @@ __global__ void vr_count_kernel(const int32_t* __restrict__ beg, const int32_t* 
         nch[r] = c;
         npart[r] = c > 1 ? c : 0;
         split[r] = c > 1 ? 1 : 0;
+        if (c > kFixChunk) *long_rows = 1;  // a row the fix-up cuts again (host-built jobs)
     }
 }
 
@@ -1313,11 +1399,13 @@ __global__ void __launch_bounds__(256) dout_prep_kernel(const float* __restrict_
     }
 }
 
-// db_b[f] = sum over blocks (in order, compensated) of the partials.
+// db_b[f] = sum over blocks (in order, compensated) of the partials ([block][branch][d_out], or
+// [block][d_out] for b = -1).
 __global__ void db_reduce_kernel(const float* __restrict__ part, int blocks, int d_out, int b, float* db) {
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d_out; f += gridDim.x * blockDim.x) {
         float s = 0.f, c = 0.f;
-        for (int k = 0; k < blocks; ++k) kahan_add(s, c, part[((int64_t)k * kDbBranches + b) * d_out + f]);
+        for (int k = 0; k < blocks; ++k)
+            kahan_add(s, c, part[(b < 0 ? (int64_t)k : ((int64_t)k * kDbBranches + b)) * d_out + f]);
         db[f] = s - c;
     }
 }
@@ -1389,35 +1477,45 @@ relnn_status ensure_vrows(VRows& V, const int32_t* key, int64_t m, int64_t R, bo
     if (sorted) {
         RELNN_CUDA(cudaMemsetAsync(beg.p, 0, sizeof(int32_t) * r1, st));
         RELNN_CUDA(cudaMemsetAsync(end.p, 0, sizeof(int32_t) * r1, st));
-        if (m > 0) { vr_bounds_kernel<<<grid_for(m), 256, 0, st>>>(key, m, beg.as<int32_t>(), end.as<int32_t>()); note_launch(); }
+        if (m > 0) { vr_bounds_kernel<<<(unsigned)ceil_div(m, 1024), 256, 0, st>>>(key, m, beg.as<int32_t>(), end.as<int32_t>()); note_launch(); }
     } else {
         RELNN_TRY(rkey.alloc_tmp(sizeof(int32_t) * r1, st));
         if (m > 0) { vr_runs_kernel<<<grid_for(m), 256, 0, st>>>(key, m, flag.as<int32_t>(), beg.as<int32_t>(), end.as<int32_t>(),
                                                                rkey.as<int32_t>()); note_launch(); }
     }
     DevBuf cnts;  // nch | npart | split, each rows + 1 (exclusive scans in place), then the 3 totals
+                  // and the long-row flag
     RELNN_TRY(cnts.alloc_tmp(sizeof(int32_t) * (3 * (rows + 1) + 4), st));
     int32_t* nch = cnts.as<int32_t>();
     int32_t* npart = nch + rows + 1;
     int32_t* split = npart + rows + 1;
     int32_t* tot_d = split + rows + 1;
+    RELNN_CUDA(cudaMemsetAsync(tot_d + 3, 0, sizeof(int32_t), st));
     if (sorted) RELNN_TRY(V.cnt.alloc_nosync(sizeof(int32_t) * r1, st));
     RELNN_TRY(V.vr.alloc_nosync(sizeof(int4) * nv_max, st));
-    DevBuf splits;
-    RELNN_TRY(splits.alloc_tmp(sizeof(int4) * ns_max, st));
+    // the split rows {row, first partial, chunks, -1}: with no row above kFixChunk chunks they are
+    // the fix-up's jobs as they stand (no host pass), so they are written into V.fix1 directly
+    RELNN_TRY(V.fix1.alloc_nosync(sizeof(int4) * ns_max, st));
     if (rows > 0) { vr_count_kernel<<<grid_for(rows), 256, 0, st>>>(beg.as<int32_t>(), end.as<int32_t>(), rows, nch, npart, split,
-                                                                   sorted ? V.cnt.as<int32_t>() : nullptr); note_launch(); }
+                                                                   sorted ? V.cnt.as<int32_t>() : nullptr, tot_d + 3); note_launch(); }
     RELNN_TRY(exclusive_scan<int32_t>(nch, nch, rows, tot_d, st));
     RELNN_TRY(exclusive_scan<int32_t>(npart, npart, rows, tot_d + 1, st));
     RELNN_TRY(exclusive_scan<int32_t>(split, split, rows, tot_d + 2, st));
     if (rows > 0) { vr_fill_kernel<<<grid_for(rows), 256, 0, st>>>(beg.as<int32_t>(), end.as<int32_t>(),
                                                                   sorted ? nullptr : rkey.as<int32_t>(), rows, nch, npart,
-                                                                  split, V.vr.as<int4>(), splits.as<int4>()); note_launch(); }
+                                                                  split, V.vr.as<int4>(), V.fix1.as<int4>()); note_launch(); }
     RELNN_CUDA(cudaGetLastError());
-    int32_t tot[3] = {0, 0, 0};
+    int32_t tot[4] = {0, 0, 0, 0};
     RELNN_CUDA(cudaMemcpyAsync(tot, tot_d, sizeof(tot), cudaMemcpyDeviceToHost, st));
     RELNN_CUDA(cudaStreamSynchronize(st));
-    RELNN_TRY(make_fix_jobs(V, splits.as<int4>(), tot[2], st));
+    if (tot[3]) {
+        // some row has more than kFixChunk chunks: two-level jobs built on the host from the splits
+        DevBuf splits = std::move(V.fix1);
+        RELNN_TRY(make_fix_jobs(V, splits.as<int4>(), tot[2], st));
+    } else {
+        V.n_fix1 = tot[2];
+        V.n_fix2 = V.n_l2 = 0;
+    }
     V.n_parts = tot[1];
     V.nv = tot[0];
     return RELNN_OK;
@@ -1553,9 +1651,11 @@ AggCfg fwd_cfg(const Plan& p) {
 
 }  // namespace
 
-bool agg_forward_ok(const Plan& p, const CallIO& io, const float* out) {
+namespace {
+// The aggregate-first form's conditions other than the activation.
+bool agg_shape_ok(const Plan& p, const CallIO& io, const float* out) {
     if (!aligned16(out)) return false;  // the fix-up adds partial rows as float4
-    if (!p.bf16 || p.identity || p.act != RELNN_ACT_NONE) return false;
+    if (!p.bf16 || p.identity) return false;
     if (p.flags & (RELNN_FLAG_MAX | RELNN_FLAG_PUSHDOWN | RELNN_FLAG_PER_TUPLE | kPlanDense)) return false;
     if (p.Hx || p.dense_out || p.acc_out) return false;
     for (auto& b : p.br)
@@ -1565,8 +1665,22 @@ bool agg_forward_ok(const Plan& p, const CallIO& io, const float* out) {
     return aligned16(io.z) && fwd_cfg(p).N > 0;
 }
 
+// A ReLU rule's backward runs aggregate-first when every branch kept the forward's ReLU mask and
+// the rule has the dst part (the dst pass also yields db).
+bool relu_masked(const Plan& p) {
+    if (p.act != RELNN_ACT_RELU || !p.concat_dst || (p.flags & RELNN_FLAG_MAX)) return false;
+    for (auto& b : p.br)
+        if (b.m > 0 && !b.relu_mask.p) return false;
+    return true;
+}
+}  // namespace
+
+bool agg_forward_ok(const Plan& p, const CallIO& io, const float* out) {
+    return p.act == RELNN_ACT_NONE && agg_shape_ok(p, io, out);
+}
+
 bool agg_backward_ok(const Plan& p, const CallIO& io, const GradIO& g) {
-    if (!agg_forward_ok(p, io, g.dz)) return false;
+    if (!(p.act == RELNN_ACT_NONE || relu_masked(p)) || !agg_shape_ok(p, io, g.dz)) return false;
     if (!pow2_in(p.d_out, 8, 256) || p.d % 32 != 0) return false;
     return g.dout != nullptr && aligned16(g.dout) &&
            gemm_config((p.d_out + 63) / 64, (p.d + 63) / 64, (p.d + 127) / 128, true, (p.d_out + 127) / 128, p.d).N > 0;
@@ -1755,7 +1869,13 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
     // scratch: A (bf16), the CTAs' dW partials, the blocks' db partials
     const size_t a_elems = (size_t)rows_pad * cols;
     const size_t a_bytes = (a_elems * 2 + 255) & ~(size_t)255;
-    const size_t dwp = (size_t)grid_max * p.d_out * p.d, dbp = (size_t)pblocks * kDbBranches * p.d_out;
+    // ReLU rule: dY_t = dOut[seg_t] masked by the forward's ReLU mask; db then comes from the masked
+    // dst pass (its blocks' partials), not from the tuple counts
+    const bool masked = p.act == RELNN_ACT_RELU;
+    const int mask_words = ((p.d_out + 127) / 128) * 4;
+    const int64_t ss_max = (int64_t)num_sms() * 8;  // blocks of a gather-sum launch, at most
+    const size_t dwp = (size_t)grid_max * p.d_out * p.d,
+                 dbp = (size_t)std::max<int64_t>(pblocks * kDbBranches, masked ? ss_max : 0) * p.d_out;
     RELNN_TRY(p.scratch.alloc(a_bytes + sizeof(float) * (dwp + dbp)));
     uint16_t* abuf = p.scratch.as<uint16_t>();
     float* dw_part = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + a_bytes);
@@ -1773,7 +1893,7 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             for (int k = 0; k < cs.n; ++k) cs.c[k] = p.br[b0 + k].vr_out.cnt.as<int32_t>();
             { dout_prep_kernel<<<pblocks, 256, 0, st>>>(g.dout, p.n_out, p.d_out, cs, rpb, p.doutbf.as<uint16_t>(),
                                                        db_part); note_launch(); }
-            for (int k = 0; k < cs.n; ++k) {
+            for (int k = 0; k < cs.n && !masked; ++k) {
                 float* db = g.db.size() > b0 + k ? g.db[b0 + k] : nullptr;
                 if (db) { db_reduce_kernel<<<grid_for(p.d_out, 128), 128, 0, st>>>(db_part, pblocks, p.d_out, k, db); note_launch(); }
             }
@@ -1824,15 +1944,32 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             // G rows: sums of dOut rows per virtual row (src order: a row per tuple; dst order: one
             // row times the run's length), as bf16 pairs
             uint16_t* S = p.sbuf.as<uint16_t>();
-            const int ss_blocks = pass == 1 ? seg_sum_grid<false, true>(V.nv)
-                                  : p.kahan ? seg_sum_grid<true, false>(V.nv) : seg_sum_grid<false, false>(V.nv);
+            const int ss_blocks =
+                (int)std::min<int64_t>(ss_max, masked ? (pass == 1 ? seg_sum_grid<false, true, true>(V.nv)
+                                                        : p.kahan ? seg_sum_grid<true, false, true>(V.nv)
+                                                                  : seg_sum_grid<false, false, true>(V.nv))
+                                                      : (pass == 1 ? seg_sum_grid<false, true>(V.nv)
+                                                         : p.kahan ? seg_sum_grid<true, false>(V.nv)
+                                                                   : seg_sum_grid<false, false>(V.nv)));
             const int32_t* gi = pass == 0 ? b.seg_src.as<int32_t>() : b.seg.as<int32_t>();
             const int kmin = (int)tune_get(RELNN_TUNE_KAHAN_MIN);
             {
                 ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
                 const uint16_t* tb = p.doutbf.as<uint16_t>();
                 int* stw = p.status.as<int>();
-                if (pass == 0) {
+                const uint32_t* mk = masked ? b.relu_mask.as<uint32_t>() : nullptr;
+                if (masked && pass == 0) {
+                    if (p.kahan) seg_sum_kernel<true, false, true><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
+                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, kmin, mk, mask_words,
+                        b.src_perm.as<int32_t>());
+                    else seg_sum_kernel<false, false, true><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
+                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, kmin, mk, mask_words,
+                        b.src_perm.as<int32_t>());
+                } else if (masked) {
+                    seg_sum_kernel<false, true, true><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
+                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, 0, mk, mask_words, nullptr,
+                        db_part, g.dout);
+                } else if (pass == 0) {
                     if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
                                                                                         p.d_out, kpad_g, S, stw, kmin);
                     else seg_sum_kernel<false, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
@@ -1845,6 +1982,11 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
                 prof_end(pt, st);
             }
             RELNN_CUDA(cudaGetLastError());
+            if (masked && pass == 1) {
+                // db of this branch: the masked dst pass's block partials, added in block order
+                float* db = g.db.size() > i ? g.db[i] : nullptr;
+                if (db) { db_reduce_kernel<<<grid_for(p.d_out, 128), 128, 0, st>>>(db_part, ss_blocks, p.d_out, -1, db); note_launch(); }
+            }
             { pack_a_bwd_kernel<<<grid_for((int64_t)a_elems), 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, col0, p.d,
                                                                            rows_pad, cols, abuf); note_launch(); }
             CUtensorMap smap;

@@ -155,13 +155,14 @@ __global__ void dense_slots_kernel(const int32_t* cnt, const int64_t* excl, int6
 // Row i goes to its key's run (unique keys: the run's only position; else the next free one, in
 // no particular order until dense_fix_kernel sorts the run).
 __global__ void dense_place_kernel(const void* keys, int64_t n, int kt, int64_t kmin, const int64_t* excl,
-                                   int32_t* cursor, int32_t* rows_sorted, int32_t* uid_of_pos) {
+                                   int32_t* cursor, int32_t* rows_sorted, int32_t* uid_of_pos, int32_t* slot_rows) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t s = (uint64_t)load_key(keys, kt, i) - (uint64_t)kmin;
         const int64_t e = excl[s];
         const int32_t pos = (int32_t)(uint32_t)e + (cursor ? atomicAdd(&cursor[s], 1) : 0);
         rows_sorted[pos] = (int32_t)i;
         uid_of_pos[pos] = (int32_t)(e >> 32);
+        if (slot_rows) slot_rows[s] = (int32_t)i;  // unique keys only (one row per slot)
     }
 }
 
@@ -258,7 +259,7 @@ namespace {
 // The dense build over S = span + 1 slots; *done = false (nothing changed) when a key repeats more
 // than kDenseRun times, which the sort path handles.
 relnn_status dense_build(JoinTable& jt, const void* keys, int64_t n, int kt, int64_t kmin, int64_t S, bool* done,
-                         cudaStream_t st) {
+                         bool sync_end, cudaStream_t st) {
     *done = false;
     DevBuf cnt, packed;
     RELNN_TRY(cnt.alloc_tmp(sizeof(int32_t) * (S + 1), st));
@@ -288,22 +289,25 @@ relnn_status dense_build(JoinTable& jt, const void* keys, int64_t n, int kt, int
                                              jt.ukeys.as<int64_t>()); note_launch(); }
     const bool dup = U < n;
     if (dup) RELNN_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * S, st));
+    else RELNN_TRY(jt.slot_rows.alloc_nosync(sizeof(int32_t) * S, st));  // an empty slot's entry is garbage
     { dense_place_kernel<<<gn, 256, 0, st>>>(keys, n, kt, kmin, packed.as<int64_t>(), dup ? cnt.as<int32_t>() : nullptr,
-                                             jt.rows_sorted.as<int32_t>(), jt.uid_of_pos.as<int32_t>()); note_launch(); }
+                                             jt.rows_sorted.as<int32_t>(), jt.uid_of_pos.as<int32_t>(),
+                                             dup ? nullptr : jt.slot_rows.as<int32_t>()); note_launch(); }
     if (dup) { dense_fix_kernel<<<grid_for(U), 256, 0, st>>>(jt.run_start.as<int32_t>(), U, jt.rows_sorted.as<int32_t>()); note_launch(); }
     RELNN_CUDA(cudaGetLastError());
-    RELNN_CUDA(cudaStreamSynchronize(st));
+    if (sync_end) RELNN_CUDA(cudaStreamSynchronize(st));
     *done = true;
     return RELNN_OK;
 }
 
 }  // namespace
 
-relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt, cudaStream_t st) {
+relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt, cudaStream_t st, bool sync_end) {
     RELNN_CHECK_ARG(n >= 0 && n < (1ll << 31) - 1, "join build: n out of range");
     RELNN_CHECK_ARG(n == 0 || keys, "join build: null keys");
     jt.kt = kt;
     jt.n = n;
+    jt.slot_rows.release();  // only a dense build over unique keys sets it
     RELNN_TRY(jt.status.alloc_nosync(sizeof(int) * kStatusInts, st));
     RELNN_CUDA(cudaMemsetAsync(jt.status.p, 0, sizeof(int) * kStatusInts, st));
     RELNN_TRY(jt.rows_sorted.alloc_nosync(sizeof(int32_t) * std::max<int64_t>(n, 1), st));
@@ -328,7 +332,7 @@ relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt
     const uint64_t span = ((uint64_t)kmax ^ 0x8000000000000000ull) - omin;
     if (span < (uint64_t)std::max<int64_t>(4 * n, 1 << 20)) {
         bool done = false;
-        RELNN_TRY(dense_build(jt, keys, n, kt, kmin, (int64_t)span + 1, &done, st));
+        RELNN_TRY(dense_build(jt, keys, n, kt, kmin, (int64_t)span + 1, &done, sync_end, st));
         if (done) return RELNN_OK;
     }
     const int nbits = bit_length(span);

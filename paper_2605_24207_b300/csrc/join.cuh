@@ -8,6 +8,8 @@
 //   lookup           direct-address table int32[max-min+1] when the key range is small, else an
 //                    open-addressing hash table (linear probing, load <= 1/2) of int64 keys and int32
 //                    distinct-key indices.
+//   slot_rows        with the direct table and unique keys (dense build): the H row of each slot,
+//                    so a probe that needs the row takes one lookup instead of two.
 #pragma once
 
 #include "common.cuh"
@@ -23,6 +25,7 @@ struct JoinView {
     uint64_t mask;             // hash mode: capacity - 1
     const int64_t* slot_keys;  // hash mode
     const int32_t* slot_vals;  // distinct-key index per slot (-1 = empty)
+    const int32_t* slot_rows;  // direct mode, unique keys: H row per slot (else null)
     const int32_t* rows_sorted;
     const int32_t* run_start;
     const int32_t* uid_of_pos;
@@ -51,7 +54,7 @@ struct JoinTable {
     int mode = 0;
     int64_t key_min = 0, key_max = 0, direct_size = 0;
     uint64_t cap = 0;
-    DevBuf rows_sorted, run_start, uid_of_pos, ukeys, slot_keys, slot_vals, status;
+    DevBuf rows_sorted, run_start, uid_of_pos, ukeys, slot_keys, slot_vals, slot_rows, status;
 
     JoinView view() const {
         JoinView v;
@@ -61,6 +64,7 @@ struct JoinTable {
         v.mask = cap ? cap - 1 : 0;
         v.slot_keys = slot_keys.as<int64_t>();
         v.slot_vals = slot_vals.as<int32_t>();
+        v.slot_rows = slot_rows.as<int32_t>();
         v.rows_sorted = rows_sorted.as<int32_t>();
         v.run_start = run_start.as<int32_t>();
         v.uid_of_pos = uid_of_pos.as<int32_t>();
@@ -68,8 +72,11 @@ struct JoinTable {
     }
 };
 
-// Builds `jt` over keys[0..n) (device, key type kt). Synchronises `st`.
-relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt, cudaStream_t st);
+// Builds `jt` over keys[0..n) (device, key type kt). Synchronises `st` (reading sizes back); with
+// sync_end = false the last kernels of the dense build are left in flight on `st` (the caller's
+// later work on `st` is ordered after them).
+relnn_status join_table_build(JoinTable& jt, const void* keys, int64_t n, int kt, cudaStream_t st,
+                              bool sync_end = true);
 
 // Min and max of a key column (device -> host, synchronises `st`). Returns false if n == 0.
 relnn_status key_range(const void* keys, int64_t n, int kt, int64_t* kmin, int64_t* kmax,

@@ -12,6 +12,10 @@ namespace {
 
 // One thread per kIlp items, no grid-stride loop.
 constexpr int kIlp = 4;
+// Counting group-by: the largest group it orders itself (a larger one sends the plan to the radix
+// sort) and the largest group one lane orders (larger ones: a block each).
+constexpr int kGroupBig = 4096;
+constexpr int kGroupLane = 32;
 inline unsigned ilp_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, ceil_div(n, 256 * kIlp)); }
 
 inline int grid_for(int64_t n, int threads = 256) {
@@ -254,7 +258,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
 // is not zero, the caller runs emit_unique_kernel over the same outputs.
 template <class K, class V>
 __global__ void emit_all_kernel(JoinView j, const void* src, const void* dst, int64_t T, int kt, bool join_dst,
-                                uint64_t omin, unsigned long long* misses, K* t_key, V* t_val) {
+                                uint64_t omin, unsigned long long* misses, K* t_key, V* t_val, int32_t* cnt,
+                                unsigned* big) {
     const int64_t e0 = (blockIdx.x * (int64_t)blockDim.x) * kIlp + threadIdx.x;
     int64_t ks[kIlp], kd[kIlp];
 #pragma unroll
@@ -263,20 +268,33 @@ __global__ void emit_all_kernel(JoinView j, const void* src, const void* dst, in
         ks[k] = e < T ? load_key(src, kt, e) : 0;
         kd[k] = e < T ? load_key(dst, kt, e) : 0;
     }
-    int32_t a[kIlp], b[kIlp];
+    int32_t a[kIlp], b[kIlp], hs[kIlp];
+    if (j.slot_rows) {
+        // direct table with unique keys: the src H row in one lookup (the row read for a slot that
+        // holds no key is garbage, but its slot_vals entry is -1, so the tuple counts as a miss and
+        // the caller re-emits everything with emit_unique_kernel)
 #pragma unroll
-    for (int k = 0; k < kIlp; ++k) {
-        a[k] = j.lookup(ks[k]);
-        b[k] = join_dst ? j.lookup(kd[k]) : 0;
+        for (int k = 0; k < kIlp; ++k) {
+            const uint64_t os = (uint64_t)ks[k] - (uint64_t)j.key_min, od = (uint64_t)kd[k] - (uint64_t)j.key_min;
+            const bool ins = os < (uint64_t)j.direct_size;
+            a[k] = ins ? __ldg(j.slot_vals + os) : -1;
+            hs[k] = ins ? __ldg(j.slot_rows + os) : 0;
+            b[k] = !join_dst ? 0 : (od < (uint64_t)j.direct_size ? __ldg(j.slot_vals + od) : -1);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            a[k] = j.lookup(ks[k]);
+            b[k] = join_dst ? j.lookup(kd[k]) : 0;
+        }
     }
-    int32_t hs[kIlp];
     unsigned miss = 0;
 #pragma unroll
     for (int k = 0; k < kIlp; ++k) {
         const bool in = e0 + (int64_t)k * blockDim.x < T;
         const bool ok = a[k] >= 0 && b[k] >= 0;
         miss += (in && !ok) ? 1u : 0u;
-        hs[k] = in && ok ? __ldg(j.rows_sorted + a[k]) : 0;
+        if (!j.slot_rows) hs[k] = in && ok ? __ldg(j.rows_sorted + a[k]) : 0;
     }
 #pragma unroll
     for (int k = 0; k < kIlp; ++k) {
@@ -289,6 +307,187 @@ __global__ void emit_all_kernel(JoinView j, const void* src, const void* dst, in
     }
     miss = __reduce_add_sync(0xffffffffu, miss);
     if ((threadIdx.x & 31) == 0 && miss) atomicAdd(misses, (unsigned long long)miss);
+    if (cnt) {
+        // tuples per group key (the counting group-by); lanes holding the same key add once, and
+        // a count passing kGroupBig is flagged (that group-by then takes the radix sort)
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            const bool in = e0 + (int64_t)k * blockDim.x < T && a[k] >= 0 && b[k] >= 0;
+            const int key = in ? (int)b[k] : -1;
+            const unsigned mm = __match_any_sync(0xffffffffu, key);
+            if (in && lane == __ffs(mm) - 1) {
+                const int c = __popc(mm);
+                if (atomicAdd(&cnt[key], c) + c > kGroupBig) atomicOr(big, 1u);
+            }
+        }
+    }
+}
+
+// ---- counting group-by (one branch, unique H keys, E rows not carried): the emission counted the
+// tuples per group key b; one exclusive scan of packed (count, present) pairs gives each group's first
+// position and output row; an atomic scatter places every tuple's (hs, hd, seg) in its group; each
+// group is then sorted by hs, which makes the order, and so every later sum, the same run to run
+// (tuples with equal hs are equal rows, so their mutual order does not matter).
+__global__ void group_pack_kernel(const int32_t* __restrict__ cnt, int64_t n, int64_t* __restrict__ packed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cnt[i];
+        packed[i] = (int64_t)c | ((int64_t)(c > 0) << 32);
+    }
+}
+
+// Per group key b: its scatter cursor (first position) and, if present, its output key.
+__global__ void group_heads_kernel(const int32_t* __restrict__ cnt, const int64_t* __restrict__ excl, int64_t n,
+                                   const int64_t* __restrict__ ukeys, int32_t* __restrict__ cur,
+                                   int64_t* __restrict__ out_keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = excl[i];
+        cur[i] = (int32_t)(uint32_t)e;
+        if (cnt[i] > 0) out_keys[e >> 32] = ukeys[i];
+    }
+}
+
+// Tuple i (E order) to the next free position of its group (lanes with the same key take one
+// atomic and consecutive positions); writes its src H row there. (One scattered 4-byte store per
+// tuple into one array that fits in L2; the group's dst H row and output row are written per group,
+// contiguously, by the sort kernels.)
+__global__ void group_scatter_kernel(const uint32_t* __restrict__ key, const int32_t* __restrict__ val, int64_t m,
+                                     int32_t* __restrict__ cur, int32_t* __restrict__ hs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x) * kIlp + threadIdx.x;
+    uint32_t k[kIlp];
+    int32_t v[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        k[u] = i < m ? __ldg(key + i) : 0xffffffffu;
+        v[u] = i < m ? __ldg(val + i) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+        const bool in = i0 + (int64_t)u * blockDim.x < m;
+        const unsigned mm = __match_any_sync(0xffffffffu, k[u]);
+        const int leader = __ffs(mm) - 1;
+        int base = 0;
+        if (in && lane == leader) base = atomicAdd(&cur[k[u]], __popc(mm));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (in) hs[base + __popc(mm & ((1u << lane) - 1u))] = v[u];
+    }
+}
+
+// Groups of at most kGroupLane tuples: a warp takes 32 consecutive group keys, one per lane. When
+// their tuples fit (at most 32 x 32), the warp's range of hs is loaded into shared memory with
+// coalesced loads, each lane sorts its group's slice (insertion sort), and the range is stored back
+// coalesced; otherwise each lane sorts its group in place. Each lane then writes its group's dst H
+// row and output row over the group's positions. Larger groups are listed for
+// group_sort_block_kernel (which writes their hd / seg as well).
+__global__ void __launch_bounds__(256) group_sort_warp_kernel(const int32_t* __restrict__ cnt,
+                                                              const int64_t* __restrict__ excl, int64_t n,
+                                                              const int32_t* __restrict__ rows_sorted,
+                                                              int32_t* __restrict__ hs, int32_t* __restrict__ hd,
+                                                              int32_t* __restrict__ seg, int32_t* __restrict__ big_list,
+                                                              int* __restrict__ n_big) {
+    __shared__ int32_t sm[8][kGroupLane * 32];
+    const int lane = threadIdx.x & 31;
+    int32_t* buf = sm[threadIdx.x >> 5];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w * 32 < n; w += nw) {
+        const int64_t g = w * 32 + lane;
+        const int c = g < n ? cnt[g] : 0;
+        const int64_t e = g < n ? excl[g] : 0;
+        const int64_t s = (int64_t)(uint32_t)e;
+        const int32_t orow = (int32_t)(e >> 32);
+        const bool big = c > kGroupLane;
+        if (big) big_list[atomicAdd(n_big, 1)] = (int32_t)g;
+        // the warp's range of positions: from the first present group's start to the last one's end
+        const int64_t lo = __reduce_min_sync(0xffffffffu, c > 0 ? (unsigned)s : 0xffffffffu);
+        const int64_t hi = __reduce_max_sync(0xffffffffu, c > 0 ? (unsigned)(s + c) : 0u);
+        const bool staged = !__any_sync(0xffffffffu, big) && hi > lo && hi - lo <= kGroupLane * 32;
+        if (staged) {
+            const int len = (int)(hi - lo);
+            for (int i = lane; i < len; i += 32) buf[i] = hs[lo + i];
+            __syncwarp();
+            int32_t* col = buf + (s - lo);
+            for (int j = 1; j < c; ++j) {
+                const int32_t x = col[j];
+                int i = j - 1;
+                while (i >= 0 && col[i] > x) {
+                    col[i + 1] = col[i];
+                    --i;
+                }
+                col[i + 1] = x;
+            }
+            __syncwarp();
+            for (int i = lane; i < len; i += 32) hs[lo + i] = buf[i];
+            __syncwarp();
+        } else if (!big && c > 1) {
+            int32_t* col = buf;  // lane-private column: element j at j * 32 + lane
+            for (int j = 0; j < c; ++j) col[j * 32 + lane] = hs[s + j];
+            for (int j = 1; j < c; ++j) {
+                const int32_t x = col[j * 32 + lane];
+                int i = j - 1;
+                while (i >= 0 && col[i * 32 + lane] > x) {
+                    col[(i + 1) * 32 + lane] = col[i * 32 + lane];
+                    --i;
+                }
+                col[(i + 1) * 32 + lane] = x;
+            }
+            for (int j = 0; j < c; ++j) hs[s + j] = col[j * 32 + lane];
+        }
+        __syncwarp();
+        if (!big && c > 0) {
+            const int32_t r = rows_sorted[g];
+            for (int j = 0; j < c; ++j) {
+                hd[s + j] = r;
+                seg[s + j] = orow;
+            }
+        }
+    }
+}
+
+// Listed groups (kGroupLane < count <= kGroupBig), one block each at a time: bitonic sort in
+// shared memory (padded with INT_MAX to a power of two).
+__global__ void __launch_bounds__(256) group_sort_block_kernel(const int32_t* __restrict__ cnt,
+                                                               const int64_t* __restrict__ excl,
+                                                               const int32_t* __restrict__ big_list,
+                                                               const int* __restrict__ n_big,
+                                                               const int32_t* __restrict__ rows_sorted,
+                                                               int32_t* __restrict__ hs, int32_t* __restrict__ hd,
+                                                               int32_t* __restrict__ seg) {
+    __shared__ int32_t sm[kGroupBig];
+    const int nb = *n_big;
+    for (int li = blockIdx.x; li < nb; li += gridDim.x) {
+        const int32_t g = big_list[li];
+        const int c = cnt[g];
+        const int64_t s = (int64_t)(uint32_t)excl[g];
+        int P = 1;
+        while (P < c) P <<= 1;
+        __syncthreads();
+        for (int j = threadIdx.x; j < P; j += blockDim.x) sm[j] = j < c ? hs[s + j] : INT_MAX;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    const int l = i ^ jj;
+                    if (l > i) {
+                        const int32_t a = sm[i], b = sm[l];
+                        const bool up = (i & k) == 0;
+                        if ((a > b) == up) {
+                            sm[i] = b;
+                            sm[l] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const int32_t r = rows_sorted[g], orow = (int32_t)(excl[g] >> 32);
+        for (int j = threadIdx.x; j < c; j += blockDim.x) {
+            hs[s + j] = sm[j];
+            hd[s + j] = r;
+            seg[s + j] = orow;
+        }
+    }
 }
 
 // Splits (src H row << 32 | E row) payloads into hs / er.
@@ -398,6 +597,11 @@ struct Tmp {
     bool pair = false;    // 64-bit payloads (the E row rides along)
     bool in_tmp = false;  // the sorted pairs are in key_tmp / val_tmp
     uint64_t omin = 0;
+    // counting group-by: requested (eligible plan), taken (every tuple matched, no group above
+    // kGroupBig); the counts per group key (+ the flag word) and the scanned (count, present) pairs,
+    // whose total (matched tuples | output rows << 32) is read with the plan's final synchronisation
+    bool want_count = false, counted = false;
+    DevBuf cnt, gpacked;
     template <class K>
     const K* keys() const { return in_tmp ? key_tmp.as<K>() : key.as<K>(); }
     DevBuf& sorted_val() { return in_tmp ? val_tmp : val; }
@@ -429,17 +633,24 @@ relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M
         RELNN_TRY(t.val_tmp.alloc_tmp(sizeof(V) * cap, st));
         bool all_matched = false;
         if (T > 0 && filters_of(bd).n == 0) {
-            DevBuf miss;
-            RELNN_TRY(miss.alloc_tmp(sizeof(unsigned long long), st));
-            RELNN_CUDA(cudaMemsetAsync(miss.p, 0, sizeof(unsigned long long), st));
+            DevBuf miss;  // misses (u64) | the big-group flag (u32)
+            RELNN_TRY(miss.alloc_tmp(2 * sizeof(unsigned long long), st));
+            RELNN_CUDA(cudaMemsetAsync(miss.p, 0, 2 * sizeof(unsigned long long), st));
+            unsigned* big = reinterpret_cast<unsigned*>(miss.as<unsigned long long>() + 1);
+            if (t.want_count) {
+                RELNN_TRY(t.cnt.alloc_tmp(sizeof(int32_t) * std::max<int64_t>(p.n_h, 1), st));
+                RELNN_CUDA(cudaMemsetAsync(t.cnt.p, 0, sizeof(int32_t) * std::max<int64_t>(p.n_h, 1), st));
+            }
             { emit_all_kernel<K, V><<<ilp_grid(T), 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst, t.omin,
-                                                              miss.as<unsigned long long>(), t.key.as<K>(), t.val.as<V>()); note_launch(); }
+                                                              miss.as<unsigned long long>(), t.key.as<K>(), t.val.as<V>(),
+                                                              t.want_count ? t.cnt.as<int32_t>() : nullptr, big); note_launch(); }
             RELNN_CUDA(cudaGetLastError());
-            unsigned long long mu = 0;
-            RELNN_CUDA(cudaMemcpyAsync(&mu, miss.p, sizeof(mu), cudaMemcpyDeviceToHost, st));
+            unsigned long long mu[2] = {0, 0};
+            RELNN_CUDA(cudaMemcpyAsync(mu, miss.p, sizeof(mu), cudaMemcpyDeviceToHost, st));
             RELNN_CUDA(cudaStreamSynchronize(st));
-            all_matched = mu == 0;
+            all_matched = mu[0] == 0;
             if (all_matched) M = T;
+            t.counted = t.want_count && all_matched && (unsigned)mu[1] == 0;
         }
         if (T > 0 && !all_matched) {
             const int64_t n_tiles = ceil_div(T, kEmitTile);
@@ -494,9 +705,42 @@ relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M
 template <class K, class V>
 relnn_status emit_and_sort(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M, int nbits, cudaStream_t st) {
     RELNN_TRY((emit_pairs<K, V>(p, bd, t, M, st)));
-    if (*M >= (1ll << 31) - 1) return RELNN_OK;
+    if (*M >= (1ll << 31) - 1 || t.counted) return RELNN_OK;  // counted: grouped by group_by_counting
     return radix_sort_pairs<K, V>(t.key.as<K>(), t.val.as<V>(), t.key_tmp.as<K>(), t.val_tmp.as<V>(), *M, nbits, st,
                                   &t.in_tmp);
+}
+
+// The counting group-by of an emitted branch (t.counted): hs, hd and seg of every tuple in output
+// order, the output keys, and in t.gpacked the scanned (count, present) pairs.
+relnn_status group_by_counting(Plan& p, BranchPlan& b, Tmp& t, cudaStream_t st) {
+    const JoinTable& HT = p.Ht();
+    const int64_t n = p.n_h, M = b.m;
+    RELNN_TRY(t.gpacked.alloc_tmp(sizeof(int64_t) * (n + 1), st));
+    { group_pack_kernel<<<grid_for(n), 256, 0, st>>>(t.cnt.as<int32_t>(), n, t.gpacked.as<int64_t>()); note_launch(); }
+    RELNN_TRY(exclusive_scan<int64_t>(t.gpacked.as<int64_t>(), t.gpacked.as<int64_t>(), n, t.gpacked.as<int64_t>() + n, st));
+    RELNN_TRY(p.out_keys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(n, 1), st));
+    DevBuf cur, lst;
+    RELNN_TRY(cur.alloc_tmp(sizeof(int32_t) * std::max<int64_t>(n, 1), st));
+    { group_heads_kernel<<<grid_for(n), 256, 0, st>>>(t.cnt.as<int32_t>(), t.gpacked.as<int64_t>(), n,
+                                                    HT.ukeys.as<int64_t>(), cur.as<int32_t>(),
+                                                    p.out_keys.as<int64_t>()); note_launch(); }
+    if (M > 0)
+        { group_scatter_kernel<<<ilp_grid(M), 256, 0, st>>>(t.key.as<uint32_t>(), t.val.as<int32_t>(), M,
+                                                            cur.as<int32_t>(), b.hs.as<int32_t>()); note_launch(); }
+    // groups above kGroupLane tuples: at most M / (kGroupLane + 1) of them, listed, then one block each
+    const int64_t n_list = M / (kGroupLane + 1) + 1;
+    RELNN_TRY(lst.alloc_tmp(sizeof(int32_t) * (n_list + 1), st));
+    int* n_big = lst.as<int>() + n_list;
+    RELNN_CUDA(cudaMemsetAsync(n_big, 0, sizeof(int), st));
+    { group_sort_warp_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8)),
+                                256, 0, st>>>(t.cnt.as<int32_t>(), t.gpacked.as<int64_t>(), n, HT.rows_sorted.as<int32_t>(),
+                                              b.hs.as<int32_t>(), b.hd.as<int32_t>(), b.seg.as<int32_t>(),
+                                              lst.as<int32_t>(), n_big); note_launch(); }
+    { group_sort_block_kernel<<<(unsigned)std::min<int64_t>(n_list, (int64_t)num_sms() * 4), 256, 0, st>>>(
+        t.cnt.as<int32_t>(), t.gpacked.as<int64_t>(), lst.as<int32_t>(), n_big, HT.rows_sorted.as<int32_t>(),
+        b.hs.as<int32_t>(), b.hd.as<int32_t>(), b.seg.as<int32_t>()); note_launch(); }
+    RELNN_CUDA(cudaGetLastError());
+    return RELNN_OK;
 }
 
 relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tmp& t, cudaStream_t st) {
@@ -515,6 +759,11 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
         t.wide = nbits > 32;
     }
     t.pair = b.d_r > 0;
+    // the counting group-by: one branch, a dst join over unique H keys, no E row carried, no
+    // selection, no MAX (its tie order is the E order), not a stream chunk
+    t.want_count = p.join_dst && !t.wide && !t.pair && p.br.size() == 1 && p.Ht().n_unique == p.n_h &&
+                   !(p.flags & RELNN_FLAG_MAX) && !p.dense_out && filters_of(bd).n == 0 &&
+                   tune_get(RELNN_TUNE_GROUP_SORT) == 1;
     int64_t M = 0;
     if (t.wide) {
         if (t.pair) RELNN_TRY((emit_and_sort<uint64_t, int64_t>(p, bd, t, &M, nbits, st)));
@@ -528,8 +777,17 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
         return RELNN_ENOTSUP;
     }
     b.m = M;
-    // hs / er from the sorted payloads; hd and seg follow once the output rows are known
     const int64_t m1 = std::max<int64_t>(M, 1);
+    if (t.counted) {
+        RELNN_TRY(b.hs.alloc_nosync(4 * m1, st));
+        RELNN_TRY(b.hd.alloc_nosync(4 * m1, st));
+        RELNN_TRY(b.seg.alloc_nosync(4 * (m1 + 1), st));
+        RELNN_TRY(group_by_counting(p, b, t, st));
+        t.key_tmp.release();
+        t.val_tmp.release();
+        return RELNN_OK;
+    }
+    // hs / er from the sorted payloads; hd and seg follow once the output rows are known
     if (t.pair) {
         RELNN_TRY(b.hs.alloc_nosync(4 * m1, st));
         RELNN_TRY(b.er.alloc_nosync(4 * m1, st));
@@ -621,7 +879,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     RELNN_CUDA(cudaMemsetAsync(p.status.p, 0, sizeof(int) * kStatusInts, st));
 
     // a1: build side over H.id
-    if (!p.Hx) RELNN_TRY(join_table_build(p.H, desc->d_h_ids, desc->n_h, p.kt, st));
+    if (!p.Hx) RELNN_TRY(join_table_build(p.H, desc->d_h_ids, desc->n_h, p.kt, st, false));
     const JoinTable& HT = p.Ht();
     const int64_t U = HT.n_unique;
 
@@ -637,6 +895,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
 
     // output key set and output row of every matched tuple
     int32_t nout_join = 0;
+    int64_t counted_total = -1;
     if (p.join_dst && p.dense_out) {
         // stream chunk: output row = distinct index of the dst key; presence kept by the stream
         for (auto i = 0u; i < p.br.size(); ++i)
@@ -649,6 +908,11 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
             }
         RELNN_CUDA(cudaGetLastError());
         nout_join = (int32_t)U;
+    } else if (p.join_dst && tmp.size() == 1 && tmp[0].counted) {
+        // counting group-by: output keys, hd and seg are written; the output-row count is the high
+        // half of the scanned total, read with the final synchronisation
+        RELNN_CUDA(cudaMemcpyAsync(&counted_total, tmp[0].gpacked.as<int64_t>() + p.n_h, sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost, st));
     } else if (p.join_dst) {
         DevBuf present;
         RELNN_TRY(present.alloc_tmp(sizeof(int32_t) * (U + 1), st));
@@ -704,6 +968,7 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
     int dev_status = 0;
     RELNN_CUDA(cudaMemcpyAsync(&dev_status, p.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     RELNN_CUDA(cudaStreamSynchronize(st));
+    if (counted_total >= 0) nout_join = (int32_t)(counted_total >> 32);
     if (p.join_dst) p.n_out = nout_join;
     if (dev_status) {
         set_device_error(dev_status);

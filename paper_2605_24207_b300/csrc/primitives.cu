@@ -158,7 +158,7 @@ __device__ void block_excl_scan_small(int32_t* v, int count, int32_t* warp_tot) 
 // + in lower lanes of its step (__match_any_sync / popc). The block first reorders its tile by
 // digit in shared memory, so that each digit's keys leave as one contiguous run (coalesced stores).
 template <class K, class V>
-__global__ void rs_scatter_kernel(const K* __restrict__ keys, const V* __restrict__ vals,
+__global__ void __launch_bounds__(kSortThreads, 4) rs_scatter_kernel(const K* __restrict__ keys, const V* __restrict__ vals,
                                   K* __restrict__ okeys, V* __restrict__ ovals, int64_t n,
                                   int shift, unsigned mask, const int32_t* __restrict__ offs, int nblocks) {
     extern __shared__ __align__(16) int32_t sm[];

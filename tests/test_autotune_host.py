@@ -23,14 +23,16 @@ def test_size_buckets_are_powers_of_four():
 
 
 def test_apply_sets_knobs_and_returns_flags():
-    saved = {k: R.tune_get(k) for k in range(5)}
+    saved = {k: R.tune_get(k) for k in range(6)}
     try:
         assert A.apply(dict(form="per_tuple", agg_rows=32, agg_stages=3, agg_epi=4, kahan_min=17,
-                            sort_bits=10)) == R.FLAG_PER_TUPLE
+                            sort_bits=10, group_sort=1)) == R.FLAG_PER_TUPLE
         assert [R.tune_get(k) for k in (R.TUNE_AGG_ROWS, R.TUNE_AGG_STAGES, R.TUNE_AGG_EPI, R.TUNE_KAHAN_MIN,
-                                        R.TUNE_SORT_BITS)] == [32, 3, 4, 17, 10]
+                                        R.TUNE_SORT_BITS, R.TUNE_GROUP_SORT)] == [32, 3, 4, 17, 10, 1]
+        assert A.apply(dict(form="per_tuple", tile128=True)) == R.FLAG_PER_TUPLE | R.FLAG_TILE128
         assert A.apply({"form": "pushdown"}) == R.FLAG_PUSHDOWN
         assert R.tune_get(R.TUNE_AGG_EPI) == 8 and R.tune_get(R.TUNE_SORT_BITS) == 8
+        assert R.tune_get(R.TUNE_GROUP_SORT) == 0
         assert A.apply(None) == 0
         with pytest.raises(R.RelnnError):
             R.tune_set(R.TUNE_AGG_EPI, 6)

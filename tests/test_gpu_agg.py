@@ -188,3 +188,40 @@ def test_forward_repeat_is_deterministic(gpu):
     out2 = plan.forward(t["z"], t["W"], t["b"])
     torch.cuda.synchronize()
     assert np.array_equal(out, out2.cpu().numpy())
+
+
+@pytest.mark.parametrize("d,d_out,src_s", [(64, 64, 1.2), (128, 128, 1.1), (32, 32, 1.5), (64, 256, 1.1)])
+def test_relu_backward_aggregate_first(gpu, d, d_out, src_s):
+    """A ReLU rule whose forward kept its mask: the backward sums the masked dOut rows per H row
+    (src pass: each tuple's mask bits; dst pass: per-feature counts of active tuples, which also give
+    db) and runs the same GEMMs as a linear rule. Compared with the FP64 oracle's gradient and with the
+    per-tuple backward (RELNN_FLAG_PER_TUPLE) from the same mask."""
+    rel = W.make_rule(120, 30_011, 3000, d, d_out, np.int32, src_dist="zipf", src_s=src_s, act="relu")
+    flags = R.FLAG_BF16 | R.FLAG_RELU_MASK
+    keys, out, plan, t = run_rule(rel, flags=flags, z_dtype=torch.bfloat16)
+    dout = np.random.default_rng(9).standard_normal(out.shape).astype(np.float32)
+    dW, db, dz, _ = plan.backward(to_dev(dout), t["z"], t["W"], t["b"], t["r"])
+    torch.cuda.synchronize()
+    plan.check()
+    brs = [OBr(b.src, b.dst, bf16_round(b.W), b.b, None) for b in rel.branches]
+    oW, ob, oz, _ = O.rule_backward(rel.h_ids, bf16_round(rel.z), brs, keys, dout, act=rel.act)
+    # the GPU's ReLU decisions come from its bf16 forward; a few tuples near 0 may differ
+    assert rel_frob(dW[0].cpu().numpy(), oW[0]) <= 2e-2
+    assert rel_frob(db[0].cpu().numpy(), ob[0]) <= 2e-2
+    assert rel_frob(dz.cpu().numpy(), oz) <= 2e-2
+    keys2, out2, plan2, t2 = run_rule(rel, flags=flags | R.FLAG_PER_TUPLE, z_dtype=torch.bfloat16)
+    dW2, db2, dz2, _ = plan2.backward(to_dev(dout), t2["z"], t2["W"], t2["b"], t2["r"])
+    torch.cuda.synchronize()
+    assert rel_frob(dW[0].cpu().numpy(), dW2[0].cpu().numpy().astype(np.float64)) <= 1e-2
+    assert rel_frob(db[0].cpu().numpy(), db2[0].cpu().numpy().astype(np.float64)) <= 1e-4
+    assert rel_frob(dz.cpu().numpy(), dz2.cpu().numpy().astype(np.float64)) <= 1e-2
+
+
+def test_relu_backward_aggregate_first_is_deterministic(gpu):
+    rel = W.make_rule(121, 20_000, 1500, 64, 64, np.int32, src_dist="zipf", src_s=1.3, act="relu")
+    keys, out, plan, t = run_rule(rel, flags=R.FLAG_BF16 | R.FLAG_RELU_MASK, z_dtype=torch.bfloat16)
+    dout = to_dev(np.random.default_rng(2).standard_normal(out.shape).astype(np.float32))
+    g1 = plan.backward(dout, t["z"], t["W"], t["b"], t["r"])
+    g2 = plan.backward(dout, t["z"], t["W"], t["b"], t["r"])
+    torch.cuda.synchronize()
+    assert torch.equal(g1[0][0], g2[0][0]) and torch.equal(g1[1][0], g2[1][0]) and torch.equal(g1[2], g2[2])

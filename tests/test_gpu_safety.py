@@ -47,16 +47,19 @@ def test_serve_poll_times_out_then_completes(gpu):
         keys, src, dst, z = W.serving_query(5, 1_000_000, 1_000_000, 64)
         q = (torch.from_numpy(keys).cuda(), torch.from_numpy(z).cuda().to(torch.bfloat16),
              torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
-        t = srv.submit(*q)
+        # twelve 1M-tuple queries on one worker: the last one completes milliseconds after submission,
+        # far beyond the 50 us poll (whose wait may oversleep by the OS timer slack)
+        tickets = [srv.submit(*q) for _ in range(12)]
         res = R.Result()
-        st = srv.L.relnn_serve_poll(srv._h, t, C.byref(res), 50)
+        st = srv.L.relnn_serve_poll(srv._h, tickets[-1], C.byref(res), 50)
         assert st == ETIMEDOUT
-        r = None
-        for _ in range(200):
-            r = srv.poll(t, 100_000)
-            if r is not None:
-                break
-        assert r is not None and r[0].numel() > 0
-        srv.release(t)
+        for t in tickets:
+            r = None
+            for _ in range(200):
+                r = srv.poll(t, 100_000)
+                if r is not None:
+                    break
+            assert r is not None and r[0].numel() > 0
+            srv.release(t)
     finally:
         srv.close()
