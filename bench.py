@@ -550,18 +550,22 @@ class C3:
         pr = self.prog
         m1, m2 = pr.p1.n_matched, pr.p2.n_matched
         n_h, n1, n2 = int(self.t["h"].numel()), pr.p1.n_out, pr.p2.n_out
-        # rule 1 (ReLU) runs per tuple on the tensor cores: forward 2 x 128 x 64 FLOP per tuple, the
-        # backward's two GEMMs (dX, dW) twice that (the src pass's recomputed dX slice not counted).
-        # Rule 2 (linear) runs aggregate-first and is HBM-bound: forward = per tuple two 4-byte
-        # indices, per output row its descriptor (twice), H1 rows once (bf16) and output rows once;
-        # backward = per pass and tuple one 4-byte index, per H1 row its descriptor (twice), dOut rows
-        # (bf16) and H1 rows (bf16) once, dz rows written (src pass) or read and written (dst pass).
-        agg_f = 8 * m2 + 32 * n2 + n1 * 64 * 2 + n2 * 64 * 4
-        agg_b = 2 * (4 * m2 + 32 * n1 + n2 * 64 * 2 + n1 * 64 * 2) + n1 * 64 * 4 * 3
-        return {R.PROF_BWD_TC: ("bwd_tc_kernel (rule 1)", 2.0 * 2.0 * 128 * 64 * m1, "tensor"),
-                R.PROF_FWD_TC: ("fwd_tc_kernel (rule 1)", 2.0 * 128 * 64 * m1, "tensor"),
-                R.PROF_AGG_FWD: ("agg_tc_kernel<fwd> (rule 2)", float(agg_f), "hbm"),
-                R.PROF_AGG_BWD: ("agg_tc_kernel<bwd> (rule 2)", float(agg_b), "hbm"),
+        # rule 1 (ReLU) runs its forward per tuple on the tensor cores (2 x 128 x 64 FLOP per tuple,
+        # keeping the ReLU mask); rule 2 (linear) its forward aggregate-first, and both backwards run
+        # aggregate-first (rule 1 through the mask). HBM-bound work per step: the gather-sums (5
+        # launches: rule 2's forward, two passes per backward) read per tuple a 4-byte index (+ a
+        # 4-byte mask word and its index for rule 1's src pass), each gathered row once (bf16) and
+        # write a bf16 pair (4 x 64 B) per H row; the GEMMs (5 launches) read those pairs and each
+        # H row once and write each output / dz row once (f32, dz rows read back by the dst pass).
+        sum_b = (4 * m2 + n1 * 64 * 2 + n2 * 256) + 2 * (4 * m2 + n2 * 64 * 2 + n1 * 256) + \
+                2 * (4 * m1 + n1 * 64 * 2 + n_h * 256) + 8 * m1
+        gemm_f = n2 * 256 + n2 * 128 + n2 * 256
+        gemm_b = 2 * (n1 * 256 + n1 * 128 + n1 * 256) + 2 * (n_h * 256 + n_h * 128 + n_h * 256)
+        return {R.PROF_FWD_TC: ("fwd_tc_kernel (rule 1)", 2.0 * 128 * 64 * m1, "tensor"),
+                R.PROF_AGG_SUM: ("seg_sum_kernel (rule 2 forward; both backwards)", float(sum_b), "hbm"),
+                R.PROF_AGG_FWD: ("agg_gemm_kernel forward (rule 2)", float(gemm_f), "hbm"),
+                R.PROF_AGG_BWD: ("agg_gemm_kernel backward (both rules)", float(gemm_b), "hbm"),
+                R.PROF_BWD_TC: ("bwd_tc_kernel (per-tuple backward, if taken)", 2.0 * 2.0 * 128 * 64 * m1, "tensor"),
                 R.PROF_FWD_FP32: ("fwd_fp32_lane_kernel (readout)", float(n2 * 64 * 4 + n2 * 4), "hbm")}
 
     def e2e_setup(self):

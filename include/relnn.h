@@ -474,9 +474,11 @@ relnn_status relnn_profile_reset(void);
  *                          4; or 2..4, capped at what fits)
  *   RELNN_TUNE_AGG_EPI     epilogue warps of that GEMM: 4 (one per TMEM lane quarter) or 8 (two per
  *                          quarter, each on every other 32-row chunk); 0 = 8
- *   RELNN_TUNE_KAHAN_MIN   with RELNN_FLAG_KAHAN, the gather-sum of the aggregate-first form
- *                          compensates only rows of at least this many tuples (rows cut into chunks
- *                          always); 0 = every row (default)
+ *   RELNN_TUNE_KAHAN_MIN   with RELNN_FLAG_KAHAN, the aggregate-first form's gather-sum compensates
+ *                          inside a chunk of at most 32 tuples only for rows of at least this many
+ *                          tuples (and the chunks of cut rows); above 32 (default 33) no chunk is
+ *                          compensated inside, and the compensation is where a row's error grows:
+ *                          the fix-up adding the chunk partials of rows longer than 32 tuples
  *   RELNN_TUNE_GROUP_SORT  group-by of a single-branch plan over unique H keys: 0 = the stable radix
  *                          sort (groups in E order; default); 1 = by counting (a count per group key
  *                          during the emission, one scan, an atomic scatter, each group then ordered

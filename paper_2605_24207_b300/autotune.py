@@ -32,7 +32,7 @@ from . import workloads as W
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "relnn_b300", "autotune.json")
 
 # the library's defaults (what every knob is when nothing is tuned)
-DEFAULTS = {"form": "agg", "agg_rows": 0, "agg_stages": 0, "agg_epi": 8, "kahan_min": 0, "sort_bits": 8,
+DEFAULTS = {"form": "agg", "agg_rows": 0, "agg_stages": 0, "agg_epi": 8, "kahan_min": 33, "sort_bits": 8,
             "tile128": False, "group_sort": 0}
 _FORM_FLAG = {"agg": 0, "per_tuple": R.FLAG_PER_TUPLE, "pushdown": R.FLAG_PUSHDOWN}
 
@@ -100,7 +100,7 @@ def candidates(kahan: bool, linear: bool = True, pushdown: bool = True):
     for rows in (0, 32, 64):
         for stages in (0, 2, 3):
             for epi in (4, 8):
-                for kmin in ((0, 33) if kahan else (0,)):
+                for kmin in ((0, 33) if kahan else (33,)):
                     out.append(dict(DEFAULTS, agg_rows=rows, agg_stages=stages, agg_epi=epi, kahan_min=kmin))
     return out
 

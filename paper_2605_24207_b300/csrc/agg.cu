@@ -628,7 +628,7 @@ constexpr int kSegIdx = 32 * kChunk;  // tuple indices of a warp's 32 virtual ro
 
 // MASK (the backward of a ReLU rule): every tuple's row is taken through its ReLU mask bits (the
 // forward's per-tuple mask, uint32 [m][mask_words], bit o of word o / 32 = feature o active). The
-// src pass finds a tuple's mask through perm (src order -> plan order); the dst pass (SINGLE) counts,
+// src pass reads the mask already permuted into its tuple order; the dst pass (SINGLE) counts,
 // per feature, the active tuples of the run (plan positions x .. x + n - 1) and also sums its rows,
 // from the f32 table tbl_f32 (16-byte aligned rows), into this block's db partial db_part[block][w]
 // (the warps' sums added in warp order).
@@ -640,7 +640,6 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
                                                                  int* status, int kahan_min,
                                                                  const uint32_t* __restrict__ mask = nullptr,
                                                                  int mask_words = 0,
-                                                                 const int32_t* __restrict__ perm = nullptr,
                                                                  float* __restrict__ db_part = nullptr,
                                                                  const float* __restrict__ tbl_f32 = nullptr) {
     __shared__ int32_t s_idx[SINGLE ? 1 : kSegWarps][SINGLE ? 1 : kSegIdx];
@@ -741,19 +740,20 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
                         if (t0 + q < n) {
                             const int r = sidx[xo + t0 + q];
                             if (in_bounds(r, tbl_rows, status)) u[q] = __ldg(base + (int64_t)r * L);
-                            if (MASK) mk[q] = __ldg(mask + (int64_t)__ldg(perm + x0 + xo + t0 + q) * mask_words + mword) >> msh;
+                            if (MASK) mk[q] = __ldcs(mask + (int64_t)(x0 + xo + t0 + q) * mask_words + mword) >> msh;
                         }
                     }
 #pragma unroll
                     for (int q = 0; q < kUnroll; ++q) {
                         if (q >= slots) break;
                         if (MASK) {
-                            // a bf16 element whose ReLU was inactive becomes +0
+                            // a bf16 element whose ReLU was inactive becomes +0: bit j of the byte
+                            // selects element j; (bit * 0xffff) spreads a bit over a 16-bit half
                             const uint32_t m8 = mk[q];
-                            u[q].x &= ((m8 & 1u) ? 0x0000ffffu : 0u) | ((m8 & 2u) ? 0xffff0000u : 0u);
-                            u[q].y &= ((m8 & 4u) ? 0x0000ffffu : 0u) | ((m8 & 8u) ? 0xffff0000u : 0u);
-                            u[q].z &= ((m8 & 16u) ? 0x0000ffffu : 0u) | ((m8 & 32u) ? 0xffff0000u : 0u);
-                            u[q].w &= ((m8 & 64u) ? 0x0000ffffu : 0u) | ((m8 & 128u) ? 0xffff0000u : 0u);
+                            u[q].x &= (m8 & 1u) * 0x0000ffffu | ((m8 >> 1) & 1u) * 0xffff0000u;
+                            u[q].y &= ((m8 >> 2) & 1u) * 0x0000ffffu | ((m8 >> 3) & 1u) * 0xffff0000u;
+                            u[q].z &= ((m8 >> 4) & 1u) * 0x0000ffffu | ((m8 >> 5) & 1u) * 0xffff0000u;
+                            u[q].w &= ((m8 >> 6) & 1u) * 0x0000ffffu | ((m8 >> 7) & 1u) * 0xffff0000u;
                         }
                         add8(acc, cmp, u[q], kh);
                     }
@@ -800,6 +800,16 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
             for (int k = 0; k < kSegWarps; ++k) sacc += s_db[k][f];
             db_part[(int64_t)blockIdx.x * w + f] = sacc;
         }
+    }
+}
+
+// The ReLU mask rows in the src pass's tuple order, keeping only the words that hold features:
+// out[i][w] = mask[perm[i]][w] for w < out_words (= ceil(d_out / 32) <= mask_words).
+__global__ void permute_mask_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ perm, int64_t m,
+                                    int mask_words, int out_words, uint32_t* __restrict__ out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t* row = mask + (int64_t)__ldg(perm + t) * mask_words;
+        for (int w = 0; w < out_words; ++w) out[t * out_words + w] = __ldg(row + w);
     }
 }
 
@@ -1309,14 +1319,24 @@ __global__ void pack_a_bwd_kernel(const void* W, int w_bf16, int d_out, int d_in
 }
 
 // dW[g][col0 + i] = sum over CTAs (in order) of part[c][g][i].
-__global__ void agg_reduce_dw_kernel(const float* __restrict__ part, int grid, int n_g, int d_z, float* dW, int d_in,
-                                     int col0) {
+// dW slice = sum over the CTAs' partials, in CTA order: 32 elements per block, warp w adds CTAs w,
+// w + 8, ... (8 independent chains of loads), then the 8 warps' sums are added in warp order.
+__global__ void __launch_bounds__(256) agg_reduce_dw_kernel(const float* __restrict__ part, int grid, int n_g,
+                                                            int d_z, float* dW, int d_in, int col0) {
+    __shared__ float red[8][32];
     const int64_t n = (int64_t)n_g * d_z;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int c = 0; c < grid; ++c) s += part[(int64_t)c * n + i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = blockIdx.x * 32ll + lane;
+    float s = 0.f;
+    if (i < n)
+        for (int c = w; c < grid; c += 8) s += part[(int64_t)c * n + i];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < n) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += red[k][lane];
         const int64_t g = i / d_z, k = i - g * d_z;
-        dW[g * d_in + col0 + k] = s;
+        dW[g * d_in + col0 + k] = t;
     }
 }
 
@@ -1401,12 +1421,24 @@ __global__ void __launch_bounds__(256) dout_prep_kernel(const float* __restrict_
 
 // db_b[f] = sum over blocks (in order, compensated) of the partials ([block][branch][d_out], or
 // [block][d_out] for b = -1).
-__global__ void db_reduce_kernel(const float* __restrict__ part, int blocks, int d_out, int b, float* db) {
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d_out; f += gridDim.x * blockDim.x) {
-        float s = 0.f, c = 0.f;
-        for (int k = 0; k < blocks; ++k)
+// (32 features per block; warp w takes blocks w, w + 8, ... compensated, then the 8 warps' sums are
+// added in warp order, compensated)
+__global__ void __launch_bounds__(256) db_reduce_kernel(const float* __restrict__ part, int blocks, int d_out, int b,
+                                                        float* db) {
+    __shared__ float red[8][32][2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int f = blockIdx.x * 32 + lane;
+    float s = 0.f, c = 0.f;
+    if (f < d_out)
+        for (int k = w; k < blocks; k += 8)
             kahan_add(s, c, part[(b < 0 ? (int64_t)k : ((int64_t)k * kDbBranches + b)) * d_out + f]);
-        db[f] = s - c;
+    red[w][lane][0] = s;
+    red[w][lane][1] = c;
+    __syncthreads();
+    if (w == 0 && f < d_out) {
+        float t = 0.f, tc = 0.f;
+        for (int k = 0; k < 8; ++k) kahan_add(t, tc, red[k][lane][0] - red[k][lane][1]);
+        db[f] = t - tc;
     }
 }
 
@@ -1718,8 +1750,11 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
-    const int ss_blocks = p.kahan ? seg_sum_grid<true, false>(nv_max) : seg_sum_grid<false, false>(nv_max);
     const int kmin = (int)tune_get(RELNN_TUNE_KAHAN_MIN);
+    // compensation inside the 32-tuple chunks only when the threshold reaches them (the chunks of a
+    // longer row are always added with compensation by the fix-up)
+    const bool ksum = p.kahan && kmin <= kChunk;
+    const int ss_blocks = ksum ? seg_sum_grid<true, false>(nv_max) : seg_sum_grid<false, false>(nv_max);
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         const VRows& V = b.vr_out;
@@ -1728,7 +1763,7 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         {
             ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
             const uint16_t* zt = reinterpret_cast<const uint16_t*>(io.z);
-            if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
+            if (ksum) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
                                                                                 p.n_h, p.d, kpad, S, p.status.as<int>(), kmin);
             else seg_sum_kernel<false, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
                                                                           p.n_h, p.d, kpad, S, p.status.as<int>(), kmin);
@@ -1895,7 +1930,7 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
                                                        db_part); note_launch(); }
             for (int k = 0; k < cs.n && !masked; ++k) {
                 float* db = g.db.size() > b0 + k ? g.db[b0 + k] : nullptr;
-                if (db) { db_reduce_kernel<<<grid_for(p.d_out, 128), 128, 0, st>>>(db_part, pblocks, p.d_out, k, db); note_launch(); }
+                if (db) { db_reduce_kernel<<<(unsigned)ceil_div(p.d_out, 32), 256, 0, st>>>(db_part, pblocks, p.d_out, k, db); note_launch(); }
             }
         }
         RELNN_CUDA(cudaGetLastError());
@@ -1928,6 +1963,7 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
         RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
+    DevBuf mask_src;  // ReLU rule: the mask in the src pass's tuple order
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         float* dW = g.dW.size() > i ? g.dW[i] : nullptr;
@@ -1944,33 +1980,39 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             // G rows: sums of dOut rows per virtual row (src order: a row per tuple; dst order: one
             // row times the run's length), as bf16 pairs
             uint16_t* S = p.sbuf.as<uint16_t>();
+            const int kmin = (int)tune_get(RELNN_TUNE_KAHAN_MIN);
+            const bool ksum = p.kahan && kmin <= kChunk;  // as in the forward
             const int ss_blocks =
                 (int)std::min<int64_t>(ss_max, masked ? (pass == 1 ? seg_sum_grid<false, true, true>(V.nv)
-                                                        : p.kahan ? seg_sum_grid<true, false, true>(V.nv)
-                                                                  : seg_sum_grid<false, false, true>(V.nv))
+                                                        : ksum ? seg_sum_grid<true, false, true>(V.nv)
+                                                               : seg_sum_grid<false, false, true>(V.nv))
                                                       : (pass == 1 ? seg_sum_grid<false, true>(V.nv)
-                                                         : p.kahan ? seg_sum_grid<true, false>(V.nv)
-                                                                   : seg_sum_grid<false, false>(V.nv)));
+                                                         : ksum ? seg_sum_grid<true, false>(V.nv)
+                                                                : seg_sum_grid<false, false>(V.nv)));
             const int32_t* gi = pass == 0 ? b.seg_src.as<int32_t>() : b.seg.as<int32_t>();
-            const int kmin = (int)tune_get(RELNN_TUNE_KAHAN_MIN);
             {
                 ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
                 const uint16_t* tb = p.doutbf.as<uint16_t>();
                 int* stw = p.status.as<int>();
                 const uint32_t* mk = masked ? b.relu_mask.as<uint32_t>() : nullptr;
                 if (masked && pass == 0) {
-                    if (p.kahan) seg_sum_kernel<true, false, true><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
-                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, kmin, mk, mask_words,
-                        b.src_perm.as<int32_t>());
+                    // the mask in src order first (one gather of 4 x mask_words bytes per tuple)
+                    const int src_words = (p.d_out + 31) / 32;
+                    RELNN_TRY(mask_src.alloc_tmp(sizeof(uint32_t) * (size_t)b.m * src_words, st));
+                    { permute_mask_kernel<<<grid_for(b.m), 256, 0, st>>>(mk, b.src_perm.as<int32_t>(), b.m, mask_words,
+                                                                         src_words, mask_src.as<uint32_t>()); note_launch(); }
+                    if (ksum) seg_sum_kernel<true, false, true><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
+                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, kmin, mask_src.as<uint32_t>(),
+                        src_words);
                     else seg_sum_kernel<false, false, true><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
-                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, kmin, mk, mask_words,
-                        b.src_perm.as<int32_t>());
+                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, kmin, mask_src.as<uint32_t>(),
+                        src_words);
                 } else if (masked) {
                     seg_sum_kernel<false, true, true><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
-                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, 0, mk, mask_words, nullptr,
-                        db_part, g.dout);
+                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw, 0, mk, mask_words, db_part,
+                        g.dout);
                 } else if (pass == 0) {
-                    if (p.kahan) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
+                    if (ksum) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
                                                                                         p.d_out, kpad_g, S, stw, kmin);
                     else seg_sum_kernel<false, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
                                                                                   p.d_out, kpad_g, S, stw, kmin);
@@ -1985,7 +2027,7 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             if (masked && pass == 1) {
                 // db of this branch: the masked dst pass's block partials, added in block order
                 float* db = g.db.size() > i ? g.db[i] : nullptr;
-                if (db) { db_reduce_kernel<<<grid_for(p.d_out, 128), 128, 0, st>>>(db_part, ss_blocks, p.d_out, -1, db); note_launch(); }
+                if (db) { db_reduce_kernel<<<(unsigned)ceil_div(p.d_out, 32), 256, 0, st>>>(db_part, ss_blocks, p.d_out, -1, db); note_launch(); }
             }
             { pack_a_bwd_kernel<<<grid_for((int64_t)a_elems), 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, col0, p.d,
                                                                            rows_pad, cols, abuf); note_launch(); }
@@ -2034,7 +2076,7 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
                                 p.kahan, p.n_h, p.status.as<int>(), st));
             if (dW) {
                 const int64_t nw = (int64_t)p.d_out * p.d;
-                { agg_reduce_dw_kernel<<<grid_for(nw), 256, 0, st>>>(dw_part, grid, p.d_out, p.d, dW, p.d_in, col0); note_launch(); }
+                { agg_reduce_dw_kernel<<<(unsigned)ceil_div(nw, 32), 256, 0, st>>>(dw_part, grid, p.d_out, p.d, dW, p.d_in, col0); note_launch(); }
             }
             RELNN_CUDA(cudaGetLastError());
         }

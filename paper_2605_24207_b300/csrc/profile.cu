@@ -47,7 +47,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 constexpr int kKnobs = 6;
-std::atomic<int64_t> g_knobs[kKnobs] = {{8}, {0}, {0}, {0}, {0}, {0}};
+std::atomic<int64_t> g_knobs[kKnobs] = {{8}, {0}, {0}, {0}, {33}, {0}};
 bool knob_ok(int knob, int64_t v) {
     switch (knob) {
         case RELNN_TUNE_SORT_BITS: return v >= 4 && v <= 11;

@@ -84,6 +84,10 @@ struct relnn_server_s {
     int64_t mem_in_use = 0;
     int in_system = 0;
     bool stopping = false;
+    // the device's free memory as last read (cudaMemGetInfo), and when; re-read when older than
+    // 2 ms or when a batch would take more than half of it
+    int64_t free_seen = 0;
+    std::chrono::steady_clock::time_point free_when{};
     std::vector<std::thread> workers;
 };
 
@@ -201,17 +205,25 @@ void worker_main(relnn_server_s* S) {
                        (!S->queue.empty() && S->mem_in_use + S->queue.front()->mem <= S->budget);
             });
             if (S->queue.empty()) break;  // stopping and drained
-            // the device's free memory now (other batches and other processes hold some of it): a
-            // batch is admitted only while its estimate fits in 90 % of it as well as in the budget
-            lk.unlock();
-            size_t free_b = 0, total_b = 0;
-            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-                (void)cudaGetLastError();
-                free_b = (size_t)S->budget;
+            // the device's free memory (other batches and other processes hold some of it): a batch
+            // is admitted only while its estimate fits in 90 % of it as well as in the budget. The
+            // reading is refreshed at an admission when it is older than 2 ms or when the front
+            // query alone would take more than half of it (a driver query per admission otherwise
+            // serialises the workers' launches)
+            const Clock::time_point now0 = Clock::now();
+            if (now0 - S->free_when > std::chrono::milliseconds(2) || 2 * S->queue.front()->mem > S->free_seen) {
+                lk.unlock();
+                size_t free_b = 0, total_b = 0;
+                if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    free_b = (size_t)S->budget;
+                }
+                lk.lock();
+                S->free_seen = (int64_t)free_b;
+                S->free_when = now0;
+                if (S->queue.empty()) continue;
             }
-            const int64_t avail = (int64_t)(0.9 * (double)free_b);
-            lk.lock();
-            if (S->queue.empty()) continue;
+            const int64_t avail = (int64_t)(0.9 * (double)S->free_seen);
             while (!S->queue.empty()) {
                 Query* q = S->queue.front();
                 if (!batch.empty() && ((int)batch.size() >= S->cfg.max_batch_queries ||

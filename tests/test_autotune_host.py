@@ -12,7 +12,7 @@ def test_candidates_cover_forms_and_defaults():
     assert dict(A.DEFAULTS) in c
     assert {x["form"] for x in c} == {"agg", "per_tuple", "pushdown"}
     assert {x["agg_epi"] for x in c} == {4, 8}
-    assert all(x["kahan_min"] == 0 for x in c)
+    assert all(x["kahan_min"] == 33 for x in c)
     assert {x["kahan_min"] for x in A.candidates(kahan=True)} == {0, 33}
 
 
