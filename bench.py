@@ -246,7 +246,10 @@ class C2:
         t = self.t
         p = R.RulePlan(t["h"], [(t["src"], t["dst"])], self.d, self.d_out, flags=self.flags)
         p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
-        return p
+        # done with the plan: its memory is freed in the stream's order (relnn_plan_release), not
+        # with a device-wide wait
+        p.release()
+        return None
 
     def kernels(self):
         """Library kernels of a step: id -> (name, algorithmic work per step, bound)."""
@@ -258,6 +261,11 @@ class C2:
         # output row (bf16) and writes each output row once (f32). Per-tuple form (tensor):
         # 2 d_in d_out FLOP per tuple.
         sb, gb = self.agg_bytes()
+        if R.tune_get(R.TUNE_AGG_FUSE):
+            # fused: one kernel, no pair buffer (its compulsory bytes + the descriptors and dst indices)
+            return {R.PROF_AGG_FWD: ("agg_gemm_kernel fused (producer-warp gather-sum + tcgen05 GEMM)",
+                                     float(self.forward_bytes() + 20 * self.n_vrows), "hbm"),
+                    R.PROF_FWD_TC: ("fwd_tc_kernel", 2.0 * (2 * self.d) * self.d_out * self.matched, "tensor")}
         return {R.PROF_AGG_SUM: ("seg_sum_kernel (gather-sum)", float(sb), "hbm"),
                 R.PROF_AGG_FWD: ("agg_gemm_kernel (TMA + tcgen05 GEMM)", float(gb), "hbm"),
                 R.PROF_FWD_TC: ("fwd_tc_kernel", 2.0 * (2 * self.d) * self.d_out * self.matched, "tensor")}
@@ -689,7 +697,8 @@ class C4:
         from paper_2605_24207_b300 import relnn as R
         p = R.RulePlan(self.t["h"], self.brs, 64, 96, flags=self.flags, d_r=64)
         p.forward(self.t["z"], self.W, self.b, self.r, out=self.out)
-        return p
+        p.release()  # stream-ordered free, as in the single-rule step
+        return None
 
     def kernels(self):
         from paper_2605_24207_b300 import relnn as R
@@ -804,7 +813,8 @@ class C1B:
         t = self.t
         p = R.RulePlan(t["h"], [(t["src"], t["dst"])], 16, 16)
         p.forward(t["z"], [t["W"]], [t["b"]], out=self.out)
-        return p
+        p.release()  # stream-ordered free, as in the single-rule step
+        return None
 
     def kernels(self):
         from paper_2605_24207_b300 import relnn as R

@@ -20,6 +20,9 @@
  *     released only by the matching *_destroy call.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls marked
  *     "async" only enqueue work on it; calls marked "sync" return after the stream has drained.
+ *     A plan's workspaces are allocated and grown in the order of the stream of the call that
+ *     needs them, so calls on one plan must be ordered by the caller: issued on one stream, or
+ *     ordered across streams (events, or a synchronisation) before a call on another stream.
  *   - Keys are int32 (RELNN_I32) or int64 (RELNN_I64). INT64_MAX is reserved and rejected as an H
  *     key. Embeddings are row-major [rows, width] with contiguous rows, f32 or bf16.
  *   - W uses the torch nn.Linear layout [d_out, d_in] row-major; b is f32 [d_out].
@@ -483,13 +486,19 @@ relnn_status relnn_profile_reset(void);
  *                          sort (groups in E order; default); 1 = by counting (a count per group key
  *                          during the emission, one scan, an atomic scatter, each group then ordered
  *                          by src H row), falling back to the radix sort when a tuple does not match
- *                          or a group holds more than 4096 tuples                                   */
+ *                          or a group holds more than 4096 tuples
+ *   RELNN_TUNE_AGG_FUSE    aggregate-first forward of a unique-key plan: 0 = two kernels (the
+ *                          gather-sum writes each row's bf16 pair to memory, the GEMM reads it back;
+ *                          default); 1 / 2 = one kernel whose producer warps write the pairs straight
+ *                          into the GEMM's shared-memory stages (4 epilogue + 8 producer warps, or
+ *                          8 + 4); plans with Kahan summation inside chunks stay with two kernels   */
 #define RELNN_TUNE_SORT_BITS 0
 #define RELNN_TUNE_AGG_ROWS 1
 #define RELNN_TUNE_AGG_STAGES 2
 #define RELNN_TUNE_AGG_EPI 3
 #define RELNN_TUNE_KAHAN_MIN 4
 #define RELNN_TUNE_GROUP_SORT 5
+#define RELNN_TUNE_AGG_FUSE 6
 relnn_status relnn_tune_set(int32_t knob, int64_t value);
 relnn_status relnn_tune_get(int32_t knob, int64_t* value);
 

@@ -8,7 +8,8 @@ a BF16 linear rule and the knobs of the kernels it runs:
     default for linear SUM rules), per-tuple (the Linear on every matched tuple, RELNN_FLAG_PER_TUPLE)
     or push-down (the Linear once per H row, RELNN_FLAG_PUSHDOWN);
   - for the aggregate-first GEMM: tile rows (RELNN_TUNE_AGG_ROWS), pipeline stages
-    (RELNN_TUNE_AGG_STAGES) and epilogue warps (RELNN_TUNE_AGG_EPI: 4 or 8, two kernel instances);
+    (RELNN_TUNE_AGG_STAGES) and epilogue warps (RELNN_TUNE_AGG_EPI: 4 or 8, two kernel instances),
+    or the fused kernel whose producer warps write the sums into its stages (RELNN_TUNE_AGG_FUSE);
   - with Kahan summation, the degree below which rows are summed plainly (RELNN_TUNE_KAHAN_MIN);
   - for the plan, the radix digit width of the group sort (RELNN_TUNE_SORT_BITS), or the counting
     group-by instead of the radix sort (RELNN_TUNE_GROUP_SORT).
@@ -33,7 +34,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "relnn_b300", "a
 
 # the library's defaults (what every knob is when nothing is tuned)
 DEFAULTS = {"form": "agg", "agg_rows": 0, "agg_stages": 0, "agg_epi": 8, "kahan_min": 33, "sort_bits": 8,
-            "tile128": False, "group_sort": 0}
+            "tile128": False, "group_sort": 0, "agg_fuse": 0}
 _FORM_FLAG = {"agg": 0, "per_tuple": R.FLAG_PER_TUPLE, "pushdown": R.FLAG_PUSHDOWN}
 
 
@@ -68,6 +69,7 @@ def apply(cfg: dict) -> int:
     R.tune_set(R.TUNE_KAHAN_MIN, int(c["kahan_min"]))
     R.tune_set(R.TUNE_SORT_BITS, int(c["sort_bits"]))
     R.tune_set(R.TUNE_GROUP_SORT, int(c["group_sort"]))
+    R.tune_set(R.TUNE_AGG_FUSE, int(c["agg_fuse"]))
     return _FORM_FLAG[c["form"]] | (R.FLAG_TILE128 if c["tile128"] else 0)
 
 
@@ -102,6 +104,9 @@ def candidates(kahan: bool, linear: bool = True, pushdown: bool = True):
             for epi in (4, 8):
                 for kmin in ((0, 33) if kahan else (33,)):
                     out.append(dict(DEFAULTS, agg_rows=rows, agg_stages=stages, agg_epi=epi, kahan_min=kmin))
+    # the fused forward (measured 1.9x slower than the two kernels on the single-rule relation: its
+    # producer warps cannot keep enough row loads in flight within one CTA), timed once
+    out.append(dict(DEFAULTS, agg_fuse=1))
     return out
 
 

@@ -644,6 +644,18 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
                                                                  const float* __restrict__ tbl_f32 = nullptr) {
     __shared__ int32_t s_idx[SINGLE ? 1 : kSegWarps][SINGLE ? 1 : kSegIdx];
     __shared__ float s_db[MASK && SINGLE ? kSegWarps : 1][MASK && SINGLE ? 256 : 1];
+    // src pass of a ReLU rule: the AND mask of 8 bf16 elements for each byte of mask bits
+    __shared__ uint4 s_lut[MASK && !SINGLE ? 256 : 1];
+    if (MASK && !SINGLE) {
+        for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                w[i] = ((v >> (2 * i)) & 1 ? 0x0000ffffu : 0u) | ((v >> (2 * i + 1)) & 1 ? 0xffff0000u : 0u);
+            s_lut[v] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int L = w >> 3, lsh = 31 - __clz(L), G = 32 >> lsh;
     const int grp = lane >> lsh, ch = lane & (L - 1);
@@ -747,13 +759,13 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
                     for (int q = 0; q < kUnroll; ++q) {
                         if (q >= slots) break;
                         if (MASK) {
-                            // a bf16 element whose ReLU was inactive becomes +0: bit j of the byte
-                            // selects element j; (bit * 0xffff) spreads a bit over a 16-bit half
-                            const uint32_t m8 = mk[q];
-                            u[q].x &= (m8 & 1u) * 0x0000ffffu | ((m8 >> 1) & 1u) * 0xffff0000u;
-                            u[q].y &= ((m8 >> 2) & 1u) * 0x0000ffffu | ((m8 >> 3) & 1u) * 0xffff0000u;
-                            u[q].z &= ((m8 >> 4) & 1u) * 0x0000ffffu | ((m8 >> 5) & 1u) * 0xffff0000u;
-                            u[q].w &= ((m8 >> 6) & 1u) * 0x0000ffffu | ((m8 >> 7) & 1u) * 0xffff0000u;
+                            // a bf16 element whose ReLU was inactive becomes +0 (bit j of the byte
+                            // selects element j; the byte's AND mask comes from the table)
+                            const uint4 am = s_lut[mk[q] & 0xffu];
+                            u[q].x &= am.x;
+                            u[q].y &= am.y;
+                            u[q].z &= am.z;
+                            u[q].w &= am.w;
                         }
                         add8(acc, cmp, u[q], kh);
                     }
@@ -842,7 +854,7 @@ __global__ void vr_first_kernel(const int4* __restrict__ vr, int64_t nv, const i
 constexpr int kGemmLoaders = 96;
 constexpr int kGemmMma = 3;
 constexpr int kGemmEpi0 = 4;
-constexpr int gemm_threads(int epi) { return 32 * (kGemmEpi0 + epi); }
+constexpr int gemm_threads(int epi, int prod = 0) { return 32 * (kGemmEpi0 + epi + prod); }
 
 struct GemmArgs {
     const int4* vr;
@@ -863,13 +875,23 @@ struct GemmArgs {
     int accumulate, tile_n, stages;
     uint32_t idesc, tmem_cols;
     int* status;
+    // fused forward (PROD > 0): the S pairs are not read from a buffer but summed by the producer
+    // warps: row v's tuples are gidx[vr[v].x ..) (rows of gtbl, width w_s)
+    const int32_t* gidx;
+    const uint16_t* gtbl;
+    int64_t gtbl_rows;
+    int w_s;
 };
 
 // Forward: D1 = A_src [S_hi; S_lo], D2 = A_dst R (the dst rows), Out = D1 + n (D2 + b).
 // Backward pass: D1 = A [S_hi; S_lo] is a dz row (A = a W^T block), and dW += S^T R with R = the
 // rows' z, both operands read MN-major from the staged rows, accumulated in TMEM over the CTA's tiles.
-template <bool BWD, int EPI>
-__global__ void __launch_bounds__(gemm_threads(EPI), 1)
+// PROD > 0 (forward only): PROD producer warps after the epilogue warps compute each tile's S pairs
+// (the gather-sum of seg_sum_kernel: lane groups of w_s / 8 lanes own a row, up to kUnroll row loads
+// in flight per lane) and write them straight into the stage (128B swizzle), so the pairs never
+// touch global memory.
+template <bool BWD, int EPI, int PROD = 0>
+__global__ void __launch_bounds__(gemm_threads(EPI, PROD), 1)
 agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap smap,
                 const __grid_constant__ GemmArgs a) {
     extern __shared__ uint8_t dyn_smem[];
@@ -894,7 +916,8 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < a.stages; ++s) {
-            mbar_init(smem_u32(&full[s]), kGemmLoaders + 1);  // the loaders' copies + the TMA's bytes
+            // the loaders' copies + the TMA's bytes, or + every producer thread (fused)
+            mbar_init(smem_u32(&full[s]), kGemmLoaders + (PROD > 0 ? 32 * PROD : 1));
             mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -905,6 +928,21 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
         mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
         fence_mbar_init();
+    }
+    if (PROD > 0 && a.w_s < a.kpad_s) {
+        // fused: the K padding of the S blocks (columns w_s .. kpad_s of each half) is never written
+        // by the producers and must read as zeros
+        const int pc0 = a.w_s >> 3, pcn = (a.kpad_s - a.w_s) >> 3;  // 16-byte chunks per row
+        const int per_stage = 2 * N * pcn;
+        for (int i = tid; i < a.stages * per_stage; i += blockDim.x) {
+            const int s = i / per_stage, rem = i - s * per_stage;
+            const int hl = rem / (N * pcn), rem2 = rem - hl * N * pcn;
+            const int r = rem2 / pcn, c = pc0 + (rem2 - r * pcn);
+            const uint32_t off = (uint32_t)(hl * a.n_kb_s + (c >> 3)) * blk + (uint32_t)r * 128u +
+                                 ((((uint32_t)c & 7u) ^ ((uint32_t)r & 7u)) << 4);
+            st_shared_v4(smem_u32(st_smem + (size_t)s * stage_bytes) + off, 0u, 0u, 0u, 0u);
+        }
+        fence_proxy_async();
     }
     if (warp == kGemmMma) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
     tc_fence_before();
@@ -942,7 +980,7 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
             if (!mbar_wait(smem_u32(&empty[s]), (use & 1u) ^ 1u, a.status, abort_flag)) break;
             const uint32_t sb = smem_u32(st_smem + (size_t)s * stage_bytes);
             const int64_t v0 = tile * N;
-            if (tid == 0) {
+            if (PROD == 0 && tid == 0) {
                 mbar_arrive_expect_tx(smem_u32(&full[s]), s_bytes);
                 for (int hl = 0; hl < 2; ++hl)
                     for (int kb = 0; kb < a.n_kb_s; ++kb)
@@ -1039,6 +1077,53 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
             mbar_wait(smem_u32(drain), 0, a.status, abort_flag);
         }
         __syncwarp();
+    } else if (PROD > 0 && warp >= kGemmEpi0 + EPI) {
+        // ------------------------------------------------------------------ producers (fused)
+        const int pw = warp - (kGemmEpi0 + EPI);
+        const int L = a.w_s >> 3, lsh = 31 - __clz(L), G = 32 >> lsh;
+        const int grp = lane >> lsh, ch = lane & (L - 1);
+        const uint4* __restrict__ gbase = reinterpret_cast<const uint4*>(a.gtbl) + ch;
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++lt) {
+            const int s = lt % a.stages;
+            const uint32_t use = (uint32_t)(lt / a.stages);
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&empty[s]), (use & 1u) ^ 1u, a.status, abort_flag))) break;
+            const uint32_t sb = smem_u32(st_smem + (size_t)s * stage_bytes);
+            const int64_t v0 = tile * N;
+            // steps of G rows, every PROD-th step to this warp
+            for (int k = pw; k * G < N; k += PROD) {
+                const int j = k * G + grp;
+                const int64_t v = v0 + j;
+                const int4 m = (j < N && v < a.nv) ? __ldg(a.vr + v) : make_int4(0, 0, -1, -1);
+                const int n = m.y > 0 ? m.y : 0;
+                const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)n);
+                float acc[8], cmp[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = cmp[i] = 0.f;
+                for (int t0 = 0; t0 < nmax; t0 += kUnroll) {
+                    const int slots = min(kUnroll, nmax - t0);  // warp-uniform
+                    uint4 u[kUnroll];
+#pragma unroll
+                    for (int q = 0; q < kUnroll; ++q) {
+                        if (q >= slots) break;
+                        u[q] = make_uint4(0u, 0u, 0u, 0u);
+                        if (t0 + q < n) {
+                            const int r = __ldg(a.gidx + m.x + t0 + q);
+                            if (in_bounds(r, a.gtbl_rows, a.status)) u[q] = __ldg(gbase + (int64_t)r * L);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kUnroll; ++q) {
+                        if (q >= slots) break;
+                        add8(acc, cmp, u[q], false);
+                    }
+                }
+                if (j < N) store_pair(sb, blk, a.n_kb_s, 0, j, ch, acc);
+            }
+            // the stage's rows were written through the generic proxy: visible to the tensor cores
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&full[s]));
+        }
     } else if (warp >= kGemmEpi0) {
         // ------------------------------------------------------------------ epilogue
         // EH warps per TMEM lane quarter, warp eh taking 32-row chunks eh, eh + EH, ... of a tile
@@ -1725,7 +1810,7 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
     const int m_blocks = (p.d_out + 127) / 128;
     const AggCfg cfg = gemm_config(n_kb_s, n_kb_r, m_blocks);
     const int rows_pad = m_blocks * 128, cols = (n_kb_s + n_kb_r) * 64;
-    RELNN_TRY(p.wpack.alloc(sizeof(uint16_t) * (size_t)rows_pad * cols));
+    RELNN_TRY(p.wpack.alloc_nosync(sizeof(uint16_t) * (size_t)rows_pad * cols, st));
     CUtensorMap amap;
     RELNN_TRY(encode_bf16_tile_map(&amap, p.wpack.p, cols, rows_pad));
     size_t vp_max = 0;
@@ -1734,7 +1819,7 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         VRows& V = b.vr_out;
         RELNN_TRY(ensure_vrows(V, b.seg.as<int32_t>(), b.m, p.n_out, true, st));
         if (p.concat_dst && !V.has_d1) {
-            RELNN_TRY(V.d1.alloc(sizeof(int32_t) * std::max<int64_t>(V.nv, 1), st));
+            RELNN_TRY(V.d1.alloc_nosync(sizeof(int32_t) * std::max<int64_t>(V.nv, 1), st));
             if (V.nv > 0) { vr_first_kernel<<<grid_for(V.nv), 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hd.as<int32_t>(), V.d1.as<int32_t>()); note_launch(); }
             RELNN_CUDA(cudaGetLastError());
             V.has_d1 = true;
@@ -1742,25 +1827,29 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         vp_max = std::max(vp_max, (size_t)(V.n_parts + V.n_l2) * p.d_out);
         nv_max = std::max(nv_max, V.nv);
     }
-    if (vp_max) RELNN_TRY(p.vpart.alloc(sizeof(float) * vp_max));
-    RELNN_TRY(p.sbuf.alloc(sizeof(uint16_t) * 2 * (size_t)kpad * std::max<int64_t>(nv_max, 1)));
+    if (vp_max) RELNN_TRY(p.vpart.alloc_nosync(sizeof(float) * vp_max, st));
     static bool attr_set = false;
     if (!attr_set) {
         RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false, 4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<false, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         attr_set = true;
     }
     const int kmin = (int)tune_get(RELNN_TUNE_KAHAN_MIN);
     // compensation inside the 32-tuple chunks only when the threshold reaches them (the chunks of a
     // longer row are always added with compensation by the fix-up)
     const bool ksum = p.kahan && kmin <= kChunk;
+    // fused (RELNN_TUNE_AGG_FUSE): the GEMM's own producer warps compute the pairs (plain f32 sums)
+    const int fuse = ksum ? 0 : (int)tune_get(RELNN_TUNE_AGG_FUSE);
+    if (!fuse) RELNN_TRY(p.sbuf.alloc_nosync(sizeof(uint16_t) * 2 * (size_t)kpad * std::max<int64_t>(nv_max, 1), st));
     const int ss_blocks = ksum ? seg_sum_grid<true, false>(nv_max) : seg_sum_grid<false, false>(nv_max);
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         const VRows& V = b.vr_out;
         if (V.nv == 0) continue;
-        uint16_t* S = p.sbuf.as<uint16_t>();
-        {
+        uint16_t* S = fuse ? p.wpack.as<uint16_t>() : p.sbuf.as<uint16_t>();  // (fused: the map is unused)
+        if (!fuse) {
             ProfToken pt = prof_begin(RELNN_PROF_AGG_SUM, st);
             const uint16_t* zt = reinterpret_cast<const uint16_t*>(io.z);
             if (ksum) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
@@ -1774,11 +1863,16 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         { pack_a_fwd_kernel<<<grid_for((int64_t)rows_pad * cols), 256, 0, st>>>(io.br[i].W, io.w_bf16, p.d_out, p.d_in, p.d,
                                                                                kpad, rows_pad, cols, p.wpack.as<uint16_t>()); note_launch(); }
         CUtensorMap smap;
-        RELNN_TRY(encode_bf16_tile_map(&smap, S, 2 * kpad, V.nv, cfg.N));
+        if (fuse) RELNN_TRY(encode_bf16_tile_map(&smap, S, cols, rows_pad, cfg.N));
+        else RELNN_TRY(encode_bf16_tile_map(&smap, S, 2 * kpad, V.nv, cfg.N));
         GemmArgs a{};
         a.vr = V.vr.as<int4>();
         a.nv = V.nv;
         a.n_tiles = ceil_div(V.nv, cfg.N);
+        a.gidx = b.hs.as<int32_t>();
+        a.gtbl = reinterpret_cast<const uint16_t*>(io.z);
+        a.gtbl_rows = p.n_h;
+        a.w_s = p.d;
         a.ridx = p.concat_dst ? V.d1.as<int32_t>() : nullptr;
         a.ridx_stride = 1;
         a.rtbl = reinterpret_cast<const uint16_t*>(io.z);
@@ -1802,7 +1896,9 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
         const int grid = (int)std::min<int64_t>(a.n_tiles, num_sms());
         {
             ProfToken pt = prof_begin(RELNN_PROF_AGG_FWD, st);
-            if (gemm_epi() == 4) agg_gemm_kernel<false, 4><<<grid, gemm_threads(4), cfg.smem, st>>>(amap, smap, a);
+            if (fuse == 1) agg_gemm_kernel<false, 4, 8><<<grid, gemm_threads(4, 8), cfg.smem, st>>>(amap, smap, a);
+            else if (fuse == 2) agg_gemm_kernel<false, 8, 4><<<grid, gemm_threads(8, 4), cfg.smem, st>>>(amap, smap, a);
+            else if (gemm_epi() == 4) agg_gemm_kernel<false, 4><<<grid, gemm_threads(4), cfg.smem, st>>>(amap, smap, a);
             else agg_gemm_kernel<false, 8><<<grid, gemm_threads(8), cfg.smem, st>>>(amap, smap, a);
             note_launch();
             prof_end(pt, st);
@@ -1828,7 +1924,7 @@ relnn_status forward_agg(Plan& p, const CallIO& io_in, float* out, cudaStream_t 
         return RELNN_ENOTSUP;
     }
     const int rows_pad = m_blocks * 128, cols = n_kb * 64;
-    RELNN_TRY(p.wpack.alloc(sizeof(uint16_t) * (size_t)rows_pad * cols));
+    RELNN_TRY(p.wpack.alloc_nosync(sizeof(uint16_t) * (size_t)rows_pad * cols, st));
     CUtensorMap amap;
     RELNN_TRY(encode_bf16_tile_map(&amap, p.wpack.p, cols, rows_pad));
     size_t vp_max = 0;
@@ -1836,7 +1932,7 @@ relnn_status forward_agg(Plan& p, const CallIO& io_in, float* out, cudaStream_t 
         RELNN_TRY(ensure_vrows(b.vr_out, b.seg.as<int32_t>(), b.m, p.n_out, true, st));
         vp_max = std::max(vp_max, (size_t)(b.vr_out.n_parts + b.vr_out.n_l2) * p.d_out);
     }
-    if (vp_max) RELNN_TRY(p.vpart.alloc(sizeof(float) * vp_max));
+    if (vp_max) RELNN_TRY(p.vpart.alloc_nosync(sizeof(float) * vp_max, st));
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         const VRows& V = b.vr_out;
@@ -1911,7 +2007,7 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
     const int64_t ss_max = (int64_t)num_sms() * 8;  // blocks of a gather-sum launch, at most
     const size_t dwp = (size_t)grid_max * p.d_out * p.d,
                  dbp = (size_t)std::max<int64_t>(pblocks * kDbBranches, masked ? ss_max : 0) * p.d_out;
-    RELNN_TRY(p.scratch.alloc(a_bytes + sizeof(float) * (dwp + dbp)));
+    RELNN_TRY(p.scratch.alloc_nosync(a_bytes + sizeof(float) * (dwp + dbp), st));
     uint16_t* abuf = p.scratch.as<uint16_t>();
     float* dw_part = reinterpret_cast<float*>(p.scratch.as<uint8_t>() + a_bytes);
     float* db_part = dw_part + dwp;
@@ -1920,7 +2016,7 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
     // the pass that makes the bf16 copy (tuples per output row from the forward's virtual rows).
     for (auto& b : p.br) RELNN_TRY(ensure_vrows(b.vr_out, b.seg.as<int32_t>(), b.m, p.n_out, true, st));
     if (p.n_out > 0) {
-        RELNN_TRY(p.doutbf.alloc(sizeof(uint16_t) * (size_t)p.n_out * p.d_out));
+        RELNN_TRY(p.doutbf.alloc_nosync(sizeof(uint16_t) * (size_t)p.n_out * p.d_out, st));
         const int64_t rpb = ceil_div(p.n_out, pblocks);
         for (size_t b0 = 0; b0 < p.br.size(); b0 += kDbBranches) {
             CntSet cs{};
@@ -1955,8 +2051,8 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             nv_max = std::max(nv_max, b.vr_dst.nv);
         }
     }
-    if (vp_max) RELNN_TRY(p.vpart.alloc(sizeof(float) * vp_max));
-    RELNN_TRY(p.sbuf.alloc(sizeof(uint16_t) * 2 * (size_t)kpad_g * std::max<int64_t>(nv_max, 1)));
+    if (vp_max) RELNN_TRY(p.vpart.alloc_nosync(sizeof(float) * vp_max, st));
+    RELNN_TRY(p.sbuf.alloc_nosync(sizeof(uint16_t) * 2 * (size_t)kpad_g * std::max<int64_t>(nv_max, 1), st));
     static bool attr_set = false;
     if (!attr_set) {
         RELNN_CUDA(cudaFuncSetAttribute(agg_gemm_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));

@@ -718,7 +718,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
     // dY gets anyway)
     const uint16_t* dout_bf = nullptr;
     if (g.dz && (reinterpret_cast<uintptr_t>(g.dout) & 15u) == 0 && p.n_out > 0) {
-        RELNN_TRY(p.doutbf.alloc(sizeof(uint16_t) * (size_t)p.n_out * p.d_out));
+        RELNN_TRY(p.doutbf.alloc_nosync(sizeof(uint16_t) * (size_t)p.n_out * p.d_out, st));
         f32_to_bf16(g.dout, p.n_out * (int64_t)p.d_out, p.doutbf.as<uint16_t>(), st);
         RELNN_CUDA(cudaGetLastError());
         dout_bf = p.doutbf.as<uint16_t>();
@@ -750,7 +750,7 @@ relnn_status backward_tc(Plan& p, const CallIO& io_in, const GradIO& g, cudaStre
         const size_t dbp_elems = (size_t)grid * p.d_out;
         const size_t n_maps = dmap.rows.size() + smap.rows.size() + row_src.size();
         const size_t head = ((wt_d_elems + wt_s_elems) * 2 + sizeof(int) * n_maps + 255) & ~(size_t)255;
-        RELNN_TRY(p.scratch.alloc(head + sizeof(float) * (part_elems + dbp_elems)));
+        RELNN_TRY(p.scratch.alloc_nosync(head + sizeof(float) * (part_elems + dbp_elems), st));
         uint16_t* wt_d = p.scratch.as<uint16_t>();
         uint16_t* wt_s = wt_d + wt_d_elems;
         int* d_maps = reinterpret_cast<int*>(wt_s + wt_s_elems);

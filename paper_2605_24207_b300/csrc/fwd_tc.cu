@@ -610,7 +610,7 @@ relnn_status with_bf16_z(Plan& p, const CallIO& io, CallIO& out, cudaStream_t st
     if (p.z_version != 0 && p.zbf.p && p.zbf_src == io.z && p.zbf_version == p.z_version &&
         p.zbf.bytes >= sizeof(uint16_t) * (size_t)n)
         return RELNN_OK;  // the copy converted for this table version
-    RELNN_TRY(p.zbf.alloc(sizeof(uint16_t) * n));
+    RELNN_TRY(p.zbf.alloc_nosync(sizeof(uint16_t) * n, st));
     p.zbf_src = io.z;
     p.zbf_version = p.z_version;
     const int64_t n4 = n / 4;
@@ -675,10 +675,10 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     const int unit = half_n / rep;
     int64_t max_units = 1;
     for (auto& b : p.br) max_units = std::max<int64_t>(max_units, ceil_div(b.m, unit));
-    RELNN_TRY(p.carry.alloc(sizeof(float) * 2 * p.d_out * max_units));
+    RELNN_TRY(p.carry.alloc_nosync(sizeof(float) * 2 * p.d_out * max_units, st));
     const int rows_pad = m_blocks * 128;
     const size_t wp_elems = (size_t)rows_pad * L.n_kb * 64;
-    RELNN_TRY(p.wpack.alloc(wp_elems * 2 + 256));
+    RELNN_TRY(p.wpack.alloc_nosync(wp_elems * 2 + 256, st));
     int* d_meta = reinterpret_cast<int*>(p.wpack.as<uint8_t>() + wp_elems * 2);
     int meta[2 * kMaxKb];
     for (int i = 0; i < L.n_kb; ++i) {
@@ -715,8 +715,8 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
     const bool want_mask = p.act == RELNN_ACT_RELU && (p.flags & RELNN_FLAG_RELU_MASK) && !maxagg;
     if (maxagg) {
         RELNN_CHECK_ARG(!multi, "MAX aggregator: single-branch rules only");
-        RELNN_TRY(p.carry_pos.alloc(sizeof(int32_t) * 2 * p.d_out * max_units));
-        RELNN_TRY(p.max_arg.alloc(sizeof(int32_t) * (size_t)p.n_out * p.d_out));
+        RELNN_TRY(p.carry_pos.alloc_nosync(sizeof(int32_t) * 2 * p.d_out * max_units, st));
+        RELNN_TRY(p.max_arg.alloc_nosync(sizeof(int32_t) * (size_t)p.n_out * p.d_out, st));
     }
     const int mask_words = m_blocks * 4;
     for (size_t i = 0; i < p.br.size(); ++i) {
@@ -742,7 +742,7 @@ relnn_status forward_tc(Plan& p, const CallIO& io_in, float* out, cudaStream_t s
         }
         a.status = p.status.as<int>();
         if (want_mask) {
-            RELNN_TRY(b.relu_mask.alloc(sizeof(uint32_t) * (size_t)b.m * mask_words));
+            RELNN_TRY(b.relu_mask.alloc_nosync(sizeof(uint32_t) * (size_t)b.m * mask_words, st));
             a.relu_mask = b.relu_mask.as<uint32_t>();
         }
         a.mask_words = mask_words;

@@ -137,7 +137,8 @@ __global__ void dense_pack_kernel(const int32_t* cnt, int64_t S, int64_t* packed
 }
 
 __global__ void dense_slots_kernel(const int32_t* cnt, const int64_t* excl, int64_t S, int64_t kmin, int64_t n,
-                                   int64_t U, int32_t* slot_vals, int32_t* run_start, int64_t* ukeys) {
+                                   int64_t U, int32_t* slot_vals, int32_t* run_start, int64_t* ukeys,
+                                   int32_t* slot_rows) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = excl[s];
         const int32_t u = (int32_t)(e >> 32);
@@ -147,6 +148,7 @@ __global__ void dense_slots_kernel(const int32_t* cnt, const int64_t* excl, int6
             ukeys[u] = (int64_t)((uint64_t)kmin + (uint64_t)s);
         } else {
             slot_vals[s] = -1;
+            if (slot_rows) slot_rows[s] = -1;  // (present slots get their row from the placement)
         }
         if (s == 0) run_start[U] = (int32_t)n;
     }
@@ -284,12 +286,12 @@ relnn_status dense_build(JoinTable& jt, const void* keys, int64_t n, int kt, int
     RELNN_TRY(jt.run_start.alloc_nosync(sizeof(int32_t) * (U + 1), st));
     RELNN_TRY(jt.ukeys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(U, 1), st));
     RELNN_TRY(jt.slot_vals.alloc_nosync(sizeof(int32_t) * S, st));
+    const bool dup = U < n;
+    if (!dup) RELNN_TRY(jt.slot_rows.alloc_nosync(sizeof(int32_t) * S, st));  // -1 for an empty slot
     { dense_slots_kernel<<<gs, 256, 0, st>>>(cnt.as<int32_t>(), packed.as<int64_t>(), S, kmin, n, U,
                                              jt.slot_vals.as<int32_t>(), jt.run_start.as<int32_t>(),
-                                             jt.ukeys.as<int64_t>()); note_launch(); }
-    const bool dup = U < n;
+                                             jt.ukeys.as<int64_t>(), dup ? nullptr : jt.slot_rows.as<int32_t>()); note_launch(); }
     if (dup) RELNN_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * S, st));
-    else RELNN_TRY(jt.slot_rows.alloc_nosync(sizeof(int32_t) * S, st));  // an empty slot's entry is garbage
     { dense_place_kernel<<<gn, 256, 0, st>>>(keys, n, kt, kmin, packed.as<int64_t>(), dup ? cnt.as<int32_t>() : nullptr,
                                              jt.rows_sorted.as<int32_t>(), jt.uid_of_pos.as<int32_t>(),
                                              dup ? nullptr : jt.slot_rows.as<int32_t>()); note_launch(); }

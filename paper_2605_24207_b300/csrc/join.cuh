@@ -8,8 +8,8 @@
 //   lookup           direct-address table int32[max-min+1] when the key range is small, else an
 //                    open-addressing hash table (linear probing, load <= 1/2) of int64 keys and int32
 //                    distinct-key indices.
-//   slot_rows        with the direct table and unique keys (dense build): the H row of each slot,
-//                    so a probe that needs the row takes one lookup instead of two.
+//   slot_rows        with the direct table and unique keys (dense build): the H row of each slot
+//                    (-1: no key), so a probe that needs the row takes one lookup instead of two.
 #pragma once
 
 #include "common.cuh"
@@ -25,7 +25,7 @@ struct JoinView {
     uint64_t mask;             // hash mode: capacity - 1
     const int64_t* slot_keys;  // hash mode
     const int32_t* slot_vals;  // distinct-key index per slot (-1 = empty)
-    const int32_t* slot_rows;  // direct mode, unique keys: H row per slot (else null)
+    const int32_t* slot_rows;  // direct mode, unique keys: H row per slot, -1 if none (else null)
     const int32_t* rows_sorted;
     const int32_t* run_start;
     const int32_t* uid_of_pos;

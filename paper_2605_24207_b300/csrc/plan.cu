@@ -270,15 +270,12 @@ __global__ void emit_all_kernel(JoinView j, const void* src, const void* dst, in
     }
     int32_t a[kIlp], b[kIlp], hs[kIlp];
     if (j.slot_rows) {
-        // direct table with unique keys: the src H row in one lookup (the row read for a slot that
-        // holds no key is garbage, but its slot_vals entry is -1, so the tuple counts as a miss and
-        // the caller re-emits everything with emit_unique_kernel)
+        // direct table with unique keys: the src H row in one lookup (-1: no such key)
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) {
             const uint64_t os = (uint64_t)ks[k] - (uint64_t)j.key_min, od = (uint64_t)kd[k] - (uint64_t)j.key_min;
-            const bool ins = os < (uint64_t)j.direct_size;
-            a[k] = ins ? __ldg(j.slot_vals + os) : -1;
-            hs[k] = ins ? __ldg(j.slot_rows + os) : 0;
+            hs[k] = os < (uint64_t)j.direct_size ? __ldg(j.slot_rows + os) : -1;
+            a[k] = hs[k];
             b[k] = !join_dst ? 0 : (od < (uint64_t)j.direct_size ? __ldg(j.slot_vals + od) : -1);
         }
     } else {

@@ -46,8 +46,8 @@ EvPair* take() {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
-constexpr int kKnobs = 6;
-std::atomic<int64_t> g_knobs[kKnobs] = {{8}, {0}, {0}, {0}, {33}, {0}};
+constexpr int kKnobs = 7;
+std::atomic<int64_t> g_knobs[kKnobs] = {{8}, {0}, {0}, {0}, {33}, {0}, {0}};
 bool knob_ok(int knob, int64_t v) {
     switch (knob) {
         case RELNN_TUNE_SORT_BITS: return v >= 4 && v <= 11;
@@ -56,6 +56,7 @@ bool knob_ok(int knob, int64_t v) {
         case RELNN_TUNE_AGG_EPI: return v == 0 || v == 4 || v == 8;
         case RELNN_TUNE_KAHAN_MIN: return v >= 0 && v <= (1 << 30);
         case RELNN_TUNE_GROUP_SORT: return v == 0 || v == 1;
+        case RELNN_TUNE_AGG_FUSE: return v >= 0 && v <= 2;
     }
     return false;
 }

@@ -234,7 +234,7 @@ def profile_reset():
     _check(lib().relnn_profile_reset())
 
 
-TUNE_SORT_BITS, TUNE_AGG_ROWS, TUNE_AGG_STAGES, TUNE_AGG_EPI, TUNE_KAHAN_MIN, TUNE_GROUP_SORT = 0, 1, 2, 3, 4, 5
+TUNE_SORT_BITS, TUNE_AGG_ROWS, TUNE_AGG_STAGES, TUNE_AGG_EPI, TUNE_KAHAN_MIN, TUNE_GROUP_SORT, TUNE_AGG_FUSE = 0, 1, 2, 3, 4, 5, 6
 
 
 def tune_set(knob: int, value: int):

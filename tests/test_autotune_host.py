@@ -14,6 +14,7 @@ def test_candidates_cover_forms_and_defaults():
     assert {x["agg_epi"] for x in c} == {4, 8}
     assert all(x["kahan_min"] == 33 for x in c)
     assert {x["kahan_min"] for x in A.candidates(kahan=True)} == {0, 33}
+    assert {x["agg_fuse"] for x in c} == {0, 1}
 
 
 def test_size_buckets_are_powers_of_four():
@@ -23,7 +24,7 @@ def test_size_buckets_are_powers_of_four():
 
 
 def test_apply_sets_knobs_and_returns_flags():
-    saved = {k: R.tune_get(k) for k in range(6)}
+    saved = {k: R.tune_get(k) for k in range(7)}
     try:
         assert A.apply(dict(form="per_tuple", agg_rows=32, agg_stages=3, agg_epi=4, kahan_min=17,
                             sort_bits=10, group_sort=1)) == R.FLAG_PER_TUPLE

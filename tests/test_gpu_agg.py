@@ -225,3 +225,45 @@ def test_relu_backward_aggregate_first_is_deterministic(gpu):
     g2 = plan.backward(dout, t["z"], t["W"], t["b"], t["r"])
     torch.cuda.synchronize()
     assert torch.equal(g1[0][0], g2[0][0]) and torch.equal(g1[1][0], g2[1][0]) and torch.equal(g1[2], g2[2])
+
+
+@pytest.mark.parametrize("fuse", [1, 2])
+@pytest.mark.parametrize("case", ["w128", "w64_d96", "w32", "w256", "heavy", "union", "no_concat_dst", "f32"])
+def test_fused_forward(gpu, fuse, case):
+    """The fused aggregate-first forward (RELNN_TUNE_AGG_FUSE = 1 or 2: the GEMM's producer warps
+    sum each row's tuples straight into the shared-memory stage) against the oracle, at the same bars
+    as the two-kernel form, and against the two-kernel form itself."""
+    saved = R.tune_get(R.TUNE_AGG_FUSE)
+    try:
+        if case == "w128":
+            rel, kw = W.make_rule(131, 40_000, 3000, 128, 128, np.int64, src_dist="zipf", src_s=1.1), {}
+        elif case == "w64_d96":
+            rel, kw = W.make_rule(132, 20_011, 1500, 64, 96, np.int32), {}
+        elif case == "w32":
+            rel, kw = W.make_rule(133, 20_011, 1500, 32, 64, np.int32), {}
+        elif case == "w256":
+            rel, kw = W.make_rule(134, 10_000, 900, 256, 64, np.int32), {}
+        elif case == "heavy":
+            rel, kw = W.make_rule(135, 40_000, 200, 64, 64, np.int32, dst_dist="zipf", dst_s=2.0), {}
+        elif case == "union":
+            rel, kw = W.make_rule(136, 0, 3000, 64, 96, np.int32, dst_dist="zipf", dst_s=1.0,
+                                  branch_tuples=[20_000, 10_000, 5000]), {}
+        elif case == "no_concat_dst":
+            rel = W.make_rule(137, 10_000, 900, 64, 64, np.int32)
+            rel.branches[0].W = np.ascontiguousarray(rel.branches[0].W[:, :64])
+            R.tune_set(R.TUNE_AGG_FUSE, fuse)
+            keys, out, plan, _ = run_rule(rel, flags=R.FLAG_BF16 | R.FLAG_NO_CONCAT_DST, z_dtype=torch.bfloat16)
+            ok, oo, _ = oracle_rule(rel, round_z=True, round_w=True, concat_dst=False)
+            assert np.array_equal(keys, ok)
+            assert rel_frob(out, oo) <= SAME_INPUT_TOL
+            return
+        else:
+            rel, kw = W.make_rule(138, 8000, 600, 64, 64, np.int64, missing_frac=0.1, sparse_keys=True), \
+                dict(z_dtype=torch.float32)
+        R.tune_set(R.TUNE_AGG_FUSE, 0)
+        _, out2, _, _ = run_rule(rel, flags=R.FLAG_BF16, **({"z_dtype": torch.bfloat16} | kw))
+        R.tune_set(R.TUNE_AGG_FUSE, fuse)
+        _, out, _, _ = _fwd(rel, **kw)
+        assert rel_frob(out, out2.astype(np.float64)) <= 1e-5
+    finally:
+        R.tune_set(R.TUNE_AGG_FUSE, saved)
