@@ -61,6 +61,7 @@ def parse():
                     help="c2: skip the c3 / c4 / c1b / c5 records appended to the line")
     ap.add_argument("--no-serving", action="store_true", help="c2: skip the shortened c5 record")
     ap.add_argument("--sub-queries", type=int, default=2000, help="queries of the shortened c5 record")
+    ap.add_argument("--workers", type=int, default=4, help="c5: server worker threads (streams)")
     ap.add_argument("--sub-cmp-queries", type=int, default=300,
                     help="queries the torch comparator serves in the shortened c5 record")
     return ap.parse_args()
@@ -876,7 +877,7 @@ def _torch_query(h, z, src, dst, Wt, bt):
     return uk, torch.zeros((uk.numel(), Y.shape[1]), device=Y.device).index_add_(0, inv, Y)
 
 
-def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True) -> dict:
+def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True, workers: int = 4) -> dict:
     """A stream of rule queries (T ~ logU[1k, 1M], K = T/8, z bf16[64], shared Linear 128 -> 64)
     arriving as a Poisson process at 2,000 queries/s, served by relnn_server_* with memory-admitted
     continuous batching; latency = arrival -> results ready. Paced run (clocks sampled), saturation
@@ -906,7 +907,7 @@ def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True) ->
 
     def serve(paced: bool, n: int):
         srv = R.Server(Wt, bt, 64, flags=R.FLAG_BF16, max_queue=4096, max_batch_tuples=2_000_000,
-                       max_batch_queries=64, tile128_below=thr, n_workers=4)
+                       max_batch_queries=64, tile128_below=thr, n_workers=workers)
         for g in grid[:4].tolist():  # warm-up
             t = srv.submit(*pool[g])
             while srv.poll(t, 100_000) is None:
@@ -988,7 +989,7 @@ def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True) ->
     return {"value": tuples / wall_s, "unit": UNIT, "queries": nq, "tuples": tuples,
             "config": {"workload": f"serving stream of {nq} rule queries, T ~ logU[1k,1M] (24 size classes), "
                                    f"K = T/8, int32 keys, z bf16[64], shared Linear 128->64, Poisson arrivals "
-                                   f"2000/s; value = saturation tuples/s", "tile128_below": thr},
+                                   f"2000/s; value = saturation tuples/s", "tile128_below": thr, "workers": workers},
             "serving": {"paced_p50_ms": pct(lat, 50), "paced_p99_ms": pct(lat, 99),
                         "paced_queries_per_s": nq / wall, "mean_queries_per_batch": mean_batch,
                         "saturation_queries_per_s": nq / wall_s, "saturation_tuples_per_s": tuples / wall_s,
@@ -1002,7 +1003,7 @@ def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True) ->
 
 def run_serving(args):
     """--config c5: the serving stream on its own (one JSON line)."""
-    st = serving_stats(args.n_queries, args.cmp_queries)
+    st = serving_stats(args.n_queries, args.cmp_queries, workers=args.workers)
     nq = st["queries"]
     line = {"metric": METRIC, "value": st["value"], "unit": UNIT, "n_gpus": 1, "steps": nq, "warmup": 4,
             "ms_per_step": 1e3 * st["tuples"] / st["value"] / nq, "higher_is_better": True, "scaling": "weak",
@@ -1248,7 +1249,7 @@ def run_relnn(args):
             del sw
             torch.cuda.empty_cache()
         if not args.no_serving:
-            st = serving_stats(args.sub_queries, args.sub_cmp_queries, local, with_cpu=False)
+            st = serving_stats(args.sub_queries, args.sub_cmp_queries, local, with_cpu=False, workers=args.workers)
             st["config"]["workload"] += (f" (shortened to the first {args.sub_queries} queries of the trace; the "
                                          f"torch comparator on the first {args.sub_cmp_queries})")
             subs["c5"] = st

@@ -90,6 +90,14 @@ struct AggArgs {
     uint32_t idesc_dw, dw_col;
 };
 
+// a0 += b0, a1 += b1 as one packed f32x2 add (the same IEEE round-to-nearest sum per element)
+__device__ __forceinline__ void add_f32x2(float& a0, float& a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 x, y;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\t"
+        "add.rn.f32x2 x, x, y;\n\tmov.b64 {%0, %1}, x;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(b0), "f"(b1));
+}
+
 __device__ __forceinline__ void add8(float (&acc)[8], float (&cmp)[8], const uint4& u, bool kahan) {
     const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
@@ -99,8 +107,7 @@ __device__ __forceinline__ void add8(float (&acc)[8], float (&cmp)[8], const uin
             kahan_add(acc[2 * i], cmp[2 * i], lo);
             kahan_add(acc[2 * i + 1], cmp[2 * i + 1], hi);
         } else {
-            acc[2 * i] += lo;
-            acc[2 * i + 1] += hi;
+            add_f32x2(acc[2 * i], acc[2 * i + 1], lo, hi);
         }
     }
 }
@@ -752,7 +759,7 @@ __global__ void __launch_bounds__(32 * kSegWarps, 3) seg_sum_kernel(const int4* 
                         if (t0 + q < n) {
                             const int r = sidx[xo + t0 + q];
                             if (in_bounds(r, tbl_rows, status)) u[q] = __ldg(base + (int64_t)r * L);
-                            if (MASK) mk[q] = __ldcs(mask + (int64_t)(x0 + xo + t0 + q) * mask_words + mword) >> msh;
+                            if (MASK) mk[q] = __ldg(mask + (int64_t)(x0 + xo + t0 + q) * mask_words + mword) >> msh;
                         }
                     }
 #pragma unroll
@@ -1166,10 +1173,12 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                 const int64_t vb = v0 + rr;
                 if (rr >= N || vb >= a.nv) break;
                 const int4 mt = meta[c];
-                // chunks of consecutive whole rows (no chunk partial, no row past the end) store row after
-                // row without per-row bookkeeping
+                // chunks of 32 consecutive whole rows, or of 32 consecutive chunk partials (the chunks of
+                // one long row), store row after row without per-row bookkeeping
                 const int row0 = __shfl_sync(0xffffffffu, mt.z, 0);
-                const bool simple = __all_sync(0xffffffffu, mt.w < 0 && mt.z == row0 + lane);
+                const int part0 = __shfl_sync(0xffffffffu, mt.w, 0);
+                const bool whole = __all_sync(0xffffffffu, mt.w < 0 && mt.z == row0 + lane);
+                const bool parts = !whole && __all_sync(0xffffffffu, mt.w >= 0 && mt.w == part0 + lane);
                 for (int mb = 0; mb < a.m_blocks; ++mb) {
                     if (mb * 128 + 32 * q >= a.n_feat) continue;
                     const int o = mb * 128 + 32 * q + lane;
@@ -1181,7 +1190,7 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                     tmem_ld_32x32b_x32(ta, v1);
                     if (has_r) tmem_ld_32x32b_x32(ta + (uint32_t)a.m_blocks * N, v2);
                     tmem_ld_wait();
-                    if (simple && a.out && in_bounds(row0 + 31, a.out_rows, a.status) && in_bounds(row0, a.out_rows, a.status)) {
+                    if (whole && a.out && in_bounds(row0 + 31, a.out_rows, a.status) && in_bounds(row0, a.out_rows, a.status)) {
                         float* dst = a.out + (int64_t)row0 * a.n_feat + o;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
@@ -1191,6 +1200,19 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                                 y += nj * ((has_r ? __uint_as_float(v2[j]) : 0.f) + bo);
                             }
                             if (o_ok) emit_out(dst + (int64_t)j * a.n_feat, y, a.accumulate);
+                        }
+                        continue;
+                    }
+                    if (parts && a.out) {
+                        float* dst = a.vpart + (int64_t)part0 * a.n_feat + o;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            float y = __uint_as_float(v1[j]);
+                            if (!BWD) {
+                                const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
+                                y += nj * ((has_r ? __uint_as_float(v2[j]) : 0.f) + bo);
+                            }
+                            if (o_ok) __stcg(dst + (int64_t)j * a.n_feat, y);
                         }
                         continue;
                     }
