@@ -951,6 +951,21 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
         }
         fence_proxy_async();
     }
+    if (a.w_r > 0 && a.w_r < 64 * a.n_kb_r) {
+        // the columns w_r .. 64 n_kb_r of the R block are never copied and must read as zeros (the
+        // forward's K padding: stale shared memory of an earlier kernel could hold NaN patterns, and
+        // 0 x NaN is NaN)
+        const int rc0 = a.w_r >> 3, rcn = 8 * a.n_kb_r - rc0;  // 16-byte chunks per row
+        const int per_stage = N * rcn;
+        for (int i = tid; i < a.stages * per_stage; i += blockDim.x) {
+            const int s = i / per_stage, rem = i - s * per_stage;
+            const int r = rem / rcn, c = rc0 + (rem - r * rcn);
+            const uint32_t off = (uint32_t)(2 * a.n_kb_s + (c >> 3)) * blk + (uint32_t)r * 128u +
+                                 ((((uint32_t)c & 7u) ^ ((uint32_t)r & 7u)) << 4);
+            st_shared_v4(smem_u32(st_smem + (size_t)s * stage_bytes) + off, 0u, 0u, 0u, 0u);
+        }
+        fence_proxy_async();
+    }
     if (warp == kGemmMma) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
     tc_fence_before();
     __syncthreads();

@@ -42,6 +42,16 @@ def test_forward_widths(gpu, d, d_out):
     _fwd(rel)
 
 
+@pytest.mark.parametrize("d,d_out", [(8, 16), (16, 64), (32, 32)])
+def test_forward_narrow_rows_padding_reads_zero(gpu, d, d_out):
+    """Rows narrower than a 64-column K block: the GEMM's dst block is padded with zeros it writes
+    itself (the gather-sum before it leaves index words in shared memory, and with more than 2^15 H
+    rows some of them are NaN patterns as bf16; a stale NaN times a zero weight would be NaN)."""
+    rel = W.make_rule(107, 200_000, 70_000, d, d_out, np.int32, src_dist="zipf", src_s=1.1)
+    keys, out, _, _ = _fwd(rel)
+    assert np.isfinite(out).all()
+
+
 def test_forward_same_as_per_tuple(gpu):
     rel = W.make_rule(102, 50_000, 4000, 128, 128, np.int64, src_dist="zipf", src_s=1.1)
     keys, out, _, _ = _fwd(rel)
