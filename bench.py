@@ -908,8 +908,15 @@ def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True, wo
     def serve(paced: bool, n: int):
         srv = R.Server(Wt, bt, 64, flags=R.FLAG_BF16, max_queue=4096, max_batch_tuples=2_000_000,
                        max_batch_queries=64, tile128_below=thr, n_workers=workers)
-        for g in grid[:4].tolist():  # warm-up
+        # warm-up: every size class alone, then a burst of 96 queries of mixed sizes at once (batched
+        # path, memory pool at its working set, clocks up), none of it timed
+        for g in grid.tolist():
             t = srv.submit(*pool[g])
+            while srv.poll(t, 100_000) is None:
+                pass
+            srv.release(t)
+        burst = [srv.submit(*pool[int(g)]) for g in np.resize(grid, 96)]
+        for t in burst:
             while srv.poll(t, 100_000) is None:
                 pass
             srv.release(t)

@@ -256,10 +256,12 @@ __global__ void __launch_bounds__(kEmitThreads) emit_unique_kernel(
 // Unique H keys, no selection: if every tuple matches, tuple e's pair goes to position e. This pass
 // assumes so (plain streaming, no look-back) and counts the tuples that do not match; when the count
 // is not zero, the caller runs emit_unique_kernel over the same outputs.
+// A tuple that matches nothing gets the group key `sentinel` (above every real key: it sorts to the
+// end, behind the matched tuples, which keep their E order).
 template <class K, class V>
 __global__ void emit_all_kernel(JoinView j, const void* src, const void* dst, int64_t T, int kt, bool join_dst,
                                 uint64_t omin, unsigned long long* misses, K* t_key, V* t_val, int32_t* cnt,
-                                unsigned* big) {
+                                unsigned* big, K sentinel) {
     const int64_t e0 = (blockIdx.x * (int64_t)blockDim.x) * kIlp + threadIdx.x;
     int64_t ks[kIlp], kd[kIlp];
 #pragma unroll
@@ -297,7 +299,8 @@ __global__ void emit_all_kernel(JoinView j, const void* src, const void* dst, in
     for (int k = 0; k < kIlp; ++k) {
         const int64_t e = e0 + (int64_t)k * blockDim.x;
         if (e < T) {
-            t_key[e] = join_dst ? (K)b[k] : (K)(ordered64(kd[k]) - omin);
+            const bool ok = a[k] >= 0 && b[k] >= 0;
+            t_key[e] = !ok ? sentinel : join_dst ? (K)b[k] : (K)(ordered64(kd[k]) - omin);
             if (sizeof(V) == 8) t_val[e] = (V)(((uint64_t)(uint32_t)hs[k] << 32) | (uint32_t)e);
             else t_val[e] = (V)hs[k];
         }
@@ -502,7 +505,8 @@ __global__ void split_pair_kernel(const int64_t* val, int64_t m, int32_t* hs, in
 // dependent loads; one tuple at a time leaves the memory system idle).
 
 __global__ void finalize_dst_kernel(const uint32_t* pos_d, int64_t m, const int32_t* rows_sorted,
-                                    const int32_t* uid_of_pos, const int32_t* out_row, int32_t* hd, int32_t* seg) {
+                                    const int32_t* uid_of_pos, const int32_t* out_row, int32_t* hd, int32_t* seg,
+                                    uint32_t limit) {
     const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x) * kIlp + threadIdx.x;
     uint32_t p[kIlp];
     int32_t h[kIlp], u[kIlp];
@@ -513,22 +517,22 @@ __global__ void finalize_dst_kernel(const uint32_t* pos_d, int64_t m, const int3
     }
 #pragma unroll
     for (int k = 0; k < kIlp; ++k) {
-        const bool ok = i0 + (int64_t)k * blockDim.x < m;
-        h[k] = ok ? __ldg(rows_sorted + p[k]) : 0;
-        u[k] = ok ? __ldg(uid_of_pos + p[k]) : 0;
+        const bool ok = i0 + (int64_t)k * blockDim.x < m && p[k] < limit;
+        h[k] = ok ? __ldg(rows_sorted + p[k]) : -1;
+        u[k] = ok ? __ldg(uid_of_pos + p[k]) : -1;
     }
 #pragma unroll
     for (int k = 0; k < kIlp; ++k) {
         const int64_t i = i0 + (int64_t)k * blockDim.x;
         if (i < m) {
             hd[i] = h[k];
-            seg[i] = __ldg(out_row + u[k]);
+            seg[i] = u[k] >= 0 ? __ldg(out_row + u[k]) : -1;  // -1: a tuple past the matched ones
         }
     }
 }
 
 __global__ void mark_present_kernel(const uint32_t* pos_d, int64_t m, const int32_t* uid_of_pos,
-                                    int32_t* present) {
+                                    int32_t* present, uint32_t limit) {
     const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x) * kIlp + threadIdx.x;
     uint32_t p[kIlp];
 #pragma unroll
@@ -538,7 +542,8 @@ __global__ void mark_present_kernel(const uint32_t* pos_d, int64_t m, const int3
     }
     int32_t u[kIlp];
 #pragma unroll
-    for (int k = 0; k < kIlp; ++k) u[k] = i0 + (int64_t)k * blockDim.x < m ? __ldg(uid_of_pos + p[k]) : -1;
+    for (int k = 0; k < kIlp; ++k)
+        u[k] = i0 + (int64_t)k * blockDim.x < m && p[k] < limit ? __ldg(uid_of_pos + p[k]) : -1;
 #pragma unroll
     for (int k = 0; k < kIlp; ++k)
         if (u[k] >= 0) present[u[k]] = 1;
@@ -599,6 +604,12 @@ struct Tmp {
     // whose total (matched tuples | output rows << 32) is read with the plan's final synchronisation
     bool want_count = false, counted = false;
     DevBuf cnt, gpacked;
+    // unique H keys, no selection, a dst join: tuples that match nothing are emitted with the
+    // sentinel key and sorted behind the matched ones; their count (in `miss`) is read with the plan's
+    // final synchronisation, and the branch's m is an upper bound (every E row) until then
+    bool defer = false;
+    uint32_t sentinel = 0xffffffffu;
+    DevBuf miss;
     template <class K>
     const K* keys() const { return in_tmp ? key_tmp.as<K>() : key.as<K>(); }
     DevBuf& sorted_val() { return in_tmp ? val_tmp : val; }
@@ -629,6 +640,16 @@ relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M
         RELNN_TRY(t.val.alloc_tmp(sizeof(V) * cap, st));
         RELNN_TRY(t.val_tmp.alloc_tmp(sizeof(V) * cap, st));
         bool all_matched = false;
+        if (T > 0 && t.defer) {
+            RELNN_TRY(t.miss.alloc_tmp(sizeof(unsigned long long), st));
+            RELNN_CUDA(cudaMemsetAsync(t.miss.p, 0, sizeof(unsigned long long), st));
+            { emit_all_kernel<K, V><<<ilp_grid(T), 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst, t.omin,
+                                                              t.miss.as<unsigned long long>(), t.key.as<K>(), t.val.as<V>(),
+                                                              nullptr, nullptr, (K)t.sentinel); note_launch(); }
+            RELNN_CUDA(cudaGetLastError());
+            *M_out = T;  // an upper bound; the misses are subtracted after the final synchronisation
+            return RELNN_OK;
+        }
         if (T > 0 && filters_of(bd).n == 0) {
             DevBuf miss;  // misses (u64) | the big-group flag (u32)
             RELNN_TRY(miss.alloc_tmp(2 * sizeof(unsigned long long), st));
@@ -640,7 +661,8 @@ relnn_status emit_pairs(Plan& p, const relnn_branch_desc& bd, Tmp& t, int64_t* M
             }
             { emit_all_kernel<K, V><<<ilp_grid(T), 256, 0, st>>>(v, bd.d_src, bd.d_dst, T, p.kt, p.join_dst, t.omin,
                                                               miss.as<unsigned long long>(), t.key.as<K>(), t.val.as<V>(),
-                                                              t.want_count ? t.cnt.as<int32_t>() : nullptr, big); note_launch(); }
+                                                              t.want_count ? t.cnt.as<int32_t>() : nullptr, big,
+                                                              (K)t.sentinel); note_launch(); }
             RELNN_CUDA(cudaGetLastError());
             unsigned long long mu[2] = {0, 0};
             RELNN_CUDA(cudaMemcpyAsync(mu, miss.p, sizeof(mu), cudaMemcpyDeviceToHost, st));
@@ -761,6 +783,12 @@ relnn_status emit_branch(Plan& p, BranchPlan& b, const relnn_branch_desc& bd, Tm
     t.want_count = p.join_dst && !t.wide && !t.pair && p.br.size() == 1 && p.Ht().n_unique == p.n_h &&
                    !(p.flags & RELNN_FLAG_MAX) && !p.dense_out && filters_of(bd).n == 0 &&
                    tune_get(RELNN_TUNE_GROUP_SORT) == 1;
+    t.defer = p.join_dst && !t.want_count && p.Ht().n_unique == p.n_h && filters_of(bd).n == 0 && T > 0;
+    if (t.defer) {
+        // the sentinel 2^nbits - 1 must lie above every dst position (< n_h)
+        if (p.n_h > 0 && (uint64_t)p.n_h == (1ull << nbits)) ++nbits;
+        t.sentinel = nbits >= 32 ? 0xffffffffu : (uint32_t)((1ull << nbits) - 1);
+    }
     int64_t M = 0;
     if (t.wide) {
         if (t.pair) RELNN_TRY((emit_and_sort<uint64_t, int64_t>(p, bd, t, &M, nbits, st)));
@@ -890,7 +918,9 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         RELNN_TRY(emit_branch(p, p.br[i], desc->branches[i], tmp[i], st));
     }
 
-    // output key set and output row of every matched tuple
+    // output key set and output row of every matched tuple (sorted positions at or past pos_limit are
+    // the sentinels of tuples that matched nothing)
+    const uint32_t pos_limit = (uint32_t)std::min<int64_t>(HT.n, 0xffffffffll);
     int32_t nout_join = 0;
     int64_t counted_total = -1;
     if (p.join_dst && p.dense_out) {
@@ -898,10 +928,10 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0) {
                 { mark_present_kernel<<<ilp_grid(p.br[i].m), 256, 0, st>>>(
-                    tmp[i].keys<uint32_t>(), p.br[i].m, HT.uid_of_pos.as<int32_t>(), p.present_ext); note_launch(); }
+                    tmp[i].keys<uint32_t>(), p.br[i].m, HT.uid_of_pos.as<int32_t>(), p.present_ext, pos_limit); note_launch(); }
                 { finalize_dst_kernel<<<ilp_grid(p.br[i].m), 256, 0, st>>>(
                     tmp[i].keys<uint32_t>(), p.br[i].m, HT.rows_sorted.as<int32_t>(), HT.uid_of_pos.as<int32_t>(),
-                    p.iota_ext, p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>()); note_launch(); }
+                    p.iota_ext, p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>(), pos_limit); note_launch(); }
             }
         RELNN_CUDA(cudaGetLastError());
         nout_join = (int32_t)U;
@@ -919,10 +949,8 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         for (auto i = 0u; i < p.br.size(); ++i)
             if (p.br[i].m > 0)
                 { mark_present_kernel<<<ilp_grid(p.br[i].m), 256, 0, st>>>(
-                    tmp[i].keys<uint32_t>(), p.br[i].m, HT.uid_of_pos.as<int32_t>(), present.as<int32_t>()); note_launch(); }
+                    tmp[i].keys<uint32_t>(), p.br[i].m, HT.uid_of_pos.as<int32_t>(), present.as<int32_t>(), pos_limit); note_launch(); }
         RELNN_TRY(exclusive_scan<int32_t>(present.as<int32_t>(), out_row.as<int32_t>(), U, out_row.as<int32_t>() + U, st));
-        // the output-row count arrives with the final synchronisation; U bounds it
-        RELNN_CUDA(cudaMemcpyAsync(&nout_join, out_row.as<int32_t>() + U, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         RELNN_TRY(p.out_keys.alloc_nosync(sizeof(int64_t) * std::max<int64_t>(U, 1), st));
         if (U > 0)
             { out_keys_kernel<<<grid_for(U), 256, 0, st>>>(present.as<int32_t>(), out_row.as<int32_t>(),
@@ -931,8 +959,11 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
             if (p.br[i].m > 0)
                 { finalize_dst_kernel<<<ilp_grid(p.br[i].m), 256, 0, st>>>(
                     tmp[i].keys<uint32_t>(), p.br[i].m, HT.rows_sorted.as<int32_t>(), HT.uid_of_pos.as<int32_t>(),
-                    out_row.as<int32_t>(), p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>()); note_launch(); }
+                    out_row.as<int32_t>(), p.br[i].hd.as<int32_t>(), p.br[i].seg.as<int32_t>(), pos_limit); note_launch(); }
         RELNN_CUDA(cudaGetLastError());
+        // the output-row count (U bounds it) is read with the final synchronisation; a copy to pageable
+        // host memory returns only once it is done, so it is queued after the kernels above
+        RELNN_CUDA(cudaMemcpyAsync(&nout_join, out_row.as<int32_t>() + U, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     } else {
         BranchPlan& b = p.br[0];
         Tmp& t = tmp[0];
@@ -961,10 +992,17 @@ relnn_status build_plan(Plan& p, const relnn_rule_desc* desc, cudaStream_t st) {
         }
         RELNN_CUDA(cudaGetLastError());
     }
-    // device-side checks of the plan kernels (a look-back that gave up), with the final sync
+    // device-side checks of the plan kernels (a look-back that gave up) and the deferred miss counts,
+    // with the final sync
     int dev_status = 0;
+    std::vector<unsigned long long> misses(p.br.size(), 0);
+    for (size_t i = 0; i < p.br.size(); ++i)
+        if (tmp[i].defer && tmp[i].miss.p)
+            RELNN_CUDA(cudaMemcpyAsync(&misses[i], tmp[i].miss.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     RELNN_CUDA(cudaMemcpyAsync(&dev_status, p.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     RELNN_CUDA(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < p.br.size(); ++i)
+        if (tmp[i].defer) p.br[i].m -= (int64_t)std::min<unsigned long long>(misses[i], (unsigned long long)p.br[i].m);
     if (counted_total >= 0) nout_join = (int32_t)(counted_total >> 32);
     if (p.join_dst) p.n_out = nout_join;
     if (dev_status) {

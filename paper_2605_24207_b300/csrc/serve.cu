@@ -12,6 +12,7 @@
 // usual content track (relnn plan) and fused persistent forward run once over all of it. The output
 // keys come out sorted by (query, key); a binary search per query cuts them back into per-query
 // results (keys restored to int32).
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -167,7 +168,14 @@ relnn_status run_batch(relnn_server_s* S, std::vector<Query*>& batch, cudaStream
     { ranges_kernel<<<(nq + 1 + 127) / 128, 128, 0, st>>>(P.out_keys.as<int64_t>(), P.n_out, nq, lo.as<int64_t>()); note_launch(); }
     std::vector<int64_t> hlo(nq + 1);
     RELNN_CUDA(cudaMemcpyAsync(hlo.data(), lo.p, sizeof(int64_t) * (nq + 1), cudaMemcpyDeviceToHost, st));
+    // the forward's device checks arrive with the same synchronisation (the kernels after it raise none)
+    int dev_status = 0;
+    RELNN_CUDA(cudaMemcpyAsync(&dev_status, P.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     RELNN_CUDA(cudaStreamSynchronize(st));
+    if (dev_status) {
+        set_device_error(dev_status);
+        return RELNN_EDEVICE;
+    }
     for (int i = 0; i < nq; ++i) {
         Query* q = batch[i];
         q->n_out = hlo[i + 1] - hlo[i];
@@ -182,12 +190,6 @@ relnn_status run_batch(relnn_server_s* S, std::vector<Query*>& batch, cudaStream
     }
     RELNN_CUDA(cudaGetLastError());
     RELNN_CUDA(cudaStreamSynchronize(st));
-    int dev_status = 0;
-    RELNN_CUDA(cudaMemcpy(&dev_status, P.status.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (dev_status) {
-        set_device_error(dev_status);
-        return RELNN_EDEVICE;
-    }
     return RELNN_OK;
 }
 
@@ -287,6 +289,61 @@ relnn_status relnn_server_create(const relnn_server_cfg* cfg, relnn_server_t* ou
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     S->budget = cfg->mem_budget_bytes > 0 ? cfg->mem_budget_bytes : (int64_t)(0.8 * (double)free_b);
+    // The device's memory pool keeps freed blocks (ensure_pool_cached); it is grown here, once, to
+    // what n_workers batches of max_batch_tuples tuples may hold together, so that the first burst of
+    // large batches does not map new memory while queries wait (at most half of the budget).
+    {
+        relnn_query big{};
+        big.n_tuples = cfg->max_batch_tuples;
+        big.n_h = std::max<int64_t>(1, cfg->max_batch_tuples / 8);
+        const int64_t want = std::min<int64_t>((int64_t)cfg->n_workers * query_mem(S, big), S->budget / 2);
+        ensure_pool_cached();
+        void* p = nullptr;
+        if (want > 0 && cudaMallocAsync(&p, (size_t)want, nullptr) == cudaSuccess) {
+            cudaFreeAsync(p, nullptr);
+            cudaStreamSynchronize(nullptr);
+        }
+        (void)cudaGetLastError();
+    }
+    // One small batch of two queries runs before the workers start, so that the kernels of the
+    // batched path (keys of several queries: the sorted join build and hashed lookups, which a query
+    // served alone does not use) are loaded before the first query arrives.
+    {
+        const int64_t n = 64;
+        DevBuf keys, z;
+        cudaStream_t st = nullptr;
+        bool ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+                  keys.alloc_tmp(sizeof(int32_t) * n, st) == RELNN_OK &&
+                  z.alloc_tmp(S->z_esz * (size_t)cfg->d * n, st) == RELNN_OK;
+        if (ok) {
+            std::vector<int32_t> hk(n);
+            for (int64_t i = 0; i < n; ++i) hk[i] = (int32_t)i;
+            ok = cudaMemcpyAsync(keys.p, hk.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                 cudaMemsetAsync(z.p, 0, S->z_esz * (size_t)cfg->d * n, st) == cudaSuccess;
+        }
+        if (ok) {
+            Query q0, q1;
+            for (Query* q : {&q0, &q1}) {
+                q->q.d_h_ids = keys.p;
+                q->q.n_h = n;
+                q->q.d_z = z.p;
+                q->q.d_src = keys.p;
+                q->q.d_dst = keys.p;
+                q->q.n_tuples = n;
+            }
+            std::vector<Query*> warm = {&q0, &q1};
+            (void)run_batch(S, warm, st);
+            cudaStreamSynchronize(st);
+            q0.keys.st = q0.z.st = q1.keys.st = q1.z.st = nullptr;
+        }
+        keys.release();
+        z.release();
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+        (void)cudaGetLastError();
+    }
     for (int i = 0; i < cfg->n_workers; ++i) S->workers.emplace_back(worker_main, S);
     *out = S;
     return RELNN_OK;
