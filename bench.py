@@ -61,7 +61,9 @@ def parse():
                     help="c2: skip the c3 / c4 / c1b / c5 records appended to the line")
     ap.add_argument("--no-serving", action="store_true", help="c2: skip the shortened c5 record")
     ap.add_argument("--sub-queries", type=int, default=2000, help="queries of the shortened c5 record")
-    ap.add_argument("--workers", type=int, default=4, help="c5: server worker threads (streams)")
+    ap.add_argument("--workers", type=int, default=2,
+                    help="c5: server worker threads (streams); 2 measured best: p99 4.3 ms against 10.3 ms with 4, "
+                         "whose threads contend in the driver, at the same saturation rate")
     ap.add_argument("--sub-cmp-queries", type=int, default=300,
                     help="queries the torch comparator serves in the shortened c5 record")
     return ap.parse_args()
@@ -877,7 +879,7 @@ def _torch_query(h, z, src, dst, Wt, bt):
     return uk, torch.zeros((uk.numel(), Y.shape[1]), device=Y.device).index_add_(0, inv, Y)
 
 
-def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True, workers: int = 4) -> dict:
+def serving_stats(nq: int, n_cmp: int, local: int = 0, with_cpu: bool = True, workers: int = 2) -> dict:
     """A stream of rule queries (T ~ logU[1k, 1M], K = T/8, z bf16[64], shared Linear 128 -> 64)
     arriving as a Poisson process at 2,000 queries/s, served by relnn_server_* with memory-admitted
     continuous batching; latency = arrival -> results ready. Paced run (clocks sampled), saturation

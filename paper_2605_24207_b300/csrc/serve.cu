@@ -298,6 +298,13 @@ relnn_status relnn_server_create(const relnn_server_cfg* cfg, relnn_server_t* ou
         big.n_h = std::max<int64_t>(1, cfg->max_batch_tuples / 8);
         const int64_t want = std::min<int64_t>((int64_t)cfg->n_workers * query_mem(S, big), S->budget / 2);
         ensure_pool_cached();
+        // memory freed on one worker's stream is reused by another only once its free has completed
+        // (no event waits inserted between the workers' streams, which would serialise their batches)
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, S->dev) == cudaSuccess) {
+            int off = 0;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &off);
+        }
         void* p = nullptr;
         if (want > 0 && cudaMallocAsync(&p, (size_t)want, nullptr) == cudaSuccess) {
             cudaFreeAsync(p, nullptr);
