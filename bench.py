@@ -273,6 +273,17 @@ class C2:
                 R.PROF_AGG_FWD: ("agg_gemm_kernel (TMA + tcgen05 GEMM)", float(gb), "hbm"),
                 R.PROF_FWD_TC: ("fwd_tc_kernel", 2.0 * (2 * self.d) * self.d_out * self.matched, "tensor")}
 
+    def ncu_traffic(self):
+        """DRAM bytes (read + write) per launch of the step's kernels, from one ncu capture of this
+        workload at its default size (profiles/seg_sum_kernel_rule_c2_16M.md): the two-kernel
+        aggregate-first forward only; None for other sizes or forms."""
+        from paper_2605_24207_b300 import relnn as R
+        if (self.n_tuples, self.n_keys, self.agg) != (16_000_000, 1_000_000, "sum") or not self.agg_form:
+            return None
+        if self.flags & (R.FLAG_PER_TUPLE | R.FLAG_PUSHDOWN) or R.tune_get(R.TUNE_AGG_FUSE):
+            return None
+        return {R.PROF_AGG_SUM: 482_404_864 + 472_642_304, R.PROF_AGG_FWD: 788_304_128 + 462_580_992}
+
     def agg_bytes(self):
         """(gather-sum bytes, GEMM bytes) per forward."""
         n_h = int(self.t["h"].numel())
@@ -810,6 +821,9 @@ class C1B:
         p = R.RulePlan(self.t["h"], [(self.t["src"], self.t["dst"])], 16, 16)
         self.matched, self.n_out = p.n_matched, p.n_out
         self.out = torch.empty((self.n_out, 16), dtype=torch.float32, device=dev)
+        # virtual rows of the aggregate-first forward: one per output row, or per 32 tuples of one
+        _, cnt = np.unique(self.dst, return_counts=True)
+        self.n_vrows = int(((cnt + 31) // 32).sum())
 
     def step(self):
         from paper_2605_24207_b300 import relnn as R
@@ -821,8 +835,13 @@ class C1B:
 
     def kernels(self):
         from paper_2605_24207_b300 import relnn as R
-        # f32 FMA on CUDA cores: 2 x 32 x 16 FLOP per tuple against the measured FMA probe
-        return {R.PROF_FWD_FP32: ("fwd_fp32_lane_kernel", 2.0 * 32 * 16 * self.matched, "alu")}
+        # the FP32 form aggregate-first (the rule is linear, its H keys unique): per matched tuple its
+        # 4-byte src row index, per virtual row its 16-byte descriptor and 4-byte dst row index, each
+        # H row once (f32[16]) and each output row once (f32[16]); its FLOPs (2 x 32 x 16 per virtual
+        # row, 16 per tuple) are a small share of the FMA probe's rate, so the bound is HBM
+        n_h = int(self.t["h"].numel())
+        work = 4 * self.matched + 20 * self.n_vrows + 64 * n_h + 64 * self.n_out
+        return {R.PROF_FWD_FP32: ("fwd_fp32_agg_kernel (FP32 form, aggregate-first)", float(work), "hbm")}
 
     def e2e_setup(self):
         import torch
@@ -1171,6 +1190,8 @@ def run_relnn(args):
             if other is not None:
                 r["frac_other_bf16_peak"] = achieved / other
                 r["other_bf16_peak"] = other
+            if traffic and traffic.get(kid) is not None:
+                r["traffic"] = traffic[kid]
             rows[kid] = r
         if not rows:
             return None, []

@@ -859,6 +859,125 @@ __global__ void vr_first_kernel(const int4* __restrict__ vr, int64_t nv, const i
     }
 }
 
+// ------------------------------------------------------------------------------ FP32 form
+// Aggregate-first forward of the FP32 form (f32 arithmetic on CUDA cores, no tensor cores) for linear
+// rules with narrow rows: lane = one virtual row. The lane sums its tuples' src rows in f32 in tuple
+// order (compensated with KAHAN), then applies the Linear once:
+//     y = W_src S + n (W_dst z_dst + b)
+// with W and b in shared memory (every lane reads the same element: a broadcast). A row cut into
+// chunks leaves one partial per chunk, added in chunk order by the fix-up. The per-tuple FP32 form
+// computes the same rule; the two differ by the order of f32 additions only.
+constexpr int kF32Batch = 4;  // tuples of a lane whose row loads are in flight together
+
+template <int D, bool CDST, bool KAHAN>
+__global__ void __launch_bounds__(256) fwd_fp32_agg_kernel(const int4* __restrict__ vr, int64_t nv,
+                                                        const int32_t* __restrict__ hs,
+                                                        const int32_t* __restrict__ d1,
+                                                        const float* __restrict__ z, int64_t z_rows,
+                                                        const float* __restrict__ W, const float* __restrict__ bias,
+                                                        int d_out, float* __restrict__ out, int64_t out_rows,
+                                                        float* __restrict__ vpart, int accumulate, int* status) {
+    constexpr int D4 = D / 4;
+    constexpr int DIN4 = CDST ? 2 * D4 : D4;
+    extern __shared__ float4 s_w4[];  // W [d_out][d_in / 4] (the src part, then the dst part), then b
+    float* s_b = reinterpret_cast<float*>(s_w4 + (size_t)d_out * DIN4);
+    for (int i = threadIdx.x; i < d_out * DIN4; i += blockDim.x) s_w4[i] = __ldg(reinterpret_cast<const float4*>(W) + i);
+    for (int i = threadIdx.x; i < d_out; i += blockDim.x) s_b[i] = bias ? __ldg(bias + i) : 0.f;
+    __syncthreads();
+    const float4* __restrict__ z4 = reinterpret_cast<const float4*>(z);
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        const int4 m = __ldg(vr + v);  // {first tuple, tuples, output row, chunk slot or -1}
+        const int n = m.y > 0 ? m.y : 0;
+        // the dst row's index and row are loaded with the first tuples' (one round trip each)
+        const int rd = CDST && n > 0 ? __ldg(d1 + v) : -1;
+        float sx[D], cx[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) sx[k] = cx[k] = 0.f;
+        float4 g[CDST ? D4 : 1];
+        for (int t0 = 0; t0 < n; t0 += kF32Batch) {
+            int r[kF32Batch];
+#pragma unroll
+            for (int q = 0; q < kF32Batch; ++q) r[q] = t0 + q < n ? __ldg(hs + m.x + t0 + q) : -1;
+            if (CDST && t0 == 0) {
+                const bool ok = rd >= 0 && in_bounds(rd, z_rows, status);
+#pragma unroll
+                for (int c = 0; c < D4; ++c) g[c] = ok ? __ldg(z4 + (int64_t)rd * D4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            float4 f[kF32Batch][D4];
+#pragma unroll
+            for (int q = 0; q < kF32Batch; ++q) {
+                const bool ok = r[q] >= 0 && in_bounds(r[q], z_rows, status);
+#pragma unroll
+                for (int c = 0; c < D4; ++c)
+                    f[q][c] = ok ? __ldg(z4 + (int64_t)r[q] * D4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < kF32Batch; ++q) {
+                if (t0 + q >= n) break;
+#pragma unroll
+                for (int c = 0; c < D4; ++c) {
+                    const float e[4] = {f[q][c].x, f[q][c].y, f[q][c].z, f[q][c].w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (KAHAN) kahan_add(sx[4 * c + j], cx[4 * c + j], e[j]);
+                        else sx[4 * c + j] += e[j];
+                    }
+                }
+            }
+        }
+        if (KAHAN) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) sx[k] -= cx[k];
+        }
+        float zd[CDST ? D : 1];
+        if (CDST) {
+#pragma unroll
+            for (int c = 0; c < D4; ++c) {
+                const float4 gg = n > 0 ? g[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                zd[4 * c] = gg.x;
+                zd[4 * c + 1] = gg.y;
+                zd[4 * c + 2] = gg.z;
+                zd[4 * c + 3] = gg.w;
+            }
+        }
+        const bool part = m.w >= 0;
+        if (!part && !in_bounds(m.z, out_rows, status)) continue;
+        float* dst = part ? vpart + (int64_t)m.w * d_out : out + (int64_t)m.z * d_out;
+        const float fn = (float)n;
+        // four outputs at a time, stored as one 16-byte write (d_out is a multiple of 4)
+        for (int o0 = 0; o0 < d_out; o0 += 4) {
+            float y[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4* wr = s_w4 + (size_t)(o0 + j) * DIN4;
+                float ys = 0.f, yd = 0.f;
+#pragma unroll
+                for (int c = 0; c < D4; ++c) {
+                    const float4 w = wr[c];
+                    ys = fmaf(w.x, sx[4 * c], ys);
+                    ys = fmaf(w.y, sx[4 * c + 1], ys);
+                    ys = fmaf(w.z, sx[4 * c + 2], ys);
+                    ys = fmaf(w.w, sx[4 * c + 3], ys);
+                    if (CDST) {
+                        const float4 u = wr[D4 + c];
+                        yd = fmaf(u.x, zd[4 * c], yd);
+                        yd = fmaf(u.y, zd[4 * c + 1], yd);
+                        yd = fmaf(u.z, zd[4 * c + 2], yd);
+                        yd = fmaf(u.w, zd[4 * c + 3], yd);
+                    }
+                }
+                y[j] = fmaf(fn, yd + s_b[o0 + j], ys);
+            }
+            if (part || !accumulate) {
+                *reinterpret_cast<float4*>(dst + o0) = make_float4(y[0], y[1], y[2], y[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) emit_out(dst + o0 + j, y[j], 1);
+            }
+        }
+    }
+}
+
 // warps 0-2 loaders, 3 MMA, 4.. epilogue: EPI = 4 (one per TMEM lane quarter) or 8 (two per quarter,
 // each on every other 32-row chunk of a tile)
 constexpr int kGemmLoaders = 96;
@@ -1806,6 +1925,28 @@ AggCfg fwd_cfg(const Plan& p) {
     return agg_config(n_parts * kpad / 64, (p.d_out + 127) / 128, false, 0, 0, 0);
 }
 
+template <int D, bool CDST>
+relnn_status launch_fp32_agg_t(bool kahan, int grid, size_t smem, cudaStream_t st, const int4* vr, int64_t nv,
+                               const int32_t* hs, const int32_t* d1, const float* z, int64_t z_rows, const float* W,
+                               const float* b, int d_out, float* out, int64_t out_rows, float* vpart, int acc,
+                               int* status) {
+    // W above 48 KB (d_out x d_in floats) needs the larger dynamic shared-memory limit
+    static size_t attr[2] = {0, 0};
+    if (smem > 48 * 1024 && attr[kahan ? 1 : 0] < smem) {
+        if (kahan) RELNN_CUDA(cudaFuncSetAttribute(fwd_fp32_agg_kernel<D, CDST, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else RELNN_CUDA(cudaFuncSetAttribute(fwd_fp32_agg_kernel<D, CDST, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr[kahan ? 1 : 0] = smem;
+    }
+    if (kahan) { fwd_fp32_agg_kernel<D, CDST, true><<<grid, 256, smem, st>>>(vr, nv, hs, d1, z, z_rows, W, b, d_out, out,
+                                                                          out_rows, vpart, acc, status); note_launch(); }
+    else { fwd_fp32_agg_kernel<D, CDST, false><<<grid, 256, smem, st>>>(vr, nv, hs, d1, z, z_rows, W, b, d_out, out,
+                                                                     out_rows, vpart, acc, status); note_launch(); }
+    RELNN_CUDA(cudaGetLastError());
+    return RELNN_OK;
+}
+
 }  // namespace
 
 namespace {
@@ -1841,6 +1982,66 @@ bool agg_backward_ok(const Plan& p, const CallIO& io, const GradIO& g) {
     if (!pow2_in(p.d_out, 8, 256) || p.d % 32 != 0) return false;
     return g.dout != nullptr && aligned16(g.dout) &&
            gemm_config((p.d_out + 63) / 64, (p.d + 63) / 64, (p.d + 127) / 128, true, (p.d_out + 127) / 128, p.d).N > 0;
+}
+
+bool agg_forward_fp32_ok(const Plan& p, const CallIO& io, const float* out) {
+    if (p.bf16 || p.identity || p.act != RELNN_ACT_NONE || !p.join_dst) return false;
+    if (p.flags & (RELNN_FLAG_MAX | RELNN_FLAG_PUSHDOWN | RELNN_FLAG_PER_TUPLE | kPlanDense)) return false;
+    if (p.Hx || p.dense_out || p.acc_out) return false;
+    if (p.concat_dst && p.Ht().n_unique != p.n_h) return false;  // one dst H row per virtual row
+    if (!(p.d == 4 || p.d == 8 || p.d == 16 || p.d == 32) || p.d_out % 4 != 0 || p.d_out > 256) return false;
+    if (io.z_bf16 || io.w_bf16 || !aligned16(io.z) || !aligned16(out)) return false;
+    for (size_t i = 0; i < p.br.size(); ++i)
+        if (p.br[i].d_r > 0 || !aligned16(io.br[i].W)) return false;
+    return true;
+}
+
+relnn_status forward_agg_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
+    size_t vp_max = 0;
+    for (auto& b : p.br) {
+        VRows& V = b.vr_out;
+        RELNN_TRY(ensure_vrows(V, b.seg.as<int32_t>(), b.m, p.n_out, true, st));
+        if (p.concat_dst && !V.has_d1) {
+            RELNN_TRY(V.d1.alloc_nosync(sizeof(int32_t) * std::max<int64_t>(V.nv, 1), st));
+            if (V.nv > 0) { vr_first_kernel<<<grid_for(V.nv), 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hd.as<int32_t>(), V.d1.as<int32_t>()); note_launch(); }
+            RELNN_CUDA(cudaGetLastError());
+            V.has_d1 = true;
+        }
+        vp_max = std::max(vp_max, (size_t)(V.n_parts + V.n_l2) * p.d_out);
+    }
+    if (vp_max) RELNN_TRY(p.vpart.alloc_nosync(sizeof(float) * vp_max, st));
+    const size_t smem = sizeof(float) * ((size_t)p.d_out * p.d_in + p.d_out);
+    for (size_t i = 0; i < p.br.size(); ++i) {
+        BranchPlan& b = p.br[i];
+        const VRows& V = b.vr_out;
+        if (V.nv == 0) continue;
+        const int grid = grid_for(V.nv);
+        const float* z = reinterpret_cast<const float*>(io.z);
+        const float* W = reinterpret_cast<const float*>(io.br[i].W);
+        const int32_t* d1 = p.concat_dst ? V.d1.as<int32_t>() : nullptr;
+        const int acc = i > 0 ? 1 : 0;  // every branch covers every output row: the first one stores
+        ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st);
+        relnn_status s = RELNN_OK;
+#define RELNN_F32AGG(DD)                                                                                            \
+        s = p.concat_dst ? launch_fp32_agg_t<DD, true>(p.kahan, grid, smem, st, V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), \
+                                                       d1, z, p.n_h, W, io.br[i].b, p.d_out, out, p.n_out,             \
+                                                       p.vpart.as<float>(), acc, p.status.as<int>())                   \
+                         : launch_fp32_agg_t<DD, false>(p.kahan, grid, smem, st, V.vr.as<int4>(), V.nv,                \
+                                                        b.hs.as<int32_t>(), d1, z, p.n_h, W, io.br[i].b, p.d_out, out, \
+                                                        p.n_out, p.vpart.as<float>(), acc, p.status.as<int>())
+        switch (p.d) {
+            case 4: RELNN_F32AGG(4); break;
+            case 8: RELNN_F32AGG(8); break;
+            case 16: RELNN_F32AGG(16); break;
+            default: RELNN_F32AGG(32); break;
+        }
+#undef RELNN_F32AGG
+        prof_end(pt, st);
+        RELNN_TRY(s);
+        RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d_out, out, p.d_out, i > 0,
+                            p.kahan, p.n_out, p.status.as<int>(), st));
+    }
+    return RELNN_OK;
 }
 
 // Two-kernel forward (unique H keys or no dst part): gather-sum into S, then the TMA-fed GEMM.

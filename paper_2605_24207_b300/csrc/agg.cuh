@@ -16,6 +16,11 @@ bool agg_forward_ok(const Plan& p, const CallIO& io, const float* out);
 bool agg_backward_ok(const Plan& p, const CallIO& io, const GradIO& g);
 
 relnn_status forward_agg(Plan& p, const CallIO& io, float* out, cudaStream_t st);
+// FP32 form (f32 on CUDA cores), aggregate-first: no activation, SUM or MEAN, no per-tuple
+// embedding, unique H keys (or no dst part), d in {4, 8, 16, 32}, d_out a multiple of 4 (<= 256),
+// f32 z and W, z / W / out 16-byte aligned, RELNN_FLAG_PER_TUPLE not set, not a streamed chunk.
+bool agg_forward_fp32_ok(const Plan& p, const CallIO& io, const float* out);
+relnn_status forward_agg_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 relnn_status backward_agg(Plan& p, const CallIO& io, const GradIO& g, cudaStream_t st);
 
 // 2-D bf16 tensor map over a row-major [rows][cols] matrix, box 64 columns x box_rows rows, 128-byte

@@ -2,6 +2,7 @@
 // the FP64 definition to ~1e-5 relative. One block owns 32-tuple tiles in turn; one thread owns one
 // output feature o and keeps y[t][o] for the tile's 32 tuples in registers, so the SUM over a run of
 // equal output rows is a sequential walk in registers (Sec. 2.2 projected union with SUM).
+#include "agg.cuh"
 #include "fwd.cuh"
 #include "maxagg.cuh"
 
@@ -530,6 +531,8 @@ relnn_status launch_fixup(const int32_t* seg, int64_t m, int tile, int64_t n_til
 
 relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
     RELNN_CHECK_ARG(p.d_in <= 1024 && p.d_out <= 256, "FP32 form: d_in <= 1024 and d_out <= 256 required");
+    // linear rules with narrow rows: the SUM first, then the Linear once per output row (agg.cu)
+    if (agg_forward_fp32_ok(p, io, out)) return forward_agg_fp32(p, io, out, st);
     // several branches add into one output; a stream chunk adds into the stream's accumulator
     const bool multi = p.br.size() > 1 || p.acc_out;
     if (p.br.size() > 1 && !p.acc_out) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));

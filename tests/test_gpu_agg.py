@@ -277,3 +277,55 @@ def test_fused_forward(gpu, fuse, case):
         assert rel_frob(out, out2.astype(np.float64)) <= 1e-5
     finally:
         R.tune_set(R.TUNE_AGG_FUSE, saved)
+
+
+FP32_TOL = 1e-5
+
+
+@pytest.mark.parametrize("case", ["c1", "d4", "d8_dout64", "d32_dout256", "hubs_kahan", "two_level", "union",
+                                  "no_concat_dst", "mean", "dup_keys_falls_back", "f32_instances"])
+def test_fp32_aggregate_first_forward(gpu, case):
+    """The FP32 form's aggregate-first forward (f32 on CUDA cores: each output row's src rows summed
+    first, the Linear applied once per row) against the FP64 oracle at the FP32 bar (1e-5) and
+    against the per-tuple FP32 form (RELNN_FLAG_PER_TUPLE) on the same inputs; key sets and join
+    sizes bit-exact. Covers every supported width, rows cut into chunks (hubs; more than 256 chunks:
+    the two-level fix-up), Kahan, unions, no dst part, MEAN and a plan with duplicate H keys (which
+    takes the per-tuple form)."""
+    flags, kw = 0, {}
+    if case == "c1":
+        rel = W.config1(0)
+    elif case == "d4":
+        rel = W.make_rule(151, 30_011, 2000, 4, 8, np.int32, src_dist="zipf", src_s=1.1)
+    elif case == "d8_dout64":
+        rel = W.make_rule(152, 20_000, 1500, 8, 64, np.int64, sparse_keys=True, missing_frac=0.05)
+    elif case == "d32_dout256":
+        rel = W.make_rule(153, 10_000, 800, 32, 256, np.int32)
+    elif case == "hubs_kahan":
+        rel, flags = W.make_rule(154, 60_000, 3000, 16, 16, np.int32, dst_dist="zipf", dst_s=1.3), R.FLAG_KAHAN
+    elif case == "two_level":
+        rel = W.make_rule(155, 40_000, 200, 16, 32, np.int32, dst_dist="zipf", dst_s=2.0)
+    elif case == "union":
+        rel = W.make_rule(156, 0, 3000, 16, 16, np.int32, dst_dist="zipf", dst_s=1.0,
+                          branch_tuples=[20_000, 10_000, 5000])
+    elif case == "no_concat_dst":
+        rel = W.make_rule(157, 10_000, 900, 16, 16, np.int32)
+        rel.branches[0].W = np.ascontiguousarray(rel.branches[0].W[:, :16])
+        flags, kw = R.FLAG_NO_CONCAT_DST, dict(concat_dst=False)
+    elif case == "mean":
+        rel, flags = W.make_rule(158, 20_000, 1500, 16, 16, np.int32, dst_dist="zipf", dst_s=1.2), R.FLAG_MEAN
+    elif case == "dup_keys_falls_back":
+        rel = W.make_rule(159, 8000, 600, 16, 16, np.int64, dup_frac=0.3)
+    else:
+        rel = W.make_rule(160, 200_000, 30_000, 16, 16, np.int32, src_dist="zipf", src_s=1.1)
+    keys, out, plan, _ = run_rule(rel, flags=flags)
+    if case == "mean":
+        ok, oo, sizes = O.rule_forward(rel.h_ids, rel.z, [OBr(b.src, b.dst, b.W, b.b, None) for b in rel.branches],
+                                       agg="mean")
+    else:
+        ok, oo, sizes = oracle_rule(rel, **kw)
+    assert np.array_equal(keys, ok)
+    assert plan.matched == sizes
+    assert rel_frob(out, oo) <= FP32_TOL
+    keys2, out2, _, _ = run_rule(rel, flags=flags | R.FLAG_PER_TUPLE)
+    assert np.array_equal(keys, keys2)
+    assert rel_frob(out, out2.astype(np.float64)) <= FP32_TOL
