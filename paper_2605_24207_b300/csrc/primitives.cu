@@ -93,6 +93,90 @@ __global__ void scan_apply_kernel(const T* __restrict__ in, T* __restrict__ out,
     }
 }
 
+// Single-pass form (inputs above one tile): each block takes the next tile from a counter (so every
+// earlier tile has started), scans it, publishes its sum, looks back over the published states of
+// the earlier tiles 32 at a time (a tile that has its inclusive prefix ends the walk) and publishes
+// its own inclusive prefix. State word of a tile: flag in the top two bits (1: sum only, 2:
+// inclusive prefix), value in the low 62 (32-bit non-negative counts). Waits are bounded: after
+// the wait budget the block gives up, raises RELNN_DEV_TIMEOUT in `status` (if given) and uses what
+// it has. One launch instead of reduce, scan of the block sums and apply.
+constexpr unsigned long long kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanVal = (1ull << 62) - 1;
+
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) scan_lb_kernel(const T* in, T* out, int64_t n, T* total,
+                                                           unsigned long long* words, int* status) {
+    __shared__ T ws[kScanThreads / 32];
+    __shared__ int tile_s;
+    __shared__ T excl_s;
+    if (threadIdx.x == 0) tile_s = (int)atomicAdd(reinterpret_cast<unsigned*>(words), 1u);
+    __syncthreads();
+    const int tile = tile_s;
+    unsigned long long* state = words + 1;
+    const int64_t base = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k;
+        const T t = i < n ? in[i] : T(0);
+        v[k] = run;
+        run += t;
+    }
+    const T incl = warp_incl_scan(run);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    T woff = 0, btot = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        woff += w < warp ? ws[w] : T(0);
+        btot += ws[w];
+    }
+    if (warp == 0) {
+        if (lane == 0)
+            atomicExch(&state[tile], (tile == 0 ? kScanInc : kScanAgg) | ((unsigned long long)btot & kScanVal));
+        long long excl = 0;
+        int window = tile - 1;
+        const unsigned long long t_start = globaltimer_ns();
+        const unsigned long long budget = wait_budget_ns(status);
+        unsigned spins = 0;
+        while (window >= 0) {
+            const int idx = window - lane;
+            unsigned long long w = kScanInc;  // before tile 0: an inclusive zero
+            if (idx >= 0) w = *reinterpret_cast<volatile unsigned long long*>(&state[idx]);
+            const unsigned flag = (unsigned)(w >> 62);
+            if (__any_sync(0xffffffffu, flag == 0)) {  // an earlier tile has not published yet
+                if ((++spins & 63u) == 0 && globaltimer_ns() - t_start > budget) {
+                    if (lane == 0) raise_status(status, RELNN_DEV_TIMEOUT);
+                    break;
+                }
+                continue;
+            }
+            const unsigned inc_mask = __ballot_sync(0xffffffffu, flag == 2);
+            const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;  // lanes 0..stop contribute
+            long long x = lane <= stop ? (long long)(w & kScanVal) : 0;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            excl += x;
+            if (inc_mask) break;
+            window -= 32;
+        }
+        if (lane == 0) {
+            if (tile > 0) atomicExch(&state[tile], kScanInc | ((unsigned long long)(excl + (long long)btot) & kScanVal));
+            excl_s = (T)excl;
+        }
+    }
+    __syncthreads();
+    const T off = excl_s + woff + incl - run;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k;
+        if (i < n) out[i] = v[k] + off;
+    }
+    // the last tile's last thread: its exclusive offset plus its own items is the sum of all n
+    if (total && tile == (int)gridDim.x - 1 && threadIdx.x == kScanThreads - 1) *total = off + run;
+}
+
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortSteps = 16;
@@ -245,7 +329,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) rs_scatter_kernel(const K* __
 }  // namespace
 
 template <class T>
-relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream_t st) {
+relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream_t st, int* status) {
     if (n <= 0) {
         if (total) RELNN_CUDA(cudaMemsetAsync(total, 0, sizeof(T), st));
         return RELNN_OK;
@@ -256,20 +340,35 @@ relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream
         RELNN_CUDA(cudaGetLastError());
         return RELNN_OK;
     }
-    T* sums = nullptr;
-    RELNN_CUDA(cudaMallocAsync(&sums, sizeof(T) * nb, st));
-    { scan_reduce_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums); note_launch(); }
-    relnn_status s = exclusive_scan<T>(sums, sums, nb, nullptr, st);
+    if (sizeof(T) == 8) {
+        // 64-bit inputs (packed (count, present) pairs can pass 2^62): reduce, scan the block sums, apply
+        T* sums = nullptr;
+        RELNN_CUDA(cudaMallocAsync(&sums, sizeof(T) * nb, st));
+        { scan_reduce_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums); note_launch(); }
+        relnn_status s = exclusive_scan<T>(sums, sums, nb, nullptr, st, status);
+        if (s == RELNN_OK) {
+            { scan_apply_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums, total); note_launch(); }
+            if (cudaGetLastError() != cudaSuccess) s = RELNN_ECUDA;
+        }
+        cudaFreeAsync(sums, st);
+        return s;
+    }
+    // single pass with a decoupled look-back: the tile counter and one state word per tile (32-bit
+    // inputs: n < 2^31 counts below 2^31 sum below 2^62)
+    unsigned long long* words = nullptr;
+    RELNN_CUDA(cudaMallocAsync(&words, sizeof(unsigned long long) * (nb + 1), st));
+    relnn_status s = RELNN_OK;
+    if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (nb + 1), st) != cudaSuccess) s = RELNN_ECUDA;
     if (s == RELNN_OK) {
-        { scan_apply_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums, total); note_launch(); }
+        { scan_lb_kernel<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, total, words, status); note_launch(); }
         if (cudaGetLastError() != cudaSuccess) s = RELNN_ECUDA;
     }
-    cudaFreeAsync(sums, st);
+    cudaFreeAsync(words, st);
     return s;
 }
 
-template relnn_status exclusive_scan<int32_t>(const int32_t*, int32_t*, int64_t, int32_t*, cudaStream_t);
-template relnn_status exclusive_scan<int64_t>(const int64_t*, int64_t*, int64_t, int64_t*, cudaStream_t);
+template relnn_status exclusive_scan<int32_t>(const int32_t*, int32_t*, int64_t, int32_t*, cudaStream_t, int*);
+template relnn_status exclusive_scan<int64_t>(const int64_t*, int64_t*, int64_t, int64_t*, cudaStream_t, int*);
 
 template <class K, class V>
 relnn_status radix_sort_pairs(K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n, int nbits, cudaStream_t st,

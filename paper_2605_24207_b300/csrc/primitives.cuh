@@ -6,11 +6,13 @@
 
 namespace relnn {
 
-// Exclusive prefix sum of in[0..n) into out[0..n) (in == out allowed). If total != nullptr the
-// sum of all n inputs is written there (device). Temporary storage is stream-ordered
-// (cudaMallocAsync) and released before return; the call is asynchronous.
+// Exclusive prefix sum of in[0..n) into out[0..n) (in == out allowed; inputs non-negative). If
+// total != nullptr the sum of all n inputs is written there (device). Temporary
+// storage is stream-ordered (cudaMallocAsync) and released before return; the call is asynchronous.
+// 32-bit inputs above one tile (4096 items) take a single pass whose blocks wait (bounded) on earlier
+// tiles; a wait that runs out raises RELNN_DEV_TIMEOUT in `status` (device status word, may be null).
 template <class T>
-relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream_t st);
+relnn_status exclusive_scan(const T* in, T* out, int64_t n, T* total, cudaStream_t st, int* status = nullptr);
 
 // Stable LSD radix sort of n (key, value) pairs by the low `nbits` bits of the key (K = uint32_t or
 // uint64_t, V = int32_t or int64_t). keys_tmp/vals_tmp are scratch of n entries each. With
