@@ -1353,17 +1353,21 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                         }
                         continue;
                     }
+                    // each lane's row as one word: the output row, -(slot + 1) for a chunk partial, or
+                    // INT_MIN for none
+                    const int myoff = (mt.z < 0 || !a.out) ? INT_MIN : (mt.w >= 0 ? -(mt.w + 1) : mt.z);
+                    const bool wok = o_ok && a.out;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int row = __shfl_sync(0xffffffffu, mt.z, j);
-                        const int part = __shfl_sync(0xffffffffu, mt.w, j);
-                        const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
-                        if (row < 0) break;
-                        if (o_ok && a.out && in_bounds(part >= 0 ? 0 : row, a.out_rows, a.status)) {
-                            const float d2 = has_r ? __uint_as_float(v2[j]) : 0.f;
-                            const float y = BWD ? __uint_as_float(v1[j]) : __uint_as_float(v1[j]) + nj * (d2 + bo);
-                            if (part >= 0) __stcg(a.vpart + (int64_t)part * a.n_feat + o, y);
-                            else emit_out(a.out + (int64_t)row * a.n_feat + o, y, a.accumulate);
+                        const int off = __shfl_sync(0xffffffffu, myoff, j);
+                        float y = __uint_as_float(v1[j]);
+                        if (!BWD) {
+                            const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
+                            y += nj * ((has_r ? __uint_as_float(v2[j]) : 0.f) + bo);
+                        }
+                        if (wok && off != INT_MIN) {
+                            if (off < 0) __stcg(a.vpart + (int64_t)(-off - 1) * a.n_feat + o, y);
+                            else if (in_bounds(off, a.out_rows, a.status)) emit_out(a.out + (int64_t)off * a.n_feat + o, y, a.accumulate);
                         }
                     }
                 }
