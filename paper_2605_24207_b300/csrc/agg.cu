@@ -1730,9 +1730,10 @@ relnn_status make_fix_jobs(VRows& V, const int4* d_splits, int64_t n_split, cuda
     return RELNN_OK;
 }
 
-// Builds (once) the virtual rows of an ordered tuple list: `sorted` = the keys ascend over rows
-// 0..R-1 and every row gets at least one virtual row (an empty row writes zeros); otherwise the
-// rows are the runs of equal keys in list order. A sorted list takes one synchronisation (the
+// Builds (once) the virtual rows of an ordered tuple list: `sorted` = every key in 0..R-1 occupies
+// one contiguous run of the list (the keys ascend, or each key's tuples are grouped) and the rows
+// come in key order, every row with at least one virtual row (an empty row writes zeros);
+// otherwise the rows are the runs of equal keys in list order. A sorted list takes one synchronisation (the
 // totals; buffers are sized by bounds and allocated before it), plus one when rows were cut.
 relnn_status ensure_vrows(VRows& V, const int32_t* key, int64_t m, int64_t R, bool sorted, cudaStream_t st) {
     if (V.nv >= 0) return RELNN_OK;
@@ -2288,7 +2289,11 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
     for (auto& b : p.br) {
         RELNN_TRY(ensure_src_order(p, b, st));
         RELNN_TRY(ensure_vrows(b.vr_src, b.hs_src.as<int32_t>(), b.m, p.n_h, true, st));
-        if (n_pass > 1) RELNN_TRY(ensure_vrows(b.vr_dst, b.hd.as<int32_t>(), b.m, 0, false, st));
+        // dst pass: one virtual row per H row in H-row order (the tuples of one dst H row are one
+        // contiguous run of the plan's order), so the GEMM adds into consecutive dz rows; only when
+        // that adds at most as many empty rows as there are runs, else the runs in plan order
+        const bool h_order = 2 * p.n_out >= p.n_h;
+        if (n_pass > 1) RELNN_TRY(ensure_vrows(b.vr_dst, b.hd.as<int32_t>(), b.m, h_order ? p.n_h : 0, h_order, st));
         vp_max = std::max(vp_max, (size_t)(b.vr_src.n_parts + b.vr_src.n_l2) * p.d);
         nv_max = std::max(nv_max, b.vr_src.nv);
         if (n_pass > 1) {
