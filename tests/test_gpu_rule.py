@@ -230,3 +230,21 @@ def test_plan_release_in_stream_order(gpu):
     assert np.array_equal(keys.cpu().numpy(), ok)
     assert rel_frob(out.cpu().numpy(), oo) <= 1e-5
     plan.release()  # a second release is a no-op
+
+
+@pytest.mark.parametrize("n_keys", [1, 2, 1024, 1000, 4096])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_unmatched_tuples_sorted_last(gpu, n_keys, bf16):
+    """Unique H keys without a selection: tuples whose src or dst key is absent from H get a sentinel
+    group key above every dst position and sort behind the matched ones, whose count is read with
+    the plan's final synchronisation. Key spaces whose size is a power of two (the sentinel then
+    needs one more key bit), a single key, and ragged sizes; join sizes and key sets bit-exact, values
+    at the form's bar."""
+    rel = W.make_rule(90 + n_keys, 3 * n_keys + 777, n_keys, 16, 16, np.int32, missing_frac=0.3)
+    flags = R.FLAG_BF16 if bf16 else 0
+    keys, out, plan, _ = run_rule(rel, flags=flags, z_dtype=torch.bfloat16 if bf16 else torch.float32)
+    ok, oo, sizes = oracle_rule(rel, round_z=bf16, round_w=bf16)
+    assert np.array_equal(keys, ok)
+    assert plan.matched == sizes
+    assert plan.n_out == ok.size
+    assert rel_frob(out, oo) <= (1e-4 if bf16 else FP32_TOL)
