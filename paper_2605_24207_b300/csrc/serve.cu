@@ -8,10 +8,11 @@
 // next free worker, so batches overlap on the device.
 //
 // A batch is one rule over disjoint key ranges: key k of the i-th query of the batch becomes
-// (i << 32) + (k + 2^31) (int64, order-preserving), the queries' H.z rows are concatenated, and the
-// usual content track (relnn plan) and fused persistent forward run once over all of it. The output
-// keys come out sorted by (query, key); a binary search per query cuts them back into per-query
-// results (keys restored to int32).
+// (i << kb) + (k - kmin_i) (int64, order-preserving; kmin_i the query's least H key, kb the width of
+// the widest query's H key span, so dense queries make a dense batch), the queries' H.z rows are
+// concatenated, and the usual content track (relnn plan) and fused persistent forward run once over
+// all of it. The output keys come out sorted by (query, key); a binary search per query cuts them
+// back into per-query results (keys restored to int32).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -23,6 +24,7 @@
 #include <vector>
 
 #include "fwd.cuh"
+#include "primitives.cuh"
 
 namespace relnn {
 namespace {
@@ -30,21 +32,51 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int kPollUs = 2000;  // how long an idle worker polls the queue before it sleeps
 
-__global__ void batch_keys_kernel(const int32_t* __restrict__ in, int64_t n, int64_t prefix, int64_t* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = prefix + ((int64_t)in[i] + 2147483648ll);
+// Key k of the i-th query of a batch becomes (i << kb) + (k - kmin_i), kmin_i the least H key of
+// the query and kb the width of the widest query's H key span, so that the batch's key space stays as
+// dense as its queries' (the join build then addresses it directly). An E key outside its query's H
+// span matches nothing: it becomes -1, below every batch key.
+__global__ void batch_keys_kernel(const int32_t* __restrict__ in, int64_t n, int64_t prefix, int32_t kmin,
+                                  int32_t kmax, int64_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = in[i];
+        out[i] = (k < kmin || k > kmax) ? -1 : prefix + ((int64_t)k - kmin);
+    }
 }
 
-__global__ void strip_keys_kernel(const int64_t* __restrict__ in, int64_t n, int32_t* __restrict__ out) {
+__global__ void strip_keys_kernel(const int64_t* __restrict__ in, int64_t n, int64_t mask, int32_t kmin,
+                                  int32_t* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (int32_t)((in[i] & 0xffffffffll) - 2147483648ll);
+        out[i] = (int32_t)((in[i] & mask) + kmin);
+}
+
+// Least and largest H key of every query of a batch (blockIdx.y = query): mm[2 i] / mm[2 i + 1] hold
+// them order-preserved as unsigned (k + 2^31), reduced by warp then atomics.
+struct QKeys {
+    const int32_t* k;
+    int64_t n;
+};
+__global__ void query_minmax_kernel(const QKeys* __restrict__ qs, unsigned* __restrict__ mm) {
+    const QKeys q = qs[blockIdx.y];
+    unsigned lo = 0xffffffffu, hi = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < q.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned u = (unsigned)q.k[i] ^ 0x80000000u;
+        lo = min(lo, u);
+        hi = max(hi, u);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(mm + 2 * blockIdx.y, lo);
+        atomicMax(mm + 2 * blockIdx.y + 1, hi);
+    }
 }
 
 // lo[q] = first output row of query q (keys are sorted by query prefix); lo[nq] = n.
-__global__ void ranges_kernel(const int64_t* __restrict__ keys, int64_t n, int nq, int64_t* __restrict__ lo) {
+__global__ void ranges_kernel(const int64_t* __restrict__ keys, int64_t n, int nq, int kb, int64_t* __restrict__ lo) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q > nq) return;
-    const int64_t target = (int64_t)q << 32;
+    const int64_t target = (int64_t)q << kb;
     int64_t a = 0, b = n;
     while (a < b) {
         const int64_t mid = (a + b) >> 1;
@@ -123,17 +155,52 @@ relnn_status run_batch(relnn_server_s* S, std::vector<Query*>& batch, cudaStream
     RELNN_TRY(sk.alloc_tmp(sizeof(int64_t) * std::max<int64_t>(T, 1), st));
     RELNN_TRY(dk.alloc_tmp(sizeof(int64_t) * std::max<int64_t>(T, 1), st));
     RELNN_TRY(lo.alloc_tmp(sizeof(int64_t) * (nq + 1), st));
+    // every query's H key range (one launch, one synchronisation), then the batch key width
+    std::vector<QKeys> qk(nq);
+    for (int i = 0; i < nq; ++i) qk[i] = QKeys{(const int32_t*)batch[i]->q.d_h_ids, batch[i]->q.n_h};
+    DevBuf qd, mmb;
+    RELNN_TRY(qd.alloc_tmp(sizeof(QKeys) * nq, st));
+    RELNN_TRY(mmb.alloc_tmp(sizeof(unsigned) * 2 * nq, st));
+    std::vector<unsigned> mm(2 * nq);
+    for (int i = 0; i < nq; ++i) {
+        mm[2 * i] = 0xffffffffu;
+        mm[2 * i + 1] = 0u;
+    }
+    RELNN_CUDA(cudaMemcpyAsync(qd.p, qk.data(), sizeof(QKeys) * nq, cudaMemcpyHostToDevice, st));
+    RELNN_CUDA(cudaMemcpyAsync(mmb.p, mm.data(), sizeof(unsigned) * 2 * nq, cudaMemcpyHostToDevice, st));
+    int64_t kmax_n = 1;
+    for (int i = 0; i < nq; ++i) kmax_n = std::max<int64_t>(kmax_n, batch[i]->q.n_h);
+    { query_minmax_kernel<<<dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(kmax_n, 256 * 8), 64)), (unsigned)nq),
+                            256, 0, st>>>(qd.as<QKeys>(), mmb.as<unsigned>()); note_launch(); }
+    RELNN_CUDA(cudaMemcpyAsync(mm.data(), mmb.p, sizeof(unsigned) * 2 * nq, cudaMemcpyDeviceToHost, st));
+    RELNN_CUDA(cudaStreamSynchronize(st));
+    std::vector<int32_t> qmin(nq), qmax(nq);
+    int kb = 1;
+    for (int i = 0; i < nq; ++i) {
+        if (batch[i]->q.n_h == 0) {
+            qmin[i] = 1;
+            qmax[i] = 0;  // an empty H: every E key is out of range
+            continue;
+        }
+        qmin[i] = (int32_t)(mm[2 * i] ^ 0x80000000u);
+        qmax[i] = (int32_t)(mm[2 * i + 1] ^ 0x80000000u);
+        const uint64_t span = (uint64_t)((int64_t)qmax[i] - qmin[i]);
+        kb = std::max(kb, bit_length(span));
+    }
     for (int i = 0; i < nq; ++i) {
         const relnn_query& q = batch[i]->q;
-        const int64_t prefix = (int64_t)i << 32;
+        const int64_t prefix = (int64_t)i << kb;
         if (q.n_h > 0) {
-            { batch_keys_kernel<<<grid_for(q.n_h), 256, 0, st>>>((const int32_t*)q.d_h_ids, q.n_h, prefix, hk.as<int64_t>() + h_off[i]); note_launch(); }
+            { batch_keys_kernel<<<grid_for(q.n_h), 256, 0, st>>>((const int32_t*)q.d_h_ids, q.n_h, prefix, qmin[i], qmax[i],
+                                                                hk.as<int64_t>() + h_off[i]); note_launch(); }
             RELNN_CUDA(cudaMemcpyAsync(zb.as<uint8_t>() + h_off[i] * d * S->z_esz, q.d_z, q.n_h * d * S->z_esz,
                                        cudaMemcpyDeviceToDevice, st));
         }
         if (q.n_tuples > 0) {
-            { batch_keys_kernel<<<grid_for(q.n_tuples), 256, 0, st>>>((const int32_t*)q.d_src, q.n_tuples, prefix, sk.as<int64_t>() + t_off[i]); note_launch(); }
-            { batch_keys_kernel<<<grid_for(q.n_tuples), 256, 0, st>>>((const int32_t*)q.d_dst, q.n_tuples, prefix, dk.as<int64_t>() + t_off[i]); note_launch(); }
+            { batch_keys_kernel<<<grid_for(q.n_tuples), 256, 0, st>>>((const int32_t*)q.d_src, q.n_tuples, prefix, qmin[i], qmax[i],
+                                                                     sk.as<int64_t>() + t_off[i]); note_launch(); }
+            { batch_keys_kernel<<<grid_for(q.n_tuples), 256, 0, st>>>((const int32_t*)q.d_dst, q.n_tuples, prefix, qmin[i], qmax[i],
+                                                                     dk.as<int64_t>() + t_off[i]); note_launch(); }
         }
     }
     RELNN_CUDA(cudaGetLastError());
@@ -170,7 +237,7 @@ relnn_status run_batch(relnn_server_s* S, std::vector<Query*>& batch, cudaStream
         if (P.bf16) RELNN_TRY(forward_tc(P, io, bo.as<float>(), st));
         else RELNN_TRY(forward_fp32(P, io, bo.as<float>(), st));
     }
-    { ranges_kernel<<<(nq + 1 + 127) / 128, 128, 0, st>>>(P.out_keys.as<int64_t>(), P.n_out, nq, lo.as<int64_t>()); note_launch(); }
+    { ranges_kernel<<<(nq + 1 + 127) / 128, 128, 0, st>>>(P.out_keys.as<int64_t>(), P.n_out, nq, kb, lo.as<int64_t>()); note_launch(); }
     std::vector<int64_t> hlo(nq + 1);
     RELNN_CUDA(cudaMemcpyAsync(hlo.data(), lo.p, sizeof(int64_t) * (nq + 1), cudaMemcpyDeviceToHost, st));
     // the forward's device checks arrive with the same synchronisation (the kernels after it raise none)
@@ -188,7 +255,8 @@ relnn_status run_batch(relnn_server_s* S, std::vector<Query*>& batch, cudaStream
         if (q->n_out > 0) {
             RELNN_TRY(q->keys.alloc_tmp(sizeof(int32_t) * q->n_out, st));
             RELNN_TRY(q->z.alloc_tmp(sizeof(float) * q->n_out * d_out, st));
-            { strip_keys_kernel<<<grid_for(q->n_out), 256, 0, st>>>(P.out_keys.as<int64_t>() + hlo[i], q->n_out, q->keys.as<int32_t>()); note_launch(); }
+            { strip_keys_kernel<<<grid_for(q->n_out), 256, 0, st>>>(P.out_keys.as<int64_t>() + hlo[i], q->n_out,
+                                                                    ((int64_t)1 << kb) - 1, qmin[i], q->keys.as<int32_t>()); note_launch(); }
             RELNN_CUDA(cudaMemcpyAsync(q->z.p, bo.as<float>() + hlo[i] * d_out, sizeof(float) * q->n_out * d_out,
                                        cudaMemcpyDeviceToDevice, st));
         }
