@@ -396,8 +396,8 @@ relnn_status relnn_server_create(const relnn_server_cfg* cfg, relnn_server_t* ou
         (void)cudaGetLastError();
     }
     // One small batch of two queries runs before the workers start, so that the kernels of the
-    // batched path (keys of several queries: the sorted join build and hashed lookups, which a query
-    // served alone does not use) are loaded before the first query arrives.
+    // batched path (the key range of every query, the batch keys, the plan and the result split) are
+    // loaded before the first query arrives.
     {
         const int64_t n = 64;
         DevBuf keys, z;
