@@ -1316,6 +1316,11 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                 const int part0 = __shfl_sync(0xffffffffu, mt.w, 0);
                 const bool whole = __all_sync(0xffffffffu, mt.w < 0 && mt.z == row0 + lane);
                 const bool parts = !whole && __all_sync(0xffffffffu, mt.w >= 0 && mt.w == part0 + lane);
+                // each lane's row as one word for the general path: the output row, -(slot + 1) for a
+                // chunk partial, or INT_MIN for none
+                const int myoff = (mt.z < 0 || !a.out) ? INT_MIN : (mt.w >= 0 ? -(mt.w + 1) : mt.z);
+                const bool whole_ok = whole && a.out && in_bounds(row0 + 31, a.out_rows, a.status) &&
+                                      in_bounds(row0, a.out_rows, a.status);
                 for (int mb = 0; mb < a.m_blocks; ++mb) {
                     if (mb * 128 + 32 * q >= a.n_feat) continue;
                     const int o = mb * 128 + 32 * q + lane;
@@ -1323,51 +1328,49 @@ agg_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant_
                     const float bo = mb == 0 ? bias_r[0] : bias_r[1];
                     const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * buf_cols +
                                         (uint32_t)mb * N + (uint32_t)rr;
-                    uint32_t v1[32], v2[32];
-                    tmem_ld_32x32b_x32(ta, v1);
-                    if (has_r) tmem_ld_32x32b_x32(ta + (uint32_t)a.m_blocks * N, v2);
-                    tmem_ld_wait();
-                    if (whole && a.out && in_bounds(row0 + 31, a.out_rows, a.status) && in_bounds(row0, a.out_rows, a.status)) {
-                        float* dst = a.out + (int64_t)row0 * a.n_feat + o;
+                    // eight rows (TMEM columns) at a time in a loop that is not unrolled: the three store
+                    // paths stay small enough for the instruction cache (fully unrolled, chunks mixing
+                    // whole rows and chunk partials stalled on instruction fetch)
+#pragma unroll 1
+                    for (int jp = 0; jp < 32; jp += 8) {
+                        uint32_t v1[8], v2[8];
+                        tmem_ld_32x32b_x8(ta + (uint32_t)jp, v1);
+                        if (has_r) tmem_ld_32x32b_x8(ta + (uint32_t)a.m_blocks * N + (uint32_t)jp, v2);
+                        tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            float y = __uint_as_float(v1[j]);
+                        for (int u = 0; u < 8; ++u) {
+                            tmem_ld_after(v1[u]);
+                            if (has_r) tmem_ld_after(v2[u]);
+                        }
+                        float y[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            y[u] = __uint_as_float(v1[u]);
                             if (!BWD) {
-                                const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
-                                y += nj * ((has_r ? __uint_as_float(v2[j]) : 0.f) + bo);
+                                const float nj = (float)__shfl_sync(0xffffffffu, mt.y, jp + u);
+                                y[u] += nj * ((has_r ? __uint_as_float(v2[u]) : 0.f) + bo);
                             }
-                            if (o_ok) emit_out(dst + (int64_t)j * a.n_feat, y, a.accumulate);
                         }
-                        continue;
-                    }
-                    if (parts && a.out) {
-                        float* dst = a.vpart + (int64_t)part0 * a.n_feat + o;
+                        if (whole_ok) {
+                            float* dst = a.out + (int64_t)(row0 + jp) * a.n_feat + o;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            float y = __uint_as_float(v1[j]);
-                            if (!BWD) {
-                                const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
-                                y += nj * ((has_r ? __uint_as_float(v2[j]) : 0.f) + bo);
+                            for (int u = 0; u < 8; ++u)
+                                if (o_ok) emit_out(dst + (int64_t)u * a.n_feat, y[u], a.accumulate);
+                        } else if (parts && a.out) {
+                            float* dst = a.vpart + (int64_t)(part0 + jp) * a.n_feat + o;
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (o_ok) __stcg(dst + (int64_t)u * a.n_feat, y[u]);
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int off = __shfl_sync(0xffffffffu, myoff, jp + u);
+                                if (o_ok && a.out && off != INT_MIN) {
+                                    if (off < 0) __stcg(a.vpart + (int64_t)(-off - 1) * a.n_feat + o, y[u]);
+                                    else if (in_bounds(off, a.out_rows, a.status))
+                                        emit_out(a.out + (int64_t)off * a.n_feat + o, y[u], a.accumulate);
+                                }
                             }
-                            if (o_ok) __stcg(dst + (int64_t)j * a.n_feat, y);
-                        }
-                        continue;
-                    }
-                    // each lane's row as one word: the output row, -(slot + 1) for a chunk partial, or
-                    // INT_MIN for none
-                    const int myoff = (mt.z < 0 || !a.out) ? INT_MIN : (mt.w >= 0 ? -(mt.w + 1) : mt.z);
-                    const bool wok = o_ok && a.out;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int off = __shfl_sync(0xffffffffu, myoff, j);
-                        float y = __uint_as_float(v1[j]);
-                        if (!BWD) {
-                            const float nj = (float)__shfl_sync(0xffffffffu, mt.y, j);
-                            y += nj * ((has_r ? __uint_as_float(v2[j]) : 0.f) + bo);
-                        }
-                        if (wok && off != INT_MIN) {
-                            if (off < 0) __stcg(a.vpart + (int64_t)(-off - 1) * a.n_feat + o, y);
-                            else if (in_bounds(off, a.out_rows, a.status)) emit_out(a.out + (int64_t)off * a.n_feat + o, y, a.accumulate);
                         }
                     }
                 }
