@@ -631,7 +631,6 @@ agg_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ 
 // SINGLE: every tuple of a virtual row names the same table row (the backward's runs of equal dst
 // rows): the row is loaded once and multiplied by the tuple count (exact in f32, count <= 32).
 constexpr int kSegWarps = 8;
-constexpr int kSegIdx = 32 * kChunk;  // tuple indices of a warp's 32 virtual rows
 // row loads in flight per lane of the gather-sum: 6 with four blocks per SM (at most 64 registers)
 // measured 4 % faster on the single-rule workload than 8 with three
 constexpr int kSegUnroll = 6;
@@ -652,7 +651,13 @@ __global__ void __launch_bounds__(32 * kSegWarps, 4) seg_sum_kernel(const int4* 
                                                                  int mask_words = 0,
                                                                  float* __restrict__ db_part = nullptr,
                                                                  const float* __restrict__ tbl_f32 = nullptr) {
-    __shared__ int32_t s_idx[SINGLE ? 1 : kSegWarps][SINGLE ? 1 : kSegIdx];
+    // MASK (src pass): batches of 16 rows, whose mask words are staged in shared memory with their
+    // indices (one contiguous copy per batch instead of a second load per tuple)
+    constexpr bool SMASK = MASK && !SINGLE;
+    constexpr int kBR = SMASK ? 16 : 32;  // virtual rows per batch
+    constexpr int kBI = kBR * kChunk;     // their tuple indices at most
+    __shared__ int32_t s_idx[SINGLE ? 1 : kSegWarps][SINGLE ? 1 : kBI];
+    __shared__ uint32_t s_mk[SMASK ? kSegWarps : 1][SMASK ? 2 * kBI : 1];
     __shared__ float s_db[MASK && SINGLE ? kSegWarps : 1][MASK && SINGLE ? 256 : 1];
     // src pass of a ReLU rule: the AND mask of 8 bf16 elements for each byte of mask bits
     __shared__ uint4 s_lut[MASK && !SINGLE ? 256 : 1];
@@ -674,13 +679,15 @@ __global__ void __launch_bounds__(32 * kSegWarps, 4) seg_sum_kernel(const int4* 
     const uint4* __restrict__ base = reinterpret_cast<const uint4*>(tbl) + ch;
     const int pitch = 2 * kpad, nck = kpad >> 3;
     int32_t* sidx = s_idx[SINGLE ? 0 : threadIdx.x >> 5];
+    uint32_t* smk = s_mk[SMASK ? threadIdx.x >> 5 : 0];
+    const bool stage_mask = SMASK && mask_words <= 2;
     const int mword = (8 * ch) >> 5, msh = (8 * ch) & 31;  // this lane's 8 features in the mask
     float dbacc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) dbacc[i] = 0.f;
-    for (int64_t vb = warp0 * 32; vb < nv; vb += nw * 32) {
-        const int4 mine = vb + lane < nv ? __ldg(vr + vb + lane) : make_int4(0, 0, -1, -1);
-        const int nrows = (int)imin64(32, nv - vb);
+    for (int64_t vb = warp0 * kBR; vb < nv; vb += nw * kBR) {
+        const int4 mine = (lane < kBR && vb + lane < nv) ? __ldg(vr + vb + lane) : make_int4(0, 0, -1, -1);
+        const int nrows = (int)imin64(kBR, nv - vb);
         const int myn = mine.y > 0 ? mine.y : 0;
         int x0 = 0;
         bool ok = true;
@@ -689,11 +696,13 @@ __global__ void __launch_bounds__(32 * kSegWarps, 4) seg_sum_kernel(const int4* 
             const int cnt = (int)__reduce_add_sync(0xffffffffu, (unsigned)myn);
             const int x1 = (int)__reduce_max_sync(0xffffffffu, (unsigned)(myn > 0 ? mine.x + myn : 0));
             // the non-empty rows' tuples must tile [x0, x0 + cnt) (virtual rows are in tuple order)
-            ok = cnt == 0 || (x1 - x0 == cnt && cnt <= kSegIdx);
+            ok = cnt == 0 || (x1 - x0 == cnt && cnt <= kBI);
             if (!ok && lane == 0) raise_status(status, RELNN_DEV_BOUNDS);
             __syncwarp();
             if (ok)
                 for (int i = lane; i < cnt; i += 32) sidx[i] = __ldg(gidx + x0 + i);
+            if (ok && stage_mask)
+                for (int i = lane; i < cnt * mask_words; i += 32) smk[i] = __ldg(mask + (int64_t)x0 * mask_words + i);
             __syncwarp();
         }
         for (int j0 = 0; j0 < nrows; j0 += G) {
@@ -762,7 +771,9 @@ __global__ void __launch_bounds__(32 * kSegWarps, 4) seg_sum_kernel(const int4* 
                         if (t0 + q < n) {
                             const int r = sidx[xo + t0 + q];
                             if (in_bounds(r, tbl_rows, status)) u[q] = __ldg(base + (int64_t)r * L);
-                            if (MASK) mk[q] = __ldg(mask + (int64_t)(x0 + xo + t0 + q) * mask_words + mword) >> msh;
+                            if (MASK)
+                                mk[q] = (stage_mask ? smk[(xo + t0 + q) * mask_words + mword]
+                                                    : __ldg(mask + (int64_t)(x0 + xo + t0 + q) * mask_words + mword)) >> msh;
                         }
                     }
 #pragma unroll
