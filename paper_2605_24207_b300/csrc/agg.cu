@@ -90,24 +90,20 @@ struct AggArgs {
     uint32_t idesc_dw, dw_col;
 };
 
-// a0 += b0, a1 += b1 as one packed f32x2 add (the same IEEE round-to-nearest sum per element)
-__device__ __forceinline__ void add_f32x2(float& a0, float& a1, float b0, float b1) {
-    asm("{\n\t.reg .b64 x, y;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\t"
-        "add.rn.f32x2 x, x, y;\n\tmov.b64 {%0, %1}, x;\n\t}"
-        : "+f"(a0), "+f"(a1)
-        : "f"(b0), "f"(b1));
-}
-
 __device__ __forceinline__ void add8(float (&acc)[8], float (&cmp)[8], const uint4& u, bool kahan) {
     const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float lo = __uint_as_float(w[i] << 16), hi = __uint_as_float(w[i] & 0xffff0000u);
         if (kahan) {
-            kahan_add(acc[2 * i], cmp[2 * i], lo);
-            kahan_add(acc[2 * i + 1], cmp[2 * i + 1], hi);
+            kahan_add(acc[2 * i], cmp[2 * i], __uint_as_float(w[i] << 16));
+            kahan_add(acc[2 * i + 1], cmp[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u));
         } else {
-            add_f32x2(acc[2 * i], acc[2 * i + 1], lo, hi);
+            // mixed-precision add (sm_100+): the bf16 half is widened inside the add, so no separate
+            // unpack; the widening is exact, so the sum equals the unpack-then-add.rn.f32 result
+            asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+                "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
+                : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
+                : "r"(w[i]));
         }
     }
 }
