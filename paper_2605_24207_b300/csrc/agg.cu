@@ -90,6 +90,16 @@ struct AggArgs {
     uint32_t idesc_dw, dw_col;
 };
 
+// a0 += low bf16 of w, a1 += high bf16 of w, by the mixed-precision add (sm_100+): the bf16 operand
+// is widened inside the add, so no separate unpack; the widening is exact, so the sums equal the
+// unpack-then-add.rn.f32 results
+__device__ __forceinline__ void add_bf16x2(float& a0, float& a1, uint32_t w) {
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "r"(w));
+}
+
 __device__ __forceinline__ void add8(float (&acc)[8], float (&cmp)[8], const uint4& u, bool kahan) {
     const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
@@ -98,12 +108,7 @@ __device__ __forceinline__ void add8(float (&acc)[8], float (&cmp)[8], const uin
             kahan_add(acc[2 * i], cmp[2 * i], __uint_as_float(w[i] << 16));
             kahan_add(acc[2 * i + 1], cmp[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u));
         } else {
-            // mixed-precision add (sm_100+): the bf16 half is widened inside the add, so no separate
-            // unpack; the widening is exact, so the sum equals the unpack-then-add.rn.f32 result
-            asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
-                "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
-                : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
-                : "r"(w[i]));
+            add_bf16x2(acc[2 * i], acc[2 * i + 1], w[i]);
         }
     }
 }
@@ -849,6 +854,122 @@ int seg_sum_grid(int64_t nv) {
     if (per_sm <= 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_sum_kernel<KAHAN, SINGLE, MASK>, 32 * kSegWarps, 0) !=
             cudaSuccess) {
+            (void)cudaGetLastError();
+            per_sm = 0;
+        }
+        per_sm = std::max(1, per_sm);
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nv, 32 * kSegWarps), (int64_t)num_sms() * per_sm));
+}
+
+// The plain gather-sum (no compensation, no mask) with 32-byte lane chunks, for rows of w = 16 .. 256
+// elements (a power of two) in a 32-byte aligned table: a lane owns 16 elements of its row
+// (one 256-bit load per tuple), so each tuple's index, address and load serve 16 adds instead of 8.
+// The same sums in the same order as seg_sum_kernel<false, false>, so the same S bit for bit.
+template <int U>
+__global__ void __launch_bounds__(32 * kSegWarps, 4) seg_sum_wide_kernel(const int4* __restrict__ vr, int64_t nv,
+                                                                      const int32_t* __restrict__ gidx,
+                                                                      const uint16_t* __restrict__ tbl, int64_t tbl_rows,
+                                                                      int w, int kpad, uint16_t* __restrict__ S,
+                                                                      int* status) {
+    constexpr int kBI = 32 * kChunk;
+    __shared__ int32_t s_idx[kSegWarps][kBI];
+    const int lane = threadIdx.x & 31;
+    const int L = w >> 4, lsh = 31 - __clz(L), G = 32 >> lsh;
+    const int grp = lane >> lsh, ch = lane & (L - 1);
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint16_t* __restrict__ base = tbl + 16 * ch;
+    const int pitch = 2 * kpad, nck = kpad >> 3;
+    int32_t* sidx = s_idx[threadIdx.x >> 5];
+    for (int64_t vb = warp0 * 32; vb < nv; vb += nw * 32) {
+        const int4 mine = vb + lane < nv ? __ldg(vr + vb + lane) : make_int4(0, 0, -1, -1);
+        const int nrows = (int)imin64(32, nv - vb);
+        const int myn = mine.y > 0 ? mine.y : 0;
+        const int x0 = (int)__reduce_min_sync(0xffffffffu, (unsigned)(myn > 0 ? mine.x : INT_MAX));
+        const int cnt = (int)__reduce_add_sync(0xffffffffu, (unsigned)myn);
+        const int x1 = (int)__reduce_max_sync(0xffffffffu, (unsigned)(myn > 0 ? mine.x + myn : 0));
+        // the non-empty rows' tuples must tile [x0, x0 + cnt) (virtual rows are in tuple order)
+        const bool ok = cnt == 0 || (x1 - x0 == cnt && cnt <= kBI);
+        if (!ok && lane == 0) raise_status(status, RELNN_DEV_BOUNDS);
+        __syncwarp();
+        if (ok)
+            for (int i = lane; i < cnt; i += 32) sidx[i] = __ldg(gidx + x0 + i);
+        __syncwarp();
+        for (int j0 = 0; j0 < nrows; j0 += G) {
+            const int j = j0 + grp;
+            const int jj = j < nrows ? j : 0;
+            const int n_j = __shfl_sync(0xffffffffu, myn, jj);
+            const int x_j = __shfl_sync(0xffffffffu, mine.x, jj);
+            const int n = (j < nrows && ok) ? n_j : 0;
+            const int xo = x_j - x0;
+            float acc[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+            const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)n);
+            for (int t0 = 0; t0 < nmax; t0 += U) {
+                const int slots = min(U, nmax - t0);  // warp-uniform
+                uint32_t u[U][8];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    if (q >= slots) break;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) u[q][i] = 0u;
+                    if (t0 + q < n) {
+                        const int r = sidx[xo + t0 + q];
+                        if (in_bounds(r, tbl_rows, status))
+                            asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                                : "=r"(u[q][0]), "=r"(u[q][1]), "=r"(u[q][2]), "=r"(u[q][3]), "=r"(u[q][4]),
+                                  "=r"(u[q][5]), "=r"(u[q][6]), "=r"(u[q][7])
+                                : "l"(base + (int64_t)r * w));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    if (q >= slots) break;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) add_bf16x2(acc[2 * i], acc[2 * i + 1], u[q][i]);
+                }
+            }
+            if (j < nrows) {
+                uint32_t hi[8], lo[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    hi[i] = pack_bf16x2(acc[2 * i], acc[2 * i + 1]);
+                    const float h0 = __uint_as_float(hi[i] << 16), h1 = __uint_as_float(hi[i] & 0xffff0000u);
+                    lo[i] = pack_bf16x2(acc[2 * i] - h0, acc[2 * i + 1] - h1);
+                }
+                uint16_t* row = S + (vb + j) * pitch;
+                uint4* ph = reinterpret_cast<uint4*>(row + 16 * ch);
+                uint4* pl = reinterpret_cast<uint4*>(row + kpad + 16 * ch);
+                ph[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                ph[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+                pl[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                pl[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+                // 8-element chunks past w: the zero padding of each half
+                for (int c = 2 * L + ch; c < nck; c += L) {
+                    *reinterpret_cast<uint4*>(row + 8 * c) = make_uint4(0u, 0u, 0u, 0u);
+                    *reinterpret_cast<uint4*>(row + kpad + 8 * c) = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+        }
+    }
+}
+
+constexpr int kSegUnrollWide = 3;  // 256-bit row loads in flight per lane (the same bytes as 6 x 16)
+
+// The wide gather-sum is taken for rows of 64 .. 256 elements in a 32-byte aligned table. Narrower
+// rows keep the 16-byte form: with twice the rows side by side in a warp, the warp-uniform loop over
+// the longest row's tuples leaves more lanes idle (rows of 32: 16 % slower, measured).
+bool seg_sum_wide_ok(int w, const void* tbl) {
+    return w >= 64 && w <= 256 && (w & (w - 1)) == 0 && ((uintptr_t)tbl & 31) == 0;
+}
+
+int seg_sum_wide_grid(int64_t nv) {
+    static int per_sm = 0;
+    if (per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_sum_wide_kernel<kSegUnrollWide>, 32 * kSegWarps,
+                                                          0) != cudaSuccess) {
             (void)cudaGetLastError();
             per_sm = 0;
         }
@@ -2099,7 +2220,9 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
     // fused (RELNN_TUNE_AGG_FUSE): the GEMM's own producer warps compute the pairs (plain f32 sums)
     const int fuse = ksum ? 0 : (int)tune_get(RELNN_TUNE_AGG_FUSE);
     if (!fuse) RELNN_TRY(p.sbuf.alloc_nosync(sizeof(uint16_t) * 2 * (size_t)kpad * std::max<int64_t>(nv_max, 1), st));
-    const int ss_blocks = ksum ? seg_sum_grid<true, false>(nv_max) : seg_sum_grid<false, false>(nv_max);
+    const bool wide = !ksum && seg_sum_wide_ok(p.d, io.z);
+    const int ss_blocks = ksum ? seg_sum_grid<true, false>(nv_max)
+                               : wide ? seg_sum_wide_grid(nv_max) : seg_sum_grid<false, false>(nv_max);
     for (size_t i = 0; i < p.br.size(); ++i) {
         BranchPlan& b = p.br[i];
         const VRows& V = b.vr_out;
@@ -2110,6 +2233,8 @@ relnn_status forward_two_kernel(Plan& p, const CallIO& io, float* out, cudaStrea
             const uint16_t* zt = reinterpret_cast<const uint16_t*>(io.z);
             if (ksum) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
                                                                                 p.n_h, p.d, kpad, S, p.status.as<int>(), kmin);
+            else if (wide) seg_sum_wide_kernel<kSegUnrollWide><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
+                V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt, p.n_h, p.d, kpad, S, p.status.as<int>());
             else seg_sum_kernel<false, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), zt,
                                                                           p.n_h, p.d, kpad, S, p.status.as<int>(), kmin);
             note_launch();
@@ -2338,12 +2463,14 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
             uint16_t* S = p.sbuf.as<uint16_t>();
             const int kmin = (int)tune_get(RELNN_TUNE_KAHAN_MIN);
             const bool ksum = p.kahan && kmin <= kChunk;  // as in the forward
+            const bool wide = !masked && pass == 0 && !ksum && seg_sum_wide_ok(p.d_out, p.doutbf.p);
             const int ss_blocks =
                 (int)std::min<int64_t>(ss_max, masked ? (pass == 1 ? seg_sum_grid<false, true, true>(V.nv)
                                                         : ksum ? seg_sum_grid<true, false, true>(V.nv)
                                                                : seg_sum_grid<false, false, true>(V.nv))
                                                       : (pass == 1 ? seg_sum_grid<false, true>(V.nv)
                                                          : ksum ? seg_sum_grid<true, false>(V.nv)
+                                                         : wide ? seg_sum_wide_grid(V.nv)
                                                                 : seg_sum_grid<false, false>(V.nv)));
             const int32_t* gi = pass == 0 ? b.seg_src.as<int32_t>() : b.seg.as<int32_t>();
             {
@@ -2370,6 +2497,8 @@ relnn_status backward_agg(Plan& p, const CallIO& io_in, const GradIO& g, cudaStr
                 } else if (pass == 0) {
                     if (ksum) seg_sum_kernel<true, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
                                                                                         p.d_out, kpad_g, S, stw, kmin);
+                    else if (wide) seg_sum_wide_kernel<kSegUnrollWide><<<ss_blocks, 32 * kSegWarps, 0, st>>>(
+                        V.vr.as<int4>(), V.nv, gi, tb, p.n_out, p.d_out, kpad_g, S, stw);
                     else seg_sum_kernel<false, false><<<ss_blocks, 32 * kSegWarps, 0, st>>>(V.vr.as<int4>(), V.nv, gi, tb, p.n_out,
                                                                                   p.d_out, kpad_g, S, stw, kmin);
                 } else {
