@@ -274,15 +274,15 @@ class C2:
                 R.PROF_FWD_TC: ("fwd_tc_kernel", 2.0 * (2 * self.d) * self.d_out * self.matched, "tensor")}
 
     def ncu_traffic(self):
-        """DRAM bytes (read + write) per launch of the step's kernels, from one ncu capture of this
-        workload at its default size (profiles/seg_sum_kernel_rule_c2_16M.md): the two-kernel
-        aggregate-first forward only; None for other sizes or forms."""
+        """DRAM bytes (read + write) per launch of the step's kernels, from one ncu capture
+        (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of this workload at its default size:
+        the two-kernel aggregate-first forward only; None for other sizes or forms."""
         from paper_2605_24207_b300 import relnn as R
         if (self.n_tuples, self.n_keys, self.agg) != (16_000_000, 1_000_000, "sum") or not self.agg_form:
             return None
         if self.flags & (R.FLAG_PER_TUPLE | R.FLAG_PUSHDOWN) or R.tune_get(R.TUNE_AGG_FUSE):
             return None
-        return {R.PROF_AGG_SUM: 482_404_864 + 472_642_304, R.PROF_AGG_FWD: 788_304_128 + 462_580_992}
+        return {R.PROF_AGG_SUM: 472_517_376 + 467_636_992, R.PROF_AGG_FWD: 788_276_992 + 462_302_208}
 
     def agg_bytes(self):
         """(gather-sum bytes, GEMM bytes) per forward."""
