@@ -584,11 +584,11 @@ class C3:
         gemm_f = n2 * 256 + n2 * 128 + n2 * 256
         gemm_b = 2 * (n1 * 256 + n1 * 128 + n1 * 256) + 2 * (n_h * 256 + n_h * 128 + n_h * 256)
         return {R.PROF_FWD_TC: ("fwd_tc_kernel (rule 1)", 2.0 * 128 * 64 * m1, "tensor"),
-                R.PROF_AGG_SUM: ("seg_sum_kernel (rule 2 forward; both backwards)", float(sum_b), "hbm"),
+                R.PROF_AGG_SUM: ("seg_sum kernels (rule 2 forward; both backwards)", float(sum_b), "hbm"),
                 R.PROF_AGG_FWD: ("agg_gemm_kernel forward (rule 2)", float(gemm_f), "hbm"),
                 R.PROF_AGG_BWD: ("agg_gemm_kernel backward (both rules)", float(gemm_b), "hbm"),
                 R.PROF_BWD_TC: ("bwd_tc_kernel (per-tuple backward, if taken)", 2.0 * 2.0 * 128 * 64 * m1, "tensor"),
-                R.PROF_FWD_FP32: ("fwd_fp32_lane_kernel (readout)", float(n2 * 64 * 4 + n2 * 4), "hbm")}
+                R.PROF_FWD_FP32: ("fwd_identity_agg_kernel (readout gather-sum)", float(n2 * 64 * 4 + n2 * 4), "hbm")}
 
     def e2e_setup(self):
         import torch

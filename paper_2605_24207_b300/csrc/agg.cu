@@ -2135,6 +2135,111 @@ bool agg_forward_fp32_ok(const Plan& p, const CallIO& io, const float* out) {
     return true;
 }
 
+// Identity rules of the FP32 form (no Linear, no activation, Concat = z_src only: e.g. a SUM
+// readout Out(g; SUM z) :- H(k; z), G(k, g)): out[row] = the f32 sum of z[hs_t] over the row's
+// tuples. Lane groups of d / 4 lanes each own one virtual row at a time (a lane = one 16-byte column
+// chunk), with kIdUnroll row loads in flight per lane; whole rows are written (or, for a later
+// branch of a union, added), chunk partials of cut rows go to vpart for the fix-up. The per-tuple
+// FP32 form computes the same sums in tuple order; the two differ by the order of f32 additions only.
+constexpr int kIdUnroll = 4;
+
+template <bool KAHAN>
+__global__ void __launch_bounds__(256) fwd_identity_agg_kernel(const int4* __restrict__ vr, int64_t nv,
+                                                            const int32_t* __restrict__ hs,
+                                                            const float* __restrict__ z, int64_t z_rows, int d,
+                                                            float* __restrict__ out, int64_t out_rows,
+                                                            float* __restrict__ vpart, int accumulate, int* status) {
+    const int lane = threadIdx.x & 31;
+    const int L = d >> 2, lsh = 31 - __clz(L), G = 32 >> lsh;
+    const int grp = lane >> lsh, ch = lane & (L - 1);
+    const int64_t g0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * G + grp;
+    const int64_t gs = (((int64_t)gridDim.x * blockDim.x) >> 5) * G;
+    const float4* __restrict__ z4 = reinterpret_cast<const float4*>(z) + ch;
+    for (int64_t v = g0; v < nv; v += gs) {
+        const int4 m = __ldg(vr + v);  // {first tuple, tuples, output row, chunk slot or -1}
+        const int n = m.y > 0 ? m.y : 0;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), cmp = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t0 = 0; t0 < n; t0 += kIdUnroll) {
+            float4 u[kIdUnroll];
+#pragma unroll
+            for (int q = 0; q < kIdUnroll; ++q) {
+                u[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (t0 + q < n) {
+                    const int r = __ldg(hs + m.x + t0 + q);
+                    if (in_bounds(r, z_rows, status)) u[q] = __ldg(z4 + (int64_t)r * L);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kIdUnroll; ++q) {
+                if (t0 + q >= n) break;
+                if (KAHAN) {
+                    kahan_add(acc.x, cmp.x, u[q].x);
+                    kahan_add(acc.y, cmp.y, u[q].y);
+                    kahan_add(acc.z, cmp.z, u[q].z);
+                    kahan_add(acc.w, cmp.w, u[q].w);
+                } else {
+                    acc.x += u[q].x;
+                    acc.y += u[q].y;
+                    acc.z += u[q].z;
+                    acc.w += u[q].w;
+                }
+            }
+        }
+        if (m.w >= 0) {
+            reinterpret_cast<float4*>(vpart + (int64_t)m.w * d)[ch] = acc;
+        } else if (m.z >= 0 && in_bounds(m.z, out_rows, status)) {
+            float4* dst = reinterpret_cast<float4*>(out + (int64_t)m.z * d) + ch;
+            if (accumulate) {
+                const float4 o = *dst;
+                acc = make_float4(o.x + acc.x, o.y + acc.y, o.z + acc.z, o.w + acc.w);
+            }
+            *dst = acc;
+        }
+    }
+}
+
+bool agg_forward_identity_ok(const Plan& p, const CallIO& io, const float* out) {
+    if (p.bf16 || !p.identity || p.act != RELNN_ACT_NONE || p.concat_dst) return false;
+    if (p.flags & (RELNN_FLAG_MAX | RELNN_FLAG_PUSHDOWN | RELNN_FLAG_PER_TUPLE | kPlanDense)) return false;
+    if (p.Hx || p.dense_out || p.acc_out) return false;
+    if (!(p.d == 4 || p.d == 8 || p.d == 16 || p.d == 32 || p.d == 64 || p.d == 128) || p.d_out != p.d) return false;
+    if (io.z_bf16 || !aligned16(io.z) || !aligned16(out)) return false;
+    for (size_t i = 0; i < p.br.size(); ++i)
+        if (p.br[i].d_r > 0) return false;
+    return true;
+}
+
+relnn_status forward_agg_identity(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
+    size_t vp_max = 0;
+    for (auto& b : p.br) {
+        RELNN_TRY(ensure_vrows(b.vr_out, b.seg.as<int32_t>(), b.m, p.n_out, true, st));
+        vp_max = std::max(vp_max, (size_t)(b.vr_out.n_parts + b.vr_out.n_l2) * p.d);
+    }
+    if (vp_max) RELNN_TRY(p.vpart.alloc_nosync(sizeof(float) * vp_max, st));
+    for (size_t i = 0; i < p.br.size(); ++i) {
+        BranchPlan& b = p.br[i];
+        const VRows& V = b.vr_out;
+        if (V.nv == 0) continue;
+        const int G = 32 / (p.d / 4);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(V.nv, 8 * (int64_t)G), (int64_t)num_sms() * 8));
+        const float* z = reinterpret_cast<const float*>(io.z);
+        const int acc = i > 0 ? 1 : 0;  // every branch covers every output row: the first one stores
+        ProfToken pt = prof_begin(RELNN_PROF_FWD_FP32, st);
+        if (p.kahan)
+            fwd_identity_agg_kernel<true><<<grid, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), z, p.n_h, p.d,
+                                                                out, p.n_out, p.vpart.as<float>(), acc, p.status.as<int>());
+        else
+            fwd_identity_agg_kernel<false><<<grid, 256, 0, st>>>(V.vr.as<int4>(), V.nv, b.hs.as<int32_t>(), z, p.n_h, p.d,
+                                                                 out, p.n_out, p.vpart.as<float>(), acc, p.status.as<int>());
+        note_launch();
+        prof_end(pt, st);
+        RELNN_CUDA(cudaGetLastError());
+        RELNN_TRY(agg_fixup(V, p.vpart.as<float>(), p.vpart.as<float>() + (size_t)V.n_parts * p.d, out, p.d, i > 0,
+                            p.kahan, p.n_out, p.status.as<int>(), st));
+    }
+    return RELNN_OK;
+}
+
 relnn_status forward_agg_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st) {
     size_t vp_max = 0;
     for (auto& b : p.br) {

@@ -21,6 +21,11 @@ relnn_status forward_agg(Plan& p, const CallIO& io, float* out, cudaStream_t st)
 // f32 z and W, z / W / out 16-byte aligned, RELNN_FLAG_PER_TUPLE not set, not a streamed chunk.
 bool agg_forward_fp32_ok(const Plan& p, const CallIO& io, const float* out);
 relnn_status forward_agg_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st);
+// FP32 form, identity rules (no Linear, no activation, Concat = z_src only, no per-tuple embedding):
+// the aggregate-first gather-sum for d in {4, 8, 16, 32, 64, 128}, f32 z, z / out 16-byte aligned,
+// RELNN_FLAG_PER_TUPLE not set, not a streamed chunk.
+bool agg_forward_identity_ok(const Plan& p, const CallIO& io, const float* out);
+relnn_status forward_agg_identity(Plan& p, const CallIO& io, float* out, cudaStream_t st);
 relnn_status backward_agg(Plan& p, const CallIO& io, const GradIO& g, cudaStream_t st);
 
 // 2-D bf16 tensor map over a row-major [rows][cols] matrix, box 64 columns x box_rows rows, 128-byte

@@ -533,6 +533,8 @@ relnn_status forward_fp32(Plan& p, const CallIO& io, float* out, cudaStream_t st
     RELNN_CHECK_ARG(p.d_in <= 1024 && p.d_out <= 256, "FP32 form: d_in <= 1024 and d_out <= 256 required");
     // linear rules with narrow rows: the SUM first, then the Linear once per output row (agg.cu)
     if (agg_forward_fp32_ok(p, io, out)) return forward_agg_fp32(p, io, out, st);
+    // identity rules (e.g. a SUM readout): the gather-sum alone
+    if (agg_forward_identity_ok(p, io, out)) return forward_agg_identity(p, io, out, st);
     // several branches add into one output; a stream chunk adds into the stream's accumulator
     const bool multi = p.br.size() > 1 || p.acc_out;
     if (p.br.size() > 1 && !p.acc_out) RELNN_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.n_out * p.d_out, st));

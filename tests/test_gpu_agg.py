@@ -357,3 +357,61 @@ def test_fp32_aggregate_first_forward(gpu, case):
     keys2, out2, _, _ = run_rule(rel, flags=flags | R.FLAG_PER_TUPLE)
     assert np.array_equal(keys, keys2)
     assert rel_frob(out, out2.astype(np.float64)) <= FP32_TOL
+
+
+def _identity_rel(seed, k, groups, d, dst_s=None):
+    """Out(g; SUM z) :- H(k; z), G(k, g): every H row in one group (uniform, or Zipf over the groups)."""
+    rng = np.random.default_rng(seed)
+    h = rng.permutation(k).astype(np.int32)
+    z = rng.standard_normal((k, d)).astype(np.float32)
+    if dst_s is None:
+        g = rng.integers(0, groups, size=k).astype(np.int32)
+    else:
+        g = (rng.zipf(dst_s, size=k) % groups).astype(np.int32)
+    return W.Relations(h_ids=h, z=z, branches=[W.Branch(src=h.copy(), dst=g, W=None, b=None)])
+
+
+@pytest.mark.parametrize("case", ["readout8_d64_kahan", "readout8_d64", "readout_d128", "readout_d4_hubs",
+                                  "join_dst_d32", "union_d16", "mean_d64", "d48_falls_back"])
+def test_fp32_identity_aggregate_first(gpu, case):
+    """Identity rules of the FP32 form (no Linear: a SUM of the src rows per output row, e.g. the SUM
+    readout) take the aggregate-first gather-sum for d in {4, ..., 128}: against the FP64 oracle at
+    the FP32 bar and against the per-tuple FP32 form on the same inputs; key sets and join sizes
+    bit-exact. Covers groups of 25,000 rows (more than 256 chunks: the two-level fix-up), Kahan,
+    hub groups, a joined dst without Concat, a union of branches, MEAN and a width that takes the
+    per-tuple form."""
+    flags, okw, agg = R.FLAG_NO_JOIN_DST, dict(join_dst=False, concat_dst=False), "sum"
+    if case == "readout8_d64_kahan":
+        rel, flags = _identity_rel(170, 200_000, 8, 64), flags | R.FLAG_KAHAN
+    elif case == "readout8_d64":
+        rel = _identity_rel(171, 200_000, 8, 64)
+    elif case == "readout_d128":
+        rel = _identity_rel(172, 100_000, 3000, 128)
+    elif case == "readout_d4_hubs":
+        rel = _identity_rel(173, 150_000, 500, 4, dst_s=1.5)
+    elif case == "join_dst_d32":
+        rel = W.make_rule(174, 60_000, 4000, 32, 32, np.int32, src_dist="zipf", src_s=1.1, dst_dist="zipf", dst_s=1.2)
+        rel.branches[0].W, rel.branches[0].b = None, None
+        flags, okw = R.FLAG_NO_CONCAT_DST, dict(concat_dst=False)
+    elif case == "union_d16":
+        rel = W.make_rule(175, 0, 3000, 16, 16, np.int32, dst_dist="zipf", dst_s=1.0,
+                          branch_tuples=[20_000, 10_000, 5000])
+        for b in rel.branches:
+            b.W, b.b = None, None
+        flags, okw = R.FLAG_NO_CONCAT_DST, dict(concat_dst=False)
+    elif case == "mean_d64":
+        rel, flags, agg = _identity_rel(176, 50_000, 300, 64), flags | R.FLAG_MEAN, "mean"
+    else:
+        rel = _identity_rel(177, 20_000, 100, 48)
+    keys, out, plan, _ = run_rule(rel, flags=flags)
+    if agg == "mean":
+        brs = [OBr(b.src, b.dst, None, None, None) for b in rel.branches]
+        ok, oo, sizes = O.rule_forward(rel.h_ids, rel.z, brs, agg="mean", **okw)
+    else:
+        ok, oo, sizes = oracle_rule(rel, **okw)
+    assert np.array_equal(keys, ok)
+    assert plan.matched == sizes
+    assert rel_frob(out, oo) <= FP32_TOL
+    keys2, out2, _, _ = run_rule(rel, flags=flags | R.FLAG_PER_TUPLE)
+    assert np.array_equal(keys, keys2)
+    assert rel_frob(out, out2.astype(np.float64)) <= FP32_TOL
