@@ -1141,15 +1141,16 @@ def run_relnn(args):
         return e0.elapsed_time(e1) / reps
 
     def measure(wl, steps, warmup):
-        """Device time per step (CUDA events on the launching stream, max over ranks), the library
-        kernels' CUDA-event times, launches and the clocks sampled during the timed region."""
+        """Device time per step (CUDA events on the launching stream, max over ranks), launches and
+        the clocks sampled during the timed region; then the library kernels' CUDA-event times over
+        the same number of steps run again with every profiled launch bracketed by events (those
+        events stay out of the region the step time comes from)."""
         clk = Clocks(local)
         for _ in range(warmup):
             wl.step()
         torch.cuda.synchronize()
         barrier()
-        R.profile_reset()
-        R.profile_enable(True)
+        R.profile_enable(False)
         n0 = R.launch_count()
         torch.cuda.synchronize()
         barrier()
@@ -1163,9 +1164,15 @@ def run_relnn(args):
         tw, te1 = time.perf_counter() - tw0, time.time()
         barrier()
         launches = R.launch_count() - n0
-        R.profile_enable(False)
         clocks = clk.stop(te0, te1)
         ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        # the kernels' durations: the same steps again, each profiled launch between two events
+        R.profile_reset()
+        R.profile_enable(True)
+        for _ in range(steps):
+            keep = wl.step()
+        torch.cuda.synchronize()
+        R.profile_enable(False)
         ks = {kid: R.profile_read(kid) for kid in wl.kernels()}
         plan_ms, plan_n = R.profile_read(R.PROF_PLAN)
         del keep
