@@ -116,8 +116,10 @@ __global__ void bw_dy_kernel(BwArgs a) {
 __global__ void bw_identity_kernel(BwArgs a) {
     const int q = a.d_in / 4;
     const int64_t n = a.m * q;
+    // a row of q 4-feature chunks: the tuple by a shift when q is a power of two (no 64-bit division)
+    const int lq = (q & (q - 1)) == 0 ? __ffs(q) - 1 : -1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / q;
+        const int64_t t = lq >= 0 ? i >> lq : i / q;
         const int k = (int)(i - t * q) * 4;
         const float4 v = *reinterpret_cast<const float4*>(a.dout + (int64_t)a.seg[t] * a.d_out + k);
         if (k < a.d) {
